@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Time-to-D of SP2 density-matrix purification on one GB300.
+
+A step is one full purification F -> D (Gershgorin bounds, scaling, the squaring
+loop with the device-side parameterless stop, output) of the dense workload
+N=8192, nocc=4096: spectrum uniform in [-1,-0.005] U [0.005,1] (gap 0.01) with
+eigenvectors from the QR factor of a seeded Gaussian matrix.  F (512 MiB FP64) is
+resident in HBM before the timed region; every buffer the loop streams is larger
+than the 129 MB L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-D & TFLOP/s, mixed vs FP64 SP2 on 1 GB300 at ||D-D_ref||_F/sqrt(nocc)<=1e-6"
+WORKLOAD = "dense N=8192 nocc=4096 gap=0.01, random-Q (QR of seeded Gaussian, seed 0)"
+N_DEFAULT, NOCC_DEFAULT, GAP_DEFAULT = 8192, 4096, 0.01
+# FP64 runs on the SMs' FP64 FMA pipes: the nominal 1.25 TFLOP/s over 152 SMs at the
+# 2070 MHz maximum clock is 4 flop per clock per SM (2 FMA); the peak is taken at the
+# clock measured during the timed region.
+SMS, FP64_FLOP_PER_CLK_SM, SM_MAX_MHZ = 152, 4.0, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--N", type=int, default=N_DEFAULT)
+    ap.add_argument("--nocc", type=int, default=None)
+    ap.add_argument("--gap", type=float, default=GAP_DEFAULT)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("SP2_BENCH_GLOO") is None else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(F_np, nocc, n_squares_full, budget_s):
+    """Time the CPU oracle on a bounded sample: bounds, scaling and as many
+    iterations (one N^3 matrix product each) as fit in `budget_s`; the full
+    time-to-D is extrapolated linearly to `n_squares_full` products."""
+    import numpy as np
+    from oracle import sp2_oracle as o
+    t0 = time.perf_counter()
+    lmin, lmax = o.gershgorin_bounds(F_np)
+    X = o.initial_scaling(F_np, lmin, lmax)
+    t_setup = time.perf_counter() - t0
+    iters, t_it = 0, 0.0
+    while True:
+        t1 = time.perf_counter()
+        X2 = X @ X
+        v = o.idempotency_error_fro(X, X2)
+        tr = float(np.trace(X))
+        X = X2 if tr > nocc else 2.0 * X - X2
+        t_it += time.perf_counter() - t1
+        iters += 1
+        if t_setup + t_it >= budget_s or iters >= n_squares_full:
+            break
+    del v
+    per = t_it / iters
+    est_ms = (t_setup + per * n_squares_full) * 1e3
+    return est_ms, {"setup_s": t_setup, "iters_timed": iters, "s_per_iter": per}
+
+
+def reference_counts():
+    try:
+        return json.load(open(os.path.join(ROOT, "oracle", "iteration_counts.json")))
+    except Exception:
+        return {}
+
+
+def run_reference(a, ws, rank):
+    """The oracle arm: the CPU FP64 oracle timed on the host cores."""
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+    from paper_1507_02087_gb300 import inputs
+    nocc = a.nocc if a.nocc is not None else a.N // 2
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    case = inputs.dense_gapped(a.N, nocc, gap=a.gap, seed=0, device=dev, want_exact=False)
+    F_np = case.F.cpu().numpy()
+    key = f"dense_N{a.N}_nocc{nocc}_gap{a.gap:g}_seed0"
+    counts = reference_counts().get(key)
+    n_sq = counts["squares"] if counts else 60
+    times = []
+    info = None
+    budget = max(2.0, a.cpu_sample_s / 3)
+    for step in range(a.warmup + a.steps):
+        est, info = oracle_sample(F_np, nocc, n_sq, budget)
+        if step >= a.warmup:
+            times.append(est)
+    ms = statistics.mean(times)
+    flops = a.N * a.N * (a.N + 1) * n_sq
+    cores = os.cpu_count()
+    sample = (f"Gershgorin bounds, scaling and the first {info['iters_timed']} of {n_sq} iterations "
+              f"(one FP64 N^3 product each) per step, extrapolated linearly; squares count "
+              f"{'from oracle/iteration_counts.json' if counts else 'assumed 60'}")
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": a.N, "nocc": nocc, "gap": a.gap,
+                       "precision": "fp64 (CPU oracle, numpy/OpenBLAS)"},
+            "tflops": flops / (ms * 1e-3) / 1e12,
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    ws, rank, local = dist_setup()
+    if a.impl == "reference":
+        run_reference(a, ws, rank)
+        return
+    import numpy as np
+    import torch
+    from paper_1507_02087_gb300 import inputs, sp2
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nocc = a.nocc if a.nocc is not None else a.N // 2
+    N = a.N
+    case = inputs.dense_gapped(N, nocc, gap=a.gap, seed=0, device=dev, want_exact=True)
+    F = case.F.contiguous()
+    D_exact = case.D_exact
+    D = torch.empty_like(F)
+    stream = torch.cuda.current_stream()
+    P = sp2.Purifier(N, nocc, a.precision)
+
+    def err_vs_exact():
+        return float(torch.linalg.norm(D - D_exact)) / math.sqrt(nocc)
+
+    for _ in range(a.warmup):
+        P.run(F, D, stream)
+    torch.cuda.synchronize()
+    info = P.info()
+    err = err_vs_exact()
+
+    clocks = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms, loop_ms, squares = [], [], []
+    for _ in range(a.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.run(F, D, stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        inf = P.info()
+        loop_ms.append(inf["loop_ms"])
+        squares.append(inf["hist_len"])
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = max_over_ranks(statistics.mean(step_ms), ws)
+    info = P.info()
+    err_last = err_vs_exact()
+
+    # algorithmic work: one symmetric square = N^2 (N+1) flops (upper triangle with
+    # the diagonal, N multiply-adds each)
+    flops_sq = N * N * (N + 1)
+    n_sq = statistics.mean(squares)
+    tflops = flops_sq * n_sq / (ms * 1e-3) / 1e12
+    kern_ms = statistics.mean(l / s for l, s in zip(loop_ms, squares))   # square + finalize, per launch
+    mhz = clk.get("sm_mhz") or SM_MAX_MHZ
+    fp64_peak = SMS * FP64_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
+    achieved = flops_sq / (kern_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "syrk_f64_kernel (+finalize)", "achieved": achieved,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "peak_source": f"152 SMs x 4 FP64 flop/clk x {mhz:.0f} MHz (median SM clock under load)",
+                "traffic": None}
+
+    # end to end through the public API with host buffers (copies inside the timed region)
+    e2e_steps = a.e2e_steps if a.e2e_steps is not None else max(1, min(a.steps, 2))
+    F_h = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
+    F_h.copy_(F.cpu())
+    D_h = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
+    F_hn, D_hn = F_h.numpy(), D_h.numpy()
+    P.run_host(F_hn, D_hn, stream)          # warm the staging buffers
+    e2e_ms = []
+    for _ in range(e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.run_host(F_hn, D_hn, stream)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = {"value": max_over_ranks(statistics.mean(e2e_ms), ws), "unit": "ms",
+           "h2d_bytes_per_step": N * N * 8, "d2h_bytes_per_step": N * N * 8}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        F_np = F.cpu().numpy()
+        est, sinfo = oracle_sample(F_np, nocc, int(round(n_sq)), a.cpu_sample_s)
+        cpu = {"value": est, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": (f"CPU FP64 oracle (numpy/OpenBLAS): Gershgorin, scaling and "
+                          f"{sinfo['iters_timed']} of {int(round(n_sq))} iterations at N={N}, "
+                          f"extrapolated linearly ({sinfo['s_per_iter']:.2f} s per iteration)")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": N, "nocc": nocc, "gap": a.gap,
+                           "precision": a.precision, "parallelism": "replicas" if ws > 1 else "1 GPU",
+                           "l2": "no flush: F, X buffers 512 MiB each > 129 MB L2"},
+                "tflops": tflops, "squares": n_sq, "n_iter": info["n_iter"],
+                "stop_reason": info["stop_reason"], "err_vs_exact": err_last, "err_first_run": err,
+                "loop_ms": statistics.mean(loop_ms),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(sum(4 + 2 * s for s in squares)),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    P.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,123 @@
+/*
+ * sp2.h -- C ABI of the GB300 SP2 density-matrix purification library.
+ *
+ * The library turns a symmetric Fock matrix F (N x N) into the density matrix D,
+ * the orthogonal projector onto the eigenvectors of the n_occ smallest eigenvalues
+ * of F (Kruchinina, Rudberg, Rubensson, arXiv:1507.02087, §1, definition of D).
+ * It runs the original SP2 recursive expansion (Alg. 3): X_0 = (lmax I - F) /
+ * (lmax - lmin) with Gershgorin bounds, then X_i = X_{i-1}^2 if Tr[X_{i-1}] > n_occ
+ * and X_i = 2 X_{i-1} - X_{i-1}^2 otherwise, and stops with the paper's parameterless
+ * test on v_i = ||X_i - X_i^2||_F (§2, Frobenius estimate; Alg. 3 stop):
+ *   stop at the first i >= 2 with p_i != p_{i-1}, v_{i-2} < 1 and
+ *   log(v_i / C) / log(v_{i-2}) < qtilde,  C = (71 + 17 sqrt(17)) / 32, qtilde = 1.8.
+ * Two readings where the paper is silent are built in: the order test is only
+ * evaluated when v_{i-2} < 1 (§2 assumes it), and a trace guard stops when the trace
+ * does not move the way the chosen polynomial must move it in exact arithmetic
+ * (reason SP2_STOP_TRACE_GUARD; see sp2_stop_reason).
+ *
+ * Everything is enqueued on the caller's CUDA stream; the stopping test runs on the
+ * device, so a run makes no host synchronisation until sp2_get_info.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are dense, row-major, N x N, leading dimension N, FP64, and F must be
+ *    exactly symmetric (both triangles hold the same value).  "_dev" pointers are
+ *    device memory of the current CUDA device, "_host" pointers host memory.
+ *  - The caller owns F and D.  F is only read.  D may not alias F.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *  - Every function returns an sp2_status; none aborts, traps or prints.  Errors
+ *    found on the device (non-finite input, exhausted wait) surface through
+ *    sp2_get_info's `status`.
+ *  - A handle is not thread-safe: calls on one handle must be serialised by the
+ *    caller, and at most one run per handle may be in flight at a time.
+ */
+#ifndef SP2_H
+#define SP2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SP2_OK = 0,
+  SP2_ERR_INVALID_ARG = 1,  /* bad size, null pointer, aliasing, bad option */
+  SP2_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  SP2_ERR_NONFINITE = 3,    /* F holds a NaN or an infinity (found on the device) */
+  SP2_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+  SP2_ERR_NOMEM = 5,        /* workspace allocation failed */
+  SP2_ERR_NO_GAP = 6,       /* lmax == lmin with 0 < n_occ < N: F = cI has no gap */
+  SP2_ERR_UNSUPPORTED = 7   /* option not available in this build */
+} sp2_status;
+
+/* Why a run stopped (sp2_info.stop_reason). */
+typedef enum {
+  SP2_STOP_ORDER = 0,        /* the paper's convergence-order test fired (Alg. 3) */
+  SP2_STOP_TRACE_GUARD = 1,  /* trace moved the wrong way: rounding dominates */
+  SP2_STOP_EXACT = 2,        /* n_occ in {0, N}, or X exactly idempotent */
+  SP2_STOP_CAP = 3           /* max_iter reached (safety net) */
+} sp2_stop_reason;
+
+/* Arithmetic of the squaring X -> X^2. */
+typedef enum {
+  SP2_PREC_FP64 = 0   /* FP64 products and FP64 everything (the plain method) */
+} sp2_precision;
+
+typedef struct {
+  int32_t max_iter;   /* iteration cap, 1..SP2_MAX_ITER (default 200) */
+  int32_t guard;      /* 1 = trace guard on (default), 0 = paper's test only */
+  double  qtilde;     /* relaxed order, default 1.8 (§2) */
+} sp2_opts;
+
+#define SP2_MAX_ITER 512
+
+typedef struct {
+  int32_t status;          /* sp2_status of the last run (device-side errors) */
+  int32_t n_iter;          /* n: D = X_n */
+  int32_t stop_reason;     /* sp2_stop_reason */
+  int32_t hist_len;        /* entries valid in v[] and trace[] (squares performed) */
+  double  lambda_min;      /* Gershgorin bounds used for the scaling */
+  double  lambda_max;
+  double  loop_ms;         /* device time of the iteration loop of the last run, from CUDA
+                              events recorded on the run's stream around the loop */
+  const double*  v;        /* v[i] = ||X_i - X_i^2||_F, i < hist_len (host memory owned by the handle) */
+  const double*  trace;    /* trace[i] = Tr[X_i], i <= n_iter */
+  const uint8_t* p;        /* p[i] in {0,1} for 1 <= i <= n_iter: 1 = X^2, 0 = 2X - X^2 */
+} sp2_info;
+
+typedef struct sp2_ctx* sp2_handle;
+
+/* Fill `opts` with the defaults (max_iter 200, guard on, qtilde 1.8). */
+void sp2_default_opts(sp2_opts* opts);
+
+/* Create a handle for problems of size N (1 <= N <= 65536) with n_occ occupied
+ * orbitals (0 <= n_occ <= N), allocating its device workspace (two N x N ping-pong
+ * buffers, padded to a multiple of 64, plus history) on the current device.
+ * opts may be NULL for the defaults.  On failure *out is set to NULL. */
+sp2_status sp2_create(int64_t N, int64_t n_occ, int32_t precision, const sp2_opts* opts,
+                      sp2_handle* out);
+
+/* Enqueue one purification F_dev -> D_dev on `stream` (Alg. 3 with the stop above).
+ * Asynchronous: returns after enqueueing; no host synchronisation happens.  On a
+ * device-side error D's contents are unspecified and sp2_get_info reports it. */
+sp2_status sp2_run(sp2_handle h, const double* F_dev, double* D_dev, void* stream);
+
+/* The same with host buffers: copies F_host to the device, runs, copies D back
+ * into D_host and synchronises `stream` before returning.  Pinned host memory gives
+ * the fastest copies; pageable memory works. */
+sp2_status sp2_run_host(sp2_handle h, const double* F_host, double* D_host, void* stream);
+
+/* Wait for the handle's last run to finish and describe it.  The arrays in *out stay
+ * valid until the next run or sp2_destroy. */
+sp2_status sp2_get_info(sp2_handle h, sp2_info* out);
+
+/* Free the handle and its workspace (synchronises the device first).  NULL is a no-op. */
+void sp2_destroy(sp2_handle h);
+
+/* Human-readable name of a status code (static storage). */
+const char* sp2_status_string(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SP2_H */

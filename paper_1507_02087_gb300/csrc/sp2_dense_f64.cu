@@ -1,0 +1,340 @@
+// FP64 dense SP2 path: Gershgorin bounds, the initial scaling, the symmetric
+// squaring with its fused polynomial epilogue, the device-side stop test and the
+// output copy (Alg. 3 of Kruchinina, Rudberg, Rubensson, arXiv:1507.02087).
+//
+// Data layout: the two ping-pong buffers hold X_{i-1} and X_i as ld x ld FP64
+// row-major matrices, ld = N rounded up to a multiple of 64, with a zero border.
+// The border stays zero through the iteration (0^2 = 0 and 2*0 - 0 = 0), so the
+// squaring works on whole 64 x 64 tiles with no bounds checks.
+#include "sp2_common.cuh"
+#include "sp2_kernels.h"
+
+namespace sp2 {
+
+// ---- Gershgorin bounds (a1) ------------------------------------------------------------
+// One warp per row: lo_i = F_ii - sum_{j != i} |F_ij|, hi_i = F_ii + sum_{j != i} |F_ij|.
+// Each block keeps the min / max over its rows; the init kernel combines blocks.
+constexpr int kGershThreads = 256;
+
+__global__ void __launch_bounds__(kGershThreads)
+gershgorin_kernel(const double* __restrict__ F, int64_t ldf, int N, double* __restrict__ part_lo,
+                  double* __restrict__ part_hi, int* __restrict__ part_bad) {
+  __shared__ double s_lo[kGershThreads / 32], s_hi[kGershThreads / 32];
+  __shared__ int s_bad[kGershThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warps_total = gridDim.x * (kGershThreads / 32);
+  double lo = INFINITY, hi = -INFINITY;
+  int bad = 0;
+  for (int i = blockIdx.x * (kGershThreads / 32) + warp; i < N; i += warps_total) {
+    const double* row = F + (int64_t)i * ldf;
+    double r = 0.0;
+    for (int j = lane; j < N; j += 32) {
+      double a = row[j];
+      if (j != i) r += fabs(a);
+      if (!isfinite(a)) bad = 1;
+    }
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    const double d = row[i];
+    lo = fmin(lo, d - r);
+    hi = fmax(hi, d + r);
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) { s_lo[warp] = lo; s_hi[warp] = hi; s_bad[warp] = bad; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kGershThreads / 32; ++w) {
+      s_lo[0] = fmin(s_lo[0], s_lo[w]);
+      s_hi[0] = fmax(s_hi[0], s_hi[w]);
+      s_bad[0] |= s_bad[w];
+    }
+    part_lo[blockIdx.x] = s_lo[0];
+    part_hi[blockIdx.x] = s_hi[0];
+    part_bad[blockIdx.x] = s_bad[0];
+  }
+}
+
+// ---- run initialisation: bounds, special cases, Tr[X_0] -------------------------------
+constexpr int kInitThreads = 1024;
+
+__global__ void __launch_bounds__(kInitThreads)
+init_kernel(DevState* st, const double* __restrict__ F, int64_t ldf, const double* __restrict__ part_lo,
+            const double* __restrict__ part_hi, const int* __restrict__ part_bad, int nparts) {
+  __shared__ double sm[32];
+  __shared__ double s_lmin, s_lmax;
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) {
+    double lo = INFINITY, hi = -INFINITY;
+    int bad = 0;
+    for (int b = 0; b < nparts; ++b) {
+      lo = fmin(lo, part_lo[b]);
+      hi = fmax(hi, part_hi[b]);
+      bad |= part_bad[b];
+    }
+    if (!isfinite(lo) || !isfinite(hi)) bad = 1;
+    s_lmin = lo; s_lmax = hi; s_bad = bad;
+  }
+  __syncthreads();
+  const double lmin = s_lmin, lmax = s_lmax;
+  const int N = st->N, nocc = st->nocc;
+  // Tr[X_0] over the stored diagonal, each entry rounded exactly as the scaling kernel
+  // rounds it.
+  double t = 0.0;
+  const double w = lmax - lmin;
+  for (int i = threadIdx.x; i < N; i += kInitThreads) t += (lmax - F[(int64_t)i * ldf + i]) / w;
+  t = block_sum<kInitThreads>(t, sm);
+  if (threadIdx.x == 0) {
+    st->lmin = lmin; st->lmax = lmax;
+    st->k = 0; st->done = 0; st->n_out = 0; st->reason = SP2_STOP_EXACT;
+    st->status = SP2_OK; st->out_buf = 0; st->out_mode = OUT_COPY; st->hist_len = 0;
+    st->tr[0] = 0.0; st->p[0] = 0;
+    if (s_bad) {
+      st->status = SP2_ERR_NONFINITE; st->done = 1; st->out_mode = OUT_NAN;
+    } else if (nocc == 0) {
+      st->done = 1; st->out_mode = OUT_ZERO;
+    } else if (nocc == N) {
+      st->done = 1; st->out_mode = OUT_IDENTITY;
+    } else if (!(lmax > lmin)) {
+      st->status = SP2_ERR_NO_GAP; st->done = 1; st->out_mode = OUT_NAN;
+    } else {
+      st->tr[0] = t;
+    }
+  }
+}
+
+// ---- initial scaling X_0 = (lmax I - F) / (lmax - lmin) (a2) -------------------------
+__global__ void scale_kernel(const DevState* st, const double* __restrict__ F, int64_t ldf,
+                             double* __restrict__ X0, int ld) {
+  if (st->done) return;
+  const int N = st->N;
+  const double lmax = st->lmax, w = st->lmax - st->lmin;
+  const int64_t total = (int64_t)N * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    const double f = F[(int64_t)i * ldf + j];
+    X0[(int64_t)i * ld + j] = ((i == j ? lmax : 0.0) - f) / w;
+  }
+}
+
+// ---- symmetric squaring with the fused SP2 epilogue (a3, a4, a5) -----------------------
+// CTA tile 64 x 64 of S = X X^T (= X^2, X symmetric) for an upper tile (I <= J), K in
+// steps of 16 staged through shared memory, 256 threads each owning a 4 x 4 block.
+// Epilogue: X_k = S (p_k = 1) or 2 X - S (p_k = 0) written to the tile and its mirror;
+// the tile's share of ||X_{k-1} - S||_F^2 (off-diagonal tiles count twice) and of
+// Tr[X_k] go to a per-tile slot, summed in a fixed order by the finalize kernel.
+constexpr int kTile = 64, kTK = 16, kSyrkThreads = 256;
+
+__global__ void __launch_bounds__(kSyrkThreads)
+syrk_f64_kernel(const DevState* st, double* buf0, double* buf1, double* __restrict__ part) {
+  if (st->done) return;
+  __shared__ double As[2][kTK][kTile + 1];
+  __shared__ double Bs[2][kTK][kTile + 1];
+  __shared__ double sred[32];
+  const int ld = st->ld;
+  const int T = ld / kTile;
+  const int kprev = st->k;                      // X_{k-1} with k = kprev + 1
+  const double* __restrict__ Xin = (kprev & 1) ? buf1 : buf0;
+  double* __restrict__ Xout = (kprev & 1) ? buf0 : buf1;
+  const int pk = st->tr[kprev] > (double)st->nocc ? 1 : 0;   // Alg. 3 trace test
+
+  int I, J;
+  upper_tile(blockIdx.x, T, I, J);
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+  const int lm = tid >> 4, lk = tid & 15;        // loader: rows lm + 16 j, column lk
+  const double* Arow = Xin + (int64_t)(I * kTile) * ld;
+  const double* Brow = Xin + (int64_t)(J * kTile) * ld;
+
+  double acc[4][4];
+  #pragma unroll
+  for (int r = 0; r < 4; ++r)
+    #pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+
+  double ra[4], rb[4];
+  #pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    ra[j] = Arow[(int64_t)(lm + 16 * j) * ld + lk];
+    rb[j] = Brow[(int64_t)(lm + 16 * j) * ld + lk];
+  }
+  int buf = 0;
+  for (int k0 = 0; k0 < ld; k0 += kTK) {
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      As[buf][lk][lm + 16 * j] = ra[j];
+      Bs[buf][lk][lm + 16 * j] = rb[j];
+    }
+    __syncthreads();
+    if (k0 + kTK < ld) {
+      #pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        ra[j] = Arow[(int64_t)(lm + 16 * j) * ld + k0 + kTK + lk];
+        rb[j] = Brow[(int64_t)(lm + 16 * j) * ld + k0 + kTK + lk];
+      }
+    }
+    #pragma unroll
+    for (int kk = 0; kk < kTK; ++kk) {
+      double a[4], b[4];
+      #pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[buf][kk][ty * 4 + r];
+      #pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[buf][kk][tx * 4 + c];
+      #pragma unroll
+      for (int r = 0; r < 4; ++r)
+        #pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    buf ^= 1;
+  }
+
+  double v2 = 0.0, trace = 0.0;
+  #pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int gi = I * kTile + ty * 4 + r;
+    #pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int gj = J * kTile + tx * 4 + c;
+      const double x = Xin[(int64_t)gi * ld + gj];
+      const double s = acc[r][c];
+      const double d = x - s;
+      v2 = fma(d, d, v2);
+      const double xn = pk ? s : (2.0 * x - s);
+      Xout[(int64_t)gi * ld + gj] = xn;
+      if (I != J) Xout[(int64_t)gj * ld + gi] = xn;
+      if (gi == gj) trace += xn;
+    }
+  }
+  if (I != J) v2 *= 2.0;
+  v2 = block_sum<kSyrkThreads>(v2, sred);
+  trace = block_sum<kSyrkThreads>(trace, sred);
+  if (tid == 0) {
+    part[2 * blockIdx.x] = v2;
+    part[2 * blockIdx.x + 1] = trace;
+  }
+}
+
+// ---- per-iteration reduction and stop test (a5 reductions, a7) ----------------------------
+constexpr int kFinThreads = 1024;
+
+__global__ void __launch_bounds__(kFinThreads)
+finalize_kernel(DevState* st, const double* __restrict__ part, int ntiles,
+                cudaGraphConditionalHandle cond) {
+  __shared__ double sm[32];
+  if (st->done) {
+    if (threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+    return;
+  }
+  double v2 = 0.0, tr = 0.0;
+  for (int t = threadIdx.x; t < ntiles; t += kFinThreads) {
+    v2 += part[2 * t];
+    tr += part[2 * t + 1];
+  }
+  v2 = block_sum<kFinThreads>(v2, sm);
+  tr = block_sum<kFinThreads>(tr, sm);
+  if (threadIdx.x != 0) return;
+
+  const int k = st->k + 1;                       // the square just completed
+  const int pk = st->tr[k - 1] > (double)st->nocc ? 1 : 0;
+  st->v[k - 1] = sqrt(v2);                       // v_{k-1} = ||X_{k-1} - X_{k-1}^2||_F
+  st->tr[k] = tr;                                // Tr[X_k]
+  st->p[k] = (uint8_t)pk;
+  st->k = k;
+  st->hist_len = k;
+
+  bool stop = true;
+  const int i = k - 1;
+  if (!isfinite(v2) || !isfinite(tr)) {
+    st->status = SP2_ERR_NONFINITE; st->out_mode = OUT_NAN; st->n_out = i;
+  } else if (k == 1 && st->v[0] == 0.0) {
+    st->reason = SP2_STOP_EXACT; st->n_out = 0; st->out_buf = 0;
+  } else if (i >= 2 && st->p[i] != st->p[i - 1] && order_test_stops(st->v[i], st->v[i - 2], st->qtilde)) {
+    st->reason = SP2_STOP_ORDER; st->n_out = i; st->out_buf = i & 1;
+  } else if (i >= st->max_iter) {
+    st->reason = SP2_STOP_CAP; st->n_out = i; st->out_buf = i & 1;
+  } else if (st->guard && ((pk == 1 && tr >= st->tr[k - 1]) || (pk == 0 && tr <= st->tr[k - 1]))) {
+    st->reason = SP2_STOP_TRACE_GUARD; st->n_out = k; st->out_buf = k & 1;
+  } else {
+    stop = false;
+  }
+  if (stop) {
+    st->done = 1;
+    cudaGraphSetConditional(cond, 0);
+  }
+}
+
+// ---- output -----------------------------------------------------------------------------
+__global__ void copy_out_kernel(const DevState* st, const double* __restrict__ buf0,
+                                const double* __restrict__ buf1, int ld, double* __restrict__ D,
+                                int64_t ldd) {
+  const int N = st->N;
+  const int mode = st->out_mode;
+  const double* __restrict__ X = st->out_buf ? buf1 : buf0;
+  const int64_t total = (int64_t)N * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    double val;
+    if (mode == OUT_COPY) val = X[(int64_t)i * ld + j];
+    else if (mode == OUT_ZERO) val = 0.0;
+    else if (mode == OUT_IDENTITY) val = (i == j) ? 1.0 : 0.0;
+    else val = __longlong_as_double(0x7ff8000000000000ll);
+    D[(int64_t)i * ldd + j] = val;
+  }
+}
+
+// ---- host-side launchers ------------------------------------------------------------------
+static int elementwise_blocks(int64_t total) {
+  int64_t b = (total + 255) / 256;
+  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+cudaError_t launch_bounds_and_init(DevState* st, const double* F, int64_t ldf, int N,
+                                   double* part_lo, double* part_hi, int* part_bad, int nparts,
+                                   cudaStream_t s) {
+  gershgorin_kernel<<<nparts, kGershThreads, 0, s>>>(F, ldf, N, part_lo, part_hi, part_bad);
+  init_kernel<<<1, kInitThreads, 0, s>>>(st, F, ldf, part_lo, part_hi, part_bad, nparts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_f64(const DevState* st, const double* F, int64_t ldf, int N, double* X0,
+                             int ld, cudaStream_t s) {
+  scale_kernel<<<elementwise_blocks((int64_t)N * N), 256, 0, s>>>(st, F, ldf, X0, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t add_f64_loop_body(cudaGraph_t body, DevState* st, double* buf0, double* buf1, double* part,
+                              int T, cudaGraphConditionalHandle cond) {
+  const int ntiles = T * (T + 1) / 2;
+  cudaGraphNode_t n_sq, n_fin;
+  {
+    void* args[] = {&st, &buf0, &buf1, &part};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)syrk_f64_kernel;
+    kp.gridDim = dim3(ntiles);
+    kp.blockDim = dim3(kSyrkThreads);
+    kp.kernelParams = args;
+    cudaError_t e = cudaGraphAddKernelNode(&n_sq, body, nullptr, 0, &kp);
+    if (e != cudaSuccess) return e;
+  }
+  {
+    int nt = ntiles;
+    void* args[] = {&st, &part, &nt, &cond};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)finalize_kernel;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(kFinThreads);
+    kp.kernelParams = args;
+    cudaError_t e = cudaGraphAddKernelNode(&n_fin, body, &n_sq, 1, &kp);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_copy_out(const DevState* st, const double* buf0, const double* buf1, int ld, int N,
+                            double* D, int64_t ldd, cudaStream_t s) {
+  copy_out_kernel<<<elementwise_blocks((int64_t)N * N), 256, 0, s>>>(st, buf0, buf1, ld, D, ldd);
+  return cudaGetLastError();
+}
+
+}  // namespace sp2

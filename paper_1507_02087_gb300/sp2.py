@@ -1,0 +1,170 @@
+"""Python binding of the C ABI in include/sp2.h (argument marshalling only).
+
+Every step of the purification runs in libsp2.so's CUDA kernels; this module only
+passes torch/numpy buffer addresses and CUDA stream handles through ctypes.  If the
+library has not been built the first call raises: there is no CPU fallback.
+
+The functions keep the C names (sp2_create, sp2_run, sp2_run_host, sp2_get_info,
+sp2_destroy); `Purifier` wraps one handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsp2.so")
+
+SP2_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA runtime error", 3: "non-finite value in F",
+          4: "device-side wait timed out", 5: "out of device memory", 6: "no gap (F = cI)",
+          7: "unsupported option"}
+STOP_ORDER, STOP_TRACE_GUARD, STOP_EXACT, STOP_CAP = 0, 1, 2, 3
+PRECISIONS = {"fp64": 0}
+MAX_ITER = 512
+
+
+class SP2Error(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, 'unknown')} (status {code})")
+        self.code = code
+
+
+class sp2_opts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("guard", ctypes.c_int32), ("qtilde", ctypes.c_double)]
+
+
+class sp2_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_iter", ctypes.c_int32), ("stop_reason", ctypes.c_int32),
+                ("hist_len", ctypes.c_int32), ("lambda_min", ctypes.c_double),
+                ("lambda_max", ctypes.c_double), ("loop_ms", ctypes.c_double), ("v", ctypes.POINTER(ctypes.c_double)),
+                ("trace", ctypes.POINTER(ctypes.c_double)), ("p", ctypes.POINTER(ctypes.c_uint8))]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsp2.so (built in-tree by paper_1507_02087_gb300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run `python -m paper_1507_02087_gb300.build` "
+                               "(the SP2 path has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.sp2_default_opts.argtypes = [ctypes.POINTER(sp2_opts)]
+        L.sp2_default_opts.restype = None
+        L.sp2_create.argtypes = [i64, i64, i32, ctypes.POINTER(sp2_opts), ctypes.POINTER(vp)]
+        L.sp2_create.restype = i32
+        L.sp2_run.argtypes = [vp, vp, vp, vp]
+        L.sp2_run.restype = i32
+        L.sp2_run_host.argtypes = [vp, vp, vp, vp]
+        L.sp2_run_host.restype = i32
+        L.sp2_get_info.argtypes = [vp, ctypes.POINTER(sp2_info)]
+        L.sp2_get_info.restype = i32
+        L.sp2_destroy.argtypes = [vp]
+        L.sp2_destroy.restype = None
+        L.sp2_status_string.argtypes = [i32]
+        L.sp2_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != SP2_OK:
+        raise SP2Error(code, where)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def sp2_create(N: int, nocc: int, precision: str = "fp64", *, max_iter: int = 200, guard: bool = True,
+               qtilde: float = 1.8) -> int:
+    o = sp2_opts(max_iter, 1 if guard else 0, qtilde)
+    h = ctypes.c_void_p()
+    _check(lib().sp2_create(N, nocc, PRECISIONS[precision], ctypes.byref(o), ctypes.byref(h)), "sp2_create")
+    return h.value
+
+
+def sp2_run(h: int, F, D, stream=None) -> None:
+    """Enqueue F -> D (torch CUDA float64 tensors, contiguous N x N) on `stream`."""
+    _check(lib().sp2_run(h, F.data_ptr(), D.data_ptr(), _stream_ptr(stream)), "sp2_run")
+
+
+def sp2_run_host(h: int, F: np.ndarray, D: np.ndarray, stream=None) -> None:
+    """Host buffers in and out (copies inside the call); returns when D is written."""
+    _check(lib().sp2_run_host(h, F.ctypes.data, D.ctypes.data, _stream_ptr(stream)), "sp2_run_host")
+
+
+def sp2_get_info(h: int) -> dict:
+    info = sp2_info()
+    _check(lib().sp2_get_info(h, ctypes.byref(info)), "sp2_get_info")
+    n, hl = info.n_iter, info.hist_len
+    return {
+        "status": info.status,
+        "n_iter": n,
+        "stop_reason": info.stop_reason,
+        "hist_len": hl,
+        "lambda_min": info.lambda_min,
+        "lambda_max": info.lambda_max,
+        "loop_ms": info.loop_ms,
+        "v": np.ctypeslib.as_array(info.v, shape=(MAX_ITER + 2,))[:hl].copy(),
+        "trace": np.ctypeslib.as_array(info.trace, shape=(MAX_ITER + 2,))[:hl + 1].copy(),
+        "p": np.ctypeslib.as_array(info.p, shape=(MAX_ITER + 2,))[:hl + 1].copy(),
+    }
+
+
+def sp2_destroy(h: int) -> None:
+    if h:
+        lib().sp2_destroy(h)
+
+
+class Purifier:
+    """One handle: F (N x N, symmetric, float64) -> density matrix D."""
+
+    def __init__(self, N: int, nocc: int, precision: str = "fp64", **opts):
+        self.N, self.nocc, self.precision = N, nocc, precision
+        self.h = sp2_create(N, nocc, precision, **opts)
+
+    def run(self, F, D=None, stream=None):
+        import torch
+        if F.dtype != torch.float64 or not F.is_cuda or not F.is_contiguous() or F.shape != (self.N, self.N):
+            raise ValueError("F must be a contiguous CUDA float64 tensor of shape (N, N)")
+        if D is None:
+            D = torch.empty_like(F)
+        sp2_run(self.h, F, D, stream)
+        return D
+
+    def run_host(self, F: np.ndarray, D: np.ndarray | None = None, stream=None) -> np.ndarray:
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        if D is None:
+            D = np.empty_like(F)
+        sp2_run_host(self.h, F, D, stream)
+        return D
+
+    def info(self) -> dict:
+        return sp2_get_info(self.h)
+
+    def close(self):
+        sp2_destroy(self.h)
+        self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.h:
+                self.close()
+        except Exception:
+            pass

@@ -1,0 +1,149 @@
+"""Parity of the FP64 GPU path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerance: ||D - D_oracle||_F / sqrt(nocc) <= 1e-10 and the stopping iteration
+within +-1 of the oracle's.  Both sides compute in FP64 but sum in different
+orders, so the histories agree to rounding until the stagnation floor.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import sp2_oracle as o
+from paper_1507_02087_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL_FP64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def sp2mod():
+    from paper_1507_02087_gb300 import sp2
+    sp2.lib()
+    return sp2
+
+
+def run_gpu(sp2mod, F_np, nocc, **opts):
+    N = F_np.shape[0]
+    F = torch.from_numpy(np.ascontiguousarray(F_np)).cuda()
+    with sp2mod.Purifier(N, nocc, "fp64", **opts) as P:
+        D = P.run(F)
+        info = P.info()
+    return D.cpu().numpy(), info
+
+
+def compare_with_oracle(D, info, res, nocc, tol=TOL_FP64):
+    assert info["status"] == 0
+    assert abs(info["n_iter"] - res.n) <= 1, (info["n_iter"], res.n)
+    assert o.rel_error(D, res.D, nocc) <= tol
+    m = min(info["n_iter"], res.n)
+    assert list(info["p"][1:m + 1]) == list(res.p[1:m + 1])
+    # history agrees to rounding while far above the floor
+    for i in range(min(len(info["v"]), len(res.v))):
+        if res.v[i] > 1e-6:
+            assert info["v"][i] == pytest.approx(res.v[i], rel=1e-8)
+    assert info["lambda_min"] == pytest.approx(res.lmin, rel=1e-13)
+    assert info["lambda_max"] == pytest.approx(res.lmax, rel=1e-13)
+
+
+@pytest.mark.parametrize("N,nocc,gap", [(2, 1, 0.2), (3, 2, 0.2), (17, 9, 0.1), (64, 32, 0.1),
+                                         (65, 20, 0.05), (129, 64, 0.1), (200, 150, 0.02)])
+def test_dense_parity_small(sp2mod, N, nocc, gap):
+    case = inputs.dense_gapped(N, nocc, gap=gap, seed=N)
+    F = case.F.numpy()
+    res = o.sp2(F, nocc)
+    D, info = run_gpu(sp2mod, F, nocc)
+    compare_with_oracle(D, info, res, nocc)
+    assert o.rel_error(D, case.D_exact.numpy(), nocc) <= TOL_FP64
+
+
+def test_dense_n400(sp2mod):
+    case = inputs.dense_n400()
+    F = case.F.numpy()
+    res = o.sp2(F, case.nocc)
+    D, info = run_gpu(sp2mod, F, case.nocc)
+    compare_with_oracle(D, info, res, case.nocc)
+    assert info["stop_reason"] == o.STOP_ORDER
+
+
+def test_dense_n1500_several_tiles_ragged(sp2mod):
+    # 1500 = 23 full 64-tiles + a ragged tail of 28
+    case = inputs.dense_gapped(1500, 700, gap=0.05, seed=5)
+    F = case.F.numpy()
+    res = o.sp2(F, case.nocc)
+    D, info = run_gpu(sp2mod, F, case.nocc)
+    compare_with_oracle(D, info, res, case.nocc)
+
+
+def test_diagonal_matches_scalar_recursion(sp2mod):
+    g = np.random.Generator(np.random.PCG64(3))
+    N, nocc = 100, 41
+    lam = np.concatenate([g.uniform(-1, -0.02, nocc), g.uniform(0.03, 1.0, N - nocc)])
+    g.shuffle(lam)
+    D, info = run_gpu(sp2mod, np.diag(lam), nocc)
+    lo, hi = o.gershgorin_bounds(np.diag(lam))
+    xs, n, reason, v, tr, p = o.sp2_scalar(lam, nocc, lo, hi)
+    assert (info["n_iter"], info["stop_reason"]) == (n, reason)
+    assert list(info["p"][1:n + 1]) == p[1:]
+    assert np.array_equal(np.diag(D), np.array(xs))       # squares of a diagonal are exact
+    assert np.count_nonzero(D - np.diag(np.diag(D))) == 0
+
+
+def test_trivial_occupations_and_n1(sp2mod):
+    F = np.diag([0.3, -0.2, 0.1, 0.7])
+    D, info = run_gpu(sp2mod, F, 0)
+    assert info["stop_reason"] == o.STOP_EXACT and np.array_equal(D, np.zeros((4, 4)))
+    D, info = run_gpu(sp2mod, F, 4)
+    assert info["stop_reason"] == o.STOP_EXACT and np.array_equal(D, np.eye(4))
+    D, info = run_gpu(sp2mod, np.array([[2.5]]), 1)
+    assert np.array_equal(D, np.ones((1, 1)))
+
+
+def test_errors_reported_not_faulted(sp2mod):
+    F = inputs.dense_gapped(40, 20, gap=0.1, seed=1).F.numpy().copy()
+    F[3, 5] = F[5, 3] = np.nan
+    D, info = run_gpu(sp2mod, F, 20)
+    assert info["status"] == 3 and np.isnan(D).all()
+    F[3, 5] = F[5, 3] = np.inf
+    D, info = run_gpu(sp2mod, F, 20)
+    assert info["status"] == 3
+    D, info = run_gpu(sp2mod, 2.0 * np.eye(8), 4)
+    assert info["status"] == 6
+    with pytest.raises(sp2mod.SP2Error):
+        sp2mod.Purifier(8, 9)
+
+
+def test_cap_and_guard_options(sp2mod):
+    case = inputs.dense_gapped(96, 48, gap=0.05, seed=9)
+    F = case.F.numpy()
+    D, info = run_gpu(sp2mod, F, 48, max_iter=5)
+    res = o.sp2(F, 48, max_iter=5)
+    assert info["stop_reason"] == o.STOP_CAP == res.stop_reason and info["n_iter"] == 5
+    assert o.rel_error(D, res.D, 48) <= 1e-12
+    D, info = run_gpu(sp2mod, F, 48, guard=False)
+    res = o.sp2(F, 48, guard=False)
+    compare_with_oracle(D, info, res, 48)
+
+
+def test_handle_reuse_and_host_entry(sp2mod):
+    case = inputs.dense_gapped(300, 120, gap=0.1, seed=4)
+    F = case.F.numpy()
+    res = o.sp2(F, 120)
+    with sp2mod.Purifier(300, 120) as P:
+        D1 = P.run(torch.from_numpy(F).cuda()).cpu().numpy()
+        i1 = P.info()
+        D2 = P.run_host(F)
+        i2 = P.info()
+    assert np.array_equal(D1, D2)        # deterministic: same reduction order every run
+    assert i1["n_iter"] == i2["n_iter"]
+    compare_with_oracle(D2, i2, res, 120)
+
+
+def test_dense_n2048_against_oracle(sp2mod):
+    case = inputs.dense_gapped(2048, 1024, gap=0.01, seed=0)
+    F = case.F.numpy()
+    res = o.sp2(F, 1024)
+    D, info = run_gpu(sp2mod, F, 1024)
+    compare_with_oracle(D, info, res, 1024)
+    assert o.rel_error(D, case.D_exact.numpy(), 1024) <= TOL_FP64
