@@ -1,12 +1,15 @@
 #!/usr/bin/env python
 """Time-to-D of SP2 density-matrix purification on one GB300.
 
-A step is one full purification F -> D (Gershgorin bounds, scaling, the squaring
-loop with the device-side parameterless stop, output) of the dense workload
-N=8192, nocc=4096: spectrum uniform in [-1,-0.005] U [0.005,1] (gap 0.01) with
-eigenvectors from the QR factor of a seeded Gaussian matrix.  F (512 MiB FP64) is
-resident in HBM before the timed region; every buffer the loop streams is larger
-than the 129 MB L2, so no flush is needed between steps.
+A step is one full purification F -> D of the dense workload N=8192, nocc=4096:
+spectrum uniform in [-1,-0.005] U [0.005,1] (gap 0.01) with eigenvectors from the QR
+factor of a seeded Gaussian matrix.  The timed path is the mixed-precision one
+(Gershgorin bounds, scaling, tensor-core squares with the device-side parameterless
+stop, the F-driven subspace correction and a refinement pair), whose result must
+be within ||D - D_exact||_F / sqrt(nocc) <= 1e-6 of the exact projector; the plain
+FP64 path is timed beside it for the comparison.  F (512 MiB FP64) is resident in
+HBM before the timed region; every buffer the loop streams is larger than the
+129 MB L2, so no flush is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line (rank 0).
@@ -27,25 +30,30 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time-to-D & TFLOP/s, mixed vs FP64 SP2 on 1 GB300 at ||D-D_ref||_F/sqrt(nocc)<=1e-6"
-WORKLOAD = "dense N=8192 nocc=4096 gap=0.01, random-Q (QR of seeded Gaussian, seed 0)"
-N_DEFAULT, NOCC_DEFAULT, GAP_DEFAULT = 8192, 4096, 0.01
-# FP64 runs on the SMs' FP64 FMA pipes: the nominal 1.25 TFLOP/s over 152 SMs at the
-# 2070 MHz maximum clock is 4 flop per clock per SM (2 FMA); the peak is taken at the
-# clock measured during the timed region.
+N_DEFAULT, GAP_DEFAULT = 8192, 0.01
+TOL = 1e-6
+# FP64 runs on the SMs' FP64 pipes: the nominal 1.25 TFLOP/s over 152 SMs at the
+# 2070 MHz maximum clock is 4 flop per clock per SM; taken at the measured clock.
 SMS, FP64_FLOP_PER_CLK_SM, SM_MAX_MHZ = 152, 4.0, 2070.0
+SPLIT_PRODUCTS = 6   # bf16 piece products per FP32-grade product on the tensor cores
+
+
+def workload_name(N, nocc, gap):
+    return f"dense N={N} nocc={nocc} gap={gap:g}, random-Q (QR of seeded Gaussian, seed 0)"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--N", type=int, default=N_DEFAULT)
     ap.add_argument("--nocc", type=int, default=None)
     ap.add_argument("--gap", type=float, default=GAP_DEFAULT)
-    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed runs of the FP64 path (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     return ap.parse_args()
@@ -88,7 +96,7 @@ class ClockSampler:
             self.p.kill()
         self.f.flush()
         self.f.seek(0)
-        sm, smax, reasons = [], None, set()
+        sm, smax, power, reasons = [], None, [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.f.read().splitlines():
             parts = [x.strip() for x in line.split(",")]
@@ -97,6 +105,7 @@ class ClockSampler:
             try:
                 sm.append(float(parts[1]))
                 smax = float(parts[2])
+                power.append(float(parts[3]))
             except ValueError:
                 continue
             for nm, val in zip(names, parts[5:9]):
@@ -104,7 +113,7 @@ class ClockSampler:
                     reasons.add(nm)
         os.unlink(self.f.name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def dist_setup():
@@ -134,9 +143,9 @@ def max_over_ranks(x: float, ws: int) -> float:
 
 
 def oracle_sample(F_np, nocc, n_squares_full, budget_s):
-    """Time the CPU oracle on a bounded sample: bounds, scaling and as many
-    iterations (one N^3 matrix product each) as fit in `budget_s`; the full
-    time-to-D is extrapolated linearly to `n_squares_full` products."""
+    """Time the CPU oracle on a bounded sample: bounds, scaling and as many iterations
+    (one N^3 matrix product each) as fit in `budget_s`; the full time-to-D is
+    extrapolated linearly to `n_squares_full` products."""
     import numpy as np
     from oracle import sp2_oracle as o
     t0 = time.perf_counter()
@@ -147,62 +156,69 @@ def oracle_sample(F_np, nocc, n_squares_full, budget_s):
     while True:
         t1 = time.perf_counter()
         X2 = X @ X
-        v = o.idempotency_error_fro(X, X2)
+        o.idempotency_error_fro(X, X2)
         tr = float(np.trace(X))
         X = X2 if tr > nocc else 2.0 * X - X2
         t_it += time.perf_counter() - t1
         iters += 1
         if t_setup + t_it >= budget_s or iters >= n_squares_full:
             break
-    del v
     per = t_it / iters
     est_ms = (t_setup + per * n_squares_full) * 1e3
     return est_ms, {"setup_s": t_setup, "iters_timed": iters, "s_per_iter": per}
 
 
-def reference_counts():
+def oracle_squares(N, nocc, gap):
     try:
-        return json.load(open(os.path.join(ROOT, "oracle", "iteration_counts.json")))
+        data = json.load(open(os.path.join(ROOT, "oracle", "iteration_counts.json")))
+        return data[f"dense_N{N}_nocc{nocc}_gap{gap:g}_seed0"]["squares"]
     except Exception:
-        return {}
+        return None
 
 
 def run_reference(a, ws, rank):
-    """The oracle arm: the CPU FP64 oracle timed on the host cores."""
+    """The oracle arm: the CPU FP64 oracle, as it stands, timed on the host cores."""
     if rank != 0:
         return
-    import numpy as np
     import torch
     from paper_1507_02087_gb300 import inputs
     nocc = a.nocc if a.nocc is not None else a.N // 2
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     case = inputs.dense_gapped(a.N, nocc, gap=a.gap, seed=0, device=dev, want_exact=False)
     F_np = case.F.cpu().numpy()
-    key = f"dense_N{a.N}_nocc{nocc}_gap{a.gap:g}_seed0"
-    counts = reference_counts().get(key)
-    n_sq = counts["squares"] if counts else 60
-    times = []
-    info = None
+    n_sq = oracle_squares(a.N, nocc, a.gap)
+    known = n_sq is not None
+    n_sq = n_sq or 60
+    times, info = [], None
     budget = max(2.0, a.cpu_sample_s / 3)
     for step in range(a.warmup + a.steps):
         est, info = oracle_sample(F_np, nocc, n_sq, budget)
         if step >= a.warmup:
             times.append(est)
     ms = statistics.mean(times)
-    flops = a.N * a.N * (a.N + 1) * n_sq
-    cores = os.cpu_count()
-    sample = (f"Gershgorin bounds, scaling and the first {info['iters_timed']} of {n_sq} iterations "
-              f"(one FP64 N^3 product each) per step, extrapolated linearly; squares count "
-              f"{'from oracle/iteration_counts.json' if counts else 'assumed 60'}")
+    sample = (f"per step: Gershgorin bounds, scaling and the first {info['iters_timed']} of the oracle's "
+              f"{n_sq} FP64 iterations (one numpy N^3 product each) at N={a.N}, extrapolated linearly; "
+              f"the square count {'comes from a full oracle run (oracle/iteration_counts.json)' if known else 'is assumed'}")
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": a.N, "nocc": nocc, "gap": a.gap,
+            "config": {"workload": workload_name(a.N, nocc, a.gap), "N": a.N, "nocc": nocc, "gap": a.gap,
                        "precision": "fp64 (CPU oracle, numpy/OpenBLAS)"},
-            "tflops": flops / (ms * 1e-3) / 1e12,
-            "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def useful_flops(N, squares, deriv_steps, corrected, refine_steps):
+    """Algorithmic flops of one mixed run, counting each symmetric square as N^2 (N+1)
+    (upper triangle with the diagonal, N multiply-adds each), a general product as 2 N^3."""
+    sq = N * N * (N + 1)
+    f = squares * sq
+    if corrected:
+        f += 2 * N ** 3 + sq + deriv_steps * 2 * sq
+    f += refine_steps * sq
+    return f
 
 
 def main():
@@ -211,7 +227,6 @@ def main():
     if a.impl == "reference":
         run_reference(a, ws, rank)
         return
-    import numpy as np
     import torch
     from paper_1507_02087_gb300 import inputs, sp2
 
@@ -232,14 +247,13 @@ def main():
     for _ in range(a.warmup):
         P.run(F, D, stream)
     torch.cuda.synchronize()
-    info = P.info()
-    err = err_vs_exact()
+    err_first = err_vs_exact()
 
     clocks = ClockSampler(local)
     barrier(ws)
     torch.cuda.synchronize()
     clocks.start()
-    step_ms, loop_ms, squares = [], [], []
+    step_ms, loop_ms, infos = [], [], []
     for _ in range(a.steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -250,37 +264,84 @@ def main():
         step_ms.append(e0.elapsed_time(e1))
         inf = P.info()
         loop_ms.append(inf["loop_ms"])
-        squares.append(inf["hist_len"])
+        infos.append(inf)
     torch.cuda.synchronize()
     barrier(ws)
     clk = clocks.stop()
     ms = max_over_ranks(statistics.mean(step_ms), ws)
-    info = P.info()
-    err_last = err_vs_exact()
+    info = infos[-1]
+    err = err_vs_exact()
+    status_ok = all(i["status"] == 0 for i in infos)
+    mixed = a.precision == "mixed"
+    squares = info["hist_len"]
+    n_iter = info["n_iter"]
+    flops = useful_flops(N, squares, n_iter, mixed, 2 if mixed else 0) if mixed else N * N * (N + 1) * squares
+    tflops = flops / (ms * 1e-3) / 1e12
+    launches_per_step = (3 + 2 * squares + 1) if not mixed else (3 + 2 * squares + 2 + 2 * n_iter + 3 + 1)
 
-    # algorithmic work: one symmetric square = N^2 (N+1) flops (upper triangle with
-    # the diagonal, N multiply-adds each)
-    flops_sq = N * N * (N + 1)
-    n_sq = statistics.mean(squares)
-    tflops = flops_sq * n_sq / (ms * 1e-3) / 1e12
-    kern_ms = statistics.mean(l / s for l, s in zip(loop_ms, squares))   # square + finalize, per launch
-    mhz = clk.get("sm_mhz") or SM_MAX_MHZ
-    fp64_peak = SMS * FP64_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
-    achieved = flops_sq / (kern_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "syrk_f64_kernel (+finalize)", "achieved": achieved,
-                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                "peak_source": f"152 SMs x 4 FP64 flop/clk x {mhz:.0f} MHz (median SM clock under load)",
-                "traffic": None}
+    # roofline of the dominant kernel, timed on its own inside the same device loop:
+    # a forward-only handle runs the square + stop-test loop; loop time / squares is
+    # the average duration of one square launch (plus the few-microsecond stop test).
+    peaks = load_peaks()
+    if mixed:
+        with sp2.Purifier(N, nocc, "mixed", corrections=0, refine_steps=0) as Pf:
+            Pf.run(F, D, stream)
+            kt = []
+            for _ in range(max(1, min(3, a.steps))):
+                Pf.run(F, D, stream)
+                fi = Pf.info()
+                kt.append(fi["loop_ms"] / fi["hist_len"])
+        kern_ms = statistics.mean(kt)
+        alg = SPLIT_PRODUCTS * N * N * (N + 1)        # six bf16 piece products of an upper-triangle square
+        achieved = alg / (kern_ms * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        roofline = {"bound": "tensor", "kernel": "tc_gemm_kernel (forward square, MODE_SP2_STEP)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "ms_per_launch": kern_ms,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
+                    "algorithmic_flops_per_launch": alg, "traffic": None}
+    else:
+        kern_ms = statistics.mean(l / s for l, s in zip(loop_ms, [i["hist_len"] for i in infos]))
+        mhz = clk.get("sm_mhz") or SM_MAX_MHZ
+        peak = SMS * FP64_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
+        alg = N * N * (N + 1)
+        achieved = alg / (kern_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": "syrk_f64_kernel (+finalize)", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "ms_per_launch": kern_ms,
+                    "peak_source": f"152 SMs x 4 FP64 flop/clk x {mhz:.0f} MHz (median SM clock under load)",
+                    "algorithmic_flops_per_launch": alg, "traffic": None}
+
+    # the plain FP64 path, for the comparison the metric asks for
+    fp64 = None
+    if mixed and a.fp64_steps > 0:
+        with sp2.Purifier(N, nocc, "fp64") as P64:
+            D64 = torch.empty_like(F)
+            tms = []
+            for _ in range(a.fp64_steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                P64.run(F, D64, stream)
+                e1.record(stream)
+                e1.synchronize()
+                tms.append(e0.elapsed_time(e1))
+            i64 = P64.info()
+            e64 = float(torch.linalg.norm(D64 - D_exact)) / math.sqrt(nocc)
+            del D64
+        sq64 = i64["hist_len"]
+        fp64 = {"time_to_d_ms": statistics.mean(tms), "steps": a.fp64_steps, "n_iter": i64["n_iter"],
+                "squares": sq64, "err_vs_exact": e64,
+                "tflops": N * N * (N + 1) * sq64 / (statistics.mean(tms) * 1e-3) / 1e12,
+                "speedup_mixed_vs_fp64": statistics.mean(tms) / ms}
 
     # end to end through the public API with host buffers (copies inside the timed region)
-    e2e_steps = a.e2e_steps if a.e2e_steps is not None else max(1, min(a.steps, 2))
     F_h = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
     F_h.copy_(F.cpu())
     D_h = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
     F_hn, D_hn = F_h.numpy(), D_h.numpy()
-    P.run_host(F_hn, D_hn, stream)          # warm the staging buffers
+    P.run_host(F_hn, D_hn, stream)          # allocates the staging buffers once
     e2e_ms = []
-    for _ in range(e2e_steps):
+    for _ in range(max(1, a.e2e_steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         P.run_host(F_hn, D_hn, stream)
@@ -290,26 +351,28 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
-        F_np = F.cpu().numpy()
-        est, sinfo = oracle_sample(F_np, nocc, int(round(n_sq)), a.cpu_sample_s)
+        n_or = oracle_squares(N, nocc, a.gap) or (fp64["squares"] if fp64 else squares)
+        est, sinfo = oracle_sample(F.cpu().numpy(), nocc, n_or, a.cpu_sample_s)
         cpu = {"value": est, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": (f"CPU FP64 oracle (numpy/OpenBLAS): Gershgorin, scaling and "
-                          f"{sinfo['iters_timed']} of {int(round(n_sq))} iterations at N={N}, "
-                          f"extrapolated linearly ({sinfo['s_per_iter']:.2f} s per iteration)")}
+               "sample": (f"CPU FP64 oracle (numpy/OpenBLAS): Gershgorin, scaling and {sinfo['iters_timed']} of "
+                          f"its {n_or} iterations at N={N}, extrapolated linearly "
+                          f"({sinfo['s_per_iter']:.2f} s per iteration)")}
 
     if rank == 0:
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "N": N, "nocc": nocc, "gap": a.gap,
-                           "precision": a.precision, "parallelism": "replicas" if ws > 1 else "1 GPU",
-                           "l2": "no flush: F, X buffers 512 MiB each > 129 MB L2"},
-                "tflops": tflops, "squares": n_sq, "n_iter": info["n_iter"],
-                "stop_reason": info["stop_reason"], "err_vs_exact": err_last, "err_first_run": err,
-                "loop_ms": statistics.mean(loop_ms),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(sum(4 + 2 * s for s in squares)),
-                "clocks": clk}
+                "vs_baseline": None, "dtype": "bf16x6->f32 (mixed), f64 reductions" if mixed else "f64",
+                "data": "synthetic",
+                "config": {"workload": workload_name(N, nocc, a.gap), "N": N, "nocc": nocc, "gap": a.gap,
+                           "precision": a.precision,
+                           "parallelism": "replicas" if ws > 1 else "1 GPU",
+                           "l2": "no flush: F 512 MiB and the streamed iterates exceed the 129 MB L2"},
+                "err_vs_exact": err, "err_first_run": err_first, "meets_tolerance": bool(err <= TOL and status_ok),
+                "tolerance": TOL, "status_ok": status_ok,
+                "tflops_useful": tflops, "squares": squares, "n_iter": n_iter,
+                "stop_reason": info["stop_reason"], "loop_ms": statistics.mean(loop_ms),
+                "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches_per_step * a.steps), "clocks": clk}
         print(json.dumps(line), flush=True)
     P.close()
 

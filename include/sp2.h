@@ -60,13 +60,27 @@ typedef enum {
 
 /* Arithmetic of the squaring X -> X^2. */
 typedef enum {
-  SP2_PREC_FP64 = 0   /* FP64 products and FP64 everything (the plain method) */
+  SP2_PREC_FP64 = 0,  /* FP64 products and FP64 everything (the plain method) */
+  SP2_PREC_MIXED = 1  /* X held as FP32 values, each stored exactly as three bf16
+                         pieces; squares on the tcgen05 tensor cores as the six piece
+                         products with FP32 accumulation; FP64 bounds, reductions and
+                         stop test; then a first-order correction of the occupied
+                         subspace driven by F (see sp2_opts.corrections) and a
+                         refinement pair.  Needs (max_iter + 8) * 6 * ld^2 bytes of
+                         workspace, ld = N rounded up to a multiple of 128. */
 } sp2_precision;
 
 typedef struct {
-  int32_t max_iter;   /* iteration cap, 1..SP2_MAX_ITER (default 200) */
-  int32_t guard;      /* 1 = trace guard on (default), 0 = paper's test only */
-  double  qtilde;     /* relaxed order, default 1.8 (§2) */
+  int32_t max_iter;     /* iteration cap, 1..SP2_MAX_ITER (default 200) */
+  int32_t guard;        /* 1 = trace guard on (default), 0 = paper's test only */
+  double  qtilde;       /* relaxed order, default 1.8 (§2) */
+  int32_t corrections;  /* SP2_PREC_MIXED: first-order subspace corrections, 0 or 1 (default 1) */
+  int32_t refine_steps; /* SP2_PREC_MIXED: purification steps after the correction, 0 or 2 (default 2):
+                           an alternating pair, X^2 and 2X - X^2, which squares the remaining
+                           eigenvalue error */
+  int32_t refine_fp64;  /* SP2_PREC_MIXED: 1 = refinement pair in FP64 (two FP64 squares),
+                           0 = on the tensor cores like the expansion (default 0) */
+  int32_t reserved;     /* must be 0 */
 } sp2_opts;
 
 #define SP2_MAX_ITER 512
@@ -87,13 +101,15 @@ typedef struct {
 
 typedef struct sp2_ctx* sp2_handle;
 
-/* Fill `opts` with the defaults (max_iter 200, guard on, qtilde 1.8). */
+/* Fill `opts` with the defaults (max_iter 200, guard on, qtilde 1.8, 1 correction,
+ * a 2-step refinement pair on the tensor cores). */
 void sp2_default_opts(sp2_opts* opts);
 
 /* Create a handle for problems of size N (1 <= N <= 65536) with n_occ occupied
- * orbitals (0 <= n_occ <= N), allocating its device workspace (two N x N ping-pong
- * buffers, padded to a multiple of 64, plus history) on the current device.
- * opts may be NULL for the defaults.  On failure *out is set to NULL. */
+ * orbitals (0 <= n_occ <= N), allocating its device workspace on the current device:
+ * for SP2_PREC_FP64 two N x N FP64 ping-pong buffers padded to a multiple of 64; for
+ * SP2_PREC_MIXED the piece arena described at SP2_PREC_MIXED.  opts may be NULL for
+ * the defaults.  On failure *out is set to NULL. */
 sp2_status sp2_create(int64_t N, int64_t n_occ, int32_t precision, const sp2_opts* opts,
                       sp2_handle* out);
 

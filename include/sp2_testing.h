@@ -1,0 +1,31 @@
+/*
+ * sp2_testing.h -- internal kernels of libsp2 exposed for unit tests.
+ *
+ * Not part of the purification API; the paper has no counterpart.  These entry
+ * points let tests check the tensor-core matrix product on its own.
+ */
+#ifndef SP2_TESTING_H
+#define SP2_TESTING_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* C = A B^T with the tcgen05 product used by SP2_PREC_MIXED.
+ * `arena_dev`: device buffer of `nslots` slots, each three bf16 planes of ld x ld
+ * (row-major, plane-major), so slot s piece p element (i, j) sits at
+ * ((s * 3 + p) * ld + i) * ld + j.  A is slot a_slot, B is slot b_slot; each
+ * matrix is the sum of its three pieces.  ld must be a positive multiple of 256 and
+ * arena_dev 16-byte aligned.  With upper = 1 only C's upper triangle is computed and
+ * mirrored (meaningful when A B^T is symmetric); with upper = 0 every element is.
+ * out_dev: ld x ld FP32, row-major.  Synchronises `stream`; returns an sp2_status
+ * (SP2_ERR_TIMEOUT if a device-side wait gave up). */
+int32_t sp2_test_tc_gemm(const void* arena_dev, int32_t ld, int32_t nslots, int32_t a_slot, int32_t b_slot,
+                         int32_t upper, float* out_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SP2_TESTING_H */

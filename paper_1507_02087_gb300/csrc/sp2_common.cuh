@@ -44,6 +44,8 @@ struct DevState {
   int32_t out_buf;     // 0 or 1
   int32_t out_mode;    // OutMode
   int32_t hist_len;
+  int32_t dk;          // derivative steps completed (mixed path correction)
+  int32_t round_fp32;  // 1: X_0 is rounded to FP32 (mixed path)
   // history
   double v[SP2_MAX_ITER + 2];
   double tr[SP2_MAX_ITER + 2];
@@ -57,6 +59,38 @@ __device__ __forceinline__ bool order_test_stops(double v_i, double v_im2, doubl
   if (!(v_im2 < 1.0)) return false;
   if (v_i == 0.0) return false;
   return log(v_i / kC2sp) / log(v_im2) < qtilde;
+}
+
+// Records square k = st->k + 1 (v_{k-1}, Tr[X_k], p_k) and applies the stop rules in
+// the order the iteration meets them: the order test for X_{k-1} (Alg. 3, evaluated
+// one square late because v_{k-1} needs X_{k-1}^2), the cap, then the trace guard for
+// X_k, which compares Tr[X_k] with `tr_ref` = Tr[X_{k-1}].  Returns true if the run
+// stops; single thread.
+__device__ __forceinline__ bool record_and_test(DevState* st, int pk, double v_prev, double tr_new,
+                                                double tr_ref) {
+  const int k = st->k + 1;
+  st->v[k - 1] = v_prev;
+  st->tr[k] = tr_new;
+  st->p[k] = (uint8_t)pk;
+  st->k = k;
+  st->hist_len = k;
+  const int i = k - 1;
+  bool stop = true;
+  if (!isfinite(v_prev) || !isfinite(tr_new)) {
+    st->status = SP2_ERR_NONFINITE; st->out_mode = OUT_NAN; st->n_out = i;
+  } else if (k == 1 && v_prev == 0.0) {
+    st->reason = SP2_STOP_EXACT; st->n_out = 0; st->out_buf = 0;
+  } else if (i >= 2 && st->p[i] != st->p[i - 1] && order_test_stops(st->v[i], st->v[i - 2], st->qtilde)) {
+    st->reason = SP2_STOP_ORDER; st->n_out = i; st->out_buf = i & 1;
+  } else if (i >= st->max_iter) {
+    st->reason = SP2_STOP_CAP; st->n_out = i; st->out_buf = i & 1;
+  } else if (st->guard && ((pk == 1 && tr_new >= tr_ref) || (pk == 0 && tr_new <= tr_ref))) {
+    st->reason = SP2_STOP_TRACE_GUARD; st->n_out = k; st->out_buf = k & 1;
+  } else {
+    stop = false;
+  }
+  if (stop) st->done = 1;
+  return stop;
 }
 
 // Deterministic block-wide sum (fixed shuffle tree, then warps in index order).

@@ -81,10 +81,15 @@ init_kernel(DevState* st, const double* __restrict__ F, int64_t ldf, const doubl
   // rounds it.
   double t = 0.0;
   const double w = lmax - lmin;
-  for (int i = threadIdx.x; i < N; i += kInitThreads) t += (lmax - F[(int64_t)i * ldf + i]) / w;
+  const int r32 = st->round_fp32;
+  for (int i = threadIdx.x; i < N; i += kInitThreads) {
+    const double x = (lmax - F[(int64_t)i * ldf + i]) / w;
+    t += r32 ? (double)(float)x : x;
+  }
   t = block_sum<kInitThreads>(t, sm);
   if (threadIdx.x == 0) {
     st->lmin = lmin; st->lmax = lmax;
+    st->dk = 0;
     st->k = 0; st->done = 0; st->n_out = 0; st->reason = SP2_STOP_EXACT;
     st->status = SP2_OK; st->out_buf = 0; st->out_mode = OUT_COPY; st->hist_len = 0;
     st->tr[0] = 0.0; st->p[0] = 0;
@@ -125,19 +130,12 @@ __global__ void scale_kernel(const DevState* st, const double* __restrict__ F, i
 // Tr[X_k] go to a per-tile slot, summed in a fixed order by the finalize kernel.
 constexpr int kTile = 64, kTK = 16, kSyrkThreads = 256;
 
-__global__ void __launch_bounds__(kSyrkThreads)
-syrk_f64_kernel(const DevState* st, double* buf0, double* buf1, double* __restrict__ part) {
-  if (st->done) return;
+__device__ __forceinline__ void syrk_f64_tile(const double* __restrict__ Xin, double* __restrict__ Xout, int ld,
+                                              int pk, double* __restrict__ part) {
   __shared__ double As[2][kTK][kTile + 1];
   __shared__ double Bs[2][kTK][kTile + 1];
   __shared__ double sred[32];
-  const int ld = st->ld;
   const int T = ld / kTile;
-  const int kprev = st->k;                      // X_{k-1} with k = kprev + 1
-  const double* __restrict__ Xin = (kprev & 1) ? buf1 : buf0;
-  double* __restrict__ Xout = (kprev & 1) ? buf0 : buf1;
-  const int pk = st->tr[kprev] > (double)st->nocc ? 1 : 0;   // Alg. 3 trace test
-
   int I, J;
   upper_tile(blockIdx.x, T, I, J);
   const int tid = threadIdx.x;
@@ -214,53 +212,70 @@ syrk_f64_kernel(const DevState* st, double* buf0, double* buf1, double* __restri
   }
 }
 
+
+__global__ void __launch_bounds__(kSyrkThreads)
+syrk_f64_kernel(const DevState* st, double* buf0, double* buf1, double* __restrict__ part) {
+  if (st->done) return;
+  const int kprev = st->k;                      // X_{k-1} with k = kprev + 1
+  const double* Xin = (kprev & 1) ? buf1 : buf0;
+  double* Xout = (kprev & 1) ? buf0 : buf1;
+  const int pk = st->tr[kprev] > (double)st->nocc ? 1 : 0;   // Alg. 3 trace test
+  syrk_f64_tile(Xin, Xout, st->ld, pk, part);
+}
+
+// FP64 purification step on the mixed path's result: the polynomial alternates with
+// the last one of the low-precision expansion (step 0 takes the other one, step 1 the
+// same one), so each pair squares the remaining eigenvalue error (the composition of
+// x^2 and 2x - x^2, §4).
+__global__ void __launch_bounds__(kSyrkThreads)
+refine_f64_kernel(const DevState* st, const double* Xin, double* Xout, int ld, int step,
+                  double* __restrict__ part) {
+  if (st->status != SP2_OK || st->out_mode != OUT_COPY) return;
+  const int plast = st->p[st->n_out];
+  const int pk = step == 0 ? 1 - plast : plast;
+  syrk_f64_tile(Xin, Xout, ld, pk, part);
+}
+
 // ---- per-iteration reduction and stop test (a5 reductions, a7) ----------------------------
 constexpr int kFinThreads = 1024;
 
+// Partials come in records of `stride` doubles.  FP64 path (stride 2): (v^2 part,
+// Tr[X_k] part) with Tr[X_k] summed over the stored diagonal.  Mixed path (stride 4):
+// (v^2 part, ||X_{k-1}||_F^2 part, Tr[X_{k-1}] part, 0): there Tr[X_k] is taken from
+// the identity Tr[X^2] = ||X||_F^2 for symmetric X (Tr[X_k] = ||X_{k-1}||_F^2 after
+// X^2, 2 Tr[X_{k-1}] - ||X_{k-1}||_F^2 after 2X - X^2), so the polynomial choice does
+// not inherit the bias of the tensor cores' accumulation.
 __global__ void __launch_bounds__(kFinThreads)
-finalize_kernel(DevState* st, const double* __restrict__ part, int ntiles,
+finalize_kernel(DevState* st, const double* __restrict__ part, int nparts, int stride,
                 cudaGraphConditionalHandle cond) {
   __shared__ double sm[32];
   if (st->done) {
     if (threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
     return;
   }
-  double v2 = 0.0, tr = 0.0;
-  for (int t = threadIdx.x; t < ntiles; t += kFinThreads) {
-    v2 += part[2 * t];
-    tr += part[2 * t + 1];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int t = threadIdx.x; t < nparts; t += kFinThreads) {
+    a += part[(int64_t)stride * t];
+    b += part[(int64_t)stride * t + 1];
+    if (stride > 2) c += part[(int64_t)stride * t + 2];
   }
-  v2 = block_sum<kFinThreads>(v2, sm);
-  tr = block_sum<kFinThreads>(tr, sm);
+  a = block_sum<kFinThreads>(a, sm);
+  b = block_sum<kFinThreads>(b, sm);
+  c = block_sum<kFinThreads>(c, sm);
   if (threadIdx.x != 0) return;
 
   const int k = st->k + 1;                       // the square just completed
   const int pk = st->tr[k - 1] > (double)st->nocc ? 1 : 0;
-  st->v[k - 1] = sqrt(v2);                       // v_{k-1} = ||X_{k-1} - X_{k-1}^2||_F
-  st->tr[k] = tr;                                // Tr[X_k]
-  st->p[k] = (uint8_t)pk;
-  st->k = k;
-  st->hist_len = k;
-
-  bool stop = true;
-  const int i = k - 1;
-  if (!isfinite(v2) || !isfinite(tr)) {
-    st->status = SP2_ERR_NONFINITE; st->out_mode = OUT_NAN; st->n_out = i;
-  } else if (k == 1 && st->v[0] == 0.0) {
-    st->reason = SP2_STOP_EXACT; st->n_out = 0; st->out_buf = 0;
-  } else if (i >= 2 && st->p[i] != st->p[i - 1] && order_test_stops(st->v[i], st->v[i - 2], st->qtilde)) {
-    st->reason = SP2_STOP_ORDER; st->n_out = i; st->out_buf = i & 1;
-  } else if (i >= st->max_iter) {
-    st->reason = SP2_STOP_CAP; st->n_out = i; st->out_buf = i & 1;
-  } else if (st->guard && ((pk == 1 && tr >= st->tr[k - 1]) || (pk == 0 && tr <= st->tr[k - 1]))) {
-    st->reason = SP2_STOP_TRACE_GUARD; st->n_out = k; st->out_buf = k & 1;
+  double tr_new, tr_ref;
+  if (stride > 2) {
+    tr_new = pk ? b : 2.0 * c - b;
+    tr_ref = c;
   } else {
-    stop = false;
+    tr_new = b;
+    tr_ref = st->tr[k - 1];
   }
-  if (stop) {
-    st->done = 1;
-    cudaGraphSetConditional(cond, 0);
-  }
+  // v_{k-1} = ||X_{k-1} - X_{k-1}^2||_F
+  if (record_and_test(st, pk, sqrt(a), tr_new, tr_ref)) cudaGraphSetConditional(cond, 0);
 }
 
 // ---- output -----------------------------------------------------------------------------
@@ -303,32 +318,55 @@ cudaError_t launch_scale_f64(const DevState* st, const double* F, int64_t ldf, i
   return cudaGetLastError();
 }
 
+cudaError_t add_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, DevState* st,
+                              double* part, int nparts, int stride, cudaGraphConditionalHandle cond,
+                              cudaGraphNode_t* node) {
+  void* args[] = {&st, &part, &nparts, &stride, &cond};
+  cudaKernelNodeParams kp = {};
+  kp.func = (void*)finalize_kernel;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(kFinThreads);
+  kp.kernelParams = args;
+  return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
+}
+
 cudaError_t add_f64_loop_body(cudaGraph_t body, DevState* st, double* buf0, double* buf1, double* part,
                               int T, cudaGraphConditionalHandle cond) {
   const int ntiles = T * (T + 1) / 2;
   cudaGraphNode_t n_sq, n_fin;
-  {
-    void* args[] = {&st, &buf0, &buf1, &part};
-    cudaKernelNodeParams kp = {};
-    kp.func = (void*)syrk_f64_kernel;
-    kp.gridDim = dim3(ntiles);
-    kp.blockDim = dim3(kSyrkThreads);
-    kp.kernelParams = args;
-    cudaError_t e = cudaGraphAddKernelNode(&n_sq, body, nullptr, 0, &kp);
-    if (e != cudaSuccess) return e;
+  void* args[] = {&st, &buf0, &buf1, &part};
+  cudaKernelNodeParams kp = {};
+  kp.func = (void*)syrk_f64_kernel;
+  kp.gridDim = dim3(ntiles);
+  kp.blockDim = dim3(kSyrkThreads);
+  kp.kernelParams = args;
+  cudaError_t e = cudaGraphAddKernelNode(&n_sq, body, nullptr, 0, &kp);
+  if (e != cudaSuccess) return e;
+  return add_finalize_node(body, &n_sq, 1, st, part, ntiles, 2, cond, &n_fin);
+}
+
+cudaError_t launch_refine_f64(const DevState* st, const double* Xin, double* Xout, int ld, int step, double* part,
+                              cudaStream_t s) {
+  const int T = ld / kTile;
+  refine_f64_kernel<<<T * (T + 1) / 2, kSyrkThreads, 0, s>>>(st, Xin, Xout, ld, step, part);
+  return cudaGetLastError();
+}
+
+__global__ void copy_f64_kernel(const DevState* st, const double* __restrict__ X, int ld, double* __restrict__ D,
+                                int64_t ldd) {
+  const int N = st->N;
+  const int64_t total = (int64_t)N * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    D[(int64_t)i * ldd + j] = X[(int64_t)i * ld + j];
   }
-  {
-    int nt = ntiles;
-    void* args[] = {&st, &part, &nt, &cond};
-    cudaKernelNodeParams kp = {};
-    kp.func = (void*)finalize_kernel;
-    kp.gridDim = dim3(1);
-    kp.blockDim = dim3(kFinThreads);
-    kp.kernelParams = args;
-    cudaError_t e = cudaGraphAddKernelNode(&n_fin, body, &n_sq, 1, &kp);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+}
+
+cudaError_t launch_copy_f64(const DevState* st, const double* X, int ld, int N, double* D, int64_t ldd,
+                            cudaStream_t s) {
+  copy_f64_kernel<<<elementwise_blocks((int64_t)N * N), 256, 0, s>>>(st, X, ld, D, ldd);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_copy_out(const DevState* st, const double* buf0, const double* buf1, int ld, int N,

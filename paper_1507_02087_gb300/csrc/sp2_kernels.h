@@ -28,3 +28,41 @@ cudaError_t launch_copy_out(const DevState* st, const double* buf0, const double
                             double* D, int64_t ldd, cudaStream_t s);
 
 }  // namespace sp2
+
+// ---- mixed-precision (tensor-core) path -------------------------------------------------
+#include <cuda.h>
+
+namespace sp2 {
+namespace tc { struct Job; }
+
+// Per-iteration reduction + stop test over `nparts` (v^2, trace) partial pairs.
+cudaError_t add_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, DevState* st,
+                              double* part, int nparts, int stride, cudaGraphConditionalHandle cond,
+                              cudaGraphNode_t* node);
+
+// TMA tensor maps over a piece arena of `nslots` ld x ld matrices (boxes 128 and 256 rows).
+cudaError_t tc_make_maps(void* arena, int ld, int nslots, CUtensorMap* mapA, CUtensorMap* mapB);
+int tc_grid(int ld, int upper);
+int tc_tiles(int ld, int upper);
+cudaError_t tc_launch(const CUtensorMap& A, const CUtensorMap& B, const tc::Job& job, cudaStream_t s);
+cudaError_t tc_add_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const CUtensorMap& A,
+                        const CUtensorMap& B, const tc::Job& job, cudaGraphNode_t* node);
+
+cudaError_t launch_scale_split(const DevState* st, const double* F, int64_t ldf, int N, void* arena,
+                               int64_t slot_elems, int ld, int x_slot, int f_slot, cudaStream_t s);
+cudaError_t add_deriv_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, DevState* st,
+                                    cudaGraphConditionalHandle cond, cudaGraphNode_t* node);
+cudaError_t launch_assemble(const DevState* st, const void* arena, int64_t slot_elems, int ld, int hist0, int dx0,
+                            int use_dx, int r0, int from_r0, int N, double* D, int64_t ldd, cudaStream_t s);
+cudaError_t add_corrected_to_pieces_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const DevState* st,
+                                         void* arena, int64_t slot_elems, int ld, int hist0, int dx0, int use_dx,
+                                         int r0, int N, cudaGraphNode_t* node);
+}  // namespace sp2
+
+namespace sp2 {
+// FP64 purification step `step` (0 or 1) on an ld x ld FP64 matrix (mixed-path refinement).
+cudaError_t launch_refine_f64(const DevState* st, const double* Xin, double* Xout, int ld, int step, double* part,
+                              cudaStream_t s);
+cudaError_t launch_copy_f64(const DevState* st, const double* X, int ld, int N, double* D, int64_t ldd,
+                            cudaStream_t s);
+}  // namespace sp2

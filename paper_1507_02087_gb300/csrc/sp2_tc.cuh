@@ -1,0 +1,85 @@
+// Tensor-core (tcgen05) path: definitions shared by the GEMM kernel and the host side.
+//
+// Matrices on this path are FP32 values stored exactly as three bf16 "pieces"
+// x = (p0 + p1) + p2 (p0 = bf16(x), p1 = bf16(x - p0), p2 = x - p0 - p1; each
+// difference is exact in FP32, and the last one fits in bf16).  A product X Y^T is
+// the sum of the six piece products p_a q_b with a + b <= 2, each a bf16 MMA with
+// FP32 accumulation, which carries the product to FP32 accuracy.
+//
+// All piece matrices of a handle live in one "arena": slot s holds the three planes
+// of one ld x ld matrix, plane-major ([slot][piece][row][col], bf16).  One 4-D TMA
+// tensor map (col, row, piece, slot) covers the arena, so a kernel selects operands
+// by slot index.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "sp2_common.cuh"
+
+namespace sp2 {
+namespace tc {
+
+constexpr int BM = 128;          // tile rows (MMA M)
+constexpr int BN = 128;          // tile cols (MMA N)
+constexpr int BK = 32;           // k-block: 32 bf16 = 64 B rows, 64-byte swizzle
+constexpr int NP = 3;            // pieces per matrix
+constexpr int STAGES = 4;
+// The tensor cores' FP32 accumulation drops the bits an addend loses in alignment
+// (it rounds toward zero), so a long sum of same-sign products drifts low by about
+// K * 2^-25 of its value.  The MMAs therefore accumulate CHUNK_KB k-blocks (64 terms)
+// at a time into one of NBUF tensor-memory buffers, and the epilogue adds the chunk
+// sums into registers with round-to-nearest FP32 additions.
+constexpr int CHUNK_KB = 2;
+constexpr int NBUF = 4;
+constexpr int A_PIECE_BYTES = BM * BK * 2;
+constexpr int B_PIECE_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = NP * (A_PIECE_BYTES + B_PIECE_BYTES);
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;   // + alignment slack
+constexpr int THREADS = 192;     // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
+constexpr int TMEM_COLS = NBUF * BN;   // four 128 x 128 fp32 chunk accumulators
+constexpr int LD_ALIGN = 128;    // ld is a multiple of the tile size
+
+enum Mode : int32_t {
+  MODE_STORE_F32 = 0,   // C -> fp32 buffer (tests)
+  MODE_SP2_STEP = 1,    // X_k = C or 2 X_{k-1} - C, with ||X_{k-1} - C||_F^2, ||X_{k-1}||_F^2 and
+                        // Tr X_{k-1} partials
+  MODE_DERIV_STEP = 2,  // dX_j = C or 2 dX_{j-1} - C
+  MODE_STORE_PIECES = 3,// C -> pieces (full tiles)
+  MODE_DF_COMBINE = 4   // dX_0 = s (M + M^T - 2 C) with s = -1/(lmax - lmin)
+};
+
+// Where the operands come from.  With `slots_from_state`, slot indices are offset by
+// the device state so one captured launch serves every iteration of a loop.
+enum SlotRule : int32_t {
+  SLOTS_FIXED = 0,
+  SLOTS_FORWARD = 1,    // A = B = in = hist0 + k, out = hist0 + k + 1      (k = st->k)
+  SLOTS_DERIV = 2,      // j = st->dk + 1: (X_{j-1}, dX_{j-1}) + (dX_{j-1}, X_{j-1}) -> dX_j
+  SLOTS_CORR_M = 3,     // M = P F with P = X_n:  A = hist0 + n, B = f_slot, out = m_slot
+  SLOTS_CORR_DF = 4,    // W = M P:  A = m_slot, B = hist0 + n, in = m_slot, out = dx0
+  SLOTS_REFINE = 5      // purification step s = a_slot[0] on the corrected D: s = 0 maps
+                        // r0_slot -> r0_slot + 1 with the polynomial other than p_n, s = 1
+                        // maps back with p_n (an alternating pair, §4)
+};
+
+struct Job {
+  int32_t ld;
+  int32_t mode;
+  int32_t upper;        // 1: symmetric result from upper tiles, mirror written
+  int32_t nterms;       // 1 or 2 (sum of two products, same accumulator)
+  int32_t rule;
+  int32_t a_slot[2], b_slot[2];
+  int32_t in_slot, out_slot;
+  int32_t hist0, dx0, m_slot, f_slot;
+  int32_t r0_slot;
+  __nv_bfloat16* arena;
+  int64_t slot_elems;   // 3 * ld * ld
+  float* out32;         // MODE_STORE_F32
+  DevState* st;
+  double* part;         // per (tile, epilogue warp) partials for MODE_SP2_STEP, 4 doubles each
+  int32_t* err;         // set to SP2_ERR_TIMEOUT if a wait gave up
+};
+
+}  // namespace tc
+}  // namespace sp2

@@ -1,0 +1,546 @@
+// Persistent tcgen05 GEMM over 3-piece bf16 operands with the SP2 epilogues.
+//
+// C[I-tile, J-tile] = sum_k A[rows I, k] B[rows J, k] (both operands K-major row
+// panels; X symmetric makes X X^T = X^2), as the six piece products with a+b <= 2.
+// One CTA per SM walks the tile list.  Warp 0 feeds a 4-stage TMA ring (64-byte
+// swizzle, 32-wide k-blocks); warp 1 issues the MMAs (128 x 128 x 16) and closes a
+// tensor-memory chunk buffer every CHUNK_KB k-blocks; warps 2-5 add each closed chunk
+// into FP32 registers (round to nearest) and, after the last chunk of a tile, run the
+// epilogue.  Four chunk buffers let the MMAs run ahead of the draining.
+//
+// With `upper` set only tiles with J >= I are computed; element (r, c) with c >= r is
+// written at (r, c) and, if c > r, at (c, r), so the result is exactly symmetric.
+// Every mbarrier wait is bounded (2 s); a wait that gives up sets *err =
+// SP2_ERR_TIMEOUT and the kernel winds down, waiting (bounded) for its own copies and
+// MMAs before it frees tensor memory.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
+#include "../../include/sp2_testing.h"
+#include "sp2_kernels.h"
+#include "sp2_tc.cuh"
+#include "tc_ptx.cuh"
+
+namespace sp2 {
+namespace tc {
+
+using namespace sp2::ptx;
+
+constexpr uint64_t kWaitNs = 2000000000ull;
+static_assert(BM == BN, "square tiles");
+
+struct Resolved {
+  int a[2], b[2], in, out, pk;
+  bool active;
+};
+
+__device__ __forceinline__ Resolved resolve(const Job& j) {
+  Resolved r;
+  r.a[0] = j.a_slot[0]; r.a[1] = j.a_slot[1];
+  r.b[0] = j.b_slot[0]; r.b[1] = j.b_slot[1];
+  r.in = j.in_slot; r.out = j.out_slot; r.pk = 1; r.active = true;
+  const DevState* st = j.st;
+  if (j.rule == SLOTS_FIXED) return r;
+  const bool ok_run = st->status == SP2_OK && st->out_mode == OUT_COPY;
+  switch (j.rule) {
+    case SLOTS_FORWARD: {
+      const int k = st->k;
+      r.a[0] = r.b[0] = r.in = j.hist0 + k;
+      r.out = j.hist0 + k + 1;
+      r.pk = st->tr[k] > (double)st->nocc ? 1 : 0;   // Alg. 3 trace test
+      r.active = !st->done;
+      break;
+    }
+    case SLOTS_DERIV: {
+      const int jj = st->dk + 1;
+      const int xs = j.hist0 + jj - 1;
+      const int di = j.dx0 + ((jj - 1) & 1);
+      r.a[0] = xs; r.b[0] = di;
+      r.a[1] = di; r.b[1] = xs;
+      r.in = di; r.out = j.dx0 + (jj & 1);
+      r.pk = st->p[jj];
+      r.active = ok_run && st->dk < st->n_out;
+      break;
+    }
+    case SLOTS_CORR_M: {
+      r.a[0] = j.hist0 + st->n_out; r.b[0] = j.f_slot; r.out = j.m_slot;
+      r.active = ok_run && st->n_out > 0;
+      break;
+    }
+    case SLOTS_CORR_DF: {
+      r.a[0] = j.m_slot; r.b[0] = j.hist0 + st->n_out; r.in = j.m_slot; r.out = j.dx0;
+      r.active = ok_run && st->n_out > 0;
+      break;
+    }
+    case SLOTS_REFINE: {
+      const int s = j.a_slot[0];
+      const int plast = st->p[st->n_out];
+      r.a[0] = r.b[0] = r.in = j.r0_slot + s;
+      r.out = j.r0_slot + (1 - s);
+      r.pk = s == 0 ? 1 - plast : plast;
+      r.active = ok_run;
+      break;
+    }
+    default: break;
+  }
+  return r;
+}
+
+__host__ __device__ __forceinline__ int tiles_total(int ld, int upper) {
+  const int R = ld / BM;
+  return upper ? R * (R + 1) / 2 : R * R;
+}
+
+// Tiles in row-major order; with `upper`, row I holds J = I .. R-1.
+__device__ __forceinline__ void tile_ij(int t, int ld, int upper, int& I, int& J) {
+  const int R = ld / BM;
+  if (!upper) { I = t / R; J = t % R; return; }
+  int i = 0;
+  while (t >= R - i) { t -= R - i; ++i; }
+  I = i;
+  J = i + t;
+}
+
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
+  p0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(p0);
+  p1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(p1);
+  p2 = __float2bfloat16_rn(r2);
+}
+
+__device__ __forceinline__ float join3(__nv_bfloat16 p0, __nv_bfloat16 p1, __nv_bfloat16 p2) {
+  return (__bfloat162float(p0) + __bfloat162float(p1)) + __bfloat162float(p2);
+}
+
+// 32 consecutive values of row r starting at column c0 from the three planes of a slot.
+__device__ __forceinline__ void load_row32(const __nv_bfloat16* slot, int64_t plane, int64_t off, float (&x)[32]) {
+  #pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const uint4 a = *reinterpret_cast<const uint4*>(slot + off + 8 * h);
+    const uint4 b = *reinterpret_cast<const uint4*>(slot + plane + off + 8 * h);
+    const uint4 c = *reinterpret_cast<const uint4*>(slot + 2 * plane + off + 8 * h);
+    const __nv_bfloat16* pa = reinterpret_cast<const __nv_bfloat16*>(&a);
+    const __nv_bfloat16* pb = reinterpret_cast<const __nv_bfloat16*>(&b);
+    const __nv_bfloat16* pc = reinterpret_cast<const __nv_bfloat16*>(&c);
+    #pragma unroll
+    for (int e = 0; e < 8; ++e) x[8 * h + e] = join3(pa[e], pb[e], pc[e]);
+  }
+}
+
+__device__ __forceinline__ void store_row32(__nv_bfloat16* slot, int64_t plane, int64_t off, const float (&x)[32]) {
+  #pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    uint4 a, b, c;
+    __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(&a);
+    __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>(&b);
+    __nv_bfloat16* pc = reinterpret_cast<__nv_bfloat16*>(&c);
+    #pragma unroll
+    for (int e = 0; e < 8; ++e) split3(x[8 * h + e], pa[e], pb[e], pc[e]);
+    *reinterpret_cast<uint4*>(slot + off + 8 * h) = a;
+    *reinterpret_cast<uint4*>(slot + plane + off + 8 * h) = b;
+    *reinterpret_cast<uint4*>(slot + 2 * plane + off + 8 * h) = c;
+  }
+}
+
+__device__ __forceinline__ void store_one(__nv_bfloat16* slot, int64_t plane, int64_t off, float v) {
+  __nv_bfloat16 a, b, c;
+  split3(v, a, b, c);
+  slot[off] = a;
+  slot[plane + off] = b;
+  slot[2 * plane + off] = c;
+}
+
+struct Partials {
+  double v2;    // sum of w (x - c)^2   (w = 2 off the diagonal, 1 on it)
+  double fro2;  // sum of w x^2
+  double trd;   // sum of the diagonal x
+};
+
+// Epilogue for row r, columns c0 .. c0+31 of the tile, with the accumulated product s.
+__device__ __forceinline__ void epilogue_chunk(const Job& job, const Resolved& R, int r, int c0,
+                                               const float (&s)[32], Partials& P) {
+  const int ld = job.ld;
+  const int64_t plane = (int64_t)ld * ld;
+  const bool upper = job.upper != 0;
+  const bool all_keep = !upper || c0 >= r;
+  const bool none_keep = upper && c0 + 31 < r;
+  if (none_keep) return;
+  const int64_t row_off = (int64_t)r * ld + c0;
+
+  if (job.mode == MODE_STORE_F32) {
+    #pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int c = c0 + j;
+      if (all_keep || c >= r) job.out32[row_off + j] = s[j];
+      if (upper && c > r) job.out32[(int64_t)c * ld + r] = s[j];
+    }
+    return;
+  }
+
+  __nv_bfloat16* out = job.arena + (int64_t)R.out * job.slot_elems;
+  float xn[32];
+  if (job.mode == MODE_STORE_PIECES) {
+    #pragma unroll
+    for (int j = 0; j < 32; ++j) xn[j] = s[j];
+  } else {
+    const __nv_bfloat16* in = job.arena + (int64_t)R.in * job.slot_elems;
+    float x[32];
+    load_row32(in, plane, row_off, x);
+    if (job.mode == MODE_DF_COMBINE) {
+      const double w = job.st->lmax - job.st->lmin;
+      const float sc = (float)(-1.0 / w);
+      #pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int64_t toff = (int64_t)(c0 + j) * ld + r;
+        const float mt = join3(in[toff], in[plane + toff], in[2 * plane + toff]);
+        xn[j] = sc * ((x[j] + mt) - 2.0f * s[j]);
+      }
+    } else {
+      float vacc = 0.f, facc = 0.f;
+      #pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        xn[j] = R.pk ? s[j] : fmaf(2.0f, x[j], -s[j]);
+        if (job.mode == MODE_SP2_STEP) {
+          const int c = c0 + j;
+          const float d = x[j] - s[j];
+          const float wgt = !upper ? 1.f : (c > r ? 2.f : (c == r ? 1.f : 0.f));
+          vacc = fmaf(wgt * d, d, vacc);
+          facc = fmaf(wgt * x[j], x[j], facc);
+          if (c == r) P.trd += (double)x[j];
+        }
+      }
+      P.v2 += (double)vacc;
+      P.fro2 += (double)facc;
+    }
+  }
+  if (all_keep) {
+    store_row32(out, plane, row_off, xn);
+  } else {
+    #pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (c0 + j >= r) store_one(out, plane, row_off + j, xn[j]);
+  }
+  if (upper) {
+    #pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int c = c0 + j;
+      if (c > r) store_one(out, plane, (int64_t)c * ld + r, xn[j]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const Job job) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t accf_bar[NBUF];
+  __shared__ __align__(8) uint64_t acce_bar[NBUF];
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ volatile int abort_s;
+
+  const Resolved R = resolve(job);
+  if (!R.active) return;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int a = 0; a < NBUF; ++a) { mbar_init(&accf_bar[a], 1); mbar_init(&acce_bar[a], 4); }
+    mbar_init(&drain_bar, 1);
+    abort_s = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base_s, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_base_s;
+  const int ld = job.ld;
+  const int ntiles = tiles_total(ld, job.upper);
+  const int nkb = ld / BK;
+  const int nchunks = job.nterms * nkb / CHUNK_KB;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      prefetch_tmap(&mapA);
+      prefetch_tmap(&mapB);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int armed[STAGES];
+      uint32_t armed_par[STAGES];
+      for (int s = 0; s < STAGES; ++s) { armed[s] = 0; armed_par[s] = 0; }
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int I, J;
+        tile_ij(t, ld, job.upper, I, J);
+        for (int term = 0; term < job.nterms && ok; ++term) {
+          for (int kb = 0; kb < nkb; ++kb) {
+            if (abort_s || !mbar_wait(&empty_bar[stage], phase ^ 1, globaltimer_ns() + kWaitNs)) {
+              ok = false;
+              break;
+            }
+            uint8_t* sA = smem + stage * STAGE_BYTES;
+            uint8_t* sB = sA + NP * A_PIECE_BYTES;
+            mbar_arrive_expect_tx(&full_bar[stage], STAGE_BYTES);
+            #pragma unroll
+            for (int p = 0; p < NP; ++p)
+              tma_load_4d(sA + p * A_PIECE_BYTES, &mapA, kb * BK, I * BM, p, R.a[term], &full_bar[stage]);
+            #pragma unroll
+            for (int p = 0; p < NP; ++p)
+              tma_load_4d(sB + p * B_PIECE_BYTES, &mapB, kb * BK, J * BN, p, R.b[term], &full_bar[stage]);
+            armed[stage] = 1;
+            armed_par[stage] = phase;
+            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          }
+        }
+      }
+      if (!ok) { abort_s = 1; atomicExch(job.err, (int)SP2_ERR_TIMEOUT); }
+      // wait (bounded) until every copy issued here has landed
+      for (int s = 0; s < STAGES; ++s)
+        if (armed[s]) mbar_wait(&full_bar[s], armed_par[s], globaltimer_ns() + kWaitNs);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16_f32(BM, BN);
+      // piece pairs (a, b) with a + b <= 2, smallest products first
+      const int pa[6] = {2, 1, 0, 1, 0, 0};
+      const int pb[6] = {0, 1, 2, 0, 1, 0};
+      int stage = 0, buf = 0;
+      uint32_t phase = 0, bphase = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int ch = 0; ch < nchunks && ok; ++ch) {
+          if (abort_s || !mbar_wait(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + kWaitNs)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t dt = tmem_base + (uint32_t)(buf * BN);
+          uint32_t accumulate = 0;
+          for (int kc = 0; kc < CHUNK_KB; ++kc) {
+            if (abort_s || !mbar_wait(&full_bar[stage], phase, globaltimer_ns() + kWaitNs)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
+            const uint32_t sB = sA + NP * A_PIECE_BYTES;
+            #pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              #pragma unroll
+              for (int q = 0; q < 6; ++q) {
+                const uint64_t ad = smem_desc_sw64(sA + pa[q] * A_PIECE_BYTES + kk * 32);
+                const uint64_t bd = smem_desc_sw64(sB + pb[q] * B_PIECE_BYTES + kk * 32);
+                mma_bf16(dt, ad, bd, idesc, accumulate);
+                accumulate = 1;
+              }
+            }
+            mma_commit(&empty_bar[stage]);
+            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          mma_commit(&accf_bar[buf]);
+          if (++buf == NBUF) { buf = 0; bphase ^= 1; }
+        }
+      }
+      if (!ok) { abort_s = 1; atomicExch(job.err, (int)SP2_ERR_TIMEOUT); }
+      mma_commit(&drain_bar);
+      mbar_wait(&drain_bar, 0, globaltimer_ns() + kWaitNs);
+    }
+  } else {
+    // ---------------- chunk draining + epilogue (warps 2..5) ----------------
+    const int q = warp & 3;      // TMEM lanes 32q .. 32q+31
+    int buf = 0;
+    uint32_t bphase = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      float acc[BN / 32][32];
+      #pragma unroll
+      for (int g = 0; g < BN / 32; ++g)
+        #pragma unroll
+        for (int j = 0; j < 32; ++j) acc[g][j] = 0.f;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        int got = 0;
+        if (lane == 0) got = !abort_s && mbar_wait(&accf_bar[buf], bphase, globaltimer_ns() + kWaitNs);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) {
+          if (lane == 0) { abort_s = 1; atomicExch(job.err, (int)SP2_ERR_TIMEOUT); }
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t trow = tmem_base + (uint32_t)(buf * BN) + ((uint32_t)(32 * q) << 16);
+        #pragma unroll
+        for (int g = 0; g < BN / 32; ++g) {
+          uint32_t raw[32];
+          tmem_ld32(trow + g * 32, raw);
+          tmem_wait_ld();
+          #pragma unroll
+          for (int j = 0; j < 32; ++j) acc[g][j] += __uint_as_float(raw[j]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce_bar[buf]);
+        if (++buf == NBUF) { buf = 0; bphase ^= 1; }
+      }
+      if (!ok) break;
+      int I, J;
+      tile_ij(t, ld, job.upper, I, J);
+      const int r = I * BM + 32 * q + lane;
+      Partials P = {0.0, 0.0, 0.0};
+      #pragma unroll
+      for (int g = 0; g < BN / 32; ++g) epilogue_chunk(job, R, r, J * BN + g * 32, acc[g], P);
+      if (job.mode == MODE_SP2_STEP) {
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          P.v2 += __shfl_xor_sync(0xffffffffu, P.v2, o);
+          P.fro2 += __shfl_xor_sync(0xffffffffu, P.fro2, o);
+          P.trd += __shfl_xor_sync(0xffffffffu, P.trd, o);
+        }
+        if (lane == 0) {
+          double* dst = job.part + 4 * (4 * (int64_t)t + q);
+          dst[0] = P.v2;
+          dst[1] = P.fro2;
+          dst[2] = P.trd;
+          dst[3] = 0.0;
+        }
+      }
+    }
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
+}  // namespace tc
+
+// ---- host side ----------------------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+cudaError_t tc_make_maps(void* arena, int ld, int nslots, CUtensorMap* mapA, CUtensorMap* mapB) {
+  auto enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  if (ld % tc::LD_ALIGN != 0 || (reinterpret_cast<uintptr_t>(arena) & 15) != 0) return cudaErrorInvalidValue;
+  cuuint64_t dims[4] = {(cuuint64_t)ld, (cuuint64_t)ld, (cuuint64_t)tc::NP, (cuuint64_t)nslots};
+  cuuint64_t strides[3] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * ld * 2, (cuuint64_t)tc::NP * ld * ld * 2};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  cuuint32_t boxA[4] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM, 1, 1};
+  cuuint32_t boxB[4] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BN, 1, 1};
+  CUresult r1 = enc(mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, arena, dims, strides, boxA, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = enc(mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, arena, dims, strides, boxB, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+static int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+int tc_grid(int ld, int upper) {
+  const int t = tc::tiles_total(ld, upper);
+  const int s = sm_count();
+  return t < s ? t : s;
+}
+
+int tc_tiles(int ld, int upper) { return tc::tiles_total(ld, upper); }
+
+static cudaError_t tc_prepare() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(tc::tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       tc::SMEM_BYTES);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+cudaError_t tc_launch(const CUtensorMap& A, const CUtensorMap& B, const tc::Job& job, cudaStream_t s) {
+  cudaError_t e = tc_prepare();
+  if (e != cudaSuccess) return e;
+  tc::tc_gemm_kernel<<<tc_grid(job.ld, job.upper), tc::THREADS, tc::SMEM_BYTES, s>>>(A, B, job);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_add_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const CUtensorMap& A,
+                        const CUtensorMap& B, const tc::Job& job, cudaGraphNode_t* node) {
+  cudaError_t e = tc_prepare();
+  if (e != cudaSuccess) return e;
+  CUtensorMap a = A, b = B;
+  tc::Job j = job;
+  void* args[] = {&a, &b, &j};
+  cudaKernelNodeParams kp = {};
+  kp.func = (void*)tc::tc_gemm_kernel;
+  kp.gridDim = dim3(tc_grid(job.ld, job.upper));
+  kp.blockDim = dim3(tc::THREADS);
+  kp.sharedMemBytes = tc::SMEM_BYTES;
+  kp.kernelParams = args;
+  return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
+}
+
+}  // namespace sp2
+
+extern "C" int32_t sp2_test_tc_gemm(const void* arena_dev, int32_t ld, int32_t nslots, int32_t a_slot,
+                                    int32_t b_slot, int32_t upper, float* out_dev, void* stream) {
+  if (!arena_dev || !out_dev || ld <= 0 || ld % sp2::tc::LD_ALIGN != 0 || nslots <= 0 || a_slot < 0 ||
+      b_slot < 0 || a_slot >= nslots || b_slot >= nslots || (upper != 0 && upper != 1))
+    return SP2_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CUtensorMap A, B;
+  if (sp2::tc_make_maps(const_cast<void*>(arena_dev), ld, nslots, &A, &B) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SP2_ERR_CUDA;
+  }
+  int32_t* err = nullptr;
+  if (cudaMallocAsync((void**)&err, sizeof(int32_t), s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SP2_ERR_NOMEM;
+  }
+  int32_t herr = 0;
+  sp2::tc::Job j;
+  std::memset(&j, 0, sizeof(j));
+  j.ld = ld;
+  j.mode = sp2::tc::MODE_STORE_F32;
+  j.upper = upper;
+  j.nterms = 1;
+  j.rule = sp2::tc::SLOTS_FIXED;
+  j.a_slot[0] = a_slot;
+  j.b_slot[0] = b_slot;
+  j.arena = (__nv_bfloat16*)const_cast<void*>(arena_dev);
+  j.slot_elems = (int64_t)3 * ld * ld;
+  j.out32 = out_dev;
+  j.err = err;
+  bool ok = cudaMemsetAsync(err, 0, sizeof(int32_t), s) == cudaSuccess &&
+            sp2::tc_launch(A, B, j, s) == cudaSuccess &&
+            cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+            cudaFreeAsync(err, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    (void)cudaGetLastError();
+    return SP2_ERR_CUDA;
+  }
+  return herr;
+}

@@ -22,7 +22,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA runtime error", 3: "non-finit
           4: "device-side wait timed out", 5: "out of device memory", 6: "no gap (F = cI)",
           7: "unsupported option"}
 STOP_ORDER, STOP_TRACE_GUARD, STOP_EXACT, STOP_CAP = 0, 1, 2, 3
-PRECISIONS = {"fp64": 0}
+PRECISIONS = {"fp64": 0, "mixed": 1}
 MAX_ITER = 512
 
 
@@ -33,7 +33,9 @@ class SP2Error(RuntimeError):
 
 
 class sp2_opts(ctypes.Structure):
-    _fields_ = [("max_iter", ctypes.c_int32), ("guard", ctypes.c_int32), ("qtilde", ctypes.c_double)]
+    _fields_ = [("max_iter", ctypes.c_int32), ("guard", ctypes.c_int32), ("qtilde", ctypes.c_double),
+                ("corrections", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
+                ("refine_fp64", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class sp2_info(ctypes.Structure):
@@ -69,6 +71,8 @@ def lib() -> ctypes.CDLL:
         L.sp2_destroy.restype = None
         L.sp2_status_string.argtypes = [i32]
         L.sp2_status_string.restype = ctypes.c_char_p
+        L.sp2_test_tc_gemm.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp]
+        L.sp2_test_tc_gemm.restype = i32
         _lib = L
     return _lib
 
@@ -86,8 +90,9 @@ def _stream_ptr(stream) -> int:
 
 
 def sp2_create(N: int, nocc: int, precision: str = "fp64", *, max_iter: int = 200, guard: bool = True,
-               qtilde: float = 1.8) -> int:
-    o = sp2_opts(max_iter, 1 if guard else 0, qtilde)
+               qtilde: float = 1.8, corrections: int = 1, refine_steps: int = 2,
+               refine_fp64: bool = False) -> int:
+    o = sp2_opts(max_iter, 1 if guard else 0, qtilde, corrections, refine_steps, 1 if refine_fp64 else 0, 0)
     h = ctypes.c_void_p()
     _check(lib().sp2_create(N, nocc, PRECISIONS[precision], ctypes.byref(o), ctypes.byref(h)), "sp2_create")
     return h.value
@@ -119,6 +124,13 @@ def sp2_get_info(h: int) -> dict:
         "trace": np.ctypeslib.as_array(info.trace, shape=(MAX_ITER + 2,))[:hl + 1].copy(),
         "p": np.ctypeslib.as_array(info.p, shape=(MAX_ITER + 2,))[:hl + 1].copy(),
     }
+
+
+def sp2_test_tc_gemm(arena, ld: int, nslots: int, a_slot: int, b_slot: int, upper: bool, out,
+                     stream=None) -> None:
+    """Tensor-core product C = A B^T over a bf16 piece arena (see include/sp2_testing.h)."""
+    _check(lib().sp2_test_tc_gemm(arena.data_ptr(), ld, nslots, a_slot, b_slot, 1 if upper else 0,
+                                  out.data_ptr(), _stream_ptr(stream)), "sp2_test_tc_gemm")
 
 
 def sp2_destroy(h: int) -> None:

@@ -15,7 +15,7 @@ LIB = os.path.join(ROOT, "paper_1507_02087_gb300", "libsp2.so")
 
 def declared_functions():
     names = set()
-    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(sp2_\w+)\s*\(", text, flags=re.M):
@@ -47,14 +47,15 @@ def test_library_exports_every_declared_symbol(built):
         assert hasattr(lib, n)
 
 
-def test_status_strings_without_gpu(built):
+def test_status_strings_and_defaults_without_gpu(built):
     from paper_1507_02087_gb300 import sp2
     L = sp2.lib()
     assert L.sp2_status_string(0) == b"ok"
     assert L.sp2_status_string(3).startswith(b"non-finite")
     o = sp2.sp2_opts()
     L.sp2_default_opts(ctypes.byref(o))
-    assert (o.max_iter, o.guard, o.qtilde) == (200, 1, 1.8)
+    assert (o.max_iter, o.guard, o.qtilde, o.corrections, o.refine_steps, o.refine_fp64, o.reserved) == \
+        (200, 1, 1.8, 1, 2, 0, 0)
 
 
 def test_invalid_arguments_rejected_before_any_cuda_call(built):
@@ -65,33 +66,37 @@ def test_invalid_arguments_rejected_before_any_cuda_call(built):
     assert L.sp2_create(10, 11, 0, None, ctypes.byref(h)) == 1
     assert L.sp2_create(10, -1, 0, None, ctypes.byref(h)) == 1
     assert L.sp2_create(10, 5, 99, None, ctypes.byref(h)) == 7
-    bad = sp2.sp2_opts(0, 1, 1.8)
-    assert L.sp2_create(10, 5, 0, ctypes.byref(bad), ctypes.byref(h)) == 1
-    assert h.value is None
+    for bad in (sp2.sp2_opts(0, 1, 1.8, 1, 2, 0, 0),      # max_iter
+                sp2.sp2_opts(10, 2, 1.8, 1, 2, 0, 0),     # guard
+                sp2.sp2_opts(10, 1, 0.0, 1, 2, 0, 0),     # qtilde
+                sp2.sp2_opts(10, 1, 1.8, 2, 2, 0, 0),     # corrections
+                sp2.sp2_opts(10, 1, 1.8, 1, 1, 0, 0),     # refine_steps
+                sp2.sp2_opts(10, 1, 1.8, 1, 2, 3, 0),     # refine_fp64
+                sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 5)):    # reserved
+        assert L.sp2_create(10, 5, 1, ctypes.byref(bad), ctypes.byref(h)) == 1
+        assert h.value is None
     assert L.sp2_run(None, None, None, None) == 1
+    assert L.sp2_run_host(None, None, None, None) == 1
     assert L.sp2_get_info(None, None) == 1
+    assert L.sp2_test_tc_gemm(None, 256, 1, 0, 0, 0, None, None) == 1
     L.sp2_destroy(None)
 
 
 def test_struct_layout_matches_c():
     from paper_1507_02087_gb300 import sp2
-    src = r'''
-#include <stdio.h>
-#include <stddef.h>
-#include "sp2.h"
-int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(sp2_opts), offsetof(sp2_opts, qtilde),
-         sizeof(sp2_info), offsetof(sp2_info, lambda_min), offsetof(sp2_info, loop_ms), offsetof(sp2_info, v),
-         offsetof(sp2_info, trace), offsetof(sp2_info, p));
-  return 0;
-}'''
+    fields_opts = ["max_iter", "guard", "qtilde", "corrections", "refine_steps", "refine_fp64", "reserved"]
+    fields_info = ["status", "n_iter", "stop_reason", "hist_len", "lambda_min", "lambda_max", "loop_ms",
+                   "v", "trace", "p"]
+    prints = [f"offsetof(sp2_opts, {f})" for f in fields_opts] + ["sizeof(sp2_opts)"]
+    prints += [f"offsetof(sp2_info, {f})" for f in fields_info] + ["sizeof(sp2_info)"]
+    src = ("#include <stdio.h>\n#include <stddef.h>\n#include \"sp2.h\"\nint main(void) {\n" +
+           "".join(f'  printf("%zu\\n", (size_t){p});\n' for p in prints) + "  return 0;\n}\n")
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
         exe = os.path.join(d, "t")
         open(c, "w").write(src)
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = list(map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()))
-    py = [ctypes.sizeof(sp2.sp2_opts), sp2.sp2_opts.qtilde.offset, ctypes.sizeof(sp2.sp2_info),
-          sp2.sp2_info.lambda_min.offset, sp2.sp2_info.loop_ms.offset, sp2.sp2_info.v.offset, sp2.sp2_info.trace.offset,
-          sp2.sp2_info.p.offset]
+    py = [getattr(sp2.sp2_opts, f).offset for f in fields_opts] + [ctypes.sizeof(sp2.sp2_opts)]
+    py += [getattr(sp2.sp2_info, f).offset for f in fields_info] + [ctypes.sizeof(sp2.sp2_info)]
     assert vals == py

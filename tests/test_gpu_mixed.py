@@ -1,0 +1,135 @@
+"""Parity of the mixed-precision path (tensor-core squares, correction, refinement)
+with the CPU FP64 oracle, through the C ABI.
+
+Tolerance: ||D - D_ref||_F / sqrt(nocc) <= 1e-6 (the mixed path's stated bound).
+The low-precision expansion reaches its rounding floor earlier than FP64, so its
+stopping iteration is at most the FP64 oracle's (plus one for the one-square lag).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import sp2_oracle as o
+from paper_1507_02087_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module")
+def sp2mod():
+    from paper_1507_02087_gb300 import sp2
+    sp2.lib()
+    return sp2
+
+
+def run_gpu(sp2mod, F, nocc, **opts):
+    F = F if isinstance(F, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(F))
+    F = F.to("cuda", torch.float64).contiguous()
+    with sp2mod.Purifier(F.shape[0], nocc, "mixed", **opts) as P:
+        D = P.run(F)
+        info = P.info()
+    return D, info
+
+
+@pytest.mark.parametrize("N,nocc,gap", [(2, 1, 0.2), (17, 9, 0.1), (129, 64, 0.1), (300, 120, 0.05),
+                                         (1500, 700, 0.02)])
+def test_mixed_small_and_ragged(sp2mod, N, nocc, gap):
+    case = inputs.dense_gapped(N, nocc, gap=gap, seed=N)
+    F = case.F.numpy()
+    ref = o.sp2(F, nocc)
+    D, info = run_gpu(sp2mod, F, nocc)
+    assert info["status"] == 0
+    assert info["stop_reason"] in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
+    assert info["n_iter"] <= ref.n + 1
+    assert o.rel_error(D.cpu().numpy(), ref.D, nocc) <= TOL_MIXED
+    assert torch.equal(D, D.T)
+
+
+def test_mixed_n400(sp2mod):
+    case = inputs.dense_n400()
+    ref = o.sp2(case.F.numpy(), case.nocc)
+    D, info = run_gpu(sp2mod, case.F, case.nocc)
+    assert info["status"] == 0 and info["n_iter"] <= ref.n + 1
+    assert o.rel_error(D.cpu().numpy(), ref.D, case.nocc) <= TOL_MIXED
+    inv = o.invariants(case.F.numpy(), D.cpu().numpy(), case.nocc)
+    assert inv["trace_err"] < 1e-3 and inv["idem_err"] < 1e-4 and inv["comm_err"] < 1e-4
+
+
+def test_mixed_n2048_small_gap(sp2mod):
+    case = inputs.dense_gapped(2048, 1024, gap=0.01, seed=0)
+    ref = o.sp2(case.F.numpy(), 1024)
+    D, info = run_gpu(sp2mod, case.F, 1024)
+    assert info["status"] == 0 and info["n_iter"] <= ref.n + 1
+    assert o.rel_error(D.cpu().numpy(), ref.D, 1024) <= TOL_MIXED
+
+
+def test_mixed_options(sp2mod):
+    case = inputs.dense_gapped(600, 300, gap=0.05, seed=3)
+    ref = o.sp2(case.F.numpy(), 300)
+    errs = {}
+    for key, opts in {"none": dict(corrections=0, refine_steps=0),
+                      "corr": dict(corrections=1, refine_steps=0),
+                      "corr+tc": dict(corrections=1, refine_steps=2),
+                      "corr+fp64": dict(corrections=1, refine_steps=2, refine_fp64=True)}.items():
+        D, info = run_gpu(sp2mod, case.F, 300, **opts)
+        assert info["status"] == 0
+        errs[key] = o.rel_error(D.cpu().numpy(), ref.D, 300)
+    # the correction removes most of the low-precision subspace error
+    assert errs["corr"] < errs["none"] / 3
+    assert errs["corr+tc"] <= TOL_MIXED and errs["corr+fp64"] <= TOL_MIXED
+
+
+def test_mixed_deterministic_and_host_entry(sp2mod):
+    case = inputs.dense_gapped(700, 350, gap=0.05, seed=8)
+    F = case.F.numpy()
+    with sp2mod.Purifier(700, 350, "mixed") as P:
+        D1 = P.run(torch.from_numpy(F).cuda()).cpu().numpy()
+        D2 = P.run_host(F)
+        D3 = P.run(torch.from_numpy(F).cuda()).cpu().numpy()
+        info = P.info()
+    assert info["status"] == 0
+    assert np.array_equal(D1, D2) and np.array_equal(D1, D3)
+
+
+def test_mixed_special_cases(sp2mod):
+    F = np.diag([0.3, -0.2, 0.1, 0.7])
+    D, info = run_gpu(sp2mod, F, 0)
+    assert info["stop_reason"] == o.STOP_EXACT and float(D.abs().max()) == 0.0
+    D, info = run_gpu(sp2mod, F, 4)
+    assert torch.equal(D.cpu(), torch.eye(4, dtype=torch.float64))
+    D, info = run_gpu(sp2mod, np.array([[0.5]]), 1)
+    assert float(D[0, 0]) == 1.0
+    F = inputs.dense_gapped(64, 32, gap=0.1, seed=2).F.numpy().copy()
+    F[1, 2] = F[2, 1] = np.nan
+    D, info = run_gpu(sp2mod, F, 32)
+    assert info["status"] == 3 and bool(torch.isnan(D).all())
+    D, info = run_gpu(sp2mod, 3.0 * np.eye(16), 8)
+    assert info["status"] == 6
+
+
+def test_mixed_diagonal_f(sp2mod):
+    g = np.random.Generator(np.random.PCG64(4))
+    N, nocc = 200, 77
+    lam = np.concatenate([g.uniform(-1, -0.05, nocc), g.uniform(0.05, 1.0, N - nocc)])
+    g.shuffle(lam)
+    D, info = run_gpu(sp2mod, np.diag(lam), nocc)
+    exact = np.diag((lam < 0).astype(float))
+    assert o.rel_error(D.cpu().numpy(), exact, nocc) <= TOL_MIXED
+
+
+def test_mixed_full_size_n8192(sp2mod):
+    # the benchmark workload, in the launch configuration the benchmark times
+    case = inputs.dense_n8192(device="cuda")
+    D, info = run_gpu(sp2mod, case.F, case.nocc)
+    assert info["status"] == 0
+    err = float(torch.linalg.norm(D - case.D_exact)) / math.sqrt(case.nocc)
+    assert err <= TOL_MIXED
+    # invariants at full size: trace, idempotency, commutation with F
+    assert abs(float(torch.trace(D)) - case.nocc) < 1e-2
+    DD = D @ D
+    assert float(torch.linalg.norm(DD - D)) / math.sqrt(case.nocc) < 1e-5
+    FD = case.F @ D
+    assert float(torch.linalg.norm(FD - FD.T)) / math.sqrt(case.nocc) < 1e-5

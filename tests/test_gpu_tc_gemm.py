@@ -1,0 +1,80 @@
+"""The tcgen05 product used by the mixed path, checked on its own through the C ABI.
+
+Operands are FP32 matrices stored exactly as three bf16 pieces; the product of two
+such matrices (six piece products, FP32 accumulation) must match the FP64 product
+of the same FP32 values to FP32 accuracy.
+"""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sp2mod():
+    from paper_1507_02087_gb300 import sp2
+    sp2.lib()
+    return sp2
+
+
+def pieces(x32: torch.Tensor) -> torch.Tensor:
+    """x = (p0 + p1) + p2 exactly, p_i bf16 (round to nearest even at each step)."""
+    p0 = x32.to(torch.bfloat16)
+    r1 = x32 - p0.float()
+    p1 = r1.to(torch.bfloat16)
+    r2 = r1 - p1.float()
+    p2 = r2.to(torch.bfloat16)
+    assert torch.equal((p0.float() + p1.float()) + p2.float(), x32)
+    return torch.stack([p0, p1, p2])
+
+
+def run(sp2mod, mats, a, b, upper):
+    ld = mats[0].shape[0]
+    arena = torch.stack([pieces(m) for m in mats]).contiguous()
+    out = torch.full((ld, ld), float("nan"), dtype=torch.float32, device="cuda")
+    sp2mod.sp2_test_tc_gemm(arena, ld, len(mats), a, b, upper, out)
+    return out
+
+
+def rel(C, R):
+    return float(torch.linalg.norm(C.double() - R) / torch.linalg.norm(R))
+
+
+@pytest.mark.parametrize("ld", [256, 512, 1024, 4096])
+def test_general_product(sp2mod, ld):
+    g = torch.Generator(device="cpu").manual_seed(ld)
+    A = torch.randn(ld, ld, generator=g).float().cuda()
+    B = torch.randn(ld, ld, generator=g).float().cuda() * 1e-3
+    C = run(sp2mod, [A, B], 0, 1, False)
+    R = A.double() @ B.double().T
+    assert torch.isfinite(C).all()
+    # FP32 accumulation over K = ld terms: relative error a few 1e-6
+    assert rel(C, R) < 1e-5
+    # each element, against its own magnitude scale (sum of |a_ik b_jk|)
+    scale = (A.double().abs() @ B.double().abs().T)
+    assert float(((C.double() - R).abs() / scale).max()) < 1e-5
+
+
+@pytest.mark.parametrize("ld", [256, 768, 2048, 4096])
+def test_symmetric_square_upper(sp2mod, ld):
+    g = torch.Generator(device="cpu").manual_seed(100 + ld)
+    X = torch.randn(ld, ld, generator=g, dtype=torch.float64)
+    X = ((X + X.T) / (2 * ld ** 0.5)).float().cuda()
+    C = run(sp2mod, [X], 0, 0, True)
+    R = X.double() @ X.double()
+    assert torch.equal(C, C.T)               # mirror writes: exactly symmetric
+    assert rel(C, R) < 1e-5
+
+
+def test_slot_selection_and_zero_border(sp2mod):
+    ld = 512
+    g = torch.Generator(device="cpu").manual_seed(7)
+    mats = [torch.zeros(ld, ld, device="cuda") for _ in range(4)]
+    N = 300
+    mats[2][:N, :N] = torch.randn(N, N, generator=g).cuda()
+    mats[3][:N, :N] = torch.randn(N, N, generator=g).cuda()
+    C = run(sp2mod, mats, 2, 3, False)
+    R = mats[2].double() @ mats[3].double().T
+    assert rel(C, R) < 1e-5
+    assert float(C[N:, :].abs().max()) == 0.0 and float(C[:, N:].abs().max()) == 0.0
