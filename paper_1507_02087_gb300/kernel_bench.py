@@ -1,0 +1,59 @@
+"""Micro-benchmark of the tensor-core square on its own (through the C ABI).
+
+Builds a random symmetric FP32 matrix X of size ld, stores it as three bf16 pieces
+and times C = X X^T with the same tcgen05 kernel the mixed SP2 path uses (upper
+tiles + mirror, FP32 output).  Used for kernel profiling on a small, self-contained
+case:  python -m paper_1507_02087_gb300.kernel_bench --ld 8192 --reps 5
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import torch
+
+from . import sp2
+
+
+def pieces(x32: torch.Tensor) -> torch.Tensor:
+    p0 = x32.to(torch.bfloat16)
+    r1 = x32 - p0.float()
+    p1 = r1.to(torch.bfloat16)
+    p2 = (r1 - p1.float()).to(torch.bfloat16)
+    return torch.stack([p0, p1, p2])
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--ld", type=int, default=8192)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--full", action="store_true", help="all tiles (general product) instead of upper + mirror")
+    a = ap.parse_args()
+    ld = a.ld
+    g = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.randn(ld, ld, device="cuda", generator=g)
+    X = ((X + X.T) / (2 * ld ** 0.5)).float()
+    arena = pieces(X).unsqueeze(0).contiguous()
+    out = torch.empty(ld, ld, device="cuda", dtype=torch.float32)
+    upper = not a.full
+    sp2.sp2_test_tc_gemm(arena, ld, 1, 0, 0, upper, out)    # warm-up
+    times = []
+    for _ in range(a.reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sp2.sp2_test_tc_gemm(arena, ld, 1, 0, 0, upper, out)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = min(times)
+    R = ld // 128
+    tiles = R * (R + 1) // 2 if upper else R * R
+    executed = 6 * tiles * 128 * 128 * ld * 2
+    print(json.dumps({"ld": ld, "upper": upper, "ms": ms, "tiles": tiles,
+                      "executed_tflops": executed / (ms * 1e-3) / 1e12,
+                      "algorithmic_tflops": 6 * ld * ld * (ld + 1) / (ms * 1e-3) / 1e12 if upper else None}))
+
+
+if __name__ == "__main__":
+    main()
