@@ -130,6 +130,23 @@ sp2_status sp2_get_info(sp2_handle h, sp2_info* out);
 /* Free the handle and its workspace (synchronises the device first).  NULL is a no-op. */
 void sp2_destroy(sp2_handle h);
 
+/* FP64 purification that allocates no memory (the paper has no counterpart; this is a
+ * service for callers that cannot call cudaMalloc, e.g. code running under another
+ * component's allocator or in loops where entering the allocator is not allowed).
+ * Same method and result as an SP2_PREC_FP64 handle with default options
+ * (max_iter 200, guard on, qtilde 1.8), for 1 <= N <= SP2_NOALLOC_MAX_N.
+ * F_dev, D_dev: N x N device buffers as in sp2_run.  info_dev: NULL or 4 device
+ * int32 that receive (status, n_iter, stop_reason, hist_len) when the run ends.
+ * Asynchronous on `stream`.  The workspace is one fixed device array inside the
+ * library (about 4.2 MB, held on every GPU that loads the library until exit);
+ * N > SP2_NOALLOC_MAX_N returns SP2_ERR_INVALID_ARG.  The first call on a device
+ * looks up that array's device address, so make it before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU race and must be serialised
+ * by the caller. */
+#define SP2_NOALLOC_MAX_N 512
+sp2_status sp2_run_fp64_noalloc(const double* F_dev, double* D_dev, int64_t N, int64_t n_occ,
+                                int32_t* info_dev, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* sp2_status_string(int32_t status);
 

@@ -298,6 +298,25 @@ __global__ void copy_out_kernel(const DevState* st, const double* __restrict__ b
   }
 }
 
+// Reduction + stop test of one FP64 square for loops driven without a CUDA graph:
+// the same rules as finalize_kernel (stride 2), ending the loop through st->done only.
+__global__ void __launch_bounds__(kFinThreads)
+finalize_plain_kernel(DevState* st, const double* __restrict__ part, int nparts) {
+  __shared__ double sm[32];
+  if (st->done) return;
+  double a = 0.0, b = 0.0;
+  for (int t = threadIdx.x; t < nparts; t += kFinThreads) {
+    a += part[2 * (int64_t)t];
+    b += part[2 * (int64_t)t + 1];
+  }
+  a = block_sum<kFinThreads>(a, sm);
+  b = block_sum<kFinThreads>(b, sm);
+  if (threadIdx.x != 0) return;
+  const int k = st->k + 1;
+  const int pk = st->tr[k - 1] > (double)st->nocc ? 1 : 0;
+  record_and_test(st, pk, sqrt(a), b, st->tr[k - 1]);
+}
+
 // ---- host-side launchers ------------------------------------------------------------------
 static int elementwise_blocks(int64_t total) {
   int64_t b = (total + 255) / 256;
@@ -315,6 +334,14 @@ cudaError_t launch_bounds_and_init(DevState* st, const double* F, int64_t ldf, i
 cudaError_t launch_scale_f64(const DevState* st, const double* F, int64_t ldf, int N, double* X0,
                              int ld, cudaStream_t s) {
   scale_kernel<<<elementwise_blocks((int64_t)N * N), 256, 0, s>>>(st, F, ldf, X0, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f64_step_plain(DevState* st, double* buf0, double* buf1, double* part, int T,
+                                  cudaStream_t s) {
+  const int ntiles = T * (T + 1) / 2;
+  syrk_f64_kernel<<<ntiles, kSyrkThreads, 0, s>>>(st, buf0, buf1, part);
+  finalize_plain_kernel<<<1, kFinThreads, 0, s>>>(st, part, ntiles);
   return cudaGetLastError();
 }
 

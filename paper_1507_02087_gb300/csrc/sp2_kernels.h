@@ -60,6 +60,10 @@ cudaError_t add_corrected_to_pieces_node(cudaGraph_t g, const cudaGraphNode_t* d
 }  // namespace sp2
 
 namespace sp2 {
+// One FP64 square + stop test launched directly on a stream (no graph); a no-op once
+// st->done is set.
+cudaError_t launch_f64_step_plain(DevState* st, double* buf0, double* buf1, double* part, int T,
+                                  cudaStream_t s);
 // FP64 purification step `step` (0 or 1) on an ld x ld FP64 matrix (mixed-path refinement).
 cudaError_t launch_refine_f64(const DevState* st, const double* Xin, double* Xout, int ld, int step, double* part,
                               cudaStream_t s);

@@ -73,6 +73,8 @@ def lib() -> ctypes.CDLL:
         L.sp2_status_string.restype = ctypes.c_char_p
         L.sp2_test_tc_gemm.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp]
         L.sp2_test_tc_gemm.restype = i32
+        L.sp2_run_fp64_noalloc.argtypes = [vp, vp, i64, i64, vp, vp]
+        L.sp2_run_fp64_noalloc.restype = i32
         _lib = L
     return _lib
 
