@@ -130,6 +130,32 @@ sp2_status sp2_get_info(sp2_handle h, sp2_info* out);
 /* Free the handle and its workspace (synchronises the device first).  NULL is a no-op. */
 void sp2_destroy(sp2_handle h);
 
+/* ---- batches of problems of uneven size ------------------------------------------------
+ * A batch handle holds `count` independent problems (1 <= count <= SP2_MAX_BATCH), problem
+ * i of size N[i] with n_occ[i] occupied orbitals.  With SP2_PREC_MIXED one run of the
+ * batch is one stream-ordered launch sequence: every round of the expansion is a single
+ * persistent tensor-core launch over the tiles of all problems still iterating, each
+ * problem stops on its own parameterless test (Alg. 3), and the correction, derivative
+ * and refinement rounds are batched the same way.  With SP2_PREC_FP64 the problems run one
+ * after the other on the FP64 path.  Workspace is the sum of the single-problem workspaces. */
+#define SP2_MAX_BATCH 256
+typedef struct sp2_batch_ctx* sp2_batch;
+
+/* Create a batch handle; N and n_occ are host arrays of `count` entries.  opts as for
+ * sp2_create (refine_fp64 must be 0 for SP2_PREC_MIXED batches with count > 1). */
+sp2_status sp2_create_batch(int32_t count, const int64_t* N, const int64_t* n_occ, int32_t precision,
+                            const sp2_opts* opts, sp2_batch* out);
+
+/* Enqueue the batch: F_dev[i] -> D_dev[i] (host arrays of `count` device pointers, each
+ * buffer as in sp2_run).  Asynchronous; no host synchronisation. */
+sp2_status sp2_run_batch(sp2_batch hb, const double* const* F_dev, double* const* D_dev, void* stream);
+
+/* Wait for the batch's last run and describe problem i (arrays valid until the next run). */
+sp2_status sp2_get_info_batch(sp2_batch hb, int32_t i, sp2_info* out);
+
+/* Free a batch handle (synchronises the device first).  NULL is a no-op. */
+void sp2_destroy_batch(sp2_batch hb);
+
 /* FP64 purification that allocates no memory (the paper has no counterpart; this is a
  * service for callers that cannot call cudaMalloc, e.g. code running under another
  * component's allocator or in loops where entering the allocator is not allowed).

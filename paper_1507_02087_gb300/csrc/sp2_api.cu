@@ -1,56 +1,30 @@
 // C-ABI layer: handles, workspace, and the device-controlled loops as CUDA graphs
-// with conditional WHILE nodes, plus the host-buffer entry point.
+// with conditional WHILE nodes, plus the host-buffer and batch entry points.
 //
 // FP64 run:  bounds + init, scaling, [WHILE: FP64 square + stop test], output copy.
-// Mixed run: bounds + init, scaling + piece split, [WHILE: tensor-core square + stop
-//            test], correction GEMMs (M = P F, dX_0 from M + M^T - 2 M P),
-//            [WHILE: derivative step], D = X_n + dX_n, optional FP64 refinement pair.
+// Mixed run (a batch of one or more problems):
+//   batched bounds + init + scaling/piece split,
+//   [WHILE: one tensor-core launch squaring every live problem, per-problem stop test],
+//   correction GEMMs (M = P F, dX_0 from M + M^T - 2 M P),
+//   [WHILE: one derivative step for every problem short of its n],
+//   refinement pair on the corrected D, output.
 // Nothing waits on the host in between; the loop conditions are cleared on the device.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <numeric>
+#include <vector>
 
 #include "sp2_common.cuh"
 #include "sp2_kernels.h"
 #include "sp2_tc.cuh"
 
 using sp2::DevState;
-
-struct sp2_ctx {
-  int64_t N = 0, nocc = 0;
-  int32_t precision = 0;
-  sp2_opts opts{};
-  int device = 0;
-  int ld = 0, T = 0, nparts = 0;
-  // FP64 path (and the mixed path's refinement)
-  double* buf[2] = {nullptr, nullptr};
-  double* part = nullptr;
-  double* part_lo = nullptr;
-  double* part_hi = nullptr;
-  int* part_bad = nullptr;
-  DevState* st_dev = nullptr;
-  DevState* st_host = nullptr;   // pinned mirror for sp2_get_info
-  int32_t* err_dev = nullptr;    // device-side wait failures
-  int32_t* err_host = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaGraphConditionalHandle cond = 0, cond2 = 0;
-  cudaStream_t last_stream = nullptr;
-  bool ran = false;
-  double* stage_F = nullptr;     // device staging for sp2_run_host
-  double* stage_D = nullptr;
-  cudaEvent_t ev_loop[2] = {nullptr, nullptr};
-  // mixed path
-  void* arena = nullptr;
-  int64_t slot_elems = 0;
-  int nslots = 0, hist0 = 0, dx0 = 0, m_slot = 0, f_slot = 0, r0_slot = 0;
-  CUtensorMap mapA, mapB;
-  double* part_tc = nullptr;
-  int tiles_upper = 0;
-};
+using sp2::tc::Instance;
 
 #define SP2_TRY(expr)                              \
   do {                                             \
@@ -85,33 +59,19 @@ extern "C" const char* sp2_status_string(int32_t s) {
   }
 }
 
-static void free_ctx(sp2_ctx* h) {
-  if (!h) return;
-  int cur = 0;
-  cudaGetDevice(&cur);
-  cudaSetDevice(h->device);
-  cudaDeviceSynchronize();
-  if (h->exec) cudaGraphExecDestroy(h->exec);
-  if (h->graph) cudaGraphDestroy(h->graph);
-  cudaFree(h->buf[0]);
-  cudaFree(h->buf[1]);
-  cudaFree(h->part);
-  cudaFree(h->part_lo);
-  cudaFree(h->part_hi);
-  cudaFree(h->part_bad);
-  cudaFree(h->st_dev);
-  cudaFree(h->err_dev);
-  cudaFree(h->stage_F);
-  cudaFree(h->stage_D);
-  cudaFree(h->arena);
-  cudaFree(h->part_tc);
-  if (h->st_host) cudaFreeHost(h->st_host);
-  if (h->err_host) cudaFreeHost(h->err_host);
-  if (h->ev_loop[0]) cudaEventDestroy(h->ev_loop[0]);
-  if (h->ev_loop[1]) cudaEventDestroy(h->ev_loop[1]);
-  (void)cudaGetLastError();
-  cudaSetDevice(cur);
-  delete h;
+static bool opts_valid(const sp2_opts& o) {
+  return o.max_iter >= 1 && o.max_iter <= SP2_MAX_ITER && o.qtilde > 0.0 && (o.guard == 0 || o.guard == 1) &&
+         o.corrections >= 0 && o.corrections <= 1 && (o.refine_steps == 0 || o.refine_steps == 2) &&
+         (o.refine_fp64 == 0 || o.refine_fp64 == 1) && o.reserved == 0;
+}
+
+static DevState initial_state(int64_t N, int64_t nocc, const sp2_opts& o, int ld, int round_fp32) {
+  DevState init;
+  std::memset(&init, 0, sizeof(init));
+  init.N = (int32_t)N; init.ld = ld; init.nocc = (int32_t)nocc;
+  init.max_iter = o.max_iter; init.guard = o.guard; init.qtilde = o.qtilde;
+  init.round_fp32 = round_fp32;
+  return init;
 }
 
 static sp2_status add_while(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, cudaGraphConditionalHandle* cond,
@@ -128,86 +88,322 @@ static sp2_status add_while(cudaGraph_t g, const cudaGraphNode_t* deps, int ndep
   return SP2_OK;
 }
 
-static sp2_status build_graph_f64(sp2_ctx* h) {
+// ---------------------------------------------------------------------------------------------
+// Mixed-precision engine: `count` problems, stored largest first (internal order).
+// ---------------------------------------------------------------------------------------------
+struct MixedEngine {
+  int count = 0;
+  sp2_opts opts{};
+  std::vector<int> user_of;        // internal index -> user index
+  std::vector<int> internal_of;    // user index -> internal index
+  std::vector<int64_t> N, nocc;    // internal order
+  std::vector<Instance> inst_host;
+  Instance* inst_dev = nullptr;
+  DevState* st_dev = nullptr;
+  DevState* st_host = nullptr;     // pinned mirror
+  std::vector<void*> arenas;
+  std::vector<double*> parts;
+  double* part_lo = nullptr;
+  double* part_hi = nullptr;
+  int* part_bad = nullptr;
+  int pb = 1, sb = 1;
+  int total_upper = 0, total_full = 0;
+  int32_t* err_dev = nullptr;
+  int32_t* err_host = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond = 0, cond2 = 0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  double* fbuf[2] = {nullptr, nullptr};   // FP64 refinement (single problem only)
+  double* fpart = nullptr;
+  int fld = 0;
+
+  ~MixedEngine() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaFree(inst_dev);
+    cudaFree(st_dev);
+    for (void* a : arenas) cudaFree(a);
+    for (double* p : parts) cudaFree(p);
+    cudaFree(part_lo);
+    cudaFree(part_hi);
+    cudaFree(part_bad);
+    cudaFree(err_dev);
+    cudaFree(fbuf[0]);
+    cudaFree(fbuf[1]);
+    cudaFree(fpart);
+    if (st_host) cudaFreeHost(st_host);
+    if (err_host) cudaFreeHost(err_host);
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+    (void)cudaGetLastError();
+  }
+
+  sp2::tc::Job job(int mode, int upper, int rule, int nterms = 1) const {
+    sp2::tc::Job j;
+    std::memset(&j, 0, sizeof(j));
+    j.mode = mode;
+    j.upper = upper;
+    j.nterms = nterms;
+    j.rule = rule;
+    j.count = count;
+    j.total_tiles = upper ? total_upper : total_full;
+    j.inst = inst_dev;
+    j.err = err_dev;
+    return j;
+  }
+
+  sp2_status init(int cnt, const int64_t* Nu, const int64_t* noccu, const sp2_opts& o) {
+    using namespace sp2::tc;
+    count = cnt;
+    opts = o;
+    user_of.resize(count);
+    std::iota(user_of.begin(), user_of.end(), 0);
+    std::stable_sort(user_of.begin(), user_of.end(), [&](int a, int b) { return Nu[a] > Nu[b]; });
+    internal_of.resize(count);
+    for (int k = 0; k < count; ++k) internal_of[user_of[k]] = k;
+    N.resize(count);
+    nocc.resize(count);
+    int64_t maxN = 1;
+    for (int k = 0; k < count; ++k) {
+      N[k] = Nu[user_of[k]];
+      nocc[k] = noccu[user_of[k]];
+      maxN = std::max(maxN, N[k]);
+    }
+    pb = (int)std::max<int64_t>(1, std::min<int64_t>((maxN + 7) / 8, std::max(4, 2048 / count)));
+    sb = (int)std::max<int64_t>(1, std::min<int64_t>((maxN * maxN + 255) / 256, std::max(4, 2432 / count)));
+    if (cudaMalloc(&inst_dev, sizeof(Instance) * count) != cudaSuccess ||
+        cudaMalloc(&st_dev, sizeof(DevState) * count) != cudaSuccess ||
+        cudaMallocHost(&st_host, sizeof(DevState) * count) != cudaSuccess ||
+        cudaMalloc(&part_lo, sizeof(double) * count * pb) != cudaSuccess ||
+        cudaMalloc(&part_hi, sizeof(double) * count * pb) != cudaSuccess ||
+        cudaMalloc(&part_bad, sizeof(int) * count * pb) != cudaSuccess ||
+        cudaMalloc(&err_dev, sizeof(int32_t)) != cudaSuccess ||
+        cudaMallocHost(&err_host, sizeof(int32_t)) != cudaSuccess || cudaEventCreate(&ev[0]) != cudaSuccess ||
+        cudaEventCreate(&ev[1]) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return SP2_ERR_NOMEM;
+    }
+    inst_host.resize(count);
+    arenas.assign(count, nullptr);
+    parts.assign(count, nullptr);
+    const int H = o.max_iter + 2;
+    int off_u = 0, off_f = 0;
+    for (int k = 0; k < count; ++k) {
+      Instance& I = inst_host[k];
+      std::memset(&I, 0, sizeof(I));
+      const int ld = (int)((N[k] + LD_ALIGN - 1) / LD_ALIGN * LD_ALIGN);
+      I.ld = ld;
+      I.hist0 = 0;
+      I.dx0 = H;
+      I.m_slot = H + 2;
+      I.f_slot = H + 3;
+      I.r0_slot = H + 4;
+      const int nslots = H + 6;
+      I.slot_elems = (int64_t)NP * ld * ld;
+      I.st = st_dev + k;
+      I.tile_off_upper = off_u;
+      I.tile_off_full = off_f;
+      off_u += tiles_of(ld, 1);
+      off_f += tiles_of(ld, 0);
+      const size_t abytes = (size_t)nslots * I.slot_elems * 2;
+      if (cudaMalloc(&arenas[k], abytes) != cudaSuccess ||
+          cudaMalloc(&parts[k], sizeof(double) * 16 * tiles_of(ld, 1)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return SP2_ERR_NOMEM;
+      }
+      // zero borders stay zero for the life of the handle (every step maps 0 to 0)
+      SP2_TRY(cudaMemset(arenas[k], 0, abytes));
+      I.arena = (__nv_bfloat16*)arenas[k];
+      I.part = parts[k];
+      SP2_TRY(sp2::tc_make_maps(arenas[k], ld, nslots, &I.mapA, &I.mapB));
+      st_host[k] = initial_state(N[k], nocc[k], o, ld, 1);
+    }
+    total_upper = off_u;
+    total_full = off_f;
+    SP2_TRY(cudaMemcpy(inst_dev, inst_host.data(), sizeof(Instance) * count, cudaMemcpyHostToDevice));
+    SP2_TRY(cudaMemcpy(st_dev, st_host, sizeof(DevState) * count, cudaMemcpyHostToDevice));
+    SP2_TRY(cudaMemset(err_dev, 0, sizeof(int32_t)));
+    *err_host = 0;
+    if (o.refine_steps > 0 && o.refine_fp64) {
+      if (count != 1) return SP2_ERR_UNSUPPORTED;
+      fld = (int)((N[0] + 63) / 64 * 64);
+      const size_t fb = (size_t)fld * fld * sizeof(double);
+      const int T = fld / 64;
+      if (cudaMalloc(&fbuf[0], fb) != cudaSuccess || cudaMalloc(&fbuf[1], fb) != cudaSuccess ||
+          cudaMalloc(&fpart, sizeof(double) * T * (T + 1)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return SP2_ERR_NOMEM;
+      }
+      SP2_TRY(cudaMemset(fbuf[0], 0, fb));
+      SP2_TRY(cudaMemset(fbuf[1], 0, fb));
+    }
+    return build_graph();
+  }
+
+  sp2_status build_graph() {
+    using namespace sp2::tc;
+    SP2_TRY(cudaGraphCreate(&graph, 0));
+    cudaGraphNode_t n_fwd, n_sq, last;
+    cudaGraph_t body;
+    sp2_status s = add_while(graph, nullptr, 0, &cond, &n_fwd, &body);
+    if (s != SP2_OK) return s;
+    SP2_TRY(sp2::tc_add_node(body, nullptr, 0, job(MODE_SP2_STEP, 1, SLOTS_FORWARD), &n_sq));
+    SP2_TRY(sp2::batch_add_forward_tail(body, &n_sq, inst_dev, count, cond));
+    last = n_fwd;
+    if (opts.corrections > 0) {
+      cudaGraphNode_t n_m, n_df, n_der, n_dsq;
+      SP2_TRY(sp2::tc_add_node(graph, &last, 1, job(MODE_STORE_PIECES, 0, SLOTS_CORR_M), &n_m));
+      SP2_TRY(sp2::tc_add_node(graph, &n_m, 1, job(MODE_DF_COMBINE, 1, SLOTS_CORR_DF), &n_df));
+      cudaGraph_t dbody;
+      s = add_while(graph, &n_df, 1, &cond2, &n_der, &dbody);
+      if (s != SP2_OK) return s;
+      SP2_TRY(sp2::tc_add_node(dbody, nullptr, 0, job(MODE_DERIV_STEP, 1, SLOTS_DERIV, 2), &n_dsq));
+      SP2_TRY(sp2::batch_add_deriv_tail(dbody, &n_dsq, inst_dev, count, cond2));
+      last = n_der;
+    }
+    if (opts.refine_steps > 0 && !opts.refine_fp64) {
+      cudaGraphNode_t n_piece, n_r0, n_r1;
+      SP2_TRY(sp2::batch_add_corrected_to_pieces(graph, &last, inst_dev, count, sb, opts.corrections > 0,
+                                                 &n_piece));
+      // one SP2 step each: new = p ? C : 2 in - C with C = in^2
+      Job jr = job(MODE_DERIV_STEP, 1, SLOTS_REFINE);
+      jr.a_slot[0] = 0;
+      SP2_TRY(sp2::tc_add_node(graph, &n_piece, 1, jr, &n_r0));
+      jr.a_slot[0] = 1;
+      SP2_TRY(sp2::tc_add_node(graph, &n_r0, 1, jr, &n_r1));
+    }
+    SP2_TRY(cudaGraphInstantiate(&exec, graph, 0));
+    return SP2_OK;
+  }
+
+  // F/D in user order.
+  sp2_status enqueue(const double* const* F, double* const* D, cudaStream_t s) {
+    sp2::BatchPtrs ptrs;
+    std::memset(&ptrs, 0, sizeof(ptrs));
+    for (int k = 0; k < count; ++k) {
+      ptrs.F[k] = F[user_of[k]];
+      ptrs.D[k] = D[user_of[k]];
+    }
+    SP2_TRY(cudaMemsetAsync(err_dev, 0, sizeof(int32_t), s));
+    SP2_TRY(sp2::batch_launch_prologue(inst_dev, count, pb, sb, ptrs, part_lo, part_hi, part_bad, s));
+    SP2_TRY(cudaEventRecord(ev[0], s));
+    SP2_TRY(cudaGraphLaunch(exec, s));
+    SP2_TRY(cudaEventRecord(ev[1], s));
+    const int use_dx = opts.corrections > 0;
+    if (opts.refine_steps > 0 && opts.refine_fp64) {
+      SP2_TRY(sp2::batch_launch_assemble(inst_dev, count, sb, use_dx, 0, ptrs, fbuf[0], s));
+      SP2_TRY(sp2::launch_refine_f64(st_dev, fbuf[0], fbuf[1], fld, 0, fpart, s));
+      SP2_TRY(sp2::launch_refine_f64(st_dev, fbuf[1], fbuf[0], fld, 1, fpart, s));
+      SP2_TRY(sp2::launch_copy_f64(st_dev, fbuf[0], fld, (int)N[0], ptrs.D[0], N[0], s));
+    } else {
+      SP2_TRY(sp2::batch_launch_assemble(inst_dev, count, sb, use_dx, opts.refine_steps > 0 ? 1 : 0, ptrs,
+                                         nullptr, s));
+    }
+    SP2_TRY(cudaMemcpyAsync(st_host, st_dev, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s));
+    SP2_TRY(cudaMemcpyAsync(err_host, err_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    return SP2_OK;
+  }
+
+  void info(int user_index, bool ran, sp2_info* out) const {
+    const DevState* st = st_host + internal_of[user_index];
+    out->status = ran ? st->status : SP2_OK;
+    if (ran && out->status == SP2_OK && *err_host != 0) out->status = *err_host;
+    out->n_iter = st->n_out;
+    out->stop_reason = st->reason;
+    out->hist_len = st->hist_len;
+    out->lambda_min = st->lmin;
+    out->lambda_max = st->lmax;
+    float ms = 0.f;
+    if (ran && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) out->loop_ms = ms;
+    (void)cudaGetLastError();
+    out->v = st->v;
+    out->trace = st->tr;
+    out->p = st->p;
+  }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Single-problem handle
+// ---------------------------------------------------------------------------------------------
+struct sp2_ctx {
+  int64_t N = 0, nocc = 0;
+  int32_t precision = 0;
+  sp2_opts opts{};
+  int device = 0;
+  cudaStream_t last_stream = nullptr;
+  bool ran = false;
+  double* stage_F = nullptr;     // device staging for sp2_run_host
+  double* stage_D = nullptr;
+  // FP64 path
+  int ld = 0, T = 0, nparts = 0;
+  double* buf[2] = {nullptr, nullptr};
+  double* part = nullptr;
+  double* part_lo = nullptr;
+  double* part_hi = nullptr;
+  int* part_bad = nullptr;
+  DevState* st_dev = nullptr;
+  DevState* st_host = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  cudaEvent_t ev_loop[2] = {nullptr, nullptr};
+  // mixed path
+  MixedEngine* mixed = nullptr;
+};
+
+static void free_ctx(sp2_ctx* h) {
+  if (!h) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  delete h->mixed;
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  cudaFree(h->buf[0]);
+  cudaFree(h->buf[1]);
+  cudaFree(h->part);
+  cudaFree(h->part_lo);
+  cudaFree(h->part_hi);
+  cudaFree(h->part_bad);
+  cudaFree(h->st_dev);
+  cudaFree(h->stage_F);
+  cudaFree(h->stage_D);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->ev_loop[0]) cudaEventDestroy(h->ev_loop[0]);
+  if (h->ev_loop[1]) cudaEventDestroy(h->ev_loop[1]);
+  (void)cudaGetLastError();
+  cudaSetDevice(cur);
+  delete h;
+}
+
+static sp2_status create_f64(sp2_ctx* h) {
+  h->ld = (int)((h->N + 63) / 64 * 64);
+  h->T = h->ld / 64;
+  h->nparts = (int)((h->N + 7) / 8 < 1024 ? (h->N + 7) / 8 : 1024);
+  const size_t bytes = (size_t)h->ld * h->ld * sizeof(double);
+  const size_t ntiles = (size_t)h->T * (h->T + 1) / 2;
+  bool ok = cudaMalloc(&h->part, ntiles * 2 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&h->part_lo, h->nparts * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&h->part_hi, h->nparts * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&h->part_bad, h->nparts * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->st_dev, sizeof(DevState)) == cudaSuccess &&
+            cudaMallocHost(&h->st_host, sizeof(DevState)) == cudaSuccess &&
+            cudaEventCreate(&h->ev_loop[0]) == cudaSuccess && cudaEventCreate(&h->ev_loop[1]) == cudaSuccess &&
+            cudaMalloc(&h->buf[0], bytes) == cudaSuccess && cudaMalloc(&h->buf[1], bytes) == cudaSuccess;
+  if (!ok) { (void)cudaGetLastError(); return SP2_ERR_NOMEM; }
+  DevState init = initial_state(h->N, h->nocc, h->opts, h->ld, 0);
+  SP2_TRY(cudaMemcpy(h->st_dev, &init, sizeof(init), cudaMemcpyHostToDevice));
+  SP2_TRY(cudaMemset(h->buf[0], 0, bytes));
+  SP2_TRY(cudaMemset(h->buf[1], 0, bytes));
+  *h->st_host = init;
   SP2_TRY(cudaGraphCreate(&h->graph, 0));
   cudaGraphNode_t node;
   cudaGraph_t body;
   sp2_status s = add_while(h->graph, nullptr, 0, &h->cond, &node, &body);
   if (s != SP2_OK) return s;
   SP2_TRY(sp2::add_f64_loop_body(body, h->st_dev, h->buf[0], h->buf[1], h->part, h->T, h->cond));
-  SP2_TRY(cudaGraphInstantiate(&h->exec, h->graph, 0));
-  return SP2_OK;
-}
-
-static sp2::tc::Job base_job(const sp2_ctx* h) {
-  sp2::tc::Job j;
-  std::memset(&j, 0, sizeof(j));
-  j.ld = h->ld;
-  j.arena = (__nv_bfloat16*)h->arena;
-  j.slot_elems = h->slot_elems;
-  j.st = h->st_dev;
-  j.err = h->err_dev;
-  j.hist0 = h->hist0;
-  j.dx0 = h->dx0;
-  j.m_slot = h->m_slot;
-  j.f_slot = h->f_slot;
-  j.r0_slot = h->r0_slot;
-  j.nterms = 1;
-  return j;
-}
-
-static sp2_status build_graph_mixed(sp2_ctx* h) {
-  using namespace sp2::tc;
-  SP2_TRY(cudaGraphCreate(&h->graph, 0));
-  cudaGraphNode_t n_fwd, n_sq, n_fin;
-  cudaGraph_t body;
-  sp2_status s = add_while(h->graph, nullptr, 0, &h->cond, &n_fwd, &body);
-  if (s != SP2_OK) return s;
-  Job fwd = base_job(h);
-  fwd.mode = MODE_SP2_STEP;
-  fwd.upper = 1;
-  fwd.rule = SLOTS_FORWARD;
-  fwd.part = h->part_tc;
-  SP2_TRY(sp2::tc_add_node(body, nullptr, 0, h->mapA, h->mapB, fwd, &n_sq));
-  SP2_TRY(sp2::add_finalize_node(body, &n_sq, 1, h->st_dev, h->part_tc, 4 * h->tiles_upper, 4, h->cond, &n_fin));
-  if (h->opts.corrections > 0) {
-    cudaGraphNode_t n_m, n_df, n_der, n_dsq, n_dfin;
-    Job jm = base_job(h);
-    jm.mode = MODE_STORE_PIECES;
-    jm.upper = 0;
-    jm.rule = SLOTS_CORR_M;
-    SP2_TRY(sp2::tc_add_node(h->graph, &n_fwd, 1, h->mapA, h->mapB, jm, &n_m));
-    Job jd = base_job(h);
-    jd.mode = MODE_DF_COMBINE;
-    jd.upper = 1;
-    jd.rule = SLOTS_CORR_DF;
-    SP2_TRY(sp2::tc_add_node(h->graph, &n_m, 1, h->mapA, h->mapB, jd, &n_df));
-    cudaGraph_t dbody;
-    s = add_while(h->graph, &n_df, 1, &h->cond2, &n_der, &dbody);
-    if (s != SP2_OK) return s;
-    Job jv = base_job(h);
-    jv.mode = MODE_DERIV_STEP;
-    jv.upper = 1;
-    jv.nterms = 2;
-    jv.rule = SLOTS_DERIV;
-    SP2_TRY(sp2::tc_add_node(dbody, nullptr, 0, h->mapA, h->mapB, jv, &n_dsq));
-    SP2_TRY(sp2::add_deriv_finalize_node(dbody, &n_dsq, 1, h->st_dev, h->cond2, &n_dfin));
-    n_fwd = n_der;
-  }
-  if (h->opts.refine_steps > 0 && !h->opts.refine_fp64) {
-    cudaGraphNode_t n_piece, n_r0, n_r1;
-    SP2_TRY(sp2::add_corrected_to_pieces_node(h->graph, &n_fwd, 1, h->st_dev, h->arena, h->slot_elems, h->ld,
-                                              h->hist0, h->dx0, h->opts.corrections > 0, h->r0_slot, (int)h->N,
-                                              &n_piece));
-    Job jr = base_job(h);
-    jr.mode = MODE_DERIV_STEP;   // new = p ? C : 2 in - C with C = in^2: one SP2 step
-    jr.upper = 1;
-    jr.rule = SLOTS_REFINE;
-    jr.a_slot[0] = 0;
-    SP2_TRY(sp2::tc_add_node(h->graph, &n_piece, 1, h->mapA, h->mapB, jr, &n_r0));
-    jr.a_slot[0] = 1;
-    SP2_TRY(sp2::tc_add_node(h->graph, &n_r0, 1, h->mapA, h->mapB, jr, &n_r1));
-  }
   SP2_TRY(cudaGraphInstantiate(&h->exec, h->graph, 0));
   return SP2_OK;
 }
@@ -221,73 +417,20 @@ extern "C" sp2_status sp2_create(int64_t N, int64_t nocc, int32_t precision, con
   sp2_opts o;
   sp2_default_opts(&o);
   if (opts) o = *opts;
-  if (o.max_iter < 1 || o.max_iter > SP2_MAX_ITER || !(o.qtilde > 0.0) || (o.guard != 0 && o.guard != 1) ||
-      o.corrections < 0 || o.corrections > 1 || (o.refine_steps != 0 && o.refine_steps != 2) ||
-      (o.refine_fp64 != 0 && o.refine_fp64 != 1) || o.reserved != 0)
-    return SP2_ERR_INVALID_ARG;
-
+  if (!opts_valid(o)) return SP2_ERR_INVALID_ARG;
   sp2_ctx* h = new (std::nothrow) sp2_ctx();
   if (!h) return SP2_ERR_NOMEM;
   h->N = N; h->nocc = nocc; h->precision = precision; h->opts = o;
   if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; (void)cudaGetLastError(); return SP2_ERR_CUDA; }
-  const bool mixed = precision == SP2_PREC_MIXED;
-  const int align = mixed ? sp2::tc::LD_ALIGN : 64;
-  h->ld = (int)((N + align - 1) / align * align);
-  h->T = h->ld / 64;
-  h->nparts = (int)((N + 7) / 8 < 1024 ? (N + 7) / 8 : 1024);
-  const size_t bytes = (size_t)h->ld * h->ld * sizeof(double);
-  const size_t ntiles = (size_t)h->T * (h->T + 1) / 2;
-  const bool need_f64 = !mixed || (o.refine_steps > 0 && o.refine_fp64);
-  bool ok = cudaMalloc(&h->part, ntiles * 2 * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&h->part_lo, h->nparts * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&h->part_hi, h->nparts * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&h->part_bad, h->nparts * sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&h->st_dev, sizeof(DevState)) == cudaSuccess &&
-            cudaMalloc(&h->err_dev, sizeof(int32_t)) == cudaSuccess &&
-            cudaMallocHost(&h->st_host, sizeof(DevState)) == cudaSuccess &&
-            cudaMallocHost(&h->err_host, sizeof(int32_t)) == cudaSuccess &&
-            cudaEventCreate(&h->ev_loop[0]) == cudaSuccess && cudaEventCreate(&h->ev_loop[1]) == cudaSuccess;
-  if (ok && need_f64)
-    ok = cudaMalloc(&h->buf[0], bytes) == cudaSuccess && cudaMalloc(&h->buf[1], bytes) == cudaSuccess;
-  if (ok && mixed) {
-    h->hist0 = 0;
-    const int H = o.max_iter + 2;
-    h->dx0 = H;
-    h->m_slot = H + 2;
-    h->f_slot = H + 3;
-    h->r0_slot = H + 4;
-    h->nslots = H + 6;
-    h->slot_elems = (int64_t)sp2::tc::NP * h->ld * h->ld;
-    h->tiles_upper = sp2::tc_tiles(h->ld, 1);
-    ok = cudaMalloc(&h->arena, (size_t)h->nslots * h->slot_elems * 2) == cudaSuccess &&
-         cudaMalloc(&h->part_tc, (size_t)h->tiles_upper * 16 * sizeof(double)) == cudaSuccess;
-  }
-  if (!ok) { (void)cudaGetLastError(); free_ctx(h); return SP2_ERR_NOMEM; }
-  // Zero borders stay zero for the whole life of the handle (every step maps 0 to 0).
-  DevState init;
-  std::memset(&init, 0, sizeof(init));
-  init.N = (int32_t)N; init.ld = h->ld; init.nocc = (int32_t)nocc;
-  init.max_iter = o.max_iter; init.guard = o.guard; init.qtilde = o.qtilde;
-  init.round_fp32 = mixed ? 1 : 0;
-  bool okz = cudaMemcpy(h->st_dev, &init, sizeof(init), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemset(h->err_dev, 0, sizeof(int32_t)) == cudaSuccess;
-  if (okz && need_f64)
-    okz = cudaMemset(h->buf[0], 0, bytes) == cudaSuccess && cudaMemset(h->buf[1], 0, bytes) == cudaSuccess;
-  if (okz && mixed) okz = cudaMemset(h->arena, 0, (size_t)h->nslots * h->slot_elems * 2) == cudaSuccess;
-  if (!okz) { (void)cudaGetLastError(); free_ctx(h); return SP2_ERR_CUDA; }
-  *h->st_host = init;
-  *h->err_host = 0;
-  sp2_status s = SP2_OK;
-  if (mixed) {
-    if (sp2::tc_make_maps(h->arena, h->ld, h->nslots, &h->mapA, &h->mapB) != cudaSuccess) {
-      (void)cudaGetLastError(); free_ctx(h); return SP2_ERR_CUDA;
-    }
-    s = build_graph_mixed(h);
+  sp2_status s;
+  if (precision == SP2_PREC_MIXED) {
+    h->mixed = new (std::nothrow) MixedEngine();
+    s = h->mixed ? h->mixed->init(1, &N, &nocc, o) : SP2_ERR_NOMEM;
   } else {
-    s = build_graph_f64(h);
+    s = create_f64(h);
   }
+  if (s == SP2_OK && cudaDeviceSynchronize() != cudaSuccess) { (void)cudaGetLastError(); s = SP2_ERR_CUDA; }
   if (s != SP2_OK) { free_ctx(h); return s; }
-  if (cudaDeviceSynchronize() != cudaSuccess) { (void)cudaGetLastError(); free_ctx(h); return SP2_ERR_CUDA; }
   *out = h;
   return SP2_OK;
 }
@@ -298,48 +441,32 @@ static bool overlaps(const void* a, const void* b, size_t bytes) {
   return x < y + bytes && y < x + bytes;
 }
 
-static sp2_status enqueue_run(sp2_ctx* h, const double* F, int64_t ldf, double* D, int64_t ldd,
-                              cudaStream_t s) {
+static sp2_status enqueue_f64(sp2_ctx* h, const double* F, double* D, cudaStream_t s) {
   const int N = (int)h->N;
-  SP2_TRY(cudaMemsetAsync(h->err_dev, 0, sizeof(int32_t), s));
-  SP2_TRY(sp2::launch_bounds_and_init(h->st_dev, F, ldf, N, h->part_lo, h->part_hi, h->part_bad,
-                                      h->nparts, s));
-  if (h->precision == SP2_PREC_MIXED) {
-    SP2_TRY(sp2::launch_scale_split(h->st_dev, F, ldf, N, h->arena, h->slot_elems, h->ld, h->hist0, h->f_slot, s));
-  } else {
-    SP2_TRY(sp2::launch_scale_f64(h->st_dev, F, ldf, N, h->buf[0], h->ld, s));
-  }
+  SP2_TRY(sp2::launch_bounds_and_init(h->st_dev, F, N, N, h->part_lo, h->part_hi, h->part_bad, h->nparts, s));
+  SP2_TRY(sp2::launch_scale_f64(h->st_dev, F, N, N, h->buf[0], h->ld, s));
   SP2_TRY(cudaEventRecord(h->ev_loop[0], s));
   SP2_TRY(cudaGraphLaunch(h->exec, s));
   SP2_TRY(cudaEventRecord(h->ev_loop[1], s));
-  if (h->precision == SP2_PREC_MIXED) {
-    const int use_dx = h->opts.corrections > 0;
-    if (h->opts.refine_steps > 0 && h->opts.refine_fp64) {
-      SP2_TRY(sp2::launch_assemble(h->st_dev, h->arena, h->slot_elems, h->ld, h->hist0, h->dx0, use_dx, h->r0_slot,
-                                   0, N, h->buf[0], h->ld, s));
-      SP2_TRY(sp2::launch_refine_f64(h->st_dev, h->buf[0], h->buf[1], h->ld, 0, h->part, s));
-      SP2_TRY(sp2::launch_refine_f64(h->st_dev, h->buf[1], h->buf[0], h->ld, 1, h->part, s));
-      SP2_TRY(sp2::launch_copy_f64(h->st_dev, h->buf[0], h->ld, N, D, ldd, s));
-    } else {
-      const int from_r0 = h->opts.refine_steps > 0 ? 1 : 0;
-      SP2_TRY(sp2::launch_assemble(h->st_dev, h->arena, h->slot_elems, h->ld, h->hist0, h->dx0, use_dx, h->r0_slot,
-                                   from_r0, N, D, ldd, s));
-    }
-  } else {
-    SP2_TRY(sp2::launch_copy_out(h->st_dev, h->buf[0], h->buf[1], h->ld, N, D, ldd, s));
-  }
+  SP2_TRY(sp2::launch_copy_out(h->st_dev, h->buf[0], h->buf[1], h->ld, N, D, N, s));
   SP2_TRY(cudaMemcpyAsync(h->st_host, h->st_dev, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-  SP2_TRY(cudaMemcpyAsync(h->err_host, h->err_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  h->last_stream = s;
-  h->ran = true;
   return SP2_OK;
+}
+
+static sp2_status enqueue_run(sp2_ctx* h, const double* F, double* D, cudaStream_t s) {
+  sp2_status st = h->mixed ? h->mixed->enqueue(&F, &D, s) : enqueue_f64(h, F, D, s);
+  if (st == SP2_OK) {
+    h->last_stream = s;
+    h->ran = true;
+  }
+  return st;
 }
 
 extern "C" sp2_status sp2_run(sp2_handle h, const double* F_dev, double* D_dev, void* stream) {
   if (!h || !F_dev || !D_dev) return SP2_ERR_INVALID_ARG;
   const size_t bytes = (size_t)h->N * h->N * sizeof(double);
   if (overlaps(F_dev, D_dev, bytes)) return SP2_ERR_INVALID_ARG;
-  return enqueue_run(h, F_dev, h->N, D_dev, h->N, (cudaStream_t)stream);
+  return enqueue_run(h, F_dev, D_dev, (cudaStream_t)stream);
 }
 
 extern "C" sp2_status sp2_run_host(sp2_handle h, const double* F_host, double* D_host, void* stream) {
@@ -356,7 +483,7 @@ extern "C" sp2_status sp2_run_host(sp2_handle h, const double* F_host, double* D
     }
   }
   SP2_TRY(cudaMemcpyAsync(h->stage_F, F_host, bytes, cudaMemcpyHostToDevice, s));
-  sp2_status st = enqueue_run(h, h->stage_F, h->N, h->stage_D, h->N, s);
+  sp2_status st = enqueue_run(h, h->stage_F, h->stage_D, s);
   if (st != SP2_OK) return st;
   SP2_TRY(cudaMemcpyAsync(D_host, h->stage_D, bytes, cudaMemcpyDeviceToHost, s));
   SP2_TRY(cudaStreamSynchronize(s));
@@ -367,9 +494,12 @@ extern "C" sp2_status sp2_get_info(sp2_handle h, sp2_info* out) {
   if (!h || !out) return SP2_ERR_INVALID_ARG;
   std::memset(out, 0, sizeof(*out));
   if (h->ran) SP2_TRY(cudaStreamSynchronize(h->last_stream));
+  if (h->mixed) {
+    h->mixed->info(0, h->ran, out);
+    return SP2_OK;
+  }
   const DevState* s = h->st_host;
   out->status = h->ran ? s->status : SP2_OK;
-  if (h->ran && out->status == SP2_OK && *h->err_host != 0) out->status = *h->err_host;
   out->n_iter = s->n_out;
   out->stop_reason = s->reason;
   out->hist_len = s->hist_len;
@@ -385,3 +515,94 @@ extern "C" sp2_status sp2_get_info(sp2_handle h, sp2_info* out) {
 }
 
 extern "C" void sp2_destroy(sp2_handle h) { free_ctx(h); }
+
+// ---------------------------------------------------------------------------------------------
+// Batch handle
+// ---------------------------------------------------------------------------------------------
+struct sp2_batch_ctx {
+  int count = 0;
+  int32_t precision = 0;
+  int device = 0;
+  std::vector<int64_t> N;
+  MixedEngine* mixed = nullptr;          // SP2_PREC_MIXED
+  std::vector<sp2_ctx*> singles;         // SP2_PREC_FP64: one handle per problem
+  cudaStream_t last_stream = nullptr;
+  bool ran = false;
+};
+
+extern "C" void sp2_destroy_batch(sp2_batch hb) {
+  if (!hb) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(hb->device);
+  cudaDeviceSynchronize();
+  delete hb->mixed;
+  for (sp2_ctx* h : hb->singles) free_ctx(h);
+  (void)cudaGetLastError();
+  cudaSetDevice(cur);
+  delete hb;
+}
+
+extern "C" sp2_status sp2_create_batch(int32_t count, const int64_t* N, const int64_t* nocc, int32_t precision,
+                                       const sp2_opts* opts, sp2_batch* out) {
+  if (!out) return SP2_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (count < 1 || count > SP2_MAX_BATCH || !N || !nocc) return SP2_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i)
+    if (N[i] < 1 || N[i] > 65536 || nocc[i] < 0 || nocc[i] > N[i]) return SP2_ERR_INVALID_ARG;
+  if (precision != SP2_PREC_FP64 && precision != SP2_PREC_MIXED) return SP2_ERR_UNSUPPORTED;
+  sp2_opts o;
+  sp2_default_opts(&o);
+  if (opts) o = *opts;
+  if (!opts_valid(o)) return SP2_ERR_INVALID_ARG;
+  if (precision == SP2_PREC_MIXED && o.refine_steps > 0 && o.refine_fp64 && count > 1) return SP2_ERR_UNSUPPORTED;
+  sp2_batch_ctx* hb = new (std::nothrow) sp2_batch_ctx();
+  if (!hb) return SP2_ERR_NOMEM;
+  hb->count = count;
+  hb->precision = precision;
+  hb->N.assign(N, N + count);
+  if (cudaGetDevice(&hb->device) != cudaSuccess) { delete hb; (void)cudaGetLastError(); return SP2_ERR_CUDA; }
+  sp2_status s = SP2_OK;
+  if (precision == SP2_PREC_MIXED) {
+    hb->mixed = new (std::nothrow) MixedEngine();
+    s = hb->mixed ? hb->mixed->init(count, N, nocc, o) : SP2_ERR_NOMEM;
+  } else {
+    hb->singles.assign(count, nullptr);
+    for (int i = 0; i < count && s == SP2_OK; ++i) s = sp2_create(N[i], nocc[i], SP2_PREC_FP64, &o, &hb->singles[i]);
+  }
+  if (s == SP2_OK && cudaDeviceSynchronize() != cudaSuccess) { (void)cudaGetLastError(); s = SP2_ERR_CUDA; }
+  if (s != SP2_OK) { sp2_destroy_batch(hb); return s; }
+  *out = hb;
+  return SP2_OK;
+}
+
+extern "C" sp2_status sp2_run_batch(sp2_batch hb, const double* const* F_dev, double* const* D_dev, void* stream) {
+  if (!hb || !F_dev || !D_dev) return SP2_ERR_INVALID_ARG;
+  for (int i = 0; i < hb->count; ++i) {
+    if (!F_dev[i] || !D_dev[i]) return SP2_ERR_INVALID_ARG;
+    if (overlaps(F_dev[i], D_dev[i], (size_t)hb->N[i] * hb->N[i] * sizeof(double))) return SP2_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  sp2_status st = SP2_OK;
+  if (hb->mixed) {
+    st = hb->mixed->enqueue(F_dev, D_dev, s);
+  } else {
+    for (int i = 0; i < hb->count && st == SP2_OK; ++i) st = enqueue_run(hb->singles[i], F_dev[i], D_dev[i], s);
+  }
+  if (st == SP2_OK) {
+    hb->last_stream = s;
+    hb->ran = true;
+  }
+  return st;
+}
+
+extern "C" sp2_status sp2_get_info_batch(sp2_batch hb, int32_t i, sp2_info* out) {
+  if (!hb || !out || i < 0 || i >= hb->count) return SP2_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  if (hb->mixed) {
+    if (hb->ran) SP2_TRY(cudaStreamSynchronize(hb->last_stream));
+    hb->mixed->info(i, hb->ran, out);
+    return SP2_OK;
+  }
+  return sp2_get_info(hb->singles[i], out);
+}

@@ -1,65 +1,45 @@
 // Internal launchers shared by the C-ABI layer (not part of the public ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace sp2 {
 
 struct DevState;
+namespace tc {
+struct Instance;
+struct Job;
+constexpr int kMaxBatchPtrs = 256;
+}  // namespace tc
 
+// F and D of every instance of a run, passed to kernels by value.
+struct BatchPtrs {
+  const double* F[tc::kMaxBatchPtrs];
+  double* D[tc::kMaxBatchPtrs];
+};
+
+// ---- FP64 path ----------------------------------------------------------------------------
 // a1 + run set-up: Gershgorin partial bounds over `nparts` blocks, then one block
 // that combines them, handles the trivial occupations and computes Tr[X_0].
 cudaError_t launch_bounds_and_init(DevState* st, const double* F, int64_t ldf, int N,
                                    double* part_lo, double* part_hi, int* part_bad, int nparts,
                                    cudaStream_t s);
-
 // a2: X_0 = (lmax I - F) / (lmax - lmin) into an ld x ld FP64 buffer.
 cudaError_t launch_scale_f64(const DevState* st, const double* F, int64_t ldf, int N, double* X0,
                              int ld, cudaStream_t s);
-
 // a3-a5, a7 for the FP64 path: the body of the device-controlled loop (square +
 // finalize), added to `body` as kernel nodes.
 cudaError_t add_f64_loop_body(cudaGraph_t body, DevState* st, double* buf0, double* buf1, double* part,
                               int T, cudaGraphConditionalHandle cond);
-
-// D = X_n (or 0 / I / NaN for the special outcomes).
-cudaError_t launch_copy_out(const DevState* st, const double* buf0, const double* buf1, int ld, int N,
-                            double* D, int64_t ldd, cudaStream_t s);
-
-}  // namespace sp2
-
-// ---- mixed-precision (tensor-core) path -------------------------------------------------
-#include <cuda.h>
-
-namespace sp2 {
-namespace tc { struct Job; }
-
-// Per-iteration reduction + stop test over `nparts` (v^2, trace) partial pairs.
+// Per-iteration reduction + stop test over `nparts` partial records of `stride` doubles.
 cudaError_t add_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, DevState* st,
                               double* part, int nparts, int stride, cudaGraphConditionalHandle cond,
                               cudaGraphNode_t* node);
-
-// TMA tensor maps over a piece arena of `nslots` ld x ld matrices (boxes 128 and 256 rows).
-cudaError_t tc_make_maps(void* arena, int ld, int nslots, CUtensorMap* mapA, CUtensorMap* mapB);
-int tc_grid(int ld, int upper);
-int tc_tiles(int ld, int upper);
-cudaError_t tc_launch(const CUtensorMap& A, const CUtensorMap& B, const tc::Job& job, cudaStream_t s);
-cudaError_t tc_add_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const CUtensorMap& A,
-                        const CUtensorMap& B, const tc::Job& job, cudaGraphNode_t* node);
-
-cudaError_t launch_scale_split(const DevState* st, const double* F, int64_t ldf, int N, void* arena,
-                               int64_t slot_elems, int ld, int x_slot, int f_slot, cudaStream_t s);
-cudaError_t add_deriv_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, DevState* st,
-                                    cudaGraphConditionalHandle cond, cudaGraphNode_t* node);
-cudaError_t launch_assemble(const DevState* st, const void* arena, int64_t slot_elems, int ld, int hist0, int dx0,
-                            int use_dx, int r0, int from_r0, int N, double* D, int64_t ldd, cudaStream_t s);
-cudaError_t add_corrected_to_pieces_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const DevState* st,
-                                         void* arena, int64_t slot_elems, int ld, int hist0, int dx0, int use_dx,
-                                         int r0, int N, cudaGraphNode_t* node);
-}  // namespace sp2
-
-namespace sp2 {
+// D = X_n (or 0 / I / NaN for the special outcomes).
+cudaError_t launch_copy_out(const DevState* st, const double* buf0, const double* buf1, int ld, int N,
+                            double* D, int64_t ldd, cudaStream_t s);
 // One FP64 square + stop test launched directly on a stream (no graph); a no-op once
 // st->done is set.
 cudaError_t launch_f64_step_plain(DevState* st, double* buf0, double* buf1, double* part, int T,
@@ -69,4 +49,26 @@ cudaError_t launch_refine_f64(const DevState* st, const double* Xin, double* Xou
                               cudaStream_t s);
 cudaError_t launch_copy_f64(const DevState* st, const double* X, int ld, int N, double* D, int64_t ldd,
                             cudaStream_t s);
+
+// ---- tensor-core path ------------------------------------------------------------------------
+// TMA tensor maps over a piece arena of `nslots` ld x ld matrices (boxes of 128 rows).
+cudaError_t tc_make_maps(void* arena, int ld, int nslots, CUtensorMap* mapA, CUtensorMap* mapB);
+int tc_tiles(int ld, int upper);
+int tc_grid_for(int total_tiles);
+cudaError_t tc_launch(const tc::Job& job, cudaStream_t s);
+cudaError_t tc_add_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const tc::Job& job,
+                        cudaGraphNode_t* node);
+
+// Batched elementwise kernels and loop tails of the mixed path (all instances at once).
+cudaError_t batch_launch_prologue(const tc::Instance* inst, int count, int pb, int sb, const BatchPtrs& ptrs,
+                                  double* part_lo, double* part_hi, int* part_bad, cudaStream_t s);
+cudaError_t batch_add_forward_tail(cudaGraph_t g, const cudaGraphNode_t* dep, const tc::Instance* inst, int count,
+                                   cudaGraphConditionalHandle cond);
+cudaError_t batch_add_deriv_tail(cudaGraph_t g, const cudaGraphNode_t* dep, const tc::Instance* inst, int count,
+                                 cudaGraphConditionalHandle cond);
+cudaError_t batch_add_corrected_to_pieces(cudaGraph_t g, const cudaGraphNode_t* dep, const tc::Instance* inst,
+                                          int count, int sb, int use_dx, cudaGraphNode_t* node);
+cudaError_t batch_launch_assemble(const tc::Instance* inst, int count, int sb, int use_dx, int from_r0,
+                                  const BatchPtrs& ptrs, double* f64_buf, cudaStream_t s);
+
 }  // namespace sp2

@@ -1,9 +1,15 @@
-// Mixed-precision path: elementwise kernels around the tensor-core GEMM.
+// Mixed-precision path: the batched kernels around the tensor-core GEMM.  Every
+// kernel here works on all instances of a batch at once (a single problem is a batch
+// of one); per-run buffers (F and D of every instance) arrive by value in a Ptrs
+// record, so one launch covers the whole batch with no per-instance host work.
 //
+//  * bounds / init: Gershgorin bounds per instance, special cases, Tr[X_0].
 //  * scale_split: X_0 = (lmax I - F)/(lmax - lmin) in FP64, rounded to FP32 and stored
 //    as three bf16 pieces (history slot 0); F itself as pieces for the correction.
-//  * deriv_finalize: advances the derivative loop and clears its condition.
-//  * assemble: D = X_n + dX_n in FP64 (the first-order correction), or X_n alone.
+//  * finalize / check: per-instance reduction + stop test after each round of squares;
+//    the loop's condition is cleared once every instance has stopped.
+//  * deriv_advance: advances every instance's derivative loop.
+//  * corrected_to_pieces, assemble: D = X_n + dX_n (then the refinement pair) in FP64.
 //
 // Correction (a reading for the mixed path; the paper has no precision scheme):
 // the low-precision expansion returns X_n close to the projector P of a matrix near
@@ -19,6 +25,8 @@
 
 namespace sp2 {
 
+using tc::Instance;
+
 __device__ __forceinline__ void split3_(float x, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
   p0 = __float2bfloat16_rn(x);
   const float r1 = x - __bfloat162float(p0);
@@ -31,138 +39,308 @@ __device__ __forceinline__ float join3_(const __nv_bfloat16* s, int64_t plane, i
   return (__bfloat162float(s[off]) + __bfloat162float(s[plane + off])) + __bfloat162float(s[2 * plane + off]);
 }
 
-__global__ void scale_split_kernel(const DevState* st, const double* __restrict__ F, int64_t ldf,
-                                   __nv_bfloat16* __restrict__ arena, int64_t slot_elems, int ld, int x_slot,
-                                   int f_slot) {
-  if (st->done) return;
+__device__ __forceinline__ bool ok_run(const DevState* st) {
+  return st->status == SP2_OK && st->out_mode == OUT_COPY;
+}
+
+// ---- bounds and initialisation ------------------------------------------------------------
+constexpr int kGT = 256;
+
+// Blocks [i * pb, (i+1) * pb) handle instance i; warp per row.
+__global__ void __launch_bounds__(kGT)
+batch_gersh_kernel(const Instance* inst, int count, int pb, BatchPtrs ptrs, double* part_lo, double* part_hi,
+                   int* part_bad) {
+  __shared__ double s_lo[kGT / 32], s_hi[kGT / 32];
+  __shared__ int s_bad[kGT / 32];
+  const int i = blockIdx.x / pb, b = blockIdx.x % pb;
+  if (i >= count) return;
+  const DevState* st = inst[i].st;
   const int N = st->N;
-  const double lmax = st->lmax, w = st->lmax - st->lmin;
-  const int64_t plane = (int64_t)ld * ld;
-  __nv_bfloat16* X = arena + (int64_t)x_slot * slot_elems;
-  __nv_bfloat16* Fp = arena + (int64_t)f_slot * slot_elems;
-  const int64_t total = (int64_t)N * N;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / N), j = (int)(e % N);
-    const double f = F[(int64_t)i * ldf + j];
-    const float x = (float)(((i == j ? lmax : 0.0) - f) / w);
-    const int64_t off = (int64_t)i * ld + j;
-    __nv_bfloat16 a, b, c;
-    split3_(x, a, b, c);
-    X[off] = a; X[plane + off] = b; X[2 * plane + off] = c;
-    split3_((float)f, a, b, c);
-    Fp[off] = a; Fp[plane + off] = b; Fp[2 * plane + off] = c;
+  const double* F = ptrs.F[i];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double lo = INFINITY, hi = -INFINITY;
+  int bad = 0;
+  for (int r = b * (kGT / 32) + warp; r < N; r += pb * (kGT / 32)) {
+    const double* row = F + (int64_t)r * N;
+    double s = 0.0;
+    for (int j = lane; j < N; j += 32) {
+      const double a = row[j];
+      if (j != r) s += fabs(a);
+      if (!isfinite(a)) bad = 1;
+    }
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double d = row[r];
+    lo = fmin(lo, d - s);
+    hi = fmax(hi, d + s);
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) { s_lo[warp] = lo; s_hi[warp] = hi; s_bad[warp] = bad; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kGT / 32; ++w) {
+      s_lo[0] = fmin(s_lo[0], s_lo[w]);
+      s_hi[0] = fmax(s_hi[0], s_hi[w]);
+      s_bad[0] |= s_bad[w];
+    }
+    part_lo[blockIdx.x] = s_lo[0];
+    part_hi[blockIdx.x] = s_hi[0];
+    part_bad[blockIdx.x] = s_bad[0];
   }
 }
 
-__global__ void deriv_finalize_kernel(DevState* st, cudaGraphConditionalHandle cond) {
-  const bool ok_run = st->status == SP2_OK && st->out_mode == OUT_COPY;
-  if (!ok_run || st->dk >= st->n_out) {
-    cudaGraphSetConditional(cond, 0);
-    return;
+constexpr int kIT = 1024;
+
+__global__ void __launch_bounds__(kIT)
+batch_init_kernel(const Instance* inst, int count, int pb, BatchPtrs ptrs, const double* part_lo,
+                  const double* part_hi, const int* part_bad) {
+  __shared__ double sm[32];
+  __shared__ double s_lmin, s_lmax;
+  __shared__ int s_bad;
+  const int i = blockIdx.x;
+  if (i >= count) return;
+  DevState* st = inst[i].st;
+  const double* F = ptrs.F[i];
+  if (threadIdx.x == 0) {
+    double lo = INFINITY, hi = -INFINITY;
+    int bad = 0;
+    for (int b = 0; b < pb; ++b) {
+      lo = fmin(lo, part_lo[i * pb + b]);
+      hi = fmax(hi, part_hi[i * pb + b]);
+      bad |= part_bad[i * pb + b];
+    }
+    if (!isfinite(lo) || !isfinite(hi)) bad = 1;
+    s_lmin = lo; s_lmax = hi; s_bad = bad;
   }
-  st->dk += 1;
-  if (st->dk >= st->n_out) cudaGraphSetConditional(cond, 0);
+  __syncthreads();
+  const double lmin = s_lmin, lmax = s_lmax, w = lmax - lmin;
+  const int N = st->N, nocc = st->nocc;
+  double t = 0.0;   // Tr[X_0] over the stored (FP32-rounded) diagonal
+  for (int r = threadIdx.x; r < N; r += kIT) t += (double)(float)((lmax - F[(int64_t)r * N + r]) / w);
+  t = block_sum<kIT>(t, sm);
+  if (threadIdx.x == 0) {
+    st->lmin = lmin; st->lmax = lmax;
+    st->dk = 0;
+    st->k = 0; st->done = 0; st->n_out = 0; st->reason = SP2_STOP_EXACT;
+    st->status = SP2_OK; st->out_buf = 0; st->out_mode = OUT_COPY; st->hist_len = 0;
+    st->tr[0] = 0.0; st->p[0] = 0;
+    if (s_bad) {
+      st->status = SP2_ERR_NONFINITE; st->done = 1; st->out_mode = OUT_NAN;
+    } else if (nocc == 0) {
+      st->done = 1; st->out_mode = OUT_ZERO;
+    } else if (nocc == N) {
+      st->done = 1; st->out_mode = OUT_IDENTITY;
+    } else if (!(lmax > lmin)) {
+      st->status = SP2_ERR_NO_GAP; st->done = 1; st->out_mode = OUT_NAN;
+    } else {
+      st->tr[0] = t;
+    }
+  }
 }
+
+// Blocks [i * sb, (i+1) * sb) handle instance i, grid-stride over its N x N elements.
+__global__ void batch_scale_split_kernel(const Instance* inst, int count, int sb, BatchPtrs ptrs) {
+  const int i = blockIdx.x / sb, b = blockIdx.x % sb;
+  if (i >= count) return;
+  const Instance& In = inst[i];
+  const DevState* st = In.st;
+  if (st->done) return;
+  const int N = st->N, ld = In.ld;
+  const double lmax = st->lmax, w = st->lmax - st->lmin;
+  const int64_t plane = (int64_t)ld * ld;
+  __nv_bfloat16* X = In.arena + (int64_t)In.hist0 * In.slot_elems;
+  __nv_bfloat16* Fp = In.arena + (int64_t)In.f_slot * In.slot_elems;
+  const double* F = ptrs.F[i];
+  const int64_t total = (int64_t)N * N;
+  for (int64_t e = b * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)sb * blockDim.x) {
+    const int r = (int)(e / N), c = (int)(e % N);
+    const double f = F[e];
+    const float x = (float)(((r == c ? lmax : 0.0) - f) / w);
+    const int64_t off = (int64_t)r * ld + c;
+    __nv_bfloat16 a, bb, cc;
+    split3_(x, a, bb, cc);
+    X[off] = a; X[plane + off] = bb; X[2 * plane + off] = cc;
+    split3_((float)f, a, bb, cc);
+    Fp[off] = a; Fp[plane + off] = bb; Fp[2 * plane + off] = cc;
+  }
+}
+
+// ---- per-round reduction, stop test and loop conditions ----------------------------------
+constexpr int kFT = 1024;
+
+// One block per instance: (v^2, ||X_{k-1}||_F^2, Tr[X_{k-1}]) partials, 4 per (tile, warp).
+// Tr[X_k] comes from Tr[X^2] = ||X||_F^2 (symmetric X): ||X_{k-1}||_F^2 after X^2,
+// 2 Tr[X_{k-1}] - ||X_{k-1}||_F^2 after 2X - X^2, so the polynomial choice does not
+// inherit the bias of the tensor cores' accumulation.
+__global__ void __launch_bounds__(kFT) batch_finalize_kernel(const Instance* inst, int count) {
+  __shared__ double sm[32];
+  const int i = blockIdx.x;
+  if (i >= count) return;
+  const Instance& In = inst[i];
+  DevState* st = In.st;
+  if (st->done) return;
+  const int nparts = 4 * tc::tiles_of(In.ld, 1);
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int t = threadIdx.x; t < nparts; t += kFT) {
+    a += In.part[4 * (int64_t)t];
+    b += In.part[4 * (int64_t)t + 1];
+    c += In.part[4 * (int64_t)t + 2];
+  }
+  a = block_sum<kFT>(a, sm);
+  b = block_sum<kFT>(b, sm);
+  c = block_sum<kFT>(c, sm);
+  if (threadIdx.x != 0) return;
+  const int k = st->k + 1;
+  const int pk = st->tr[k - 1] > (double)st->nocc ? 1 : 0;
+  const double tr_new = pk ? b : 2.0 * c - b;
+  record_and_test(st, pk, sqrt(a), tr_new, c);
+}
+
+// Clears `cond` once no instance needs another round: which = 0 for the expansion
+// (every instance done), 1 for the derivative loop (every instance at dk == n_out).
+__global__ void batch_check_kernel(const Instance* inst, int count, int which, cudaGraphConditionalHandle cond) {
+  __shared__ int busy;
+  if (threadIdx.x == 0) busy = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const DevState* st = inst[i].st;
+    const bool more = which == 0 ? !st->done : (ok_run(st) && st->dk < st->n_out);
+    if (more) atomicOr(&busy, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !busy) cudaGraphSetConditional(cond, 0);
+}
+
+// After a derivative round: every instance still short of n_out has done one more step.
+__global__ void batch_deriv_advance_kernel(const Instance* inst, int count, cudaGraphConditionalHandle cond) {
+  __shared__ int busy;
+  if (threadIdx.x == 0) busy = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    DevState* st = inst[i].st;
+    if (ok_run(st) && st->dk < st->n_out) {
+      st->dk += 1;
+      if (st->dk < st->n_out) atomicOr(&busy, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !busy) cudaGraphSetConditional(cond, 0);
+}
+
+// ---- corrected result and output ------------------------------------------------------------
 
 // The corrected D = X_n + dX_n rounded to FP32 and split into pieces in slot r0, the
 // input of the tensor-core refinement pair.
-__global__ void corrected_to_pieces_kernel(const DevState* st, __nv_bfloat16* __restrict__ arena, int64_t slot_elems,
-                                           int ld, int hist0, int dx0, int use_dx, int r0) {
-  if (st->status != SP2_OK || st->out_mode != OUT_COPY) return;
-  const int N = st->N;
+__global__ void batch_corrected_to_pieces_kernel(const Instance* inst, int count, int sb, int use_dx) {
+  const int i = blockIdx.x / sb, b = blockIdx.x % sb;
+  if (i >= count) return;
+  const Instance& In = inst[i];
+  const DevState* st = In.st;
+  if (!ok_run(st)) return;
+  const int N = st->N, ld = In.ld;
   const int64_t plane = (int64_t)ld * ld;
   const int n = st->n_out;
-  const __nv_bfloat16* X = arena + (int64_t)(hist0 + n) * slot_elems;
-  const __nv_bfloat16* dX = arena + (int64_t)(dx0 + (n & 1)) * slot_elems;
-  __nv_bfloat16* R = arena + (int64_t)r0 * slot_elems;
+  const __nv_bfloat16* X = In.arena + (int64_t)(In.hist0 + n) * In.slot_elems;
+  const __nv_bfloat16* dX = In.arena + (int64_t)(In.dx0 + (n & 1)) * In.slot_elems;
+  __nv_bfloat16* R = In.arena + (int64_t)In.r0_slot * In.slot_elems;
   const bool corr = use_dx && n > 0 && st->dk == n;
   const int64_t total = (int64_t)N * N;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / N), j = (int)(e % N);
-    const int64_t off = (int64_t)i * ld + j;
+  for (int64_t e = b * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)sb * blockDim.x) {
+    const int r = (int)(e / N), c = (int)(e % N);
+    const int64_t off = (int64_t)r * ld + c;
     double val = (double)join3_(X, plane, off);
     if (corr) val += (double)join3_(dX, plane, off);
-    __nv_bfloat16 a, b, c;
-    split3_((float)val, a, b, c);
-    R[off] = a; R[plane + off] = b; R[2 * plane + off] = c;
+    __nv_bfloat16 a, bb, cc;
+    split3_((float)val, a, bb, cc);
+    R[off] = a; R[plane + off] = bb; R[2 * plane + off] = cc;
   }
 }
 
 // D in FP64: from slot r0 (after the tensor-core refinement) when from_r0, else
-// X_n (+ dX_n with the correction).
-__global__ void assemble_kernel(const DevState* st, const __nv_bfloat16* __restrict__ arena, int64_t slot_elems,
-                                int ld, int hist0, int dx0, int use_dx, int r0, int from_r0,
-                                double* __restrict__ D, int64_t ldd) {
-  const int N = st->N;
+// X_n (+ dX_n with the correction); 0 / I / NaN for the special outcomes.
+__global__ void batch_assemble_kernel(const Instance* inst, int count, int sb, int use_dx, int from_r0,
+                                      BatchPtrs ptrs, int to_f64_buf, double* f64_buf) {
+  const int i = blockIdx.x / sb, b = blockIdx.x % sb;
+  if (i >= count) return;
+  const Instance& In = inst[i];
+  const DevState* st = In.st;
+  const int N = st->N, ld = In.ld;
   const int mode = st->out_mode;
   const int64_t plane = (int64_t)ld * ld;
   const int n = st->n_out;
-  const __nv_bfloat16* X = arena + (int64_t)(from_r0 ? r0 : hist0 + n) * slot_elems;
-  const __nv_bfloat16* dX = arena + (int64_t)(dx0 + (n & 1)) * slot_elems;
+  const __nv_bfloat16* X = In.arena + (int64_t)(from_r0 ? In.r0_slot : In.hist0 + n) * In.slot_elems;
+  const __nv_bfloat16* dX = In.arena + (int64_t)(In.dx0 + (n & 1)) * In.slot_elems;
   const bool corr = !from_r0 && use_dx && n > 0 && st->dk == n;
+  double* D = to_f64_buf ? f64_buf : ptrs.D[i];
+  const int64_t ldd = to_f64_buf ? ld : N;
   const int64_t total = (int64_t)N * N;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / N), j = (int)(e % N);
+  for (int64_t e = b * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)sb * blockDim.x) {
+    const int r = (int)(e / N), c = (int)(e % N);
     double val;
     if (mode == OUT_COPY) {
-      const int64_t off = (int64_t)i * ld + j;
+      const int64_t off = (int64_t)r * ld + c;
       val = (double)join3_(X, plane, off);
       if (corr) val += (double)join3_(dX, plane, off);
     } else if (mode == OUT_ZERO) {
       val = 0.0;
     } else if (mode == OUT_IDENTITY) {
-      val = (i == j) ? 1.0 : 0.0;
+      val = (r == c) ? 1.0 : 0.0;
     } else {
       val = __longlong_as_double(0x7ff8000000000000ll);
     }
-    D[(int64_t)i * ldd + j] = val;
+    D[(int64_t)r * ldd + c] = val;
   }
 }
 
-static int ew_blocks(int64_t total) {
-  int64_t b = (total + 255) / 256;
-  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
-}
+// ---- host-side launchers ------------------------------------------------------------------
 
-cudaError_t launch_scale_split(const DevState* st, const double* F, int64_t ldf, int N, void* arena,
-                               int64_t slot_elems, int ld, int x_slot, int f_slot, cudaStream_t s) {
-  scale_split_kernel<<<ew_blocks((int64_t)N * N), 256, 0, s>>>(st, F, ldf, (__nv_bfloat16*)arena, slot_elems, ld,
-                                                                x_slot, f_slot);
-  return cudaGetLastError();
-}
-
-cudaError_t add_deriv_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, DevState* st,
-                                    cudaGraphConditionalHandle cond, cudaGraphNode_t* node) {
-  void* args[] = {&st, &cond};
+static cudaError_t add_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, void* func, dim3 grid,
+                            dim3 block, void** args, cudaGraphNode_t* node) {
   cudaKernelNodeParams kp = {};
-  kp.func = (void*)deriv_finalize_kernel;
-  kp.gridDim = dim3(1);
-  kp.blockDim = dim3(1);
+  kp.func = func;
+  kp.gridDim = grid;
+  kp.blockDim = block;
   kp.kernelParams = args;
   return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
 }
 
-cudaError_t launch_assemble(const DevState* st, const void* arena, int64_t slot_elems, int ld, int hist0, int dx0,
-                            int use_dx, int r0, int from_r0, int N, double* D, int64_t ldd, cudaStream_t s) {
-  assemble_kernel<<<ew_blocks((int64_t)N * N), 256, 0, s>>>(st, (const __nv_bfloat16*)arena, slot_elems, ld, hist0,
-                                                             dx0, use_dx, r0, from_r0, D, ldd);
+cudaError_t batch_launch_prologue(const Instance* inst, int count, int pb, int sb, const BatchPtrs& ptrs,
+                                  double* part_lo, double* part_hi, int* part_bad, cudaStream_t s) {
+  batch_gersh_kernel<<<count * pb, kGT, 0, s>>>(inst, count, pb, ptrs, part_lo, part_hi, part_bad);
+  batch_init_kernel<<<count, kIT, 0, s>>>(inst, count, pb, ptrs, part_lo, part_hi, part_bad);
+  batch_scale_split_kernel<<<count * sb, 256, 0, s>>>(inst, count, sb, ptrs);
   return cudaGetLastError();
 }
 
-cudaError_t add_corrected_to_pieces_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const DevState* st,
-                                         void* arena, int64_t slot_elems, int ld, int hist0, int dx0, int use_dx,
-                                         int r0, int N, cudaGraphNode_t* node) {
-  __nv_bfloat16* a = (__nv_bfloat16*)arena;
-  void* args[] = {&st, &a, &slot_elems, &ld, &hist0, &dx0, &use_dx, &r0};
-  cudaKernelNodeParams kp = {};
-  kp.func = (void*)corrected_to_pieces_kernel;
-  kp.gridDim = dim3(ew_blocks((int64_t)N * N));
-  kp.blockDim = dim3(256);
-  kp.kernelParams = args;
-  return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
+cudaError_t batch_add_forward_tail(cudaGraph_t g, const cudaGraphNode_t* dep, const Instance* inst, int count,
+                                   cudaGraphConditionalHandle cond) {
+  cudaGraphNode_t n_fin, n_chk;
+  void* a1[] = {&inst, &count};
+  cudaError_t e = add_node(g, dep, 1, (void*)batch_finalize_kernel, dim3(count), dim3(kFT), a1, &n_fin);
+  if (e != cudaSuccess) return e;
+  int which = 0;
+  void* a2[] = {&inst, &count, &which, &cond};
+  return add_node(g, &n_fin, 1, (void*)batch_check_kernel, dim3(1), dim3(256), a2, &n_chk);
+}
+
+cudaError_t batch_add_deriv_tail(cudaGraph_t g, const cudaGraphNode_t* dep, const Instance* inst, int count,
+                                 cudaGraphConditionalHandle cond) {
+  cudaGraphNode_t n;
+  void* a[] = {&inst, &count, &cond};
+  return add_node(g, dep, 1, (void*)batch_deriv_advance_kernel, dim3(1), dim3(256), a, &n);
+}
+
+cudaError_t batch_add_corrected_to_pieces(cudaGraph_t g, const cudaGraphNode_t* dep, const Instance* inst, int count,
+                                          int sb, int use_dx, cudaGraphNode_t* node) {
+  void* a[] = {&inst, &count, &sb, &use_dx};
+  return add_node(g, dep, 1, (void*)batch_corrected_to_pieces_kernel, dim3(count * sb), dim3(256), a, node);
+}
+
+cudaError_t batch_launch_assemble(const Instance* inst, int count, int sb, int use_dx, int from_r0,
+                                  const BatchPtrs& ptrs, double* f64_buf, cudaStream_t s) {
+  batch_assemble_kernel<<<count * sb, 256, 0, s>>>(inst, count, sb, use_dx, from_r0, ptrs, f64_buf ? 1 : 0,
+                                                   f64_buf);
+  return cudaGetLastError();
 }
 
 }  // namespace sp2

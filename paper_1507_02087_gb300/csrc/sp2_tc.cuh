@@ -1,4 +1,5 @@
-// Tensor-core (tcgen05) path: definitions shared by the GEMM kernel and the host side.
+// Tensor-core (tcgen05) path: definitions shared by the GEMM kernel, the batched
+// elementwise kernels and the host side.
 //
 // Matrices on this path are FP32 values stored exactly as three bf16 "pieces"
 // x = (p0 + p1) + p2 (p0 = bf16(x), p1 = bf16(x - p0), p2 = x - p0 - p1; each
@@ -6,10 +7,11 @@
 // the sum of the six piece products p_a q_b with a + b <= 2, each a bf16 MMA with
 // FP32 accumulation, which carries the product to FP32 accuracy.
 //
-// All piece matrices of a handle live in one "arena": slot s holds the three planes
-// of one ld x ld matrix, plane-major ([slot][piece][row][col], bf16).  One 4-D TMA
-// tensor map (col, row, piece, slot) covers the arena, so a kernel selects operands
-// by slot index.
+// Every problem ("instance") owns a piece arena: slot s holds the three planes of one
+// ld x ld matrix, plane-major ([slot][piece][row][col], bf16).  A 4-D TMA tensor map
+// (col, row, piece, slot) per instance covers its arena, so a kernel selects operands
+// by instance and slot.  A launch works on the tiles of all live instances of a batch
+// (a single problem is a batch of one).
 #pragma once
 
 #include <cuda.h>
@@ -40,20 +42,21 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;   // + alignment slack
 constexpr int THREADS = 192;     // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
 constexpr int TMEM_COLS = NBUF * BN;   // four 128 x 128 fp32 chunk accumulators
 constexpr int LD_ALIGN = 128;    // ld is a multiple of the tile size
+constexpr int MAX_BATCH = 256;   // instances per batch
 
 enum Mode : int32_t {
   MODE_STORE_F32 = 0,   // C -> fp32 buffer (tests)
   MODE_SP2_STEP = 1,    // X_k = C or 2 X_{k-1} - C, with ||X_{k-1} - C||_F^2, ||X_{k-1}||_F^2 and
                         // Tr X_{k-1} partials
-  MODE_DERIV_STEP = 2,  // dX_j = C or 2 dX_{j-1} - C
+  MODE_DERIV_STEP = 2,  // dX_j = C or 2 dX_{j-1} - C (also one plain SP2 step with C = in^2)
   MODE_STORE_PIECES = 3,// C -> pieces (full tiles)
   MODE_DF_COMBINE = 4   // dX_0 = s (M + M^T - 2 C) with s = -1/(lmax - lmin)
 };
 
-// Where the operands come from.  With `slots_from_state`, slot indices are offset by
-// the device state so one captured launch serves every iteration of a loop.
+// Where the operands come from.  Slot indices are computed from the instance's device
+// state, so one captured launch serves every iteration of a loop.
 enum SlotRule : int32_t {
-  SLOTS_FIXED = 0,
+  SLOTS_FIXED = 0,      // a_slot / b_slot / out as given (tests)
   SLOTS_FORWARD = 1,    // A = B = in = hist0 + k, out = hist0 + k + 1      (k = st->k)
   SLOTS_DERIV = 2,      // j = st->dk + 1: (X_{j-1}, dX_{j-1}) + (dX_{j-1}, X_{j-1}) -> dX_j
   SLOTS_CORR_M = 3,     // M = P F with P = X_n:  A = hist0 + n, B = f_slot, out = m_slot
@@ -63,23 +66,39 @@ enum SlotRule : int32_t {
                         // maps back with p_n (an alternating pair, §4)
 };
 
-struct Job {
+// One problem of a batch (device memory; the tensor maps are read by TMA from here).
+struct alignas(64) Instance {
+  CUtensorMap mapA;     // box 32 x 128 (A operand)
+  CUtensorMap mapB;     // box 32 x 128 (B operand)
+  __nv_bfloat16* arena;
+  int64_t slot_elems;   // 3 * ld * ld
+  DevState* st;
+  double* part;         // forward-square partials: 4 doubles per (tile, epilogue warp)
   int32_t ld;
+  int32_t tile_off_upper;   // first global tile index of this instance (upper schedule)
+  int32_t tile_off_full;    // first global tile index (full schedule)
+  int32_t hist0, dx0, m_slot, f_slot, r0_slot;
+};
+
+struct Job {
   int32_t mode;
   int32_t upper;        // 1: symmetric result from upper tiles, mirror written
   int32_t nterms;       // 1 or 2 (sum of two products, same accumulator)
   int32_t rule;
-  int32_t a_slot[2], b_slot[2];
-  int32_t in_slot, out_slot;
-  int32_t hist0, dx0, m_slot, f_slot;
-  int32_t r0_slot;
-  __nv_bfloat16* arena;
-  int64_t slot_elems;   // 3 * ld * ld
+  int32_t count;        // instances in the batch
+  int32_t total_tiles;  // over all instances, for this schedule
+  const Instance* inst;
+  int32_t a_slot[2], b_slot[2];   // SLOTS_FIXED operands; SLOTS_REFINE step in a_slot[0]
+  int32_t out_slot;
+  int32_t _pad;
   float* out32;         // MODE_STORE_F32
-  DevState* st;
-  double* part;         // per (tile, epilogue warp) partials for MODE_SP2_STEP, 4 doubles each
   int32_t* err;         // set to SP2_ERR_TIMEOUT if a wait gave up
 };
+
+__host__ __device__ __forceinline__ int tiles_of(int ld, int upper) {
+  const int R = ld / BM;
+  return upper ? R * (R + 1) / 2 : R * R;
+}
 
 }  // namespace tc
 }  // namespace sp2

@@ -1,9 +1,12 @@
-// Persistent tcgen05 GEMM over 3-piece bf16 operands with the SP2 epilogues.
+// Persistent tcgen05 GEMM over 3-piece bf16 operands with the SP2 epilogues, for a
+// batch of problems of uneven size.
 //
 // C[I-tile, J-tile] = sum_k A[rows I, k] B[rows J, k] (both operands K-major row
 // panels; X symmetric makes X X^T = X^2), as the six piece products with a+b <= 2.
-// One CTA per SM walks the tile list.  Warp 0 feeds a 4-stage TMA ring (64-byte
-// swizzle, 32-wide k-blocks); warp 1 issues the MMAs (128 x 128 x 16) and closes a
+// One CTA per SM walks the global tile list (the tiles of every instance, largest
+// instances first); tiles of instances that have already stopped are skipped.
+// Warp 0 feeds a 4-stage TMA ring (64-byte swizzle, 32-wide k-blocks) from the
+// instance's tensor maps; warp 1 issues the MMAs (128 x 128 x 16) and closes a
 // tensor-memory chunk buffer every CHUNK_KB k-blocks; warps 2-5 add each closed chunk
 // into FP32 registers (round to nearest) and, after the last chunk of a tile, run the
 // epilogue.  Four chunk buffers let the MMAs run ahead of the draining.
@@ -36,49 +39,49 @@ struct Resolved {
   bool active;
 };
 
-__device__ __forceinline__ Resolved resolve(const Job& j) {
+__device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
   Resolved r;
   r.a[0] = j.a_slot[0]; r.a[1] = j.a_slot[1];
   r.b[0] = j.b_slot[0]; r.b[1] = j.b_slot[1];
-  r.in = j.in_slot; r.out = j.out_slot; r.pk = 1; r.active = true;
-  const DevState* st = j.st;
+  r.in = j.a_slot[0]; r.out = j.out_slot; r.pk = 1; r.active = true;
   if (j.rule == SLOTS_FIXED) return r;
+  const DevState* st = I.st;
   const bool ok_run = st->status == SP2_OK && st->out_mode == OUT_COPY;
   switch (j.rule) {
     case SLOTS_FORWARD: {
       const int k = st->k;
-      r.a[0] = r.b[0] = r.in = j.hist0 + k;
-      r.out = j.hist0 + k + 1;
+      r.a[0] = r.b[0] = r.in = I.hist0 + k;
+      r.out = I.hist0 + k + 1;
       r.pk = st->tr[k] > (double)st->nocc ? 1 : 0;   // Alg. 3 trace test
       r.active = !st->done;
       break;
     }
     case SLOTS_DERIV: {
       const int jj = st->dk + 1;
-      const int xs = j.hist0 + jj - 1;
-      const int di = j.dx0 + ((jj - 1) & 1);
+      const int xs = I.hist0 + jj - 1;
+      const int di = I.dx0 + ((jj - 1) & 1);
       r.a[0] = xs; r.b[0] = di;
       r.a[1] = di; r.b[1] = xs;
-      r.in = di; r.out = j.dx0 + (jj & 1);
+      r.in = di; r.out = I.dx0 + (jj & 1);
       r.pk = st->p[jj];
       r.active = ok_run && st->dk < st->n_out;
       break;
     }
     case SLOTS_CORR_M: {
-      r.a[0] = j.hist0 + st->n_out; r.b[0] = j.f_slot; r.out = j.m_slot;
+      r.a[0] = I.hist0 + st->n_out; r.b[0] = I.f_slot; r.out = I.m_slot;
       r.active = ok_run && st->n_out > 0;
       break;
     }
     case SLOTS_CORR_DF: {
-      r.a[0] = j.m_slot; r.b[0] = j.hist0 + st->n_out; r.in = j.m_slot; r.out = j.dx0;
+      r.a[0] = I.m_slot; r.b[0] = I.hist0 + st->n_out; r.in = I.m_slot; r.out = I.dx0;
       r.active = ok_run && st->n_out > 0;
       break;
     }
     case SLOTS_REFINE: {
       const int s = j.a_slot[0];
       const int plast = st->p[st->n_out];
-      r.a[0] = r.b[0] = r.in = j.r0_slot + s;
-      r.out = j.r0_slot + (1 - s);
+      r.a[0] = r.b[0] = r.in = I.r0_slot + s;
+      r.out = I.r0_slot + (1 - s);
       r.pk = s == 0 ? 1 - plast : plast;
       r.active = ok_run;
       break;
@@ -88,19 +91,28 @@ __device__ __forceinline__ Resolved resolve(const Job& j) {
   return r;
 }
 
-__host__ __device__ __forceinline__ int tiles_total(int ld, int upper) {
-  const int R = ld / BM;
-  return upper ? R * (R + 1) / 2 : R * R;
-}
-
-// Tiles in row-major order; with `upper`, row I holds J = I .. R-1.
-__device__ __forceinline__ void tile_ij(int t, int ld, int upper, int& I, int& J) {
-  const int R = ld / BM;
-  if (!upper) { I = t / R; J = t % R; return; }
+// Global tile t -> (instance, tile row I, tile column J).  Tiles are in row-major order
+// within an instance; with `upper`, row I holds J = I .. R-1.
+__device__ __forceinline__ int locate(const Job& job, int t, int& I, int& J) {
   int i = 0;
-  while (t >= R - i) { t -= R - i; ++i; }
-  I = i;
-  J = i + t;
+  for (; i + 1 < job.count; ++i) {
+    const Instance& nx = job.inst[i + 1];
+    const int off = job.upper ? nx.tile_off_upper : nx.tile_off_full;
+    if (t < off) break;
+  }
+  const Instance& in = job.inst[i];
+  t -= job.upper ? in.tile_off_upper : in.tile_off_full;
+  const int R = in.ld / BM;
+  if (!job.upper) {
+    I = t / R;
+    J = t % R;
+  } else {
+    int r = 0;
+    while (t >= R - r) { t -= R - r; ++r; }
+    I = r;
+    J = r + t;
+  }
+  return i;
 }
 
 __device__ __forceinline__ void split3(float x, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
@@ -160,9 +172,9 @@ struct Partials {
 };
 
 // Epilogue for row r, columns c0 .. c0+31 of the tile, with the accumulated product s.
-__device__ __forceinline__ void epilogue_chunk(const Job& job, const Resolved& R, int r, int c0,
-                                               const float (&s)[32], Partials& P) {
-  const int ld = job.ld;
+__device__ __forceinline__ void epilogue_chunk(const Job& job, const Instance& In, const Resolved& R, int r,
+                                               int c0, const float (&s)[32], Partials& P) {
+  const int ld = In.ld;
   const int64_t plane = (int64_t)ld * ld;
   const bool upper = job.upper != 0;
   const bool all_keep = !upper || c0 >= r;
@@ -180,17 +192,17 @@ __device__ __forceinline__ void epilogue_chunk(const Job& job, const Resolved& R
     return;
   }
 
-  __nv_bfloat16* out = job.arena + (int64_t)R.out * job.slot_elems;
+  __nv_bfloat16* out = In.arena + (int64_t)R.out * In.slot_elems;
   float xn[32];
   if (job.mode == MODE_STORE_PIECES) {
     #pragma unroll
     for (int j = 0; j < 32; ++j) xn[j] = s[j];
   } else {
-    const __nv_bfloat16* in = job.arena + (int64_t)R.in * job.slot_elems;
+    const __nv_bfloat16* in = In.arena + (int64_t)R.in * In.slot_elems;
     float x[32];
     load_row32(in, plane, row_off, x);
     if (job.mode == MODE_DF_COMBINE) {
-      const double w = job.st->lmax - job.st->lmin;
+      const double w = In.st->lmax - In.st->lmin;
       const float sc = (float)(-1.0 / w);
       #pragma unroll
       for (int j = 0; j < 32; ++j) {
@@ -232,8 +244,7 @@ __device__ __forceinline__ void epilogue_chunk(const Job& job, const Resolved& R
   }
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
-tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const Job job) {
+__global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
@@ -242,9 +253,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ volatile int abort_s;
-
-  const Resolved R = resolve(job);
-  if (!R.active) return;
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -260,16 +268,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = tmem_base_s;
-  const int ld = job.ld;
-  const int ntiles = tiles_total(ld, job.upper);
-  const int nkb = ld / BK;
-  const int nchunks = job.nterms * nkb / CHUNK_KB;
+  const int ntiles = job.total_tiles;
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      prefetch_tmap(&mapA);
-      prefetch_tmap(&mapB);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -278,7 +281,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       for (int s = 0; s < STAGES; ++s) { armed[s] = 0; armed_par[s] = 0; }
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int I, J;
-        tile_ij(t, ld, job.upper, I, J);
+        const int ii = locate(job, t, I, J);
+        const Instance& In = job.inst[ii];
+        const Resolved R = resolve(job, In);
+        if (!R.active) continue;
+        const CUtensorMap* mA = &In.mapA;
+        const CUtensorMap* mB = &In.mapB;
+        const int nkb = In.ld / BK;
         for (int term = 0; term < job.nterms && ok; ++term) {
           for (int kb = 0; kb < nkb; ++kb) {
             if (abort_s || !mbar_wait(&empty_bar[stage], phase ^ 1, globaltimer_ns() + kWaitNs)) {
@@ -290,10 +299,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             mbar_arrive_expect_tx(&full_bar[stage], STAGE_BYTES);
             #pragma unroll
             for (int p = 0; p < NP; ++p)
-              tma_load_4d(sA + p * A_PIECE_BYTES, &mapA, kb * BK, I * BM, p, R.a[term], &full_bar[stage]);
+              tma_load_4d(sA + p * A_PIECE_BYTES, mA, kb * BK, I * BM, p, R.a[term], &full_bar[stage]);
             #pragma unroll
             for (int p = 0; p < NP; ++p)
-              tma_load_4d(sB + p * B_PIECE_BYTES, &mapB, kb * BK, J * BN, p, R.b[term], &full_bar[stage]);
+              tma_load_4d(sB + p * B_PIECE_BYTES, mB, kb * BK, J * BN, p, R.b[term], &full_bar[stage]);
             armed[stage] = 1;
             armed_par[stage] = phase;
             if (++stage == STAGES) { stage = 0; phase ^= 1; }
@@ -316,6 +325,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       uint32_t phase = 0, bphase = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int I, J;
+        const int ii = locate(job, t, I, J);
+        const Instance& In = job.inst[ii];
+        if (!resolve(job, In).active) continue;
+        const int nchunks = job.nterms * (In.ld / BK) / CHUNK_KB;
         for (int ch = 0; ch < nchunks && ok; ++ch) {
           if (abort_s || !mbar_wait(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + kWaitNs)) { ok = false; break; }
           tc_fence_after();
@@ -355,6 +369,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     uint32_t bphase = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int I, J;
+      const int ii = locate(job, t, I, J);
+      const Instance& In = job.inst[ii];
+      const Resolved R = resolve(job, In);
+      if (!R.active) continue;
+      const int nchunks = job.nterms * (In.ld / BK) / CHUNK_KB;
       float acc[BN / 32][32];
       #pragma unroll
       for (int g = 0; g < BN / 32; ++g)
@@ -385,12 +405,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         if (++buf == NBUF) { buf = 0; bphase ^= 1; }
       }
       if (!ok) break;
-      int I, J;
-      tile_ij(t, ld, job.upper, I, J);
       const int r = I * BM + 32 * q + lane;
       Partials P = {0.0, 0.0, 0.0};
       #pragma unroll
-      for (int g = 0; g < BN / 32; ++g) epilogue_chunk(job, R, r, J * BN + g * 32, acc[g], P);
+      for (int g = 0; g < BN / 32; ++g) epilogue_chunk(job, In, R, r, J * BN + g * 32, acc[g], P);
       if (job.mode == MODE_SP2_STEP) {
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -399,7 +417,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
           P.trd += __shfl_xor_sync(0xffffffffu, P.trd, o);
         }
         if (lane == 0) {
-          double* dst = job.part + 4 * (4 * (int64_t)t + q);
+          const int lt = t - In.tile_off_upper;        // tile index within the instance
+          double* dst = In.part + 4 * (4 * (int64_t)lt + q);
           dst[0] = P.v2;
           dst[1] = P.fro2;
           dst[2] = P.trd;
@@ -462,13 +481,12 @@ static int sm_count() {
   return n;
 }
 
-int tc_grid(int ld, int upper) {
-  const int t = tc::tiles_total(ld, upper);
+int tc_grid_for(int total_tiles) {
   const int s = sm_count();
-  return t < s ? t : s;
+  return total_tiles < s ? (total_tiles < 1 ? 1 : total_tiles) : s;
 }
 
-int tc_tiles(int ld, int upper) { return tc::tiles_total(ld, upper); }
+int tc_tiles(int ld, int upper) { return tc::tiles_of(ld, upper); }
 
 static cudaError_t tc_prepare() {
   static bool done = false;
@@ -479,23 +497,22 @@ static cudaError_t tc_prepare() {
   return e;
 }
 
-cudaError_t tc_launch(const CUtensorMap& A, const CUtensorMap& B, const tc::Job& job, cudaStream_t s) {
+cudaError_t tc_launch(const tc::Job& job, cudaStream_t s) {
   cudaError_t e = tc_prepare();
   if (e != cudaSuccess) return e;
-  tc::tc_gemm_kernel<<<tc_grid(job.ld, job.upper), tc::THREADS, tc::SMEM_BYTES, s>>>(A, B, job);
+  tc::tc_gemm_kernel<<<tc_grid_for(job.total_tiles), tc::THREADS, tc::SMEM_BYTES, s>>>(job);
   return cudaGetLastError();
 }
 
-cudaError_t tc_add_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const CUtensorMap& A,
-                        const CUtensorMap& B, const tc::Job& job, cudaGraphNode_t* node) {
+cudaError_t tc_add_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const tc::Job& job,
+                        cudaGraphNode_t* node) {
   cudaError_t e = tc_prepare();
   if (e != cudaSuccess) return e;
-  CUtensorMap a = A, b = B;
   tc::Job j = job;
-  void* args[] = {&a, &b, &j};
+  void* args[] = {&j};
   cudaKernelNodeParams kp = {};
   kp.func = (void*)tc::tc_gemm_kernel;
-  kp.gridDim = dim3(tc_grid(job.ld, job.upper));
+  kp.gridDim = dim3(tc_grid_for(job.total_tiles));
   kp.blockDim = dim3(tc::THREADS);
   kp.sharedMemBytes = tc::SMEM_BYTES;
   kp.kernelParams = args;
@@ -510,34 +527,42 @@ extern "C" int32_t sp2_test_tc_gemm(const void* arena_dev, int32_t ld, int32_t n
       b_slot < 0 || a_slot >= nslots || b_slot >= nslots || (upper != 0 && upper != 1))
     return SP2_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  CUtensorMap A, B;
-  if (sp2::tc_make_maps(const_cast<void*>(arena_dev), ld, nslots, &A, &B) != cudaSuccess) {
+  sp2::tc::Instance hinst;
+  std::memset(&hinst, 0, sizeof(hinst));
+  if (sp2::tc_make_maps(const_cast<void*>(arena_dev), ld, nslots, &hinst.mapA, &hinst.mapB) != cudaSuccess) {
     (void)cudaGetLastError();
     return SP2_ERR_CUDA;
   }
+  hinst.arena = (__nv_bfloat16*)const_cast<void*>(arena_dev);
+  hinst.slot_elems = (int64_t)3 * ld * ld;
+  hinst.ld = ld;
+  // device copies of the instance record and the error word (test entry point only)
+  sp2::tc::Instance* dinst = nullptr;
   int32_t* err = nullptr;
-  if (cudaMallocAsync((void**)&err, sizeof(int32_t), s) != cudaSuccess) {
+  if (cudaMallocAsync((void**)&dinst, sizeof(hinst), s) != cudaSuccess ||
+      cudaMallocAsync((void**)&err, sizeof(int32_t), s) != cudaSuccess) {
     (void)cudaGetLastError();
     return SP2_ERR_NOMEM;
   }
   int32_t herr = 0;
   sp2::tc::Job j;
   std::memset(&j, 0, sizeof(j));
-  j.ld = ld;
   j.mode = sp2::tc::MODE_STORE_F32;
   j.upper = upper;
   j.nterms = 1;
   j.rule = sp2::tc::SLOTS_FIXED;
+  j.count = 1;
+  j.total_tiles = sp2::tc::tiles_of(ld, upper);
+  j.inst = dinst;
   j.a_slot[0] = a_slot;
   j.b_slot[0] = b_slot;
-  j.arena = (__nv_bfloat16*)const_cast<void*>(arena_dev);
-  j.slot_elems = (int64_t)3 * ld * ld;
   j.out32 = out_dev;
   j.err = err;
-  bool ok = cudaMemsetAsync(err, 0, sizeof(int32_t), s) == cudaSuccess &&
-            sp2::tc_launch(A, B, j, s) == cudaSuccess &&
+  bool ok = cudaMemcpyAsync(dinst, &hinst, sizeof(hinst), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+            cudaMemsetAsync(err, 0, sizeof(int32_t), s) == cudaSuccess && sp2::tc_launch(j, s) == cudaSuccess &&
             cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
-            cudaFreeAsync(err, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+            cudaFreeAsync(err, s) == cudaSuccess && cudaFreeAsync(dinst, s) == cudaSuccess &&
+            cudaStreamSynchronize(s) == cudaSuccess;
   if (!ok) {
     (void)cudaGetLastError();
     return SP2_ERR_CUDA;

@@ -75,6 +75,15 @@ def lib() -> ctypes.CDLL:
         L.sp2_test_tc_gemm.restype = i32
         L.sp2_run_fp64_noalloc.argtypes = [vp, vp, i64, i64, vp, vp]
         L.sp2_run_fp64_noalloc.restype = i32
+        L.sp2_create_batch.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(i64), i32,
+                                       ctypes.POINTER(sp2_opts), ctypes.POINTER(vp)]
+        L.sp2_create_batch.restype = i32
+        L.sp2_run_batch.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+        L.sp2_run_batch.restype = i32
+        L.sp2_get_info_batch.argtypes = [vp, i32, ctypes.POINTER(sp2_info)]
+        L.sp2_get_info_batch.restype = i32
+        L.sp2_destroy_batch.argtypes = [vp]
+        L.sp2_destroy_batch.restype = None
         _lib = L
     return _lib
 
@@ -113,6 +122,42 @@ def sp2_run_host(h: int, F: np.ndarray, D: np.ndarray, stream=None) -> None:
 def sp2_get_info(h: int) -> dict:
     info = sp2_info()
     _check(lib().sp2_get_info(h, ctypes.byref(info)), "sp2_get_info")
+    return _info_dict(info)
+
+
+def sp2_create_batch(Ns, noccs, precision: str = "mixed", *, max_iter: int = 200, guard: bool = True,
+                     qtilde: float = 1.8, corrections: int = 1, refine_steps: int = 2,
+                     refine_fp64: bool = False) -> int:
+    count = len(Ns)
+    o = sp2_opts(max_iter, 1 if guard else 0, qtilde, corrections, refine_steps, 1 if refine_fp64 else 0, 0)
+    n_arr = (ctypes.c_int64 * count)(*Ns)
+    o_arr = (ctypes.c_int64 * count)(*noccs)
+    h = ctypes.c_void_p()
+    _check(lib().sp2_create_batch(count, n_arr, o_arr, PRECISIONS[precision], ctypes.byref(o), ctypes.byref(h)),
+           "sp2_create_batch")
+    return h.value
+
+
+def sp2_run_batch(hb: int, Fs, Ds, stream=None) -> None:
+    """Enqueue every F_i -> D_i of the batch (torch CUDA float64 tensors)."""
+    count = len(Fs)
+    f_arr = (ctypes.c_void_p * count)(*[F.data_ptr() for F in Fs])
+    d_arr = (ctypes.c_void_p * count)(*[D.data_ptr() for D in Ds])
+    _check(lib().sp2_run_batch(hb, f_arr, d_arr, _stream_ptr(stream)), "sp2_run_batch")
+
+
+def sp2_get_info_batch(hb: int, i: int) -> dict:
+    info = sp2_info()
+    _check(lib().sp2_get_info_batch(hb, i, ctypes.byref(info)), "sp2_get_info_batch")
+    return _info_dict(info)
+
+
+def sp2_destroy_batch(hb: int) -> None:
+    if hb:
+        lib().sp2_destroy_batch(hb)
+
+
+def _info_dict(info) -> dict:
     n, hl = info.n_iter, info.hist_len
     return {
         "status": info.status,
@@ -138,6 +183,46 @@ def sp2_test_tc_gemm(arena, ld: int, nslots: int, a_slot: int, b_slot: int, uppe
 def sp2_destroy(h: int) -> None:
     if h:
         lib().sp2_destroy(h)
+
+
+class BatchPurifier:
+    """One batch handle: F_i (N_i x N_i) -> D_i for problems of uneven size."""
+
+    def __init__(self, Ns, noccs, precision: str = "mixed", **opts):
+        self.Ns, self.noccs, self.precision = list(Ns), list(noccs), precision
+        self.h = sp2_create_batch(self.Ns, self.noccs, precision, **opts)
+
+    def run(self, Fs, Ds=None, stream=None):
+        import torch
+        if len(Fs) != len(self.Ns):
+            raise ValueError("one F per problem")
+        for F, N in zip(Fs, self.Ns):
+            if F.dtype != torch.float64 or not F.is_cuda or not F.is_contiguous() or F.shape != (N, N):
+                raise ValueError("each F must be a contiguous CUDA float64 tensor of its problem's shape")
+        if Ds is None:
+            Ds = [torch.empty_like(F) for F in Fs]
+        sp2_run_batch(self.h, Fs, Ds, stream)
+        return Ds
+
+    def info(self, i: int) -> dict:
+        return sp2_get_info_batch(self.h, i)
+
+    def close(self):
+        sp2_destroy_batch(self.h)
+        self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.h:
+                self.close()
+        except Exception:
+            pass
 
 
 class Purifier:

@@ -1,0 +1,98 @@
+"""Batches of problems of uneven size through the C ABI (sp2_run_batch).
+
+Each problem of a mixed batch is squared in the same persistent tensor-core launches
+as the others and stops on its own test; its result must equal (bit for bit) what a
+single-problem handle computes, and match the FP64 oracle within the mixed tolerance.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sp2_oracle as o
+from paper_1507_02087_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL_MIXED = 1e-6
+TOL_FP64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def sp2mod():
+    from paper_1507_02087_gb300 import sp2
+    sp2.lib()
+    return sp2
+
+
+def small_batch():
+    # uneven sizes, ragged tails, one problem spanning several tiles, mixed gaps
+    spec = [(130, 60, 0.1, 1), (17, 9, 0.2, 2), (300, 150, 0.05, 3), (1, 1, 0.1, 4), (257, 100, 0.02, 5),
+            (64, 32, 0.1, 6), (520, 260, 0.03, 7)]
+    cases = [inputs.dense_gapped(N, nocc, gap=gap, seed=seed) for N, nocc, gap, seed in spec]
+    return cases
+
+
+def test_mixed_batch_matches_singles_and_oracle(sp2mod):
+    cases = small_batch()
+    Fs = [c.F.cuda() for c in cases]
+    with sp2mod.BatchPurifier([c.N for c in cases], [c.nocc for c in cases], "mixed") as B:
+        Ds = B.run(Fs)
+        infos = [B.info(i) for i in range(len(cases))]
+    for c, F, D, info in zip(cases, Fs, Ds, infos):
+        assert info["status"] == 0
+        with sp2mod.Purifier(c.N, c.nocc, "mixed") as P:
+            Ds1 = P.run(F)
+            i1 = P.info()
+        assert torch.equal(D, Ds1), c.name           # identical arithmetic per problem
+        assert info["n_iter"] == i1["n_iter"]
+        ref = o.sp2(c.F.numpy(), c.nocc)
+        assert o.rel_error(D.cpu().numpy(), ref.D, c.nocc) <= TOL_MIXED, c.name
+    # problems stop independently
+    assert len({i["n_iter"] for i in infos}) > 1
+
+
+def test_mixed_batch_isolates_bad_problems(sp2mod):
+    good = inputs.dense_gapped(200, 100, gap=0.05, seed=9)
+    bad = inputs.dense_gapped(150, 75, gap=0.05, seed=10).F.numpy().copy()
+    bad[3, 4] = bad[4, 3] = np.nan
+    Fs = [good.F.cuda(), torch.from_numpy(bad).cuda(), torch.eye(40, dtype=torch.float64, device="cuda") * 2.0,
+          good.F.cuda()]
+    noccs = [100, 75, 20, 0]
+    with sp2mod.BatchPurifier([200, 150, 40, 200], noccs, "mixed") as B:
+        Ds = B.run(Fs)
+        infos = [B.info(i) for i in range(4)]
+    ref = o.sp2(good.F.numpy(), 100)
+    assert infos[0]["status"] == 0 and o.rel_error(Ds[0].cpu().numpy(), ref.D, 100) <= TOL_MIXED
+    assert infos[1]["status"] == 3 and bool(torch.isnan(Ds[1]).all())
+    assert infos[2]["status"] == 6
+    assert infos[3]["stop_reason"] == o.STOP_EXACT and float(Ds[3].abs().max()) == 0.0
+
+
+def test_fp64_batch_matches_oracle(sp2mod):
+    cases = small_batch()[:4]
+    Fs = [c.F.cuda() for c in cases]
+    with sp2mod.BatchPurifier([c.N for c in cases], [c.nocc for c in cases], "fp64") as B:
+        Ds = B.run(Fs)
+        infos = [B.info(i) for i in range(len(cases))]
+    for c, D, info in zip(cases, Ds, infos):
+        ref = o.sp2(c.F.numpy(), c.nocc)
+        assert info["status"] == 0 and abs(info["n_iter"] - ref.n) <= 1
+        assert o.rel_error(D.cpu().numpy(), ref.D, c.nocc) <= TOL_FP64
+
+
+def test_batch64_workload_sampled(sp2mod):
+    # the 64-problem workload (sizes log-uniform in [128, 2048], seed 1): every problem
+    # against its exact projector, and four of them against the oracle
+    cases = inputs.dense_batch(device="cuda")
+    with sp2mod.BatchPurifier([c.N for c in cases], [c.nocc for c in cases], "mixed") as B:
+        Ds = B.run([c.F for c in cases])
+        infos = [B.info(i) for i in range(len(cases))]
+    for c, D, info in zip(cases, Ds, infos):
+        assert info["status"] == 0
+        err = float(torch.linalg.norm(D - c.D_exact)) / c.nocc ** 0.5
+        assert err <= TOL_MIXED, (c.name, err)
+    for k in (0, 17, 40, 63):
+        c = cases[k]
+        if c.N > 1100:
+            continue
+        ref = o.sp2(c.F.cpu().numpy(), c.nocc)
+        assert o.rel_error(Ds[k].cpu().numpy(), ref.D, c.nocc) <= TOL_MIXED
