@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["dense", "batch64"], default="dense",
+                    help="dense: one N x N problem (default N=8192); batch64: 64 problems, N log-uniform "
+                         "in [128, 2048], seed 1")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--N", type=int, default=N_DEFAULT)
     ap.add_argument("--nocc", type=int, default=None)
@@ -221,11 +224,68 @@ def useful_flops(N, squares, deriv_steps, corrected, refine_steps):
     return f
 
 
+def run_batch(a, ws, rank, local):
+    """64 problems of uneven size in one batch: mixed (one launch sequence, per-problem
+    stops) against the FP64 path (problems one after the other)."""
+    import torch
+    from paper_1507_02087_gb300 import inputs, sp2
+    torch.cuda.set_device(local)
+    cases = inputs.dense_batch(device=torch.device("cuda", local))
+    Ns, noccs = [c.N for c in cases], [c.nocc for c in cases]
+    Fs = [c.F for c in cases]
+    stream = torch.cuda.current_stream()
+
+    def timed(B, steps):
+        Ds = [torch.empty_like(F) for F in Fs]
+        tms = []
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.run(Fs, Ds, stream)
+            e1.record(stream)
+            e1.synchronize()
+            tms.append(e0.elapsed_time(e1))
+        errs = [float(torch.linalg.norm(D - c.D_exact)) / math.sqrt(c.nocc) for D, c in zip(Ds, cases)]
+        infos = [B.info(i) for i in range(len(cases))]
+        return statistics.mean(tms), max(errs), infos
+
+    with sp2.BatchPurifier(Ns, noccs, "mixed") as B:
+        timed(B, a.warmup)
+        clocks = ClockSampler(local)
+        barrier(ws)
+        clocks.start()
+        ms, err, infos = timed(B, a.steps)
+        clk = clocks.stop()
+    ms = max_over_ranks(ms, ws)
+    flops = sum(useful_flops(N, i["hist_len"], i["n_iter"], True, 2) for N, i in zip(Ns, infos))
+    fp64 = None
+    if a.fp64_steps > 0:
+        with sp2.BatchPurifier(Ns, noccs, "fp64") as B64:
+            ms64, err64, inf64 = timed(B64, a.fp64_steps)
+        fp64 = {"time_to_d_ms": ms64, "max_err_vs_exact": err64, "speedup_mixed_vs_fp64": ms64 / ms}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x6->f32 (mixed), f64 reductions", "data": "synthetic",
+            "config": {"workload": "batch of 64 dense problems, N log-uniform in [128, 2048] (seed 1), "
+                                   "nocc = N/2, gap uniform in [0.005, 0.1]", "count": len(cases),
+                       "sum_N3": sum(N ** 3 for N in Ns), "precision": "mixed"},
+            "max_err_vs_exact": err, "meets_tolerance": bool(err <= TOL),
+            "tflops_useful": flops / (ms * 1e-3) / 1e12,
+            "n_iter_range": [min(i["n_iter"] for i in infos), max(i["n_iter"] for i in infos)],
+            "fp64_path": fp64, "clocks": clk}), flush=True)
+
+
 def main():
     a = parse()
     ws, rank, local = dist_setup()
     if a.impl == "reference":
         run_reference(a, ws, rank)
+        return
+    if a.workload == "batch64":
+        run_batch(a, ws, rank, local)
         return
     import torch
     from paper_1507_02087_gb300 import inputs, sp2

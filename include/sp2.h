@@ -80,7 +80,11 @@ typedef struct {
                            eigenvalue error */
   int32_t refine_fp64;  /* SP2_PREC_MIXED: 1 = refinement pair in FP64 (two FP64 squares),
                            0 = on the tensor cores like the expansion (default 0) */
-  int32_t reserved;     /* must be 0 */
+  int32_t launch_mode;  /* 0 = the loops run as CUDA-graph conditional WHILE nodes (default);
+                           1 = the same kernels launched on the stream up to the iteration cap,
+                           each returning at once after the device-side stop (same results and
+                           work plus a few microseconds per idle launch; for tools that cannot
+                           follow conditional graph nodes, such as kernel profilers) */
 } sp2_opts;
 
 #define SP2_MAX_ITER 512

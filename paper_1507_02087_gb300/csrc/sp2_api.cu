@@ -42,7 +42,7 @@ extern "C" void sp2_default_opts(sp2_opts* o) {
   o->corrections = 1;
   o->refine_steps = 2;
   o->refine_fp64 = 0;
-  o->reserved = 0;
+  o->launch_mode = 0;
 }
 
 extern "C" const char* sp2_status_string(int32_t s) {
@@ -62,7 +62,7 @@ extern "C" const char* sp2_status_string(int32_t s) {
 static bool opts_valid(const sp2_opts& o) {
   return o.max_iter >= 1 && o.max_iter <= SP2_MAX_ITER && o.qtilde > 0.0 && (o.guard == 0 || o.guard == 1) &&
          o.corrections >= 0 && o.corrections <= 1 && (o.refine_steps == 0 || o.refine_steps == 2) &&
-         (o.refine_fp64 == 0 || o.refine_fp64 == 1) && o.reserved == 0;
+         (o.refine_fp64 == 0 || o.refine_fp64 == 1) && (o.launch_mode == 0 || o.launch_mode == 1);
 }
 
 static DevState initial_state(int64_t N, int64_t nocc, const sp2_opts& o, int ld, int round_fp32) {
@@ -277,6 +277,33 @@ struct MixedEngine {
     return SP2_OK;
   }
 
+  // The graph's loops as plain stream launches (launch_mode 1): every launch after the
+  // device-side stop returns at once, so the work and the results are the same.
+  sp2_status enqueue_loops_plain(cudaStream_t s) {
+    using namespace sp2::tc;
+    for (int it = 0; it <= opts.max_iter; ++it) {
+      SP2_TRY(sp2::tc_launch(job(MODE_SP2_STEP, 1, SLOTS_FORWARD), s));
+      SP2_TRY(sp2::batch_launch_forward_tail(inst_dev, count, s));
+    }
+    if (opts.corrections > 0) {
+      SP2_TRY(sp2::tc_launch(job(MODE_STORE_PIECES, 0, SLOTS_CORR_M), s));
+      SP2_TRY(sp2::tc_launch(job(MODE_DF_COMBINE, 1, SLOTS_CORR_DF), s));
+      for (int it = 0; it <= opts.max_iter + 1; ++it) {
+        SP2_TRY(sp2::tc_launch(job(MODE_DERIV_STEP, 1, SLOTS_DERIV, 2), s));
+        SP2_TRY(sp2::batch_launch_deriv_tail(inst_dev, count, s));
+      }
+    }
+    if (opts.refine_steps > 0 && !opts.refine_fp64) {
+      SP2_TRY(sp2::batch_launch_corrected_to_pieces(inst_dev, count, sb, opts.corrections > 0, s));
+      Job jr = job(MODE_DERIV_STEP, 1, SLOTS_REFINE);
+      jr.a_slot[0] = 0;
+      SP2_TRY(sp2::tc_launch(jr, s));
+      jr.a_slot[0] = 1;
+      SP2_TRY(sp2::tc_launch(jr, s));
+    }
+    return SP2_OK;
+  }
+
   // F/D in user order.
   sp2_status enqueue(const double* const* F, double* const* D, cudaStream_t s) {
     sp2::BatchPtrs ptrs;
@@ -288,7 +315,12 @@ struct MixedEngine {
     SP2_TRY(cudaMemsetAsync(err_dev, 0, sizeof(int32_t), s));
     SP2_TRY(sp2::batch_launch_prologue(inst_dev, count, pb, sb, ptrs, part_lo, part_hi, part_bad, s));
     SP2_TRY(cudaEventRecord(ev[0], s));
-    SP2_TRY(cudaGraphLaunch(exec, s));
+    if (opts.launch_mode == 0) {
+      SP2_TRY(cudaGraphLaunch(exec, s));
+    } else {
+      sp2_status st = enqueue_loops_plain(s);
+      if (st != SP2_OK) return st;
+    }
     SP2_TRY(cudaEventRecord(ev[1], s));
     const int use_dx = opts.corrections > 0;
     if (opts.refine_steps > 0 && opts.refine_fp64) {
@@ -446,7 +478,12 @@ static sp2_status enqueue_f64(sp2_ctx* h, const double* F, double* D, cudaStream
   SP2_TRY(sp2::launch_bounds_and_init(h->st_dev, F, N, N, h->part_lo, h->part_hi, h->part_bad, h->nparts, s));
   SP2_TRY(sp2::launch_scale_f64(h->st_dev, F, N, N, h->buf[0], h->ld, s));
   SP2_TRY(cudaEventRecord(h->ev_loop[0], s));
-  SP2_TRY(cudaGraphLaunch(h->exec, s));
+  if (h->opts.launch_mode == 0) {
+    SP2_TRY(cudaGraphLaunch(h->exec, s));
+  } else {
+    for (int it = 0; it <= h->opts.max_iter; ++it)
+      SP2_TRY(sp2::launch_f64_step_plain(h->st_dev, h->buf[0], h->buf[1], h->part, h->T, s));
+  }
   SP2_TRY(cudaEventRecord(h->ev_loop[1], s));
   SP2_TRY(sp2::launch_copy_out(h->st_dev, h->buf[0], h->buf[1], h->ld, N, D, N, s));
   SP2_TRY(cudaMemcpyAsync(h->st_host, h->st_dev, sizeof(DevState), cudaMemcpyDeviceToHost, s));

@@ -68,6 +68,10 @@ cudaError_t batch_add_deriv_tail(cudaGraph_t g, const cudaGraphNode_t* dep, cons
                                  cudaGraphConditionalHandle cond);
 cudaError_t batch_add_corrected_to_pieces(cudaGraph_t g, const cudaGraphNode_t* dep, const tc::Instance* inst,
                                           int count, int sb, int use_dx, cudaGraphNode_t* node);
+cudaError_t batch_launch_forward_tail(const tc::Instance* inst, int count, cudaStream_t s);
+cudaError_t batch_launch_deriv_tail(const tc::Instance* inst, int count, cudaStream_t s);
+cudaError_t batch_launch_corrected_to_pieces(const tc::Instance* inst, int count, int sb, int use_dx,
+                                             cudaStream_t s);
 cudaError_t batch_launch_assemble(const tc::Instance* inst, int count, int sb, int use_dx, int from_r0,
                                   const BatchPtrs& ptrs, double* f64_buf, cudaStream_t s);
 

@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(kFT) batch_finalize_kernel(const Instance* ins
 
 // Clears `cond` once no instance needs another round: which = 0 for the expansion
 // (every instance done), 1 for the derivative loop (every instance at dk == n_out).
+// Only used inside the loop graphs.
 __global__ void batch_check_kernel(const Instance* inst, int count, int which, cudaGraphConditionalHandle cond) {
   __shared__ int busy;
   if (threadIdx.x == 0) busy = 0;
@@ -212,7 +213,9 @@ __global__ void batch_check_kernel(const Instance* inst, int count, int which, c
 }
 
 // After a derivative round: every instance still short of n_out has done one more step.
-__global__ void batch_deriv_advance_kernel(const Instance* inst, int count, cudaGraphConditionalHandle cond) {
+// In the loop graph (use_cond) it also clears the loop condition when none is left.
+__global__ void batch_deriv_advance_kernel(const Instance* inst, int count, cudaGraphConditionalHandle cond,
+                                           int use_cond) {
   __shared__ int busy;
   if (threadIdx.x == 0) busy = 0;
   __syncthreads();
@@ -224,7 +227,7 @@ __global__ void batch_deriv_advance_kernel(const Instance* inst, int count, cuda
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0 && !busy) cudaGraphSetConditional(cond, 0);
+  if (use_cond && threadIdx.x == 0 && !busy) cudaGraphSetConditional(cond, 0);
 }
 
 // ---- corrected result and output ------------------------------------------------------------
@@ -326,8 +329,25 @@ cudaError_t batch_add_forward_tail(cudaGraph_t g, const cudaGraphNode_t* dep, co
 cudaError_t batch_add_deriv_tail(cudaGraph_t g, const cudaGraphNode_t* dep, const Instance* inst, int count,
                                  cudaGraphConditionalHandle cond) {
   cudaGraphNode_t n;
-  void* a[] = {&inst, &count, &cond};
+  int use_cond = 1;
+  void* a[] = {&inst, &count, &cond, &use_cond};
   return add_node(g, dep, 1, (void*)batch_deriv_advance_kernel, dim3(1), dim3(256), a, &n);
+}
+
+// Stream-launched forms of the loop tails (launch_mode 1: no graph).
+cudaError_t batch_launch_forward_tail(const Instance* inst, int count, cudaStream_t s) {
+  batch_finalize_kernel<<<count, kFT, 0, s>>>(inst, count);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_launch_deriv_tail(const Instance* inst, int count, cudaStream_t s) {
+  batch_deriv_advance_kernel<<<1, 256, 0, s>>>(inst, count, 0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_launch_corrected_to_pieces(const Instance* inst, int count, int sb, int use_dx, cudaStream_t s) {
+  batch_corrected_to_pieces_kernel<<<count * sb, 256, 0, s>>>(inst, count, sb, use_dx);
+  return cudaGetLastError();
 }
 
 cudaError_t batch_add_corrected_to_pieces(cudaGraph_t g, const cudaGraphNode_t* dep, const Instance* inst, int count,

@@ -67,6 +67,27 @@ def test_mixed_batch_isolates_bad_problems(sp2mod):
     assert infos[3]["stop_reason"] == o.STOP_EXACT and float(Ds[3].abs().max()) == 0.0
 
 
+def test_stream_launch_mode_gives_the_same_results(sp2mod):
+    # launch_mode 1 (plain stream launches with device-side early exit, for profilers)
+    # runs the same kernels as the loop graphs: results must be identical
+    cases = small_batch()[:3]
+    Fs = [c.F.cuda() for c in cases]
+    out = {}
+    for mode in (0, 1):
+        with sp2mod.BatchPurifier([c.N for c in cases], [c.nocc for c in cases], "mixed", max_iter=80,
+                                  launch_mode=mode) as B:
+            out[mode] = (B.run(Fs), [B.info(i)["n_iter"] for i in range(3)])
+    assert out[0][1] == out[1][1]
+    for a, b in zip(out[0][0], out[1][0]):
+        assert torch.equal(a, b)
+    F = cases[2].F.cuda()
+    r = {}
+    for mode in (0, 1):
+        with sp2mod.Purifier(F.shape[0], cases[2].nocc, "fp64", max_iter=80, launch_mode=mode) as P:
+            r[mode] = (P.run(F), P.info()["n_iter"])
+    assert r[0][1] == r[1][1] and torch.equal(r[0][0], r[1][0])
+
+
 def test_fp64_batch_matches_oracle(sp2mod):
     cases = small_batch()[:4]
     Fs = [c.F.cuda() for c in cases]
