@@ -160,6 +160,35 @@ sp2_status sp2_get_info_batch(sp2_batch hb, int32_t i, sp2_info* out);
 /* Free a batch handle (synchronises the device first).  NULL is a no-op. */
 void sp2_destroy_batch(sp2_batch hb);
 
+/* ---- block-sparse matrices with block truncation ------------------------------------------
+ * The recursive expansion with truncation (Alg. 1: X~_i = X_i + E_i) on a symmetric
+ * block-sparse F with 32 x 32 blocks: X~_0 and every iterate are kept as BSR with FP32
+ * blocks, and E_i drops every off-diagonal block whose Frobenius norm is below tau
+ * (||X_IJ||_F^2 < tau^2, evaluated in FP64 in a fixed order: each block row of squares
+ * left to right, then the row sums top to bottom); diagonal blocks are always kept.
+ * The squares are block-sparse products over the symbolic pattern of X~^2; bounds,
+ * traces, norms and the stop test (Alg. 3 with the trace guard) are FP64, on the device. */
+typedef struct sp2_bsr_ctx* sp2_bsr;
+
+/* N: a multiple of 32, at most 65536.  tau >= 0 (0 keeps every stored block).  opts as
+ * for sp2_create (corrections, refine_steps and refine_fp64 are ignored).  Workspace is
+ * about 10 KB per block of (N/32)^2, i.e. ~11 GB at N = 32768. */
+sp2_status sp2_create_bsr(int64_t N, int64_t n_occ, double tau, const sp2_opts* opts, sp2_bsr* out);
+
+/* F as BSR in device memory: row_ptr [N/32 + 1] (int32), col_idx [nnzb] (int32, sorted
+ * in each block row, every diagonal block present), vals [nnzb][32][32] (FP64, row-major
+ * blocks); F must be exactly symmetric.  D_dev: NULL, or an N x N FP64 device buffer that
+ * receives D densely.  Asynchronous. */
+sp2_status sp2_run_bsr(sp2_bsr h, const int32_t* row_ptr_dev, const int32_t* col_idx_dev, const double* vals_dev,
+                       int64_t nnzb, double* D_dev, void* stream);
+
+/* Wait for the last run and describe it; *nnzb_out (if not NULL) receives the number of
+ * stored blocks of D. */
+sp2_status sp2_get_info_bsr(sp2_bsr h, sp2_info* out, int64_t* nnzb_out);
+
+/* Free the handle (synchronises the device first).  NULL is a no-op. */
+void sp2_destroy_bsr(sp2_bsr h);
+
 /* FP64 purification that allocates no memory (the paper has no counterpart; this is a
  * service for callers that cannot call cudaMalloc, e.g. code running under another
  * component's allocator or in loops where entering the allocator is not allowed).

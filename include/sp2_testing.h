@@ -25,6 +25,17 @@ extern "C" {
 int32_t sp2_test_tc_gemm(const void* arena_dev, int32_t ld, int32_t nslots, int32_t a_slot, int32_t b_slot,
                          int32_t upper, float* out_dev, void* stream);
 
+/* Block truncation decision of the block-sparse path on its own: for every 32 x 32 block
+ * (I, J) of the dense N x N FP32 device matrix, keep_dev[I * (N/32) + J] = 1 if I == J or
+ * ||block||_F^2 >= tau^2 (FP64, the fixed summation order of sp2_create_bsr), else 0.
+ * Synchronises `stream`. */
+int32_t sp2_test_bsr_keep(const float* dense_dev, int64_t N, double tau, uint8_t* keep_dev, void* stream);
+
+/* Symbolic square of the block-sparse path on its own: mask_host is an nb x nb 0/1 block
+ * pattern (host, row-major); upper_host receives the pattern of its square restricted to
+ * J >= I, as computed by the device kernels.  Synchronous. */
+int32_t sp2_test_bsr_square_pattern(const uint8_t* mask_host, int32_t nb, uint8_t* upper_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,68 @@
+"""CPU oracle for SP2 with block truncation (the E_i of Alg. 1) -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests and the benchmark's CPU-baseline leg import this module.
+
+The recursive expansion of Alg. 1 adds a perturbation E_i to every iterate; in a
+sparse setting E_i removes small parts of X_i (§1; §5 and §6 use element-magnitude
+and error-controlled removal).  Here the matrix is split into b x b blocks and E_i
+drops every off-diagonal block whose Frobenius norm is below tau (diagonal blocks
+are always kept), applied to X_0 and after every step, on a symmetric pattern.
+
+Reading (the paper fixes no block rule): a block is dropped iff ||X_IJ||_F^2 < tau^2,
+with ||X_IJ||_F^2 evaluated in FP64 from the stored values in a fixed order: each
+row's squares summed left to right, then the row sums top to bottom (each square of
+an FP32 value is exact in FP64).  The GPU path evaluates the same sums in the same
+order, so given the same stored block both sides take the same decision bit for bit.
+
+`sp2_bsr` runs Alg. 3 on dense FP64 matrices with the blocks masked after every
+step; `keep_mask` and `square_pattern` are the index work on their own.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import sp2_oracle as o
+
+
+def block_norms2(X: np.ndarray, b: int) -> np.ndarray:
+    """||X_IJ||_F^2 for every b x b block, rows of squares summed left to right, then
+    the row sums top to bottom (sequential FP64 sums via cumsum)."""
+    N = X.shape[0]
+    nb = N // b
+    Y = np.asarray(X, dtype=np.float64).reshape(nb, b, nb, b).transpose(0, 2, 1, 3)  # [I, J, r, c]
+    sq = Y * Y
+    rows = np.cumsum(sq, axis=3)[..., -1]          # [I, J, r]
+    return np.cumsum(rows, axis=2)[..., -1]         # [I, J]
+
+
+def keep_mask(X: np.ndarray, b: int, tau: float) -> np.ndarray:
+    """Blocks kept by the truncation: diagonal blocks, and off-diagonal blocks with
+    ||X_IJ||_F^2 >= tau^2.  For symmetric X the mask is symmetric."""
+    n2 = block_norms2(X, b)
+    keep = n2 >= tau * tau
+    np.fill_diagonal(keep, True)
+    return keep
+
+
+def apply_mask(X: np.ndarray, keep: np.ndarray, b: int) -> np.ndarray:
+    return X * np.kron(keep, np.ones((b, b)))
+
+
+def square_pattern(keep: np.ndarray) -> np.ndarray:
+    """Block pattern of X^2 for X with block pattern `keep`: (I, J) is structurally
+    nonzero iff some K has keep[I, K] and keep[K, J]."""
+    k = keep.astype(np.int64)
+    return (k @ k) > 0
+
+
+def sp2_bsr(F: np.ndarray, nocc: int, b: int, tau: float, *, bounds=None, max_iter: int = 200,
+            guard: bool = True):
+    """Alg. 3 with X~_i = X_i + E_i, E_i the block truncation above (FP64 values)."""
+    def perturb(i, X):
+        return apply_mask(X, keep_mask(X, b, tau), b) - X
+    return o.sp2(F, nocc, bounds=bounds, max_iter=max_iter, guard=guard, perturb=perturb)
+
+
+def gershgorin_bounds_blocks(F: np.ndarray) -> tuple[float, float]:
+    """Gershgorin discs of F (the same bounds as the dense oracle)."""
+    return o.gershgorin_bounds(F)

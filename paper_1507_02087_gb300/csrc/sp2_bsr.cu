@@ -1,0 +1,865 @@
+// Block-sparse SP2 with Frobenius block truncation (the E_i of Alg. 1).
+//
+// X~_i is a symmetric block-sparse matrix with 32 x 32 FP32 blocks, stored with both
+// triangles as BSR (row_ptr, sorted col_idx, values) plus one bitmap row per block
+// row (bit J of row I set iff block (I, J) is stored) and a popcount rank table, so
+// "where is block (I, J)" is an O(1) integer computation.  One loop round (square k):
+//
+//   1. symbolic square: the upper block pattern of S = X~_{k-1}^2 (row I of S is the
+//      OR of the bitmap rows K in row I of X~_{k-1}), listed as (I, J >= I) pairs;
+//   2. numeric square + SP2 epilogue for each pair: S_IJ = sum_K X_IK X_JK^T over
+//      the K both rows hold (increasing K), X_IJ <- S_IJ or 2 X_IJ - S_IJ (Alg. 3),
+//      the FP64 partials of ||X~_{k-1} - S||_F^2 and Tr[X_k], and ||X_IJ||_F^2 of the
+//      new block in a fixed order (row sums left to right, rows top to bottom);
+//   3. stop test on the device (Alg. 3, with the trace guard);
+//   4. truncation: off-diagonal blocks with ||X_IJ||_F^2 < tau^2 are dropped, the
+//      kept bitmap is set for (I, J) and (J, I), and X~_k is written as BSR (each kept
+//      upper block and its transpose at the rank of its column in its row).
+//
+// All index work is integer and fixed-order, so the pattern of every iterate is
+// reproducible bit for bit (and equals the host's, given the same stored blocks).
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+
+#include "../../include/sp2.h"
+#include "sp2_common.cuh"
+#include "sp2_kernels.h"
+
+namespace sp2 {
+namespace bsr {
+
+constexpr int B = 32;              // block size
+constexpr int BE = B * B;          // elements per block
+constexpr int NT = 256;            // threads of the block kernels
+constexpr int MAX_NB = 2048;       // block rows (N <= 65536)
+
+__device__ __forceinline__ int popc(uint32_t x) { return __popc(x); }
+
+struct Mat {          // one block-sparse iterate
+  int* rp;            // [nb + 1]
+  int* ci;            // [cap]
+  float* vals;        // [cap][32][32]
+  uint32_t* bits;     // [nb][W]
+  int* rank;          // [nb][W]: set bits of the row in words before w
+};
+
+struct Pairs {        // upper (I, J >= I) block pairs of a pattern
+  int* ptr;           // [nb + 1]
+  int* col;           // [cap]
+  int* row;           // [cap]
+  int* nnz;           // device count
+};
+
+// Position of block (I, K) in `m`, or -1 if absent.
+__device__ __forceinline__ int find_block(const Mat& m, int W, int I, int K) {
+  const uint32_t w = m.bits[(int64_t)I * W + (K >> 5)];
+  const uint32_t bit = 1u << (K & 31);
+  if (!(w & bit)) return -1;
+  return m.rp[I] + m.rank[(int64_t)I * W + (K >> 5)] + popc(w & (bit - 1u));
+}
+
+// ---- generic bitmap / pattern kernels ----------------------------------------------------
+__global__ void clear_words_kernel(uint32_t* bits, int64_t n, const DevState* st) {
+  if (st && !st->iter_active) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    bits[i] = 0u;
+}
+
+// per row: number of set bits (J >= I only with `upper`)
+__global__ void row_counts_kernel(const uint32_t* bits, int nb, int W, int upper, int* counts, const DevState* st) {
+  if (st && !st->iter_active) return;
+  const int I = blockIdx.x;
+  __shared__ int s;
+  if (threadIdx.x == 0) s = 0;
+  __syncthreads();
+  int c = 0;
+  for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    uint32_t x = bits[(int64_t)I * W + w];
+    if (upper) {
+      const int lo = w * 32;
+      if (lo + 31 < I) x = 0u;
+      else if (lo < I) x &= ~((1u << (I - lo)) - 1u);
+    }
+    c += popc(x);
+  }
+  atomicAdd(&s, c);
+  __syncthreads();
+  if (threadIdx.x == 0) counts[I] = s;
+}
+
+// exclusive scan of counts[0..nb) into ptr[0..nb], total in *total (one block)
+__global__ void scan_kernel(const int* counts, int nb, int* ptr, int* total, const DevState* st) {
+  if (st && !st->iter_active) return;
+  __shared__ int sm[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? counts[i] : 0;
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const int t = threadIdx.x >= o ? sm[threadIdx.x - o] : 0;
+      __syncthreads();
+      sm[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nb) ptr[i] = carry + sm[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += sm[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    ptr[nb] = carry;
+    if (total) *total = carry;
+  }
+}
+
+// rank[I][w] = set bits of row I in words < w (one block per row, W <= 64)
+__global__ void rank_kernel(const uint32_t* bits, int nb, int W, int* rank, const DevState* st) {
+  if (st && !st->iter_active) return;
+  const int I = blockIdx.x;
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int w = 0; w < W; ++w) {
+      rank[(int64_t)I * W + w] = acc;
+      acc += popc(bits[(int64_t)I * W + w]);
+    }
+  }
+}
+
+// list the set bits of every row (J >= I with `upper`) as pairs, in increasing J
+__global__ void fill_pairs_kernel(const uint32_t* bits, int nb, int W, int upper, Pairs P, const DevState* st) {
+  if (st && !st->iter_active) return;
+  const int I = blockIdx.x;
+  if (threadIdx.x == 0) {
+    int pos = P.ptr[I];
+    for (int w = 0; w < W; ++w) {
+      uint32_t x = bits[(int64_t)I * W + w];
+      const int lo = w * 32;
+      if (upper) {
+        if (lo + 31 < I) continue;
+        if (lo < I) x &= ~((1u << (I - lo)) - 1u);
+      }
+      while (x) {
+        const int b = __ffs(x) - 1;
+        x &= x - 1u;
+        P.col[pos] = lo + b;
+        P.row[pos] = I;
+        ++pos;
+      }
+    }
+  }
+}
+
+__global__ void csr_to_bits_kernel(const int* rp, const int* ci, int nb, int W, uint32_t* bits) {
+  const int I = blockIdx.x;
+  for (int e = rp[I] + threadIdx.x; e < rp[I + 1]; e += blockDim.x) {
+    const int J = ci[e];
+    atomicOr(&bits[(int64_t)I * W + (J >> 5)], 1u << (J & 31));
+  }
+}
+
+// ---- initialisation: Gershgorin bounds of the BSR input, X_0 on F's upper pattern --------
+// One block per block row; thread r < 32 sums |F| over row r of the block row.
+__global__ void bsr_gersh_kernel(const int* rp, const int* ci, const double* vals, int nb, double* lo_out,
+                                 double* hi_out, int* bad_out) {
+  const int I = blockIdx.x;
+  __shared__ double slo[B], shi[B];
+  __shared__ int sbad[B];
+  const int r = threadIdx.x;
+  double s = 0.0, d = 0.0;
+  int bad = 0;
+  if (r < B) {
+    for (int e = rp[I]; e < rp[I + 1]; ++e) {
+      const int J = ci[e];
+      const double* blk = vals + (int64_t)e * BE + r * B;
+      for (int c = 0; c < B; ++c) {
+        const double a = blk[c];
+        if (!isfinite(a)) bad = 1;
+        if (J == I && c == r) d = a;
+        else s += fabs(a);
+      }
+    }
+    slo[r] = d - s;
+    shi[r] = d + s;
+    sbad[r] = bad;
+  }
+  __syncthreads();
+  if (r == 0) {
+    double lo = slo[0], hi = shi[0];
+    int b = sbad[0];
+    for (int k = 1; k < B; ++k) { lo = fmin(lo, slo[k]); hi = fmax(hi, shi[k]); b |= sbad[k]; }
+    lo_out[I] = lo; hi_out[I] = hi; bad_out[I] = b;
+  }
+}
+
+constexpr int kIT = 1024;
+
+__global__ void __launch_bounds__(kIT)
+bsr_init_kernel(DevState* st, const int* rp, const int* ci, const double* vals, int nb, const double* lo_in,
+                const double* hi_in, const int* bad_in) {
+  __shared__ double sm[32];
+  __shared__ double s_lmin, s_lmax;
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) {
+    double lo = INFINITY, hi = -INFINITY;
+    int bad = 0;
+    for (int I = 0; I < nb; ++I) { lo = fmin(lo, lo_in[I]); hi = fmax(hi, hi_in[I]); bad |= bad_in[I]; }
+    if (!isfinite(lo) || !isfinite(hi)) bad = 1;
+    s_lmin = lo; s_lmax = hi; s_bad = bad;
+  }
+  __syncthreads();
+  const double lmin = s_lmin, lmax = s_lmax, w = lmax - lmin;
+  // Tr[X_0] over the stored (FP32) diagonal; the diagonal block of row I is found by search
+  double t = 0.0;
+  for (int i = threadIdx.x; i < nb * B; i += kIT) {
+    const int I = i / B, r = i % B;
+    double f = 0.0;
+    for (int e = rp[I]; e < rp[I + 1]; ++e)
+      if (ci[e] == I) { f = vals[(int64_t)e * BE + r * B + r]; break; }
+    t += (double)(float)((lmax - f) / w);
+  }
+  t = block_sum<kIT>(t, sm);
+  if (threadIdx.x == 0) {
+    const int N = st->N, nocc = st->nocc;
+    st->lmin = lmin; st->lmax = lmax;
+    st->dk = 0; st->k = 0; st->done = 0; st->n_out = 0; st->reason = SP2_STOP_EXACT;
+    st->status = SP2_OK; st->out_buf = 0; st->out_mode = OUT_COPY; st->hist_len = 0;
+    st->tr[0] = 0.0; st->p[0] = 0; st->iter_active = 1;
+    if (s_bad) { st->status = SP2_ERR_NONFINITE; st->done = 1; st->out_mode = OUT_NAN; }
+    else if (nocc == 0) { st->done = 1; st->out_mode = OUT_ZERO; }
+    else if (nocc == N) { st->done = 1; st->out_mode = OUT_IDENTITY; }
+    else if (!(lmax > lmin)) { st->status = SP2_ERR_NO_GAP; st->done = 1; st->out_mode = OUT_NAN; }
+    else st->tr[0] = t;
+  }
+}
+
+// ||blk||_F^2 in the fixed order (rows left to right, then rows top to bottom) by warp 0;
+// blk in shared memory with row stride B + 1.
+__device__ __forceinline__ double block_norm2_fixed(const float* blk) {
+  const int lane = threadIdx.x & 31;
+  double rs = 0.0;
+  for (int c = 0; c < B; ++c) {
+    const double x = (double)blk[lane * (B + 1) + c];
+    rs = __dadd_rn(rs, __dmul_rn(x, x));
+  }
+  double tot = 0.0;
+  for (int r = 0; r < B; ++r) tot = __dadd_rn(tot, __shfl_sync(0xffffffffu, rs, r));
+  return tot;
+}
+
+// X_0 = (lmax I - F)/(lmax - lmin) on the upper pairs of F's pattern, with the
+// truncation decision (Alg. 1: X~_0 = X_0 + E_0).
+__global__ void __launch_bounds__(NT)
+bsr_scale_pairs_kernel(const DevState* st, const int* frp, const uint32_t* fbits, const int* frank,
+                       const double* fvals, int W, Pairs P, float* svals, uint8_t* skeep, double tau2) {
+  __shared__ float blk[B * (B + 1)];
+  if (st->done) return;
+  const int nnz = *P.nnz;
+  const double lmax = st->lmax, w = st->lmax - st->lmin;
+  for (int q = blockIdx.x; q < nnz; q += gridDim.x) {
+    const int I = P.row[q], J = P.col[q];
+    const uint32_t word = fbits[(int64_t)I * W + (J >> 5)];
+    const int pos = frp[I] + frank[(int64_t)I * W + (J >> 5)] + popc(word & ((1u << (J & 31)) - 1u));
+    for (int e = threadIdx.x; e < BE; e += NT) {
+      const int r = e / B, c = e % B;
+      const double f = fvals[(int64_t)pos * BE + e];
+      const float x = (float)((((I == J && r == c) ? lmax : 0.0) - f) / w);
+      blk[r * (B + 1) + c] = x;
+      svals[(int64_t)q * BE + e] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const double n2 = block_norm2_fixed(blk);
+      if (threadIdx.x == 0) skeep[q] = (I == J || n2 >= tau2) ? 1 : 0;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- symbolic square -----------------------------------------------------------------------
+// S row I (upper part) = OR over K in row I of X of bitmap row K.
+__global__ void bsr_sym_kernel(DevState* st, Mat X, int nb, int W, uint32_t* sbits) {
+  const int I = blockIdx.x;
+  if (I == 0 && threadIdx.x == 0) st->iter_active = st->done ? 0 : 1;
+  if (st->done) return;
+  for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    uint32_t acc = 0u;
+    for (int e = X.rp[I]; e < X.rp[I + 1]; ++e) acc |= X.bits[(int64_t)X.ci[e] * W + w];
+    const int lo = w * 32;
+    if (lo + 31 < I) acc = 0u;
+    else if (lo < I) acc &= ~((1u << (I - lo)) - 1u);
+    sbits[(int64_t)I * W + w] = acc;
+  }
+}
+
+// ---- numeric square + SP2 epilogue + truncation decision -----------------------------------
+__global__ void __launch_bounds__(NT)
+bsr_numeric_kernel(const DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* skeep, double* spart,
+                   double tau2) {
+  __shared__ float As[2][B * (B + 1)];
+  __shared__ float Bs[2][B * (B + 1)];
+  __shared__ int kI[MAX_NB], kJ[MAX_NB];
+  __shared__ int s_base;
+  __shared__ float wred[NT / 32];
+  if (!st->iter_active) return;
+  const int nnz = *P.nnz;
+  const int kprev = st->k;
+  const int pk = st->tr[kprev] > (double)st->nocc ? 1 : 0;   // Alg. 3 trace test
+  const int tid = threadIdx.x;
+  const int r = tid / 8, c0 = (tid % 8) * 4;
+  for (int q = blockIdx.x; q < nnz; q += gridDim.x) {
+    const int I = P.row[q], J = P.col[q];
+    // K in row I (increasing) that row J also holds
+    if (tid == 0) s_base = 0;
+    __syncthreads();
+    const int b0 = X.rp[I], b1 = X.rp[I + 1];
+    for (int e0 = b0; e0 < b1; e0 += NT) {
+      const int e = e0 + tid;
+      int pj = -1;
+      if (e < b1) pj = find_block(X, W, J, X.ci[e]);
+      const int flag = pj >= 0;
+      // order-preserving compaction across the block
+      const unsigned bal = __ballot_sync(0xffffffffu, flag);
+      const int warp = tid >> 5, lane = tid & 31;
+      __shared__ int wcnt[NT / 32];
+      if (lane == 0) wcnt[warp] = __popc(bal);
+      __syncthreads();
+      int off = 0;
+      for (int w = 0; w < warp; ++w) off += wcnt[w];
+      if (flag) {
+        const int slot = s_base + off + __popc(bal & ((1u << lane) - 1u));
+        kI[slot] = e;
+        kJ[slot] = pj;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int t = 0;
+        for (int w = 0; w < NT / 32; ++w) t += wcnt[w];
+        s_base += t;
+      }
+      __syncthreads();
+    }
+    const int cnt = s_base;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int m = 0; m < cnt; ++m) {
+      const int buf = m & 1;
+      const float* a = X.vals + (int64_t)kI[m] * BE;
+      const float* b = X.vals + (int64_t)kJ[m] * BE;
+      for (int e = tid; e < BE; e += NT) {
+        As[buf][(e / B) * (B + 1) + e % B] = a[e];
+        Bs[buf][(e / B) * (B + 1) + e % B] = b[e];
+      }
+      __syncthreads();
+      #pragma unroll 8
+      for (int k = 0; k < B; ++k) {
+        const float av = As[buf][r * (B + 1) + k];
+        #pragma unroll
+        for (int j = 0; j < 4; ++j) acc[j] = fmaf(av, Bs[buf][(c0 + j) * (B + 1) + k], acc[j]);
+      }
+    }
+    __syncthreads();
+    // epilogue: X_old (I, J) of X~_{k-1} if stored
+    const int po = find_block(X, W, I, J);
+    float vloc = 0.f;
+    double trloc = 0.0;
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float old = po >= 0 ? X.vals[(int64_t)po * BE + r * B + c0 + j] : 0.f;
+      const float s = acc[j];
+      const float nw = pk ? s : fmaf(2.0f, old, -s);
+      const float d = old - s;
+      vloc = fmaf(d, d, vloc);
+      As[0][r * (B + 1) + c0 + j] = nw;
+      svals[(int64_t)q * BE + r * B + c0 + j] = nw;
+      if (I == J && r == c0 + j) trloc += (double)nw;
+    }
+    // block reductions (fixed tree): v^2 with weight 2 off the diagonal, trace
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      vloc += __shfl_xor_sync(0xffffffffu, vloc, o);
+      trloc += __shfl_xor_sync(0xffffffffu, trloc, o);
+    }
+    __shared__ double wtr[NT / 32];
+    if ((tid & 31) == 0) { wred[tid >> 5] = vloc; wtr[tid >> 5] = trloc; }
+    __syncthreads();
+    if (tid < 32) {
+      const double n2 = block_norm2_fixed(As[0]);
+      if (tid == 0) {
+        double v2 = 0.0, tr = 0.0;
+        for (int w = 0; w < NT / 32; ++w) { v2 += (double)wred[w]; tr += wtr[w]; }
+        spart[2 * (int64_t)q] = (I == J ? 1.0 : 2.0) * v2;
+        spart[2 * (int64_t)q + 1] = tr;
+        skeep[q] = (I == J || n2 >= tau2) ? 1 : 0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// per-round reduction over the pairs and the stop test (stored-diagonal trace)
+__global__ void __launch_bounds__(1024)
+bsr_finalize_kernel(DevState* st, const double* spart, const int* nnz_p, cudaGraphConditionalHandle cond,
+                    int use_cond) {
+  __shared__ double sm[32];
+  if (!st->iter_active) {
+    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+    return;
+  }
+  const int nnz = *nnz_p;
+  double a = 0.0, b = 0.0;
+  for (int t = threadIdx.x; t < nnz; t += 1024) { a += spart[2 * (int64_t)t]; b += spart[2 * (int64_t)t + 1]; }
+  a = block_sum<1024>(a, sm);
+  b = block_sum<1024>(b, sm);
+  if (threadIdx.x != 0) return;
+  const int k = st->k + 1;
+  const int pk = st->tr[k - 1] > (double)st->nocc ? 1 : 0;
+  record_and_test(st, pk, sqrt(a), b, st->tr[k - 1]);
+  // the loop stops after this round's truncation (the kernels below still run)
+  if (use_cond && st->done) cudaGraphSetConditional(cond, 0);
+}
+
+// ---- truncation and the next iterate ------------------------------------------------------------
+__global__ void set_kept_bits_kernel(const DevState* st, Pairs P, const uint8_t* skeep, int W, uint32_t* bits) {
+  if (st && !st->iter_active) return;
+  const int nnz = *P.nnz;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += gridDim.x * blockDim.x) {
+    if (!skeep[q]) continue;
+    const int I = P.row[q], J = P.col[q];
+    atomicOr(&bits[(int64_t)I * W + (J >> 5)], 1u << (J & 31));
+    atomicOr(&bits[(int64_t)J * W + (I >> 5)], 1u << (I & 31));
+  }
+}
+
+// kept upper block q -> row I at the rank of J, its transpose -> row J at the rank of I
+__global__ void __launch_bounds__(NT)
+fill_next_kernel(const DevState* st, Pairs P, const uint8_t* skeep, const float* svals, Mat Y, int W) {
+  if (st && !st->iter_active) return;
+  const int nnz = *P.nnz;
+  for (int q = blockIdx.x; q < nnz; q += gridDim.x) {
+    if (!skeep[q]) continue;
+    const int I = P.row[q], J = P.col[q];
+    const int pij = find_block(Y, W, I, J);
+    const int pji = find_block(Y, W, J, I);
+    if (threadIdx.x == 0) {
+      Y.ci[pij] = J;
+      Y.ci[pji] = I;
+    }
+    const float* src = svals + (int64_t)q * BE;
+    for (int e = threadIdx.x; e < BE; e += NT) {
+      const float v = src[e];
+      Y.vals[(int64_t)pij * BE + e] = v;
+      if (I != J) Y.vals[(int64_t)pji * BE + (e % B) * B + e / B] = v;
+    }
+  }
+}
+
+// dense FP64 output (N x N, leading dimension N) from the iterate the stop test chose
+__global__ void bsr_to_dense_kernel(const DevState* st, Mat X0, Mat X1, int nb, double* D) {
+  const int N = nb * B;
+  const int mode = st->out_mode;
+  const Mat X = st->out_buf ? X1 : X0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)N * N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    double val = 0.0;
+    if (mode == OUT_COPY) {
+      const int W = (nb + 31) / 32;
+      const int p = find_block(X, W, i / B, j / B);
+      if (p >= 0) val = (double)X.vals[(int64_t)p * BE + (i % B) * B + j % B];
+    } else if (mode == OUT_IDENTITY) {
+      val = (i == j) ? 1.0 : 0.0;
+    } else if (mode == OUT_NAN) {
+      val = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    D[e] = val;
+  }
+}
+
+}  // namespace bsr
+}  // namespace sp2
+
+// =================================================================================================
+// Host side: handle and C ABI
+// =================================================================================================
+using namespace sp2;
+using namespace sp2::bsr;
+
+struct sp2_bsr_ctx {
+  int64_t N = 0, nocc = 0;
+  int nb = 0, W = 0;
+  double tau = 0.0;
+  sp2_opts opts{};
+  int device = 0;
+  int64_t cap = 0, cap_s = 0;
+  Mat X[2];
+  Pairs S{}, FP{};
+  uint32_t* sbits = nullptr;
+  float* svals = nullptr;
+  uint8_t* skeep = nullptr;
+  double* spart = nullptr;
+  int* counts = nullptr;
+  uint32_t* fbits = nullptr;
+  int* frank = nullptr;
+  int* fnnz_scratch = nullptr;
+  double *glo = nullptr, *ghi = nullptr;
+  int* gbad = nullptr;
+  DevState* st_dev = nullptr;
+  DevState* st_host = nullptr;
+  int* xnnz_host = nullptr;      // pinned: rp[nb] of the output iterate
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaStream_t last = nullptr;
+  bool ran = false;
+};
+
+#define BSR_TRY(expr)                              \
+  do {                                             \
+    if ((expr) != cudaSuccess) {                   \
+      (void)cudaGetLastError();                    \
+      return SP2_ERR_CUDA;                         \
+    }                                              \
+  } while (0)
+
+static void bsr_free(sp2_bsr_ctx* h) {
+  if (!h) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  for (int p = 0; p < 2; ++p) {
+    cudaFree(h->X[p].rp); cudaFree(h->X[p].ci); cudaFree(h->X[p].vals); cudaFree(h->X[p].bits);
+    cudaFree(h->X[p].rank);
+  }
+  cudaFree(h->S.ptr); cudaFree(h->S.col); cudaFree(h->S.row); cudaFree(h->S.nnz);
+  cudaFree(h->FP.ptr); cudaFree(h->FP.col); cudaFree(h->FP.row); cudaFree(h->FP.nnz);
+  cudaFree(h->sbits); cudaFree(h->svals); cudaFree(h->skeep); cudaFree(h->spart); cudaFree(h->counts);
+  cudaFree(h->fbits); cudaFree(h->frank); cudaFree(h->glo); cudaFree(h->ghi); cudaFree(h->gbad);
+  cudaFree(h->st_dev);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->xnnz_host) cudaFreeHost(h->xnnz_host);
+  if (h->ev[0]) cudaEventDestroy(h->ev[0]);
+  if (h->ev[1]) cudaEventDestroy(h->ev[1]);
+  (void)cudaGetLastError();
+  cudaSetDevice(cur);
+  delete h;
+}
+
+static int grid_persistent() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n * 4;
+}
+
+// One loop round (the body of the WHILE node, or one unrolled round in launch mode 1).
+// The buffers alternate by round: round k reads X[(k-1)&1] and writes X[k&1]; a graph
+// body is fixed, so two bodies are recorded and the loop runs them in pairs.
+static cudaError_t add_round(sp2_bsr_ctx* h, cudaGraph_t g, cudaStream_t s, int parity, int use_cond) {
+  // parity: 0 = X[0] -> X[1], 1 = X[1] -> X[0]
+  Mat Xc = h->X[parity], Xn = h->X[1 - parity];
+  const int nb = h->nb, W = h->W;
+  const double tau2 = h->tau * h->tau;
+  const int up = 1;
+  DevState* st = h->st_dev;
+  int* sn = h->S.nnz;
+  (void)g;
+  // 1. symbolic
+  bsr_sym_kernel<<<nb, 64, 0, s>>>(st, Xc, nb, W, h->sbits);
+  row_counts_kernel<<<nb, 64, 0, s>>>(h->sbits, nb, W, up, h->counts, st);
+  scan_kernel<<<1, 1024, 0, s>>>(h->counts, nb, h->S.ptr, sn, st);
+  fill_pairs_kernel<<<nb, 32, 0, s>>>(h->sbits, nb, W, up, h->S, st);
+  // 2. numeric + 3. stop test
+  bsr_numeric_kernel<<<grid_persistent(), NT, 0, s>>>(st, Xc, W, h->S, h->svals, h->skeep, h->spart, tau2);
+  bsr_finalize_kernel<<<1, 1024, 0, s>>>(st, h->spart, sn, h->cond, use_cond);
+  // 4. truncation -> next iterate
+  clear_words_kernel<<<256, 256, 0, s>>>(Xn.bits, (int64_t)nb * W, st);
+  set_kept_bits_kernel<<<grid_persistent(), 256, 0, s>>>(st, h->S, h->skeep, W, Xn.bits);
+  rank_kernel<<<nb, 32, 0, s>>>(Xn.bits, nb, W, Xn.rank, st);
+  row_counts_kernel<<<nb, 64, 0, s>>>(Xn.bits, nb, W, 0, h->counts, st);
+  scan_kernel<<<1, 1024, 0, s>>>(h->counts, nb, Xn.rp, nullptr, st);
+  fill_next_kernel<<<grid_persistent(), NT, 0, s>>>(st, h->S, h->skeep, h->svals, Xn, W);
+  return cudaGetLastError();
+}
+
+static sp2_status build_graph(sp2_bsr_ctx* h) {
+  // The loop body holds two rounds (X[0] -> X[1] -> X[0]); it is recorded by stream
+  // capture into the WHILE node's body graph.
+  BSR_TRY(cudaGraphCreate(&h->graph, 0));
+  BSR_TRY(cudaGraphConditionalHandleCreate(&h->cond, h->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = h->cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  BSR_TRY(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  (void)grid_persistent();   // device query before capture
+  cudaStream_t cs;
+  BSR_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    add_round(h, body, cs, 0, 1);
+    add_round(h, body, cs, 1, 1);
+    cudaGraph_t out = body;
+    e = cudaStreamEndCapture(cs, &out);
+  }
+  cudaStreamDestroy(cs);
+  BSR_TRY(e);
+  BSR_TRY(cudaGraphInstantiate(&h->exec, h->graph, 0));
+  return SP2_OK;
+}
+
+extern "C" sp2_status sp2_create_bsr(int64_t N, int64_t n_occ, double tau, const sp2_opts* opts, sp2_bsr* out) {
+  if (!out) return SP2_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (N < B || N % B != 0 || N / B > MAX_NB || n_occ < 0 || n_occ > N || !(tau >= 0.0)) return SP2_ERR_INVALID_ARG;
+  sp2_opts o;
+  sp2_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.max_iter < 1 || o.max_iter > SP2_MAX_ITER || !(o.qtilde > 0.0) || (o.guard != 0 && o.guard != 1) ||
+      (o.launch_mode != 0 && o.launch_mode != 1))
+    return SP2_ERR_INVALID_ARG;
+  sp2_bsr_ctx* h = new (std::nothrow) sp2_bsr_ctx();
+  if (!h) return SP2_ERR_NOMEM;
+  h->N = N; h->nocc = n_occ; h->tau = tau; h->opts = o;
+  h->nb = (int)(N / B);
+  h->W = (h->nb + 31) / 32;
+  h->cap = (int64_t)h->nb * h->nb;
+  h->cap_s = (int64_t)h->nb * (h->nb + 1) / 2;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return SP2_ERR_CUDA; }
+  const int nb = h->nb, W = h->W;
+  bool ok = true;
+  for (int p = 0; p < 2 && ok; ++p) {
+    ok = cudaMalloc(&h->X[p].rp, sizeof(int) * (nb + 1)) == cudaSuccess &&
+         cudaMalloc(&h->X[p].ci, sizeof(int) * h->cap) == cudaSuccess &&
+         cudaMalloc(&h->X[p].vals, sizeof(float) * BE * h->cap) == cudaSuccess &&
+         cudaMalloc(&h->X[p].bits, sizeof(uint32_t) * nb * W) == cudaSuccess &&
+         cudaMalloc(&h->X[p].rank, sizeof(int) * nb * W) == cudaSuccess;
+  }
+  ok = ok && cudaMalloc(&h->S.ptr, sizeof(int) * (nb + 1)) == cudaSuccess &&
+       cudaMalloc(&h->S.col, sizeof(int) * h->cap_s) == cudaSuccess &&
+       cudaMalloc(&h->S.row, sizeof(int) * h->cap_s) == cudaSuccess &&
+       cudaMalloc(&h->S.nnz, sizeof(int)) == cudaSuccess &&
+       cudaMalloc(&h->FP.ptr, sizeof(int) * (nb + 1)) == cudaSuccess &&
+       cudaMalloc(&h->FP.col, sizeof(int) * h->cap_s) == cudaSuccess &&
+       cudaMalloc(&h->FP.row, sizeof(int) * h->cap_s) == cudaSuccess &&
+       cudaMalloc(&h->FP.nnz, sizeof(int)) == cudaSuccess &&
+       cudaMalloc(&h->sbits, sizeof(uint32_t) * nb * W) == cudaSuccess &&
+       cudaMalloc(&h->svals, sizeof(float) * BE * h->cap_s) == cudaSuccess &&
+       cudaMalloc(&h->skeep, h->cap_s) == cudaSuccess &&
+       cudaMalloc(&h->spart, sizeof(double) * 2 * h->cap_s) == cudaSuccess &&
+       cudaMalloc(&h->counts, sizeof(int) * nb) == cudaSuccess &&
+       cudaMalloc(&h->fbits, sizeof(uint32_t) * nb * W) == cudaSuccess &&
+       cudaMalloc(&h->frank, sizeof(int) * nb * W) == cudaSuccess &&
+       cudaMalloc(&h->glo, sizeof(double) * nb) == cudaSuccess &&
+       cudaMalloc(&h->ghi, sizeof(double) * nb) == cudaSuccess &&
+       cudaMalloc(&h->gbad, sizeof(int) * nb) == cudaSuccess &&
+       cudaMalloc(&h->st_dev, sizeof(DevState)) == cudaSuccess &&
+       cudaMallocHost(&h->st_host, sizeof(DevState)) == cudaSuccess &&
+       cudaMallocHost(&h->xnnz_host, sizeof(int)) == cudaSuccess &&
+       cudaEventCreate(&h->ev[0]) == cudaSuccess && cudaEventCreate(&h->ev[1]) == cudaSuccess;
+  if (!ok) { (void)cudaGetLastError(); bsr_free(h); return SP2_ERR_NOMEM; }
+  DevState init;
+  std::memset(&init, 0, sizeof(init));
+  init.N = (int32_t)N; init.ld = (int32_t)N; init.nocc = (int32_t)n_occ;
+  init.max_iter = o.max_iter; init.guard = o.guard; init.qtilde = o.qtilde; init.round_fp32 = 1;
+  *h->st_host = init;
+  *h->xnnz_host = 0;
+  if (cudaMemcpy(h->st_dev, &init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess) {
+    (void)cudaGetLastError(); bsr_free(h); return SP2_ERR_CUDA;
+  }
+  sp2_status s = o.launch_mode == 0 ? build_graph(h) : SP2_OK;
+  if (s == SP2_OK && cudaDeviceSynchronize() != cudaSuccess) { (void)cudaGetLastError(); s = SP2_ERR_CUDA; }
+  if (s != SP2_OK) { bsr_free(h); return s; }
+  *out = h;
+  return SP2_OK;
+}
+
+extern "C" void sp2_destroy_bsr(sp2_bsr h) { bsr_free(h); }
+
+extern "C" sp2_status sp2_run_bsr(sp2_bsr h, const int32_t* row_ptr_dev, const int32_t* col_idx_dev,
+                                  const double* vals_dev, int64_t nnzb, double* D_dev, void* stream) {
+  if (!h || !row_ptr_dev || !col_idx_dev || !vals_dev || nnzb < h->nb || nnzb > h->cap) return SP2_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = h->nb, W = h->W;
+  DevState* st = h->st_dev;
+  const double tau2 = h->tau * h->tau;
+  // bounds, special cases, Tr[X_0]
+  bsr_gersh_kernel<<<nb, B, 0, s>>>(row_ptr_dev, col_idx_dev, vals_dev, nb, h->glo, h->ghi, h->gbad);
+  bsr_init_kernel<<<1, kIT, 0, s>>>(st, row_ptr_dev, col_idx_dev, vals_dev, nb, h->glo, h->ghi, h->gbad);
+  // X_0 on F's upper pattern, truncated into X[0]
+  BSR_TRY(cudaMemsetAsync(h->fbits, 0, sizeof(uint32_t) * nb * W, s));
+  csr_to_bits_kernel<<<nb, 64, 0, s>>>(row_ptr_dev, col_idx_dev, nb, W, h->fbits);
+  rank_kernel<<<nb, 32, 0, s>>>(h->fbits, nb, W, h->frank, nullptr);
+  row_counts_kernel<<<nb, 64, 0, s>>>(h->fbits, nb, W, 1, h->counts, nullptr);
+  scan_kernel<<<1, 1024, 0, s>>>(h->counts, nb, h->FP.ptr, h->FP.nnz, nullptr);
+  fill_pairs_kernel<<<nb, 32, 0, s>>>(h->fbits, nb, W, 1, h->FP, nullptr);
+  bsr_scale_pairs_kernel<<<grid_persistent(), NT, 0, s>>>(st, row_ptr_dev, h->fbits, h->frank, vals_dev, W, h->FP,
+                                                           h->svals, h->skeep, tau2);
+  Mat X0 = h->X[0];
+  BSR_TRY(cudaMemsetAsync(X0.bits, 0, sizeof(uint32_t) * nb * W, s));
+  set_kept_bits_kernel<<<grid_persistent(), 256, 0, s>>>(nullptr, h->FP, h->skeep, W, X0.bits);
+  rank_kernel<<<nb, 32, 0, s>>>(X0.bits, nb, W, X0.rank, nullptr);
+  row_counts_kernel<<<nb, 64, 0, s>>>(X0.bits, nb, W, 0, h->counts, nullptr);
+  scan_kernel<<<1, 1024, 0, s>>>(h->counts, nb, X0.rp, nullptr, nullptr);
+  fill_next_kernel<<<grid_persistent(), NT, 0, s>>>(nullptr, h->FP, h->skeep, h->svals, X0, W);
+  BSR_TRY(cudaGetLastError());
+  // the loop: rounds in pairs (X[0] -> X[1] -> X[0]) until the device-side stop
+  BSR_TRY(cudaEventRecord(h->ev[0], s));
+  if (h->opts.launch_mode == 0) {
+    BSR_TRY(cudaGraphLaunch(h->exec, s));
+  } else {
+    for (int it = 0; it <= h->opts.max_iter + 1; it += 2) {
+      BSR_TRY(add_round(h, nullptr, s, 0, 0));
+      BSR_TRY(add_round(h, nullptr, s, 1, 0));
+    }
+  }
+  BSR_TRY(cudaEventRecord(h->ev[1], s));
+  if (D_dev) {
+    bsr_to_dense_kernel<<<grid_persistent() * 2, 256, 0, s>>>(st, h->X[0], h->X[1], nb, D_dev);
+    BSR_TRY(cudaGetLastError());
+  }
+  BSR_TRY(cudaMemcpyAsync(h->st_host, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  h->last = s;
+  h->ran = true;
+  return SP2_OK;
+}
+
+extern "C" sp2_status sp2_get_info_bsr(sp2_bsr h, sp2_info* out, int64_t* nnzb_out) {
+  if (!h || !out) return SP2_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  if (h->ran) BSR_TRY(cudaStreamSynchronize(h->last));
+  const DevState* s = h->st_host;
+  out->status = h->ran ? s->status : SP2_OK;
+  out->n_iter = s->n_out;
+  out->stop_reason = s->reason;
+  out->hist_len = s->hist_len;
+  out->lambda_min = s->lmin;
+  out->lambda_max = s->lmax;
+  float ms = 0.f;
+  if (h->ran && cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) == cudaSuccess) out->loop_ms = ms;
+  (void)cudaGetLastError();
+  out->v = s->v;
+  out->trace = s->tr;
+  out->p = s->p;
+  if (nnzb_out) {
+    int nz = 0;
+    if (h->ran) {
+      if (cudaMemcpy(&nz, h->X[s->out_buf].rp + h->nb, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return SP2_ERR_CUDA;
+      }
+    }
+    *nnzb_out = nz;
+  }
+  return SP2_OK;
+}
+
+// ---- test hooks: the index work on its own ----------------------------------------------------
+namespace sp2 {
+namespace bsr {
+__global__ void test_keep_kernel(const float* dense, int nb, double tau2, uint8_t* keep) {
+  __shared__ float blk[B * (B + 1)];
+  const int I = blockIdx.x / nb, J = blockIdx.x % nb;
+  const int N = nb * B;
+  for (int e = threadIdx.x; e < BE; e += blockDim.x)
+    blk[(e / B) * (B + 1) + e % B] = dense[(int64_t)(I * B + e / B) * N + J * B + e % B];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const double n2 = block_norm2_fixed(blk);
+    if (threadIdx.x == 0) keep[blockIdx.x] = (I == J || n2 >= tau2) ? 1 : 0;
+  }
+}
+}  // namespace bsr
+}  // namespace sp2
+
+#include <vector>
+
+#include "../../include/sp2_testing.h"
+
+extern "C" int32_t sp2_test_bsr_keep(const float* dense_dev, int64_t N, double tau, uint8_t* keep_dev,
+                                     void* stream) {
+  if (!dense_dev || !keep_dev || N < B || N % B || N / B > MAX_NB || !(tau >= 0.0)) return SP2_ERR_INVALID_ARG;
+  const int nb = (int)(N / B);
+  cudaStream_t s = (cudaStream_t)stream;
+  test_keep_kernel<<<nb * nb, 64, 0, s>>>(dense_dev, nb, tau * tau, keep_dev);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SP2_ERR_CUDA;
+  }
+  return SP2_OK;
+}
+
+extern "C" int32_t sp2_test_bsr_square_pattern(const uint8_t* mask_host, int32_t nb, uint8_t* upper_host) {
+  if (!mask_host || !upper_host || nb < 1 || nb > MAX_NB) return SP2_ERR_INVALID_ARG;
+  const int W = (nb + 31) / 32;
+  std::vector<int> rp(nb + 1, 0), ci;
+  for (int I = 0; I < nb; ++I) {
+    for (int J = 0; J < nb; ++J)
+      if (mask_host[(int64_t)I * nb + J]) ci.push_back(J);
+    rp[I + 1] = (int)ci.size();
+  }
+  const int64_t cap_s = (int64_t)nb * (nb + 1) / 2;
+  Mat X{};
+  Pairs P{};
+  uint32_t* sbits = nullptr;
+  int* counts = nullptr;
+  DevState* st = nullptr;
+  bool ok = cudaMalloc(&X.rp, sizeof(int) * (nb + 1)) == cudaSuccess &&
+            cudaMalloc(&X.ci, sizeof(int) * (ci.size() + 1)) == cudaSuccess &&
+            cudaMalloc(&X.bits, sizeof(uint32_t) * nb * W) == cudaSuccess &&
+            cudaMalloc(&X.rank, sizeof(int) * nb * W) == cudaSuccess &&
+            cudaMalloc(&P.ptr, sizeof(int) * (nb + 1)) == cudaSuccess &&
+            cudaMalloc(&P.col, sizeof(int) * cap_s) == cudaSuccess &&
+            cudaMalloc(&P.row, sizeof(int) * cap_s) == cudaSuccess && cudaMalloc(&P.nnz, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&sbits, sizeof(uint32_t) * nb * W) == cudaSuccess &&
+            cudaMalloc(&counts, sizeof(int) * nb) == cudaSuccess && cudaMalloc(&st, sizeof(DevState)) == cudaSuccess;
+  int nnz = 0;
+  std::vector<int> prow, pcol;
+  if (ok) {
+    DevState d;
+    std::memset(&d, 0, sizeof(d));
+    ok = cudaMemcpy(st, &d, sizeof(d), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(X.rp, rp.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+         (ci.empty() || cudaMemcpy(X.ci, ci.data(), sizeof(int) * ci.size(), cudaMemcpyHostToDevice) == cudaSuccess) &&
+         cudaMemset(X.bits, 0, sizeof(uint32_t) * nb * W) == cudaSuccess;
+  }
+  if (ok) {
+    csr_to_bits_kernel<<<nb, 64>>>(X.rp, X.ci, nb, W, X.bits);
+    rank_kernel<<<nb, 32>>>(X.bits, nb, W, X.rank, nullptr);
+    bsr_sym_kernel<<<nb, 64>>>(st, X, nb, W, sbits);
+    row_counts_kernel<<<nb, 64>>>(sbits, nb, W, 1, counts, nullptr);
+    scan_kernel<<<1, 1024>>>(counts, nb, P.ptr, P.nnz, nullptr);
+    fill_pairs_kernel<<<nb, 32>>>(sbits, nb, W, 1, P, nullptr);
+    ok = cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+         cudaMemcpy(&nnz, P.nnz, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+  }
+  if (ok) {
+    prow.resize(nnz > 0 ? nnz : 1);
+    pcol.resize(nnz > 0 ? nnz : 1);
+    ok = nnz == 0 || (cudaMemcpy(prow.data(), P.row, sizeof(int) * nnz, cudaMemcpyDeviceToHost) == cudaSuccess &&
+                      cudaMemcpy(pcol.data(), P.col, sizeof(int) * nnz, cudaMemcpyDeviceToHost) == cudaSuccess);
+  }
+  if (ok) {
+    std::memset(upper_host, 0, (size_t)nb * nb);
+    for (int q = 0; q < nnz; ++q) upper_host[(int64_t)prow[q] * nb + pcol[q]] = 1;
+  }
+  cudaFree(X.rp); cudaFree(X.ci); cudaFree(X.bits); cudaFree(X.rank);
+  cudaFree(P.ptr); cudaFree(P.col); cudaFree(P.row); cudaFree(P.nnz);
+  cudaFree(sbits); cudaFree(counts); cudaFree(st);
+  (void)cudaGetLastError();
+  return ok ? SP2_OK : SP2_ERR_CUDA;
+}

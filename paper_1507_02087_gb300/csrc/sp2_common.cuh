@@ -46,6 +46,8 @@ struct DevState {
   int32_t hist_len;
   int32_t dk;          // derivative steps completed (mixed path correction)
   int32_t round_fp32;  // 1: X_0 is rounded to FP32 (mixed path)
+  int32_t iter_active; // block-sparse path: the current loop round squares (set at its start)
+  int32_t _pad1;
   // history
   double v[SP2_MAX_ITER + 2];
   double tr[SP2_MAX_ITER + 2];

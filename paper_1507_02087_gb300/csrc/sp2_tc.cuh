@@ -66,8 +66,9 @@ enum SlotRule : int32_t {
                         // maps back with p_n (an alternating pair, §4)
 };
 
-// One problem of a batch (device memory; the tensor maps are read by TMA from here).
-struct alignas(64) Instance {
+// One problem of a batch (device memory; the tensor maps are read by TMA from here and
+// keep the alignment CUtensorMap requires).
+struct Instance {
   CUtensorMap mapA;     // box 32 x 128 (A operand)
   CUtensorMap mapB;     // box 32 x 128 (B operand)
   __nv_bfloat16* arena;

@@ -174,20 +174,21 @@ def householder_n32768(device="cuda", want_exact=True) -> DenseCase:
 
 @dataclasses.dataclass
 class TightBinding:
-    """Simple-cubic L^3 lattice, one orbital per site, periodic boundaries.
-    Site index s = x + L y + L^2 z.  Onsite +delta where x+y+z is even, -delta
-    where odd, plus Gaussian disorder; nearest-neighbour hopping -t."""
+    """Simple-cubic Lx x Ly x Lz lattice, one orbital per site, periodic boundaries.
+    Site index s = x + Lx y + Lx Ly z.  Onsite +delta where x+y+z is even, -delta where
+    odd, plus Gaussian disorder sigma; nearest-neighbour hopping -t.  With Lx = 32 the
+    32 x 32 blocks of F are the x-lines of the lattice."""
 
-    L: int
+    dims: tuple
     onsite: np.ndarray        # length N
-    rows: np.ndarray          # COO of the off-diagonal hopping (both directions)
+    rows: np.ndarray          # COO of the off-diagonal hopping (both directions, no duplicates)
     cols: np.ndarray
     hop: float
     nocc: int
 
     @property
     def N(self) -> int:
-        return self.L ** 3
+        return int(np.prod(self.dims))
 
     def dense(self, device="cpu", dtype=torch.float64) -> torch.Tensor:
         F = torch.zeros(self.N, self.N, dtype=dtype, device=device)
@@ -198,27 +199,41 @@ class TightBinding:
         F[r, c] = -self.hop
         return F
 
+    def bsr(self, b: int = 32):
+        """Block-sparse (BSR) form with b x b blocks: int32 row_ptr [N/b + 1], int32
+        col_idx [nnzb] (sorted in each block row), float64 vals [nnzb, b, b]."""
+        if self.N % b:
+            raise ValueError("N must be a multiple of the block size")
+        nb = self.N // b
+        F = self.dense().numpy()
+        blocks = F.reshape(nb, b, nb, b).transpose(0, 2, 1, 3)
+        nz = np.abs(blocks).sum(axis=(2, 3)) > 0
+        np.fill_diagonal(nz, True)
+        row_ptr = np.zeros(nb + 1, dtype=np.int32)
+        row_ptr[1:] = np.cumsum(nz.sum(axis=1))
+        I, J = np.nonzero(nz)
+        return row_ptr, J.astype(np.int32), np.ascontiguousarray(blocks[I, J])
 
-def tight_binding(L: int = 32, delta: float = 1.0, t: float = 0.3, sigma: float = 0.05,
-                  seed: int = 2) -> TightBinding:
+
+def tight_binding(L: int = 32, delta: float = 1.0, t: float = 0.3, sigma: float = 0.05, seed: int = 2,
+                  dims: tuple | None = None) -> TightBinding:
+    """dims = (Lx, Ly, Lz), default (L, L, L); nocc = N/2 (the lower band)."""
+    Lx, Ly, Lz = dims if dims is not None else (L, L, L)
+    N = Lx * Ly * Lz
     g = rng(seed)
-    x, y, z = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
-    x, y, z = x.ravel(order="F"), y.ravel(order="F"), z.ravel(order="F")
-    s = x + L * y + L * L * z
-    order = np.argsort(s)
-    x, y, z = x[order], y[order], z[order]
+    s = np.arange(N)
+    x, y, z = s % Lx, (s // Lx) % Ly, s // (Lx * Ly)
     parity = (x + y + z) % 2
-    onsite = np.where(parity == 0, delta, -delta) + sigma * g.standard_normal(L ** 3)
-    rows, cols = [], []
-    site = lambda a, b, c: (a % L) + L * (b % L) + L * L * (c % L)
-    src = np.arange(L ** 3)
-    for dx, dy, dz in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+    onsite = np.where(parity == 0, delta, -delta) + sigma * g.standard_normal(N)
+    site = lambda a, b_, c: (a % Lx) + Lx * (b_ % Ly) + Lx * Ly * (c % Lz)
+    pairs = set()
+    for dx, dy, dz, Ld in ((1, 0, 0, Lx), (0, 1, 0, Ly), (0, 0, 1, Lz)):
+        if Ld < 2:
+            continue
         dst = site(x + dx, y + dy, z + dz)
-        rows.append(src); cols.append(dst)
-        rows.append(dst); cols.append(src)
-    rows = np.concatenate(rows); cols = np.concatenate(cols)
-    if L <= 2:  # periodic wrap would double-count bonds; merge duplicates
-        key = np.unique(rows * L ** 3 + cols)
-        rows, cols = key // L ** 3, key % L ** 3
-    return TightBinding(L=L, onsite=onsite, rows=rows.astype(np.int64), cols=cols.astype(np.int64),
-                        hop=t, nocc=L ** 3 // 2)
+        for a_, b_ in zip(s.tolist(), dst.tolist()):
+            if a_ != b_:
+                pairs.add((a_, b_))
+                pairs.add((b_, a_))
+    pr = np.array(sorted(pairs), dtype=np.int64).reshape(-1, 2)
+    return TightBinding(dims=(Lx, Ly, Lz), onsite=onsite, rows=pr[:, 0], cols=pr[:, 1], hop=t, nocc=N // 2)

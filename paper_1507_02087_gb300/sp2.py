@@ -84,6 +84,18 @@ def lib() -> ctypes.CDLL:
         L.sp2_get_info_batch.restype = i32
         L.sp2_destroy_batch.argtypes = [vp]
         L.sp2_destroy_batch.restype = None
+        L.sp2_create_bsr.argtypes = [i64, i64, ctypes.c_double, ctypes.POINTER(sp2_opts), ctypes.POINTER(vp)]
+        L.sp2_create_bsr.restype = i32
+        L.sp2_run_bsr.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+        L.sp2_run_bsr.restype = i32
+        L.sp2_get_info_bsr.argtypes = [vp, ctypes.POINTER(sp2_info), ctypes.POINTER(i64)]
+        L.sp2_get_info_bsr.restype = i32
+        L.sp2_destroy_bsr.argtypes = [vp]
+        L.sp2_destroy_bsr.restype = None
+        L.sp2_test_bsr_keep.argtypes = [vp, i64, ctypes.c_double, vp, vp]
+        L.sp2_test_bsr_keep.restype = i32
+        L.sp2_test_bsr_square_pattern.argtypes = [vp, i32, vp]
+        L.sp2_test_bsr_square_pattern.restype = i32
         _lib = L
     return _lib
 
@@ -191,6 +203,53 @@ def sp2_test_tc_gemm(arena, ld: int, nslots: int, a_slot: int, b_slot: int, uppe
 def sp2_destroy(h: int) -> None:
     if h:
         lib().sp2_destroy(h)
+
+
+class BsrPurifier:
+    """Block-sparse F (32 x 32 blocks, BSR) -> D with block truncation tau."""
+
+    def __init__(self, N: int, nocc: int, tau: float, max_iter: int = 200, guard: bool = True,
+                 qtilde: float = 1.8, launch_mode: int | None = None):
+        o = _opts(max_iter, guard, qtilde, 1, 0, False, launch_mode)
+        h = ctypes.c_void_p()
+        _check(lib().sp2_create_bsr(N, nocc, tau, ctypes.byref(o), ctypes.byref(h)), "sp2_create_bsr")
+        self.N, self.nocc, self.tau, self.h = N, nocc, tau, h.value
+
+    def run(self, row_ptr, col_idx, vals, D=None, dense=True, stream=None):
+        """row_ptr/col_idx: CUDA int32 tensors, vals: CUDA float64 [nnzb, 32, 32]."""
+        import torch
+        if dense and D is None:
+            D = torch.empty(self.N, self.N, dtype=torch.float64, device=vals.device)
+        _check(lib().sp2_run_bsr(self.h, row_ptr.data_ptr(), col_idx.data_ptr(), vals.data_ptr(),
+                                 vals.shape[0], D.data_ptr() if D is not None else None, _stream_ptr(stream)),
+               "sp2_run_bsr")
+        return D
+
+    def info(self) -> dict:
+        info = sp2_info()
+        nz = ctypes.c_int64()
+        _check(lib().sp2_get_info_bsr(self.h, ctypes.byref(info), ctypes.byref(nz)), "sp2_get_info_bsr")
+        d = _info_dict(info)
+        d["nnzb"] = nz.value
+        return d
+
+    def close(self):
+        if self.h:
+            lib().sp2_destroy_bsr(self.h)
+        self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.h:
+                self.close()
+        except Exception:
+            pass
 
 
 class BatchPurifier:
