@@ -68,8 +68,8 @@ def tb_case(dims):
     return tb, (torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda(), torch.from_numpy(vals).cuda())
 
 
-@pytest.mark.parametrize("dims,tau,tol", [((32, 8, 4), 0.0, 2e-6), ((32, 8, 8), 1e-6, 5e-6),
-                                          ((32, 16, 8), 1e-4, 5e-5)])
+@pytest.mark.parametrize("dims,tau,tol", [((32, 8, 4), 0.0, 3e-6), ((32, 8, 8), 1e-6, 4e-6),
+                                          ((32, 16, 8), 1e-4, 4e-6)])
 def test_bsr_sp2_against_oracle(sp2mod, dims, tau, tol):
     tb, (rp, ci, vals) = tb_case(dims)
     F = tb.dense().numpy()
@@ -79,7 +79,10 @@ def test_bsr_sp2_against_oracle(sp2mod, dims, tau, tol):
         info = P.info()
     assert info["status"] == 0
     assert info["stop_reason"] in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
-    assert abs(info["n_iter"] - ref.n) <= 1
+    # FP32 blocks reach their rounding floor at a different square than FP64: earlier,
+    # or a few squares later when the trace-chosen polynomial repeats at the floor before
+    # the (alternation-requiring) order test can fire
+    assert ref.n - 3 <= info["n_iter"] <= ref.n + 3
     assert info["lambda_min"] == pytest.approx(ref.lmin, rel=1e-12)
     assert info["lambda_max"] == pytest.approx(ref.lmax, rel=1e-12)
     err = o.rel_error(D.cpu().numpy(), ref.D, tb.nocc)
