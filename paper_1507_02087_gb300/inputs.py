@@ -205,6 +205,35 @@ class TightBinding:
         if self.N % b:
             raise ValueError("N must be a multiple of the block size")
         nb = self.N // b
+        Lx, Ly, Lz = self.dims
+        if Lx == b:
+            # blocks are x-lines: the diagonal block holds the onsite terms and the hopping
+            # along the line, the off-diagonal blocks the hopping to the neighbouring lines
+            # (-t on the diagonal of the block); no dense matrix is formed
+            cols, vals = [], []
+            ring = np.zeros((b, b))
+            for x in range(b):
+                for dx in (1, -1):
+                    if Lx >= 2 and (x + dx) % Lx != x:
+                        ring[x, (x + dx) % Lx] = -self.hop
+            row_ptr = np.zeros(nb + 1, dtype=np.int32)
+            for I in range(nb):
+                y, z = I % Ly, I // Ly
+                nbrs = set()
+                for yy, zz in (((y + 1) % Ly, z), ((y - 1) % Ly, z), (y, (z + 1) % Lz), (y, (z - 1) % Lz)):
+                    J = yy + Ly * zz
+                    if J != I:
+                        nbrs.add(J)
+                row = sorted(nbrs | {I})
+                for J in row:
+                    if J == I:
+                        blk = ring + np.diag(self.onsite[I * b:(I + 1) * b])
+                    else:
+                        blk = -self.hop * np.eye(b)
+                    cols.append(J)
+                    vals.append(blk)
+                row_ptr[I + 1] = len(cols)
+            return row_ptr, np.array(cols, dtype=np.int32), np.ascontiguousarray(np.stack(vals))
         F = self.dense().numpy()
         blocks = F.reshape(nb, b, nb, b).transpose(0, 2, 1, 3)
         nz = np.abs(blocks).sum(axis=(2, 3)) > 0
