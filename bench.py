@@ -56,7 +56,10 @@ def parse():
     ap.add_argument("--N", type=int, default=N_DEFAULT)
     ap.add_argument("--nocc", type=int, default=None)
     ap.add_argument("--gap", type=float, default=GAP_DEFAULT)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--input", choices=["qr", "householder"], default="qr",
+                    help="eigenvectors: QR of a seeded Gaussian (seed 0) or 64 seeded Householder reflectors "
+                         "(seed 3, the N=32768 workload)")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="0 skips the host-buffer measurement")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed runs of the FP64 path (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
@@ -343,7 +346,10 @@ def main():
     dev = torch.device("cuda", local)
     nocc = a.nocc if a.nocc is not None else a.N // 2
     N = a.N
-    case = inputs.dense_gapped(N, nocc, gap=a.gap, seed=0, device=dev, want_exact=True)
+    if a.input == "householder":
+        case = inputs.householder_gapped(N, nocc, gap=a.gap, n_reflectors=64, seed=3, device=dev)
+    else:
+        case = inputs.dense_gapped(N, nocc, gap=a.gap, seed=0, device=dev, want_exact=True)
     F = case.F.contiguous()
     D_exact = case.D_exact
     D = torch.empty_like(F)
@@ -444,19 +450,21 @@ def main():
                 "speedup_mixed_vs_fp64": statistics.mean(tms) / ms}
 
     # end to end through the public API with host buffers (copies inside the timed region)
-    F_h = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
-    F_h.copy_(F.cpu())
-    D_h = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
-    F_hn, D_hn = F_h.numpy(), D_h.numpy()
-    P.run_host(F_hn, D_hn, stream)          # allocates the staging buffers once
-    e2e_ms = []
-    for _ in range(max(1, a.e2e_steps)):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        P.run_host(F_hn, D_hn, stream)
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e = {"value": max_over_ranks(statistics.mean(e2e_ms), ws), "unit": "ms",
-           "h2d_bytes_per_step": N * N * 8, "d2h_bytes_per_step": N * N * 8}
+    e2e = None
+    if a.e2e_steps > 0:
+        F_h = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
+        F_h.copy_(F.cpu())
+        D_h = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
+        F_hn, D_hn = F_h.numpy(), D_h.numpy()
+        P.run_host(F_hn, D_hn, stream)          # allocates the staging buffers once
+        e2e_ms = []
+        for _ in range(a.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            P.run_host(F_hn, D_hn, stream)
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e = {"value": max_over_ranks(statistics.mean(e2e_ms), ws), "unit": "ms",
+               "h2d_bytes_per_step": N * N * 8, "d2h_bytes_per_step": N * N * 8}
 
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
@@ -472,7 +480,9 @@ def main():
                 "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16x6->f32 (mixed), f64 reductions" if mixed else "f64",
                 "data": "synthetic",
-                "config": {"workload": workload_name(N, nocc, a.gap), "N": N, "nocc": nocc, "gap": a.gap,
+                "config": {"workload": workload_name(N, nocc, a.gap) if a.input == "qr" else
+                           f"dense N={N} nocc={nocc} gap={a.gap:g}, Q = 64 Householder reflectors (seed 3)",
+                           "N": N, "nocc": nocc, "gap": a.gap,
                            "precision": a.precision,
                            "parallelism": "replicas" if ws > 1 else "1 GPU",
                            "l2": "no flush: F 512 MiB and the streamed iterates exceed the 129 MB L2"},

@@ -85,6 +85,12 @@ typedef struct {
                            each returning at once after the device-side stop (same results and
                            work plus a few microseconds per idle launch; for tools that cannot
                            follow conditional graph nodes, such as kernel profilers) */
+  int32_t history;      /* SP2_PREC_MIXED with corrections: 0 = automatic (default), 1 = keep every
+                           iterate X_i in HBM for the derivative pass ((max_iter + 8) slots of
+                           6 ld^2 bytes), 2 = keep 11 slots and recompute X_i during the derivative
+                           pass (one more square per derivative step, bit-identical result);
+                           automatic keeps every iterate when that fits in 60% of free memory */
+  int32_t reserved;     /* must be 0 */
 } sp2_opts;
 
 #define SP2_MAX_ITER 512

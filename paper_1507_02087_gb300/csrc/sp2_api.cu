@@ -43,6 +43,8 @@ extern "C" void sp2_default_opts(sp2_opts* o) {
   o->refine_steps = 2;
   o->refine_fp64 = 0;
   o->launch_mode = 0;
+  o->history = 0;
+  o->reserved = 0;
 }
 
 extern "C" const char* sp2_status_string(int32_t s) {
@@ -62,7 +64,8 @@ extern "C" const char* sp2_status_string(int32_t s) {
 static bool opts_valid(const sp2_opts& o) {
   return o.max_iter >= 1 && o.max_iter <= SP2_MAX_ITER && o.qtilde > 0.0 && (o.guard == 0 || o.guard == 1) &&
          o.corrections >= 0 && o.corrections <= 1 && (o.refine_steps == 0 || o.refine_steps == 2) &&
-         (o.refine_fp64 == 0 || o.refine_fp64 == 1) && (o.launch_mode == 0 || o.launch_mode == 1);
+         (o.refine_fp64 == 0 || o.refine_fp64 == 1) && (o.launch_mode == 0 || o.launch_mode == 1) &&
+         o.history >= 0 && o.history <= 2 && o.reserved == 0;
 }
 
 static DevState initial_state(int64_t N, int64_t nocc, const sp2_opts& o, int ld, int round_fp32) {
@@ -188,6 +191,19 @@ struct MixedEngine {
     arenas.assign(count, nullptr);
     parts.assign(count, nullptr);
     const int H = o.max_iter + 2;
+    // Keep every iterate (full history) or recompute them in the derivative pass; without
+    // the correction no pass reads the history, so the rings suffice.
+    int lowmem = (o.history == 2 || o.corrections == 0) ? 1 : 0;
+    if (o.history == 0 && o.corrections > 0) {
+      double full = 0.0;
+      for (int k = 0; k < count; ++k) {
+        const double ld = (double)((N[k] + LD_ALIGN - 1) / LD_ALIGN * LD_ALIGN);
+        full += (double)(H + 6) * NP * ld * ld * 2.0;
+      }
+      size_t free_b = 0, total_b = 0;
+      if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { (void)cudaGetLastError(); free_b = 0; }
+      lowmem = full > 0.6 * (double)free_b ? 1 : 0;
+    }
     int off_u = 0, off_f = 0;
     for (int k = 0; k < count; ++k) {
       Instance& I = inst_host[k];
@@ -195,11 +211,15 @@ struct MixedEngine {
       const int ld = (int)((N[k] + LD_ALIGN - 1) / LD_ALIGN * LD_ALIGN);
       I.ld = ld;
       I.hist0 = 0;
-      I.dx0 = H;
-      I.m_slot = H + 2;
-      I.f_slot = H + 3;
-      I.r0_slot = H + 4;
-      const int nslots = H + 6;
+      I.lowmem = lowmem;
+      // full history: X_0..X_{H-1}, dX x2, M, F, refinement x2; low memory: X_0, two
+      // forward slots, two recompute slots, then the same five
+      const int base = lowmem ? 5 : H;
+      I.dx0 = base;
+      I.m_slot = base + 2;
+      I.f_slot = base + 3;
+      I.r0_slot = base + 4;
+      const int nslots = base + 6;
       I.slot_elems = (int64_t)NP * ld * ld;
       I.st = st_dev + k;
       I.tile_off_upper = off_u;
@@ -259,7 +279,11 @@ struct MixedEngine {
       s = add_while(graph, &n_df, 1, &cond2, &n_der, &dbody);
       if (s != SP2_OK) return s;
       SP2_TRY(sp2::tc_add_node(dbody, nullptr, 0, job(MODE_DERIV_STEP, 1, SLOTS_DERIV, 2), &n_dsq));
-      SP2_TRY(sp2::batch_add_deriv_tail(dbody, &n_dsq, inst_dev, count, cond2));
+      cudaGraphNode_t n_tail = n_dsq;
+      if (inst_host[0].lowmem) {   // low memory: X_j again, next to its derivative step
+        SP2_TRY(sp2::tc_add_node(dbody, &n_dsq, 1, job(MODE_DERIV_STEP, 1, SLOTS_RECOMPUTE), &n_tail));
+      }
+      SP2_TRY(sp2::batch_add_deriv_tail(dbody, &n_tail, inst_dev, count, cond2));
       last = n_der;
     }
     if (opts.refine_steps > 0 && !opts.refine_fp64) {
@@ -290,6 +314,7 @@ struct MixedEngine {
       SP2_TRY(sp2::tc_launch(job(MODE_DF_COMBINE, 1, SLOTS_CORR_DF), s));
       for (int it = 0; it <= opts.max_iter + 1; ++it) {
         SP2_TRY(sp2::tc_launch(job(MODE_DERIV_STEP, 1, SLOTS_DERIV, 2), s));
+        if (inst_host[0].lowmem) SP2_TRY(sp2::tc_launch(job(MODE_DERIV_STEP, 1, SLOTS_RECOMPUTE), s));
         SP2_TRY(sp2::batch_launch_deriv_tail(inst_dev, count, s));
       }
     }

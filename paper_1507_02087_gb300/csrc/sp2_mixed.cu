@@ -148,7 +148,7 @@ __global__ void batch_scale_split_kernel(const Instance* inst, int count, int sb
   const int N = st->N, ld = In.ld;
   const double lmax = st->lmax, w = st->lmax - st->lmin;
   const int64_t plane = (int64_t)ld * ld;
-  __nv_bfloat16* X = In.arena + (int64_t)In.hist0 * In.slot_elems;
+  __nv_bfloat16* X = In.arena + (int64_t)tc::xslot(In.lowmem, In.hist0, 0) * In.slot_elems;
   __nv_bfloat16* Fp = In.arena + (int64_t)In.f_slot * In.slot_elems;
   const double* F = ptrs.F[i];
   const int64_t total = (int64_t)N * N;
@@ -243,7 +243,7 @@ __global__ void batch_corrected_to_pieces_kernel(const Instance* inst, int count
   const int N = st->N, ld = In.ld;
   const int64_t plane = (int64_t)ld * ld;
   const int n = st->n_out;
-  const __nv_bfloat16* X = In.arena + (int64_t)(In.hist0 + n) * In.slot_elems;
+  const __nv_bfloat16* X = In.arena + (int64_t)tc::xslot(In.lowmem, In.hist0, n) * In.slot_elems;
   const __nv_bfloat16* dX = In.arena + (int64_t)(In.dx0 + (n & 1)) * In.slot_elems;
   __nv_bfloat16* R = In.arena + (int64_t)In.r0_slot * In.slot_elems;
   const bool corr = use_dx && n > 0 && st->dk == n;
@@ -271,7 +271,8 @@ __global__ void batch_assemble_kernel(const Instance* inst, int count, int sb, i
   const int mode = st->out_mode;
   const int64_t plane = (int64_t)ld * ld;
   const int n = st->n_out;
-  const __nv_bfloat16* X = In.arena + (int64_t)(from_r0 ? In.r0_slot : In.hist0 + n) * In.slot_elems;
+  const __nv_bfloat16* X =
+      In.arena + (int64_t)(from_r0 ? In.r0_slot : tc::xslot(In.lowmem, In.hist0, n)) * In.slot_elems;
   const __nv_bfloat16* dX = In.arena + (int64_t)(In.dx0 + (n & 1)) * In.slot_elems;
   const bool corr = !from_r0 && use_dx && n > 0 && st->dk == n;
   double* D = to_f64_buf ? f64_buf : ptrs.D[i];

@@ -61,10 +61,22 @@ enum SlotRule : int32_t {
   SLOTS_DERIV = 2,      // j = st->dk + 1: (X_{j-1}, dX_{j-1}) + (dX_{j-1}, X_{j-1}) -> dX_j
   SLOTS_CORR_M = 3,     // M = P F with P = X_n:  A = hist0 + n, B = f_slot, out = m_slot
   SLOTS_CORR_DF = 4,    // W = M P:  A = m_slot, B = hist0 + n, in = m_slot, out = dx0
-  SLOTS_REFINE = 5      // purification step s = a_slot[0] on the corrected D: s = 0 maps
+  SLOTS_REFINE = 5,     // purification step s = a_slot[0] on the corrected D: s = 0 maps
                         // r0_slot -> r0_slot + 1 with the polynomial other than p_n, s = 1
                         // maps back with p_n (an alternating pair, §4)
+  SLOTS_RECOMPUTE = 6   // low-memory instances: X_j = p_j(X_{j-1}) again during the
+                        // derivative pass (j = st->dk + 1), into a two-slot ring
 };
+
+// Slot of the forward iterate X_k.  Full history: hist0 + k.  Low memory: X_0 in slot 0,
+// X_k (k >= 1) alternating in slots 1 and 2; the derivative pass recomputes the iterates
+// into slots 3 and 4 (X_0 from slot 0).
+__host__ __device__ __forceinline__ int xslot(int lowmem, int hist0, int k) {
+  return lowmem ? (k == 0 ? 0 : 1 + (k & 1)) : hist0 + k;
+}
+__host__ __device__ __forceinline__ int rslot(int lowmem, int hist0, int j) {
+  return lowmem ? (j == 0 ? 0 : 3 + (j & 1)) : hist0 + j;
+}
 
 // One problem of a batch (device memory; the tensor maps are read by TMA from here and
 // keep the alignment CUtensorMap requires).
@@ -79,6 +91,8 @@ struct Instance {
   int32_t tile_off_upper;   // first global tile index of this instance (upper schedule)
   int32_t tile_off_full;    // first global tile index (full schedule)
   int32_t hist0, dx0, m_slot, f_slot, r0_slot;
+  int32_t lowmem;           // 1: iterates in rings, recomputed in the derivative pass
+  int32_t _pad[3];
 };
 
 struct Job {

@@ -50,15 +50,23 @@ __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
   switch (j.rule) {
     case SLOTS_FORWARD: {
       const int k = st->k;
-      r.a[0] = r.b[0] = r.in = I.hist0 + k;
-      r.out = I.hist0 + k + 1;
+      r.a[0] = r.b[0] = r.in = xslot(I.lowmem, I.hist0, k);
+      r.out = xslot(I.lowmem, I.hist0, k + 1);
       r.pk = st->tr[k] > (double)st->nocc ? 1 : 0;   // Alg. 3 trace test
       r.active = !st->done;
       break;
     }
+    case SLOTS_RECOMPUTE: {
+      const int jj = st->dk + 1;
+      r.a[0] = r.b[0] = r.in = rslot(1, I.hist0, jj - 1);
+      r.out = rslot(1, I.hist0, jj);
+      r.pk = st->p[jj];
+      r.active = I.lowmem && ok_run && jj < st->n_out;
+      break;
+    }
     case SLOTS_DERIV: {
       const int jj = st->dk + 1;
-      const int xs = I.hist0 + jj - 1;
+      const int xs = rslot(I.lowmem, I.hist0, jj - 1);
       const int di = I.dx0 + ((jj - 1) & 1);
       r.a[0] = xs; r.b[0] = di;
       r.a[1] = di; r.b[1] = xs;
@@ -68,12 +76,12 @@ __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
       break;
     }
     case SLOTS_CORR_M: {
-      r.a[0] = I.hist0 + st->n_out; r.b[0] = I.f_slot; r.out = I.m_slot;
+      r.a[0] = xslot(I.lowmem, I.hist0, st->n_out); r.b[0] = I.f_slot; r.out = I.m_slot;
       r.active = ok_run && st->n_out > 0;
       break;
     }
     case SLOTS_CORR_DF: {
-      r.a[0] = I.m_slot; r.b[0] = I.hist0 + st->n_out; r.in = I.m_slot; r.out = I.dx0;
+      r.a[0] = I.m_slot; r.b[0] = xslot(I.lowmem, I.hist0, st->n_out); r.in = I.m_slot; r.out = I.dx0;
       r.active = ok_run && st->n_out > 0;
       break;
     }

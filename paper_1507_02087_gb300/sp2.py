@@ -35,7 +35,8 @@ class SP2Error(RuntimeError):
 class sp2_opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("guard", ctypes.c_int32), ("qtilde", ctypes.c_double),
                 ("corrections", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
-                ("refine_fp64", ctypes.c_int32), ("launch_mode", ctypes.c_int32)]
+                ("refine_fp64", ctypes.c_int32), ("launch_mode", ctypes.c_int32),
+                ("history", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class sp2_info(ctypes.Structure):
@@ -112,18 +113,22 @@ def _stream_ptr(stream) -> int:
     return int(getattr(stream, "cuda_stream", stream))
 
 
-def _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode):
+HISTORY = {"auto": 0, "full": 1, "recompute": 2}
+
+
+def _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history="auto"):
     if launch_mode is None:
         launch_mode = int(os.environ.get("SP2_LAUNCH_MODE", "0"))
     return sp2_opts(max_iter, 1 if guard else 0, qtilde, corrections, refine_steps, 1 if refine_fp64 else 0,
-                    launch_mode)
+                    launch_mode, HISTORY[history], 0)
 
 
 def sp2_create(N: int, nocc: int, precision: str = "fp64", *, max_iter: int = 200, guard: bool = True,
                qtilde: float = 1.8, corrections: int = 1, refine_steps: int = 2,
-               refine_fp64: bool = False, launch_mode: int | None = None) -> int:
-    """launch_mode None reads SP2_LAUNCH_MODE from the environment (default 0, the graph)."""
-    o = _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode)
+               refine_fp64: bool = False, launch_mode: int | None = None, history: str = "auto") -> int:
+    """launch_mode None reads SP2_LAUNCH_MODE from the environment (default 0, the graph).
+    history: "auto", "full" (keep every iterate) or "recompute" (low memory)."""
+    o = _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history)
     h = ctypes.c_void_p()
     _check(lib().sp2_create(N, nocc, PRECISIONS[precision], ctypes.byref(o), ctypes.byref(h)), "sp2_create")
     return h.value
@@ -147,9 +152,9 @@ def sp2_get_info(h: int) -> dict:
 
 def sp2_create_batch(Ns, noccs, precision: str = "mixed", *, max_iter: int = 200, guard: bool = True,
                      qtilde: float = 1.8, corrections: int = 1, refine_steps: int = 2,
-                     refine_fp64: bool = False, launch_mode: int | None = None) -> int:
+                     refine_fp64: bool = False, launch_mode: int | None = None, history: str = "auto") -> int:
     count = len(Ns)
-    o = _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode)
+    o = _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history)
     n_arr = (ctypes.c_int64 * count)(*Ns)
     o_arr = (ctypes.c_int64 * count)(*noccs)
     h = ctypes.c_void_p()

@@ -83,6 +83,19 @@ def test_mixed_options(sp2mod):
     assert errs["corr+tc"] <= TOL_MIXED and errs["corr+fp64"] <= TOL_MIXED
 
 
+def test_recompute_history_is_bit_identical(sp2mod):
+    # low-memory layout: the derivative pass recomputes the iterates instead of reading
+    # them back; the kernels are deterministic, so D must not change by a bit
+    case = inputs.dense_gapped(900, 400, gap=0.02, seed=13)
+    F = case.F.cuda()
+    out = {}
+    for hist in ("full", "recompute"):
+        with sp2mod.Purifier(900, 400, "mixed", history=hist) as P:
+            out[hist] = (P.run(F), P.info()["n_iter"])
+    assert out["full"][1] == out["recompute"][1]
+    assert torch.equal(out["full"][0], out["recompute"][0])
+
+
 def test_mixed_deterministic_and_host_entry(sp2mod):
     case = inputs.dense_gapped(700, 350, gap=0.05, seed=8)
     F = case.F.numpy()
