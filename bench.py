@@ -410,7 +410,9 @@ def main():
         alg = SPLIT_PRODUCTS * N * N * (N + 1)        # six bf16 piece products of an upper-triangle square
         achieved = alg / (kern_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
-        roofline = {"bound": "tensor", "kernel": "tc_gemm_kernel (forward square, MODE_SP2_STEP)",
+        ld = -(-N // 128) * 128
+        kname = "tc_gemm_pair_kernel (256x256 tiles per SM pair" if ld % 256 == 0 else "tc_gemm_kernel (128x128 tiles"
+        roofline = {"bound": "tensor", "kernel": kname + ", forward square, MODE_SP2_STEP)",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "ms_per_launch": kern_ms,
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",

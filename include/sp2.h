@@ -90,7 +90,10 @@ typedef struct {
                            6 ld^2 bytes), 2 = keep 11 slots and recompute X_i during the derivative
                            pass (one more square per derivative step, bit-identical result);
                            automatic keeps every iterate when that fits in 60% of free memory */
-  int32_t reserved;     /* must be 0 */
+  int32_t tile;         /* SP2_PREC_MIXED tensor-core tiles: 0 = automatic (default: 2 when every
+                           problem's ld is a multiple of 256, else 1), 1 = 128 x 128 output tiles,
+                           one per SM, 2 = 256 x 256 tiles, one per pair of SMs (cta_group::2
+                           MMAs; ld rounded up to a multiple of 256) */
 } sp2_opts;
 
 #define SP2_MAX_ITER 512

@@ -17,13 +17,15 @@ extern "C" {
  * `arena_dev`: device buffer of `nslots` slots, each three bf16 planes of ld x ld
  * (row-major, plane-major), so slot s piece p element (i, j) sits at
  * ((s * 3 + p) * ld + i) * ld + j.  A is slot a_slot, B is slot b_slot; each
- * matrix is the sum of its three pieces.  ld must be a positive multiple of 256 and
+ * matrix is the sum of its three pieces.  ld must be a positive multiple of 128 and
  * arena_dev 16-byte aligned.  With upper = 1 only C's upper triangle is computed and
  * mirrored (meaningful when A B^T is symmetric); with upper = 0 every element is.
+ * tile: 1 = 128 x 128 tiles, one per SM; 2 = 256 x 256 tiles, one per pair of SMs
+ * (ld a multiple of 256); 0 = 2 when ld is a multiple of 256, else 1.
  * out_dev: ld x ld FP32, row-major.  Synchronises `stream`; returns an sp2_status
- * (SP2_ERR_TIMEOUT if a device-side wait gave up). */
+ * (SP2_ERR_INVALID_ARG for bad arguments, SP2_ERR_TIMEOUT if a device-side wait gave up). */
 int32_t sp2_test_tc_gemm(const void* arena_dev, int32_t ld, int32_t nslots, int32_t a_slot, int32_t b_slot,
-                         int32_t upper, float* out_dev, void* stream);
+                         int32_t upper, int32_t tile, float* out_dev, void* stream);
 
 /* Block truncation decision of the block-sparse path on its own: for every 32 x 32 block
  * (I, J) of the dense N x N FP32 device matrix, keep_dev[I * (N/32) + J] = 1 if I == J or

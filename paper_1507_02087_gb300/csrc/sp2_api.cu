@@ -44,7 +44,7 @@ extern "C" void sp2_default_opts(sp2_opts* o) {
   o->refine_fp64 = 0;
   o->launch_mode = 0;
   o->history = 0;
-  o->reserved = 0;
+  o->tile = 0;
 }
 
 extern "C" const char* sp2_status_string(int32_t s) {
@@ -65,7 +65,7 @@ static bool opts_valid(const sp2_opts& o) {
   return o.max_iter >= 1 && o.max_iter <= SP2_MAX_ITER && o.qtilde > 0.0 && (o.guard == 0 || o.guard == 1) &&
          o.corrections >= 0 && o.corrections <= 1 && (o.refine_steps == 0 || o.refine_steps == 2) &&
          (o.refine_fp64 == 0 || o.refine_fp64 == 1) && (o.launch_mode == 0 || o.launch_mode == 1) &&
-         o.history >= 0 && o.history <= 2 && o.reserved == 0;
+         o.history >= 0 && o.history <= 2 && o.tile >= 0 && o.tile <= 2;
 }
 
 static DevState initial_state(int64_t N, int64_t nocc, const sp2_opts& o, int ld, int round_fp32) {
@@ -110,7 +110,8 @@ struct MixedEngine {
   double* part_hi = nullptr;
   int* part_bad = nullptr;
   int pb = 1, sb = 1;
-  int total_upper = 0, total_full = 0;
+  int pair = 0;                    // tensor-core tiles: 1 = 256 x 256 per SM pair, 0 = 128 x 128 per SM
+  int total_upper = 0, total_full = 0;   // tiles of one launch, in the unit above
   int32_t* err_dev = nullptr;
   int32_t* err_host = nullptr;
   cudaGraph_t graph = nullptr;
@@ -150,6 +151,7 @@ struct MixedEngine {
     j.nterms = nterms;
     j.rule = rule;
     j.count = count;
+    j.pair = pair;
     j.total_tiles = upper ? total_upper : total_full;
     j.inst = inst_dev;
     j.err = err_dev;
@@ -191,13 +193,21 @@ struct MixedEngine {
     arenas.assign(count, nullptr);
     parts.assign(count, nullptr);
     const int H = o.max_iter + 2;
+    const int align = o.tile == 2 ? PT : LD_ALIGN;
+    auto ld_of = [&](int64_t n) { return (int)((n + align - 1) / align * align); };
+    pair = o.tile == 2 ? 1 : 0;
+    if (o.tile == 0) {
+      pair = 1;
+      for (int k = 0; k < count; ++k)
+        if (ld_of(N[k]) % PT != 0) pair = 0;
+    }
     // Keep every iterate (full history) or recompute them in the derivative pass; without
     // the correction no pass reads the history, so the rings suffice.
     int lowmem = (o.history == 2 || o.corrections == 0) ? 1 : 0;
     if (o.history == 0 && o.corrections > 0) {
       double full = 0.0;
       for (int k = 0; k < count; ++k) {
-        const double ld = (double)((N[k] + LD_ALIGN - 1) / LD_ALIGN * LD_ALIGN);
+        const double ld = (double)ld_of(N[k]);
         full += (double)(H + 6) * NP * ld * ld * 2.0;
       }
       size_t free_b = 0, total_b = 0;
@@ -208,7 +218,7 @@ struct MixedEngine {
     for (int k = 0; k < count; ++k) {
       Instance& I = inst_host[k];
       std::memset(&I, 0, sizeof(I));
-      const int ld = (int)((N[k] + LD_ALIGN - 1) / LD_ALIGN * LD_ALIGN);
+      const int ld = ld_of(N[k]);
       I.ld = ld;
       I.hist0 = 0;
       I.lowmem = lowmem;
@@ -222,13 +232,14 @@ struct MixedEngine {
       const int nslots = base + 6;
       I.slot_elems = (int64_t)NP * ld * ld;
       I.st = st_dev + k;
-      I.tile_off_upper = off_u;
-      I.tile_off_full = off_f;
-      off_u += tiles_of(ld, 1);
-      off_f += tiles_of(ld, 0);
+      I.tile_off_upper = I.tile_off_upper2 = off_u;
+      I.tile_off_full = I.tile_off_full2 = off_f;
+      off_u += pair ? pair_tiles_of(ld, 1) : tiles_of(ld, 1);
+      off_f += pair ? pair_tiles_of(ld, 0) : tiles_of(ld, 0);
+      I.nparts = nparts_of(ld, pair);
       const size_t abytes = (size_t)nslots * I.slot_elems * 2;
       if (cudaMalloc(&arenas[k], abytes) != cudaSuccess ||
-          cudaMalloc(&parts[k], sizeof(double) * 16 * tiles_of(ld, 1)) != cudaSuccess) {
+          cudaMalloc(&parts[k], sizeof(double) * 4 * I.nparts) != cudaSuccess) {
         (void)cudaGetLastError();
         return SP2_ERR_NOMEM;
       }

@@ -53,8 +53,8 @@ cudaError_t launch_copy_f64(const DevState* st, const double* X, int ld, int N, 
 // ---- tensor-core path ------------------------------------------------------------------------
 // TMA tensor maps over a piece arena of `nslots` ld x ld matrices (boxes of 128 rows).
 cudaError_t tc_make_maps(void* arena, int ld, int nslots, CUtensorMap* mapA, CUtensorMap* mapB);
-int tc_tiles(int ld, int upper);
-int tc_grid_for(int total_tiles);
+int tc_tiles(int ld, int upper, int pair);
+int tc_grid_for(int total_tiles, int pair);
 cudaError_t tc_launch(const tc::Job& job, cudaStream_t s);
 cudaError_t tc_add_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const tc::Job& job,
                         cudaGraphNode_t* node);

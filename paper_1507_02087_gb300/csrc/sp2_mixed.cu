@@ -168,7 +168,8 @@ __global__ void batch_scale_split_kernel(const Instance* inst, int count, int sb
 // ---- per-round reduction, stop test and loop conditions ----------------------------------
 constexpr int kFT = 1024;
 
-// One block per instance: (v^2, ||X_{k-1}||_F^2, Tr[X_{k-1}]) partials, 4 per (tile, warp).
+// One block per instance: (v^2, ||X_{k-1}||_F^2, Tr[X_{k-1}]) partials, one record of 4
+// doubles per (tile, epilogue warp).
 // Tr[X_k] comes from Tr[X^2] = ||X||_F^2 (symmetric X): ||X_{k-1}||_F^2 after X^2,
 // 2 Tr[X_{k-1}] - ||X_{k-1}||_F^2 after 2X - X^2, so the polynomial choice does not
 // inherit the bias of the tensor cores' accumulation.
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(kFT) batch_finalize_kernel(const Instance* ins
   const Instance& In = inst[i];
   DevState* st = In.st;
   if (st->done) return;
-  const int nparts = 4 * tc::tiles_of(In.ld, 1);
+  const int nparts = In.nparts;
   double a = 0.0, b = 0.0, c = 0.0;
   for (int t = threadIdx.x; t < nparts; t += kFT) {
     a += In.part[4 * (int64_t)t];

@@ -44,6 +44,25 @@ constexpr int TMEM_COLS = NBUF * BN;   // four 128 x 128 fp32 chunk accumulators
 constexpr int LD_ALIGN = 128;    // ld is a multiple of the tile size
 constexpr int MAX_BATCH = 256;   // instances per batch
 
+// CTA-pair tiles (cluster of two SMs, tcgen05 cta_group::2): the pair computes a 256 x 256
+// output tile with 256 x 256 x 16 MMAs issued by the even CTA.  Each CTA stages its own
+// 128 rows of A and its own 128 rows of B (half of the N dimension), so shared memory
+// carries half the bytes per flop of a 128 x 128 tile; each CTA's tensor memory holds
+// its 128 rows x 256 columns in two chunk buffers, drained by eight epilogue warps
+// (two per lane quadrant, 128 columns each).  Three warpgroups: the first holds the TMA
+// and MMA warps and gives registers back (P_REG_CTRL), the other two are the epilogue
+// and take them (P_REG_EPI); 3 x 168 launch registers = P_REG_CTRL + 2 P_REG_EPI.
+constexpr int PT = 256;              // pair tile edge
+constexpr int P_NBUF = 2;
+constexpr int P_EPI_WARPS = 8;
+constexpr int P_THREADS = 128 + 32 * P_EPI_WARPS;  // warpgroup 0: TMA, MMA, two idle warps
+constexpr int P_REG_LAUNCH = 168;    // 65536 / 384, rounded down to a multiple of 8
+constexpr int P_REG_CTRL = 56;
+constexpr int P_REG_EPI = 224;
+static_assert(P_NBUF * PT <= 512, "tensor memory columns");
+static_assert(P_REG_CTRL + 2 * P_REG_EPI <= 3 * P_REG_LAUNCH, "register split exceeds the launch budget");
+static_assert(P_REG_LAUNCH * P_THREADS <= 65536, "launch registers");
+
 enum Mode : int32_t {
   MODE_STORE_F32 = 0,   // C -> fp32 buffer (tests)
   MODE_SP2_STEP = 1,    // X_k = C or 2 X_{k-1} - C, with ||X_{k-1} - C||_F^2, ||X_{k-1}||_F^2 and
@@ -92,7 +111,9 @@ struct Instance {
   int32_t tile_off_full;    // first global tile index (full schedule)
   int32_t hist0, dx0, m_slot, f_slot, r0_slot;
   int32_t lowmem;           // 1: iterates in rings, recomputed in the derivative pass
-  int32_t _pad[3];
+  int32_t tile_off_upper2;  // first global pair-tile index (upper schedule)
+  int32_t tile_off_full2;   // first global pair-tile index (full schedule)
+  int32_t nparts;           // forward-square partial records (4 doubles each) per launch
 };
 
 struct Job {
@@ -105,7 +126,7 @@ struct Job {
   const Instance* inst;
   int32_t a_slot[2], b_slot[2];   // SLOTS_FIXED operands; SLOTS_REFINE step in a_slot[0]
   int32_t out_slot;
-  int32_t _pad;
+  int32_t pair;         // 1: 256 x 256 CTA-pair tiles (every instance's ld a multiple of 256)
   float* out32;         // MODE_STORE_F32
   int32_t* err;         // set to SP2_ERR_TIMEOUT if a wait gave up
 };
@@ -113,6 +134,16 @@ struct Job {
 __host__ __device__ __forceinline__ int tiles_of(int ld, int upper) {
   const int R = ld / BM;
   return upper ? R * (R + 1) / 2 : R * R;
+}
+
+__host__ __device__ __forceinline__ int pair_tiles_of(int ld, int upper) {
+  const int R = ld / PT;
+  return upper ? R * (R + 1) / 2 : R * R;
+}
+
+// Partial records one forward square writes: one per (tile, epilogue warp).
+__host__ __device__ __forceinline__ int nparts_of(int ld, int pair) {
+  return pair ? 2 * P_EPI_WARPS * pair_tiles_of(ld, 1) : 4 * tiles_of(ld, 1);
 }
 
 }  // namespace tc

@@ -99,18 +99,21 @@ __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
   return r;
 }
 
-// Global tile t -> (instance, tile row I, tile column J).  Tiles are in row-major order
-// within an instance; with `upper`, row I holds J = I .. R-1.
+__device__ __forceinline__ int tile_off(const Job& job, const Instance& in) {
+  if (job.pair) return job.upper ? in.tile_off_upper2 : in.tile_off_full2;
+  return job.upper ? in.tile_off_upper : in.tile_off_full;
+}
+
+// Global tile t -> (instance, tile row I, tile column J), in units of the launch's tile
+// (128 x 128, or 256 x 256 for CTA pairs).  Tiles are in row-major order within an
+// instance; with `upper`, row I holds J = I .. R-1.
 __device__ __forceinline__ int locate(const Job& job, int t, int& I, int& J) {
   int i = 0;
-  for (; i + 1 < job.count; ++i) {
-    const Instance& nx = job.inst[i + 1];
-    const int off = job.upper ? nx.tile_off_upper : nx.tile_off_full;
-    if (t < off) break;
-  }
+  for (; i + 1 < job.count; ++i)
+    if (t < tile_off(job, job.inst[i + 1])) break;
   const Instance& in = job.inst[i];
-  t -= job.upper ? in.tile_off_upper : in.tile_off_full;
-  const int R = in.ld / BM;
+  t -= tile_off(job, in);
+  const int R = in.ld / (job.pair ? PT : BM);
   if (!job.upper) {
     I = t / R;
     J = t % R;
@@ -135,34 +138,28 @@ __device__ __forceinline__ float join3(__nv_bfloat16 p0, __nv_bfloat16 p1, __nv_
   return (__bfloat162float(p0) + __bfloat162float(p1)) + __bfloat162float(p2);
 }
 
-// 32 consecutive values of row r starting at column c0 from the three planes of a slot.
-__device__ __forceinline__ void load_row32(const __nv_bfloat16* slot, int64_t plane, int64_t off, float (&x)[32]) {
+// 8 consecutive values (16-byte aligned) from / to the three planes of a slot.
+__device__ __forceinline__ void load8(const __nv_bfloat16* slot, int64_t plane, int64_t off, float (&x)[8]) {
+  const uint4 a = *reinterpret_cast<const uint4*>(slot + off);
+  const uint4 b = *reinterpret_cast<const uint4*>(slot + plane + off);
+  const uint4 c = *reinterpret_cast<const uint4*>(slot + 2 * plane + off);
+  const __nv_bfloat16* pa = reinterpret_cast<const __nv_bfloat16*>(&a);
+  const __nv_bfloat16* pb = reinterpret_cast<const __nv_bfloat16*>(&b);
+  const __nv_bfloat16* pc = reinterpret_cast<const __nv_bfloat16*>(&c);
   #pragma unroll
-  for (int h = 0; h < 4; ++h) {
-    const uint4 a = *reinterpret_cast<const uint4*>(slot + off + 8 * h);
-    const uint4 b = *reinterpret_cast<const uint4*>(slot + plane + off + 8 * h);
-    const uint4 c = *reinterpret_cast<const uint4*>(slot + 2 * plane + off + 8 * h);
-    const __nv_bfloat16* pa = reinterpret_cast<const __nv_bfloat16*>(&a);
-    const __nv_bfloat16* pb = reinterpret_cast<const __nv_bfloat16*>(&b);
-    const __nv_bfloat16* pc = reinterpret_cast<const __nv_bfloat16*>(&c);
-    #pragma unroll
-    for (int e = 0; e < 8; ++e) x[8 * h + e] = join3(pa[e], pb[e], pc[e]);
-  }
+  for (int e = 0; e < 8; ++e) x[e] = join3(pa[e], pb[e], pc[e]);
 }
 
-__device__ __forceinline__ void store_row32(__nv_bfloat16* slot, int64_t plane, int64_t off, const float (&x)[32]) {
+__device__ __forceinline__ void store8(__nv_bfloat16* slot, int64_t plane, int64_t off, const float (&x)[8]) {
+  uint4 a, b, c;
+  __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(&a);
+  __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>(&b);
+  __nv_bfloat16* pc = reinterpret_cast<__nv_bfloat16*>(&c);
   #pragma unroll
-  for (int h = 0; h < 4; ++h) {
-    uint4 a, b, c;
-    __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(&a);
-    __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>(&b);
-    __nv_bfloat16* pc = reinterpret_cast<__nv_bfloat16*>(&c);
-    #pragma unroll
-    for (int e = 0; e < 8; ++e) split3(x[8 * h + e], pa[e], pb[e], pc[e]);
-    *reinterpret_cast<uint4*>(slot + off + 8 * h) = a;
-    *reinterpret_cast<uint4*>(slot + plane + off + 8 * h) = b;
-    *reinterpret_cast<uint4*>(slot + 2 * plane + off + 8 * h) = c;
-  }
+  for (int e = 0; e < 8; ++e) split3(x[e], pa[e], pb[e], pc[e]);
+  *reinterpret_cast<uint4*>(slot + off) = a;
+  *reinterpret_cast<uint4*>(slot + plane + off) = b;
+  *reinterpret_cast<uint4*>(slot + 2 * plane + off) = c;
 }
 
 __device__ __forceinline__ void store_one(__nv_bfloat16* slot, int64_t plane, int64_t off, float v) {
@@ -179,18 +176,19 @@ struct Partials {
   double trd;   // sum of the diagonal x
 };
 
-// Epilogue for row r, columns c0 .. c0+31 of the tile, with the accumulated product s.
+// Epilogue for row r, columns c0 .. c0+31 of the tile, with the accumulated product s;
+// worked in groups of 8 columns (one 16-byte access per plane).  The Frobenius partials
+// of the 32 columns are summed in FP32 in column order, then added to P in FP64.
 __device__ __forceinline__ void epilogue_chunk(const Job& job, const Instance& In, const Resolved& R, int r,
                                                int c0, const float (&s)[32], Partials& P) {
   const int ld = In.ld;
   const int64_t plane = (int64_t)ld * ld;
   const bool upper = job.upper != 0;
-  const bool all_keep = !upper || c0 >= r;
-  const bool none_keep = upper && c0 + 31 < r;
-  if (none_keep) return;
+  if (upper && c0 + 31 < r) return;
   const int64_t row_off = (int64_t)r * ld + c0;
 
   if (job.mode == MODE_STORE_F32) {
+    const bool all_keep = !upper || c0 >= r;
     #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int c = c0 + j;
@@ -201,54 +199,60 @@ __device__ __forceinline__ void epilogue_chunk(const Job& job, const Instance& I
   }
 
   __nv_bfloat16* out = In.arena + (int64_t)R.out * In.slot_elems;
-  float xn[32];
-  if (job.mode == MODE_STORE_PIECES) {
-    #pragma unroll
-    for (int j = 0; j < 32; ++j) xn[j] = s[j];
-  } else {
-    const __nv_bfloat16* in = In.arena + (int64_t)R.in * In.slot_elems;
-    float x[32];
-    load_row32(in, plane, row_off, x);
-    if (job.mode == MODE_DF_COMBINE) {
-      const double w = In.st->lmax - In.st->lmin;
-      const float sc = (float)(-1.0 / w);
+  const __nv_bfloat16* in = In.arena + (int64_t)R.in * In.slot_elems;
+  float vacc = 0.f, facc = 0.f;
+  #pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const int cb = c0 + 8 * h;
+    if (upper && cb + 7 < r) continue;
+    float xn[8];
+    if (job.mode == MODE_STORE_PIECES) {
       #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int64_t toff = (int64_t)(c0 + j) * ld + r;
-        const float mt = join3(in[toff], in[plane + toff], in[2 * plane + toff]);
-        xn[j] = sc * ((x[j] + mt) - 2.0f * s[j]);
-      }
+      for (int j = 0; j < 8; ++j) xn[j] = s[8 * h + j];
     } else {
-      float vacc = 0.f, facc = 0.f;
-      #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        xn[j] = R.pk ? s[j] : fmaf(2.0f, x[j], -s[j]);
-        if (job.mode == MODE_SP2_STEP) {
-          const int c = c0 + j;
-          const float d = x[j] - s[j];
-          const float wgt = !upper ? 1.f : (c > r ? 2.f : (c == r ? 1.f : 0.f));
-          vacc = fmaf(wgt * d, d, vacc);
-          facc = fmaf(wgt * x[j], x[j], facc);
-          if (c == r) P.trd += (double)x[j];
+      float x[8];
+      load8(in, plane, row_off + 8 * h, x);
+      if (job.mode == MODE_DF_COMBINE) {
+        const double w = In.st->lmax - In.st->lmin;
+        const float sc = (float)(-1.0 / w);
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int64_t toff = (int64_t)(cb + j) * ld + r;
+          const float mt = join3(in[toff], in[plane + toff], in[2 * plane + toff]);
+          xn[j] = sc * ((x[j] + mt) - 2.0f * s[8 * h + j]);
+        }
+      } else {
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float sj = s[8 * h + j];
+          xn[j] = R.pk ? sj : fmaf(2.0f, x[j], -sj);
+          if (job.mode == MODE_SP2_STEP) {
+            const int c = cb + j;
+            const float d = x[j] - sj;
+            const float wgt = !upper ? 1.f : (c > r ? 2.f : (c == r ? 1.f : 0.f));
+            vacc = fmaf(wgt * d, d, vacc);
+            facc = fmaf(wgt * x[j], x[j], facc);
+            if (c == r) P.trd += (double)x[j];
+          }
         }
       }
-      P.v2 += (double)vacc;
-      P.fro2 += (double)facc;
+    }
+    if (!upper || cb >= r) {
+      store8(out, plane, row_off + 8 * h, xn);
+    } else {
+      #pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (cb + j >= r) store_one(out, plane, row_off + 8 * h + j, xn[j]);
+    }
+    if (upper) {
+      #pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (cb + j > r) store_one(out, plane, (int64_t)(cb + j) * ld + r, xn[j]);
     }
   }
-  if (all_keep) {
-    store_row32(out, plane, row_off, xn);
-  } else {
-    #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (c0 + j >= r) store_one(out, plane, row_off + j, xn[j]);
-  }
-  if (upper) {
-    #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int c = c0 + j;
-      if (c > r) store_one(out, plane, (int64_t)c * ld + r, xn[j]);
-    }
+  if (job.mode == MODE_SP2_STEP) {
+    P.v2 += (double)vacc;
+    P.fro2 += (double)facc;
   }
 }
 
@@ -443,6 +447,233 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
   }
 }
 
+// ---- CTA-pair kernel ------------------------------------------------------------------------
+// The same product and epilogues on 256 x 256 tiles, one tile per cluster of two CTAs
+// (even CTA: rows 0..127 of the tile, odd CTA: rows 128..255).  Each CTA's TMA warp
+// stages its own 128 rows of A and of B (B rows are the output columns: the even CTA
+// holds columns 0..127, the odd one 128..255) and counts the bytes on the even CTA's
+// `full` barrier, which the even CTA arms for both.  The even CTA's MMA thread issues
+// 256 x 256 x 16 pair MMAs and multicasts each commit to both CTAs (`empty` stage
+// barriers, `accf` chunk barriers); every epilogue warp of both CTAs arrives on the even
+// CTA's `acce` barrier once it has drained a chunk buffer.
+constexpr int P_SMEM_BYTES = STAGES * STAGE_BYTES + 8192 + 1024;   // + alignment and read slack
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gemm_pair_kernel(const Job job) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t accf_bar[P_NBUF];
+  __shared__ __align__(8) uint64_t acce_bar[P_NBUF];
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ volatile int abort_s;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const int pair_id = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int a = 0; a < P_NBUF; ++a) { mbar_init(&accf_bar[a], 1); mbar_init(&acce_bar[a], 2 * P_EPI_WARPS); }
+    mbar_init(&drain_bar, 1);
+    abort_s = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc_pair(&tmem_base_s, P_NBUF * PT);
+  tc_fence_before();
+  cluster_sync();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_base_s;
+  const int ntiles = job.total_tiles;
+  if (warp < 4) {
+   setmaxnreg_dec<P_REG_CTRL>();
+   if (warp == 0) {
+    // ---------------- TMA producer (both CTAs) ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int armed[STAGES];
+      uint32_t armed_par[STAGES];
+      for (int s = 0; s < STAGES; ++s) { armed[s] = 0; armed_par[s] = 0; }
+      for (int t = pair_id; t < ntiles && ok; t += npairs) {
+        int I, J;
+        const int ii = locate(job, t, I, J);
+        const Instance& In = job.inst[ii];
+        const Resolved R = resolve(job, In);
+        if (!R.active) continue;
+        const CUtensorMap* mA = &In.mapA;
+        const CUtensorMap* mB = &In.mapB;
+        const int nkb = In.ld / BK;
+        const int rowA = I * PT + (int)rank * BM;
+        const int rowB = J * PT + (int)rank * BN;
+        for (int term = 0; term < job.nterms && ok; ++term) {
+          for (int kb = 0; kb < nkb; ++kb) {
+            if (abort_s || !mbar_wait_cluster(&empty_bar[stage], phase ^ 1, globaltimer_ns() + kWaitNs)) {
+              ok = false;
+              break;
+            }
+            uint8_t* sA = smem + stage * STAGE_BYTES;
+            uint8_t* sB = sA + NP * A_PIECE_BYTES;
+            const uint32_t fb = mapa_shared(smem_u32(&full_bar[stage]), 0);
+            if (rank == 0) mbar_arrive_expect_tx(&full_bar[stage], 2 * STAGE_BYTES);
+            #pragma unroll
+            for (int p = 0; p < NP; ++p)
+              tma_load_4d_pair(sA + p * A_PIECE_BYTES, mA, kb * BK, rowA, p, R.a[term], fb);
+            #pragma unroll
+            for (int p = 0; p < NP; ++p)
+              tma_load_4d_pair(sB + p * B_PIECE_BYTES, mB, kb * BK, rowB, p, R.b[term], fb);
+            armed[stage] = 1;
+            armed_par[stage] = phase;
+            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          }
+        }
+      }
+      if (!ok) {
+        abort_s = 1;
+        atomicExch(job.err, (int)SP2_ERR_TIMEOUT);
+        // copies of the odd CTA complete on the even CTA's barriers, which it cannot
+        // observe: give copies still in flight a fixed 1 ms to land
+        const uint64_t until = globaltimer_ns() + 1000000ull;
+        while (globaltimer_ns() < until) {}
+      }
+      if (rank == 0)
+        for (int s = 0; s < STAGES; ++s)
+          if (armed[s]) mbar_wait_cluster(&full_bar[s], armed_par[s], globaltimer_ns() + kWaitNs);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (even CTA) ----------------
+    if (lane == 0 && rank == 0) {
+      const uint32_t idesc = idesc_bf16_f32(2 * BM, PT);
+      const int pa[6] = {2, 1, 0, 1, 0, 0};
+      const int pb[6] = {0, 1, 2, 0, 1, 0};
+      int stage = 0, buf = 0;
+      uint32_t phase = 0, bphase = 0;
+      bool ok = true;
+      for (int t = pair_id; t < ntiles && ok; t += npairs) {
+        int I, J;
+        const int ii = locate(job, t, I, J);
+        const Instance& In = job.inst[ii];
+        if (!resolve(job, In).active) continue;
+        const int nchunks = job.nterms * (In.ld / BK) / CHUNK_KB;
+        for (int ch = 0; ch < nchunks && ok; ++ch) {
+          if (abort_s || !mbar_wait_cluster(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + kWaitNs)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dt = tmem_base + (uint32_t)(buf * PT);
+          uint32_t accumulate = 0;
+          for (int kc = 0; kc < CHUNK_KB; ++kc) {
+            if (abort_s || !mbar_wait_cluster(&full_bar[stage], phase, globaltimer_ns() + kWaitNs)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
+            const uint32_t sB = sA + NP * A_PIECE_BYTES;
+            #pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              #pragma unroll
+              for (int q = 0; q < 6; ++q) {
+                const uint64_t ad = smem_desc_sw64(sA + pa[q] * A_PIECE_BYTES + kk * 32);
+                const uint64_t bd = smem_desc_sw64(sB + pb[q] * B_PIECE_BYTES + kk * 32);
+                mma_bf16_pair(dt, ad, bd, idesc, accumulate);
+                accumulate = 1;
+              }
+            }
+            mma_commit_pair_mc(&empty_bar[stage], 0x3);
+            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          mma_commit_pair_mc(&accf_bar[buf], 0x3);
+          if (++buf == P_NBUF) { buf = 0; bphase ^= 1; }
+        }
+      }
+      if (!ok) { abort_s = 1; atomicExch(job.err, (int)SP2_ERR_TIMEOUT); }
+      mma_commit_pair_mc(&drain_bar, 0x1);
+      mbar_wait_cluster(&drain_bar, 0, globaltimer_ns() + kWaitNs);
+    }
+   }
+  } else {
+    setmaxnreg_inc<P_REG_EPI>();
+    // ---------------- chunk draining + epilogue (warps 4..11 of both CTAs) ----------------
+    const int ew = warp - 4;       // 0..7
+    const int q = warp & 3;        // TMEM lanes 32q .. 32q+31 (the quadrant this warp may access)
+    const int hc = ew >> 2;        // columns 128 hc .. 128 hc + 127 of the tile
+    int buf = 0;
+    uint32_t bphase = 0;
+    bool ok = true;
+    for (int t = pair_id; t < ntiles && ok; t += npairs) {
+      int I, J;
+      const int ii = locate(job, t, I, J);
+      const Instance& In = job.inst[ii];
+      const Resolved R = resolve(job, In);
+      if (!R.active) continue;
+      const int nchunks = job.nterms * (In.ld / BK) / CHUNK_KB;
+      float acc[BN / 32][32];
+      #pragma unroll
+      for (int g = 0; g < BN / 32; ++g)
+        #pragma unroll
+        for (int j = 0; j < 32; ++j) acc[g][j] = 0.f;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        int got = 0;
+        if (lane == 0) got = !abort_s && mbar_wait_cluster(&accf_bar[buf], bphase, globaltimer_ns() + kWaitNs);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) {
+          if (lane == 0) { abort_s = 1; atomicExch(job.err, (int)SP2_ERR_TIMEOUT); }
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t trow = tmem_base + (uint32_t)(buf * PT + hc * BN) + ((uint32_t)(32 * q) << 16);
+        #pragma unroll
+        for (int g = 0; g < BN / 32; ++g) {
+          uint32_t raw[32];
+          tmem_ld32(trow + g * 32, raw);
+          tmem_wait_ld();
+          #pragma unroll
+          for (int j = 0; j < 32; ++j) acc[g][j] += __uint_as_float(raw[j]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&acce_bar[buf]), 0));
+        if (++buf == P_NBUF) { buf = 0; bphase ^= 1; }
+      }
+      if (!ok) break;
+      const int r = I * PT + (int)rank * BM + 32 * q + lane;
+      Partials P = {0.0, 0.0, 0.0};
+      #pragma unroll
+      for (int g = 0; g < BN / 32; ++g) epilogue_chunk(job, In, R, r, J * PT + hc * BN + g * 32, acc[g], P);
+      if (job.mode == MODE_SP2_STEP) {
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          P.v2 += __shfl_xor_sync(0xffffffffu, P.v2, o);
+          P.fro2 += __shfl_xor_sync(0xffffffffu, P.fro2, o);
+          P.trd += __shfl_xor_sync(0xffffffffu, P.trd, o);
+        }
+        if (lane == 0) {
+          const int lt = t - In.tile_off_upper2;       // pair tile index within the instance
+          double* dst = In.part + 4 * (2 * P_EPI_WARPS * (int64_t)lt + P_EPI_WARPS * rank + ew);
+          dst[0] = P.v2;
+          dst[1] = P.fro2;
+          dst[2] = P.trd;
+          dst[3] = 0.0;
+        }
+      }
+    }
+  }
+
+  // both CTAs stay resident until the pair's MMAs, copies and drains are over
+  __syncwarp();
+  tc_fence_before();
+  cluster_sync();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem_base, P_NBUF * PT);
+  }
+}
+
 }  // namespace tc
 
 // ---- host side ----------------------------------------------------------------------------
@@ -489,26 +720,57 @@ static int sm_count() {
   return n;
 }
 
-int tc_grid_for(int total_tiles) {
-  const int s = sm_count();
-  return total_tiles < s ? (total_tiles < 1 ? 1 : total_tiles) : s;
-}
-
-int tc_tiles(int ld, int upper) { return tc::tiles_of(ld, upper); }
-
 static cudaError_t tc_prepare() {
   static bool done = false;
   if (done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(tc::tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        tc::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc::tc_gemm_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::P_SMEM_BYTES);
   if (e == cudaSuccess) done = true;
   return e;
 }
 
+// Clusters of two that fit on the GPU at once (one CTA per SM); 0 if the query fails.
+static int pair_slots() {
+  static int n = -1;
+  if (n < 0) {
+    if (tc_prepare() != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * sm_count());
+    cfg.blockDim = dim3(tc::P_THREADS);
+    cfg.dynamicSmemBytes = tc::P_SMEM_BYTES;
+    int c = 0;
+    if (cudaOccupancyMaxActiveClusters(&c, (void*)tc::tc_gemm_pair_kernel, &cfg) != cudaSuccess || c <= 0) {
+      (void)cudaGetLastError();
+      c = sm_count() / 2;
+    }
+    n = c;
+  }
+  return n;
+}
+
+// Persistent grid: one CTA (or one CTA pair) per tile up to what the GPU holds at once.
+int tc_grid_for(int total_tiles, int pair) {
+  const int t = total_tiles < 1 ? 1 : total_tiles;
+  if (pair) {
+    const int slots = pair_slots() > 0 ? pair_slots() : 1;
+    return 2 * (t < slots ? t : slots);
+  }
+  const int s = sm_count();
+  return t < s ? t : s;
+}
+
+int tc_tiles(int ld, int upper, int pair) { return pair ? tc::pair_tiles_of(ld, upper) : tc::tiles_of(ld, upper); }
+
 cudaError_t tc_launch(const tc::Job& job, cudaStream_t s) {
   cudaError_t e = tc_prepare();
   if (e != cudaSuccess) return e;
-  tc::tc_gemm_kernel<<<tc_grid_for(job.total_tiles), tc::THREADS, tc::SMEM_BYTES, s>>>(job);
+  if (job.pair)
+    tc::tc_gemm_pair_kernel<<<tc_grid_for(job.total_tiles, 1), tc::P_THREADS, tc::P_SMEM_BYTES, s>>>(job);
+  else
+    tc::tc_gemm_kernel<<<tc_grid_for(job.total_tiles, 0), tc::THREADS, tc::SMEM_BYTES, s>>>(job);
   return cudaGetLastError();
 }
 
@@ -519,10 +781,10 @@ cudaError_t tc_add_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, c
   tc::Job j = job;
   void* args[] = {&j};
   cudaKernelNodeParams kp = {};
-  kp.func = (void*)tc::tc_gemm_kernel;
-  kp.gridDim = dim3(tc_grid_for(job.total_tiles));
-  kp.blockDim = dim3(tc::THREADS);
-  kp.sharedMemBytes = tc::SMEM_BYTES;
+  kp.func = job.pair ? (void*)tc::tc_gemm_pair_kernel : (void*)tc::tc_gemm_kernel;
+  kp.gridDim = dim3(tc_grid_for(job.total_tiles, job.pair));
+  kp.blockDim = dim3(job.pair ? tc::P_THREADS : tc::THREADS);
+  kp.sharedMemBytes = job.pair ? tc::P_SMEM_BYTES : tc::SMEM_BYTES;
   kp.kernelParams = args;
   return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
 }
@@ -530,10 +792,12 @@ cudaError_t tc_add_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, c
 }  // namespace sp2
 
 extern "C" int32_t sp2_test_tc_gemm(const void* arena_dev, int32_t ld, int32_t nslots, int32_t a_slot,
-                                    int32_t b_slot, int32_t upper, float* out_dev, void* stream) {
+                                    int32_t b_slot, int32_t upper, int32_t tile, float* out_dev, void* stream) {
   if (!arena_dev || !out_dev || ld <= 0 || ld % sp2::tc::LD_ALIGN != 0 || nslots <= 0 || a_slot < 0 ||
-      b_slot < 0 || a_slot >= nslots || b_slot >= nslots || (upper != 0 && upper != 1))
+      b_slot < 0 || a_slot >= nslots || b_slot >= nslots || (upper != 0 && upper != 1) || tile < 0 || tile > 2 ||
+      (tile == 2 && ld % sp2::tc::PT != 0))
     return SP2_ERR_INVALID_ARG;
+  const int pair = tile == 2 || (tile == 0 && ld % sp2::tc::PT == 0);
   cudaStream_t s = (cudaStream_t)stream;
   sp2::tc::Instance hinst;
   std::memset(&hinst, 0, sizeof(hinst));
@@ -560,7 +824,8 @@ extern "C" int32_t sp2_test_tc_gemm(const void* arena_dev, int32_t ld, int32_t n
   j.nterms = 1;
   j.rule = sp2::tc::SLOTS_FIXED;
   j.count = 1;
-  j.total_tiles = sp2::tc::tiles_of(ld, upper);
+  j.pair = pair;
+  j.total_tiles = sp2::tc_tiles(ld, upper, pair);
   j.inst = dinst;
   j.a_slot[0] = a_slot;
   j.b_slot[0] = b_slot;

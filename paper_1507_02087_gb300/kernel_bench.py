@@ -28,6 +28,8 @@ def main():
     ap.add_argument("--ld", type=int, default=8192)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--full", action="store_true", help="all tiles (general product) instead of upper + mirror")
+    ap.add_argument("--tile", default="auto", choices=["auto", "128", "pair"],
+                    help="128 x 128 tiles per SM, 256 x 256 tiles per SM pair, or auto (pair if ld % 256 == 0)")
     a = ap.parse_args()
     ld = a.ld
     g = torch.Generator(device="cuda").manual_seed(0)
@@ -36,21 +38,22 @@ def main():
     arena = pieces(X).unsqueeze(0).contiguous()
     out = torch.empty(ld, ld, device="cuda", dtype=torch.float32)
     upper = not a.full
-    sp2.sp2_test_tc_gemm(arena, ld, 1, 0, 0, upper, out)    # warm-up
+    sp2.sp2_test_tc_gemm(arena, ld, 1, 0, 0, upper, out, tile=a.tile)    # warm-up
     times = []
     for _ in range(a.reps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        sp2.sp2_test_tc_gemm(arena, ld, 1, 0, 0, upper, out)
+        sp2.sp2_test_tc_gemm(arena, ld, 1, 0, 0, upper, out, tile=a.tile)
         e1.record()
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     ms = min(times)
-    R = ld // 128
+    edge = 256 if a.tile == "pair" or (a.tile == "auto" and ld % 256 == 0) else 128
+    R = ld // edge
     tiles = R * (R + 1) // 2 if upper else R * R
-    executed = 6 * tiles * 128 * 128 * ld * 2
-    print(json.dumps({"ld": ld, "upper": upper, "ms": ms, "tiles": tiles,
+    executed = 6 * tiles * edge * edge * ld * 2
+    print(json.dumps({"ld": ld, "upper": upper, "tile_edge": edge, "ms": ms, "tiles": tiles,
                       "executed_tflops": executed / (ms * 1e-3) / 1e12,
                       "algorithmic_tflops": 6 * ld * ld * (ld + 1) / (ms * 1e-3) / 1e12 if upper else None}))
 

@@ -36,7 +36,7 @@ class sp2_opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("guard", ctypes.c_int32), ("qtilde", ctypes.c_double),
                 ("corrections", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
                 ("refine_fp64", ctypes.c_int32), ("launch_mode", ctypes.c_int32),
-                ("history", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("history", ctypes.c_int32), ("tile", ctypes.c_int32)]
 
 
 class sp2_info(ctypes.Structure):
@@ -72,7 +72,7 @@ def lib() -> ctypes.CDLL:
         L.sp2_destroy.restype = None
         L.sp2_status_string.argtypes = [i32]
         L.sp2_status_string.restype = ctypes.c_char_p
-        L.sp2_test_tc_gemm.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp]
+        L.sp2_test_tc_gemm.argtypes = [vp, i32, i32, i32, i32, i32, i32, vp, vp]
         L.sp2_test_tc_gemm.restype = i32
         L.sp2_run_fp64_noalloc.argtypes = [vp, vp, i64, i64, vp, vp]
         L.sp2_run_fp64_noalloc.restype = i32
@@ -113,22 +113,26 @@ def _stream_ptr(stream) -> int:
     return int(getattr(stream, "cuda_stream", stream))
 
 
+TILES = {"auto": 0, "128": 1, "pair": 2}
 HISTORY = {"auto": 0, "full": 1, "recompute": 2}
 
 
-def _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history="auto"):
+def _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history="auto",
+          tile="auto"):
     if launch_mode is None:
         launch_mode = int(os.environ.get("SP2_LAUNCH_MODE", "0"))
     return sp2_opts(max_iter, 1 if guard else 0, qtilde, corrections, refine_steps, 1 if refine_fp64 else 0,
-                    launch_mode, HISTORY[history], 0)
+                    launch_mode, HISTORY[history], TILES[tile])
 
 
 def sp2_create(N: int, nocc: int, precision: str = "fp64", *, max_iter: int = 200, guard: bool = True,
                qtilde: float = 1.8, corrections: int = 1, refine_steps: int = 2,
-               refine_fp64: bool = False, launch_mode: int | None = None, history: str = "auto") -> int:
+               refine_fp64: bool = False, launch_mode: int | None = None, history: str = "auto",
+               tile: str = "auto") -> int:
     """launch_mode None reads SP2_LAUNCH_MODE from the environment (default 0, the graph).
-    history: "auto", "full" (keep every iterate) or "recompute" (low memory)."""
-    o = _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history)
+    history: "auto", "full" (keep every iterate) or "recompute" (low memory).
+    tile: tensor-core tiles of the mixed path, "auto", "128" or "pair" (256 x 256 per SM pair)."""
+    o = _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history, tile)
     h = ctypes.c_void_p()
     _check(lib().sp2_create(N, nocc, PRECISIONS[precision], ctypes.byref(o), ctypes.byref(h)), "sp2_create")
     return h.value
@@ -152,9 +156,10 @@ def sp2_get_info(h: int) -> dict:
 
 def sp2_create_batch(Ns, noccs, precision: str = "mixed", *, max_iter: int = 200, guard: bool = True,
                      qtilde: float = 1.8, corrections: int = 1, refine_steps: int = 2,
-                     refine_fp64: bool = False, launch_mode: int | None = None, history: str = "auto") -> int:
+                     refine_fp64: bool = False, launch_mode: int | None = None, history: str = "auto",
+                     tile: str = "auto") -> int:
     count = len(Ns)
-    o = _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history)
+    o = _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history, tile)
     n_arr = (ctypes.c_int64 * count)(*Ns)
     o_arr = (ctypes.c_int64 * count)(*noccs)
     h = ctypes.c_void_p()
@@ -199,10 +204,11 @@ def _info_dict(info) -> dict:
 
 
 def sp2_test_tc_gemm(arena, ld: int, nslots: int, a_slot: int, b_slot: int, upper: bool, out,
-                     stream=None) -> None:
-    """Tensor-core product C = A B^T over a bf16 piece arena (see include/sp2_testing.h)."""
+                     stream=None, tile: str = "auto") -> None:
+    """Tensor-core product C = A B^T over a bf16 piece arena (see include/sp2_testing.h).
+    tile: "128" (128 x 128 per SM), "pair" (256 x 256 per SM pair) or "auto"."""
     _check(lib().sp2_test_tc_gemm(arena.data_ptr(), ld, nslots, a_slot, b_slot, 1 if upper else 0,
-                                  out.data_ptr(), _stream_ptr(stream)), "sp2_test_tc_gemm")
+                                  TILES[tile], out.data_ptr(), _stream_ptr(stream)), "sp2_test_tc_gemm")
 
 
 def sp2_destroy(h: int) -> None:

@@ -83,6 +83,30 @@ def test_mixed_options(sp2mod):
     assert errs["corr+tc"] <= TOL_MIXED and errs["corr+fp64"] <= TOL_MIXED
 
 
+@pytest.mark.parametrize("N,nocc,tile", [(1500, 700, "128"), (1500, 700, "pair"), (700, 350, "pair")])
+def test_mixed_tile_kinds(sp2mod, N, nocc, tile):
+    # 128 x 128 tiles per SM and 256 x 256 tiles per SM pair (N = 700: ld rounded to 768)
+    case = inputs.dense_gapped(N, nocc, gap=0.02, seed=21)
+    ref = o.sp2(case.F.numpy(), nocc)
+    D, info = run_gpu(sp2mod, case.F, nocc, tile=tile)
+    assert info["status"] == 0 and info["n_iter"] <= ref.n + 1
+    assert o.rel_error(D.cpu().numpy(), ref.D, nocc) <= TOL_MIXED
+    assert torch.equal(D, D.T)
+
+
+def test_batch_with_pair_tiles(sp2mod):
+    # every ld a multiple of 256: the batch runs on CTA-pair tiles
+    Ns, noccs = [256, 512, 1024, 768], [100, 256, 500, 300]
+    cases = [inputs.dense_gapped(n, k, gap=0.05, seed=40 + n) for n, k in zip(Ns, noccs)]
+    with sp2mod.BatchPurifier(Ns, noccs, "mixed") as B:
+        Ds = B.run([c.F.cuda() for c in cases])
+        infos = [B.info(i) for i in range(len(Ns))]
+    for c, k, D, info in zip(cases, noccs, Ds, infos):
+        ref = o.sp2(c.F.numpy(), k)
+        assert info["status"] == 0 and info["n_iter"] <= ref.n + 1
+        assert o.rel_error(D.cpu().numpy(), ref.D, k) <= TOL_MIXED
+
+
 def test_recompute_history_is_bit_identical(sp2mod):
     # low-memory layout: the derivative pass recomputes the iterates instead of reading
     # them back; the kernels are deterministic, so D must not change by a bit

@@ -29,11 +29,11 @@ def pieces(x32: torch.Tensor) -> torch.Tensor:
     return torch.stack([p0, p1, p2])
 
 
-def run(sp2mod, mats, a, b, upper):
+def run(sp2mod, mats, a, b, upper, tile="auto"):
     ld = mats[0].shape[0]
     arena = torch.stack([pieces(m) for m in mats]).contiguous()
     out = torch.full((ld, ld), float("nan"), dtype=torch.float32, device="cuda")
-    sp2mod.sp2_test_tc_gemm(arena, ld, len(mats), a, b, upper, out)
+    sp2mod.sp2_test_tc_gemm(arena, ld, len(mats), a, b, upper, out, tile=tile)
     return out
 
 
@@ -41,12 +41,13 @@ def rel(C, R):
     return float(torch.linalg.norm(C.double() - R) / torch.linalg.norm(R))
 
 
+@pytest.mark.parametrize("tile", ["128", "pair"])
 @pytest.mark.parametrize("ld", [256, 512, 1024, 4096])
-def test_general_product(sp2mod, ld):
+def test_general_product(sp2mod, ld, tile):
     g = torch.Generator(device="cpu").manual_seed(ld)
     A = torch.randn(ld, ld, generator=g).float().cuda()
     B = torch.randn(ld, ld, generator=g).float().cuda() * 1e-3
-    C = run(sp2mod, [A, B], 0, 1, False)
+    C = run(sp2mod, [A, B], 0, 1, False, tile)
     R = A.double() @ B.double().T
     assert torch.isfinite(C).all()
     # FP32 accumulation over K = ld terms: relative error a few 1e-6
@@ -56,12 +57,13 @@ def test_general_product(sp2mod, ld):
     assert float(((C.double() - R).abs() / scale).max()) < 1e-5
 
 
+@pytest.mark.parametrize("tile", ["128", "pair"])
 @pytest.mark.parametrize("ld", [256, 768, 2048, 4096])
-def test_symmetric_square_upper(sp2mod, ld):
+def test_symmetric_square_upper(sp2mod, ld, tile):
     g = torch.Generator(device="cpu").manual_seed(100 + ld)
     X = torch.randn(ld, ld, generator=g, dtype=torch.float64)
     X = ((X + X.T) / (2 * ld ** 0.5)).float().cuda()
-    C = run(sp2mod, [X], 0, 0, True)
+    C = run(sp2mod, [X], 0, 0, True, tile)
     R = X.double() @ X.double()
     assert torch.equal(C, C.T)               # mirror writes: exactly symmetric
     assert rel(C, R) < 1e-5
@@ -78,3 +80,26 @@ def test_slot_selection_and_zero_border(sp2mod):
     R = mats[2].double() @ mats[3].double().T
     assert rel(C, R) < 1e-5
     assert float(C[N:, :].abs().max()) == 0.0 and float(C[:, N:].abs().max()) == 0.0
+
+
+def test_pair_and_single_tiles_agree(sp2mod):
+    # the same six piece products in the same 64-term chunks: both tile kinds give the
+    # same FP32 sums up to the tensor cores' internal order within one MMA
+    ld = 1536
+    g = torch.Generator(device="cpu").manual_seed(5)
+    X = torch.randn(ld, ld, generator=g, dtype=torch.float64)
+    X = ((X + X.T) / (2 * ld ** 0.5)).float().cuda()
+    C1 = run(sp2mod, [X], 0, 0, True, "128")
+    C2 = run(sp2mod, [X], 0, 0, True, "pair")
+    R = X.double() @ X.double()
+    assert rel(C1, R) < 1e-5 and rel(C2, R) < 1e-5
+    assert float((C1.double() - C2.double()).abs().max()) < 1e-5 * float(R.abs().max())
+
+
+def test_tile_argument_checked(sp2mod):
+    arena = torch.zeros(1, 3, 384, 384, dtype=torch.bfloat16, device="cuda")
+    out = torch.empty(384, 384, device="cuda")
+    with pytest.raises(RuntimeError):
+        sp2mod.sp2_test_tc_gemm(arena, 384, 1, 0, 0, True, out, tile="pair")   # 384 is not a multiple of 256
+    sp2mod.sp2_test_tc_gemm(arena, 384, 1, 0, 0, True, out, tile="auto")       # falls back to 128 x 128 tiles
+    assert float(out.abs().max()) == 0.0
