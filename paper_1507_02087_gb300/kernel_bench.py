@@ -4,6 +4,7 @@ Builds a random symmetric FP32 matrix X of size ld, stores it as three bf16 piec
 and times C = X X^T with the same tcgen05 kernel the mixed SP2 path uses (upper
 tiles + mirror, FP32 output).  Used for kernel profiling on a small, self-contained
 case:  python -m paper_1507_02087_gb300.kernel_bench --ld 8192 --reps 5
+With --sp2 it times the SP2 forward square itself (expansion loop of a mixed handle).
 """
 from __future__ import annotations
 
@@ -30,7 +31,12 @@ def main():
     ap.add_argument("--full", action="store_true", help="all tiles (general product) instead of upper + mirror")
     ap.add_argument("--tile", default="auto", choices=["auto", "128", "pair"],
                     help="128 x 128 tiles per SM, 256 x 256 tiles per SM pair, or auto (pair if ld % 256 == 0)")
+    ap.add_argument("--sp2", action="store_true",
+                    help="time the SP2 forward square instead (expansion loop only, stream launches) on the "
+                         "dense gapped input of size ld, nocc = ld / 2, gap 0.01")
     a = ap.parse_args()
+    if a.sp2:
+        return sp2_forward(a)
     ld = a.ld
     g = torch.Generator(device="cuda").manual_seed(0)
     X = torch.randn(ld, ld, device="cuda", generator=g)
@@ -56,6 +62,29 @@ def main():
     print(json.dumps({"ld": ld, "upper": upper, "tile_edge": edge, "ms": ms, "tiles": tiles,
                       "executed_tflops": executed / (ms * 1e-3) / 1e12,
                       "algorithmic_tflops": 6 * ld * ld * (ld + 1) / (ms * 1e-3) / 1e12 if upper else None}))
+
+
+def sp2_forward(a):
+    """Forward squares of the mixed expansion (MODE_SP2_STEP epilogue: X_{k-1} read, pieces
+    written, Frobenius partials) on a 4-slot-ring handle, launched on the stream one by one
+    so that a kernel profiler sees each square."""
+    from . import inputs
+    N = a.ld
+    case = inputs.dense_gapped(N, N // 2, gap=0.01, seed=0, device="cuda", want_exact=False)
+    F = case.F
+    D = torch.empty_like(F)
+    with sp2.Purifier(N, N // 2, "mixed", corrections=0, refine_steps=0, launch_mode=1, tile=a.tile) as P:
+        P.run(F, D)
+        per = []
+        for _ in range(a.reps):
+            P.run(F, D)
+            fi = P.info()
+            per.append(fi["loop_ms"] / fi["hist_len"])
+        info = P.info()
+    ms = min(per)
+    print(json.dumps({"ld": N, "mode": "sp2_forward", "tile": a.tile, "squares": int(info["hist_len"]),
+                      "ms_per_square_incl_stop_test": ms,
+                      "algorithmic_tflops": 6 * N * N * (N + 1) / (ms * 1e-3) / 1e12}))
 
 
 if __name__ == "__main__":
