@@ -14,10 +14,24 @@ row's squares summed left to right, then the row sums top to bottom (each square
 an FP32 value is exact in FP64).  The GPU path evaluates the same sums in the same
 order, so given the same stored block both sides take the same decision bit for bit.
 
+Second rule, error-controlled truncation (`keep_mask_error`): the removed part E is
+bounded directly, ||E||_F <= tau.  The off-diagonal blocks are ordered by
+(||X_IJ||_F^2, I, J), and the longest prefix of that order whose norms, counted twice
+(a symmetric pair (I, J), (J, I) is removed together), sum to at most tau^2 is dropped;
+blocks with 2 ||X_IJ||_F^2 > tau^2 are never dropped.  Reading: the sum is taken in
+exact integer units of 2^(e - 40), where 2^e <= tau^2 < 2^(e+1) (each 2 ||X_IJ||_F^2
+rounded down to a unit, the budget tau^2 rounded down as well), so it does not depend
+on the summation order and host and device take the same decision bit for bit; the
+quantisation moves the budget by at most 2^-40 of tau^2 per dropped block.  tau = 0
+drops nothing.
+
 `sp2_bsr` runs Alg. 3 on dense FP64 matrices with the blocks masked after every
-step; `keep_mask` and `square_pattern` are the index work on their own.
+step; `keep_mask`, `keep_mask_error` and `square_pattern` are the index work on
+their own.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -44,6 +58,38 @@ def keep_mask(X: np.ndarray, b: int, tau: float) -> np.ndarray:
     return keep
 
 
+def error_units(tau: float) -> tuple[int, int]:
+    """(e, budget): 2^e <= tau^2 < 2^(e+1) and the budget floor(tau^2 / 2^(e-40))."""
+    tau2 = tau * tau
+    _, ex = math.frexp(tau2)          # tau2 = m 2^ex, m in [1/2, 1)
+    e = ex - 1
+    return e, int(math.floor(math.ldexp(tau2, 40 - e)))
+
+
+def keep_mask_error(X: np.ndarray, b: int, tau: float) -> np.ndarray:
+    """Blocks kept by the error-controlled truncation (module docstring): drop the longest
+    prefix, in (||X_IJ||^2, I, J) order over the off-diagonal upper blocks with
+    2 ||X_IJ||^2 <= tau^2, whose units 2 ||X_IJ||^2 / 2^(e-40) (rounded down) add up to
+    at most the budget."""
+    n2 = block_norms2(X, b)
+    nb = n2.shape[0]
+    keep = np.ones((nb, nb), dtype=bool)
+    tau2 = tau * tau
+    if tau2 == 0.0:
+        return keep
+    e, budget = error_units(tau)
+    cands = [(float(n2[I, J]), I, J) for I in range(nb) for J in range(I + 1, nb) if 2.0 * n2[I, J] <= tau2]
+    cands.sort()
+    total = 0
+    for v, I, J in cands:
+        u = int(math.floor(math.ldexp(v, 41 - e)))      # floor(2 v / 2^(e-40))
+        if total + u > budget:
+            break
+        total += u
+        keep[I, J] = keep[J, I] = False
+    return keep
+
+
 def apply_mask(X: np.ndarray, keep: np.ndarray, b: int) -> np.ndarray:
     return X * np.kron(keep, np.ones((b, b)))
 
@@ -56,10 +102,13 @@ def square_pattern(keep: np.ndarray) -> np.ndarray:
 
 
 def sp2_bsr(F: np.ndarray, nocc: int, b: int, tau: float, *, bounds=None, max_iter: int = 200,
-            guard: bool = True):
-    """Alg. 3 with X~_i = X_i + E_i, E_i the block truncation above (FP64 values)."""
+            guard: bool = True, rule: str = "block"):
+    """Alg. 3 with X~_i = X_i + E_i, E_i the block truncation above (FP64 values);
+    rule "block" (drop blocks with norm below tau) or "error" (||E_i||_F <= tau)."""
+    mask = keep_mask if rule == "block" else keep_mask_error
+
     def perturb(i, X):
-        return apply_mask(X, keep_mask(X, b, tau), b) - X
+        return apply_mask(X, mask(X, b, tau), b) - X
     return o.sp2(F, nocc, bounds=bounds, max_iter=max_iter, guard=guard, perturb=perturb)
 
 

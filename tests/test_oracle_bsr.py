@@ -72,3 +72,83 @@ def test_truncation_error_grows_with_tau():
     De = V[:, :tb.nocc] @ V[:, :tb.nocc].T
     errs = [o.rel_error(bo.sp2_bsr(F, tb.nocc, 32, tau).D, De, tb.nocc) for tau in (0.0, 1e-6, 1e-4)]
     assert errs[0] < 1e-13 and errs[0] <= errs[1] < errs[2] < 1e-3
+
+
+# ---- error-controlled truncation ----------------------------------------------------------
+
+def _blocks_with_norms(nb, b, norms2):
+    """Symmetric matrix whose off-diagonal upper block (I, J) has ||X_IJ||_F^2 = norms2[(I, J)]
+    exactly (one nonzero element per block, a power-of-two multiple), diagonal blocks = I."""
+    X = np.zeros((nb * b, nb * b))
+    for I in range(nb):
+        X[I * b:(I + 1) * b, I * b:(I + 1) * b] = np.eye(b)
+    for (I, J), v in norms2.items():
+        x = np.sqrt(v)
+        X[I * b, J * b] = X[J * b, I * b] = x
+    return X
+
+
+def test_error_truncation_worked_example():
+    # pairs with ||X_IJ||^2 = 1, 2, 3, 4 (x 2^-30); counted twice they weigh 2, 4, 6, 8.
+    # tau^2 = 6.5 x 2^-30 admits the first two (2 + 4 = 6) and not the third (12).
+    c = 2.0 ** -30
+    norms2 = {(0, 1): 1 * c, (0, 2): 2 * c, (1, 2): 3 * c, (2, 3): 4 * c}
+    X = _blocks_with_norms(4, 32, norms2)
+    keep = bo.keep_mask_error(X, 32, np.sqrt(6.5 * c))
+    dropped = {(I, J) for I in range(4) for J in range(I + 1, 4) if not keep[I, J]}
+    assert dropped == {(0, 1), (0, 2), (0, 3), (1, 3)}       # zero blocks weigh nothing and go first
+    assert np.array_equal(keep, keep.T) and keep.diagonal().all()
+    # the per-block rule at the same tau drops every pair with ||X_IJ|| < tau: all six off-diagonal
+    # pairs (1, 2, 3, 4 x c and the two zero blocks), so ||E||_F^2 = 20 c > tau^2
+    kb = bo.keep_mask(X, 32, np.sqrt(6.5 * c))
+    assert int((~kb).sum()) // 2 == 6
+
+
+def test_error_truncation_ties_broken_by_index():
+    c = 2.0 ** -20
+    norms2 = {(0, 3): c, (1, 2): c, (0, 1): c, (2, 3): 5 * c}
+    X = _blocks_with_norms(4, 32, norms2)
+    keep = bo.keep_mask_error(X, 32, np.sqrt(4 * c))        # room for two of the three equal pairs
+    dropped = {(I, J) for I in range(4) for J in range(I + 1, 4) if not keep[I, J]}
+    assert dropped - {(0, 2), (1, 3)} == {(0, 1), (0, 3)}    # (I, J) order among equal norms
+    assert not keep[0, 2] and not keep[1, 3]                 # the zero blocks
+
+
+def test_error_truncation_bound_and_maximality():
+    g = np.random.Generator(np.random.PCG64(11))
+    nb, b = 10, 32
+    X = g.standard_normal((nb * b, nb * b))
+    X = 0.5 * (X + X.T)
+    scale = np.exp(g.uniform(-12, 0, (nb, nb)))
+    scale = np.minimum(scale, scale.T)
+    X = X * np.kron(scale, np.ones((b, b)))
+    for tau in (1e-3, 1e-1, 3.0):
+        keep = bo.keep_mask_error(X, b, tau)
+        E = X - bo.apply_mask(X, keep, b)
+        e2 = np.linalg.norm(E) ** 2                          # library norm, independent of the rule's sums
+        assert e2 <= tau * tau * (1 + 1e-9)
+        # maximal: the smallest kept off-diagonal block would overflow the budget
+        n2 = np.array([[np.linalg.norm(X[I*b:(I+1)*b, J*b:(J+1)*b]) ** 2 for J in range(nb)] for I in range(nb)])
+        kept_off = [n2[I, J] for I in range(nb) for J in range(I + 1, nb) if keep[I, J]]
+        if kept_off:
+            assert e2 + 2 * min(kept_off) > tau * tau * (1 - 1e-9)
+
+
+def test_error_truncation_edge_cases():
+    g = np.random.Generator(np.random.PCG64(12))
+    X = g.standard_normal((128, 128))
+    X = 0.5 * (X + X.T)
+    assert bo.keep_mask_error(X, 32, 0.0).all()               # tau = 0: nothing dropped
+    keep = bo.keep_mask_error(X, 32, 1e6)                     # everything fits the budget
+    assert keep.diagonal().all() and int(keep.sum()) == 4
+    e, budget = bo.error_units(0.75)
+    assert 2.0 ** e <= 0.75 ** 2 < 2.0 ** (e + 1) and budget == int(np.floor(0.5625 * 2.0 ** (40 - e)))
+
+
+def test_bsr_oracle_error_rule_runs_and_bounds_each_step():
+    tb = inputs.tight_binding(L=4, delta=1.0, t=0.3, sigma=0.05, seed=2, dims=(32, 2, 2))
+    F = tb.dense()
+    res = bo.sp2_bsr(F, tb.nocc, 32, 1e-4, rule="error")
+    assert res.stop_reason in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
+    ref = o.sp2(F, tb.nocc)
+    assert o.rel_error(res.D, ref.D, tb.nocc) < 1e-3
