@@ -53,6 +53,12 @@ def parse():
                          "in [128, 2048], seed 1; bsr: gapped tight-binding 32^3 lattice, 32 x 32 blocks, "
                          "block truncation tau in {1e-4, 1e-6}")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--refine", choices=["tc", "fp64"], default="tc",
+                    help="mixed path: refinement pair on the tensor cores or in FP64")
+    ap.add_argument("--fp64-sample-squares", type=int, default=0,
+                    help="with --fp64-steps 0: time this many FP64 squares and estimate the FP64 time-to-D")
+    ap.add_argument("--rule", choices=["error", "block"], default="error",
+                    help="block-sparse truncation rule of the headline line (both rules are reported)")
     ap.add_argument("--N", type=int, default=N_DEFAULT)
     ap.add_argument("--nocc", type=int, default=None)
     ap.add_argument("--gap", type=float, default=GAP_DEFAULT)
@@ -292,8 +298,9 @@ def run_bsr(a, ws, rank, local):
     rp_d, ci_d, vals_d = (torch.from_numpy(x).cuda() for x in (rp, ci, vals))
     stream = torch.cuda.current_stream()
     out = {}
-    for tau in (1e-4, 1e-6):
-        with sp2.BsrPurifier(tb.N, tb.nocc, tau) as P:
+    rules = [a.rule] + [r for r in ("error", "block") if r != a.rule]
+    for rule, tau in [(r, t) for r in rules for t in (1e-4, 1e-6)]:
+        with sp2.BsrPurifier(tb.N, tb.nocc, tau, rule=rule) as P:
             for _ in range(a.warmup):
                 P.run(rp_d, ci_d, vals_d, dense=False, stream=stream)
             torch.cuda.synchronize()
@@ -308,14 +315,14 @@ def run_bsr(a, ws, rank, local):
                 tms.append(e0.elapsed_time(e1))
             info = P.info()
         nb = tb.N // 32
-        out[f"tau={tau:g}"] = {"time_to_d_ms": statistics.mean(tms), "n_iter": info["n_iter"],
+        out[f"{rule}:tau={tau:g}"] = {"time_to_d_ms": statistics.mean(tms), "n_iter": info["n_iter"],
                                "squares": info["hist_len"], "stop_reason": info["stop_reason"],
                                "nnzb_D": info["nnzb"], "kept_fraction": info["nnzb"] / nb ** 2,
                                "v_last": float(info["v"][-1]) if len(info["v"]) else None,
                                "trace_err": abs(float(info["trace"][info["n_iter"]]) - tb.nocc),
                                "ms_per_square": info["loop_ms"] / max(1, info["hist_len"])}
     if rank == 0:
-        main_ms = out["tau=0.0001"]["time_to_d_ms"]
+        main_ms = out[f"{a.rule}:tau=0.0001"]["time_to_d_ms"]
         print(json.dumps({
             "metric": "time-to-D, block-sparse SP2 with block truncation (FP32 blocks, FP64 reductions)",
             "value": main_ms, "unit": "ms", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
@@ -323,7 +330,9 @@ def run_bsr(a, ws, rank, local):
             "dtype": "f32 blocks, f64 reductions", "data": "synthetic",
             "config": {"workload": "gapped tight-binding 32x32x32 simple cubic (N=32768), delta=1, t=0.3, "
                                    "sigma=0.05 (seed 2), nocc=N/2, 32x32 blocks (x-lines)",
-                       "nnzb_F": int(rp[-1])},
+                       "nnzb_F": int(rp[-1]), "tau": 1e-4,
+                       "truncation": {"error": "error-controlled, ||E_i||_F <= tau",
+                                      "block": "per block, ||X_IJ||_F < tau dropped"}[a.rule]},
             "runs": out}), flush=True)
 
 
@@ -354,7 +363,7 @@ def main():
     D_exact = case.D_exact
     D = torch.empty_like(F)
     stream = torch.cuda.current_stream()
-    P = sp2.Purifier(N, nocc, a.precision)
+    P = sp2.Purifier(N, nocc, a.precision, refine_fp64=(a.refine == "fp64"))
 
     def err_vs_exact():
         return float(torch.linalg.norm(D - D_exact)) / math.sqrt(nocc)
@@ -450,6 +459,30 @@ def main():
                 "squares": sq64, "err_vs_exact": e64,
                 "tflops": N * N * (N + 1) * sq64 / (statistics.mean(tms) * 1e-3) / 1e12,
                 "speedup_mixed_vs_fp64": statistics.mean(tms) / ms}
+    elif mixed and a.fp64_sample_squares > 0:
+        # too long to run whole: time K FP64 squares (a handle capped at K iterations) and
+        # scale by the square count of the mixed run, which the FP64 path does not undercut
+        K = a.fp64_sample_squares
+        with sp2.Purifier(N, nocc, "fp64", max_iter=K) as P64:
+            D64 = torch.empty_like(F)
+            P64.run(F, D64, stream)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P64.run(F, D64, stream)
+            e1.record(stream)
+            e1.synchronize()
+            i64 = P64.info()
+            del D64
+        per_sq = i64["loop_ms"] / max(1, i64["hist_len"])
+        est = e0.elapsed_time(e1) - i64["loop_ms"] + per_sq * squares
+        fp64 = {"time_to_d_ms": est, "estimate": True,
+                "sample": f"{i64['hist_len']} FP64 squares timed ({per_sq:.1f} ms each), scaled to the "
+                          f"{squares} squares of the mixed run (a lower bound: the FP64 path stops at the same "
+                          f"or a later square)",
+                "tflops": N * N * (N + 1) / (per_sq * 1e-3) / 1e12,
+                "speedup_mixed_vs_fp64": est / ms}
 
     # end to end through the public API with host buffers (copies inside the timed region)
     e2e = None
@@ -480,12 +513,14 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-                "vs_baseline": None, "dtype": "bf16x6->f32 (mixed), f64 reductions" if mixed else "f64",
+                "vs_baseline": None,
+                "dtype": ("bf16x6->f32 (mixed), f64 reductions" + (", f64 refinement pair" if a.refine == "fp64"
+                                                                   else "")) if mixed else "f64",
                 "data": "synthetic",
                 "config": {"workload": workload_name(N, nocc, a.gap) if a.input == "qr" else
                            f"dense N={N} nocc={nocc} gap={a.gap:g}, Q = 64 Householder reflectors (seed 3)",
                            "N": N, "nocc": nocc, "gap": a.gap,
-                           "precision": a.precision,
+                           "precision": a.precision, "refine": a.refine if mixed else None,
                            "parallelism": "replicas" if ws > 1 else "1 GPU",
                            "l2": "no flush: F 512 MiB and the streamed iterates exceed the 129 MB L2"},
                 "err_vs_exact": err, "err_first_run": err_first, "meets_tolerance": bool(err <= TOL and status_ok),

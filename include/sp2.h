@@ -179,10 +179,27 @@ void sp2_destroy_batch(sp2_batch hb);
  * traces, norms and the stop test (Alg. 3 with the trace guard) are FP64, on the device. */
 typedef struct sp2_bsr_ctx* sp2_bsr;
 
+/* Truncation rules (the E_i of Alg. 1; the paper names thresholded and error-controlled
+ * removal of small matrix parts in its numerical sections but fixes no block rule). */
+typedef enum {
+  SP2_TRUNC_BLOCK = 0,  /* drop each off-diagonal block with ||X_IJ||_F < tau */
+  SP2_TRUNC_ERROR = 1   /* error-controlled, ||E_i||_F <= tau: over the off-diagonal blocks in
+                           (||X_IJ||_F^2, I, J) order, drop the longest prefix whose norms,
+                           counted twice (a symmetric pair goes together), add up to at most
+                           tau^2; the sums are exact integer multiples of 2^(e-40) with
+                           2^e <= tau^2 < 2^(e+1) (each 2 ||X_IJ||_F^2 and tau^2 rounded down to
+                           a multiple), so the selection does not depend on summation order */
+} sp2_trunc_rule;
+
 /* N: a multiple of 32, at most 65536.  tau >= 0 (0 keeps every stored block).  opts as
  * for sp2_create (corrections, refine_steps and refine_fp64 are ignored).  Workspace is
- * about 10 KB per block of (N/32)^2, i.e. ~11 GB at N = 32768. */
+ * about 10 KB per block of (N/32)^2, i.e. ~11 GB at N = 32768.  Rule SP2_TRUNC_BLOCK. */
 sp2_status sp2_create_bsr(int64_t N, int64_t n_occ, double tau, const sp2_opts* opts, sp2_bsr* out);
+
+/* As sp2_create_bsr with the truncation rule `rule` (an sp2_trunc_rule; anything else is
+ * SP2_ERR_INVALID_ARG). */
+sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, int32_t rule, const sp2_opts* opts,
+                             sp2_bsr* out);
 
 /* F as BSR in device memory: row_ptr [N/32 + 1] (int32), col_idx [nnzb] (int32, sorted
  * in each block row, every diagonal block present), vals [nnzb][32][32] (FP64, row-major

@@ -28,10 +28,13 @@ int32_t sp2_test_tc_gemm(const void* arena_dev, int32_t ld, int32_t nslots, int3
                          int32_t upper, int32_t tile, float* out_dev, void* stream);
 
 /* Block truncation decision of the block-sparse path on its own: for every 32 x 32 block
- * (I, J) of the dense N x N FP32 device matrix, keep_dev[I * (N/32) + J] = 1 if I == J or
- * ||block||_F^2 >= tau^2 (FP64, the fixed summation order of sp2_create_bsr), else 0.
- * Synchronises `stream`. */
-int32_t sp2_test_bsr_keep(const float* dense_dev, int64_t N, double tau, uint8_t* keep_dev, void* stream);
+ * (I, J) of the dense, symmetric N x N FP32 device matrix, keep_dev[I * (N/32) + J] = 1 if
+ * the block is kept, else 0, under `rule` (an sp2_trunc_rule of sp2.h): SP2_TRUNC_BLOCK
+ * keeps I == J or ||block||_F^2 >= tau^2 (FP64, the fixed summation order of
+ * sp2_create_bsr); SP2_TRUNC_ERROR runs the error-controlled selection of the device loop
+ * over the upper blocks (I, J >= I) in row-major order.  Synchronises `stream`. */
+int32_t sp2_test_bsr_keep(const float* dense_dev, int64_t N, double tau, int32_t rule, uint8_t* keep_dev,
+                          void* stream);
 
 /* Symbolic square of the block-sparse path on its own: mask_host is an nb x nb 0/1 block
  * pattern (host, row-major); upper_host receives the pattern of its square restricted to

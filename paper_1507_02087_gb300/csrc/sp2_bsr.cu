@@ -12,9 +12,11 @@
 //      the FP64 partials of ||X~_{k-1} - S||_F^2 and Tr[X_k], and ||X_IJ||_F^2 of the
 //      new block in a fixed order (row sums left to right, rows top to bottom);
 //   3. stop test on the device (Alg. 3, with the trace guard);
-//   4. truncation: off-diagonal blocks with ||X_IJ||_F^2 < tau^2 are dropped, the
-//      kept bitmap is set for (I, J) and (J, I), and X~_k is written as BSR (each kept
-//      upper block and its transpose at the rank of its column in its row).
+//   4. truncation: off-diagonal blocks with ||X_IJ||_F^2 < tau^2 are dropped (rule 0),
+//      or the longest prefix in (||X_IJ||_F^2, I, J) order whose doubled norms add up to
+//      at most tau^2 (rule 1, error-controlled: ||E||_F <= tau, sums in exact integer
+//      units); the kept bitmap is set for (I, J) and (J, I), and X~_k is written as BSR
+//      (each kept upper block and its transpose at the rank of its column in its row).
 //
 // All index work is integer and fixed-order, so the pattern of every iterate is
 // reproducible bit for bit (and equals the host's, given the same stored blocks).
@@ -256,7 +258,8 @@ __device__ __forceinline__ double block_norm2_fixed(const float* blk) {
 // truncation decision (Alg. 1: X~_0 = X_0 + E_0).
 __global__ void __launch_bounds__(NT)
 bsr_scale_pairs_kernel(const DevState* st, const int* frp, const uint32_t* fbits, const int* frank,
-                       const double* fvals, int W, Pairs P, float* svals, uint8_t* skeep, double tau2) {
+                       const double* fvals, int W, Pairs P, float* svals, uint8_t* skeep, double* sn2,
+                       double tau2) {
   __shared__ float blk[B * (B + 1)];
   if (st->done) return;
   const int nnz = *P.nnz;
@@ -275,7 +278,10 @@ bsr_scale_pairs_kernel(const DevState* st, const int* frp, const uint32_t* fbits
     __syncthreads();
     if (threadIdx.x < 32) {
       const double n2 = block_norm2_fixed(blk);
-      if (threadIdx.x == 0) skeep[q] = (I == J || n2 >= tau2) ? 1 : 0;
+      if (threadIdx.x == 0) {
+        skeep[q] = (I == J || n2 >= tau2) ? 1 : 0;
+        sn2[q] = n2;
+      }
     }
     __syncthreads();
   }
@@ -300,7 +306,7 @@ __global__ void bsr_sym_kernel(DevState* st, Mat X, int nb, int W, uint32_t* sbi
 // ---- numeric square + SP2 epilogue + truncation decision -----------------------------------
 __global__ void __launch_bounds__(NT)
 bsr_numeric_kernel(const DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* skeep, double* spart,
-                   double tau2) {
+                   double* sn2, double tau2) {
   __shared__ float As[2][B * (B + 1)];
   __shared__ float Bs[2][B * (B + 1)];
   __shared__ int kI[MAX_NB], kJ[MAX_NB];
@@ -395,9 +401,106 @@ bsr_numeric_kernel(const DevState* st, Mat X, int W, Pairs P, float* svals, uint
         spart[2 * (int64_t)q] = (I == J ? 1.0 : 2.0) * v2;
         spart[2 * (int64_t)q + 1] = tr;
         skeep[q] = (I == J || n2 >= tau2) ? 1 : 0;
+        sn2[q] = n2;
       }
     }
     __syncthreads();
+  }
+}
+
+// ---- error-controlled truncation (rule 1) ------------------------------------------------
+// Candidates are the off-diagonal pairs with 2 n2 <= tau^2; the candidate of pair q weighs
+// u_q = floor(2 n2_q / 2^(e-40)) units (2^e <= tau^2 < 2^(e+1)), the budget is
+// floor(tau^2 / 2^(e-40)).  The pairs with key (n2 bits, q) <= K* are dropped, K* the
+// largest key whose prefix sum is within the budget.  Integer sums do not depend on the
+// summation order, so one CTA finds K* by bisection: first over the bit pattern of n2
+// (non-negative doubles order like their bit patterns), then over q within the first
+// value that no longer fits.  The pair list is in (I, J) order, so q breaks ties as (I, J)
+// does.  `cbits` (nnz entries of scratch) caches each pair's candidate bits (~0 if none).
+constexpr int kEC = 512;
+
+__device__ __forceinline__ uint64_t ec_units(uint64_t bits, int e) {
+  return (uint64_t)floor(ldexp(__longlong_as_double((long long)bits), 41 - e));
+}
+
+__device__ __forceinline__ uint64_t ec_block_sum(uint64_t v, uint64_t* red) {
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint64_t t = threadIdx.x < kEC / 32 ? red[threadIdx.x] : 0ull;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) red[32] = t;
+  }
+  __syncthreads();
+  const uint64_t out = red[32];
+  __syncthreads();
+  return out;
+}
+
+__global__ void __launch_bounds__(kEC)
+bsr_errctl_kernel(const DevState* st, const double* n2, const int* row, const int* col, const int* nnz_p,
+                  uint64_t* cbits, uint8_t* keep, double tau2) {
+  __shared__ uint64_t red[33];
+  if (st && !st->iter_active) return;
+  const int nnz = *nnz_p;
+  const int tid = threadIdx.x;
+  constexpr uint64_t kNone = ~0ull;
+  if (!(tau2 > 0.0)) {
+    for (int q = tid; q < nnz; q += kEC) keep[q] = 1;
+    return;
+  }
+  const int e = ilogb(tau2);     // 2^e <= tau^2 < 2^(e+1)
+  const uint64_t budget = (uint64_t)floor(ldexp(tau2, 40 - e));
+  uint64_t acc = 0;
+  for (int q = tid; q < nnz; q += kEC) {
+    const double v = n2[q];
+    const bool c = row[q] != col[q] && 2.0 * v <= tau2;
+    const uint64_t b = c ? (uint64_t)__double_as_longlong(v) : kNone;
+    cbits[q] = b;
+    if (c) acc += ec_units(b, e);
+  }
+  const uint64_t total = ec_block_sum(acc, red);
+  uint64_t gbits = kNone;   // candidates with bits < gbits are dropped ...
+  int qstar = -1;           // ... and those with bits == gbits and q <= qstar
+  if (total > budget) {
+    // invariant: S(lo) <= budget < S(hi), S(t) = units of the candidates with bits <= t
+    uint64_t lo = 0, hi = (uint64_t)__double_as_longlong(tau2);
+    while (hi - lo > 1) {
+      const uint64_t mid = lo + (hi - lo) / 2;
+      acc = 0;
+      for (int q = tid; q < nnz; q += kEC) {
+        const uint64_t b = cbits[q];
+        if (b <= mid) acc += ec_units(b, e);
+      }
+      if (ec_block_sum(acc, red) <= budget) lo = mid;
+      else hi = mid;
+    }
+    acc = 0;
+    for (int q = tid; q < nnz; q += kEC) {
+      const uint64_t b = cbits[q];
+      if (b <= lo) acc += ec_units(b, e);
+    }
+    const uint64_t base = ec_block_sum(acc, red);
+    // within the value hi (the first that does not fit whole): the longest prefix in q
+    int qlo = -1, qhi = nnz - 1;
+    while (qhi - qlo > 1) {
+      const int mid = qlo + (qhi - qlo) / 2;
+      acc = 0;
+      for (int q = tid; q <= mid; q += kEC)
+        if (cbits[q] == hi) acc += ec_units(hi, e);
+      if (base + ec_block_sum(acc, red) <= budget) qlo = mid;
+      else qhi = mid;
+    }
+    gbits = hi;
+    qstar = qlo;
+  }
+  for (int q = tid; q < nnz; q += kEC) {
+    const uint64_t b = cbits[q];
+    const bool drop = b != kNone && (b < gbits || (b == gbits && q <= qstar));
+    keep[q] = drop ? 0 : 1;
   }
 }
 
@@ -493,6 +596,7 @@ struct sp2_bsr_ctx {
   int64_t N = 0, nocc = 0;
   int nb = 0, W = 0;
   double tau = 0.0;
+  int rule = 0;                  // sp2_trunc_rule
   sp2_opts opts{};
   int device = 0;
   int64_t cap = 0, cap_s = 0;
@@ -501,7 +605,8 @@ struct sp2_bsr_ctx {
   uint32_t* sbits = nullptr;
   float* svals = nullptr;
   uint8_t* skeep = nullptr;
-  double* spart = nullptr;
+  double* spart = nullptr;       // per-pair partials; also the candidate scratch of rule 1
+  double* sn2 = nullptr;         // per-pair ||X_IJ||_F^2 of the newest blocks
   int* counts = nullptr;
   uint32_t* fbits = nullptr;
   int* frank = nullptr;
@@ -541,7 +646,8 @@ static void bsr_free(sp2_bsr_ctx* h) {
   }
   cudaFree(h->S.ptr); cudaFree(h->S.col); cudaFree(h->S.row); cudaFree(h->S.nnz);
   cudaFree(h->FP.ptr); cudaFree(h->FP.col); cudaFree(h->FP.row); cudaFree(h->FP.nnz);
-  cudaFree(h->sbits); cudaFree(h->svals); cudaFree(h->skeep); cudaFree(h->spart); cudaFree(h->counts);
+  cudaFree(h->sbits); cudaFree(h->svals); cudaFree(h->skeep); cudaFree(h->spart); cudaFree(h->sn2);
+  cudaFree(h->counts);
   cudaFree(h->fbits); cudaFree(h->frank); cudaFree(h->glo); cudaFree(h->ghi); cudaFree(h->gbad);
   cudaFree(h->st_dev);
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -582,8 +688,12 @@ static cudaError_t add_round(sp2_bsr_ctx* h, cudaGraph_t g, cudaStream_t s, int 
   scan_kernel<<<1, 1024, 0, s>>>(h->counts, nb, h->S.ptr, sn, st);
   fill_pairs_kernel<<<nb, 32, 0, s>>>(h->sbits, nb, W, up, h->S, st);
   // 2. numeric + 3. stop test
-  bsr_numeric_kernel<<<grid_persistent(), NT, 0, s>>>(st, Xc, W, h->S, h->svals, h->skeep, h->spart, tau2);
+  bsr_numeric_kernel<<<grid_persistent(), NT, 0, s>>>(st, Xc, W, h->S, h->svals, h->skeep, h->spart, h->sn2,
+                                                       tau2);
   bsr_finalize_kernel<<<1, 1024, 0, s>>>(st, h->spart, sn, h->cond, use_cond);
+  if (h->rule == SP2_TRUNC_ERROR)
+    bsr_errctl_kernel<<<1, kEC, 0, s>>>(st, h->sn2, h->S.row, h->S.col, sn, reinterpret_cast<uint64_t*>(h->spart),
+                                        h->skeep, tau2);
   // 4. truncation -> next iterate
   clear_words_kernel<<<256, 256, 0, s>>>(Xn.bits, (int64_t)nb * W, st);
   set_kept_bits_kernel<<<grid_persistent(), 256, 0, s>>>(st, h->S, h->skeep, W, Xn.bits);
@@ -623,9 +733,16 @@ static sp2_status build_graph(sp2_bsr_ctx* h) {
 }
 
 extern "C" sp2_status sp2_create_bsr(int64_t N, int64_t n_occ, double tau, const sp2_opts* opts, sp2_bsr* out) {
+  return sp2_create_bsr_ex(N, n_occ, tau, SP2_TRUNC_BLOCK, opts, out);
+}
+
+extern "C" sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, int32_t rule, const sp2_opts* opts,
+                                        sp2_bsr* out) {
   if (!out) return SP2_ERR_INVALID_ARG;
   *out = nullptr;
-  if (N < B || N % B != 0 || N / B > MAX_NB || n_occ < 0 || n_occ > N || !(tau >= 0.0)) return SP2_ERR_INVALID_ARG;
+  if (N < B || N % B != 0 || N / B > MAX_NB || n_occ < 0 || n_occ > N || !(tau >= 0.0) ||
+      (rule != SP2_TRUNC_BLOCK && rule != SP2_TRUNC_ERROR))
+    return SP2_ERR_INVALID_ARG;
   sp2_opts o;
   sp2_default_opts(&o);
   if (opts) o = *opts;
@@ -634,7 +751,7 @@ extern "C" sp2_status sp2_create_bsr(int64_t N, int64_t n_occ, double tau, const
     return SP2_ERR_INVALID_ARG;
   sp2_bsr_ctx* h = new (std::nothrow) sp2_bsr_ctx();
   if (!h) return SP2_ERR_NOMEM;
-  h->N = N; h->nocc = n_occ; h->tau = tau; h->opts = o;
+  h->N = N; h->nocc = n_occ; h->tau = tau; h->rule = rule; h->opts = o;
   h->nb = (int)(N / B);
   h->W = (h->nb + 31) / 32;
   h->cap = (int64_t)h->nb * h->nb;
@@ -661,6 +778,7 @@ extern "C" sp2_status sp2_create_bsr(int64_t N, int64_t n_occ, double tau, const
        cudaMalloc(&h->svals, sizeof(float) * BE * h->cap_s) == cudaSuccess &&
        cudaMalloc(&h->skeep, h->cap_s) == cudaSuccess &&
        cudaMalloc(&h->spart, sizeof(double) * 2 * h->cap_s) == cudaSuccess &&
+       cudaMalloc(&h->sn2, sizeof(double) * h->cap_s) == cudaSuccess &&
        cudaMalloc(&h->counts, sizeof(int) * nb) == cudaSuccess &&
        cudaMalloc(&h->fbits, sizeof(uint32_t) * nb * W) == cudaSuccess &&
        cudaMalloc(&h->frank, sizeof(int) * nb * W) == cudaSuccess &&
@@ -708,7 +826,10 @@ extern "C" sp2_status sp2_run_bsr(sp2_bsr h, const int32_t* row_ptr_dev, const i
   scan_kernel<<<1, 1024, 0, s>>>(h->counts, nb, h->FP.ptr, h->FP.nnz, nullptr);
   fill_pairs_kernel<<<nb, 32, 0, s>>>(h->fbits, nb, W, 1, h->FP, nullptr);
   bsr_scale_pairs_kernel<<<grid_persistent(), NT, 0, s>>>(st, row_ptr_dev, h->fbits, h->frank, vals_dev, W, h->FP,
-                                                           h->svals, h->skeep, tau2);
+                                                           h->svals, h->skeep, h->sn2, tau2);
+  if (h->rule == SP2_TRUNC_ERROR)
+    bsr_errctl_kernel<<<1, kEC, 0, s>>>(nullptr, h->sn2, h->FP.row, h->FP.col, h->FP.nnz,
+                                        reinterpret_cast<uint64_t*>(h->spart), h->skeep, tau2);
   Mat X0 = h->X[0];
   BSR_TRY(cudaMemsetAsync(X0.bits, 0, sizeof(uint32_t) * nb * W, s));
   set_kept_bits_kernel<<<grid_persistent(), 256, 0, s>>>(nullptr, h->FP, h->skeep, W, X0.bits);
@@ -771,7 +892,7 @@ extern "C" sp2_status sp2_get_info_bsr(sp2_bsr h, sp2_info* out, int64_t* nnzb_o
 // ---- test hooks: the index work on its own ----------------------------------------------------
 namespace sp2 {
 namespace bsr {
-__global__ void test_keep_kernel(const float* dense, int nb, double tau2, uint8_t* keep) {
+__global__ void test_keep_kernel(const float* dense, int nb, double tau2, uint8_t* keep, double* n2_out) {
   __shared__ float blk[B * (B + 1)];
   const int I = blockIdx.x / nb, J = blockIdx.x % nb;
   const int N = nb * B;
@@ -780,7 +901,25 @@ __global__ void test_keep_kernel(const float* dense, int nb, double tau2, uint8_
   __syncthreads();
   if (threadIdx.x < 32) {
     const double n2 = block_norm2_fixed(blk);
-    if (threadIdx.x == 0) keep[blockIdx.x] = (I == J || n2 >= tau2) ? 1 : 0;
+    if (threadIdx.x == 0) {
+      keep[blockIdx.x] = (I == J || n2 >= tau2) ? 1 : 0;
+      n2_out[blockIdx.x] = n2;
+    }
+  }
+}
+
+// upper pairs (row-major) of an nb x nb block matrix: gather their norms, scatter decisions
+__global__ void test_pairs_gather_kernel(const double* n2_full, int nb, const int* row, const int* col, int npairs,
+                                         double* n2p) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += gridDim.x * blockDim.x)
+    n2p[q] = n2_full[(int64_t)row[q] * nb + col[q]];
+}
+
+__global__ void test_pairs_scatter_kernel(const uint8_t* keepp, int nb, const int* row, const int* col, int npairs,
+                                          uint8_t* keep) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += gridDim.x * blockDim.x) {
+    keep[(int64_t)row[q] * nb + col[q]] = keepp[q];
+    keep[(int64_t)col[q] * nb + row[q]] = keepp[q];
   }
 }
 }  // namespace bsr
@@ -790,13 +929,45 @@ __global__ void test_keep_kernel(const float* dense, int nb, double tau2, uint8_
 
 #include "../../include/sp2_testing.h"
 
-extern "C" int32_t sp2_test_bsr_keep(const float* dense_dev, int64_t N, double tau, uint8_t* keep_dev,
+extern "C" int32_t sp2_test_bsr_keep(const float* dense_dev, int64_t N, double tau, int32_t rule, uint8_t* keep_dev,
                                      void* stream) {
-  if (!dense_dev || !keep_dev || N < B || N % B || N / B > MAX_NB || !(tau >= 0.0)) return SP2_ERR_INVALID_ARG;
+  if (!dense_dev || !keep_dev || N < B || N % B || N / B > MAX_NB || !(tau >= 0.0) ||
+      (rule != SP2_TRUNC_BLOCK && rule != SP2_TRUNC_ERROR))
+    return SP2_ERR_INVALID_ARG;
   const int nb = (int)(N / B);
   cudaStream_t s = (cudaStream_t)stream;
-  test_keep_kernel<<<nb * nb, 64, 0, s>>>(dense_dev, nb, tau * tau, keep_dev);
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+  const int npairs = nb * (nb + 1) / 2;
+  std::vector<int> row(npairs), col(npairs);
+  for (int I = 0, q = 0; I < nb; ++I)
+    for (int J = I; J < nb; ++J, ++q) { row[q] = I; col[q] = J; }
+  double *n2_full = nullptr, *n2p = nullptr;
+  uint64_t* scratch = nullptr;
+  int *drow = nullptr, *dcol = nullptr, *dnp = nullptr;
+  uint8_t* keepp = nullptr;
+  bool ok = cudaMalloc(&n2_full, sizeof(double) * nb * nb) == cudaSuccess &&
+            cudaMalloc(&n2p, sizeof(double) * npairs) == cudaSuccess &&
+            cudaMalloc(&scratch, sizeof(uint64_t) * npairs) == cudaSuccess &&
+            cudaMalloc(&drow, sizeof(int) * npairs) == cudaSuccess &&
+            cudaMalloc(&dcol, sizeof(int) * npairs) == cudaSuccess && cudaMalloc(&dnp, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&keepp, npairs) == cudaSuccess;
+  if (ok) {
+    test_keep_kernel<<<nb * nb, 64, 0, s>>>(dense_dev, nb, tau * tau, keep_dev, n2_full);
+    ok = cudaGetLastError() == cudaSuccess;
+  }
+  if (ok && rule == SP2_TRUNC_ERROR) {
+    ok = cudaMemcpyAsync(drow, row.data(), sizeof(int) * npairs, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+         cudaMemcpyAsync(dcol, col.data(), sizeof(int) * npairs, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+         cudaMemcpyAsync(dnp, &npairs, sizeof(int), cudaMemcpyHostToDevice, s) == cudaSuccess;
+    if (ok) {
+      test_pairs_gather_kernel<<<256, 256, 0, s>>>(n2_full, nb, drow, dcol, npairs, n2p);
+      bsr_errctl_kernel<<<1, kEC, 0, s>>>(nullptr, n2p, drow, dcol, dnp, scratch, keepp, tau * tau);
+      test_pairs_scatter_kernel<<<256, 256, 0, s>>>(keepp, nb, drow, dcol, npairs, keep_dev);
+      ok = cudaGetLastError() == cudaSuccess;
+    }
+  }
+  ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+  cudaFree(n2_full); cudaFree(n2p); cudaFree(scratch); cudaFree(drow); cudaFree(dcol); cudaFree(dnp); cudaFree(keepp);
+  if (!ok) {
     (void)cudaGetLastError();
     return SP2_ERR_CUDA;
   }

@@ -87,13 +87,16 @@ def lib() -> ctypes.CDLL:
         L.sp2_destroy_batch.restype = None
         L.sp2_create_bsr.argtypes = [i64, i64, ctypes.c_double, ctypes.POINTER(sp2_opts), ctypes.POINTER(vp)]
         L.sp2_create_bsr.restype = i32
+        L.sp2_create_bsr_ex.argtypes = [i64, i64, ctypes.c_double, i32, ctypes.POINTER(sp2_opts),
+                                        ctypes.POINTER(vp)]
+        L.sp2_create_bsr_ex.restype = i32
         L.sp2_run_bsr.argtypes = [vp, vp, vp, vp, i64, vp, vp]
         L.sp2_run_bsr.restype = i32
         L.sp2_get_info_bsr.argtypes = [vp, ctypes.POINTER(sp2_info), ctypes.POINTER(i64)]
         L.sp2_get_info_bsr.restype = i32
         L.sp2_destroy_bsr.argtypes = [vp]
         L.sp2_destroy_bsr.restype = None
-        L.sp2_test_bsr_keep.argtypes = [vp, i64, ctypes.c_double, vp, vp]
+        L.sp2_test_bsr_keep.argtypes = [vp, i64, ctypes.c_double, i32, vp, vp]
         L.sp2_test_bsr_keep.restype = i32
         L.sp2_test_bsr_square_pattern.argtypes = [vp, i32, vp]
         L.sp2_test_bsr_square_pattern.restype = i32
@@ -216,15 +219,20 @@ def sp2_destroy(h: int) -> None:
         lib().sp2_destroy(h)
 
 
+TRUNC_RULES = {"block": 0, "error": 1}
+
+
 class BsrPurifier:
-    """Block-sparse F (32 x 32 blocks, BSR) -> D with block truncation tau."""
+    """Block-sparse F (32 x 32 blocks, BSR) -> D with block truncation tau.
+    rule: "block" (drop blocks with norm below tau) or "error" (||E||_F <= tau)."""
 
     def __init__(self, N: int, nocc: int, tau: float, max_iter: int = 200, guard: bool = True,
-                 qtilde: float = 1.8, launch_mode: int | None = None):
+                 qtilde: float = 1.8, launch_mode: int | None = None, rule: str = "block"):
         o = _opts(max_iter, guard, qtilde, 1, 0, False, launch_mode)
         h = ctypes.c_void_p()
-        _check(lib().sp2_create_bsr(N, nocc, tau, ctypes.byref(o), ctypes.byref(h)), "sp2_create_bsr")
-        self.N, self.nocc, self.tau, self.h = N, nocc, tau, h.value
+        _check(lib().sp2_create_bsr_ex(N, nocc, tau, TRUNC_RULES[rule], ctypes.byref(o), ctypes.byref(h)),
+               "sp2_create_bsr_ex")
+        self.N, self.nocc, self.tau, self.rule, self.h = N, nocc, tau, rule, h.value
 
     def run(self, row_ptr, col_idx, vals, D=None, dense=True, stream=None):
         """row_ptr/col_idx: CUDA int32 tensors, vals: CUDA float64 [nnzb, 32, 32]."""

@@ -40,12 +40,74 @@ def test_truncation_decision_bit_exact(sp2mod):
             blk *= tau * f / np.linalg.norm(blk)
     X32 = X.astype(np.float32)
     keep_gpu = torch.zeros(nb * nb, dtype=torch.uint8, device="cuda")
-    rc = sp2mod.lib().sp2_test_bsr_keep(torch.from_numpy(X32).cuda().data_ptr(), N, tau, keep_gpu.data_ptr(),
+    rc = sp2mod.lib().sp2_test_bsr_keep(torch.from_numpy(X32).cuda().data_ptr(), N, tau, 0, keep_gpu.data_ptr(),
                                         torch.cuda.current_stream().cuda_stream)
     assert rc == 0
     keep_ref = bo.keep_mask(X32.astype(np.float64), b, tau)
     assert np.array_equal(keep_gpu.cpu().numpy().reshape(nb, nb).astype(bool), keep_ref)
     assert 0 < keep_ref.sum() < nb * nb
+
+
+def _keep_gpu(sp2mod, X32, tau, rule):
+    N = X32.shape[0]
+    nb = N // 32
+    keep = torch.zeros(nb * nb, dtype=torch.uint8, device="cuda")
+    rc = sp2mod.lib().sp2_test_bsr_keep(torch.from_numpy(np.ascontiguousarray(X32)).cuda().data_ptr(), N, tau,
+                                        rule, keep.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    return keep.cpu().numpy().reshape(nb, nb).astype(bool)
+
+
+@pytest.mark.parametrize("nb,seed", [(3, 1), (24, 2), (90, 3)])
+def test_error_truncation_decision_bit_exact(sp2mod, nb, seed):
+    # symmetric block matrix with block norms spread over many decades, exact ties
+    # (repeated blocks), zero blocks, and budgets that cut inside a tie group
+    g = np.random.Generator(np.random.PCG64(seed))
+    b = 32
+    X = np.zeros((nb * b, nb * b))
+    proto = g.standard_normal((b, b))
+    for I in range(nb):
+        for J in range(I, nb):
+            kind = g.integers(0, 4)
+            if kind == 0:
+                blk = g.standard_normal((b, b)) * 10.0 ** g.uniform(-9, 0)
+            elif kind == 1:
+                blk = proto * 1e-5                       # the same block many times: exact ties
+            elif kind == 2:
+                blk = np.zeros((b, b))
+            else:
+                blk = g.standard_normal((b, b)) * 1e-4
+            if I == J:
+                blk = 0.5 * (blk + blk.T) + np.eye(b)
+            X[I * b:(I + 1) * b, J * b:(J + 1) * b] = blk
+            X[J * b:(J + 1) * b, I * b:(I + 1) * b] = blk.T
+    X32 = X.astype(np.float32)
+    n2 = bo.block_norms2(X32.astype(np.float64), b)
+    tie = float(np.float64(np.linalg.norm((proto * 1e-5).astype(np.float32).astype(np.float64)) ** 2))
+    for tau in (0.0, 1e-7, 1e-4, 3e-3, np.sqrt(7.5 * tie), 1e3):
+        keep_gpu = _keep_gpu(sp2mod, X32, tau, 1)
+        keep_ref = bo.keep_mask_error(X32.astype(np.float64), b, tau)
+        assert np.array_equal(keep_gpu, keep_ref), tau
+        E = X32.astype(np.float64) * np.kron(~keep_ref, np.ones((b, b)))
+        assert np.linalg.norm(E) <= tau * (1 + 1e-9) + 1e-300
+    assert n2.size == nb * nb
+
+
+@pytest.mark.parametrize("dims,tau,tol", [((32, 8, 4), 1e-6, 4e-6), ((32, 8, 8), 1e-4, 4e-6)])
+def test_bsr_error_rule_against_oracle(sp2mod, dims, tau, tol):
+    tb, (rp, ci, vals) = tb_case(dims)
+    F = tb.dense().numpy()
+    ref = bo.sp2_bsr(F, tb.nocc, 32, tau, rule="error")
+    with sp2mod.BsrPurifier(tb.N, tb.nocc, tau, rule="error") as P:
+        D = P.run(rp, ci, vals)
+        info = P.info()
+    assert info["status"] == 0
+    assert info["stop_reason"] in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
+    assert ref.n - 3 <= info["n_iter"] <= ref.n + 3
+    err = o.rel_error(D.cpu().numpy(), ref.D, tb.nocc)
+    assert err <= tol, err
+    Dn = D.cpu().numpy()
+    assert np.array_equal(Dn, Dn.T)
 
 
 @pytest.mark.parametrize("nb,density", [(1, 1.0), (5, 0.4), (70, 0.08), (130, 0.03)])
