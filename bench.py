@@ -42,6 +42,11 @@ def workload_name(N, nocc, gap):
     return f"dense N={N} nocc={nocc} gap={gap:g}, random-Q (QR of seeded Gaussian, seed 0)"
 
 
+# DRAM bytes (read + write) of one forward-square launch from an ncu capture of the current
+# kernel (profiles/tc_gemm_pair_sp2_forward_dram_ld8192.md), keyed by (N, tile kind).
+FWD_TRAFFIC_BYTES = {(8192, "pair"): 2.22e9 + 0.3881e9}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -269,6 +274,12 @@ def run_batch(a, ws, rank, local):
         clk = clocks.stop()
     ms = max_over_ranks(ms, ws)
     flops = sum(useful_flops(N, i["hist_len"], i["n_iter"], True, 2) for N, i in zip(Ns, infos))
+    # the tuner's choice against both fixed tile kinds on the same batch
+    tiles = {"tuned": infos[0]["tile"]}
+    for t in ("128", "pair"):
+        with sp2.BatchPurifier(Ns, noccs, "mixed", tile=t) as Bt:
+            timed(Bt, 1)
+            tiles[t + "_ms"] = timed(Bt, max(1, a.steps))[0]
     fp64 = None
     if a.fp64_steps > 0:
         with sp2.BatchPurifier(Ns, noccs, "fp64") as B64:
@@ -285,7 +296,7 @@ def run_batch(a, ws, rank, local):
             "max_err_vs_exact": err, "meets_tolerance": bool(err <= TOL),
             "tflops_useful": flops / (ms * 1e-3) / 1e12,
             "n_iter_range": [min(i["n_iter"] for i in infos), max(i["n_iter"] for i in infos)],
-            "fp64_path": fp64, "clocks": clk}), flush=True)
+            "tiles": tiles, "fp64_path": fp64, "clocks": clk}), flush=True)
 
 
 def run_bsr(a, ws, rank, local):
@@ -415,17 +426,19 @@ def main():
                 Pf.run(F, D, stream)
                 fi = Pf.info()
                 kt.append(fi["loop_ms"] / fi["hist_len"])
+            tile_used = fi["tile"]
         kern_ms = statistics.mean(kt)
         alg = SPLIT_PRODUCTS * N * N * (N + 1)        # six bf16 piece products of an upper-triangle square
         achieved = alg / (kern_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
-        ld = -(-N // 128) * 128
-        kname = "tc_gemm_pair_kernel (256x256 tiles per SM pair" if ld % 256 == 0 else "tc_gemm_kernel (128x128 tiles"
+        kname = ("tc_gemm_pair_kernel (256x256 tiles per SM pair" if tile_used == "pair"
+                 else "tc_gemm_kernel (128x128 tiles per SM")
         roofline = {"bound": "tensor", "kernel": kname + ", forward square, MODE_SP2_STEP)",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "ms_per_launch": kern_ms,
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
-                    "algorithmic_flops_per_launch": alg, "traffic": None}
+                    "algorithmic_flops_per_launch": alg,
+                    "traffic": FWD_TRAFFIC_BYTES.get((N, tile_used))}
     else:
         kern_ms = statistics.mean(l / s for l, s in zip(loop_ms, [i["hist_len"] for i in infos]))
         mhz = clk.get("sm_mhz") or SM_MAX_MHZ

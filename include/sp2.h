@@ -90,10 +90,14 @@ typedef struct {
                            6 ld^2 bytes), 2 = keep 11 slots and recompute X_i during the derivative
                            pass (one more square per derivative step, bit-identical result);
                            automatic keeps every iterate when that fits in 60% of free memory */
-  int32_t tile;         /* SP2_PREC_MIXED tensor-core tiles: 0 = automatic (default: 2 when every
-                           problem's ld is a multiple of 256, else 1), 1 = 128 x 128 output tiles,
-                           one per SM, 2 = 256 x 256 tiles, one per pair of SMs (cta_group::2
-                           MMAs; ld rounded up to a multiple of 256) */
+  int32_t tile;         /* SP2_PREC_MIXED tensor-core tiles: 1 = 128 x 128 output tiles, one per
+                           SM (ld = N rounded up to a multiple of 128); 2 = 256 x 256 tiles, one
+                           per pair of SMs (cta_group::2 MMAs; ld rounded up to a multiple of
+                           256); 0 = tuned (default): at create time one tensor-core product of
+                           the handle's problems is timed with each choice on scratch memory and
+                           the faster one is kept (when the scratch would exceed 2 GiB, a model
+                           of the two kernels' measured rates decides instead); the choice is
+                           reported in sp2_info.tile */
 } sp2_opts;
 
 #define SP2_MAX_ITER 512
@@ -110,6 +114,9 @@ typedef struct {
   const double*  v;        /* v[i] = ||X_i - X_i^2||_F, i < hist_len (host memory owned by the handle) */
   const double*  trace;    /* trace[i] = Tr[X_i], i <= n_iter */
   const uint8_t* p;        /* p[i] in {0,1} for 1 <= i <= n_iter: 1 = X^2, 0 = 2X - X^2 */
+  int32_t tile;            /* SP2_PREC_MIXED: tensor-core tiles in use, 1 = 128 x 128 per SM,
+                              2 = 256 x 256 per SM pair (as chosen by sp2_opts.tile or its
+                              tuner); 0 on the other paths */
 } sp2_info;
 
 typedef struct sp2_ctx* sp2_handle;

@@ -92,6 +92,101 @@ static sp2_status add_while(cudaGraph_t g, const cudaGraphNode_t* deps, int ndep
 }
 
 // ---------------------------------------------------------------------------------------------
+// Tile tuner for the mixed path: 1 = 128 x 128 tiles (ld a multiple of 128), 2 = 256 x 256
+// CTA-pair tiles (ld a multiple of 256).  Each candidate runs the same product a forward
+// square runs (every problem's upper tiles, pieces out, mirror written) on zeroed scratch
+// shaped like the handle's problems, one launch untimed and three timed; the faster one is
+// kept.  When the scratch would exceed kTuneBytes, a model of the kernels' measured
+// algorithmic rates at large sizes (1200 and 1580 TFLOP/s) decides instead.
+static constexpr size_t kTuneBytes = size_t(2) << 30;
+
+static int round_up(int64_t n, int a) { return (int)((n + a - 1) / a * a); }
+
+static int tune_tiles(const std::vector<int64_t>& N) {
+  using namespace sp2::tc;
+  const int count = (int)N.size();
+  double model[3] = {0.0, 0.0, 0.0};
+  size_t bytes[3] = {0, 0, 0};
+  for (int c = 1; c <= 2; ++c)
+    for (int k = 0; k < count; ++k) {
+      const double ld = round_up(N[k], c == 2 ? PT : LD_ALIGN);
+      model[c] += ld * ld * ld / (c == 2 ? 1580.0 : 1200.0);
+      bytes[c] += (size_t)2 * NP * (size_t)ld * (size_t)ld * 2;
+    }
+  const int by_model = model[2] < model[1] ? 2 : 1;
+  if (std::max(bytes[1], bytes[2]) > kTuneBytes) return by_model;
+
+  float best[3] = {0.f, 0.f, 0.f};
+  cudaStream_t s = nullptr;
+  void* scratch = nullptr;
+  Instance* dinst = nullptr;
+  int32_t* err = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaMalloc(&scratch, std::max(bytes[1], bytes[2])) == cudaSuccess &&
+            cudaMalloc(&dinst, sizeof(Instance) * count) == cudaSuccess &&
+            cudaMalloc(&err, sizeof(int32_t)) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+            cudaEventCreate(&e1) == cudaSuccess &&
+            cudaMemsetAsync(scratch, 0, std::max(bytes[1], bytes[2]), s) == cudaSuccess &&
+            cudaMemsetAsync(err, 0, sizeof(int32_t), s) == cudaSuccess;
+  std::vector<Instance> hinst(count);
+  for (int c = 1; c <= 2 && ok; ++c) {
+    const int pair = c == 2;
+    size_t off = 0;
+    int tiles = 0;
+    for (int k = 0; k < count && ok; ++k) {
+      Instance& I = hinst[k];
+      std::memset(&I, 0, sizeof(I));
+      const int ld = round_up(N[k], pair ? PT : LD_ALIGN);
+      __nv_bfloat16* arena = (__nv_bfloat16*)((char*)scratch + off);
+      off += (size_t)2 * NP * (size_t)ld * (size_t)ld * 2;
+      I.ld = ld;
+      I.arena = arena;
+      I.slot_elems = (int64_t)NP * ld * ld;
+      I.tile_off_upper = I.tile_off_upper2 = tiles;
+      tiles += sp2::tc_tiles(ld, 1, pair);
+      ok = sp2::tc_make_maps(arena, ld, 2, &I.mapA, &I.mapB) == cudaSuccess;
+    }
+    if (!ok) break;
+    Job j;
+    std::memset(&j, 0, sizeof(j));
+    j.mode = MODE_STORE_PIECES;
+    j.upper = 1;
+    j.nterms = 1;
+    j.rule = SLOTS_FIXED;
+    j.count = count;
+    j.total_tiles = tiles;
+    j.inst = dinst;
+    j.out_slot = 1;
+    j.pair = pair;
+    j.err = err;
+    ok = cudaMemcpyAsync(dinst, hinst.data(), sizeof(Instance) * count, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+         sp2::tc_launch(j, s) == cudaSuccess;
+    float t = 1e30f;
+    for (int r = 0; r < 3 && ok; ++r) {
+      float ms = 0.f;
+      ok = cudaEventRecord(e0, s) == cudaSuccess && sp2::tc_launch(j, s) == cudaSuccess &&
+           cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      t = std::min(t, ms);
+    }
+    best[c] = t;
+  }
+  int32_t herr = 0;
+  if (ok) ok = cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+               cudaStreamSynchronize(s) == cudaSuccess && herr == 0;
+  if (s) cudaStreamSynchronize(s);
+  cudaFree(scratch);
+  cudaFree(dinst);
+  cudaFree(err);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  (void)cudaGetLastError();
+  if (!ok) return by_model;
+  return best[2] < best[1] ? 2 : 1;
+}
+
 // Mixed-precision engine: `count` problems, stored largest first (internal order).
 // ---------------------------------------------------------------------------------------------
 struct MixedEngine {
@@ -193,14 +288,9 @@ struct MixedEngine {
     arenas.assign(count, nullptr);
     parts.assign(count, nullptr);
     const int H = o.max_iter + 2;
-    const int align = o.tile == 2 ? PT : LD_ALIGN;
-    auto ld_of = [&](int64_t n) { return (int)((n + align - 1) / align * align); };
-    pair = o.tile == 2 ? 1 : 0;
-    if (o.tile == 0) {
-      pair = 1;
-      for (int k = 0; k < count; ++k)
-        if (ld_of(N[k]) % PT != 0) pair = 0;
-    }
+    pair = (o.tile == 0 ? tune_tiles(N) : o.tile) == 2 ? 1 : 0;
+    const int align = pair ? PT : LD_ALIGN;
+    auto ld_of = [&](int64_t n) { return round_up(n, align); };
     // Keep every iterate (full history) or recompute them in the derivative pass; without
     // the correction no pass reads the history, so the rings suffice.
     int lowmem = (o.history == 2 || o.corrections == 0) ? 1 : 0;
@@ -388,6 +478,7 @@ struct MixedEngine {
     out->v = st->v;
     out->trace = st->tr;
     out->p = st->p;
+    out->tile = pair ? 2 : 1;
   }
 };
 

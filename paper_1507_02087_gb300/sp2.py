@@ -43,7 +43,8 @@ class sp2_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("n_iter", ctypes.c_int32), ("stop_reason", ctypes.c_int32),
                 ("hist_len", ctypes.c_int32), ("lambda_min", ctypes.c_double),
                 ("lambda_max", ctypes.c_double), ("loop_ms", ctypes.c_double), ("v", ctypes.POINTER(ctypes.c_double)),
-                ("trace", ctypes.POINTER(ctypes.c_double)), ("p", ctypes.POINTER(ctypes.c_uint8))]
+                ("trace", ctypes.POINTER(ctypes.c_double)), ("p", ctypes.POINTER(ctypes.c_uint8)),
+                ("tile", ctypes.c_int32)]
 
 
 _lib = None
@@ -203,6 +204,7 @@ def _info_dict(info) -> dict:
         "v": np.ctypeslib.as_array(info.v, shape=(MAX_ITER + 2,))[:hl].copy(),
         "trace": np.ctypeslib.as_array(info.trace, shape=(MAX_ITER + 2,))[:hl + 1].copy(),
         "p": np.ctypeslib.as_array(info.p, shape=(MAX_ITER + 2,))[:hl + 1].copy(),
+        "tile": {0: None, 1: "128", 2: "pair"}.get(info.tile),
     }
 
 

@@ -89,7 +89,7 @@ def test_struct_layout_matches_c():
     fields_opts = ["max_iter", "guard", "qtilde", "corrections", "refine_steps", "refine_fp64", "launch_mode",
                    "history", "tile"]
     fields_info = ["status", "n_iter", "stop_reason", "hist_len", "lambda_min", "lambda_max", "loop_ms",
-                   "v", "trace", "p"]
+                   "v", "trace", "p", "tile"]
     prints = [f"offsetof(sp2_opts, {f})" for f in fields_opts] + ["sizeof(sp2_opts)"]
     prints += [f"offsetof(sp2_info, {f})" for f in fields_info] + ["sizeof(sp2_info)"]
     src = ("#include <stdio.h>\n#include <stddef.h>\n#include \"sp2.h\"\nint main(void) {\n" +

@@ -31,15 +31,17 @@ def small_batch():
     return cases
 
 
-def test_mixed_batch_matches_singles_and_oracle(sp2mod):
+@pytest.mark.parametrize("tile", ["128", "pair"])
+def test_mixed_batch_matches_singles_and_oracle(sp2mod, tile):
+    # the same tile kind (and so the same padded ld) in the batch and the singles
     cases = small_batch()
     Fs = [c.F.cuda() for c in cases]
-    with sp2mod.BatchPurifier([c.N for c in cases], [c.nocc for c in cases], "mixed") as B:
+    with sp2mod.BatchPurifier([c.N for c in cases], [c.nocc for c in cases], "mixed", tile=tile) as B:
         Ds = B.run(Fs)
         infos = [B.info(i) for i in range(len(cases))]
     for c, F, D, info in zip(cases, Fs, Ds, infos):
-        assert info["status"] == 0
-        with sp2mod.Purifier(c.N, c.nocc, "mixed") as P:
+        assert info["status"] == 0 and info["tile"] == tile
+        with sp2mod.Purifier(c.N, c.nocc, "mixed", tile=tile) as P:
             Ds1 = P.run(F)
             i1 = P.info()
         assert torch.equal(D, Ds1), c.name           # identical arithmetic per problem
@@ -75,7 +77,7 @@ def test_stream_launch_mode_gives_the_same_results(sp2mod):
     out = {}
     for mode in (0, 1):
         with sp2mod.BatchPurifier([c.N for c in cases], [c.nocc for c in cases], "mixed", max_iter=80,
-                                  launch_mode=mode) as B:
+                                  launch_mode=mode, tile="128") as B:
             out[mode] = (B.run(Fs), [B.info(i)["n_iter"] for i in range(3)])
     assert out[0][1] == out[1][1]
     for a, b in zip(out[0][0], out[1][0]):
@@ -117,3 +119,26 @@ def test_batch64_workload_sampled(sp2mod):
             continue
         ref = o.sp2(c.F.cpu().numpy(), c.nocc)
         assert o.rel_error(Ds[k].cpu().numpy(), ref.D, c.nocc) <= TOL_MIXED
+
+
+def test_tile_tuner_reports_its_choice(sp2mod):
+    # tile = "auto" times both tile kinds at create time and keeps the faster; either way
+    # the results meet the mixed tolerance, and an explicit choice is reported as given
+    cases = small_batch()[:4]
+    Fs = [c.F.cuda() for c in cases]
+    with sp2mod.BatchPurifier([c.N for c in cases], [c.nocc for c in cases], "mixed") as B:
+        Ds = B.run(Fs)
+        infos = [B.info(i) for i in range(len(cases))]
+    assert len({i["tile"] for i in infos}) == 1 and infos[0]["tile"] in ("128", "pair")
+    for c, D, info in zip(cases, Ds, infos):
+        ref = o.sp2(c.F.numpy(), c.nocc)
+        assert info["status"] == 0 and o.rel_error(D.cpu().numpy(), ref.D, c.nocc) <= TOL_MIXED
+    # ld 8192 either way: 528 pair tiles fill the 76 SM pairs about 7 times over, and the pair
+    # kernel is ~1.3x faster (at ld 2048 its 36 tiles leave half the pairs idle and 128 x 128
+    # tiles win); corrections off keeps the handle small
+    with sp2mod.Purifier(8192, 4096, "mixed", corrections=0) as P:
+        assert P.info()["tile"] == "pair"
+    with sp2mod.Purifier(300, 150, "mixed", tile="128") as P:
+        assert P.info()["tile"] == "128"
+    with sp2mod.Purifier(300, 150, "fp64") as P:
+        assert P.info()["tile"] is None

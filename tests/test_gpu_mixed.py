@@ -98,7 +98,7 @@ def test_batch_with_pair_tiles(sp2mod):
     # every ld a multiple of 256: the batch runs on CTA-pair tiles
     Ns, noccs = [256, 512, 1024, 768], [100, 256, 500, 300]
     cases = [inputs.dense_gapped(n, k, gap=0.05, seed=40 + n) for n, k in zip(Ns, noccs)]
-    with sp2mod.BatchPurifier(Ns, noccs, "mixed") as B:
+    with sp2mod.BatchPurifier(Ns, noccs, "mixed", tile="pair") as B:
         Ds = B.run([c.F.cuda() for c in cases])
         infos = [B.info(i) for i in range(len(Ns))]
     for c, k, D, info in zip(cases, noccs, Ds, infos):
@@ -114,7 +114,7 @@ def test_recompute_history_is_bit_identical(sp2mod):
     F = case.F.cuda()
     out = {}
     for hist in ("full", "recompute"):
-        with sp2mod.Purifier(900, 400, "mixed", history=hist) as P:
+        with sp2mod.Purifier(900, 400, "mixed", history=hist, tile="pair") as P:
             out[hist] = (P.run(F), P.info()["n_iter"])
     assert out["full"][1] == out["recompute"][1]
     assert torch.equal(out["full"][0], out["recompute"][0])
