@@ -45,6 +45,7 @@ def workload_name(N, nocc, gap):
 # DRAM bytes (read + write) of one forward-square launch from an ncu capture of the current
 # kernel (profiles/tc_gemm_pair_sp2_forward_dram_ld8192.md), keyed by (N, tile kind).
 FWD_TRAFFIC_BYTES = {(8192, "pair"): 2.22e9 + 0.3881e9}
+FP32_FLOP_PER_CLK_SM = 256     # 128 FP32 FMA lanes per SM
 
 
 def parse():
@@ -299,6 +300,14 @@ def run_batch(a, ws, rank, local):
             "tiles": tiles, "fp64_path": fp64, "clocks": clk}), flush=True)
 
 
+def bsr_launches(squares, rule):
+    """Kernels of one block-sparse run (dense output off): 14 set-up kernels, 12 per loop
+    round (+1 each with the error-controlled rule), rounds launched in pairs by the graph."""
+    extra = 1 if rule == "error" else 0
+    rounds = squares + (squares & 1)
+    return 14 + extra + (12 + extra) * rounds
+
+
 def run_bsr(a, ws, rank, local):
     """Block-sparse path on the 32^3 tight-binding Hamiltonian (N = 32768)."""
     import torch
@@ -332,6 +341,33 @@ def run_bsr(a, ws, rank, local):
                                "v_last": float(info["v"][-1]) if len(info["v"]) else None,
                                "trace_err": abs(float(info["trace"][info["n_iter"]]) - tb.nocc),
                                "ms_per_square": info["loop_ms"] / max(1, info["hist_len"])}
+    # roofline of the numeric block square (the dominant kernel): a launch-mode-1 handle
+    # records CUDA events around each of its launches; work from the device's counters
+    with sp2.BsrPurifier(tb.N, tb.nocc, 1e-4, rule=a.rule, launch_mode=1) as P1:
+        P1.run(rp_d, ci_d, vals_d, dense=False, stream=stream)
+        P1.run(rp_d, ci_d, vals_d, dense=False, stream=stream)
+        w = P1.info()
+    clk = ClockSampler(local)
+    clk.start()
+    with sp2.BsrPurifier(tb.N, tb.nocc, 1e-4, rule=a.rule, launch_mode=1) as P1:
+        P1.run(rp_d, ci_d, vals_d, dense=False, stream=stream)
+        w = P1.info()
+    clocks = clk.stop()
+    mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+    flops = 2 * 32 ** 3 * w["block_products"]
+    streamed = 2 * 32 * 32 * 4 * w["block_products"]          # two FP32 blocks per product, no reuse
+    kern_s = w["numeric_ms"] * 1e-3
+    peak32 = SMS * FP32_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
+    peaks = load_peaks()
+    roofline = {"bound": "alu", "kernel": "bsr_numeric_kernel (FP32 CUDA-core block products, all squares)",
+                "achieved": flops / kern_s / 1e12, "peak": peak32, "unit": "TFLOP/s",
+                "frac": flops / kern_s / 1e12 / peak32,
+                "peak_source": f"152 SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz (median SM clock)",
+                "kernel_ms_per_run": w["numeric_ms"], "block_products": w["block_products"],
+                "square_blocks": w["square_blocks"],
+                "streamed_gbs": streamed / kern_s / 1e9,
+                "streamed_frac_of_hbm": streamed / kern_s / 1e9 / (peaks.get("hbm_gbs") or 6800.0),
+                "traffic": None}
     if rank == 0:
         main_ms = out[f"{a.rule}:tau=0.0001"]["time_to_d_ms"]
         print(json.dumps({
@@ -344,7 +380,8 @@ def run_bsr(a, ws, rank, local):
                        "nnzb_F": int(rp[-1]), "tau": 1e-4,
                        "truncation": {"error": "error-controlled, ||E_i||_F <= tau",
                                       "block": "per block, ||X_IJ||_F < tau dropped"}[a.rule]},
-            "runs": out}), flush=True)
+            "runs": out, "roofline": roofline,
+            "gpu_launches": a.steps * bsr_launches(out[f"{a.rule}:tau=0.0001"]["squares"], a.rule)}), flush=True)
 
 
 def main():

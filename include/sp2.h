@@ -222,6 +222,13 @@ sp2_status sp2_get_info_bsr(sp2_bsr h, sp2_info* out, int64_t* nnzb_out);
 /* Free the handle (synchronises the device first).  NULL is a no-op. */
 void sp2_destroy_bsr(sp2_bsr h);
 
+/* Work of the last run's squares (waits for the run): *block_products = 32 x 32 block
+ * products X_IK X_JK^T formed (each 2 * 32^3 flops), *square_blocks = upper blocks of the
+ * squares computed, *numeric_ms = summed device time of the numeric-square launches from
+ * CUDA events around each launch (launch_mode 1 only; 0 with the graph).  All 0 before the
+ * first run. */
+sp2_status sp2_get_work_bsr(sp2_bsr h, int64_t* block_products, int64_t* square_blocks, double* numeric_ms);
+
 /* FP64 purification that allocates no memory (the paper has no counterpart; this is a
  * service for callers that cannot call cudaMalloc, e.g. code running under another
  * component's allocator or in loops where entering the allocator is not allowed).

@@ -232,6 +232,7 @@ bsr_init_kernel(DevState* st, const int* rp, const int* ci, const double* vals, 
     st->dk = 0; st->k = 0; st->done = 0; st->n_out = 0; st->reason = SP2_STOP_EXACT;
     st->status = SP2_OK; st->out_buf = 0; st->out_mode = OUT_COPY; st->hist_len = 0;
     st->tr[0] = 0.0; st->p[0] = 0; st->iter_active = 1;
+    st->bprod = 0ull; st->sblocks = 0ull;
     if (s_bad) { st->status = SP2_ERR_NONFINITE; st->done = 1; st->out_mode = OUT_NAN; }
     else if (nocc == 0) { st->done = 1; st->out_mode = OUT_ZERO; }
     else if (nocc == N) { st->done = 1; st->out_mode = OUT_IDENTITY; }
@@ -305,7 +306,7 @@ __global__ void bsr_sym_kernel(DevState* st, Mat X, int nb, int W, uint32_t* sbi
 
 // ---- numeric square + SP2 epilogue + truncation decision -----------------------------------
 __global__ void __launch_bounds__(NT)
-bsr_numeric_kernel(const DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* skeep, double* spart,
+bsr_numeric_kernel(DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* skeep, double* spart,
                    double* sn2, double tau2) {
   __shared__ float As[2][B * (B + 1)];
   __shared__ float Bs[2][B * (B + 1)];
@@ -351,6 +352,7 @@ bsr_numeric_kernel(const DevState* st, Mat X, int W, Pairs P, float* svals, uint
       __syncthreads();
     }
     const int cnt = s_base;
+    if (tid == 0) atomicAdd(&st->bprod, (unsigned long long)cnt);
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int m = 0; m < cnt; ++m) {
       const int buf = m & 1;
@@ -521,6 +523,7 @@ bsr_finalize_kernel(DevState* st, const double* spart, const int* nnz_p, cudaGra
   if (threadIdx.x != 0) return;
   const int k = st->k + 1;
   const int pk = st->tr[k - 1] > (double)st->nocc ? 1 : 0;
+  st->sblocks += (unsigned long long)nnz;
   record_and_test(st, pk, sqrt(a), b, st->tr[k - 1]);
   // the loop stops after this round's truncation (the kernels below still run)
   if (use_cond && st->done) cudaGraphSetConditional(cond, 0);
@@ -620,6 +623,8 @@ struct sp2_bsr_ctx {
   cudaGraphExec_t exec = nullptr;
   cudaGraphConditionalHandle cond = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaEvent_t* nev = nullptr;    // launch mode 1: events around each numeric-square launch
+  int nrounds = 0;               // numeric launches recorded in the last run
   cudaStream_t last = nullptr;
   bool ran = false;
 };
@@ -654,6 +659,11 @@ static void bsr_free(sp2_bsr_ctx* h) {
   if (h->xnnz_host) cudaFreeHost(h->xnnz_host);
   if (h->ev[0]) cudaEventDestroy(h->ev[0]);
   if (h->ev[1]) cudaEventDestroy(h->ev[1]);
+  if (h->nev) {
+    for (int i = 0; i < 2 * (h->opts.max_iter + 4); ++i)
+      if (h->nev[i]) cudaEventDestroy(h->nev[i]);
+    delete[] h->nev;
+  }
   (void)cudaGetLastError();
   cudaSetDevice(cur);
   delete h;
@@ -688,8 +698,11 @@ static cudaError_t add_round(sp2_bsr_ctx* h, cudaGraph_t g, cudaStream_t s, int 
   scan_kernel<<<1, 1024, 0, s>>>(h->counts, nb, h->S.ptr, sn, st);
   fill_pairs_kernel<<<nb, 32, 0, s>>>(h->sbits, nb, W, up, h->S, st);
   // 2. numeric + 3. stop test
+  const bool timed = !use_cond && h->nev && h->nrounds < h->opts.max_iter + 4;
+  if (timed) cudaEventRecord(h->nev[2 * h->nrounds], s);
   bsr_numeric_kernel<<<grid_persistent(), NT, 0, s>>>(st, Xc, W, h->S, h->svals, h->skeep, h->spart, h->sn2,
                                                        tau2);
+  if (timed) cudaEventRecord(h->nev[2 * h->nrounds++ + 1], s);
   bsr_finalize_kernel<<<1, 1024, 0, s>>>(st, h->spart, sn, h->cond, use_cond);
   if (h->rule == SP2_TRUNC_ERROR)
     bsr_errctl_kernel<<<1, kEC, 0, s>>>(st, h->sn2, h->S.row, h->S.col, sn, reinterpret_cast<uint64_t*>(h->spart),
@@ -799,6 +812,13 @@ extern "C" sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, in
   if (cudaMemcpy(h->st_dev, &init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess) {
     (void)cudaGetLastError(); bsr_free(h); return SP2_ERR_CUDA;
   }
+  if (o.launch_mode == 1) {
+    const int ne = 2 * (o.max_iter + 4);
+    h->nev = new (std::nothrow) cudaEvent_t[ne]();
+    bool eok = h->nev != nullptr;
+    for (int i = 0; i < ne && eok; ++i) eok = cudaEventCreate(&h->nev[i]) == cudaSuccess;
+    if (!eok) { (void)cudaGetLastError(); bsr_free(h); return SP2_ERR_NOMEM; }
+  }
   sp2_status s = o.launch_mode == 0 ? build_graph(h) : SP2_OK;
   if (s == SP2_OK && cudaDeviceSynchronize() != cudaSuccess) { (void)cudaGetLastError(); s = SP2_ERR_CUDA; }
   if (s != SP2_OK) { bsr_free(h); return s; }
@@ -807,6 +827,22 @@ extern "C" sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, in
 }
 
 extern "C" void sp2_destroy_bsr(sp2_bsr h) { bsr_free(h); }
+
+extern "C" sp2_status sp2_get_work_bsr(sp2_bsr h, int64_t* block_products, int64_t* square_blocks,
+                                       double* numeric_ms) {
+  if (!h || !block_products || !square_blocks || !numeric_ms) return SP2_ERR_INVALID_ARG;
+  if (h->ran) BSR_TRY(cudaStreamSynchronize(h->last));
+  *block_products = h->ran ? (int64_t)h->st_host->bprod : 0;
+  *square_blocks = h->ran ? (int64_t)h->st_host->sblocks : 0;
+  double tot = 0.0;
+  for (int r = 0; h->ran && h->nev && r < h->nrounds; ++r) {
+    float ms = 0.f;
+    BSR_TRY(cudaEventElapsedTime(&ms, h->nev[2 * r], h->nev[2 * r + 1]));
+    tot += ms;
+  }
+  *numeric_ms = tot;
+  return SP2_OK;
+}
 
 extern "C" sp2_status sp2_run_bsr(sp2_bsr h, const int32_t* row_ptr_dev, const int32_t* col_idx_dev,
                                   const double* vals_dev, int64_t nnzb, double* D_dev, void* stream) {
@@ -843,6 +879,7 @@ extern "C" sp2_status sp2_run_bsr(sp2_bsr h, const int32_t* row_ptr_dev, const i
   if (h->opts.launch_mode == 0) {
     BSR_TRY(cudaGraphLaunch(h->exec, s));
   } else {
+    h->nrounds = 0;
     for (int it = 0; it <= h->opts.max_iter + 1; it += 2) {
       BSR_TRY(add_round(h, nullptr, s, 0, 0));
       BSR_TRY(add_round(h, nullptr, s, 1, 0));

@@ -48,6 +48,10 @@ struct DevState {
   int32_t round_fp32;  // 1: X_0 is rounded to FP32 (mixed path)
   int32_t iter_active; // block-sparse path: the current loop round squares (set at its start)
   int32_t _pad1;
+  // block-sparse path, work of the current run's squares: 32 x 32 block products and
+  // upper blocks of the squares computed
+  unsigned long long bprod;
+  unsigned long long sblocks;
   // history
   double v[SP2_MAX_ITER + 2];
   double tr[SP2_MAX_ITER + 2];

@@ -34,9 +34,15 @@ def main():
     ap.add_argument("--sp2", action="store_true",
                     help="time the SP2 forward square instead (expansion loop only, stream launches) on the "
                          "dense gapped input of size ld, nocc = ld / 2, gap 0.01")
+    ap.add_argument("--bsr", default=None, metavar="LX,LY,LZ",
+                    help="time the block-sparse squares instead, on the gapped tight-binding lattice of these "
+                         "dimensions (LX = 32), tau 1e-4, stream launches")
+    ap.add_argument("--rule", default="error", choices=["error", "block"])
     a = ap.parse_args()
     if a.sp2:
         return sp2_forward(a)
+    if a.bsr:
+        return bsr_squares(a)
     ld = a.ld
     g = torch.Generator(device="cuda").manual_seed(0)
     X = torch.randn(ld, ld, device="cuda", generator=g)
@@ -85,6 +91,23 @@ def sp2_forward(a):
     print(json.dumps({"ld": N, "mode": "sp2_forward", "tile": a.tile, "squares": int(info["hist_len"]),
                       "ms_per_square_incl_stop_test": ms,
                       "algorithmic_tflops": 6 * N * N * (N + 1) / (ms * 1e-3) / 1e12}))
+
+
+def bsr_squares(a):
+    """Block-sparse SP2 (launch mode 1) on a tight-binding lattice: work counters and the
+    summed device time of the numeric block-square launches."""
+    from . import inputs
+    dims = tuple(int(x) for x in a.bsr.split(","))
+    tb = inputs.tight_binding(dims=dims)
+    rp, ci, vals = (torch.from_numpy(x).cuda() for x in tb.bsr(32))
+    with sp2.BsrPurifier(tb.N, tb.nocc, 1e-4, rule=a.rule, launch_mode=1) as P:
+        for _ in range(max(1, a.reps)):
+            P.run(rp, ci, vals, dense=False)
+        w = P.info()
+    print(json.dumps({"N": tb.N, "dims": dims, "rule": a.rule, "n_iter": w["n_iter"], "nnzb_D": w["nnzb"],
+                      "block_products": w["block_products"], "numeric_ms": w["numeric_ms"],
+                      "tflops": 2 * 32 ** 3 * w["block_products"] / (w["numeric_ms"] * 1e-3) / 1e12,
+                      "loop_ms": w["loop_ms"]}))
 
 
 if __name__ == "__main__":

@@ -95,6 +95,8 @@ def lib() -> ctypes.CDLL:
         L.sp2_run_bsr.restype = i32
         L.sp2_get_info_bsr.argtypes = [vp, ctypes.POINTER(sp2_info), ctypes.POINTER(i64)]
         L.sp2_get_info_bsr.restype = i32
+        L.sp2_get_work_bsr.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
+        L.sp2_get_work_bsr.restype = i32
         L.sp2_destroy_bsr.argtypes = [vp]
         L.sp2_destroy_bsr.restype = None
         L.sp2_test_bsr_keep.argtypes = [vp, i64, ctypes.c_double, i32, vp, vp]
@@ -252,6 +254,10 @@ class BsrPurifier:
         _check(lib().sp2_get_info_bsr(self.h, ctypes.byref(info), ctypes.byref(nz)), "sp2_get_info_bsr")
         d = _info_dict(info)
         d["nnzb"] = nz.value
+        bp, sb, nms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().sp2_get_work_bsr(self.h, ctypes.byref(bp), ctypes.byref(sb), ctypes.byref(nms)),
+               "sp2_get_work_bsr")
+        d["block_products"], d["square_blocks"], d["numeric_ms"] = bp.value, sb.value, nms.value
         return d
 
     def close(self):
