@@ -22,6 +22,7 @@
 // reproducible bit for bit (and equals the host's, given the same stored blocks).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -305,108 +306,160 @@ __global__ void bsr_sym_kernel(DevState* st, Mat X, int nb, int W, uint32_t* sbi
 }
 
 // ---- numeric square + SP2 epilogue + truncation decision -----------------------------------
-__global__ void __launch_bounds__(NT)
+// One warp per upper pair (I, J) of the square; a CTA holds NUM_WARPS warps.  The products
+// S_IJ = sum_K X_IK X_JK^T run over the K of row I (increasing) that row J also holds.  Both
+// triangles are stored and X_KI is the exact transpose of X_IK, so the operands come from
+// block row K as X_KI and X_KJ: read row-major they give X_IK[r][k] = X_KI[k][r] and
+// X_JK[c][k] = X_KJ[k][c], k-major, without a transpose.  Each product's two blocks are
+// copied into a per-warp double buffer with cp.async while the previous product is
+// computed; each lane accumulates a 4 x 8 tile (rows 4 rg .. 4 rg + 3, columns 8 cg ..
+// 8 cg + 7, lane = 4 rg + cg) with one fmaf per term in increasing K, then k.
+constexpr int NUM_WARPS = 4;
+constexpr int NUM_THREADS = 32 * NUM_WARPS;
+constexpr int WARP_FLOATS = 2 * 2 * BE;          // two stages of (X_KI, X_KJ)
+constexpr int NUM_SMEM = NUM_WARPS * WARP_FLOATS * 4;
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// blocks pa (X_KI) and pb (X_KJ) of `vals` into stage `stg` of the warp's buffer
+__device__ __forceinline__ void issue_pair(float* wbuf, int stg, const float* vals, int pa, int pb, int lane) {
+  float* dA = wbuf + stg * 2 * BE;
+  float* dB = dA + BE;
+  const float* sA = vals + (int64_t)pa * BE;
+  const float* sB = vals + (int64_t)pb * BE;
+  #pragma unroll
+  for (int i = 0; i < BE / 128; ++i) {
+    const int off = (i * 32 + lane) * 4;
+    cp_async16(dA + off, sA + off);
+    cp_async16(dB + off, sB + off);
+  }
+  cp_async_commit();
+}
+
+__device__ __forceinline__ void product_tile(const float* wbuf, int stg, int rg, int cg, float (&acc)[4][8]) {
+  const float* At = wbuf + stg * 2 * BE;
+  const float* Bt = At + BE;
+  #pragma unroll 8
+  for (int k = 0; k < B; ++k) {
+    const float4 a = *reinterpret_cast<const float4*>(At + k * B + 4 * rg);
+    const float4 b0 = *reinterpret_cast<const float4*>(Bt + k * B + 8 * cg);
+    const float4 b1 = *reinterpret_cast<const float4*>(Bt + k * B + 8 * cg + 4);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    #pragma unroll
+    for (int i = 0; i < 4; ++i)
+      #pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+}
+
+__global__ void __launch_bounds__(NUM_THREADS)
 bsr_numeric_kernel(DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* skeep, double* spart,
                    double* sn2, double tau2) {
-  __shared__ float As[2][B * (B + 1)];
-  __shared__ float Bs[2][B * (B + 1)];
-  __shared__ int kI[MAX_NB], kJ[MAX_NB];
-  __shared__ int s_base;
-  __shared__ float wred[NT / 32];
+  extern __shared__ __align__(16) float num_smem[];
   if (!st->iter_active) return;
   const int nnz = *P.nnz;
   const int kprev = st->k;
   const int pk = st->tr[kprev] > (double)st->nocc ? 1 : 0;   // Alg. 3 trace test
-  const int tid = threadIdx.x;
-  const int r = tid / 8, c0 = (tid % 8) * 4;
-  for (int q = blockIdx.x; q < nnz; q += gridDim.x) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int rg = lane >> 2, cg = lane & 3;
+  float* wbuf = num_smem + wid * WARP_FLOATS;
+  const int gw = blockIdx.x * NUM_WARPS + wid, nw = gridDim.x * NUM_WARPS;
+  for (int q = gw; q < nnz; q += nw) {
     const int I = P.row[q], J = P.col[q];
-    // K in row I (increasing) that row J also holds
-    if (tid == 0) s_base = 0;
-    __syncthreads();
+    float acc[4][8];
+    #pragma unroll
+    for (int i = 0; i < 4; ++i)
+      #pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    int items = 0;
     const int b0 = X.rp[I], b1 = X.rp[I + 1];
-    for (int e0 = b0; e0 < b1; e0 += NT) {
-      const int e = e0 + tid;
-      int pj = -1;
-      if (e < b1) pj = find_block(X, W, J, X.ci[e]);
-      const int flag = pj >= 0;
-      // order-preserving compaction across the block
-      const unsigned bal = __ballot_sync(0xffffffffu, flag);
-      const int warp = tid >> 5, lane = tid & 31;
-      __shared__ int wcnt[NT / 32];
-      if (lane == 0) wcnt[warp] = __popc(bal);
-      __syncthreads();
-      int off = 0;
-      for (int w = 0; w < warp; ++w) off += wcnt[w];
-      if (flag) {
-        const int slot = s_base + off + __popc(bal & ((1u << lane) - 1u));
-        kI[slot] = e;
-        kJ[slot] = pj;
+    for (int e0 = b0; e0 < b1; e0 += 32) {
+      const int e = e0 + lane;
+      int pa = -1, pb = -1;
+      if (e < b1) {
+        const int K = X.ci[e];
+        pb = find_block(X, W, K, J);
+        if (pb >= 0) pa = find_block(X, W, K, I);
       }
-      __syncthreads();
-      if (tid == 0) {
-        int t = 0;
-        for (int w = 0; w < NT / 32; ++w) t += wcnt[w];
-        s_base += t;
-      }
-      __syncthreads();
-    }
-    const int cnt = s_base;
-    if (tid == 0) atomicAdd(&st->bprod, (unsigned long long)cnt);
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int m = 0; m < cnt; ++m) {
-      const int buf = m & 1;
-      const float* a = X.vals + (int64_t)kI[m] * BE;
-      const float* b = X.vals + (int64_t)kJ[m] * BE;
-      for (int e = tid; e < BE; e += NT) {
-        As[buf][(e / B) * (B + 1) + e % B] = a[e];
-        Bs[buf][(e / B) * (B + 1) + e % B] = b[e];
-      }
-      __syncthreads();
-      #pragma unroll 8
-      for (int k = 0; k < B; ++k) {
-        const float av = As[buf][r * (B + 1) + k];
-        #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[j] = fmaf(av, Bs[buf][(c0 + j) * (B + 1) + k], acc[j]);
+      // (K, I) is present whenever (I, K) is (symmetric patterns); both are checked anyway
+      unsigned mask = __ballot_sync(0xffffffffu, pa >= 0 && pb >= 0);
+      while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        const int a = __shfl_sync(0xffffffffu, pa, src);
+        const int b = __shfl_sync(0xffffffffu, pb, src);
+        issue_pair(wbuf, items & 1, X.vals, a, b, lane);
+        if (items > 0) {
+          cp_async_wait<1>();
+          __syncwarp();
+          product_tile(wbuf, (items - 1) & 1, rg, cg, acc);
+          __syncwarp();
+        }
+        ++items;
       }
     }
-    __syncthreads();
-    // epilogue: X_old (I, J) of X~_{k-1} if stored
+    if (items > 0) {
+      cp_async_wait<0>();
+      __syncwarp();
+      product_tile(wbuf, (items - 1) & 1, rg, cg, acc);
+      __syncwarp();
+    }
+    if (lane == 0) atomicAdd(&st->bprod, (unsigned long long)items);
+    // epilogue: X_old (I, J) of X~_{k-1} if stored; the new block is staged in the warp's
+    // buffer (row stride B + 1) for the fixed-order norm
     const int po = find_block(X, W, I, J);
+    float* blk = wbuf;
     float vloc = 0.f;
     double trloc = 0.0;
     #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float old = po >= 0 ? X.vals[(int64_t)po * BE + r * B + c0 + j] : 0.f;
-      const float s = acc[j];
-      const float nw = pk ? s : fmaf(2.0f, old, -s);
-      const float d = old - s;
-      vloc = fmaf(d, d, vloc);
-      As[0][r * (B + 1) + c0 + j] = nw;
-      svals[(int64_t)q * BE + r * B + c0 + j] = nw;
-      if (I == J && r == c0 + j) trloc += (double)nw;
+    for (int i = 0; i < 4; ++i) {
+      const int r = 4 * rg + i;
+      float old[8];
+      if (po >= 0) {
+        const float4 o0 = *reinterpret_cast<const float4*>(X.vals + (int64_t)po * BE + r * B + 8 * cg);
+        const float4 o1 = *reinterpret_cast<const float4*>(X.vals + (int64_t)po * BE + r * B + 8 * cg + 4);
+        old[0] = o0.x; old[1] = o0.y; old[2] = o0.z; old[3] = o0.w;
+        old[4] = o1.x; old[5] = o1.y; old[6] = o1.z; old[7] = o1.w;
+      } else {
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) old[j] = 0.f;
+      }
+      float nwv[8];
+      #pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float sv = acc[i][j];
+        nwv[j] = pk ? sv : fmaf(2.0f, old[j], -sv);
+        const float d = old[j] - sv;
+        vloc = fmaf(d, d, vloc);
+        if (I == J && r == 8 * cg + j) trloc += (double)nwv[j];
+        blk[r * (B + 1) + 8 * cg + j] = nwv[j];
+      }
+      float* dst = svals + (int64_t)q * BE + r * B + 8 * cg;
+      *reinterpret_cast<float4*>(dst) = make_float4(nwv[0], nwv[1], nwv[2], nwv[3]);
+      *reinterpret_cast<float4*>(dst + 4) = make_float4(nwv[4], nwv[5], nwv[6], nwv[7]);
     }
-    // block reductions (fixed tree): v^2 with weight 2 off the diagonal, trace
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       vloc += __shfl_xor_sync(0xffffffffu, vloc, o);
       trloc += __shfl_xor_sync(0xffffffffu, trloc, o);
     }
-    __shared__ double wtr[NT / 32];
-    if ((tid & 31) == 0) { wred[tid >> 5] = vloc; wtr[tid >> 5] = trloc; }
-    __syncthreads();
-    if (tid < 32) {
-      const double n2 = block_norm2_fixed(As[0]);
-      if (tid == 0) {
-        double v2 = 0.0, tr = 0.0;
-        for (int w = 0; w < NT / 32; ++w) { v2 += (double)wred[w]; tr += wtr[w]; }
-        spart[2 * (int64_t)q] = (I == J ? 1.0 : 2.0) * v2;
-        spart[2 * (int64_t)q + 1] = tr;
-        skeep[q] = (I == J || n2 >= tau2) ? 1 : 0;
-        sn2[q] = n2;
-      }
+    __syncwarp();
+    const double n2 = block_norm2_fixed(blk);
+    __syncwarp();
+    if (lane == 0) {
+      spart[2 * (int64_t)q] = (I == J ? 1.0 : 2.0) * (double)vloc;
+      spart[2 * (int64_t)q + 1] = trloc;
+      skeep[q] = (I == J || n2 >= tau2) ? 1 : 0;
+      sn2[q] = n2;
     }
-    __syncthreads();
   }
 }
 
@@ -669,6 +722,26 @@ static void bsr_free(sp2_bsr_ctx* h) {
   delete h;
 }
 
+// Persistent grid of the numeric square: the resident CTAs of the whole GPU.
+static int numeric_grid() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0, sms = 1, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(bsr_numeric_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, NUM_SMEM) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bsr_numeric_kernel, NUM_THREADS, NUM_SMEM) !=
+            cudaSuccess ||
+        per < 1) {
+      (void)cudaGetLastError();
+      per = 1;
+    }
+    n = std::max(1, sms) * per;
+  }
+  return n;
+}
+
 static int grid_persistent() {
   static int n = 0;
   if (!n) {
@@ -700,8 +773,8 @@ static cudaError_t add_round(sp2_bsr_ctx* h, cudaGraph_t g, cudaStream_t s, int 
   // 2. numeric + 3. stop test
   const bool timed = !use_cond && h->nev && h->nrounds < h->opts.max_iter + 4;
   if (timed) cudaEventRecord(h->nev[2 * h->nrounds], s);
-  bsr_numeric_kernel<<<grid_persistent(), NT, 0, s>>>(st, Xc, W, h->S, h->svals, h->skeep, h->spart, h->sn2,
-                                                       tau2);
+  bsr_numeric_kernel<<<numeric_grid(), NUM_THREADS, NUM_SMEM, s>>>(st, Xc, W, h->S, h->svals, h->skeep, h->spart,
+                                                                  h->sn2, tau2);
   if (timed) cudaEventRecord(h->nev[2 * h->nrounds++ + 1], s);
   bsr_finalize_kernel<<<1, 1024, 0, s>>>(st, h->spart, sn, h->cond, use_cond);
   if (h->rule == SP2_TRUNC_ERROR)
@@ -729,7 +802,8 @@ static sp2_status build_graph(sp2_bsr_ctx* h) {
   cudaGraphNode_t node;
   BSR_TRY(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &np));
   cudaGraph_t body = np.conditional.phGraph_out[0];
-  (void)grid_persistent();   // device query before capture
+  (void)grid_persistent();   // device queries before capture
+  (void)numeric_grid();
   cudaStream_t cs;
   BSR_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
