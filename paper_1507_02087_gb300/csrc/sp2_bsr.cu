@@ -468,40 +468,34 @@ bsr_numeric_kernel(DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* s
 // u_q = floor(2 n2_q / 2^(e-40)) units (2^e <= tau^2 < 2^(e+1)), the budget is
 // floor(tau^2 / 2^(e-40)).  The pairs with key (n2 bits, q) <= K* are dropped, K* the
 // largest key whose prefix sum is within the budget.  Integer sums do not depend on the
-// summation order, so one CTA finds K* by bisection: first over the bit pattern of n2
-// (non-negative doubles order like their bit patterns), then over q within the first
-// value that no longer fits.  The pair list is in (I, J) order, so q breaks ties as (I, J)
-// does.  `cbits` (nnz entries of scratch) caches each pair's candidate bits (~0 if none).
+// summation order, so one CTA finds K* by a radix select: eight passes over the bytes of
+// the n2 bit pattern (non-negative doubles order like their bit patterns), each a
+// 256-bucket histogram of units over the candidates that share the digits chosen so far,
+// find the value G whose candidates no longer all fit; they all weigh u(G), so the first
+// m = (budget - units below G) / u(G) of them in q order are dropped.  The pair list is
+// in (I, J) order, so q breaks ties as (I, J) does.  `cbits` (nnz entries of scratch)
+// caches each pair's candidate bits (~0 if none).
 constexpr int kEC = 512;
 
 __device__ __forceinline__ uint64_t ec_units(uint64_t bits, int e) {
   return (uint64_t)floor(ldexp(__longlong_as_double((long long)bits), 41 - e));
 }
 
-__device__ __forceinline__ uint64_t ec_block_sum(uint64_t v, uint64_t* red) {
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
   #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    uint64_t t = threadIdx.x < kEC / 32 ? red[threadIdx.x] : 0ull;
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) red[32] = t;
-  }
-  __syncthreads();
-  const uint64_t out = red[32];
-  __syncthreads();
-  return out;
+  return v;
 }
 
 __global__ void __launch_bounds__(kEC)
 bsr_errctl_kernel(const DevState* st, const double* n2, const int* row, const int* col, const int* nnz_p,
                   uint64_t* cbits, uint8_t* keep, double tau2) {
-  __shared__ uint64_t red[33];
+  __shared__ unsigned long long hist[256];
+  __shared__ unsigned long long s_u64[2];
+  __shared__ int s_int[kEC + 1];
   if (st && !st->iter_active) return;
   const int nnz = *nnz_p;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   constexpr uint64_t kNone = ~0ull;
   if (!(tau2 > 0.0)) {
     for (int q = tid; q < nnz; q += kEC) keep[q] = 1;
@@ -509,6 +503,9 @@ bsr_errctl_kernel(const DevState* st, const double* n2, const int* row, const in
   }
   const int e = ilogb(tau2);     // 2^e <= tau^2 < 2^(e+1)
   const uint64_t budget = (uint64_t)floor(ldexp(tau2, 40 - e));
+  // candidate bits and the total of their units
+  if (tid == 0) s_u64[0] = 0ull;
+  __syncthreads();
   uint64_t acc = 0;
   for (int q = tid; q < nnz; q += kEC) {
     const double v = n2[q];
@@ -517,40 +514,74 @@ bsr_errctl_kernel(const DevState* st, const double* n2, const int* row, const in
     cbits[q] = b;
     if (c) acc += ec_units(b, e);
   }
-  const uint64_t total = ec_block_sum(acc, red);
+  acc = warp_sum_u64(acc);
+  if (lane == 0) atomicAdd(&s_u64[0], (unsigned long long)acc);
+  __syncthreads();
+  const uint64_t total = s_u64[0];
   uint64_t gbits = kNone;   // candidates with bits < gbits are dropped ...
   int qstar = -1;           // ... and those with bits == gbits and q <= qstar
   if (total > budget) {
-    // invariant: S(lo) <= budget < S(hi), S(t) = units of the candidates with bits <= t
-    uint64_t lo = 0, hi = (uint64_t)__double_as_longlong(tau2);
-    while (hi - lo > 1) {
-      const uint64_t mid = lo + (hi - lo) / 2;
-      acc = 0;
-      for (int q = tid; q < nnz; q += kEC) {
-        const uint64_t b = cbits[q];
-        if (b <= mid) acc += ec_units(b, e);
+    uint64_t prefix = 0, pmask = 0, below = 0;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+      for (int d = tid; d < 256; d += kEC) hist[d] = 0ull;
+      __syncthreads();
+      for (int q0 = 0; q0 < nnz; q0 += kEC) {
+        const int q = q0 + tid;
+        const uint64_t b = q < nnz ? cbits[q] : kNone;
+        const bool in = b != kNone && (b & pmask) == prefix;
+        const int dig = in ? (int)((b >> shift) & 255u) : -1;
+        const uint64_t u = in ? ec_units(b, e) : 0ull;
+        const unsigned vm = __ballot_sync(0xffffffffu, in);
+        if (!vm) continue;
+        const int d0 = __shfl_sync(0xffffffffu, dig, __ffs(vm) - 1);
+        if (__all_sync(0xffffffffu, !in || dig == d0)) {
+          const uint64_t sum = warp_sum_u64(u);     // one atomic for the warp's common digit
+          if (lane == 0) atomicAdd(&hist[d0], (unsigned long long)sum);
+        } else if (in) {
+          atomicAdd(&hist[dig], (unsigned long long)u);
+        }
       }
-      if (ec_block_sum(acc, red) <= budget) lo = mid;
-      else hi = mid;
+      __syncthreads();
+      if (tid == 0) {
+        uint64_t run = below;
+        int d = 0;
+        for (; d < 255; ++d) {
+          if (run + hist[d] > budget) break;
+          run += hist[d];
+        }
+        s_u64[0] = run;
+        s_u64[1] = (uint64_t)d;
+      }
+      __syncthreads();
+      below = s_u64[0];
+      prefix |= s_u64[1] << shift;
+      pmask |= 255ull << shift;
+      __syncthreads();
     }
-    acc = 0;
-    for (int q = tid; q < nnz; q += kEC) {
-      const uint64_t b = cbits[q];
-      if (b <= lo) acc += ec_units(b, e);
+    gbits = prefix;
+    // every candidate with bits == gbits weighs u(gbits) > 0; m of them fit
+    const uint64_t ug = ec_units(gbits, e);
+    const uint64_t m = (budget - below) / ug;
+    // the m-th member in q order: counts over contiguous q ranges, then a scan
+    const int chunk = (nnz + kEC - 1) / kEC;
+    const int lo = tid * chunk, hi = min(nnz, lo + chunk);
+    int c = 0;
+    for (int q = lo; q < hi; ++q) c += cbits[q] == gbits ? 1 : 0;
+    s_int[tid + 1] = c;
+    if (tid == 0) s_int[0] = 0;
+    __syncthreads();
+    if (tid == 0) {
+      for (int t = 1; t <= kEC; ++t) s_int[t] += s_int[t - 1];
+      s_u64[0] = ~0ull;
     }
-    const uint64_t base = ec_block_sum(acc, red);
-    // within the value hi (the first that does not fit whole): the longest prefix in q
-    int qlo = -1, qhi = nnz - 1;
-    while (qhi - qlo > 1) {
-      const int mid = qlo + (qhi - qlo) / 2;
-      acc = 0;
-      for (int q = tid; q <= mid; q += kEC)
-        if (cbits[q] == hi) acc += ec_units(hi, e);
-      if (base + ec_block_sum(acc, red) <= budget) qlo = mid;
-      else qhi = mid;
+    __syncthreads();
+    if (m > 0 && (uint64_t)s_int[tid] < m && m <= (uint64_t)s_int[tid + 1]) {
+      int seen = s_int[tid];
+      for (int q = lo; q < hi; ++q)
+        if (cbits[q] == gbits && (uint64_t)(++seen) == m) { s_u64[0] = (unsigned long long)q; break; }
     }
-    gbits = hi;
-    qstar = qlo;
+    __syncthreads();
+    qstar = m > 0 ? (int)s_u64[0] : -1;
   }
   for (int q = tid; q < nnz; q += kEC) {
     const uint64_t b = cbits[q];
