@@ -253,6 +253,15 @@ struct MixedEngine {
     return j;
   }
 
+  // One derivative step: dX_j from X_{j-1} and dX_{j-1} (two products).  dX is a
+  // first-order correction far smaller than X, so its products run on the two leading
+  // pieces (about 16 bits) of each operand, half the tensor-core work of a full product.
+  sp2::tc::Job deriv_job() const {
+    sp2::tc::Job j = job(sp2::tc::MODE_DERIV_STEP, 1, sp2::tc::SLOTS_DERIV, 2);
+    j.lowprec = 1;
+    return j;
+  }
+
   sp2_status init(int cnt, const int64_t* Nu, const int64_t* noccu, const sp2_opts& o) {
     using namespace sp2::tc;
     count = cnt;
@@ -379,7 +388,7 @@ struct MixedEngine {
       cudaGraph_t dbody;
       s = add_while(graph, &n_df, 1, &cond2, &n_der, &dbody);
       if (s != SP2_OK) return s;
-      SP2_TRY(sp2::tc_add_node(dbody, nullptr, 0, job(MODE_DERIV_STEP, 1, SLOTS_DERIV, 2), &n_dsq));
+      SP2_TRY(sp2::tc_add_node(dbody, nullptr, 0, deriv_job(), &n_dsq));
       cudaGraphNode_t n_tail = n_dsq;
       if (inst_host[0].lowmem) {   // low memory: X_j again, next to its derivative step
         SP2_TRY(sp2::tc_add_node(dbody, &n_dsq, 1, job(MODE_DERIV_STEP, 1, SLOTS_RECOMPUTE), &n_tail));
@@ -414,7 +423,7 @@ struct MixedEngine {
       SP2_TRY(sp2::tc_launch(job(MODE_STORE_PIECES, 0, SLOTS_CORR_M), s));
       SP2_TRY(sp2::tc_launch(job(MODE_DF_COMBINE, 1, SLOTS_CORR_DF), s));
       for (int it = 0; it <= opts.max_iter + 1; ++it) {
-        SP2_TRY(sp2::tc_launch(job(MODE_DERIV_STEP, 1, SLOTS_DERIV, 2), s));
+        SP2_TRY(sp2::tc_launch(deriv_job(), s));
         if (inst_host[0].lowmem) SP2_TRY(sp2::tc_launch(job(MODE_DERIV_STEP, 1, SLOTS_RECOMPUTE), s));
         SP2_TRY(sp2::batch_launch_deriv_tail(inst_dev, count, s));
       }

@@ -127,6 +127,9 @@ struct Job {
   int32_t a_slot[2], b_slot[2];   // SLOTS_FIXED operands; SLOTS_REFINE step in a_slot[0]
   int32_t out_slot;
   int32_t pair;         // 1: 256 x 256 CTA-pair tiles (every instance's ld a multiple of 256)
+  int32_t lowprec;      // 1: pieces 0 and 1 of each operand only, the three products with
+                        // a + b <= 1 (about 16 significant bits; the derivative pass)
+  int32_t _pad;
   float* out32;         // MODE_STORE_F32
   int32_t* err;         // set to SP2_ERR_TIMEOUT if a wait gave up
 };

@@ -285,6 +285,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
+      const int npl = job.lowprec ? 2 : NP;   // pieces loaded per operand
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -308,12 +309,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
             }
             uint8_t* sA = smem + stage * STAGE_BYTES;
             uint8_t* sB = sA + NP * A_PIECE_BYTES;
-            mbar_arrive_expect_tx(&full_bar[stage], STAGE_BYTES);
-            #pragma unroll
-            for (int p = 0; p < NP; ++p)
+            mbar_arrive_expect_tx(&full_bar[stage], npl * (A_PIECE_BYTES + B_PIECE_BYTES));
+            for (int p = 0; p < npl; ++p)
               tma_load_4d(sA + p * A_PIECE_BYTES, mA, kb * BK, I * BM, p, R.a[term], &full_bar[stage]);
-            #pragma unroll
-            for (int p = 0; p < NP; ++p)
+            for (int p = 0; p < npl; ++p)
               tma_load_4d(sB + p * B_PIECE_BYTES, mB, kb * BK, J * BN, p, R.b[term], &full_bar[stage]);
             armed[stage] = 1;
             armed_par[stage] = phase;
@@ -330,9 +329,11 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16_f32(BM, BN);
-      // piece pairs (a, b) with a + b <= 2, smallest products first
+      // piece pairs (a, b) with a + b <= 2, smallest products first; the last three are the
+      // pairs with a + b <= 1 (low-precision jobs)
       const int pa[6] = {2, 1, 0, 1, 0, 0};
       const int pb[6] = {0, 1, 2, 0, 1, 0};
+      const int q0 = job.lowprec ? 3 : 0;
       int stage = 0, buf = 0;
       uint32_t phase = 0, bphase = 0;
       bool ok = true;
@@ -356,6 +357,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
             for (int kk = 0; kk < BK / 16; ++kk) {
               #pragma unroll
               for (int q = 0; q < 6; ++q) {
+                if (q < q0) continue;
                 const uint64_t ad = smem_desc_sw64(sA + pa[q] * A_PIECE_BYTES + kk * 32);
                 const uint64_t bd = smem_desc_sw64(sB + pb[q] * B_PIECE_BYTES + kk * 32);
                 mma_bf16(dt, ad, bd, idesc, accumulate);
@@ -490,6 +492,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
    if (warp == 0) {
     // ---------------- TMA producer (both CTAs) ----------------
     if (lane == 0) {
+      const int npl = job.lowprec ? 2 : NP;   // pieces loaded per operand
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -516,12 +519,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
             uint8_t* sA = smem + stage * STAGE_BYTES;
             uint8_t* sB = sA + NP * A_PIECE_BYTES;
             const uint32_t fb = mapa_shared(smem_u32(&full_bar[stage]), 0);
-            if (rank == 0) mbar_arrive_expect_tx(&full_bar[stage], 2 * STAGE_BYTES);
-            #pragma unroll
-            for (int p = 0; p < NP; ++p)
+            if (rank == 0) mbar_arrive_expect_tx(&full_bar[stage], 2 * npl * (A_PIECE_BYTES + B_PIECE_BYTES));
+            for (int p = 0; p < npl; ++p)
               tma_load_4d_pair(sA + p * A_PIECE_BYTES, mA, kb * BK, rowA, p, R.a[term], fb);
-            #pragma unroll
-            for (int p = 0; p < NP; ++p)
+            for (int p = 0; p < npl; ++p)
               tma_load_4d_pair(sB + p * B_PIECE_BYTES, mB, kb * BK, rowB, p, R.b[term], fb);
             armed[stage] = 1;
             armed_par[stage] = phase;
@@ -547,6 +548,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
       const uint32_t idesc = idesc_bf16_f32(2 * BM, PT);
       const int pa[6] = {2, 1, 0, 1, 0, 0};
       const int pb[6] = {0, 1, 2, 0, 1, 0};
+      const int q0 = job.lowprec ? 3 : 0;
       int stage = 0, buf = 0;
       uint32_t phase = 0, bphase = 0;
       bool ok = true;
@@ -576,6 +578,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
             for (int kk = 0; kk < BK / 16; ++kk) {
               #pragma unroll
               for (int q = 0; q < 6; ++q) {
+                if (q < q0) continue;
                 const uint64_t ad = smem_desc_sw64(sA + pa[q] * A_PIECE_BYTES + kk * 32);
                 const uint64_t bd = smem_desc_sw64(sB + pb[q] * B_PIECE_BYTES + kk * 32);
                 mma_bf16_pair(dt, ad, bd, idesc, accumulate);
