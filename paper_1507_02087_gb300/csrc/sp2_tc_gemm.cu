@@ -99,6 +99,11 @@ __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
   return r;
 }
 
+// k-blocks per tensor-memory chunk: CHUNK_KB (64 terms), twice that for low-precision jobs,
+// whose three products per k-step fill a chunk in half the time and whose 16-bit target
+// tolerates the larger accumulation bias (about 128 x 2^-25).
+__device__ __forceinline__ int chunk_kb(const Job& job) { return job.lowprec ? 2 * CHUNK_KB : CHUNK_KB; }
+
 __device__ __forceinline__ int tile_off(const Job& job, const Instance& in) {
   if (job.pair) return job.upper ? in.tile_off_upper2 : in.tile_off_full2;
   return job.upper ? in.tile_off_upper : in.tile_off_full;
@@ -342,13 +347,13 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
         const int ii = locate(job, t, I, J);
         const Instance& In = job.inst[ii];
         if (!resolve(job, In).active) continue;
-        const int nchunks = job.nterms * (In.ld / BK) / CHUNK_KB;
+        const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job);
         for (int ch = 0; ch < nchunks && ok; ++ch) {
           if (abort_s || !mbar_wait(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + kWaitNs)) { ok = false; break; }
           tc_fence_after();
           const uint32_t dt = tmem_base + (uint32_t)(buf * BN);
           uint32_t accumulate = 0;
-          for (int kc = 0; kc < CHUNK_KB; ++kc) {
+          for (int kc = 0; kc < chunk_kb(job); ++kc) {
             if (abort_s || !mbar_wait(&full_bar[stage], phase, globaltimer_ns() + kWaitNs)) { ok = false; break; }
             tc_fence_after();
             const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
@@ -388,7 +393,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
       const Instance& In = job.inst[ii];
       const Resolved R = resolve(job, In);
       if (!R.active) continue;
-      const int nchunks = job.nterms * (In.ld / BK) / CHUNK_KB;
+      const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job);
       float acc[BN / 32][32];
       #pragma unroll
       for (int g = 0; g < BN / 32; ++g)
@@ -557,7 +562,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
         const int ii = locate(job, t, I, J);
         const Instance& In = job.inst[ii];
         if (!resolve(job, In).active) continue;
-        const int nchunks = job.nterms * (In.ld / BK) / CHUNK_KB;
+        const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job);
         for (int ch = 0; ch < nchunks && ok; ++ch) {
           if (abort_s || !mbar_wait_cluster(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + kWaitNs)) {
             ok = false;
@@ -566,7 +571,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
           tc_fence_after();
           const uint32_t dt = tmem_base + (uint32_t)(buf * PT);
           uint32_t accumulate = 0;
-          for (int kc = 0; kc < CHUNK_KB; ++kc) {
+          for (int kc = 0; kc < chunk_kb(job); ++kc) {
             if (abort_s || !mbar_wait_cluster(&full_bar[stage], phase, globaltimer_ns() + kWaitNs)) {
               ok = false;
               break;
@@ -613,7 +618,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
       const Instance& In = job.inst[ii];
       const Resolved R = resolve(job, In);
       if (!R.active) continue;
-      const int nchunks = job.nterms * (In.ld / BK) / CHUNK_KB;
+      const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job);
       float acc[BN / 32][32];
       #pragma unroll
       for (int g = 0; g < BN / 32; ++g)
