@@ -31,6 +31,8 @@ Readings (also listed in the design notes):
     the unscaled polynomials, so it is checked only from n_min on, where a = 1.
   * reaching n_max without the order test firing ends the run with D = X_{n_max}
     (reason STOP_SCHEDULE).
+  * outer bounds beyond the spectral bounds (homo_out < lmin, lumo_out > lmax) are clamped
+    to them: beta_lo and gamma_lo are distances inside [0, 1] and may not be negative.
 """
 from __future__ import annotations
 
@@ -59,6 +61,7 @@ class Schedule:
 def acc_schedule(lmin: float, lmax: float, homo_out: float, homo_in: float, lumo_in: float, lumo_out: float,
                  *, delta: float = DELTA, eps: float = EPS_M, max_steps: int = 500) -> Schedule:
     """Alg. 4: the polynomial choices p_i, scale factors alpha_i, n_min and n_max."""
+    homo_out, lumo_out = max(homo_out, lmin), min(lumo_out, lmax)
     W = lmax - lmin
     b_up = 1.0 - (lmax - homo_in) / W
     b_lo = 1.0 - (lmax - homo_out) / W
@@ -69,6 +72,7 @@ def acc_schedule(lmin: float, lmax: float, homo_out: float, homo_in: float, lumo
     n_min = None
     i = 0
     while (b_up - b_up * b_up > eps or g_up - g_up * g_up > eps) or i < 2 or p[i] == p[i - 1]:
+        # (the printed condition joins the two parts with "and"; see the readings above)
         if i >= max_steps:
             raise RuntimeError("the schedule did not converge")
         i += 1
@@ -76,19 +80,24 @@ def acc_schedule(lmin: float, lmax: float, homo_out: float, homo_in: float, lumo
             b_lo, g_lo = 0.0, 0.0
             n_min = i + 1
             delta = 0.0
+        # each value is formed with one rounding per operation, in the order written
+        def fold(a, x):      # ((1 - a) + a x)^2
+            y = (1.0 - a) + a * x
+            return y * y
+
+        def lift(a, x):      # 2 a x - (a x)^2
+            y = a * x
+            return 2.0 * a * x - y * y
+
         if g_up >= b_up:
             a = 2.0 / (2.0 - g_lo)
-            g_lo = ((1.0 - a) + a * g_lo) ** 2
-            g_up = ((1.0 - a) + a * g_up) ** 2
-            b_lo = 2.0 * a * b_lo - (a * b_lo) ** 2
-            b_up = 2.0 * a * b_up - (a * b_up) ** 2
+            g_lo, g_up = fold(a, g_lo), fold(a, g_up)
+            b_lo, b_up = lift(a, b_lo), lift(a, b_up)
             p.append(1)
         else:
             a = 2.0 / (2.0 - b_lo)
-            g_lo = 2.0 * a * g_lo - (a * g_lo) ** 2
-            g_up = 2.0 * a * g_up - (a * g_up) ** 2
-            b_lo = ((1.0 - a) + a * b_lo) ** 2
-            b_up = ((1.0 - a) + a * b_up) ** 2
+            g_lo, g_up = lift(a, g_lo), lift(a, g_up)
+            b_lo, b_up = fold(a, b_lo), fold(a, b_up)
             p.append(0)
         alpha.append(a)
         bu.append(b_up)
