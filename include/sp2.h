@@ -55,7 +55,8 @@ typedef enum {
   SP2_STOP_ORDER = 0,        /* the paper's convergence-order test fired (Alg. 3) */
   SP2_STOP_TRACE_GUARD = 1,  /* trace moved the wrong way: rounding dominates */
   SP2_STOP_EXACT = 2,        /* n_occ in {0, N}, or X exactly idempotent */
-  SP2_STOP_CAP = 3           /* max_iter reached (safety net) */
+  SP2_STOP_CAP = 3,          /* max_iter reached (safety net) */
+  SP2_STOP_SCHEDULE = 4      /* SP2-ACC: the precomputed schedule ended (n_max, Alg. 4) */
 } sp2_stop_reason;
 
 /* Arithmetic of the squaring X -> X^2. */
@@ -121,6 +122,23 @@ typedef struct {
 
 typedef struct sp2_ctx* sp2_handle;
 
+/* ---- SP2-ACC: homo/lumo-based accelerated expansion (Alg. 4 and Alg. 5) -----------------
+ * With bounds of the homo and lumo eigenvalues of F, bounds = {homo_out, homo_in, lumo_in,
+ * lumo_out} with homo_out <= homo <= homo_in < lumo_in <= lumo <= lumo_out, the handle's
+ * following runs use the predefined polynomial sequence of Alg. 4 with scale-and-fold
+ * acceleration instead of the trace-based choice: at the start of each run, right after the
+ * Gershgorin bounds, one device thread computes p_i and alpha_i (X_i = ((1 - alpha_i) I +
+ * alpha_i X)^2 or 2 alpha_i X - (alpha_i X)^2), n_min (the step after the acceleration is
+ * switched off, once both lower bounds are below 0.01) and n_max; the order test runs from
+ * n_min on, the trace guard too, and a run that reaches n_max ends there with reason
+ * SP2_STOP_SCHEDULE.  Outer bounds beyond the Gershgorin bounds are clamped to them.
+ * bounds == NULL returns the handle to the trace-based expansion.  SP2_ERR_INVALID_ARG for
+ * unordered or non-finite bounds; a schedule longer than SP2_MAX_ITER steps is reported by
+ * the run (status SP2_ERR_INVALID_ARG in sp2_get_info).  Synchronous; must not overlap a run
+ * of the same handle.  Works for SP2_PREC_FP64 and SP2_PREC_MIXED handles (the mixed path's
+ * first-order correction follows the scaled polynomials). */
+int32_t sp2_set_homo_lumo(sp2_handle h, const double* bounds);
+
 /* Fill `opts` with the defaults (max_iter 200, guard on, qtilde 1.8, 1 correction,
  * a 2-step refinement pair on the tensor cores). */
 void sp2_default_opts(sp2_opts* opts);
@@ -169,6 +187,9 @@ sp2_status sp2_create_batch(int32_t count, const int64_t* N, const int64_t* n_oc
 /* Enqueue the batch: F_dev[i] -> D_dev[i] (host arrays of `count` device pointers, each
  * buffer as in sp2_run).  Asynchronous; no host synchronisation. */
 sp2_status sp2_run_batch(sp2_batch hb, const double* const* F_dev, double* const* D_dev, void* stream);
+
+/* sp2_set_homo_lumo for problem i of a batch (user order). */
+int32_t sp2_set_homo_lumo_batch(sp2_batch hb, int32_t i, const double* bounds);
 
 /* Wait for the batch's last run and describe problem i (arrays valid until the next run). */
 sp2_status sp2_get_info_batch(sp2_batch hb, int32_t i, sp2_info* out);

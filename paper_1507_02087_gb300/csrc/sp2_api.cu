@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstddef>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -692,6 +694,49 @@ extern "C" void sp2_destroy(sp2_handle h) { free_ctx(h); }
 // ---------------------------------------------------------------------------------------------
 // Batch handle
 // ---------------------------------------------------------------------------------------------
+// ---- SP2-ACC bounds -------------------------------------------------------------------------
+// The accelerated path's inputs live in the device state; the schedule itself is computed
+// by the init kernel of every run (the Gershgorin bounds it needs are found there).
+struct AccFields {
+  int32_t acc, n_min, n_max, pad;
+  double hl[4];
+};
+static_assert(offsetof(DevState, n_min) == offsetof(DevState, acc) + 4 &&
+                  offsetof(DevState, hl) == offsetof(DevState, acc) + 16,
+              "AccFields mirrors the SP2-ACC fields of DevState");
+
+static bool acc_bounds_valid(const double* b) {
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(b[i])) return false;
+  return b[0] <= b[1] && b[1] < b[2] && b[2] <= b[3];
+}
+
+static sp2_status write_acc(DevState* st_dev, DevState* st_host, const double* bounds) {
+  AccFields f;
+  std::memset(&f, 0, sizeof(f));
+  if (bounds) {
+    f.acc = 1;
+    for (int i = 0; i < 4; ++i) f.hl[i] = bounds[i];
+  }
+  SP2_TRY(cudaDeviceSynchronize());
+  SP2_TRY(cudaMemcpy(reinterpret_cast<char*>(st_dev) + offsetof(DevState, acc), &f, sizeof(f),
+                     cudaMemcpyHostToDevice));
+  st_host->acc = f.acc;
+  for (int i = 0; i < 4; ++i) st_host->hl[i] = f.hl[i];
+  return SP2_OK;
+}
+
+extern "C" int32_t sp2_set_homo_lumo(sp2_handle h, const double* bounds) {
+  if (!h || (bounds && !acc_bounds_valid(bounds))) return SP2_ERR_INVALID_ARG;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  sp2_status r = h->mixed ? write_acc(h->mixed->st_dev, h->mixed->st_host, bounds)
+                          : write_acc(h->st_dev, h->st_host, bounds);
+  cudaSetDevice(cur);
+  return r;
+}
+
 struct sp2_batch_ctx {
   int count = 0;
   int32_t precision = 0;
@@ -702,6 +747,18 @@ struct sp2_batch_ctx {
   cudaStream_t last_stream = nullptr;
   bool ran = false;
 };
+
+extern "C" int32_t sp2_set_homo_lumo_batch(sp2_batch hb, int32_t i, const double* bounds) {
+  if (!hb || i < 0 || i >= hb->count || (bounds && !acc_bounds_valid(bounds))) return SP2_ERR_INVALID_ARG;
+  if (!hb->mixed) return sp2_set_homo_lumo(hb->singles[i], bounds);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(hb->device);
+  const int k = hb->mixed->internal_of[i];
+  sp2_status r = write_acc(hb->mixed->st_dev + k, hb->mixed->st_host + k, bounds);
+  cudaSetDevice(cur);
+  return r;
+}
 
 extern "C" void sp2_destroy_batch(sp2_batch hb) {
   if (!hb) return;

@@ -52,6 +52,14 @@ struct DevState {
   // upper blocks of the squares computed
   unsigned long long bprod;
   unsigned long long sblocks;
+  // SP2-ACC (Alg. 4 / Alg. 5): set by sp2_set_homo_lumo, schedule filled by the init kernel
+  int32_t acc;         // 1: homo/lumo-based accelerated expansion
+  int32_t n_min;       // first step of the stop test (acceleration off)
+  int32_t n_max;       // last step of the schedule
+  int32_t _pad2;
+  double hl[4];        // homo_out, homo_in, lumo_in, lumo_out
+  double alpha[SP2_MAX_ITER + 2];
+  uint8_t psched[SP2_MAX_ITER + 2];
   // history
   double v[SP2_MAX_ITER + 2];
   double tr[SP2_MAX_ITER + 2];
@@ -67,10 +75,90 @@ __device__ __forceinline__ bool order_test_stops(double v_i, double v_im2, doubl
   return log(v_i / kC2sp) / log(v_im2) < qtilde;
 }
 
+// ---- SP2-ACC ---------------------------------------------------------------------------
+// Alg. 4 on the device (one thread): the polynomial p_i and scale-and-fold factor alpha_i of
+// every step, n_min (the step after the acceleration is switched off, once both lower
+// bounds are below delta = 0.01) and n_max (bounds converged to machine epsilon and the
+// last two polynomials different; the printed loop condition joins its two parts with
+// "and", read as "or").  Outer bounds beyond [lmin, lmax] are clamped to it.  Every value
+// is one correctly rounded double operation in the order of the algorithm (no fused
+// multiply-add), so the schedule equals a host evaluation of the same formulas bit for
+// bit.  Returns false if the schedule does not converge within SP2_MAX_ITER steps.
+__device__ __forceinline__ double acc_fold(double a, double x) {   // ((1 - a) + a x)^2
+  const double y = __dadd_rn(__dsub_rn(1.0, a), __dmul_rn(a, x));
+  return __dmul_rn(y, y);
+}
+__device__ __forceinline__ double acc_lift(double a, double x) {   // 2 a x - (a x)^2
+  const double y = __dmul_rn(a, x);
+  return __dsub_rn(__dmul_rn(__dmul_rn(2.0, a), x), __dmul_rn(y, y));
+}
+
+__device__ inline bool acc_schedule(DevState* st) {
+  const double lmin = st->lmin, lmax = st->lmax;
+  const double homo_out = fmax(st->hl[0], lmin), homo_in = st->hl[1];
+  const double lumo_in = st->hl[2], lumo_out = fmin(st->hl[3], lmax);
+  const double W = __dsub_rn(lmax, lmin);
+  double bu = __dsub_rn(1.0, __ddiv_rn(__dsub_rn(lmax, homo_in), W));
+  double bl = __dsub_rn(1.0, __ddiv_rn(__dsub_rn(lmax, homo_out), W));
+  double gu = __ddiv_rn(__dsub_rn(lmax, lumo_in), W);
+  double gl = __ddiv_rn(__dsub_rn(lmax, lumo_out), W);
+  const double eps = 2.220446049250313e-16;   // 2^-52
+  double delta = 0.01;
+  int i = 0, nmin = -1;
+  st->psched[0] = 0;
+  st->alpha[0] = 1.0;
+  while ((__dsub_rn(bu, __dmul_rn(bu, bu)) > eps || __dsub_rn(gu, __dmul_rn(gu, gu)) > eps) || i < 2 ||
+         st->psched[i] == st->psched[i - 1]) {
+    if (i >= SP2_MAX_ITER) return false;
+    ++i;
+    if (delta > 0.0 && bl < delta && gl < delta) {
+      bl = 0.0; gl = 0.0;
+      nmin = i + 1;
+      delta = 0.0;
+    }
+    double a;
+    if (gu >= bu) {
+      a = __ddiv_rn(2.0, __dsub_rn(2.0, gl));
+      gl = acc_fold(a, gl); gu = acc_fold(a, gu);
+      bl = acc_lift(a, bl); bu = acc_lift(a, bu);
+      st->psched[i] = 1;
+    } else {
+      a = __ddiv_rn(2.0, __dsub_rn(2.0, bl));
+      gl = acc_lift(a, gl); gu = acc_lift(a, gu);
+      bl = acc_fold(a, bl); bu = acc_fold(a, bu);
+      st->psched[i] = 0;
+    }
+    st->alpha[i] = a;
+  }
+  st->n_min = nmin < 0 ? i + 1 : nmin;
+  st->n_max = i;
+  return true;
+}
+
+// Polynomial of square j (X_j from X_{j-1}) on the accelerated path:
+// X_j = a X^2 + b X + c I, from p_j and alpha_j (Alg. 5); past n_max, p = 1 with alpha = 1.
+__device__ __forceinline__ int acc_step(const DevState* st, int j, double& a, double& b, double& c) {
+  const bool in = j >= 1 && j <= st->n_max;
+  const int p = in ? st->psched[j] : 1;
+  const double al = in ? st->alpha[j] : 1.0;
+  if (p) {
+    a = al * al;
+    b = 2.0 * al * (1.0 - al);
+    c = (1.0 - al) * (1.0 - al);
+  } else {
+    a = -al * al;
+    b = 2.0 * al;
+    c = 0.0;
+  }
+  return p;
+}
+
 // Records square k = st->k + 1 (v_{k-1}, Tr[X_k], p_k) and applies the stop rules in
 // the order the iteration meets them: the order test for X_{k-1} (Alg. 3, evaluated
-// one square late because v_{k-1} needs X_{k-1}^2), the cap, then the trace guard for
-// X_k, which compares Tr[X_k] with `tr_ref` = Tr[X_{k-1}].  Returns true if the run
+// one square late because v_{k-1} needs X_{k-1}^2; on the accelerated path from n_min
+// on, Alg. 5), the end of the schedule (accelerated path), the cap, then the trace guard
+// for X_k, which compares Tr[X_k] with `tr_ref` = Tr[X_{k-1}] (accelerated path: only
+// from n_min on, where the polynomials are the plain ones).  Returns true if the run
 // stops; single thread.
 __device__ __forceinline__ bool record_and_test(DevState* st, int pk, double v_prev, double tr_new,
                                                 double tr_ref) {
@@ -86,11 +174,15 @@ __device__ __forceinline__ bool record_and_test(DevState* st, int pk, double v_p
     st->status = SP2_ERR_NONFINITE; st->out_mode = OUT_NAN; st->n_out = i;
   } else if (k == 1 && v_prev == 0.0) {
     st->reason = SP2_STOP_EXACT; st->n_out = 0; st->out_buf = 0;
-  } else if (i >= 2 && st->p[i] != st->p[i - 1] && order_test_stops(st->v[i], st->v[i - 2], st->qtilde)) {
+  } else if (i >= (st->acc ? max(2, st->n_min) : 2) && st->p[i] != st->p[i - 1] &&
+             order_test_stops(st->v[i], st->v[i - 2], st->qtilde)) {
     st->reason = SP2_STOP_ORDER; st->n_out = i; st->out_buf = i & 1;
+  } else if (st->acc && i >= st->n_max) {
+    st->reason = SP2_STOP_SCHEDULE; st->n_out = i; st->out_buf = i & 1;
   } else if (i >= st->max_iter) {
     st->reason = SP2_STOP_CAP; st->n_out = i; st->out_buf = i & 1;
-  } else if (st->guard && ((pk == 1 && tr_new >= tr_ref) || (pk == 0 && tr_new <= tr_ref))) {
+  } else if (st->guard && (!st->acc || k >= st->n_min) &&
+             ((pk == 1 && tr_new >= tr_ref) || (pk == 0 && tr_new <= tr_ref))) {
     st->reason = SP2_STOP_TRACE_GUARD; st->n_out = k; st->out_buf = k & 1;
   } else {
     stop = false;

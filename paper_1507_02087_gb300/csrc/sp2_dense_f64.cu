@@ -103,6 +103,9 @@ init_kernel(DevState* st, const double* __restrict__ F, int64_t ldf, const doubl
       st->status = SP2_ERR_NO_GAP; st->done = 1; st->out_mode = OUT_NAN;
     } else {
       st->tr[0] = t;
+      if (st->acc && !acc_schedule(st)) {   // SP2-ACC: Alg. 4 from the bounds just found
+        st->status = SP2_ERR_INVALID_ARG; st->done = 1; st->out_mode = OUT_NAN;
+      }
     }
   }
 }
@@ -130,8 +133,11 @@ __global__ void scale_kernel(const DevState* st, const double* __restrict__ F, i
 // Tr[X_k] go to a per-tile slot, summed in a fixed order by the finalize kernel.
 constexpr int kTile = 64, kTK = 16, kSyrkThreads = 256;
 
+// gen = 1 (accelerated path): X_k = ca S + cb X + cc I, the identity term on the N true
+// diagonal entries only (the zero border stays zero).
 __device__ __forceinline__ void syrk_f64_tile(const double* __restrict__ Xin, double* __restrict__ Xout, int ld,
-                                              int pk, double* __restrict__ part) {
+                                              int pk, double* __restrict__ part, int gen = 0, double ca = 0.0,
+                                              double cb = 0.0, double cc = 0.0, int N = 0) {
   __shared__ double As[2][kTK][kTile + 1];
   __shared__ double Bs[2][kTK][kTile + 1];
   __shared__ double sred[32];
@@ -197,7 +203,7 @@ __device__ __forceinline__ void syrk_f64_tile(const double* __restrict__ Xin, do
       const double s = acc[r][c];
       const double d = x - s;
       v2 = fma(d, d, v2);
-      const double xn = pk ? s : (2.0 * x - s);
+      const double xn = gen ? fma(ca, s, fma(cb, x, (gi == gj && gi < N) ? cc : 0.0)) : (pk ? s : (2.0 * x - s));
       Xout[(int64_t)gi * ld + gj] = xn;
       if (I != J) Xout[(int64_t)gj * ld + gi] = xn;
       if (gi == gj) trace += xn;
@@ -219,6 +225,12 @@ syrk_f64_kernel(const DevState* st, double* buf0, double* buf1, double* __restri
   const int kprev = st->k;                      // X_{k-1} with k = kprev + 1
   const double* Xin = (kprev & 1) ? buf1 : buf0;
   double* Xout = (kprev & 1) ? buf0 : buf1;
+  if (st->acc) {                                // Alg. 5: the scheduled polynomial
+    double ca, cb, cc;
+    const int pk = acc_step(st, kprev + 1, ca, cb, cc);
+    syrk_f64_tile(Xin, Xout, st->ld, pk, part, 1, ca, cb, cc, st->N);
+    return;
+  }
   const int pk = st->tr[kprev] > (double)st->nocc ? 1 : 0;   // Alg. 3 trace test
   syrk_f64_tile(Xin, Xout, st->ld, pk, part);
 }
@@ -265,10 +277,11 @@ finalize_kernel(DevState* st, const double* __restrict__ part, int nparts, int s
   if (threadIdx.x != 0) return;
 
   const int k = st->k + 1;                       // the square just completed
-  const int pk = st->tr[k - 1] > (double)st->nocc ? 1 : 0;
+  double ca = 0.0, cb = 0.0, cc = 0.0;
+  const int pk = st->acc ? acc_step(st, k, ca, cb, cc) : (st->tr[k - 1] > (double)st->nocc ? 1 : 0);
   double tr_new, tr_ref;
   if (stride > 2) {
-    tr_new = pk ? b : 2.0 * c - b;
+    tr_new = st->acc ? ca * b + cb * c + cc * (double)st->N : (pk ? b : 2.0 * c - b);
     tr_ref = c;
   } else {
     tr_new = b;
@@ -313,7 +326,8 @@ finalize_plain_kernel(DevState* st, const double* __restrict__ part, int nparts)
   b = block_sum<kFinThreads>(b, sm);
   if (threadIdx.x != 0) return;
   const int k = st->k + 1;
-  const int pk = st->tr[k - 1] > (double)st->nocc ? 1 : 0;
+  double ca, cb, cc;
+  const int pk = st->acc ? acc_step(st, k, ca, cb, cc) : (st->tr[k - 1] > (double)st->nocc ? 1 : 0);
   record_and_test(st, pk, sqrt(a), b, st->tr[k - 1]);
 }
 

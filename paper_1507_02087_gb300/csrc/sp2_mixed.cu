@@ -134,6 +134,9 @@ batch_init_kernel(const Instance* inst, int count, int pb, BatchPtrs ptrs, const
       st->status = SP2_ERR_NO_GAP; st->done = 1; st->out_mode = OUT_NAN;
     } else {
       st->tr[0] = t;
+      if (st->acc && !acc_schedule(st)) {   // SP2-ACC: Alg. 4 from the bounds just found
+        st->status = SP2_ERR_INVALID_ARG; st->done = 1; st->out_mode = OUT_NAN;
+      }
     }
   }
 }
@@ -192,8 +195,16 @@ __global__ void __launch_bounds__(kFT) batch_finalize_kernel(const Instance* ins
   c = block_sum<kFT>(c, sm);
   if (threadIdx.x != 0) return;
   const int k = st->k + 1;
-  const int pk = st->tr[k - 1] > (double)st->nocc ? 1 : 0;
-  const double tr_new = pk ? b : 2.0 * c - b;
+  double tr_new;
+  int pk;
+  if (st->acc) {   // Alg. 5: X_k = a X^2 + b X + c I, so Tr[X_k] = a ||X||_F^2 + b Tr[X] + c N
+    double ca, cb, cc;
+    pk = acc_step(st, k, ca, cb, cc);
+    tr_new = ca * b + cb * c + cc * (double)st->N;
+  } else {
+    pk = st->tr[k - 1] > (double)st->nocc ? 1 : 0;
+    tr_new = pk ? b : 2.0 * c - b;
+  }
   record_and_test(st, pk, sqrt(a), tr_new, c);
 }
 

@@ -57,8 +57,8 @@ constexpr int P_NBUF = 2;
 constexpr int P_EPI_WARPS = 8;
 constexpr int P_THREADS = 128 + 32 * P_EPI_WARPS;  // warpgroup 0: TMA, MMA, two idle warps
 constexpr int P_REG_LAUNCH = 168;    // 65536 / 384, rounded down to a multiple of 8
-constexpr int P_REG_CTRL = 56;
-constexpr int P_REG_EPI = 224;
+constexpr int P_REG_CTRL = 40;
+constexpr int P_REG_EPI = 232;
 static_assert(P_NBUF * PT <= 512, "tensor memory columns");
 static_assert(P_REG_CTRL + 2 * P_REG_EPI <= 3 * P_REG_LAUNCH, "register split exceeds the launch budget");
 static_assert(P_REG_LAUNCH * P_THREADS <= 65536, "launch registers");

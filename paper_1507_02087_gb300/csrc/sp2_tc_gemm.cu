@@ -37,13 +37,28 @@ static_assert(BM == BN, "square tiles");
 struct Resolved {
   int a[2], b[2], in, out, pk;
   bool active;
+  // accelerated path (gen = 1): new = ca C + cb in + cc I (identity on the N true diagonal
+  // entries; cc = 0 for derivative steps)
+  int gen;
+  float ca, cb, cc;
 };
+
+// coefficients of step j of the accelerated schedule into R (derivative steps: no c)
+__device__ __forceinline__ void acc_coefs(const DevState* st, int j, bool deriv, Resolved& r) {
+  double a, b, c;
+  r.pk = acc_step(st, j, a, b, c);
+  r.gen = 1;
+  r.ca = (float)a;
+  r.cb = (float)b;
+  r.cc = deriv ? 0.f : (float)c;
+}
 
 __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
   Resolved r;
   r.a[0] = j.a_slot[0]; r.a[1] = j.a_slot[1];
   r.b[0] = j.b_slot[0]; r.b[1] = j.b_slot[1];
   r.in = j.a_slot[0]; r.out = j.out_slot; r.pk = 1; r.active = true;
+  r.gen = 0; r.ca = r.cb = r.cc = 0.f;
   if (j.rule == SLOTS_FIXED) return r;
   const DevState* st = I.st;
   const bool ok_run = st->status == SP2_OK && st->out_mode == OUT_COPY;
@@ -53,6 +68,7 @@ __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
       r.a[0] = r.b[0] = r.in = xslot(I.lowmem, I.hist0, k);
       r.out = xslot(I.lowmem, I.hist0, k + 1);
       r.pk = st->tr[k] > (double)st->nocc ? 1 : 0;   // Alg. 3 trace test
+      if (st->acc) acc_coefs(st, k + 1, false, r);   // Alg. 5: the scheduled polynomial
       r.active = !st->done;
       break;
     }
@@ -61,6 +77,7 @@ __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
       r.a[0] = r.b[0] = r.in = rslot(1, I.hist0, jj - 1);
       r.out = rslot(1, I.hist0, jj);
       r.pk = st->p[jj];
+      if (st->acc) acc_coefs(st, jj, false, r);
       r.active = I.lowmem && ok_run && jj < st->n_out;
       break;
     }
@@ -72,6 +89,7 @@ __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
       r.a[1] = di; r.b[1] = xs;
       r.in = di; r.out = I.dx0 + (jj & 1);
       r.pk = st->p[jj];
+      if (st->acc) acc_coefs(st, jj, true, r);   // d(a X^2 + b X) = a (X dX + dX X) + b dX
       r.active = ok_run && st->dk < st->n_out;
       break;
     }
@@ -230,7 +248,12 @@ __device__ __forceinline__ void epilogue_chunk(const Job& job, const Instance& I
         #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float sj = s[8 * h + j];
-          xn[j] = R.pk ? sj : fmaf(2.0f, x[j], -sj);
+          if (R.gen) {
+            const float id = (cb + j == r && r < In.st->N) ? R.cc : 0.f;
+            xn[j] = fmaf(R.ca, sj, fmaf(R.cb, x[j], id));
+          } else {
+            xn[j] = R.pk ? sj : fmaf(2.0f, x[j], -sj);
+          }
           if (job.mode == MODE_SP2_STEP) {
             const int c = cb + j;
             const float d = x[j] - sj;

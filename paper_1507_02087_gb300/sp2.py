@@ -21,7 +21,7 @@ SP2_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA runtime error", 3: "non-finite value in F",
           4: "device-side wait timed out", 5: "out of device memory", 6: "no gap (F = cI)",
           7: "unsupported option"}
-STOP_ORDER, STOP_TRACE_GUARD, STOP_EXACT, STOP_CAP = 0, 1, 2, 3
+STOP_ORDER, STOP_TRACE_GUARD, STOP_EXACT, STOP_CAP, STOP_SCHEDULE = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": 0, "mixed": 1}
 MAX_ITER = 512
 
@@ -77,6 +77,10 @@ def lib() -> ctypes.CDLL:
         L.sp2_test_tc_gemm.restype = i32
         L.sp2_run_fp64_noalloc.argtypes = [vp, vp, i64, i64, vp, vp]
         L.sp2_run_fp64_noalloc.restype = i32
+        L.sp2_set_homo_lumo.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.sp2_set_homo_lumo.restype = i32
+        L.sp2_set_homo_lumo_batch.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
+        L.sp2_set_homo_lumo_batch.restype = i32
         L.sp2_create_batch.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(i64), i32,
                                        ctypes.POINTER(sp2_opts), ctypes.POINTER(vp)]
         L.sp2_create_batch.restype = i32
@@ -152,6 +156,21 @@ def sp2_run(h: int, F, D, stream=None) -> None:
 def sp2_run_host(h: int, F: np.ndarray, D: np.ndarray, stream=None) -> None:
     """Host buffers in and out (copies inside the call); returns when D is written."""
     _check(lib().sp2_run_host(h, F.ctypes.data, D.ctypes.data, _stream_ptr(stream)), "sp2_run_host")
+
+
+def _bounds4(bounds):
+    if bounds is None:
+        return None
+    b = [float(x) for x in bounds]
+    if len(b) != 4:
+        raise ValueError("bounds = (homo_out, homo_in, lumo_in, lumo_out)")
+    return (ctypes.c_double * 4)(*b)
+
+
+def sp2_set_homo_lumo(h: int, bounds) -> None:
+    """SP2-ACC (Alg. 4/5) with homo/lumo bounds (homo_out, homo_in, lumo_in, lumo_out) for
+    the handle's following runs; None returns to the trace-based expansion."""
+    _check(lib().sp2_set_homo_lumo(h, _bounds4(bounds)), "sp2_set_homo_lumo")
 
 
 def sp2_get_info(h: int) -> dict:
@@ -301,6 +320,9 @@ class BatchPurifier:
     def info(self, i: int) -> dict:
         return sp2_get_info_batch(self.h, i)
 
+    def set_homo_lumo(self, i: int, bounds) -> None:
+        _check(lib().sp2_set_homo_lumo_batch(self.h, i, _bounds4(bounds)), "sp2_set_homo_lumo_batch")
+
     def close(self):
         sp2_destroy_batch(self.h)
         self.h = 0
@@ -344,6 +366,9 @@ class Purifier:
 
     def info(self) -> dict:
         return sp2_get_info(self.h)
+
+    def set_homo_lumo(self, bounds) -> None:
+        sp2_set_homo_lumo(self.h, bounds)
 
     def close(self):
         sp2_destroy(self.h)
