@@ -63,6 +63,9 @@ def parse():
                     help="mixed path: refinement pair on the tensor cores or in FP64")
     ap.add_argument("--fp64-sample-squares", type=int, default=0,
                     help="with --fp64-steps 0: time this many FP64 squares and estimate the FP64 time-to-D")
+    ap.add_argument("--acc", type=float, default=None, metavar="SLACK",
+                    help="SP2-ACC (homo/lumo-based accelerated expansion) with the construction's homo and lumo "
+                         "eigenvalues as inner bounds and SLACK as the distance of the outer ones")
     ap.add_argument("--rule", choices=["error", "block"], default="error",
                     help="block-sparse truncation rule of the headline line (both rules are reported)")
     ap.add_argument("--N", type=int, default=N_DEFAULT)
@@ -412,6 +415,13 @@ def main():
     D = torch.empty_like(F)
     stream = torch.cuda.current_stream()
     P = sp2.Purifier(N, nocc, a.precision, refine_fp64=(a.refine == "fp64"))
+    acc_bounds = None
+    if a.acc is not None:
+        import numpy as np
+        lam = np.sort(np.asarray(case.lam))
+        homo, lumo = float(lam[nocc - 1]), float(lam[nocc])
+        acc_bounds = (homo - a.acc, homo, lumo, lumo + a.acc)
+        P.set_homo_lumo(acc_bounds)
 
     def err_vs_exact():
         return float(torch.linalg.norm(D - D_exact)) / math.sqrt(nocc)
@@ -491,6 +501,8 @@ def main():
     fp64 = None
     if mixed and a.fp64_steps > 0:
         with sp2.Purifier(N, nocc, "fp64") as P64:
+            if acc_bounds is not None:
+                P64.set_homo_lumo(acc_bounds)
             D64 = torch.empty_like(F)
             tms = []
             for _ in range(a.fp64_steps):
@@ -571,6 +583,8 @@ def main():
                            f"dense N={N} nocc={nocc} gap={a.gap:g}, Q = 64 Householder reflectors (seed 3)",
                            "N": N, "nocc": nocc, "gap": a.gap,
                            "precision": a.precision, "refine": a.refine if mixed else None,
+                           "expansion": "SP2-ACC (homo/lumo bounds, slack %g)" % a.acc if a.acc is not None
+                           else "SP2 (trace-based)",
                            "parallelism": "replicas" if ws > 1 else "1 GPU",
                            "l2": "no flush: F 512 MiB and the streamed iterates exceed the 129 MB L2"},
                 "err_vs_exact": err, "err_first_run": err_first, "meets_tolerance": bool(err <= TOL and status_ok),
