@@ -59,8 +59,9 @@ def parse():
                          "in [128, 2048], seed 1; bsr: gapped tight-binding 32^3 lattice, 32 x 32 blocks, "
                          "block truncation tau in {1e-4, 1e-6}")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--refine", choices=["tc", "fp64"], default="tc",
-                    help="mixed path: refinement pair on the tensor cores or in FP64")
+    ap.add_argument("--refine", choices=["tc", "fp64", "mcweeny"], default="tc",
+                    help="mixed path: refinement pair on the tensor cores (tc) or in FP64 (fp64), or one "
+                         "McWeeny step with its square in FP64 (mcweeny)")
     ap.add_argument("--fp64-sample-squares", type=int, default=0,
                     help="with --fp64-steps 0: time this many FP64 squares and estimate the FP64 time-to-D")
     ap.add_argument("--acc", type=float, default=None, metavar="SLACK",
@@ -414,7 +415,7 @@ def main():
     D_exact = case.D_exact
     D = torch.empty_like(F)
     stream = torch.cuda.current_stream()
-    P = sp2.Purifier(N, nocc, a.precision, refine_fp64=(a.refine == "fp64"))
+    P = sp2.Purifier(N, nocc, a.precision, refine_fp64={"tc": 0, "fp64": 1, "mcweeny": 2}[a.refine])
     acc_bounds = None
     if a.acc is not None:
         import numpy as np
@@ -576,8 +577,9 @@ def main():
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None,
-                "dtype": ("bf16x6->f32 (mixed), f64 reductions" + (", f64 refinement pair" if a.refine == "fp64"
-                                                                   else "")) if mixed else "f64",
+                "dtype": ("bf16x6->f32 (mixed), f64 reductions" + {"tc": "", "fp64": ", f64 refinement pair",
+                                                                    "mcweeny": ", f64-square McWeeny step"}[a.refine])
+                if mixed else "f64",
                 "data": "synthetic",
                 "config": {"workload": workload_name(N, nocc, a.gap) if a.input == "qr" else
                            f"dense N={N} nocc={nocc} gap={a.gap:g}, Q = 64 Householder reflectors (seed 3)",

@@ -79,8 +79,12 @@ typedef struct {
   int32_t refine_steps; /* SP2_PREC_MIXED: purification steps after the correction, 0 or 2 (default 2):
                            an alternating pair, X^2 and 2X - X^2, which squares the remaining
                            eigenvalue error */
-  int32_t refine_fp64;  /* SP2_PREC_MIXED: 1 = refinement pair in FP64 (two FP64 squares),
-                           0 = on the tensor cores like the expansion (default 0) */
+  int32_t refine_fp64;  /* SP2_PREC_MIXED: 0 = refinement pair on the tensor cores like the
+                           expansion (default); 1 = the pair in FP64 (two FP64 squares); 2 = one
+                           McWeeny step 3D^2 - 2D^3 = D + E - 2DE with E = D^2 - D, the square in
+                           FP64 and the small product DE on the tensor cores (one FP64 square;
+                           squares the eigenvalue error on both sides of the gap).  1 and 2 need
+                           a single problem and two ld x ld FP64 buffers */
   int32_t launch_mode;  /* 0 = the loops run as CUDA-graph conditional WHILE nodes (default);
                            1 = the same kernels launched on the stream up to the iteration cap,
                            each returning at once after the device-side stop (same results and

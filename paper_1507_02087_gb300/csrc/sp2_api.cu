@@ -66,7 +66,7 @@ extern "C" const char* sp2_status_string(int32_t s) {
 static bool opts_valid(const sp2_opts& o) {
   return o.max_iter >= 1 && o.max_iter <= SP2_MAX_ITER && o.qtilde > 0.0 && (o.guard == 0 || o.guard == 1) &&
          o.corrections >= 0 && o.corrections <= 1 && (o.refine_steps == 0 || o.refine_steps == 2) &&
-         (o.refine_fp64 == 0 || o.refine_fp64 == 1) && (o.launch_mode == 0 || o.launch_mode == 1) &&
+         (o.refine_fp64 >= 0 && o.refine_fp64 <= 2) && (o.launch_mode == 0 || o.launch_mode == 1) &&
          o.history >= 0 && o.history <= 2 && o.tile >= 0 && o.tile <= 2;
 }
 
@@ -359,7 +359,7 @@ struct MixedEngine {
     *err_host = 0;
     if (o.refine_steps > 0 && o.refine_fp64) {
       if (count != 1) return SP2_ERR_UNSUPPORTED;
-      fld = (int)((N[0] + 63) / 64 * 64);
+      fld = inst_host[0].ld;   // the FP64 buffers share the tensor-core layout's ld (a multiple of 64)
       const size_t fb = (size_t)fld * fld * sizeof(double);
       const int T = fld / 64;
       if (cudaMalloc(&fbuf[0], fb) != cudaSuccess || cudaMalloc(&fbuf[1], fb) != cudaSuccess ||
@@ -460,7 +460,18 @@ struct MixedEngine {
     }
     SP2_TRY(cudaEventRecord(ev[1], s));
     const int use_dx = opts.corrections > 0;
-    if (opts.refine_steps > 0 && opts.refine_fp64) {
+    if (opts.refine_steps > 0 && opts.refine_fp64 == 2) {
+      // one McWeeny step: FP64 square, E = D^2 - D, D E on the tensor cores, D + E - 2 D E
+      SP2_TRY(sp2::batch_launch_assemble(inst_dev, count, sb, use_dx, 0, ptrs, fbuf[0], s));
+      SP2_TRY(sp2::launch_refine_f64(st_dev, fbuf[0], fbuf[1], fld, 2, fpart, s));
+      SP2_TRY(sp2::launch_mcw_split(inst_dev, fbuf[0], fbuf[1], sb, s));
+      sp2::tc::Job jm = job(sp2::tc::MODE_STORE_PIECES, 1, sp2::tc::SLOTS_FIXED);
+      jm.a_slot[0] = inst_host[0].r0_slot;
+      jm.b_slot[0] = inst_host[0].r0_slot + 1;
+      jm.out_slot = inst_host[0].m_slot;
+      SP2_TRY(sp2::tc_launch(jm, s));
+      SP2_TRY(sp2::launch_mcw_out(inst_dev, fbuf[0], fbuf[1], ptrs, sb, s));
+    } else if (opts.refine_steps > 0 && opts.refine_fp64) {
       SP2_TRY(sp2::batch_launch_assemble(inst_dev, count, sb, use_dx, 0, ptrs, fbuf[0], s));
       SP2_TRY(sp2::launch_refine_f64(st_dev, fbuf[0], fbuf[1], fld, 0, fpart, s));
       SP2_TRY(sp2::launch_refine_f64(st_dev, fbuf[1], fbuf[0], fld, 1, fpart, s));

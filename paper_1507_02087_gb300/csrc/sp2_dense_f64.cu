@@ -244,7 +244,7 @@ refine_f64_kernel(const DevState* st, const double* Xin, double* Xout, int ld, i
                   double* __restrict__ part) {
   if (st->status != SP2_OK || st->out_mode != OUT_COPY) return;
   const int plast = st->p[st->n_out];
-  const int pk = step == 0 ? 1 - plast : plast;
+  const int pk = step == 2 ? 1 : (step == 0 ? 1 - plast : plast);   // step 2: the plain square X^2
   syrk_f64_tile(Xin, Xout, ld, pk, part);
 }
 

@@ -74,5 +74,10 @@ cudaError_t batch_launch_corrected_to_pieces(const tc::Instance* inst, int count
                                              cudaStream_t s);
 cudaError_t batch_launch_assemble(const tc::Instance* inst, int count, int sb, int use_dx, int from_r0,
                                   const BatchPtrs& ptrs, double* f64_buf, cudaStream_t s);
+// one FP64-accurate McWeeny step on a single problem (D in Dbuf, S = D^2 in Sbuf, ld = the
+// instance's ld): split E = S - D and the pieces of D, E; then D + E - 2 D E into ptrs.D[0]
+cudaError_t launch_mcw_split(const tc::Instance* inst, const double* Dbuf, double* Sbuf, int sb, cudaStream_t s);
+cudaError_t launch_mcw_out(const tc::Instance* inst, const double* Dbuf, const double* Ebuf, const BatchPtrs& ptrs,
+                           int sb, cudaStream_t s);
 
 }  // namespace sp2

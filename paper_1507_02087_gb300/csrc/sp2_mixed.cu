@@ -308,6 +308,65 @@ __global__ void batch_assemble_kernel(const Instance* inst, int count, int sb, i
   }
 }
 
+// ---- one FP64-accurate McWeeny step (refinement option 2, single problem) --------------------
+// p(D) = 3 D^2 - 2 D^3 = D + E - 2 D E with E = D^2 - D.  D^2 comes from the FP64 square; E is
+// tiny next to D, so the product D E runs on the tensor cores (its FP32-level relative error
+// lands far below the FP64 error of E).  Each eigenvalue error e of D becomes about 3 e^2, on
+// both sides of the gap.
+// mcw_split: E = S - D in place of S = D^2 (FP64, both ld x ld), D and E as pieces into the
+// refinement slots r0 and r0 + 1.
+__global__ void mcw_split_kernel(const Instance* inst, const double* Dbuf, double* Sbuf, int sb) {
+  const Instance& In = inst[0];
+  const DevState* st = In.st;
+  if (st->status != SP2_OK || st->out_mode != OUT_COPY) return;
+  const int N = st->N, ld = In.ld;
+  const int64_t plane = (int64_t)ld * ld;
+  __nv_bfloat16* Dp = In.arena + (int64_t)In.r0_slot * In.slot_elems;
+  __nv_bfloat16* Ep = In.arena + (int64_t)(In.r0_slot + 1) * In.slot_elems;
+  const int64_t total = (int64_t)N * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)sb * blockDim.x) {
+    const int r = (int)(e / N), c = (int)(e % N);
+    const int64_t off = (int64_t)r * ld + c;
+    const double d = Dbuf[off];
+    const double ev = Sbuf[off] - d;
+    Sbuf[off] = ev;
+    __nv_bfloat16 a, b, cc;
+    split3_((float)d, a, b, cc);
+    Dp[off] = a; Dp[plane + off] = b; Dp[2 * plane + off] = cc;
+    split3_((float)ev, a, b, cc);
+    Ep[off] = a; Ep[plane + off] = b; Ep[2 * plane + off] = cc;
+  }
+}
+
+// mcw_out: D_out = D + E - 2 P, P = D E from the pieces in m_slot (the output modes of the
+// special cases as in batch_assemble_kernel).
+__global__ void mcw_out_kernel(const Instance* inst, const double* Dbuf, const double* Ebuf, BatchPtrs ptrs,
+                               int sb) {
+  const Instance& In = inst[0];
+  const DevState* st = In.st;
+  const int N = st->N, ld = In.ld;
+  const int mode = st->out_mode;
+  const int64_t plane = (int64_t)ld * ld;
+  const __nv_bfloat16* Pp = In.arena + (int64_t)In.m_slot * In.slot_elems;
+  double* D = ptrs.D[0];
+  const int64_t total = (int64_t)N * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)sb * blockDim.x) {
+    const int r = (int)(e / N), c = (int)(e % N);
+    double val;
+    if (mode == OUT_COPY && st->status == SP2_OK) {
+      const int64_t off = (int64_t)r * ld + c;
+      val = Dbuf[off] + Ebuf[off] - 2.0 * (double)join3_(Pp, plane, off);
+    } else if (mode == OUT_ZERO) {
+      val = 0.0;
+    } else if (mode == OUT_IDENTITY) {
+      val = (r == c) ? 1.0 : 0.0;
+    } else {
+      val = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    D[e] = val;
+  }
+}
+
 // ---- host-side launchers ------------------------------------------------------------------
 
 static cudaError_t add_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, void* func, dim3 grid,
@@ -376,4 +435,16 @@ cudaError_t batch_launch_assemble(const Instance* inst, int count, int sb, int u
   return cudaGetLastError();
 }
 
+}  // namespace sp2
+
+namespace sp2 {
+cudaError_t launch_mcw_split(const tc::Instance* inst, const double* Dbuf, double* Sbuf, int sb, cudaStream_t s) {
+  mcw_split_kernel<<<sb, 256, 0, s>>>(inst, Dbuf, Sbuf, sb);
+  return cudaGetLastError();
+}
+cudaError_t launch_mcw_out(const tc::Instance* inst, const double* Dbuf, const double* Ebuf, const BatchPtrs& ptrs,
+                           int sb, cudaStream_t s) {
+  mcw_out_kernel<<<sb, 256, 0, s>>>(inst, Dbuf, Ebuf, ptrs, sb);
+  return cudaGetLastError();
+}
 }  // namespace sp2

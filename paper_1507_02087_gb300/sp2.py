@@ -131,13 +131,13 @@ def _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launc
           tile="auto"):
     if launch_mode is None:
         launch_mode = int(os.environ.get("SP2_LAUNCH_MODE", "0"))
-    return sp2_opts(max_iter, 1 if guard else 0, qtilde, corrections, refine_steps, 1 if refine_fp64 else 0,
+    return sp2_opts(max_iter, 1 if guard else 0, qtilde, corrections, refine_steps, int(refine_fp64),
                     launch_mode, HISTORY[history], TILES[tile])
 
 
 def sp2_create(N: int, nocc: int, precision: str = "fp64", *, max_iter: int = 200, guard: bool = True,
                qtilde: float = 1.8, corrections: int = 1, refine_steps: int = 2,
-               refine_fp64: bool = False, launch_mode: int | None = None, history: str = "auto",
+               refine_fp64: int = 0, launch_mode: int | None = None, history: str = "auto",
                tile: str = "auto") -> int:
     """launch_mode None reads SP2_LAUNCH_MODE from the environment (default 0, the graph).
     history: "auto", "full" (keep every iterate) or "recompute" (low memory).
@@ -181,7 +181,7 @@ def sp2_get_info(h: int) -> dict:
 
 def sp2_create_batch(Ns, noccs, precision: str = "mixed", *, max_iter: int = 200, guard: bool = True,
                      qtilde: float = 1.8, corrections: int = 1, refine_steps: int = 2,
-                     refine_fp64: bool = False, launch_mode: int | None = None, history: str = "auto",
+                     refine_fp64: int = 0, launch_mode: int | None = None, history: str = "auto",
                      tile: str = "auto") -> int:
     count = len(Ns)
     o = _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history, tile)

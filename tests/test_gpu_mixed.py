@@ -73,14 +73,30 @@ def test_mixed_options(sp2mod):
     for key, opts in {"none": dict(corrections=0, refine_steps=0),
                       "tc": dict(corrections=0, refine_steps=2),
                       "corr+tc": dict(corrections=1, refine_steps=2),
-                      "corr+fp64": dict(corrections=1, refine_steps=2, refine_fp64=True)}.items():
+                      "corr+fp64": dict(corrections=1, refine_steps=2, refine_fp64=1),
+                      "corr+mcw": dict(corrections=1, refine_steps=2, refine_fp64=2)}.items():
         D, info = run_gpu(sp2mod, case.F, 300, **opts)
         assert info["status"] == 0
         errs[key] = o.rel_error(D.cpu().numpy(), ref.D, 300)
     # The refinement pair removes eigenvalue error but not subspace error; with it in
     # place, the correction must remove most of the low-precision subspace error.
     assert errs["corr+tc"] < errs["tc"] / 3
-    assert errs["corr+tc"] <= TOL_MIXED and errs["corr+fp64"] <= TOL_MIXED
+    assert errs["corr+tc"] <= TOL_MIXED and errs["corr+fp64"] <= TOL_MIXED and errs["corr+mcw"] <= TOL_MIXED
+
+
+@pytest.mark.parametrize("refine", [1, 2])
+def test_fp64_refinements_with_padded_ld(sp2mod, refine):
+    # N = 600 on CTA-pair tiles: ld = 768, not N rounded to 64; the FP64 buffers must use it.
+    # refine 1: the pair in FP64; refine 2: one McWeeny step, its square in FP64
+    case = inputs.dense_gapped(600, 300, gap=0.05, seed=3)
+    ref = o.sp2(case.F.numpy(), 300)
+    D, info = run_gpu(sp2mod, case.F, 300, tile="pair", refine_fp64=refine)
+    assert info["status"] == 0 and info["tile"] == "pair"
+    assert o.rel_error(D.cpu().numpy(), ref.D, 300) <= TOL_MIXED
+    inv = o.invariants(case.F.numpy(), D.cpu().numpy(), 300)
+    # the FP64 steps square the eigenvalue error e of the corrected D (~4e^2 for the pair,
+    # ~3e^2 for McWeeny, e ~ 1e-4 here): far below the FP32 floor, not at FP64 rounding
+    assert inv["idem_err"] < 1e-6 and inv["trace_err"] < 1e-6
 
 
 @pytest.mark.parametrize("N,nocc,tile", [(1500, 700, "128"), (1500, 700, "pair"), (700, 350, "pair")])
