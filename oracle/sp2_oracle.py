@@ -92,6 +92,18 @@ def idempotency_error_spectral(X: np.ndarray, X2: np.ndarray) -> float:
     return float(np.max(np.abs(w)))
 
 
+def mixed_norm(A: np.ndarray, b: int) -> float:
+    """||A||_M (§2): the spectral norm of the matrix of Frobenius norms of the b x b blocks of
+    A (zero-padded to a multiple of b).  e <= m <= v for e = ||A||_2, v = ||A||_F."""
+    A = np.asarray(A, dtype=np.float64)
+    N = A.shape[0]
+    nb = -(-N // b)
+    P = np.zeros((nb * b, nb * b))
+    P[:N, :N] = A
+    M = np.sqrt((P.reshape(nb, b, nb, b) ** 2).sum(axis=(1, 3)))
+    return float(np.linalg.norm(M, 2))
+
+
 def order_test_stops(v_i: float, v_im2: float, qtilde: float = QTILDE, C: float = C2_SP) -> bool:
     """Alg. 3 stop condition log(v_i/C)/log(v_{i-2}) < qtilde, evaluated only when
     v_{i-2} < 1 (see the module notes)."""
@@ -106,13 +118,14 @@ def order_test_stops(v_i: float, v_im2: float, qtilde: float = QTILDE, C: float 
 
 def sp2(F: np.ndarray, nocc: int, *, bounds: tuple[float, float] | None = None,
         max_iter: int = 200, qtilde: float = QTILDE, norm: str = "fro", guard: bool = True,
-        perturb=None) -> SP2Result:
+        perturb=None, block: int = 128) -> SP2Result:
     """Alg. 3 step by step in FP64.
 
     `perturb(i, X)` (optional) returns the truncation/noise matrix E_i added to X_i
     (Alg. 1, X~_i = X_i + E_i); by default E_i = 0 (dense, no truncation).
-    `norm` is "fro" (v_i, what the GPU path uses) or "spectral" (e_i, the paper's
-    definition; eigvalsh, small N only)."""
+    `norm` is "fro" (v_i, what the GPU path uses by default), "spectral" (e_i, the paper's
+    definition; eigvalsh, small N only) or "mixed" (m_i, the mixed norm of §2 with blocks of
+    `block` x `block`)."""
     F = np.asarray(F, dtype=np.float64)
     N = F.shape[0]
     if F.shape != (N, N):
@@ -128,7 +141,11 @@ def sp2(F: np.ndarray, nocc: int, *, bounds: tuple[float, float] | None = None,
         return SP2Result(D, 0, STOP_EXACT, lmin, lmax, [], [], [None])
     if not (lmax > lmin):
         raise ValueError("F has no spectral width: there is no homo-lumo gap")
-    err = idempotency_error_fro if norm == "fro" else idempotency_error_spectral
+    if norm == "mixed":
+        def err(X, X2):
+            return mixed_norm(X - X2, block)
+    else:
+        err = idempotency_error_fro if norm == "fro" else idempotency_error_spectral
 
     X = initial_scaling(F, lmin, lmax)
     if perturb is not None:

@@ -218,3 +218,42 @@ def test_planted_wrong_lag_is_caught():
             wrong = i
             break
     assert wrong != r.n
+
+
+# ---- the mixed norm of §2 ---------------------------------------------------------------------
+
+def test_mixed_norm_between_spectral_and_frobenius():
+    g = np.random.Generator(np.random.PCG64(31))
+    for N, b in [(50, 8), (64, 16), (100, 128), (96, 1)]:
+        A = g.standard_normal((N, N))
+        A = A + A.T
+        e = float(np.linalg.norm(A, 2))
+        m = o.mixed_norm(A, b)
+        v = float(np.linalg.norm(A, "fro"))
+        assert e <= m * (1 + 1e-12) and m <= v * (1 + 1e-12)
+
+
+def test_mixed_norm_special_block_sizes():
+    g = np.random.Generator(np.random.PCG64(32))
+    A = g.standard_normal((40, 40))
+    assert o.mixed_norm(A, 1) == pytest.approx(float(np.linalg.norm(np.abs(A), 2)), rel=1e-12)
+    assert o.mixed_norm(A, 40) == pytest.approx(float(np.linalg.norm(A, "fro")), rel=1e-12)
+    assert o.mixed_norm(A, 64) == pytest.approx(float(np.linalg.norm(A, "fro")), rel=1e-12)   # padded
+    # block-diagonal with equal blocks: the largest block's Frobenius norm
+    B = np.kron(np.eye(4), np.full((8, 8), 0.5))
+    assert o.mixed_norm(B, 8) == pytest.approx(4.0, rel=1e-12)
+
+
+def test_mixed_norm_stop_on_dense_case():
+    # the stop with m_i in place of v_i reaches the same projector; for this size the mixed
+    # norm lies between e_i and v_i at every step
+    case = inputs.dense_gapped(300, 150, gap=0.05, seed=4)
+    F = case.F.numpy()
+    rm = o.sp2(F, 150, norm="mixed", block=64)
+    rs = o.sp2(F, 150, norm="spectral")
+    rf = o.sp2(F, 150)
+    for r in (rm, rs, rf):
+        assert o.rel_error(r.D, case.D_exact.numpy() if case.D_exact is not None else rf.D, 150) < 1e-12
+    k = min(len(rm.v), len(rs.v), len(rf.v))
+    assert all(rs.v[i] <= rm.v[i] * (1 + 1e-9) and rm.v[i] <= rf.v[i] * (1 + 1e-9) for i in range(k))
+    assert rf.n <= rm.n <= rs.n + 1
