@@ -103,6 +103,13 @@ typedef struct {
                            the faster one is kept (when the scratch would exceed 2 GiB, a model
                            of the two kernels' measured rates decides instead); the choice is
                            reported in sp2_info.tile */
+  int32_t norm;         /* error measure of the stop test: 0 = Frobenius v_i = ||X_i - X_i^2||_F
+                           (default); 1 = the mixed norm m_i of §2, the spectral norm of the
+                           matrix of Frobenius norms of the square kernel's tiles (64 x 64 on the
+                           FP64 path, 128 x 128 on the mixed path), e_i <= m_i <= v_i, which stays
+                           below 1 at large N where v_i may not (power iteration on the device,
+                           scratch of (ld/b)^2 doubles).  sp2_info.v holds the measure used.
+                           The block-sparse path uses v_i */
 } sp2_opts;
 
 #define SP2_MAX_ITER 512

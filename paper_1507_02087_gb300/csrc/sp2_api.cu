@@ -47,6 +47,7 @@ extern "C" void sp2_default_opts(sp2_opts* o) {
   o->launch_mode = 0;
   o->history = 0;
   o->tile = 0;
+  o->norm = 0;
 }
 
 extern "C" const char* sp2_status_string(int32_t s) {
@@ -67,7 +68,8 @@ static bool opts_valid(const sp2_opts& o) {
   return o.max_iter >= 1 && o.max_iter <= SP2_MAX_ITER && o.qtilde > 0.0 && (o.guard == 0 || o.guard == 1) &&
          o.corrections >= 0 && o.corrections <= 1 && (o.refine_steps == 0 || o.refine_steps == 2) &&
          (o.refine_fp64 >= 0 && o.refine_fp64 <= 2) && (o.launch_mode == 0 || o.launch_mode == 1) &&
-         o.history >= 0 && o.history <= 2 && o.tile >= 0 && o.tile <= 2;
+         o.history >= 0 && o.history <= 2 && o.tile >= 0 && o.tile <= 2 &&
+         (o.norm == 0 || o.norm == 1);
 }
 
 static DevState initial_state(int64_t N, int64_t nocc, const sp2_opts& o, int ld, int round_fp32) {
@@ -76,6 +78,7 @@ static DevState initial_state(int64_t N, int64_t nocc, const sp2_opts& o, int ld
   init.N = (int32_t)N; init.ld = ld; init.nocc = (int32_t)nocc;
   init.max_iter = o.max_iter; init.guard = o.guard; init.qtilde = o.qtilde;
   init.round_fp32 = round_fp32;
+  init.norm = o.norm;
   return init;
 }
 
@@ -203,6 +206,7 @@ struct MixedEngine {
   DevState* st_host = nullptr;     // pinned mirror
   std::vector<void*> arenas;
   std::vector<double*> parts;
+  std::vector<double*> mscrs;      // mixed-norm scratch per problem (norm = 1)
   double* part_lo = nullptr;
   double* part_hi = nullptr;
   int* part_bad = nullptr;
@@ -226,6 +230,7 @@ struct MixedEngine {
     cudaFree(st_dev);
     for (void* a : arenas) cudaFree(a);
     for (double* p : parts) cudaFree(p);
+    for (double* p : mscrs) cudaFree(p);
     cudaFree(part_lo);
     cudaFree(part_hi);
     cudaFree(part_bad);
@@ -338,6 +343,7 @@ struct MixedEngine {
       off_u += pair ? pair_tiles_of(ld, 1) : tiles_of(ld, 1);
       off_f += pair ? pair_tiles_of(ld, 0) : tiles_of(ld, 0);
       I.nparts = nparts_of(ld, pair);
+      I.rec_pair = pair;
       const size_t abytes = (size_t)nslots * I.slot_elems * 2;
       if (cudaMalloc(&arenas[k], abytes) != cudaSuccess ||
           cudaMalloc(&parts[k], sizeof(double) * 4 * I.nparts) != cudaSuccess) {
@@ -348,6 +354,16 @@ struct MixedEngine {
       SP2_TRY(cudaMemset(arenas[k], 0, abytes));
       I.arena = (__nv_bfloat16*)arenas[k];
       I.part = parts[k];
+      if (o.norm == 1) {
+        const int nb = ld / BM;
+        double* ms = nullptr;
+        if (cudaMalloc(&ms, sizeof(double) * ((size_t)nb * nb + 2 * nb)) != cudaSuccess) {
+          (void)cudaGetLastError();
+          return SP2_ERR_NOMEM;
+        }
+        mscrs.push_back(ms);
+        I.mscr = ms;
+      }
       SP2_TRY(sp2::tc_make_maps(arenas[k], ld, nslots, &I.mapA, &I.mapB));
       st_host[k] = initial_state(N[k], nocc[k], o, ld, 1);
     }
@@ -523,6 +539,7 @@ struct sp2_ctx {
   double* part_lo = nullptr;
   double* part_hi = nullptr;
   int* part_bad = nullptr;
+  double* mscr = nullptr;        // mixed-norm scratch (norm = 1): T^2 + 2T doubles
   DevState* st_dev = nullptr;
   DevState* st_host = nullptr;
   cudaGraph_t graph = nullptr;
@@ -545,6 +562,7 @@ static void free_ctx(sp2_ctx* h) {
   cudaFree(h->buf[0]);
   cudaFree(h->buf[1]);
   cudaFree(h->part);
+  cudaFree(h->mscr);
   cudaFree(h->part_lo);
   cudaFree(h->part_hi);
   cudaFree(h->part_bad);
@@ -573,6 +591,8 @@ static sp2_status create_f64(sp2_ctx* h) {
             cudaMallocHost(&h->st_host, sizeof(DevState)) == cudaSuccess &&
             cudaEventCreate(&h->ev_loop[0]) == cudaSuccess && cudaEventCreate(&h->ev_loop[1]) == cudaSuccess &&
             cudaMalloc(&h->buf[0], bytes) == cudaSuccess && cudaMalloc(&h->buf[1], bytes) == cudaSuccess;
+  if (ok && h->opts.norm == 1)
+    ok = cudaMalloc(&h->mscr, sizeof(double) * ((size_t)h->T * h->T + 2 * h->T)) == cudaSuccess;
   if (!ok) { (void)cudaGetLastError(); return SP2_ERR_NOMEM; }
   DevState init = initial_state(h->N, h->nocc, h->opts, h->ld, 0);
   SP2_TRY(cudaMemcpy(h->st_dev, &init, sizeof(init), cudaMemcpyHostToDevice));
@@ -584,7 +604,7 @@ static sp2_status create_f64(sp2_ctx* h) {
   cudaGraph_t body;
   sp2_status s = add_while(h->graph, nullptr, 0, &h->cond, &node, &body);
   if (s != SP2_OK) return s;
-  SP2_TRY(sp2::add_f64_loop_body(body, h->st_dev, h->buf[0], h->buf[1], h->part, h->T, h->cond));
+  SP2_TRY(sp2::add_f64_loop_body(body, h->st_dev, h->buf[0], h->buf[1], h->part, h->T, h->cond, h->mscr));
   SP2_TRY(cudaGraphInstantiate(&h->exec, h->graph, 0));
   return SP2_OK;
 }
@@ -631,7 +651,7 @@ static sp2_status enqueue_f64(sp2_ctx* h, const double* F, double* D, cudaStream
     SP2_TRY(cudaGraphLaunch(h->exec, s));
   } else {
     for (int it = 0; it <= h->opts.max_iter; ++it)
-      SP2_TRY(sp2::launch_f64_step_plain(h->st_dev, h->buf[0], h->buf[1], h->part, h->T, s));
+      SP2_TRY(sp2::launch_f64_step_plain(h->st_dev, h->buf[0], h->buf[1], h->part, h->T, s, h->mscr));
   }
   SP2_TRY(cudaEventRecord(h->ev_loop[1], s));
   SP2_TRY(sp2::launch_copy_out(h->st_dev, h->buf[0], h->buf[1], h->ld, N, D, N, s));

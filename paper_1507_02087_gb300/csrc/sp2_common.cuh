@@ -47,7 +47,7 @@ struct DevState {
   int32_t dk;          // derivative steps completed (mixed path correction)
   int32_t round_fp32;  // 1: X_0 is rounded to FP32 (mixed path)
   int32_t iter_active; // block-sparse path: the current loop round squares (set at its start)
-  int32_t _pad1;
+  int32_t norm;        // error measure of the stop: 0 = Frobenius v_i, 1 = mixed norm m_i (§2)
   // block-sparse path, work of the current run's squares: 32 x 32 block products and
   // upper blocks of the squares computed
   unsigned long long bprod;
@@ -209,6 +209,54 @@ __device__ __forceinline__ double block_sum(double x, double* smem) {
   t = smem[0];
   __syncthreads();
   return t;
+}
+
+// Index of upper tile (I, J), I <= J, in a T x T grid whose upper tiles are numbered by rows.
+__host__ __device__ __forceinline__ int64_t upper_index(int I, int J, int T) {
+  return (int64_t)I * T - (int64_t)I * (I - 1) / 2 + (J - I);
+}
+
+// Mixed norm (§2): the spectral norm of the nb x nb matrix of block Frobenius norms, from
+// `block_n2(I, J)` = ||block (I, J)||_F^2 for I <= J (the matrix is symmetric).  One CTA of
+// NT threads: the matrix goes to `scr` (nb^2 doubles, then two vectors of nb), and its
+// largest eigenvalue comes from kMixedIters power steps from the all-ones vector, the last
+// one as a Rayleigh quotient; every sum in a fixed order.
+constexpr int kMixedIters = 200;
+
+template <int NT, class BlockN2>
+__device__ double mixed_norm_cta(int nb, double* scr, double* sm, BlockN2 block_n2) {
+  double* M = scr;
+  double* x = scr + (int64_t)nb * nb;
+  double* y = x + nb;
+  const int tid = threadIdx.x;
+  for (int64_t e = tid; e < (int64_t)nb * nb; e += NT) {
+    const int I = (int)(e / nb), J = (int)(e % nb);
+    M[e] = sqrt(fmax(block_n2(min(I, J), max(I, J)), 0.0));
+  }
+  for (int i = tid; i < nb; i += NT) x[i] = 1.0 / sqrt((double)nb);
+  __syncthreads();
+  double lam = 0.0;
+  for (int it = 0; it < kMixedIters; ++it) {
+    for (int i = tid; i < nb; i += NT) {
+      double acc = 0.0;
+      for (int j = 0; j < nb; ++j) acc += M[(int64_t)i * nb + j] * x[j];
+      y[i] = acc;
+    }
+    __syncthreads();
+    double ss = 0.0, xy = 0.0;
+    for (int i = tid; i < nb; i += NT) {
+      ss += y[i] * y[i];
+      xy += x[i] * y[i];
+    }
+    ss = block_sum<NT>(ss, sm);
+    xy = block_sum<NT>(xy, sm);
+    lam = xy;                                  // x has unit norm: Rayleigh quotient
+    if (!(ss > 0.0)) { lam = 0.0; break; }
+    const double inv = 1.0 / sqrt(ss);
+    for (int i = tid; i < nb; i += NT) x[i] = y[i] * inv;
+    __syncthreads();
+  }
+  return lam;
 }
 
 // Row/column of upper-triangular tile `t` in a T x T tile grid, tiles ordered by row.

@@ -259,7 +259,7 @@ constexpr int kFinThreads = 1024;
 // not inherit the bias of the tensor cores' accumulation.
 __global__ void __launch_bounds__(kFinThreads)
 finalize_kernel(DevState* st, const double* __restrict__ part, int nparts, int stride,
-                cudaGraphConditionalHandle cond) {
+                cudaGraphConditionalHandle cond, double* mscr) {
   __shared__ double sm[32];
   if (st->done) {
     if (threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
@@ -274,6 +274,14 @@ finalize_kernel(DevState* st, const double* __restrict__ part, int nparts, int s
   a = block_sum<kFinThreads>(a, sm);
   b = block_sum<kFinThreads>(b, sm);
   c = block_sum<kFinThreads>(c, sm);
+  double vk = sqrt(a);                           // v_{k-1} = ||X_{k-1} - X_{k-1}^2||_F
+  if (st->norm && mscr) {                        // or m_{k-1}, the mixed norm over 64 x 64 tiles
+    const int T = st->ld / kTile;
+    vk = mixed_norm_cta<kFinThreads>(T, mscr, sm, [&](int I, int J) {
+      const double v2 = part[(int64_t)stride * upper_index(I, J, T)];
+      return I == J ? v2 : 0.5 * v2;             // off-diagonal tiles hold both mirror halves
+    });
+  }
   if (threadIdx.x != 0) return;
 
   const int k = st->k + 1;                       // the square just completed
@@ -287,8 +295,7 @@ finalize_kernel(DevState* st, const double* __restrict__ part, int nparts, int s
     tr_new = b;
     tr_ref = st->tr[k - 1];
   }
-  // v_{k-1} = ||X_{k-1} - X_{k-1}^2||_F
-  if (record_and_test(st, pk, sqrt(a), tr_new, tr_ref)) cudaGraphSetConditional(cond, 0);
+  if (record_and_test(st, pk, vk, tr_new, tr_ref)) cudaGraphSetConditional(cond, 0);
 }
 
 // ---- output -----------------------------------------------------------------------------
@@ -314,7 +321,7 @@ __global__ void copy_out_kernel(const DevState* st, const double* __restrict__ b
 // Reduction + stop test of one FP64 square for loops driven without a CUDA graph:
 // the same rules as finalize_kernel (stride 2), ending the loop through st->done only.
 __global__ void __launch_bounds__(kFinThreads)
-finalize_plain_kernel(DevState* st, const double* __restrict__ part, int nparts) {
+finalize_plain_kernel(DevState* st, const double* __restrict__ part, int nparts, double* mscr) {
   __shared__ double sm[32];
   if (st->done) return;
   double a = 0.0, b = 0.0;
@@ -324,11 +331,19 @@ finalize_plain_kernel(DevState* st, const double* __restrict__ part, int nparts)
   }
   a = block_sum<kFinThreads>(a, sm);
   b = block_sum<kFinThreads>(b, sm);
+  double vk = sqrt(a);
+  if (st->norm && mscr) {
+    const int T = st->ld / kTile;
+    vk = mixed_norm_cta<kFinThreads>(T, mscr, sm, [&](int I, int J) {
+      const double v2 = part[2 * upper_index(I, J, T)];
+      return I == J ? v2 : 0.5 * v2;
+    });
+  }
   if (threadIdx.x != 0) return;
   const int k = st->k + 1;
   double ca, cb, cc;
   const int pk = st->acc ? acc_step(st, k, ca, cb, cc) : (st->tr[k - 1] > (double)st->nocc ? 1 : 0);
-  record_and_test(st, pk, sqrt(a), b, st->tr[k - 1]);
+  record_and_test(st, pk, vk, b, st->tr[k - 1]);
 }
 
 // ---- host-side launchers ------------------------------------------------------------------
@@ -352,17 +367,17 @@ cudaError_t launch_scale_f64(const DevState* st, const double* F, int64_t ldf, i
 }
 
 cudaError_t launch_f64_step_plain(DevState* st, double* buf0, double* buf1, double* part, int T,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, double* mscr) {
   const int ntiles = T * (T + 1) / 2;
   syrk_f64_kernel<<<ntiles, kSyrkThreads, 0, s>>>(st, buf0, buf1, part);
-  finalize_plain_kernel<<<1, kFinThreads, 0, s>>>(st, part, ntiles);
+  finalize_plain_kernel<<<1, kFinThreads, 0, s>>>(st, part, ntiles, mscr);
   return cudaGetLastError();
 }
 
 cudaError_t add_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, DevState* st,
                               double* part, int nparts, int stride, cudaGraphConditionalHandle cond,
-                              cudaGraphNode_t* node) {
-  void* args[] = {&st, &part, &nparts, &stride, &cond};
+                              cudaGraphNode_t* node, double* mscr) {
+  void* args[] = {&st, &part, &nparts, &stride, &cond, &mscr};
   cudaKernelNodeParams kp = {};
   kp.func = (void*)finalize_kernel;
   kp.gridDim = dim3(1);
@@ -372,7 +387,7 @@ cudaError_t add_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int nd
 }
 
 cudaError_t add_f64_loop_body(cudaGraph_t body, DevState* st, double* buf0, double* buf1, double* part,
-                              int T, cudaGraphConditionalHandle cond) {
+                              int T, cudaGraphConditionalHandle cond, double* mscr) {
   const int ntiles = T * (T + 1) / 2;
   cudaGraphNode_t n_sq, n_fin;
   void* args[] = {&st, &buf0, &buf1, &part};
@@ -383,7 +398,7 @@ cudaError_t add_f64_loop_body(cudaGraph_t body, DevState* st, double* buf0, doub
   kp.kernelParams = args;
   cudaError_t e = cudaGraphAddKernelNode(&n_sq, body, nullptr, 0, &kp);
   if (e != cudaSuccess) return e;
-  return add_finalize_node(body, &n_sq, 1, st, part, ntiles, 2, cond, &n_fin);
+  return add_finalize_node(body, &n_sq, 1, st, part, ntiles, 2, cond, &n_fin, mscr);
 }
 
 cudaError_t launch_refine_f64(const DevState* st, const double* Xin, double* Xout, int ld, int step, double* part,

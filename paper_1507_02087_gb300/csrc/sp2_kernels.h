@@ -30,20 +30,21 @@ cudaError_t launch_bounds_and_init(DevState* st, const double* F, int64_t ldf, i
 cudaError_t launch_scale_f64(const DevState* st, const double* F, int64_t ldf, int N, double* X0,
                              int ld, cudaStream_t s);
 // a3-a5, a7 for the FP64 path: the body of the device-controlled loop (square +
-// finalize), added to `body` as kernel nodes.
+// finalize), added to `body` as kernel nodes.  `mscr` (T^2 + 2T doubles, or null) is the
+// scratch of the mixed-norm stop, used when the state asks for it.
 cudaError_t add_f64_loop_body(cudaGraph_t body, DevState* st, double* buf0, double* buf1, double* part,
-                              int T, cudaGraphConditionalHandle cond);
+                              int T, cudaGraphConditionalHandle cond, double* mscr = nullptr);
 // Per-iteration reduction + stop test over `nparts` partial records of `stride` doubles.
 cudaError_t add_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, DevState* st,
                               double* part, int nparts, int stride, cudaGraphConditionalHandle cond,
-                              cudaGraphNode_t* node);
+                              cudaGraphNode_t* node, double* mscr = nullptr);
 // D = X_n (or 0 / I / NaN for the special outcomes).
 cudaError_t launch_copy_out(const DevState* st, const double* buf0, const double* buf1, int ld, int N,
                             double* D, int64_t ldd, cudaStream_t s);
 // One FP64 square + stop test launched directly on a stream (no graph); a no-op once
 // st->done is set.
 cudaError_t launch_f64_step_plain(DevState* st, double* buf0, double* buf1, double* part, int T,
-                                  cudaStream_t s);
+                                  cudaStream_t s, double* mscr = nullptr);
 // FP64 purification step `step` (0 or 1) on an ld x ld FP64 matrix (mixed-path refinement).
 cudaError_t launch_refine_f64(const DevState* st, const double* Xin, double* Xout, int ld, int step, double* part,
                               cudaStream_t s);

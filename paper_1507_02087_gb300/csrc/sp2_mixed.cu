@@ -193,6 +193,23 @@ __global__ void __launch_bounds__(kFT) batch_finalize_kernel(const Instance* ins
   a = block_sum<kFT>(a, sm);
   b = block_sum<kFT>(b, sm);
   c = block_sum<kFT>(c, sm);
+  double vk = sqrt(a);
+  if (st->norm && In.mscr) {
+    // mixed norm over 128 x 128 blocks: a 128 x 128 tile holds 4 records (one per epilogue
+    // warp, 32 rows each); a 256 x 256 pair tile holds 16, record 8 rank + 4 hc + q covering
+    // rows 128 rank + 32 q .., columns 128 hc ..; off-diagonal blocks are counted twice
+    const int nb = In.ld / tc::BM;
+    const double* pt = In.part;
+    const int pair = In.rec_pair;
+    vk = mixed_norm_cta<kFT>(nb, In.mscr, sm, [&](int I, int J) {
+      int64_t r0;
+      if (pair) r0 = 16 * upper_index(I / 2, J / 2, nb / 2) + 8 * (I & 1) + 4 * (J & 1);
+      else r0 = 4 * upper_index(I, J, nb);
+      double v2 = 0.0;
+      for (int q = 0; q < 4; ++q) v2 += pt[4 * (r0 + q)];
+      return I == J ? v2 : 0.5 * v2;
+    });
+  }
   if (threadIdx.x != 0) return;
   const int k = st->k + 1;
   double tr_new;
@@ -205,7 +222,7 @@ __global__ void __launch_bounds__(kFT) batch_finalize_kernel(const Instance* ins
     pk = st->tr[k - 1] > (double)st->nocc ? 1 : 0;
     tr_new = pk ? b : 2.0 * c - b;
   }
-  record_and_test(st, pk, sqrt(a), tr_new, c);
+  record_and_test(st, pk, vk, tr_new, c);
 }
 
 // Clears `cond` once no instance needs another round: which = 0 for the expansion

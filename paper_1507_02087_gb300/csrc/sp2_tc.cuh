@@ -114,6 +114,8 @@ struct Instance {
   int32_t tile_off_upper2;  // first global pair-tile index (upper schedule)
   int32_t tile_off_full2;   // first global pair-tile index (full schedule)
   int32_t nparts;           // forward-square partial records (4 doubles each) per launch
+  int32_t rec_pair;         // 1: the records come from CTA-pair tiles (16 per 256 x 256 tile)
+  double* mscr;             // mixed-norm scratch ((ld/128)^2 + 2 ld/128 doubles), or null
 };
 
 struct Job {

@@ -36,7 +36,7 @@ class sp2_opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("guard", ctypes.c_int32), ("qtilde", ctypes.c_double),
                 ("corrections", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
                 ("refine_fp64", ctypes.c_int32), ("launch_mode", ctypes.c_int32),
-                ("history", ctypes.c_int32), ("tile", ctypes.c_int32)]
+                ("history", ctypes.c_int32), ("tile", ctypes.c_int32), ("norm", ctypes.c_int32)]
 
 
 class sp2_info(ctypes.Structure):
@@ -124,25 +124,26 @@ def _stream_ptr(stream) -> int:
 
 
 TILES = {"auto": 0, "128": 1, "pair": 2}
+NORMS = {"fro": 0, "mixed": 1}
 HISTORY = {"auto": 0, "full": 1, "recompute": 2}
 
 
 def _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history="auto",
-          tile="auto"):
+          tile="auto", norm="fro"):
     if launch_mode is None:
         launch_mode = int(os.environ.get("SP2_LAUNCH_MODE", "0"))
     return sp2_opts(max_iter, 1 if guard else 0, qtilde, corrections, refine_steps, int(refine_fp64),
-                    launch_mode, HISTORY[history], TILES[tile])
+                    launch_mode, HISTORY[history], TILES[tile], NORMS[norm])
 
 
 def sp2_create(N: int, nocc: int, precision: str = "fp64", *, max_iter: int = 200, guard: bool = True,
                qtilde: float = 1.8, corrections: int = 1, refine_steps: int = 2,
                refine_fp64: int = 0, launch_mode: int | None = None, history: str = "auto",
-               tile: str = "auto") -> int:
+               tile: str = "auto", norm: str = "fro") -> int:
     """launch_mode None reads SP2_LAUNCH_MODE from the environment (default 0, the graph).
     history: "auto", "full" (keep every iterate) or "recompute" (low memory).
     tile: tensor-core tiles of the mixed path, "auto", "128" or "pair" (256 x 256 per SM pair)."""
-    o = _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history, tile)
+    o = _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history, tile, norm)
     h = ctypes.c_void_p()
     _check(lib().sp2_create(N, nocc, PRECISIONS[precision], ctypes.byref(o), ctypes.byref(h)), "sp2_create")
     return h.value
@@ -182,9 +183,9 @@ def sp2_get_info(h: int) -> dict:
 def sp2_create_batch(Ns, noccs, precision: str = "mixed", *, max_iter: int = 200, guard: bool = True,
                      qtilde: float = 1.8, corrections: int = 1, refine_steps: int = 2,
                      refine_fp64: int = 0, launch_mode: int | None = None, history: str = "auto",
-                     tile: str = "auto") -> int:
+                     tile: str = "auto", norm: str = "fro") -> int:
     count = len(Ns)
-    o = _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history, tile)
+    o = _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history, tile, norm)
     n_arr = (ctypes.c_int64 * count)(*Ns)
     o_arr = (ctypes.c_int64 * count)(*noccs)
     h = ctypes.c_void_p()

@@ -55,7 +55,7 @@ def test_status_strings_and_defaults_without_gpu(built):
     o = sp2.sp2_opts()
     L.sp2_default_opts(ctypes.byref(o))
     assert (o.max_iter, o.guard, o.qtilde, o.corrections, o.refine_steps, o.refine_fp64, o.launch_mode,
-            o.history, o.tile) == (200, 1, 1.8, 1, 2, 0, 0, 0, 0)
+            o.history, o.tile, o.norm) == (200, 1, 1.8, 1, 2, 0, 0, 0, 0, 0)
 
 
 def test_invalid_arguments_rejected_before_any_cuda_call(built):
@@ -66,15 +66,16 @@ def test_invalid_arguments_rejected_before_any_cuda_call(built):
     assert L.sp2_create(10, 11, 0, None, ctypes.byref(h)) == 1
     assert L.sp2_create(10, -1, 0, None, ctypes.byref(h)) == 1
     assert L.sp2_create(10, 5, 99, None, ctypes.byref(h)) == 7
-    for bad in (sp2.sp2_opts(0, 1, 1.8, 1, 2, 0, 0, 0, 0),      # max_iter
-                sp2.sp2_opts(10, 2, 1.8, 1, 2, 0, 0, 0, 0),     # guard
-                sp2.sp2_opts(10, 1, 0.0, 1, 2, 0, 0, 0, 0),     # qtilde
-                sp2.sp2_opts(10, 1, 1.8, 2, 2, 0, 0, 0, 0),     # corrections
-                sp2.sp2_opts(10, 1, 1.8, 1, 1, 0, 0, 0, 0),     # refine_steps
-                sp2.sp2_opts(10, 1, 1.8, 1, 2, 3, 0, 0, 0),     # refine_fp64
-                sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 5, 0, 0),     # launch_mode
-                sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 0, 3, 0),     # history
-                sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 0, 0, 3)):    # tile
+    for bad in (sp2.sp2_opts(0, 1, 1.8, 1, 2, 0, 0, 0, 0, 0),      # max_iter
+                sp2.sp2_opts(10, 2, 1.8, 1, 2, 0, 0, 0, 0, 0),     # guard
+                sp2.sp2_opts(10, 1, 0.0, 1, 2, 0, 0, 0, 0, 0),     # qtilde
+                sp2.sp2_opts(10, 1, 1.8, 2, 2, 0, 0, 0, 0, 0),     # corrections
+                sp2.sp2_opts(10, 1, 1.8, 1, 1, 0, 0, 0, 0, 0),     # refine_steps
+                sp2.sp2_opts(10, 1, 1.8, 1, 2, 3, 0, 0, 0, 0),     # refine_fp64
+                sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 5, 0, 0, 0),     # launch_mode
+                sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 0, 3, 0, 0),     # history
+                sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 0, 0, 3, 0),     # tile
+                sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 0, 0, 0, 2)):    # norm
         assert L.sp2_create(10, 5, 1, ctypes.byref(bad), ctypes.byref(h)) == 1
         assert h.value is None
     assert L.sp2_run(None, None, None, None) == 1
@@ -87,7 +88,7 @@ def test_invalid_arguments_rejected_before_any_cuda_call(built):
 def test_struct_layout_matches_c():
     from paper_1507_02087_gb300 import sp2
     fields_opts = ["max_iter", "guard", "qtilde", "corrections", "refine_steps", "refine_fp64", "launch_mode",
-                   "history", "tile"]
+                   "history", "tile", "norm"]
     fields_info = ["status", "n_iter", "stop_reason", "hist_len", "lambda_min", "lambda_max", "loop_ms",
                    "v", "trace", "p", "tile"]
     prints = [f"offsetof(sp2_opts, {f})" for f in fields_opts] + ["sizeof(sp2_opts)"]
