@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--acc", type=float, default=None, metavar="SLACK",
                     help="SP2-ACC (homo/lumo-based accelerated expansion) with the construction's homo and lumo "
                          "eigenvalues as inner bounds and SLACK as the distance of the outer ones")
+    ap.add_argument("--mcweeny", choices=["mcw", "mcw-acc"], default=None,
+                    help="FP64 path: the McWeeny expansion (mcw) or McW-ACC with the construction's gap as the "
+                         "gap estimate, mu = 0 (the construction splits the spectrum at 0)")
     ap.add_argument("--rule", choices=["error", "block"], default="error",
                     help="block-sparse truncation rule of the headline line (both rules are reported)")
     ap.add_argument("--N", type=int, default=N_DEFAULT)
@@ -416,6 +419,10 @@ def main():
     D = torch.empty_like(F)
     stream = torch.cuda.current_stream()
     P = sp2.Purifier(N, nocc, a.precision, refine_fp64={"tc": 0, "fp64": 1, "mcweeny": 2}[a.refine])
+    if a.mcweeny is not None:
+        if a.precision != "fp64":
+            raise SystemExit("--mcweeny needs --precision fp64")
+        P.set_mcweeny(a.mcweeny, 0.0, a.gap)
     acc_bounds = None
     if a.acc is not None:
         import numpy as np
@@ -585,8 +592,9 @@ def main():
                            f"dense N={N} nocc={nocc} gap={a.gap:g}, Q = 64 Householder reflectors (seed 3)",
                            "N": N, "nocc": nocc, "gap": a.gap,
                            "precision": a.precision, "refine": a.refine if mixed else None,
-                           "expansion": "SP2-ACC (homo/lumo bounds, slack %g)" % a.acc if a.acc is not None
-                           else "SP2 (trace-based)",
+                           "expansion": ("SP2-ACC (homo/lumo bounds, slack %g)" % a.acc if a.acc is not None
+                                         else {"mcw": "McWeeny (mu = 0)", "mcw-acc": "McW-ACC (mu = 0, xi = gap)"}
+                                         [a.mcweeny] if a.mcweeny else "SP2 (trace-based)"),
                            "parallelism": "replicas" if ws > 1 else "1 GPU",
                            "l2": "no flush: F 512 MiB and the streamed iterates exceed the 129 MB L2"},
                 "err_vs_exact": err, "err_first_run": err_first, "meets_tolerance": bool(err <= TOL and status_ok),

@@ -150,6 +150,18 @@ typedef struct sp2_ctx* sp2_handle;
  * first-order correction follows the scaled polynomials). */
 int32_t sp2_set_homo_lumo(sp2_handle h, const double* bounds);
 
+/* ---- McWeeny expansion (§3) on SP2_PREC_FP64 handles -------------------------------------
+ * mode 1: McWeeny, X_0 = (mu I - F) / gamma + I/2 with gamma = 2 max(lmax - mu, mu - lmin)
+ * (Gershgorin lmin, lmax), X_i = 3 X_{i-1}^2 - 2 X_{i-1}^3 (two FP64 products per step), and
+ * the parameterless stop with C_2^mw = 4 on consecutive errors, log(v_i/4)/log(v_{i-1}) < qtilde
+ * (evaluated when v_{i-1} < 1).  mode 2: McW-ACC (§3.1) with gap estimate xi > 0 (some
+ * eigenvalue of F lies in [mu - xi/2, mu + xi/2]): X_s = alpha (X - I/2) + I/2 before each step,
+ * alpha from the beta recursion; the acceleration is switched off once beta < 0.01 and the stop
+ * test runs from the step after.  mode 0 returns to SP2.  mu is the chemical potential (between
+ * the homo and lumo eigenvalues); n_occ still selects the trivial cases 0 and N.  Allocates one
+ * more ld x ld FP64 buffer on first use; synchronous; SP2_ERR_UNSUPPORTED on mixed handles. */
+int32_t sp2_set_mcweeny(sp2_handle h, int32_t mode, double mu, double xi);
+
 /* Fill `opts` with the defaults (max_iter 200, guard on, qtilde 1.8, 1 correction,
  * a 2-step refinement pair on the tensor cores). */
 void sp2_default_opts(sp2_opts* opts);

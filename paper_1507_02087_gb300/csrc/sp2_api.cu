@@ -540,6 +540,8 @@ struct sp2_ctx {
   double* part_hi = nullptr;
   int* part_bad = nullptr;
   double* mscr = nullptr;        // mixed-norm scratch (norm = 1): T^2 + 2T doubles
+  int mcw = 0;                   // 0: SP2, 1: McWeeny, 2: McW-ACC (FP64 path)
+  double* sbuf = nullptr;        // McWeeny: the shifted square S_s (ld x ld)
   DevState* st_dev = nullptr;
   DevState* st_host = nullptr;
   cudaGraph_t graph = nullptr;
@@ -563,6 +565,7 @@ static void free_ctx(sp2_ctx* h) {
   cudaFree(h->buf[1]);
   cudaFree(h->part);
   cudaFree(h->mscr);
+  cudaFree(h->sbuf);
   cudaFree(h->part_lo);
   cudaFree(h->part_hi);
   cudaFree(h->part_bad);
@@ -575,6 +578,25 @@ static void free_ctx(sp2_ctx* h) {
   (void)cudaGetLastError();
   cudaSetDevice(cur);
   delete h;
+}
+
+// The FP64 path's loop graph: a WHILE node around {square, stop test} (SP2) or {shifted
+// square, stop test, product} (McWeeny).
+static sp2_status build_f64_graph(sp2_ctx* h) {
+  if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
+  if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+  SP2_TRY(cudaGraphCreate(&h->graph, 0));
+  cudaGraphNode_t node;
+  cudaGraph_t body;
+  sp2_status s = add_while(h->graph, nullptr, 0, &h->cond, &node, &body);
+  if (s != SP2_OK) return s;
+  if (h->mcw)
+    SP2_TRY(sp2::add_mcw_loop_body(body, h->st_dev, h->buf[0], h->buf[1], h->sbuf, h->part, h->T, h->cond,
+                                   h->mscr));
+  else
+    SP2_TRY(sp2::add_f64_loop_body(body, h->st_dev, h->buf[0], h->buf[1], h->part, h->T, h->cond, h->mscr));
+  SP2_TRY(cudaGraphInstantiate(&h->exec, h->graph, 0));
+  return SP2_OK;
 }
 
 static sp2_status create_f64(sp2_ctx* h) {
@@ -599,14 +621,7 @@ static sp2_status create_f64(sp2_ctx* h) {
   SP2_TRY(cudaMemset(h->buf[0], 0, bytes));
   SP2_TRY(cudaMemset(h->buf[1], 0, bytes));
   *h->st_host = init;
-  SP2_TRY(cudaGraphCreate(&h->graph, 0));
-  cudaGraphNode_t node;
-  cudaGraph_t body;
-  sp2_status s = add_while(h->graph, nullptr, 0, &h->cond, &node, &body);
-  if (s != SP2_OK) return s;
-  SP2_TRY(sp2::add_f64_loop_body(body, h->st_dev, h->buf[0], h->buf[1], h->part, h->T, h->cond, h->mscr));
-  SP2_TRY(cudaGraphInstantiate(&h->exec, h->graph, 0));
-  return SP2_OK;
+  return build_f64_graph(h);
 }
 
 extern "C" sp2_status sp2_create(int64_t N, int64_t nocc, int32_t precision, const sp2_opts* opts,
@@ -651,7 +666,10 @@ static sp2_status enqueue_f64(sp2_ctx* h, const double* F, double* D, cudaStream
     SP2_TRY(cudaGraphLaunch(h->exec, s));
   } else {
     for (int it = 0; it <= h->opts.max_iter; ++it)
-      SP2_TRY(sp2::launch_f64_step_plain(h->st_dev, h->buf[0], h->buf[1], h->part, h->T, s, h->mscr));
+      if (h->mcw)
+        SP2_TRY(sp2::launch_mcw_step_plain(h->st_dev, h->buf[0], h->buf[1], h->sbuf, h->part, h->T, s, h->mscr));
+      else
+        SP2_TRY(sp2::launch_f64_step_plain(h->st_dev, h->buf[0], h->buf[1], h->part, h->T, s, h->mscr));
   }
   SP2_TRY(cudaEventRecord(h->ev_loop[1], s));
   SP2_TRY(sp2::launch_copy_out(h->st_dev, h->buf[0], h->buf[1], h->ld, N, D, N, s));
@@ -764,6 +782,40 @@ extern "C" int32_t sp2_set_homo_lumo(sp2_handle h, const double* bounds) {
   cudaSetDevice(h->device);
   sp2_status r = h->mixed ? write_acc(h->mixed->st_dev, h->mixed->st_host, bounds)
                           : write_acc(h->st_dev, h->st_host, bounds);
+  cudaSetDevice(cur);
+  return r;
+}
+
+// ---- McWeeny expansion (FP64 handles) -------------------------------------------------------
+extern "C" int32_t sp2_set_mcweeny(sp2_handle h, int32_t mode, double mu, double xi) {
+  if (!h || mode < 0 || mode > 2 || (mode > 0 && !std::isfinite(mu)) ||
+      (mode == 2 && !(std::isfinite(xi) && xi > 0.0)))
+    return SP2_ERR_INVALID_ARG;
+  if (h->mixed) return SP2_ERR_UNSUPPORTED;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  sp2_status r = SP2_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) r = SP2_ERR_CUDA;
+  if (r == SP2_OK && mode > 0 && !h->sbuf) {
+    const size_t bytes = (size_t)h->ld * h->ld * sizeof(double);
+    if (cudaMalloc(&h->sbuf, bytes) != cudaSuccess || cudaMemset(h->sbuf, 0, bytes) != cudaSuccess) r = SP2_ERR_NOMEM;
+  }
+  if (r == SP2_OK) {
+    const int32_t m = mode;
+    const double mx[2] = {mode > 0 ? mu : 0.0, mode == 2 ? xi : 0.0};
+    static_assert(offsetof(DevState, xi) == offsetof(DevState, mu) + sizeof(double), "mu, xi adjacent");
+    char* base = reinterpret_cast<char*>(h->st_dev);
+    if (cudaMemcpy(base + offsetof(DevState, mcw), &m, sizeof(m), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(base + offsetof(DevState, mu), mx, sizeof(mx), cudaMemcpyHostToDevice) != cudaSuccess)
+      r = SP2_ERR_CUDA;
+  }
+  if (r == SP2_OK) {
+    h->st_host->mcw = mode;
+    h->mcw = mode;
+    if (h->opts.launch_mode == 0) r = build_f64_graph(h);
+  }
+  (void)cudaGetLastError();
   cudaSetDevice(cur);
   return r;
 }

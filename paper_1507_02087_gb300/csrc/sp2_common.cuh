@@ -60,6 +60,14 @@ struct DevState {
   double hl[4];        // homo_out, homo_in, lumo_in, lumo_out
   double alpha[SP2_MAX_ITER + 2];
   uint8_t psched[SP2_MAX_ITER + 2];
+  // McWeeny expansion (§3; FP64 path): set by sp2_set_mcweeny; alpha[] holds the McW-ACC
+  // factors and n_min the first step of the stop test
+  int32_t mcw;         // 0: SP2, 1: McWeeny, 2: McW-ACC
+  int32_t _pad3;
+  double mu, xi;       // chemical potential, gap estimate (McW-ACC)
+  // initial scaling X_0 = (scale_a I - F) / scale_w: SP2 (lmax, lmax - lmin); McWeeny
+  // (mu + gamma/2, gamma) with gamma = 2 max(lmax - mu, mu - lmin)
+  double scale_a, scale_w;
   // history
   double v[SP2_MAX_ITER + 2];
   double tr[SP2_MAX_ITER + 2];
@@ -68,12 +76,15 @@ struct DevState {
 
 // The paper's convergence-order test (Alg. 3; §2 relaxed order qtilde), only
 // evaluated when v_{i-2} < 1, and in its logarithmic form.
-__device__ __forceinline__ bool order_test_stops(double v_i, double v_im2, double qtilde) {
+__device__ __forceinline__ bool order_test_stops(double v_i, double v_im2, double qtilde, double C = kC2sp) {
   if (v_im2 == 0.0) return true;
   if (!(v_im2 < 1.0)) return false;
   if (v_i == 0.0) return false;
-  return log(v_i / kC2sp) / log(v_im2) < qtilde;
+  return log(v_i / C) / log(v_im2) < qtilde;
 }
+
+// McWeeny (§3): C_2^mw = 4, the maximum of (p(x) - p(x)^2) / (x - x^2)^2 = 3 + 4x - 4x^2.
+constexpr double kC2mw = 4.0;
 
 // ---- SP2-ACC ---------------------------------------------------------------------------
 // Alg. 4 on the device (one thread): the polynomial p_i and scale-and-fold factor alpha_i of
@@ -153,6 +164,31 @@ __device__ __forceinline__ int acc_step(const DevState* st, int j, double& a, do
   return p;
 }
 
+// McW-ACC schedule (§3.1) for steps 1..max_iter: alpha_i = 3 / sqrt(12 beta^2 - 18 beta + 9)
+// while the acceleration is on, beta_0 = (1 - xi / gamma) / 2, beta <- p(alpha (beta - 1/2) + 1/2);
+// the acceleration is switched off for good once beta < 0.01 (n_min = the step after), as
+// the Frobenius estimate may stop the accelerated scheme early.  McWeeny: alpha = 1, n_min = 1.
+__device__ inline void mcw_schedule(DevState* st, double gamma) {
+  double beta = __dmul_rn(0.5, __dsub_rn(1.0, __ddiv_rn(st->xi, gamma)));
+  bool on = st->mcw == 2;
+  int nmin = on ? -1 : 1;
+  st->alpha[0] = 1.0;
+  for (int i = 1; i <= st->max_iter; ++i) {
+    if (on && beta < 0.01) {
+      on = false;
+      nmin = i + 1;
+    }
+    const double a = on ? __ddiv_rn(3.0, __dsqrt_rn(__dadd_rn(__dsub_rn(__dmul_rn(__dmul_rn(12.0, beta), beta),
+                                                                       __dmul_rn(18.0, beta)), 9.0)))
+                        : 1.0;
+    const double bs = __dadd_rn(__dmul_rn(a, __dsub_rn(beta, 0.5)), 0.5);
+    const double bs2 = __dmul_rn(bs, bs);
+    beta = __dsub_rn(__dmul_rn(3.0, bs2), __dmul_rn(__dmul_rn(2.0, bs2), bs));
+    st->alpha[i] = a;
+  }
+  st->n_min = nmin < 0 ? st->max_iter + 1 : nmin;
+}
+
 // Records square k = st->k + 1 (v_{k-1}, Tr[X_k], p_k) and applies the stop rules in
 // the order the iteration meets them: the order test for X_{k-1} (Alg. 3, evaluated
 // one square late because v_{k-1} needs X_{k-1}^2; on the accelerated path from n_min
@@ -170,6 +206,21 @@ __device__ __forceinline__ bool record_and_test(DevState* st, int pk, double v_p
   st->hist_len = k;
   const int i = k - 1;
   bool stop = true;
+  if (st->mcw) {   // McWeeny: consecutive errors, C = 4, from n_min on; no trace rule
+    if (!isfinite(v_prev)) {
+      st->status = SP2_ERR_NONFINITE; st->out_mode = OUT_NAN; st->n_out = i;
+    } else if (k == 1 && v_prev == 0.0) {
+      st->reason = SP2_STOP_EXACT; st->n_out = 0; st->out_buf = 0;
+    } else if (i >= max(1, st->n_min) && order_test_stops(st->v[i], st->v[i - 1], st->qtilde, kC2mw)) {
+      st->reason = SP2_STOP_ORDER; st->n_out = i; st->out_buf = i & 1;
+    } else if (i >= st->max_iter) {
+      st->reason = SP2_STOP_CAP; st->n_out = i; st->out_buf = i & 1;
+    } else {
+      stop = false;
+    }
+    if (stop) st->done = 1;
+    return stop;
+  }
   if (!isfinite(v_prev) || !isfinite(tr_new)) {
     st->status = SP2_ERR_NONFINITE; st->out_mode = OUT_NAN; st->n_out = i;
   } else if (k == 1 && v_prev == 0.0) {

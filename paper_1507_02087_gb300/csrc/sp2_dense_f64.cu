@@ -77,18 +77,26 @@ init_kernel(DevState* st, const double* __restrict__ F, int64_t ldf, const doubl
   __syncthreads();
   const double lmin = s_lmin, lmax = s_lmax;
   const int N = st->N, nocc = st->nocc;
+  // X_0 = (sa I - F) / sw: (lmax, lmax - lmin) for SP2 (Alg. 3), (mu + gamma/2, gamma) with
+  // gamma = 2 max(lmax - mu, mu - lmin) for McWeeny (§3)
+  double sa = lmax, sw = lmax - lmin;
+  if (st->mcw) {
+    sw = 2.0 * fmax(lmax - st->mu, st->mu - lmin);
+    sa = st->mu + 0.5 * sw;
+  }
   // Tr[X_0] over the stored diagonal, each entry rounded exactly as the scaling kernel
   // rounds it.
   double t = 0.0;
-  const double w = lmax - lmin;
+  const double w = sw;
   const int r32 = st->round_fp32;
   for (int i = threadIdx.x; i < N; i += kInitThreads) {
-    const double x = (lmax - F[(int64_t)i * ldf + i]) / w;
+    const double x = (sa - F[(int64_t)i * ldf + i]) / w;
     t += r32 ? (double)(float)x : x;
   }
   t = block_sum<kInitThreads>(t, sm);
   if (threadIdx.x == 0) {
     st->lmin = lmin; st->lmax = lmax;
+    st->scale_a = sa; st->scale_w = sw;
     st->dk = 0;
     st->k = 0; st->done = 0; st->n_out = 0; st->reason = SP2_STOP_EXACT;
     st->status = SP2_OK; st->out_buf = 0; st->out_mode = OUT_COPY; st->hist_len = 0;
@@ -103,7 +111,10 @@ init_kernel(DevState* st, const double* __restrict__ F, int64_t ldf, const doubl
       st->status = SP2_ERR_NO_GAP; st->done = 1; st->out_mode = OUT_NAN;
     } else {
       st->tr[0] = t;
-      if (st->acc && !acc_schedule(st)) {   // SP2-ACC: Alg. 4 from the bounds just found
+      if (st->mcw) {
+        if (!(sw > 0.0)) { st->status = SP2_ERR_NO_GAP; st->done = 1; st->out_mode = OUT_NAN; }
+        else mcw_schedule(st, sw);
+      } else if (st->acc && !acc_schedule(st)) {   // SP2-ACC: Alg. 4 from the bounds just found
         st->status = SP2_ERR_INVALID_ARG; st->done = 1; st->out_mode = OUT_NAN;
       }
     }
@@ -115,7 +126,7 @@ __global__ void scale_kernel(const DevState* st, const double* __restrict__ F, i
                              double* __restrict__ X0, int ld) {
   if (st->done) return;
   const int N = st->N;
-  const double lmax = st->lmax, w = st->lmax - st->lmin;
+  const double lmax = st->scale_a, w = st->scale_w;   // (lmax, lmax - lmin) for SP2
   const int64_t total = (int64_t)N * N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -135,9 +146,12 @@ constexpr int kTile = 64, kTK = 16, kSyrkThreads = 256;
 
 // gen = 1 (accelerated path): X_k = ca S + cb X + cc I, the identity term on the N true
 // diagonal entries only (the zero border stays zero).
+// Bin (if given): the product is Xin Bin^T instead of Xin Xin^T (the McWeeny step's S X);
+// the epilogue's x is still the element of Xin.
 __device__ __forceinline__ void syrk_f64_tile(const double* __restrict__ Xin, double* __restrict__ Xout, int ld,
                                               int pk, double* __restrict__ part, int gen = 0, double ca = 0.0,
-                                              double cb = 0.0, double cc = 0.0, int N = 0) {
+                                              double cb = 0.0, double cc = 0.0, int N = 0,
+                                              const double* __restrict__ Bin = nullptr) {
   __shared__ double As[2][kTK][kTile + 1];
   __shared__ double Bs[2][kTK][kTile + 1];
   __shared__ double sred[32];
@@ -148,7 +162,7 @@ __device__ __forceinline__ void syrk_f64_tile(const double* __restrict__ Xin, do
   const int ty = tid >> 4, tx = tid & 15;
   const int lm = tid >> 4, lk = tid & 15;        // loader: rows lm + 16 j, column lk
   const double* Arow = Xin + (int64_t)(I * kTile) * ld;
-  const double* Brow = Xin + (int64_t)(J * kTile) * ld;
+  const double* Brow = (Bin ? Bin : Xin) + (int64_t)(J * kTile) * ld;
 
   double acc[4][4];
   #pragma unroll
@@ -235,6 +249,30 @@ syrk_f64_kernel(const DevState* st, double* buf0, double* buf1, double* __restri
   syrk_f64_tile(Xin, Xout, st->ld, pk, part);
 }
 
+// ---- McWeeny expansion (§3), two products per step ------------------------------------------
+// Step k (from X_{k-1} in buf[(k-1) & 1]), with X_s = alpha (X - I/2) + I/2 = alpha X + c I,
+// c = (1 - alpha)/2:  mcw_square writes S_s = X_s^2 = alpha^2 X^2 + 2 alpha c X + c^2 I to S and
+// the partials of ||X_{k-1} - X_{k-1}^2||_F for the stop test; mcw_prod (after the test, unless
+// it stopped) writes X_k = 3 S_s - 2 S_s X_s = (3 - 2c) S_s - 2 alpha S_s X_{k-1} to buf[k & 1].
+__global__ void __launch_bounds__(kSyrkThreads)
+mcw_square_kernel(const DevState* st, const double* buf0, const double* buf1, double* S, double* __restrict__ part) {
+  if (st->done) return;
+  const int j = st->k + 1;
+  const double* Xin = (st->k & 1) ? buf1 : buf0;
+  const double a = st->alpha[j], c = 0.5 * (1.0 - a);
+  syrk_f64_tile(Xin, S, st->ld, 1, part, 1, a * a, 2.0 * a * c, c * c, st->N);
+}
+
+__global__ void __launch_bounds__(kSyrkThreads)
+mcw_prod_kernel(const DevState* st, double* buf0, double* buf1, const double* S, double* __restrict__ part) {
+  if (st->done) return;
+  const int k = st->k;                             // the square just recorded
+  const double* Xprev = ((k - 1) & 1) ? buf1 : buf0;
+  double* Xout = (k & 1) ? buf1 : buf0;
+  const double a = st->alpha[k], c = 0.5 * (1.0 - a);
+  syrk_f64_tile(S, Xout, st->ld, 1, part, 1, -2.0 * a, 3.0 - 2.0 * c, 0.0, st->N, Xprev);
+}
+
 // FP64 purification step on the mixed path's result: the polynomial alternates with
 // the last one of the low-precision expansion (step 0 takes the other one, step 1 the
 // same one), so each pair squares the remaining eigenvalue error (the composition of
@@ -286,13 +324,13 @@ finalize_kernel(DevState* st, const double* __restrict__ part, int nparts, int s
 
   const int k = st->k + 1;                       // the square just completed
   double ca = 0.0, cb = 0.0, cc = 0.0;
-  const int pk = st->acc ? acc_step(st, k, ca, cb, cc) : (st->tr[k - 1] > (double)st->nocc ? 1 : 0);
+  const int pk = st->mcw ? 1 : st->acc ? acc_step(st, k, ca, cb, cc) : (st->tr[k - 1] > (double)st->nocc ? 1 : 0);
   double tr_new, tr_ref;
   if (stride > 2) {
     tr_new = st->acc ? ca * b + cb * c + cc * (double)st->N : (pk ? b : 2.0 * c - b);
     tr_ref = c;
   } else {
-    tr_new = b;
+    tr_new = st->mcw ? 0.0 : b;                  // McWeeny: no trace rule, none recorded
     tr_ref = st->tr[k - 1];
   }
   if (record_and_test(st, pk, vk, tr_new, tr_ref)) cudaGraphSetConditional(cond, 0);
@@ -343,7 +381,7 @@ finalize_plain_kernel(DevState* st, const double* __restrict__ part, int nparts,
   const int k = st->k + 1;
   double ca, cb, cc;
   const int pk = st->acc ? acc_step(st, k, ca, cb, cc) : (st->tr[k - 1] > (double)st->nocc ? 1 : 0);
-  record_and_test(st, pk, vk, b, st->tr[k - 1]);
+  record_and_test(st, st->mcw ? 1 : pk, vk, st->mcw ? 0.0 : b, st->tr[k - 1]);
 }
 
 // ---- host-side launchers ------------------------------------------------------------------
@@ -371,6 +409,38 @@ cudaError_t launch_f64_step_plain(DevState* st, double* buf0, double* buf1, doub
   const int ntiles = T * (T + 1) / 2;
   syrk_f64_kernel<<<ntiles, kSyrkThreads, 0, s>>>(st, buf0, buf1, part);
   finalize_plain_kernel<<<1, kFinThreads, 0, s>>>(st, part, ntiles, mscr);
+  return cudaGetLastError();
+}
+
+cudaError_t add_mcw_loop_body(cudaGraph_t body, DevState* st, double* buf0, double* buf1, double* S, double* part,
+                              int T, cudaGraphConditionalHandle cond, double* mscr) {
+  const int ntiles = T * (T + 1) / 2;
+  cudaGraphNode_t n_sq, n_fin, n_pr;
+  const double* b0 = buf0;
+  const double* b1 = buf1;
+  void* a1[] = {&st, &b0, &b1, &S, &part};
+  cudaKernelNodeParams kp = {};
+  kp.func = (void*)mcw_square_kernel;
+  kp.gridDim = dim3(ntiles);
+  kp.blockDim = dim3(kSyrkThreads);
+  kp.kernelParams = a1;
+  cudaError_t e = cudaGraphAddKernelNode(&n_sq, body, nullptr, 0, &kp);
+  if (e != cudaSuccess) return e;
+  e = add_finalize_node(body, &n_sq, 1, st, part, ntiles, 2, cond, &n_fin, mscr);
+  if (e != cudaSuccess) return e;
+  const double* Sc = S;
+  void* a2[] = {&st, &buf0, &buf1, &Sc, &part};
+  kp.func = (void*)mcw_prod_kernel;
+  kp.kernelParams = a2;
+  return cudaGraphAddKernelNode(&n_pr, body, &n_fin, 1, &kp);
+}
+
+cudaError_t launch_mcw_step_plain(DevState* st, double* buf0, double* buf1, double* S, double* part, int T,
+                                  cudaStream_t s, double* mscr) {
+  const int ntiles = T * (T + 1) / 2;
+  mcw_square_kernel<<<ntiles, kSyrkThreads, 0, s>>>(st, buf0, buf1, S, part);
+  finalize_plain_kernel<<<1, kFinThreads, 0, s>>>(st, part, ntiles, mscr);
+  mcw_prod_kernel<<<ntiles, kSyrkThreads, 0, s>>>(st, buf0, buf1, S, part);
   return cudaGetLastError();
 }
 

@@ -34,6 +34,12 @@ cudaError_t launch_scale_f64(const DevState* st, const double* F, int64_t ldf, i
 // scratch of the mixed-norm stop, used when the state asks for it.
 cudaError_t add_f64_loop_body(cudaGraph_t body, DevState* st, double* buf0, double* buf1, double* part,
                               int T, cudaGraphConditionalHandle cond, double* mscr = nullptr);
+// The McWeeny expansion's loop body (FP64): shifted square into S, finalize (stop test),
+// then X_k = (3 - 2c) S - 2 alpha S X_{k-1}; S is an ld x ld FP64 buffer.
+cudaError_t add_mcw_loop_body(cudaGraph_t body, DevState* st, double* buf0, double* buf1, double* S, double* part,
+                              int T, cudaGraphConditionalHandle cond, double* mscr);
+cudaError_t launch_mcw_step_plain(DevState* st, double* buf0, double* buf1, double* S, double* part, int T,
+                                  cudaStream_t s, double* mscr);
 // Per-iteration reduction + stop test over `nparts` partial records of `stride` doubles.
 cudaError_t add_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, DevState* st,
                               double* part, int nparts, int stride, cudaGraphConditionalHandle cond,

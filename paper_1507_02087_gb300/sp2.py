@@ -80,6 +80,8 @@ def lib() -> ctypes.CDLL:
         L.sp2_set_homo_lumo.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.sp2_set_homo_lumo.restype = i32
         L.sp2_set_homo_lumo_batch.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
+        L.sp2_set_mcweeny.argtypes = [vp, i32, ctypes.c_double, ctypes.c_double]
+        L.sp2_set_mcweeny.restype = i32
         L.sp2_set_homo_lumo_batch.restype = i32
         L.sp2_create_batch.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(i64), i32,
                                        ctypes.POINTER(sp2_opts), ctypes.POINTER(vp)]
@@ -370,6 +372,12 @@ class Purifier:
 
     def set_homo_lumo(self, bounds) -> None:
         sp2_set_homo_lumo(self.h, bounds)
+
+    def set_mcweeny(self, mode: str | None, mu: float = 0.0, xi: float = 0.0) -> None:
+        """McWeeny expansion on an FP64 handle: mode "mcw", "mcw-acc" (gap estimate xi) or None
+        (back to SP2); mu is the chemical potential."""
+        m = {None: 0, "mcw": 1, "mcw-acc": 2}[mode]
+        _check(lib().sp2_set_mcweeny(self.h, m, float(mu), float(xi)), "sp2_set_mcweeny")
 
     def close(self):
         sp2_destroy(self.h)
