@@ -498,9 +498,11 @@ def main():
         kern_ms = statistics.mean(l / s for l, s in zip(loop_ms, [i["hist_len"] for i in infos]))
         mhz = clk.get("sm_mhz") or SM_MAX_MHZ
         peak = SMS * FP64_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
-        alg = N * N * (N + 1)
+        alg = N * N * (N + 1) * (2 if a.mcweeny else 1)     # McWeeny: two products per step
         achieved = alg / (kern_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": "syrk_f64_kernel (+finalize)", "achieved": achieved, "peak": peak,
+        kname = ("mcw_square_kernel + mcw_prod_kernel (+finalize), one McWeeny step" if a.mcweeny
+                 else "syrk_f64_kernel (+finalize)")
+        roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "ms_per_launch": kern_ms,
                     "peak_source": f"152 SMs x 4 FP64 flop/clk x {mhz:.0f} MHz (median SM clock under load)",
                     "algorithmic_flops_per_launch": alg, "traffic": None}
