@@ -17,8 +17,8 @@ McW-ACC (§3.1): with a gap estimate xi such that some eigenvalue of F lies in
     X_i = 3 X_s^2 - 2 X_s^3,   beta_s = alpha (beta - 1/2) + 1/2,   beta <- 3 beta_s^2 - 2 beta_s^3.
 
 Readings (also listed in the design notes):
-  * the error is v_i = ||X_i - X_i^2||_F in place of the spectral e_i (§3.2 shows the regular
-    scheme then never stops early);
+  * the error is v_i = ||X_i - X_i^2||_F in place of the spectral e_i by default (§3.2 shows the
+    regular scheme then never stops early); norm="spectral" takes e_i itself;
   * as for SP2 the order test is evaluated only when v_{i-1} < 1 (v_{i-1} = 0 stops, v_i = 0
     does not);
   * acceleration: §3.2 shows the Frobenius estimate can stop the accelerated scheme early and
@@ -70,8 +70,10 @@ def initial_mcw(F: np.ndarray, mu: float, lmin: float, lmax: float) -> tuple[np.
 
 def mcweeny(F: np.ndarray, mu: float, *, xi: float = 0.0, accelerate: bool = False,
             bounds: tuple[float, float] | None = None, max_iter: int = 200, qtilde: float = o.QTILDE,
-            delta: float = DELTA) -> o.SP2Result:
-    """McWeeny (accelerate False) or McW-ACC (True) step by step in FP64."""
+            delta: float = DELTA, norm: str = "fro") -> o.SP2Result:
+    """McWeeny (accelerate False) or McW-ACC (True) step by step in FP64.  `norm`: "fro" (v_i)
+    or "spectral" (e_i = ||X_i - X_i^2||_2, §2; eigvalsh, small N only)."""
+    err = o.idempotency_error_fro if norm == "fro" else o.idempotency_error_spectral
     F = np.asarray(F, dtype=np.float64)
     N = F.shape[0]
     lmin, lmax = o.gershgorin_bounds(F) if bounds is None else bounds
@@ -80,7 +82,7 @@ def mcweeny(F: np.ndarray, mu: float, *, xi: float = 0.0, accelerate: bool = Fal
     X, gamma = initial_mcw(F, mu, lmin, lmax)
     alpha, n_min = mcw_schedule(gamma, xi, accelerate, max_iter, delta)
     X2 = X @ X
-    v = [o.idempotency_error_fro(X, X2)]
+    v = [err(X, X2)]
     tr = [float(np.trace(X))]
     p = [None]
     for i in range(1, max_iter + 1):
@@ -89,7 +91,7 @@ def mcweeny(F: np.ndarray, mu: float, *, xi: float = 0.0, accelerate: bool = Fal
         S = Xs @ Xs
         Xi = 3.0 * S - 2.0 * (S @ Xs)
         X2i = Xi @ Xi
-        v.append(o.idempotency_error_fro(Xi, X2i))
+        v.append(err(Xi, X2i))
         tr.append(float(np.trace(Xi)))
         p.append(1)
         if i >= n_min and o.order_test_stops(v[i], v[i - 1], qtilde, C2_MW):

@@ -119,8 +119,10 @@ def apply_step(X: np.ndarray, p: int, a: float) -> np.ndarray:
 
 def sp2_acc(F: np.ndarray, nocc: int, homo_out: float, homo_in: float, lumo_in: float, lumo_out: float, *,
             bounds: tuple[float, float] | None = None, qtilde: float = o.QTILDE, guard: bool = True,
-            delta: float = DELTA, sched: Schedule | None = None) -> o.SP2Result:
-    """Alg. 5 step by step in FP64 (Alg. 4 supplies the schedule)."""
+            delta: float = DELTA, sched: Schedule | None = None, norm: str = "fro") -> o.SP2Result:
+    """Alg. 5 step by step in FP64 (Alg. 4 supplies the schedule).  `norm`: "fro" (v_i) or
+    "spectral" (e_i = ||X_i - X_i^2||_2, the error of §2; eigvalsh, small N only)."""
+    err = o.idempotency_error_fro if norm == "fro" else o.idempotency_error_spectral
     F = np.asarray(F, dtype=np.float64)
     N = F.shape[0]
     lmin, lmax = o.gershgorin_bounds(F) if bounds is None else bounds
@@ -133,7 +135,7 @@ def sp2_acc(F: np.ndarray, nocc: int, homo_out: float, homo_in: float, lumo_in: 
         sched = acc_schedule(lmin, lmax, homo_out, homo_in, lumo_in, lumo_out, delta=delta)
     X = o.initial_scaling(F, lmin, lmax)
     X2 = X @ X
-    v = [o.idempotency_error_fro(X, X2)]
+    v = [err(X, X2)]
     tr = [float(np.trace(X))]
     p = [None]
     if v[0] == 0.0:
@@ -146,7 +148,7 @@ def sp2_acc(F: np.ndarray, nocc: int, homo_out: float, homo_in: float, lumo_in: 
         if guard and i >= sched.n_min and ((pi == 1 and tr[i] >= tr[i - 1]) or (pi == 0 and tr[i] <= tr[i - 1])):
             return o.SP2Result(Xi, i, o.STOP_TRACE_GUARD, lmin, lmax, v, tr, p)
         X2i = Xi @ Xi
-        v.append(o.idempotency_error_fro(Xi, X2i))
+        v.append(err(Xi, X2i))
         if i >= max(2, sched.n_min) and p[i] != p[i - 1] and o.order_test_stops(v[i], v[i - 2], qtilde):
             return o.SP2Result(Xi, i, o.STOP_ORDER, lmin, lmax, v, tr, p)
         X = Xi

@@ -101,6 +101,28 @@ def dense_n400(device="cpu", want_exact=True) -> DenseCase:
                         name="dense N=400 nocc=200 gap=0.1")
 
 
+def dense_equidistant_noisy(N: int, nocc: int, occupied: tuple[float, float], unoccupied: tuple[float, float],
+                            noise_norm: float, count: int, seed: int = 0,
+                            noise_seed: int = 7) -> tuple[np.ndarray, np.ndarray]:
+    """The dense example of §4.1: equidistant occupied and unoccupied eigenvalues, eigenvectors
+    from the QR factorisation of a Gaussian matrix (PCG64(seed)), and `count` symmetric Gaussian
+    perturbations E_0, E_1, ... of spectral norm `noise_norm` (PCG64(noise_seed), drawn in that
+    order, each (G + G^T)/2 rescaled by its largest |eigenvalue|).  Returns (F, E) as float64
+    numpy arrays, E of shape (count, N, N)."""
+    g = rng(seed)
+    lam = np.concatenate([np.linspace(*occupied, nocc), np.linspace(*unoccupied, N - nocc)])
+    Q, _ = np.linalg.qr(g.standard_normal((N, N)))
+    F = (Q * lam) @ Q.T
+    F = 0.5 * (F + F.T)
+    gn = rng(noise_seed)
+    E = np.empty((count, N, N))
+    for i in range(count):
+        G = gn.standard_normal((N, N))
+        G = 0.5 * (G + G.T)
+        E[i] = G * (noise_norm / np.max(np.abs(np.linalg.eigvalsh(G))))
+    return F, E
+
+
 def dense_n8192(device="cpu", want_exact=True) -> DenseCase:
     """N=8192, nocc=4096, spectrum in [-1,1] with gap 0.01 at nocc, seed 0."""
     return dense_gapped(8192, 4096, gap=0.01, seed=0, device=device, want_exact=want_exact,

@@ -96,3 +96,37 @@ def test_acceleration_saves_iterations():
     assert acc.stop_reason == o.STOP_ORDER and plain.stop_reason == o.STOP_ORDER
     assert acc.n < plain.n
     assert o.rel_error(acc.D, plain.D, 100) < 1e-12
+
+
+def test_spectral_error_on_diagonal_is_largest_scalar_error():
+    # a diagonal F keeps every X_i diagonal, so e_i = max_j |x_j - x_j^2| (no eigensolver);
+    # the error measure changes only where the run stops, never the iterates
+    gen = np.random.Generator(np.random.PCG64(9))
+    N = 90
+    lam = np.concatenate([gen.uniform(-1, -0.05, 40), gen.uniform(0.05, 1, N - 40)])
+    gen.shuffle(lam)
+    F = np.diag(lam)
+    for acc in (False, True):
+        rs = om.mcweeny(F, 0.0, xi=0.1, accelerate=acc, norm="spectral")
+        rf = om.mcweeny(F, 0.0, xi=0.1, accelerate=acc)
+        gamma = 2 * max(rs.lmax, -rs.lmin)
+        alpha, _ = om.mcw_schedule(gamma, 0.1, acc, 200)
+        xs = (0.0 - lam) / gamma + 0.5
+        for i in range(len(rs.v)):
+            if rs.v[i] > 1e-12:                      # above the rounding floor
+                assert rs.v[i] == pytest.approx(float(np.max(np.abs(xs - xs * xs))), rel=1e-9)
+            assert rs.v[i] <= rf.v[i] * (1 + 1e-12) if i < len(rf.v) else True
+            ys = alpha[i + 1] * (xs - 0.5) + 0.5 if i + 1 < len(alpha) else xs
+            xs = 3 * ys * ys - 2 * ys * ys * ys
+        assert abs(rs.n - rf.n) <= 1 and rs.stop_reason == o.STOP_ORDER
+
+
+def test_spectral_stop_dense_between_bounds():
+    # e_i <= v_i <= sqrt(N) e_i on the same iterates, and the spectral stop reaches the projector
+    case = inputs.dense_gapped(120, 60, gap=0.05, seed=4)
+    F = case.F.numpy()
+    rs = om.mcweeny(F, 0.0, xi=0.05, accelerate=True, norm="spectral")
+    rf = om.mcweeny(F, 0.0, xi=0.05, accelerate=True)
+    for i in range(min(len(rs.v), len(rf.v))):
+        assert rs.v[i] <= rf.v[i] * (1 + 1e-12) and rf.v[i] <= math.sqrt(120) * rs.v[i] * (1 + 1e-12)
+    assert o.rel_error(rs.D, jacobi.density_by_definition(F, 60), 60) < 1e-12

@@ -126,3 +126,26 @@ def test_schedule_keeps_true_homo_lumo_in_unit_interval():
         xh, xl = f(xh), f(xl)
         assert 0.0 <= xl <= 1.0 and 0.0 <= xh <= 1.0      # eigenvalues stay in [0, 1]
     assert xh > 1 - 1e-8 and xl < 1e-8
+
+
+def test_spectral_error_on_diagonal_is_largest_scalar_error():
+    # diagonal F: e_i = max_j |x_j - x_j^2| of the scalar map (no eigensolver involved)
+    g = np.random.Generator(np.random.PCG64(12))
+    N, nocc = 80, 30
+    lam = np.concatenate([g.uniform(-1, -0.03, nocc), g.uniform(0.03, 1.0, N - nocc)])
+    g.shuffle(lam)
+    F = np.diag(lam)
+    lmin, lmax = o.gershgorin_bounds(F)
+    homo, lumo = float(np.max(lam[lam < 0])), float(np.min(lam[lam > 0]))
+    sched = oa.acc_schedule(lmin, lmax, homo, homo, lumo, lumo)
+    rs = oa.sp2_acc(F, nocc, homo, homo, lumo, lumo, sched=sched, norm="spectral")
+    rf = oa.sp2_acc(F, nocc, homo, homo, lumo, lumo, sched=sched)
+    d = np.diag(rs.D)
+    xs, n, reason, p = oa.sp2_acc_scalar(lam, nocc, lmin, lmax, sched)
+    assert np.array_equal(d, np.array(xs)) and rs.p == p[:len(rs.p)]
+    # the last record is e_n of D = X_n itself: max_j |d_j - d_j^2|
+    assert len(rs.v) == rs.n + 1
+    assert rs.v[-1] == pytest.approx(float(np.max(np.abs(d - d * d))), rel=1e-9, abs=1e-300)
+    for i in range(min(len(rs.v), len(rf.v))):
+        assert rs.v[i] <= rf.v[i] * (1 + 1e-12) and rf.v[i] <= np.sqrt(N) * rs.v[i] * (1 + 1e-12)
+    assert abs(rs.n - rf.n) <= 1
