@@ -108,8 +108,14 @@ typedef struct {
                            matrix of Frobenius norms of the square kernel's tiles (64 x 64 on the
                            FP64 path, 128 x 128 on the mixed path), e_i <= m_i <= v_i, which stays
                            below 1 at large N where v_i may not (power iteration on the device,
-                           scratch of (ld/b)^2 doubles).  sp2_info.v holds the measure used.
-                           The block-sparse path uses v_i */
+                           scratch of (ld/b)^2 doubles); 2 = the spectral norm e_i itself, the
+                           error the stop is defined on (§2), estimated after every square by 32
+                           Lanczos steps on X - X^2 (a lower bound of e_i within about 1e-3
+                           relative; 66 small launches and 32 reads of two ld x ld FP64 matrices
+                           per square, scratch of 3 ld doubles + 6 KB): FP64 handles only (SP2,
+                           SP2-ACC and McWeeny), SP2_ERR_UNSUPPORTED elsewhere.
+                           sp2_info.v holds the measure used.  The block-sparse path uses v_i
+                           (any other value: SP2_ERR_UNSUPPORTED) */
 } sp2_opts;
 
 #define SP2_MAX_ITER 512
@@ -149,6 +155,15 @@ typedef struct sp2_ctx* sp2_handle;
  * of the same handle.  Works for SP2_PREC_FP64 and SP2_PREC_MIXED handles (the mixed path's
  * first-order correction follows the scaled polynomials). */
 int32_t sp2_set_homo_lumo(sp2_handle h, const double* bounds);
+
+/* Outer bounds of the spectrum of F for the scaling (§3: the extremal eigenvalues or any bounds
+ * with lambda_min <= lambda_1 and lambda_max >= lambda_N serve), in place of the Gershgorin
+ * bounds: bounds = {lambda_min, lambda_max}, used by every later run of the handle (SP2, SP2-ACC
+ * and McWeeny scaling alike) and reported in sp2_info; NULL returns to the Gershgorin bounds.
+ * Bounds that do not contain the spectrum void the method's guarantees (no check is made).
+ * Synchronous.  SP2_ERR_INVALID_ARG for non-finite or unordered bounds; SP2_ERR_UNSUPPORTED on
+ * mixed-precision handles. */
+int32_t sp2_set_bounds(sp2_handle h, const double* bounds);
 
 /* ---- McWeeny expansion (§3) on SP2_PREC_FP64 handles -------------------------------------
  * mode 1: McWeeny, X_0 = (mu I - F) / gamma + I/2 with gamma = 2 max(lmax - mu, mu - lmin)

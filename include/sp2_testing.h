@@ -1,8 +1,10 @@
 /*
  * sp2_testing.h -- internal kernels of libsp2 exposed for unit tests.
  *
- * Not part of the purification API; the paper has no counterpart.  These entry
- * points let tests check the tensor-core matrix product on its own.
+ * Not part of the purification API.  These entry points let tests check the
+ * tensor-core matrix product, the block truncation and the symbolic square on their
+ * own, and run Alg. 1 with prescribed perturbations E_i (the noise of the §4.1
+ * example).
  */
 #ifndef SP2_TESTING_H
 #define SP2_TESTING_H
@@ -40,6 +42,15 @@ int32_t sp2_test_bsr_keep(const float* dense_dev, int64_t N, double tau, int32_t
  * pattern (host, row-major); upper_host receives the pattern of its square restricted to
  * J >= I, as computed by the device kernels.  Synchronous. */
 int32_t sp2_test_bsr_square_pattern(const uint8_t* mask_host, int32_t nb, uint8_t* upper_host);
+
+/* Alg. 1 with prescribed perturbations on an FP64 handle (SP2 or SP2-ACC expansion): later runs
+ * add E_i to X_i as soon as it is formed, X~_i = X_i + E_i (X_0 after the scaling, X_i after
+ * square i), before its trace and error are taken; E_i = 0 for i >= count.  E_dev holds `count`
+ * consecutive N x N row-major FP64 device matrices, owned by the caller and read by every run
+ * until the hook is switched off (E_dev NULL or count 0).  Synchronous; the loop graph is
+ * rebuilt.  SP2_ERR_INVALID_ARG for count < 0 or a missing E_dev; SP2_ERR_UNSUPPORTED on mixed
+ * handles and with the McWeeny expansion. */
+int32_t sp2_test_set_perturbation(struct sp2_ctx* h, const double* E_dev, int64_t count);
 
 #ifdef __cplusplus
 }

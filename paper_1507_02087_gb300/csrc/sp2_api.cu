@@ -69,7 +69,7 @@ static bool opts_valid(const sp2_opts& o) {
          o.corrections >= 0 && o.corrections <= 1 && (o.refine_steps == 0 || o.refine_steps == 2) &&
          (o.refine_fp64 >= 0 && o.refine_fp64 <= 2) && (o.launch_mode == 0 || o.launch_mode == 1) &&
          o.history >= 0 && o.history <= 2 && o.tile >= 0 && o.tile <= 2 &&
-         (o.norm == 0 || o.norm == 1);
+         o.norm >= 0 && o.norm <= 2;
 }
 
 static DevState initial_state(int64_t N, int64_t nocc, const sp2_opts& o, int ld, int round_fp32) {
@@ -540,6 +540,9 @@ struct sp2_ctx {
   double* part_hi = nullptr;
   int* part_bad = nullptr;
   double* mscr = nullptr;        // mixed-norm scratch (norm = 1): T^2 + 2T doubles
+  void* lz = nullptr;            // Lanczos scratch (norm = 2): lanczos_scratch_bytes(ld)
+  const double* pert = nullptr;  // prescribed perturbations E_0.. (caller-owned, testing hook)
+  int64_t pert_count = 0;
   int mcw = 0;                   // 0: SP2, 1: McWeeny, 2: McW-ACC (FP64 path)
   double* sbuf = nullptr;        // McWeeny: the shifted square S_s (ld x ld)
   DevState* st_dev = nullptr;
@@ -565,6 +568,7 @@ static void free_ctx(sp2_ctx* h) {
   cudaFree(h->buf[1]);
   cudaFree(h->part);
   cudaFree(h->mscr);
+  cudaFree(h->lz);
   cudaFree(h->sbuf);
   cudaFree(h->part_lo);
   cudaFree(h->part_hi);
@@ -592,9 +596,10 @@ static sp2_status build_f64_graph(sp2_ctx* h) {
   if (s != SP2_OK) return s;
   if (h->mcw)
     SP2_TRY(sp2::add_mcw_loop_body(body, h->st_dev, h->buf[0], h->buf[1], h->sbuf, h->part, h->T, h->cond,
-                                   h->mscr));
+                                   h->mscr, h->lz, (int)h->N));
   else
-    SP2_TRY(sp2::add_f64_loop_body(body, h->st_dev, h->buf[0], h->buf[1], h->part, h->T, h->cond, h->mscr));
+    SP2_TRY(sp2::add_f64_loop_body(body, h->st_dev, h->buf[0], h->buf[1], h->part, h->T, h->cond, h->mscr, h->lz,
+                                   (int)h->N, h->pert, h->pert_count));
   SP2_TRY(cudaGraphInstantiate(&h->exec, h->graph, 0));
   return SP2_OK;
 }
@@ -615,6 +620,7 @@ static sp2_status create_f64(sp2_ctx* h) {
             cudaMalloc(&h->buf[0], bytes) == cudaSuccess && cudaMalloc(&h->buf[1], bytes) == cudaSuccess;
   if (ok && h->opts.norm == 1)
     ok = cudaMalloc(&h->mscr, sizeof(double) * ((size_t)h->T * h->T + 2 * h->T)) == cudaSuccess;
+  if (ok && h->opts.norm == 2) ok = cudaMalloc(&h->lz, sp2::lanczos_scratch_bytes(h->ld)) == cudaSuccess;
   if (!ok) { (void)cudaGetLastError(); return SP2_ERR_NOMEM; }
   DevState init = initial_state(h->N, h->nocc, h->opts, h->ld, 0);
   SP2_TRY(cudaMemcpy(h->st_dev, &init, sizeof(init), cudaMemcpyHostToDevice));
@@ -634,6 +640,7 @@ extern "C" sp2_status sp2_create(int64_t N, int64_t nocc, int32_t precision, con
   sp2_default_opts(&o);
   if (opts) o = *opts;
   if (!opts_valid(o)) return SP2_ERR_INVALID_ARG;
+  if (o.norm == 2 && precision != SP2_PREC_FP64) return SP2_ERR_UNSUPPORTED;   // spectral stop: FP64 path
   sp2_ctx* h = new (std::nothrow) sp2_ctx();
   if (!h) return SP2_ERR_NOMEM;
   h->N = N; h->nocc = nocc; h->precision = precision; h->opts = o;
@@ -661,15 +668,18 @@ static sp2_status enqueue_f64(sp2_ctx* h, const double* F, double* D, cudaStream
   const int N = (int)h->N;
   SP2_TRY(sp2::launch_bounds_and_init(h->st_dev, F, N, N, h->part_lo, h->part_hi, h->part_bad, h->nparts, s));
   SP2_TRY(sp2::launch_scale_f64(h->st_dev, F, N, N, h->buf[0], h->ld, s));
+  if (h->pert) SP2_TRY(sp2::launch_perturb(h->st_dev, h->buf[0], h->buf[1], h->pert, h->pert_count, N, 1, s));
   SP2_TRY(cudaEventRecord(h->ev_loop[0], s));
   if (h->opts.launch_mode == 0) {
     SP2_TRY(cudaGraphLaunch(h->exec, s));
   } else {
     for (int it = 0; it <= h->opts.max_iter; ++it)
       if (h->mcw)
-        SP2_TRY(sp2::launch_mcw_step_plain(h->st_dev, h->buf[0], h->buf[1], h->sbuf, h->part, h->T, s, h->mscr));
+        SP2_TRY(sp2::launch_mcw_step_plain(h->st_dev, h->buf[0], h->buf[1], h->sbuf, h->part, h->T, s, h->mscr,
+                                           h->lz, N));
       else
-        SP2_TRY(sp2::launch_f64_step_plain(h->st_dev, h->buf[0], h->buf[1], h->part, h->T, s, h->mscr));
+        SP2_TRY(sp2::launch_f64_step_plain(h->st_dev, h->buf[0], h->buf[1], h->part, h->T, s, h->mscr, h->lz, N,
+                                           h->pert, h->pert_count));
   }
   SP2_TRY(cudaEventRecord(h->ev_loop[1], s));
   SP2_TRY(sp2::launch_copy_out(h->st_dev, h->buf[0], h->buf[1], h->ld, N, D, N, s));
@@ -791,7 +801,7 @@ extern "C" int32_t sp2_set_mcweeny(sp2_handle h, int32_t mode, double mu, double
   if (!h || mode < 0 || mode > 2 || (mode > 0 && !std::isfinite(mu)) ||
       (mode == 2 && !(std::isfinite(xi) && xi > 0.0)))
     return SP2_ERR_INVALID_ARG;
-  if (h->mixed) return SP2_ERR_UNSUPPORTED;
+  if (h->mixed || (mode > 0 && h->pert)) return SP2_ERR_UNSUPPORTED;
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(h->device);
@@ -813,6 +823,49 @@ extern "C" int32_t sp2_set_mcweeny(sp2_handle h, int32_t mode, double mu, double
   if (r == SP2_OK) {
     h->st_host->mcw = mode;
     h->mcw = mode;
+    if (h->opts.launch_mode == 0) r = build_f64_graph(h);
+  }
+  (void)cudaGetLastError();
+  cudaSetDevice(cur);
+  return r;
+}
+
+extern "C" int32_t sp2_set_bounds(sp2_handle h, const double* bounds) {
+  if (!h || (bounds && !(std::isfinite(bounds[0]) && std::isfinite(bounds[1]) && bounds[0] < bounds[1])))
+    return SP2_ERR_INVALID_ARG;
+  if (h->mixed) return SP2_ERR_UNSUPPORTED;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  sp2_status r = SP2_OK;
+  const int32_t on = bounds ? 1 : 0;
+  const double b[2] = {bounds ? bounds[0] : 0.0, bounds ? bounds[1] : 0.0};
+  static_assert(offsetof(DevState, ub_hi) == offsetof(DevState, ub_lo) + sizeof(double), "ub_lo, ub_hi adjacent");
+  char* base = reinterpret_cast<char*>(h->st_dev);
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(base + offsetof(DevState, ubounds), &on, sizeof(on), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(base + offsetof(DevState, ub_lo), b, sizeof(b), cudaMemcpyHostToDevice) != cudaSuccess)
+    r = SP2_ERR_CUDA;
+  if (r == SP2_OK) {
+    h->st_host->ubounds = on;
+    h->st_host->ub_lo = b[0];
+    h->st_host->ub_hi = b[1];
+  }
+  (void)cudaGetLastError();
+  cudaSetDevice(cur);
+  return r;
+}
+
+extern "C" int32_t sp2_test_set_perturbation(sp2_handle h, const double* E_dev, int64_t count) {
+  if (!h || count < 0 || (count > 0 && !E_dev)) return SP2_ERR_INVALID_ARG;
+  if (h->mixed || (count > 0 && h->mcw)) return SP2_ERR_UNSUPPORTED;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  sp2_status r = cudaDeviceSynchronize() == cudaSuccess ? SP2_OK : SP2_ERR_CUDA;
+  if (r == SP2_OK) {
+    h->pert = count > 0 ? E_dev : nullptr;
+    h->pert_count = count > 0 ? count : 0;
     if (h->opts.launch_mode == 0) r = build_f64_graph(h);
   }
   (void)cudaGetLastError();
@@ -869,6 +922,7 @@ extern "C" sp2_status sp2_create_batch(int32_t count, const int64_t* N, const in
   if (opts) o = *opts;
   if (!opts_valid(o)) return SP2_ERR_INVALID_ARG;
   if (precision == SP2_PREC_MIXED && o.refine_steps > 0 && o.refine_fp64 && count > 1) return SP2_ERR_UNSUPPORTED;
+  if (o.norm == 2 && precision != SP2_PREC_FP64) return SP2_ERR_UNSUPPORTED;
   sp2_batch_ctx* hb = new (std::nothrow) sp2_batch_ctx();
   if (!hb) return SP2_ERR_NOMEM;
   hb->count = count;

@@ -867,6 +867,7 @@ extern "C" sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, in
   if (o.max_iter < 1 || o.max_iter > SP2_MAX_ITER || !(o.qtilde > 0.0) || (o.guard != 0 && o.guard != 1) ||
       (o.launch_mode != 0 && o.launch_mode != 1))
     return SP2_ERR_INVALID_ARG;
+  if (o.norm != 0) return SP2_ERR_UNSUPPORTED;       // the block-sparse stop uses the Frobenius v_i
   sp2_bsr_ctx* h = new (std::nothrow) sp2_bsr_ctx();
   if (!h) return SP2_ERR_NOMEM;
   h->N = N; h->nocc = n_occ; h->tau = tau; h->rule = rule; h->opts = o;

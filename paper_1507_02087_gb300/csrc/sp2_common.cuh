@@ -47,11 +47,17 @@ struct DevState {
   int32_t dk;          // derivative steps completed (mixed path correction)
   int32_t round_fp32;  // 1: X_0 is rounded to FP32 (mixed path)
   int32_t iter_active; // block-sparse path: the current loop round squares (set at its start)
-  int32_t norm;        // error measure of the stop: 0 = Frobenius v_i, 1 = mixed norm m_i (§2)
+  int32_t norm;        // error measure of the stop: 0 = Frobenius v_i, 1 = mixed norm m_i (§2),
+                       // 2 = spectral e_i (Lanczos; FP64 path)
   // block-sparse path, work of the current run's squares: 32 x 32 block products and
   // upper blocks of the squares computed
   unsigned long long bprod;
   unsigned long long sblocks;
+  double spec_e;       // norm = 2: the Lanczos estimate of ||X_{k-1} - X_{k-1}^2||_2 of the last square
+  double tr_shift;     // Tr[E_k] of a prescribed perturbation added to the square just written
+  int32_t ubounds;     // 1: the caller's outer bounds (ub_lo, ub_hi) replace the Gershgorin bounds
+  int32_t _pad4;
+  double ub_lo, ub_hi;
   // SP2-ACC (Alg. 4 / Alg. 5): set by sp2_set_homo_lumo, schedule filled by the init kernel
   int32_t acc;         // 1: homo/lumo-based accelerated expansion
   int32_t n_min;       // first step of the stop test (acceleration off)

@@ -72,6 +72,10 @@ init_kernel(DevState* st, const double* __restrict__ F, int64_t ldf, const doubl
       bad |= part_bad[b];
     }
     if (!isfinite(lo) || !isfinite(hi)) bad = 1;
+    if (st->ubounds) {                           // any outer bounds of the spectrum serve (§3)
+      lo = st->ub_lo;
+      hi = st->ub_hi;
+    }
     s_lmin = lo; s_lmax = hi; s_bad = bad;
   }
   __syncthreads();
@@ -98,6 +102,7 @@ init_kernel(DevState* st, const double* __restrict__ F, int64_t ldf, const doubl
     st->lmin = lmin; st->lmax = lmax;
     st->scale_a = sa; st->scale_w = sw;
     st->dk = 0;
+    st->tr_shift = 0.0;
     st->k = 0; st->done = 0; st->n_out = 0; st->reason = SP2_STOP_EXACT;
     st->status = SP2_OK; st->out_buf = 0; st->out_mode = OUT_COPY; st->hist_len = 0;
     st->tr[0] = 0.0; st->p[0] = 0;
@@ -313,7 +318,8 @@ finalize_kernel(DevState* st, const double* __restrict__ part, int nparts, int s
   b = block_sum<kFinThreads>(b, sm);
   c = block_sum<kFinThreads>(c, sm);
   double vk = sqrt(a);                           // v_{k-1} = ||X_{k-1} - X_{k-1}^2||_F
-  if (st->norm && mscr) {                        // or m_{k-1}, the mixed norm over 64 x 64 tiles
+  if (st->norm == 2) vk = st->spec_e;            // or e_{k-1}, the Lanczos estimate of the 2-norm
+  if (st->norm == 1 && mscr) {                   // or m_{k-1}, the mixed norm over 64 x 64 tiles
     const int T = st->ld / kTile;
     vk = mixed_norm_cta<kFinThreads>(T, mscr, sm, [&](int I, int J) {
       const double v2 = part[(int64_t)stride * upper_index(I, J, T)];
@@ -330,7 +336,7 @@ finalize_kernel(DevState* st, const double* __restrict__ part, int nparts, int s
     tr_new = st->acc ? ca * b + cb * c + cc * (double)st->N : (pk ? b : 2.0 * c - b);
     tr_ref = c;
   } else {
-    tr_new = st->mcw ? 0.0 : b;                  // McWeeny: no trace rule, none recorded
+    tr_new = st->mcw ? 0.0 : b + st->tr_shift;   // McWeeny: no trace rule, none recorded
     tr_ref = st->tr[k - 1];
   }
   if (record_and_test(st, pk, vk, tr_new, tr_ref)) cudaGraphSetConditional(cond, 0);
@@ -370,7 +376,8 @@ finalize_plain_kernel(DevState* st, const double* __restrict__ part, int nparts,
   a = block_sum<kFinThreads>(a, sm);
   b = block_sum<kFinThreads>(b, sm);
   double vk = sqrt(a);
-  if (st->norm && mscr) {
+  if (st->norm == 2) vk = st->spec_e;
+  if (st->norm == 1 && mscr) {
     const int T = st->ld / kTile;
     vk = mixed_norm_cta<kFinThreads>(T, mscr, sm, [&](int I, int J) {
       const double v2 = part[2 * upper_index(I, J, T)];
@@ -381,7 +388,40 @@ finalize_plain_kernel(DevState* st, const double* __restrict__ part, int nparts,
   const int k = st->k + 1;
   double ca, cb, cc;
   const int pk = st->acc ? acc_step(st, k, ca, cb, cc) : (st->tr[k - 1] > (double)st->nocc ? 1 : 0);
-  record_and_test(st, st->mcw ? 1 : pk, vk, st->mcw ? 0.0 : b, st->tr[k - 1]);
+  record_and_test(st, st->mcw ? 1 : pk, vk, st->mcw ? 0.0 : b + st->tr_shift, st->tr[k - 1]);
+}
+
+// ---- prescribed perturbation (Alg. 1: X~_i = X_i + E_i) ----------------------------------------
+// E holds `count` consecutive N x N row-major matrices; E_i (i < count) is added to X_i as soon
+// as it is formed: X_0 after the scaling (initial = 1, Tr[E_0] added to Tr[X_0] at once), X_k
+// after square k (Tr[E_k] to st->tr_shift, which the finalize adds to the square's trace).  The
+// trace is summed by block 0 in a fixed order.
+__global__ void perturb_kernel(DevState* st, double* buf0, double* buf1, const double* __restrict__ E,
+                               int64_t count, int initial) {
+  __shared__ double sm[32];
+  if (st->done) return;
+  const int i = initial ? 0 : st->k + 1;
+  if (i >= count) {
+    if (!initial && blockIdx.x == 0 && threadIdx.x == 0) st->tr_shift = 0.0;
+    return;
+  }
+  const int N = st->N, ld = st->ld;
+  double* X = initial ? buf0 : (((st->k + 1) & 1) ? buf1 : buf0);
+  const double* Ei = E + (int64_t)i * N * N;
+  const int64_t total = (int64_t)N * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / N), c = (int)(e % N);
+    X[(int64_t)r * ld + c] += Ei[e];
+  }
+  if (blockIdx.x != 0) return;
+  double t = 0.0;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) t += Ei[(int64_t)j * N + j];
+  t = block_sum<256>(t, sm);
+  if (threadIdx.x == 0) {
+    if (initial) st->tr[0] += t;
+    else st->tr_shift = t;
+  }
 }
 
 // ---- host-side launchers ------------------------------------------------------------------
@@ -404,16 +444,30 @@ cudaError_t launch_scale_f64(const DevState* st, const double* F, int64_t ldf, i
   return cudaGetLastError();
 }
 
+cudaError_t launch_perturb(DevState* st, double* buf0, double* buf1, const double* E, int64_t count, int N,
+                           int initial, cudaStream_t s) {
+  perturb_kernel<<<elementwise_blocks((int64_t)N * N), 256, 0, s>>>(st, buf0, buf1, E, count, initial);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_f64_step_plain(DevState* st, double* buf0, double* buf1, double* part, int T,
-                                  cudaStream_t s, double* mscr) {
+                                  cudaStream_t s, double* mscr, void* lz, int N, const double* E, int64_t ecount) {
   const int ntiles = T * (T + 1) / 2;
   syrk_f64_kernel<<<ntiles, kSyrkThreads, 0, s>>>(st, buf0, buf1, part);
+  if (lz) {
+    cudaError_t e = launch_lanczos(st, buf0, buf1, nullptr, lz, N, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (E) {
+    cudaError_t e = launch_perturb(st, buf0, buf1, E, ecount, N, 0, s);
+    if (e != cudaSuccess) return e;
+  }
   finalize_plain_kernel<<<1, kFinThreads, 0, s>>>(st, part, ntiles, mscr);
   return cudaGetLastError();
 }
 
 cudaError_t add_mcw_loop_body(cudaGraph_t body, DevState* st, double* buf0, double* buf1, double* S, double* part,
-                              int T, cudaGraphConditionalHandle cond, double* mscr) {
+                              int T, cudaGraphConditionalHandle cond, double* mscr, void* lz, int N) {
   const int ntiles = T * (T + 1) / 2;
   cudaGraphNode_t n_sq, n_fin, n_pr;
   const double* b0 = buf0;
@@ -426,6 +480,7 @@ cudaError_t add_mcw_loop_body(cudaGraph_t body, DevState* st, double* buf0, doub
   kp.kernelParams = a1;
   cudaError_t e = cudaGraphAddKernelNode(&n_sq, body, nullptr, 0, &kp);
   if (e != cudaSuccess) return e;
+  if (lz && (e = add_lanczos_nodes(body, n_sq, st, buf0, buf1, S, lz, N, &n_sq)) != cudaSuccess) return e;
   e = add_finalize_node(body, &n_sq, 1, st, part, ntiles, 2, cond, &n_fin, mscr);
   if (e != cudaSuccess) return e;
   const double* Sc = S;
@@ -436,9 +491,13 @@ cudaError_t add_mcw_loop_body(cudaGraph_t body, DevState* st, double* buf0, doub
 }
 
 cudaError_t launch_mcw_step_plain(DevState* st, double* buf0, double* buf1, double* S, double* part, int T,
-                                  cudaStream_t s, double* mscr) {
+                                  cudaStream_t s, double* mscr, void* lz, int N) {
   const int ntiles = T * (T + 1) / 2;
   mcw_square_kernel<<<ntiles, kSyrkThreads, 0, s>>>(st, buf0, buf1, S, part);
+  if (lz) {
+    cudaError_t e = launch_lanczos(st, buf0, buf1, S, lz, N, s);
+    if (e != cudaSuccess) return e;
+  }
   finalize_plain_kernel<<<1, kFinThreads, 0, s>>>(st, part, ntiles, mscr);
   mcw_prod_kernel<<<ntiles, kSyrkThreads, 0, s>>>(st, buf0, buf1, S, part);
   return cudaGetLastError();
@@ -457,7 +516,8 @@ cudaError_t add_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int nd
 }
 
 cudaError_t add_f64_loop_body(cudaGraph_t body, DevState* st, double* buf0, double* buf1, double* part,
-                              int T, cudaGraphConditionalHandle cond, double* mscr) {
+                              int T, cudaGraphConditionalHandle cond, double* mscr, void* lz, int N,
+                              const double* E, int64_t ecount) {
   const int ntiles = T * (T + 1) / 2;
   cudaGraphNode_t n_sq, n_fin;
   void* args[] = {&st, &buf0, &buf1, &part};
@@ -468,6 +528,18 @@ cudaError_t add_f64_loop_body(cudaGraph_t body, DevState* st, double* buf0, doub
   kp.kernelParams = args;
   cudaError_t e = cudaGraphAddKernelNode(&n_sq, body, nullptr, 0, &kp);
   if (e != cudaSuccess) return e;
+  if (lz && (e = add_lanczos_nodes(body, n_sq, st, buf0, buf1, nullptr, lz, N, &n_sq)) != cudaSuccess) return e;
+  if (E) {
+    int initial = 0;
+    void* pa[] = {&st, &buf0, &buf1, &E, &ecount, &initial};
+    kp.func = (void*)perturb_kernel;
+    kp.gridDim = dim3(elementwise_blocks((int64_t)N * N));
+    kp.blockDim = dim3(256);
+    kp.kernelParams = pa;
+    cudaGraphNode_t n_pt;
+    if ((e = cudaGraphAddKernelNode(&n_pt, body, &n_sq, 1, &kp)) != cudaSuccess) return e;
+    n_sq = n_pt;
+  }
   return add_finalize_node(body, &n_sq, 1, st, part, ntiles, 2, cond, &n_fin, mscr);
 }
 

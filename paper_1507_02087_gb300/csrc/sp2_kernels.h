@@ -31,15 +31,29 @@ cudaError_t launch_scale_f64(const DevState* st, const double* F, int64_t ldf, i
                              int ld, cudaStream_t s);
 // a3-a5, a7 for the FP64 path: the body of the device-controlled loop (square +
 // finalize), added to `body` as kernel nodes.  `mscr` (T^2 + 2T doubles, or null) is the
-// scratch of the mixed-norm stop, used when the state asks for it.
+// scratch of the mixed-norm stop, used when the state asks for it; `lz` (lanczos_scratch_bytes,
+// or null) adds the Lanczos estimate of the spectral norm between the square and the finalize.
 cudaError_t add_f64_loop_body(cudaGraph_t body, DevState* st, double* buf0, double* buf1, double* part,
-                              int T, cudaGraphConditionalHandle cond, double* mscr = nullptr);
+                              int T, cudaGraphConditionalHandle cond, double* mscr = nullptr,
+                              void* lz = nullptr, int N = 0, const double* E = nullptr, int64_t ecount = 0);
+// Alg. 1's prescribed perturbation: E_i (i < count, N x N row-major each) added to X_0 (initial)
+// or to the square just written; in the loop bodies it follows the Lanczos nodes.
+cudaError_t launch_perturb(DevState* st, double* buf0, double* buf1, const double* E, int64_t count, int N,
+                           int initial, cudaStream_t s);
 // The McWeeny expansion's loop body (FP64): shifted square into S, finalize (stop test),
 // then X_k = (3 - 2c) S - 2 alpha S X_{k-1}; S is an ld x ld FP64 buffer.
 cudaError_t add_mcw_loop_body(cudaGraph_t body, DevState* st, double* buf0, double* buf1, double* S, double* part,
-                              int T, cudaGraphConditionalHandle cond, double* mscr);
+                              int T, cudaGraphConditionalHandle cond, double* mscr, void* lz = nullptr, int N = 0);
 cudaError_t launch_mcw_step_plain(DevState* st, double* buf0, double* buf1, double* S, double* part, int T,
-                                  cudaStream_t s, double* mscr);
+                                  cudaStream_t s, double* mscr, void* lz = nullptr, int N = 0);
+// Spectral-norm estimate e_{k-1} = ||X_{k-1} - X_{k-1}^2||_2 (Lanczos) of the square just written,
+// into st->spec_e: graph nodes after `dep` (the last one in *last), or stream launches.  S is the
+// McWeeny step's shifted square (null for SP2 / SP2-ACC).
+size_t lanczos_scratch_bytes(int ld);
+cudaError_t add_lanczos_nodes(cudaGraph_t g, cudaGraphNode_t dep, DevState* st, const double* buf0,
+                              const double* buf1, const double* S, void* lz, int N, cudaGraphNode_t* last);
+cudaError_t launch_lanczos(DevState* st, const double* buf0, const double* buf1, const double* S, void* lz,
+                           int N, cudaStream_t s);
 // Per-iteration reduction + stop test over `nparts` partial records of `stride` doubles.
 cudaError_t add_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, DevState* st,
                               double* part, int nparts, int stride, cudaGraphConditionalHandle cond,
@@ -50,7 +64,8 @@ cudaError_t launch_copy_out(const DevState* st, const double* buf0, const double
 // One FP64 square + stop test launched directly on a stream (no graph); a no-op once
 // st->done is set.
 cudaError_t launch_f64_step_plain(DevState* st, double* buf0, double* buf1, double* part, int T,
-                                  cudaStream_t s, double* mscr = nullptr);
+                                  cudaStream_t s, double* mscr = nullptr, void* lz = nullptr, int N = 0,
+                                  const double* E = nullptr, int64_t ecount = 0);
 // FP64 purification step `step` (0 or 1) on an ld x ld FP64 matrix (mixed-path refinement).
 cudaError_t launch_refine_f64(const DevState* st, const double* Xin, double* Xout, int ld, int step, double* part,
                               cudaStream_t s);

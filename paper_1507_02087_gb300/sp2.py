@@ -109,6 +109,10 @@ def lib() -> ctypes.CDLL:
         L.sp2_test_bsr_keep.restype = i32
         L.sp2_test_bsr_square_pattern.argtypes = [vp, i32, vp]
         L.sp2_test_bsr_square_pattern.restype = i32
+        L.sp2_set_bounds.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.sp2_set_bounds.restype = i32
+        L.sp2_test_set_perturbation.argtypes = [vp, vp, i64]
+        L.sp2_test_set_perturbation.restype = i32
         _lib = L
     return _lib
 
@@ -126,7 +130,7 @@ def _stream_ptr(stream) -> int:
 
 
 TILES = {"auto": 0, "128": 1, "pair": 2}
-NORMS = {"fro": 0, "mixed": 1}
+NORMS = {"fro": 0, "mixed": 1, "spectral": 2}
 HISTORY = {"auto": 0, "full": 1, "recompute": 2}
 
 
@@ -372,6 +376,25 @@ class Purifier:
 
     def set_homo_lumo(self, bounds) -> None:
         sp2_set_homo_lumo(self.h, bounds)
+
+    def set_bounds(self, bounds) -> None:
+        """Outer spectral bounds (lambda_min, lambda_max) for the scaling in place of the
+        Gershgorin bounds (FP64 handles); None returns to Gershgorin."""
+        arr = None if bounds is None else (ctypes.c_double * 2)(*[float(x) for x in bounds])
+        _check(lib().sp2_set_bounds(self.h, arr), "sp2_set_bounds")
+
+    def set_perturbation(self, E) -> None:
+        """Testing hook (Alg. 1): E is a contiguous CUDA float64 tensor (count, N, N); later runs
+        add E[i] to X_i as it is formed.  The tensor is kept alive here; None switches it off."""
+        import torch
+        if E is None:
+            _check(lib().sp2_test_set_perturbation(self.h, None, 0), "sp2_test_set_perturbation")
+            self._pert = None
+            return
+        if E.dtype != torch.float64 or not E.is_cuda or not E.is_contiguous() or E.shape[1:] != (self.N, self.N):
+            raise ValueError("E must be a contiguous CUDA float64 tensor of shape (count, N, N)")
+        _check(lib().sp2_test_set_perturbation(self.h, E.data_ptr(), E.shape[0]), "sp2_test_set_perturbation")
+        self._pert = E
 
     def set_mcweeny(self, mode: str | None, mu: float = 0.0, xi: float = 0.0) -> None:
         """McWeeny expansion on an FP64 handle: mode "mcw", "mcw-acc" (gap estimate xi) or None

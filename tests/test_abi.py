@@ -75,12 +75,18 @@ def test_invalid_arguments_rejected_before_any_cuda_call(built):
                 sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 5, 0, 0, 0),     # launch_mode
                 sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 0, 3, 0, 0),     # history
                 sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 0, 0, 3, 0),     # tile
-                sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 0, 0, 0, 2)):    # norm
+                sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 0, 0, 0, 3)):    # norm
         assert L.sp2_create(10, 5, 1, ctypes.byref(bad), ctypes.byref(h)) == 1
         assert h.value is None
+    # the spectral-norm stop (norm = 2) exists on the FP64 path only
+    spec = sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 0, 0, 0, 2)
+    assert L.sp2_create(10, 5, 1, ctypes.byref(spec), ctypes.byref(h)) == 7
+    assert h.value is None
     assert L.sp2_run(None, None, None, None) == 1
     assert L.sp2_run_host(None, None, None, None) == 1
     assert L.sp2_get_info(None, None) == 1
+    assert L.sp2_set_bounds(None, None) == 1
+    assert L.sp2_test_set_perturbation(None, None, 0) == 1
     assert L.sp2_test_tc_gemm(None, 256, 1, 0, 0, 0, 0, None, None) == 1
     L.sp2_destroy(None)
 
