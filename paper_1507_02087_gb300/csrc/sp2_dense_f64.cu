@@ -455,7 +455,7 @@ cudaError_t launch_f64_step_plain(DevState* st, double* buf0, double* buf1, doub
   const int ntiles = T * (T + 1) / 2;
   syrk_f64_kernel<<<ntiles, kSyrkThreads, 0, s>>>(st, buf0, buf1, part);
   if (lz) {
-    cudaError_t e = launch_lanczos(st, buf0, buf1, nullptr, lz, N, s);
+    cudaError_t e = launch_lanczos(st, buf0, buf1, nullptr, part, ntiles, lz, N, T * kTile, s);
     if (e != cudaSuccess) return e;
   }
   if (E) {
@@ -480,7 +480,7 @@ cudaError_t add_mcw_loop_body(cudaGraph_t body, DevState* st, double* buf0, doub
   kp.kernelParams = a1;
   cudaError_t e = cudaGraphAddKernelNode(&n_sq, body, nullptr, 0, &kp);
   if (e != cudaSuccess) return e;
-  if (lz && (e = add_lanczos_nodes(body, n_sq, st, buf0, buf1, S, lz, N, &n_sq)) != cudaSuccess) return e;
+  if (lz && (e = add_lanczos_nodes(body, n_sq, st, buf0, buf1, S, part, ntiles, lz, N, T * kTile, &n_sq)) != cudaSuccess) return e;
   e = add_finalize_node(body, &n_sq, 1, st, part, ntiles, 2, cond, &n_fin, mscr);
   if (e != cudaSuccess) return e;
   const double* Sc = S;
@@ -495,7 +495,7 @@ cudaError_t launch_mcw_step_plain(DevState* st, double* buf0, double* buf1, doub
   const int ntiles = T * (T + 1) / 2;
   mcw_square_kernel<<<ntiles, kSyrkThreads, 0, s>>>(st, buf0, buf1, S, part);
   if (lz) {
-    cudaError_t e = launch_lanczos(st, buf0, buf1, S, lz, N, s);
+    cudaError_t e = launch_lanczos(st, buf0, buf1, S, part, ntiles, lz, N, T * kTile, s);
     if (e != cudaSuccess) return e;
   }
   finalize_plain_kernel<<<1, kFinThreads, 0, s>>>(st, part, ntiles, mscr);
@@ -528,7 +528,7 @@ cudaError_t add_f64_loop_body(cudaGraph_t body, DevState* st, double* buf0, doub
   kp.kernelParams = args;
   cudaError_t e = cudaGraphAddKernelNode(&n_sq, body, nullptr, 0, &kp);
   if (e != cudaSuccess) return e;
-  if (lz && (e = add_lanczos_nodes(body, n_sq, st, buf0, buf1, nullptr, lz, N, &n_sq)) != cudaSuccess) return e;
+  if (lz && (e = add_lanczos_nodes(body, n_sq, st, buf0, buf1, nullptr, part, ntiles, lz, N, T * kTile, &n_sq)) != cudaSuccess) return e;
   if (E) {
     int initial = 0;
     void* pa[] = {&st, &buf0, &buf1, &E, &ecount, &initial};

@@ -48,12 +48,14 @@ cudaError_t launch_mcw_step_plain(DevState* st, double* buf0, double* buf1, doub
                                   cudaStream_t s, double* mscr, void* lz = nullptr, int N = 0);
 // Spectral-norm estimate e_{k-1} = ||X_{k-1} - X_{k-1}^2||_2 (Lanczos) of the square just written,
 // into st->spec_e: graph nodes after `dep` (the last one in *last), or stream launches.  S is the
-// McWeeny step's shifted square (null for SP2 / SP2-ACC).
+// McWeeny step's shifted square (null for SP2 / SP2-ACC); part / ntiles are the square's
+// (v^2, trace) partial records, whose v^2 sum sets the FP32 scaling of X - X^2.
 size_t lanczos_scratch_bytes(int ld);
 cudaError_t add_lanczos_nodes(cudaGraph_t g, cudaGraphNode_t dep, DevState* st, const double* buf0,
-                              const double* buf1, const double* S, void* lz, int N, cudaGraphNode_t* last);
-cudaError_t launch_lanczos(DevState* st, const double* buf0, const double* buf1, const double* S, void* lz,
-                           int N, cudaStream_t s);
+                              const double* buf1, const double* S, const double* part, int ntiles, void* lz,
+                              int N, int ld, cudaGraphNode_t* last);
+cudaError_t launch_lanczos(DevState* st, const double* buf0, const double* buf1, const double* S,
+                           const double* part, int ntiles, void* lz, int N, int ld, cudaStream_t s);
 // Per-iteration reduction + stop test over `nparts` partial records of `stride` doubles.
 cudaError_t add_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, DevState* st,
                               double* part, int nparts, int stride, cudaGraphConditionalHandle cond,

@@ -9,12 +9,17 @@
 // kLzSteps steps of the symmetric Lanczos recurrence (three-term, no reorthogonalisation: lost
 // orthogonality only repeats converged extreme Ritz values) from a fixed start vector.  The
 // extreme eigenvalues of the tridiagonal matrix come from multisection with Sturm counts (one
-// warp, 32 points a round).  The Ritz values are inside the spectrum, so the estimate is a lower
+// warp, 32 points a round, in FP32: the tridiagonal of the scaled A is O(1) and the estimate only
+// needs a few digits).  The Ritz values are inside the spectrum, so the estimate is a lower
 // bound of e that approaches it from below; the stop test only needs its logarithm.
 //
-// Kernels per estimate: start (1 CTA), kLzSteps x {matvec (one warp per row over the grid),
-// update (1 CTA)}, eig (1 warp): 2 kLzSteps + 2 launches, added to the loop graph between the
-// square and the stop test.  Traffic: two ld x ld FP64 matrices per matvec.
+// Per estimate: start (1 CTA: coefficients, start vector, a power-of-two scale 2^-s with 2^s near
+// v_{k-1} from the square's Frobenius partials), form (A 2^-s rounded to FP32 once: the ld x ld
+// FP32 matrix, half the bytes of one FP64 iterate, is then read kLzSteps times, from L2 where it
+// fits), kLzSteps x step (w = A q_j, one warp per row, FP32 products summed in FP32 per lane and
+// FP64 across lanes; the last CTA to finish, found by an atomic ticket after a fence, runs the
+// FP64 three-term update, so no CTA waits on another), eig (1 warp).  The FP32 rounding of A and
+// of the products perturbs A by about 1e-7 of its norm, far below the Lanczos truncation error.
 #include <math.h>
 
 #include "sp2_common.cuh"
@@ -24,29 +29,32 @@ namespace sp2 {
 namespace {
 
 constexpr int kLzSteps = 32;          // Lanczos steps per estimate
-constexpr int kLzThreads = 1024;      // start / update: one CTA
-constexpr int kLzMvThreads = 256;     // matvec: 8 warps, one row per warp at a time
-constexpr int kLzMvBlocks = 152 * 4;  // matvec grid cap = number of partial sums
-constexpr int kSturmRounds = 14;      // 33^14 > 2^70: far below FP64 resolution
+constexpr int kLzThreads = 1024;      // start: one CTA
+constexpr int kLzMvThreads = 512;     // step: 16 warps, one row per warp at a time
+constexpr int kLzMvBlocks = 152 * 2;  // step grid cap = number of partial sums
+constexpr int kSturmRounds = 6;       // 33^6 > 2^30: below FP32 resolution of the interval
 
 struct LzScratch {
-  const double* Xa;           // X_{k-1}
-  const double* Y;            // the stored product of this step
-  double ab;                  // a + b
-  double c;                   // identity coefficient of Y
-  double inv_a;               // 1 / a
+  double scale;               // 2^-s applied before rounding A to FP32
   int32_t m;                  // completed steps
   int32_t live;               // 0 once the Krylov space is invariant (beta = 0) or not finite
+  uint32_t ticket;            // CTAs of the current step that have finished their rows
+  int32_t _pad;
   double alpha[kLzSteps];     // diagonal of the tridiagonal matrix
   double beta[kLzSteps + 1];  // beta[j] couples q_{j-1} and q_j; beta[0] = 0
   double part[kLzMvBlocks];   // per-CTA partials of q_j . A q_j
 };
+// followed by q_{j-1}, q_j, w (FP64, ld each), q_j in FP32 (ld) and A 2^-s in FP32 (ld x ld)
 
 constexpr size_t kVecOff = (sizeof(LzScratch) + 255) / 256 * 256;
 
 __device__ __forceinline__ double* lz_vec(LzScratch* lz, int ld, int which) {
   return reinterpret_cast<double*>(reinterpret_cast<char*>(lz) + kVecOff) + (size_t)which * ld;
 }
+__device__ __forceinline__ float* lz_q32(LzScratch* lz, int ld) {
+  return reinterpret_cast<float*>(lz_vec(lz, ld, 3));
+}
+__device__ __forceinline__ float* lz_a32(LzScratch* lz, int ld) { return lz_q32(lz, ld) + ld; }
 
 // Start vector entry i: SplitMix64 (Steele, Lea, Flood 2014) of the index, mapped to [-1, 1).
 __device__ __forceinline__ double start_entry(int i) {
@@ -57,37 +65,46 @@ __device__ __forceinline__ double start_entry(int i) {
   return (double)(z >> 11) * 0x1p-52 - 1.0;
 }
 
+// X_{k-1}, the stored product Y and its coefficients (a, b, c) for the square just written.
+__device__ __forceinline__ void lz_operands(const DevState* st, const double* buf0, const double* buf1,
+                                            const double* S, const double*& Xa, const double*& Y, double& a,
+                                            double& b, double& c) {
+  const int k = st->k;
+  Xa = (k & 1) ? buf1 : buf0;
+  if (st->mcw) {                                 // S_s = (alpha X + c0 I)^2, c0 = (1 - alpha) / 2
+    const double al = st->alpha[k + 1], c0 = 0.5 * (1.0 - al);
+    a = al * al; b = 2.0 * al * c0; c = c0 * c0;
+    Y = S;
+    return;
+  }
+  if (st->acc) {
+    acc_step(st, k + 1, a, b, c);
+  } else {
+    const int pk = st->tr[k] > (double)st->nocc ? 1 : 0;
+    a = pk ? 1.0 : -1.0; b = pk ? 0.0 : 2.0; c = 0.0;
+  }
+  Y = (k & 1) ? buf0 : buf1;
+}
+
 __global__ void __launch_bounds__(kLzThreads)
-lz_start_kernel(const DevState* st, const double* buf0, const double* buf1, const double* S, LzScratch* lz) {
+lz_start_kernel(const DevState* st, const double* __restrict__ part, int ntiles, LzScratch* lz) {
   __shared__ double sm[32];
   if (st->done) return;
-  const int N = st->N, ld = st->ld, k = st->k;    // the square k + 1 has just been written
+  const int N = st->N, ld = st->ld;
+  double v2 = 0.0;                               // v_{k-1}^2 from the square's partials
+  for (int t = threadIdx.x; t < ntiles; t += kLzThreads) v2 += part[2 * (int64_t)t];
+  v2 = block_sum<kLzThreads>(v2, sm);
   double* qp = lz_vec(lz, ld, 0);
   double* q = lz_vec(lz, ld, 1);
+  float* q32 = lz_q32(lz, ld);
   if (threadIdx.x == 0) {
-    const double* Xprev = (k & 1) ? buf1 : buf0;
-    double a, b, c;
-    const double* Y;
-    if (st->mcw) {                               // S_s = (alpha X + c0 I)^2, c0 = (1 - alpha) / 2
-      const double al = st->alpha[k + 1], c0 = 0.5 * (1.0 - al);
-      a = al * al; b = 2.0 * al * c0; c = c0 * c0;
-      Y = S;
-    } else {
-      if (st->acc) {
-        acc_step(st, k + 1, a, b, c);
-      } else {
-        const int pk = st->tr[k] > (double)st->nocc ? 1 : 0;
-        a = pk ? 1.0 : -1.0; b = pk ? 0.0 : 2.0; c = 0.0;
-      }
-      Y = (k & 1) ? buf0 : buf1;
-    }
-    lz->Xa = Xprev;
-    lz->Y = Y;
-    lz->ab = a + b;
-    lz->c = c;
-    lz->inv_a = 1.0 / a;
+    const double v = sqrt(v2);
+    int e = (v > 0.0 && isfinite(v)) ? ilogb(v) : 0;
+    e = e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
+    lz->scale = ldexp(1.0, -e);
     lz->m = 0;
     lz->live = 1;
+    lz->ticket = 0;
     lz->beta[0] = 0.0;
   }
   double ss = 0.0;
@@ -99,159 +116,213 @@ lz_start_kernel(const DevState* st, const double* buf0, const double* buf1, cons
   }
   ss = block_sum<kLzThreads>(ss, sm);
   const double inv = 1.0 / sqrt(ss);
-  for (int i = threadIdx.x; i < N; i += kLzThreads) q[i] *= inv;
-}
-
-// w = A q_j, one warp per row (16-byte loads along the row), and the CTA's share of q_j . w.
-__global__ void __launch_bounds__(kLzMvThreads)
-lz_matvec_kernel(const DevState* st, LzScratch* lz) {
-  __shared__ double sm[32];
-  if (st->done || !lz->live) return;
-  const int N = st->N, ld = st->ld;
-  const double2* __restrict__ X = reinterpret_cast<const double2*>(lz->Xa);
-  const double2* __restrict__ Y = reinterpret_cast<const double2*>(lz->Y);
-  const double ab = lz->ab, c = lz->c, inv_a = lz->inv_a;
-  const double* __restrict__ q = lz_vec(lz, ld, 1);
-  const double2* __restrict__ q2 = reinterpret_cast<const double2*>(q);
-  double* w = lz_vec(lz, ld, 2);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int h = ld / 2;
-  double pa = 0.0;
-  for (int r = blockIdx.x * (kLzMvThreads / 32) + warp; r < N; r += gridDim.x * (kLzMvThreads / 32)) {
-    const double2* xr = X + (int64_t)r * h;
-    const double2* yr = Y + (int64_t)r * h;
-    double s = 0.0;
-    for (int j = lane; j < h; j += 32) {
-      const double2 x = xr[j], y = yr[j], v = q2[j];
-      s = fma(fma(ab, x.x, -y.x), v.x, s);
-      s = fma(fma(ab, x.y, -y.y), v.y, s);
-    }
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const double wr = fma(c, q[r], s) * inv_a;
-    if (lane == 0) {
-      w[r] = wr;
-      pa = fma(q[r], wr, pa);
-    }
+  for (int i = threadIdx.x; i < ld; i += kLzThreads) {
+    const double u = q[i] * inv;
+    q[i] = u;
+    q32[i] = (float)u;
   }
-  pa = block_sum<kLzMvThreads>(pa, sm);
-  if (threadIdx.x == 0) lz->part[blockIdx.x] = pa;
 }
 
-// alpha_j = q_j . w; r = w - alpha_j q_j - beta_j q_{j-1}; beta_{j+1} = ||r||; q_{j+1} = r / beta_{j+1}.
-__global__ void __launch_bounds__(kLzThreads)
-lz_update_kernel(const DevState* st, LzScratch* lz, int j, int nblk) {
+// A 2^-s = ((a + b) X_{k-1} - Y + c I) (2^-s / a), rounded to FP32, over the whole ld x ld
+// buffer (the zero border stays zero; the identity term on the N true diagonal entries).
+__global__ void lz_form_kernel(const DevState* st, const double* buf0, const double* buf1, const double* S,
+                               LzScratch* lz) {
+  if (st->done) return;
+  const int N = st->N, ld = st->ld;
+  const double* Xa;
+  const double* Y;
+  double a, b, c;
+  lz_operands(st, buf0, buf1, S, Xa, Y, a, b, c);
+  const double ab = a + b, f = lz->scale / a;
+  const double2* __restrict__ X2 = reinterpret_cast<const double2*>(Xa);
+  const double2* __restrict__ Y2 = reinterpret_cast<const double2*>(Y);
+  float2* __restrict__ A2 = reinterpret_cast<float2*>(lz_a32(lz, ld));
+  const int h = ld / 2;
+  const int64_t total = (int64_t)ld * h;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / h), c2 = 2 * (int)(e % h);
+    const double2 x = X2[e], y = Y2[e];
+    double d0 = fma(ab, x.x, -y.x), d1 = fma(ab, x.y, -y.y);
+    if (r < N && r == c2) d0 += c;
+    if (r < N && r == c2 + 1) d1 += c;
+    A2[e] = make_float2((float)(d0 * f), (float)(d1 * f));
+  }
+}
+
+// One Lanczos step: w = A q_j (one warp per row, FP32 products, 16-byte loads) and the CTA's
+// share of q_j . w; the last CTA to finish its rows then computes alpha_j = q_j . w,
+// r = w - alpha_j q_j - beta_j q_{j-1}, beta_{j+1} = ||r|| and q_{j+1} = r / beta_{j+1} in FP64.
+__global__ void __launch_bounds__(kLzMvThreads)
+lz_step_kernel(const DevState* st, LzScratch* lz, int j) {
   __shared__ double sm[32];
+  __shared__ int s_last;
   if (st->done || !lz->live) return;
   const int N = st->N, ld = st->ld;
+  const float4* __restrict__ A = reinterpret_cast<const float4*>(lz_a32(lz, ld));
+  const float4* __restrict__ q4 = reinterpret_cast<const float4*>(lz_q32(lz, ld));
   double* qp = lz_vec(lz, ld, 0);
   double* q = lz_vec(lz, ld, 1);
   double* w = lz_vec(lz, ld, 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int h = ld / 4;
+  double pa = 0.0;
+  for (int r = blockIdx.x * (kLzMvThreads / 32) + warp; r < N; r += gridDim.x * (kLzMvThreads / 32)) {
+    const float4* ar = A + (int64_t)r * h;
+    float s0 = 0.f, s1 = 0.f;
+    int i = lane;
+    for (; i + 32 < h; i += 64) {
+      const float4 x0 = ar[i], v0 = q4[i], x1 = ar[i + 32], v1 = q4[i + 32];
+      s0 = fmaf(x0.x, v0.x, s0); s0 = fmaf(x0.y, v0.y, s0); s0 = fmaf(x0.z, v0.z, s0); s0 = fmaf(x0.w, v0.w, s0);
+      s1 = fmaf(x1.x, v1.x, s1); s1 = fmaf(x1.y, v1.y, s1); s1 = fmaf(x1.z, v1.z, s1); s1 = fmaf(x1.w, v1.w, s1);
+    }
+    if (i < h) {
+      const float4 x0 = ar[i], v0 = q4[i];
+      s0 = fmaf(x0.x, v0.x, s0); s0 = fmaf(x0.y, v0.y, s0); s0 = fmaf(x0.z, v0.z, s0); s0 = fmaf(x0.w, v0.w, s0);
+    }
+    double s = (double)s0 + (double)s1;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      w[r] = s;
+      pa = fma(q[r], s, pa);
+    }
+  }
+  if (lane == 0) __threadfence();                // this warp's w rows, before the ticket
+  pa = block_sum<kLzMvThreads>(pa, sm);
+  if (threadIdx.x == 0) {
+    lz->part[blockIdx.x] = pa;
+    __threadfence();
+    s_last = atomicAdd(&lz->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+
+  // the last CTA: every row of w and every partial is written
   double a = 0.0;
-  for (int t = threadIdx.x; t < nblk; t += kLzThreads) a += lz->part[t];
-  a = block_sum<kLzThreads>(a, sm);
+  for (int t = threadIdx.x; t < (int)gridDim.x; t += kLzMvThreads) a += __ldcg(&lz->part[t]);
+  a = block_sum<kLzMvThreads>(a, sm);
   const double bj = lz->beta[j];
   double ss = 0.0;
-  for (int i = threadIdx.x; i < N; i += kLzThreads) {
-    const double r = w[i] - a * q[i] - bj * qp[i];
+  for (int i = threadIdx.x; i < N; i += kLzMvThreads) {
+    const double r = __ldcg(&w[i]) - a * q[i] - bj * qp[i];
     w[i] = r;
     ss = fma(r, r, ss);
   }
-  ss = block_sum<kLzThreads>(ss, sm);
+  ss = block_sum<kLzMvThreads>(ss, sm);
   const double b = sqrt(ss);
   const bool finite = isfinite(a) && isfinite(b);
+  const bool more = j + 1 < kLzSteps && finite && b > 1e-300;
   if (threadIdx.x == 0) {
     lz->alpha[j] = finite ? a : __longlong_as_double(0x7ff8000000000000ll);
     lz->m = j + 1;
     if (j + 1 < kLzSteps) lz->beta[j + 1] = b;
-    if (!finite || !(b > 1e-300)) lz->live = 0;
+    if (!more) lz->live = 0;
+    lz->ticket = 0;
   }
-  if (j + 1 == kLzSteps || !finite || !(b > 1e-300)) return;
+  if (!more) return;
   const double ib = 1.0 / b;
-  for (int i = threadIdx.x; i < N; i += kLzThreads) {
+  float* q32 = lz_q32(lz, ld);
+  for (int i = threadIdx.x; i < N; i += kLzMvThreads) {
+    const double u = w[i] * ib;
     qp[i] = q[i];
-    q[i] = w[i] * ib;
+    q[i] = u;
+    q32[i] = (float)u;
   }
 }
 
 // Number of eigenvalues of the m x m tridiagonal (alpha, beta) below x: the count of negative
 // pivots of the LDL^T factorisation of T - x I (Sturm sequence), tiny pivots pushed to -pivmin.
-__device__ __forceinline__ int sturm_count(const double* al, const double* be, int m, double x) {
-  constexpr double kPivMin = 1e-300;
-  double d = al[0] - x;
-  if (fabs(d) < kPivMin) d = -kPivMin;
-  int cnt = d < 0.0;
+__device__ __forceinline__ int sturm_count(const float* al, const float* be2, int m, float x) {
+  constexpr float kPivMin = 1e-30f;
+  float d = al[0] - x;
+  if (fabsf(d) < kPivMin) d = -kPivMin;
+  int cnt = d < 0.0f;
   for (int i = 1; i < m; ++i) {
-    d = (al[i] - x) - be[i] * be[i] / d;
-    if (fabs(d) < kPivMin) d = -kPivMin;
-    cnt += d < 0.0;
+    d = (al[i] - x) - be2[i] / d;
+    if (fabsf(d) < kPivMin) d = -kPivMin;
+    cnt += d < 0.0f;
   }
   return cnt;
 }
 
 __global__ void __launch_bounds__(32)
 lz_eig_kernel(DevState* st, const LzScratch* lz) {
-  __shared__ double al[kLzSteps], be[kLzSteps];
+  __shared__ float al[kLzSteps], be2[kLzSteps];
   if (st->done) return;
   const int lane = threadIdx.x;
   const int m = lz->m;
-  if (lane < m) {
-    al[lane] = lz->alpha[lane];
-    be[lane] = lane ? lz->beta[lane] : 0.0;
-  }
-  __syncwarp();
-  double lo = INFINITY, hi = -INFINITY;
   bool bad = m < 1;
-  for (int i = 0; i < m; ++i) {                  // Gershgorin interval of T
-    const double rad = fabs(be[i]) + (i + 1 < m ? fabs(be[i + 1]) : 0.0);
-    lo = fmin(lo, al[i] - rad);
-    hi = fmax(hi, al[i] + rad);
-    bad = bad || !isfinite(al[i]) || !isfinite(be[i]);
+  if (lane < m) {
+    const double a = lz->alpha[lane], b = lane ? lz->beta[lane] : 0.0;
+    bad = bad || !isfinite(a) || !isfinite(b) || fabs(a) > 1e30 || fabs(b) > 1e15;
+    al[lane] = (float)a;
+    be2[lane] = (float)(b * b);
   }
+  bad = __any_sync(0xffffffffu, bad);
+  __syncwarp();
   if (bad) {
     if (lane == 0) st->spec_e = __longlong_as_double(0x7ff8000000000000ll);
     return;
   }
-  const double pad = 1e-300 + 0x1p-50 * fmax(fabs(lo), fabs(hi));
+  float lo = INFINITY, hi = -INFINITY;
+  for (int i = 0; i < m; ++i) {                  // Gershgorin interval of T
+    const float rad = sqrtf(be2[i]) + (i + 1 < m ? sqrtf(be2[i + 1]) : 0.0f);
+    lo = fminf(lo, al[i] - rad);
+    hi = fmaxf(hi, al[i] + rad);
+  }
+  const float pad = 1e-30f + 0x1p-20f * fmaxf(fabsf(lo), fabsf(hi));
   lo -= pad;
   hi += pad;
-  double lo1 = lo, hi1 = hi, lo2 = lo, hi2 = hi;  // brackets of the largest and the smallest
+  float lo1 = lo, hi1 = hi, lo2 = lo, hi2 = hi;  // brackets of the largest and the smallest
   for (int round = 0; round < kSturmRounds; ++round) {
-    const double f = (double)(lane + 1) / 33.0;
-    const double x1 = lo1 + (hi1 - lo1) * f;
-    const double x2 = lo2 + (hi2 - lo2) * f;
+    const float f = (float)(lane + 1) / 33.0f;
+    const float x1 = lo1 + (hi1 - lo1) * f;
+    const float x2 = lo2 + (hi2 - lo2) * f;
     // largest: the points with fewer than m eigenvalues below them form a prefix
-    const int L = __popc(__ballot_sync(0xffffffffu, sturm_count(al, be, m, x1) <= m - 1));
+    const int L = __popc(__ballot_sync(0xffffffffu, sturm_count(al, be2, m, x1) <= m - 1));
     // smallest: the points with no eigenvalue below them form a prefix
-    const int S = __popc(__ballot_sync(0xffffffffu, sturm_count(al, be, m, x2) == 0));
-    const double xl1 = __shfl_sync(0xffffffffu, x1, L > 0 ? L - 1 : 0);
-    const double xh1 = __shfl_sync(0xffffffffu, x1, L < 32 ? L : 31);
-    const double xl2 = __shfl_sync(0xffffffffu, x2, S > 0 ? S - 1 : 0);
-    const double xh2 = __shfl_sync(0xffffffffu, x2, S < 32 ? S : 31);
+    const int S = __popc(__ballot_sync(0xffffffffu, sturm_count(al, be2, m, x2) == 0));
+    const float xl1 = __shfl_sync(0xffffffffu, x1, L > 0 ? L - 1 : 0);
+    const float xh1 = __shfl_sync(0xffffffffu, x1, L < 32 ? L : 31);
+    const float xl2 = __shfl_sync(0xffffffffu, x2, S > 0 ? S - 1 : 0);
+    const float xh2 = __shfl_sync(0xffffffffu, x2, S < 32 ? S : 31);
     if (L > 0) lo1 = xl1;
     if (L < 32) hi1 = xh1;
     if (S > 0) lo2 = xl2;
     if (S < 32) hi2 = xh2;
   }
-  if (lane == 0) st->spec_e = fmax(fabs(0.5 * (lo1 + hi1)), fabs(0.5 * (lo2 + hi2)));
+  if (lane == 0) {
+    const double top = 0.5 * ((double)lo1 + (double)hi1), bot = 0.5 * ((double)lo2 + (double)hi2);
+    st->spec_e = fmax(fabs(top), fabs(bot)) / lz->scale;
+  }
 }
 
-int matvec_blocks(int N) {
+int step_blocks(int N) {
   const int b = (N + kLzMvThreads / 32 - 1) / (kLzMvThreads / 32);
   return b < kLzMvBlocks ? (b < 1 ? 1 : b) : kLzMvBlocks;
 }
 
+int form_blocks(int ld) {
+  const int64_t b = ((int64_t)ld * (ld / 2) + 255) / 256;
+  return (int)(b < 152 * 16 ? b : 152 * 16);
+}
+
 }  // namespace
 
-size_t lanczos_scratch_bytes(int ld) { return kVecOff + 3 * sizeof(double) * (size_t)ld; }
+size_t lanczos_scratch_bytes(int ld) {
+  return kVecOff + 3 * sizeof(double) * (size_t)ld + sizeof(float) * ((size_t)ld + (size_t)ld * ld);
+}
 
 cudaError_t add_lanczos_nodes(cudaGraph_t g, cudaGraphNode_t dep, DevState* st, const double* buf0,
-                              const double* buf1, const double* S, void* scratch, int N, cudaGraphNode_t* last) {
+                              const double* buf1, const double* S, const double* part, int ntiles, void* scratch,
+                              int N, int ld, cudaGraphNode_t* last) {
   LzScratch* lz = static_cast<LzScratch*>(scratch);
   const DevState* cst = st;
   cudaKernelNodeParams kp = {};
   cudaGraphNode_t prev = dep, node;
-  void* a0[] = {&cst, &buf0, &buf1, &S, &lz};
+  void* a0[] = {&cst, &part, &ntiles, &lz};
   kp.func = (void*)lz_start_kernel;
   kp.gridDim = dim3(1);
   kp.blockDim = dim3(kLzThreads);
@@ -259,20 +330,19 @@ cudaError_t add_lanczos_nodes(cudaGraph_t g, cudaGraphNode_t dep, DevState* st, 
   cudaError_t e = cudaGraphAddKernelNode(&node, g, &prev, 1, &kp);
   if (e != cudaSuccess) return e;
   prev = node;
-  int nblk = matvec_blocks(N);
+  void* a1[] = {&cst, &buf0, &buf1, &S, &lz};
+  kp.func = (void*)lz_form_kernel;
+  kp.gridDim = dim3(form_blocks(ld));
+  kp.blockDim = dim3(256);
+  kp.kernelParams = a1;
+  if ((e = cudaGraphAddKernelNode(&node, g, &prev, 1, &kp)) != cudaSuccess) return e;
+  prev = node;
   for (int j = 0; j < kLzSteps; ++j) {
-    void* a1[] = {&cst, &lz};
-    kp.func = (void*)lz_matvec_kernel;
-    kp.gridDim = dim3(nblk);
-    kp.blockDim = dim3(kLzMvThreads);
-    kp.kernelParams = a1;
-    if ((e = cudaGraphAddKernelNode(&node, g, &prev, 1, &kp)) != cudaSuccess) return e;
-    prev = node;
     int jj = j;
-    void* a2[] = {&cst, &lz, &jj, &nblk};
-    kp.func = (void*)lz_update_kernel;
-    kp.gridDim = dim3(1);
-    kp.blockDim = dim3(kLzThreads);
+    void* a2[] = {&cst, &lz, &jj};
+    kp.func = (void*)lz_step_kernel;
+    kp.gridDim = dim3(step_blocks(N));
+    kp.blockDim = dim3(kLzMvThreads);
     kp.kernelParams = a2;
     if ((e = cudaGraphAddKernelNode(&node, g, &prev, 1, &kp)) != cudaSuccess) return e;
     prev = node;
@@ -288,15 +358,12 @@ cudaError_t add_lanczos_nodes(cudaGraph_t g, cudaGraphNode_t dep, DevState* st, 
   return e;
 }
 
-cudaError_t launch_lanczos(DevState* st, const double* buf0, const double* buf1, const double* S, void* scratch,
-                           int N, cudaStream_t s) {
+cudaError_t launch_lanczos(DevState* st, const double* buf0, const double* buf1, const double* S,
+                           const double* part, int ntiles, void* scratch, int N, int ld, cudaStream_t s) {
   LzScratch* lz = static_cast<LzScratch*>(scratch);
-  const int nblk = matvec_blocks(N);
-  lz_start_kernel<<<1, kLzThreads, 0, s>>>(st, buf0, buf1, S, lz);
-  for (int j = 0; j < kLzSteps; ++j) {
-    lz_matvec_kernel<<<nblk, kLzMvThreads, 0, s>>>(st, lz);
-    lz_update_kernel<<<1, kLzThreads, 0, s>>>(st, lz, j, nblk);
-  }
+  lz_start_kernel<<<1, kLzThreads, 0, s>>>(st, part, ntiles, lz);
+  lz_form_kernel<<<form_blocks(ld), 256, 0, s>>>(st, buf0, buf1, S, lz);
+  for (int j = 0; j < kLzSteps; ++j) lz_step_kernel<<<step_blocks(N), kLzMvThreads, 0, s>>>(st, lz, j);
   lz_eig_kernel<<<1, 32, 0, s>>>(st, lz);
   return cudaGetLastError();
 }
