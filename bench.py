@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--mcweeny", choices=["mcw", "mcw-acc"], default=None,
                     help="FP64 path: the McWeeny expansion (mcw) or McW-ACC with the construction's gap as the "
                          "gap estimate, mu = 0 (the construction splits the spectrum at 0)")
+    ap.add_argument("--norm", choices=["fro", "mixed", "spectral"], default="fro",
+                    help="error measure of the stop: Frobenius v_i, mixed norm m_i, or the spectral e_i "
+                         "(Lanczos; --precision fp64 only)")
     ap.add_argument("--rule", choices=["error", "block"], default="error",
                     help="block-sparse truncation rule of the headline line (both rules are reported)")
     ap.add_argument("--N", type=int, default=N_DEFAULT)
@@ -418,7 +421,9 @@ def main():
     D_exact = case.D_exact
     D = torch.empty_like(F)
     stream = torch.cuda.current_stream()
-    P = sp2.Purifier(N, nocc, a.precision, refine_fp64={"tc": 0, "fp64": 1, "mcweeny": 2}[a.refine])
+    if a.norm == "spectral" and a.precision != "fp64":
+        raise SystemExit("--norm spectral needs --precision fp64")
+    P = sp2.Purifier(N, nocc, a.precision, refine_fp64={"tc": 0, "fp64": 1, "mcweeny": 2}[a.refine], norm=a.norm)
     if a.mcweeny is not None:
         if a.precision != "fp64":
             raise SystemExit("--mcweeny needs --precision fp64")
@@ -467,7 +472,10 @@ def main():
     n_iter = info["n_iter"]
     flops = useful_flops(N, squares, n_iter, mixed, 2 if mixed else 0) if mixed else N * N * (N + 1) * squares
     tflops = flops / (ms * 1e-3) / 1e12
-    launches_per_step = (3 + 2 * squares + 1) if not mixed else (3 + 2 * squares + 2 + 2 * n_iter + 3 + 1)
+    # FP64 path per square: square (+ McWeeny product) + finalize (+ 35 Lanczos launches for the
+    # spectral stop); bounds, init, scaling and the output copy once
+    per_square = 2 + (1 if a.mcweeny else 0) + (35 if a.norm == "spectral" else 0)
+    launches_per_step = (3 + per_square * squares + 1) if not mixed else (3 + 2 * squares + 2 + 2 * n_iter + 3 + 1)
 
     # roofline of the dominant kernel, timed on its own inside the same device loop:
     # a forward-only handle runs the square + stop-test loop; loop time / squares is
@@ -593,7 +601,7 @@ def main():
                 "config": {"workload": workload_name(N, nocc, a.gap) if a.input == "qr" else
                            f"dense N={N} nocc={nocc} gap={a.gap:g}, Q = 64 Householder reflectors (seed 3)",
                            "N": N, "nocc": nocc, "gap": a.gap,
-                           "precision": a.precision, "refine": a.refine if mixed else None,
+                           "precision": a.precision, "refine": a.refine if mixed else None, "norm": a.norm,
                            "expansion": ("SP2-ACC (homo/lumo bounds, slack %g)" % a.acc if a.acc is not None
                                          else {"mcw": "McWeeny (mu = 0)", "mcw-acc": "McW-ACC (mu = 0, xi = gap)"}
                                          [a.mcweeny] if a.mcweeny else "SP2 (trace-based)"),
