@@ -167,3 +167,58 @@ def test_bsr_launch_modes_agree_and_errors(sp2mod):
     with sp2mod.BsrPurifier(tb.N, tb.nocc, 1e-5) as P:
         D = P.run(rp, ci, bad)
         assert P.info()["status"] == 3 and bool(torch.isnan(D).all())
+
+
+def test_bsr_full_size_32cubed_a_posteriori(sp2mod):
+    """The 32^3 lattice (N = 32768) in the benchmark's configuration (error-controlled rule,
+    tau = 1e-4, graph launch).  No oracle runs at this size, so the test checks what holds at any
+    size and bounds the distance to the exact projector P from it: with P~ the projector onto
+    the eigenvectors of D above 1/2, ||D - P~||_F <= ||D^2 - D||_F / (1 - 2 m) (m the largest
+    distance of an eigenvalue of D from {0, 1}) and, by the sin-theta theorem with the gap delta
+    of F, ||P~ - P||_F <= ||[F, P~]||_F / delta <= (||[F, D]||_F + 2 ||F||_2 ||D - P~||_F) / delta."""
+    import math
+    tb = inputs.tight_binding(L=32)
+    rp, ci, vals = tb.bsr(32)
+    rp_d, ci_d, vals_d = (torch.from_numpy(x).cuda() for x in (rp, ci, vals))
+    with sp2mod.BsrPurifier(tb.N, tb.nocc, 1e-4, rule="error") as P:
+        D = P.run(rp_d, ci_d, vals_d)
+        info = P.info()
+    assert info["status"] == 0 and info["stop_reason"] in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
+    assert torch.equal(D, D.T)
+    nocc = tb.nocc
+    tr = float(torch.trace(D))
+    # F D from the sparse F in FP64 (onsite diagonal, hopping -t to the six neighbours)
+    r = torch.from_numpy(tb.rows).cuda()
+    c = torch.from_numpy(tb.cols).cuda()
+    idx = torch.cat([torch.stack([r, c]), torch.arange(tb.N, device="cuda").repeat(2, 1)], dim=1)
+    val = torch.cat([torch.full((r.numel(),), -tb.hop, dtype=torch.float64, device="cuda"),
+                     torch.from_numpy(tb.onsite).cuda()])
+    Fs = torch.sparse_coo_tensor(idx, val, (tb.N, tb.N)).coalesce()
+    FD = torch.sparse.mm(Fs, D)
+    comm = float(torch.linalg.norm(FD - FD.T))            # [F, D] = F D - (F D)^T for symmetric F, D
+    del FD
+    # D^2 - D with FP32 products (no TF32): error ~1e-7 of ||D||_F^2 / sqrt(N), far below the FP32 floor of D
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    D32 = D.float()
+    idem = float(torch.linalg.norm((D32 @ D32).double() - D))
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    del D32
+    # the gap: without disorder the bands are +-sqrt(Delta^2 + eps_k^2) (bipartite lattice), so
+    # |lambda| >= Delta = 1; the onsite disorder moves every eigenvalue by at most its largest
+    # magnitude (Weyl), so the gap around 0 is at least 2 (Delta - max |noise|)
+    onsite = tb.onsite
+    delta_gap = 2.0 * (1.0 - float(np.max(np.abs(np.abs(onsite) - 1.0))))
+    Fnorm = float(np.max(np.abs(onsite))) + 6 * tb.hop     # Gershgorin
+    m = 0.01                                               # eigenvalues of D within 0.01 of {0, 1}:
+    assert idem < m / 2                                    # |d - d^2| >= m (1 - m) > m / 2 otherwise
+    d_ptilde = idem / (1 - 2 * m)
+    bound = d_ptilde + (comm + 2 * Fnorm * d_ptilde) / delta_gap
+    print(f"trace err {tr - nocc:.3e} idem {idem:.3e} comm {comm:.3e} gap {delta_gap:.3f} "
+          f"bound/sqrt(nocc) {bound / math.sqrt(nocc):.3e} n {info['n_iter']} kept {info['nnzb']}")
+    assert abs(tr - nocc) < 0.5                            # P~ has rank nocc
+    # budget: n truncations of ||E_i||_F <= tau, each moving the subspace by at most
+    # tau (1 + 2 ||F|| / delta) / delta to first order: 15 * 1e-4 * 3.7 / 1.6 / 128 ~ 3e-5 per
+    # sqrt(nocc), plus the FP32 floor of the stored blocks (measured bound: 8e-6)
+    budget = info["n_iter"] * 1e-4 * (1 + 2 * Fnorm / delta_gap) / delta_gap / math.sqrt(nocc)
+    assert bound / math.sqrt(nocc) <= budget + 1e-5

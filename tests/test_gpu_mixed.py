@@ -187,3 +187,17 @@ def test_mixed_full_size_n8192(sp2mod):
     assert float(torch.linalg.norm(DD - D)) / math.sqrt(case.nocc) < 1e-5
     FD = case.F @ D
     assert float(torch.linalg.norm(FD - FD.T)) / math.sqrt(case.nocc) < 1e-5
+
+
+def test_mixed_full_size_n32768_householder(sp2mod):
+    # the dense N = 32768 workload (Q from 64 Householder reflectors, gap 1e-3, kappa ~ 2e3) with
+    # the FP64-square McWeeny refinement, against the exact projector the construction fixes
+    case = inputs.householder_n32768(device="cuda")
+    with sp2mod.Purifier(32768, 16384, "mixed", refine_fp64=2) as P:
+        D = P.run(case.F)
+        info = P.info()
+    assert info["status"] == 0
+    assert info["stop_reason"] in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
+    err = float(torch.linalg.norm(D - case.D_exact)) / math.sqrt(case.nocc)
+    assert err <= TOL_MIXED
+    assert torch.equal(D, D.T)
