@@ -25,9 +25,20 @@ on the summation order and host and device take the same decision bit for bit; t
 quantisation moves the budget by at most 2^-40 of tau^2 per dropped block.  tau = 0
 drops nothing.
 
+Third rule, mixed-norm truncation (`keep_mask_mixed`; §6 removes small elements with
+the mixed norm of the removed part bounded, citing its selection algorithm): the
+off-diagonal blocks are ordered by (||X_IJ||_F^2, I, J) as above, and the longest prefix
+is dropped in which every block row of the removed part's matrix of block norms,
+M_E[I, J] = ||E_IJ||_F (both triangles), sums to at most tau.  The spectral norm of a
+nonnegative symmetric matrix is at most its largest row sum, so ||E||_2 <= ||E||_M =
+||M_E||_2 <= tau.  Reading: the row sums are taken in exact integer units of 2^(e - 40),
+2^e <= tau < 2^(e+1), each ||X_IJ||_F (the correctly rounded square root of the FP64
+||X_IJ||_F^2) rounded down to a unit and the budget tau rounded down, so host and device
+take the same decision bit for bit; blocks with ||X_IJ||_F > tau are never dropped.
+
 `sp2_bsr` runs Alg. 3 on dense FP64 matrices with the blocks masked after every
-step; `keep_mask`, `keep_mask_error` and `square_pattern` are the index work on
-their own.
+step; `keep_mask`, `keep_mask_error`, `keep_mask_mixed` and `square_pattern` are the
+index work on their own.
 """
 from __future__ import annotations
 
@@ -90,6 +101,38 @@ def keep_mask_error(X: np.ndarray, b: int, tau: float) -> np.ndarray:
     return keep
 
 
+def mixed_units(tau: float) -> tuple[int, int]:
+    """(e, budget): 2^e <= tau < 2^(e+1) and the budget floor(tau / 2^(e-40))."""
+    _, ex = math.frexp(tau)
+    e = ex - 1
+    return e, int(math.floor(math.ldexp(tau, 40 - e)))
+
+
+def keep_mask_mixed(X: np.ndarray, b: int, tau: float) -> np.ndarray:
+    """Blocks kept by the mixed-norm truncation (module docstring): in (||X_IJ||^2, I, J) order
+    over the off-diagonal upper blocks with ||X_IJ|| <= tau, drop blocks while both block rows
+    they touch stay within the budget of units; the first block that does not fit ends the
+    prefix."""
+    n2 = block_norms2(X, b)
+    nb = n2.shape[0]
+    keep = np.ones((nb, nb), dtype=bool)
+    if tau == 0.0:
+        return keep
+    e, budget = mixed_units(tau)
+    cands = [(float(n2[I, J]), I, J) for I in range(nb) for J in range(I + 1, nb)
+             if math.sqrt(float(n2[I, J])) <= tau]
+    cands.sort()
+    rows = [0] * nb
+    for v, I, J in cands:
+        u = int(math.floor(math.ldexp(math.sqrt(v), 40 - e)))
+        if rows[I] + u > budget or rows[J] + u > budget:
+            break
+        rows[I] += u
+        rows[J] += u
+        keep[I, J] = keep[J, I] = False
+    return keep
+
+
 def apply_mask(X: np.ndarray, keep: np.ndarray, b: int) -> np.ndarray:
     return X * np.kron(keep, np.ones((b, b)))
 
@@ -102,14 +145,16 @@ def square_pattern(keep: np.ndarray) -> np.ndarray:
 
 
 def sp2_bsr(F: np.ndarray, nocc: int, b: int, tau: float, *, bounds=None, max_iter: int = 200,
-            guard: bool = True, rule: str = "block"):
+            guard: bool = True, rule: str = "block", norm: str = "fro"):
     """Alg. 3 with X~_i = X_i + E_i, E_i the block truncation above (FP64 values);
-    rule "block" (drop blocks with norm below tau) or "error" (||E_i||_F <= tau)."""
-    mask = keep_mask if rule == "block" else keep_mask_error
+    rule "block" (drop blocks with norm below tau), "error" (||E_i||_F <= tau) or "mixed"
+    (||E_i||_M <= tau through the row sums); norm "fro" (v_i) or "mixed" (m_i with the
+    b x b blocks, the pairing of the §6 calculations)."""
+    mask = {"block": keep_mask, "error": keep_mask_error, "mixed": keep_mask_mixed}[rule]
 
     def perturb(i, X):
         return apply_mask(X, mask(X, b, tau), b) - X
-    return o.sp2(F, nocc, bounds=bounds, max_iter=max_iter, guard=guard, perturb=perturb)
+    return o.sp2(F, nocc, bounds=bounds, max_iter=max_iter, guard=guard, perturb=perturb, norm=norm, block=b)
 
 
 def gershgorin_bounds_blocks(F: np.ndarray) -> tuple[float, float]:

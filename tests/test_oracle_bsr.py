@@ -152,3 +152,82 @@ def test_bsr_oracle_error_rule_runs_and_bounds_each_step():
     assert res.stop_reason in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
     ref = o.sp2(F, tb.nocc)
     assert o.rel_error(res.D, ref.D, tb.nocc) < 1e-3
+
+
+# ---- mixed-norm truncation (||E||_M <= tau through the block-row sums) ----------------------
+
+def _mixed_norm_of_removed(X, keep, b):
+    # library block norms and library spectral norm, independent of the rule's unit sums
+    nb = X.shape[0] // b
+    E = X - bo.apply_mask(X, keep, b)
+    M = np.array([[np.linalg.norm(E[I*b:(I+1)*b, J*b:(J+1)*b]) for J in range(nb)] for I in range(nb)])
+    return E, M
+
+
+def test_mixed_truncation_worked_example():
+    # pairs with ||X_IJ|| = 1, 2, 3, 4 (x 2^-20) on (0,1), (0,2), (1,2), (2,3); tau = 4.5 x 2^-20.
+    # In order: the zero blocks (0,3), (1,3); then (0,1) (rows 0, 1: 1, 1), (0,2) (rows 0, 2: 3, 2);
+    # (1,2) would bring row 2 to 5 > 4.5 and ends the prefix, so (2,3) stays although row 3 is empty.
+    c = 2.0 ** -20
+    norms2 = {(0, 1): (1 * c) ** 2, (0, 2): (2 * c) ** 2, (1, 2): (3 * c) ** 2, (2, 3): (4 * c) ** 2}
+    X = _blocks_with_norms(4, 32, norms2)
+    keep = bo.keep_mask_mixed(X, 32, 4.5 * c)
+    dropped = {(I, J) for I in range(4) for J in range(I + 1, 4) if not keep[I, J]}
+    assert dropped == {(0, 1), (0, 2), (0, 3), (1, 3)}
+    assert np.array_equal(keep, keep.T) and keep.diagonal().all()
+    E, M = _mixed_norm_of_removed(X, keep, 32)
+    assert np.linalg.norm(M, 2) == pytest.approx(np.sqrt(5.0) * c, rel=1e-12)   # [[0,1,2],[1,0,0],[2,0,0]] c
+    # the error rule with this selection's ||E||_F^2 = 2 (1 + 4) c^2 as its budget drops the same
+    # blocks: both walk the same order, here only the budgets differ
+    ke = bo.keep_mask_error(X, 32, np.sqrt(2 * (1 + 4) * c * c))
+    assert np.array_equal(ke, keep)
+
+
+def test_mixed_truncation_bound_and_maximality():
+    g = np.random.Generator(np.random.PCG64(21))
+    nb, b = 10, 32
+    X = g.standard_normal((nb * b, nb * b))
+    X = 0.5 * (X + X.T)
+    scale = np.exp(g.uniform(-12, 0, (nb, nb)))
+    scale = np.minimum(scale, scale.T)
+    X = X * np.kron(scale, np.ones((b, b)))
+    for tau in (1e-3, 1e-1, 3.0, 30.0):
+        keep = bo.keep_mask_mixed(X, b, tau)
+        E, M = _mixed_norm_of_removed(X, keep, b)
+        mn = np.linalg.norm(M, 2)
+        assert mn <= tau * (1 + 1e-9)                                  # ||E||_M <= tau
+        assert np.max(np.abs(np.linalg.eigvalsh(E))) <= mn * (1 + 1e-9)  # ||E||_2 <= ||E||_M
+        assert M.sum(axis=1).max() <= tau * (1 + 1e-9)                 # the row sums the rule bounds
+        # maximal: the first kept candidate in (norm^2, I, J) order overflows one of its rows
+        n2 = np.array([[np.linalg.norm(X[I*b:(I+1)*b, J*b:(J+1)*b]) ** 2 for J in range(nb)] for I in range(nb)])
+        kept = sorted((n2[I, J], I, J) for I in range(nb) for J in range(I + 1, nb)
+                      if keep[I, J] and np.sqrt(n2[I, J]) <= tau)
+        if kept:
+            v, I, J = kept[0]
+            rs = M.sum(axis=1)
+            assert max(rs[I], rs[J]) + np.sqrt(v) > tau * (1 - 1e-9)
+
+
+def test_mixed_truncation_edge_cases():
+    g = np.random.Generator(np.random.PCG64(22))
+    X = g.standard_normal((128, 128))
+    X = 0.5 * (X + X.T)
+    assert bo.keep_mask_mixed(X, 32, 0.0).all()                    # tau = 0: nothing dropped
+    keep = bo.keep_mask_mixed(X, 32, 1e6)                          # every row sum fits
+    assert keep.diagonal().all() and int(keep.sum()) == 4
+    e, budget = bo.mixed_units(0.75)
+    assert 2.0 ** e <= 0.75 < 2.0 ** (e + 1) and budget == int(np.floor(0.75 * 2.0 ** (40 - e)))
+
+
+def test_bsr_oracle_mixed_rule_and_mixed_norm_stop():
+    # the pairing of the §6 calculations: mixed-norm truncation and the mixed-norm stop with the
+    # truncation's blocks
+    tb = inputs.tight_binding(L=4, delta=1.0, t=0.3, sigma=0.05, seed=2, dims=(32, 2, 2))
+    F = tb.dense()
+    res = bo.sp2_bsr(F, tb.nocc, 32, 1e-4, rule="mixed", norm="mixed")
+    assert res.stop_reason in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
+    ref = o.sp2(F, tb.nocc)
+    assert o.rel_error(res.D, ref.D, tb.nocc) < 1e-3
+    fro = bo.sp2_bsr(F, tb.nocc, 32, 1e-4, rule="mixed")
+    for i in range(min(len(res.v), len(fro.v))):                    # m_i <= v_i on the same iterates
+        assert res.v[i] <= fro.v[i] * (1 + 1e-12)
