@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--norm", choices=["fro", "mixed", "spectral"], default="fro",
                     help="error measure of the stop: Frobenius v_i, mixed norm m_i, or the spectral e_i "
                          "(Lanczos; --precision fp64 only)")
-    ap.add_argument("--rule", choices=["error", "block"], default="error",
+    ap.add_argument("--rule", choices=["error", "block", "mixed"], default="error",
                     help="block-sparse truncation rule of the headline line (both rules are reported)")
     ap.add_argument("--N", type=int, default=N_DEFAULT)
     ap.add_argument("--nocc", type=int, default=None)
@@ -312,10 +312,12 @@ def run_batch(a, ws, rank, local):
 
 def bsr_launches(squares, rule):
     """Kernels of one block-sparse run (dense output off): 14 set-up kernels, 12 per loop
-    round (+1 each with the error-controlled rule), rounds launched in pairs by the graph."""
-    extra = 1 if rule == "error" else 0
+    round (+1 each with the error-controlled rule, +3 with the mixed-norm rule, +35 Lanczos
+    launches per round for the mixed-norm stop that goes with it), rounds launched in pairs."""
+    extra = {"error": 1, "mixed": 3}.get(rule, 0)
+    lz = 35 if rule == "mixed" else 0
     rounds = squares + (squares & 1)
-    return 14 + extra + (12 + extra) * rounds
+    return 14 + extra + (12 + extra + lz) * rounds
 
 
 def run_bsr(a, ws, rank, local):
@@ -328,9 +330,10 @@ def run_bsr(a, ws, rank, local):
     rp_d, ci_d, vals_d = (torch.from_numpy(x).cuda() for x in (rp, ci, vals))
     stream = torch.cuda.current_stream()
     out = {}
-    rules = [a.rule] + [r for r in ("error", "block") if r != a.rule]
+    rules = [a.rule] + [r for r in ("error", "block", "mixed") if r != a.rule]
     for rule, tau in [(r, t) for r in rules for t in (1e-4, 1e-6)]:
-        with sp2.BsrPurifier(tb.N, tb.nocc, tau, rule=rule) as P:
+        # the mixed-norm rule runs with the mixed-norm stop (the pairing of the paper's §6)
+        with sp2.BsrPurifier(tb.N, tb.nocc, tau, rule=rule, norm="mixed" if rule == "mixed" else "fro") as P:
             for _ in range(a.warmup):
                 P.run(rp_d, ci_d, vals_d, dense=False, stream=stream)
             torch.cuda.synchronize()
@@ -353,13 +356,15 @@ def run_bsr(a, ws, rank, local):
                                "ms_per_square": info["loop_ms"] / max(1, info["hist_len"])}
     # roofline of the numeric block square (the dominant kernel): a launch-mode-1 handle
     # records CUDA events around each of its launches; work from the device's counters
-    with sp2.BsrPurifier(tb.N, tb.nocc, 1e-4, rule=a.rule, launch_mode=1) as P1:
+    with sp2.BsrPurifier(tb.N, tb.nocc, 1e-4, rule=a.rule, launch_mode=1,
+                         norm="mixed" if a.rule == "mixed" else "fro") as P1:
         P1.run(rp_d, ci_d, vals_d, dense=False, stream=stream)
         P1.run(rp_d, ci_d, vals_d, dense=False, stream=stream)
         w = P1.info()
     clk = ClockSampler(local)
     clk.start()
-    with sp2.BsrPurifier(tb.N, tb.nocc, 1e-4, rule=a.rule, launch_mode=1) as P1:
+    with sp2.BsrPurifier(tb.N, tb.nocc, 1e-4, rule=a.rule, launch_mode=1,
+                         norm="mixed" if a.rule == "mixed" else "fro") as P1:
         P1.run(rp_d, ci_d, vals_d, dense=False, stream=stream)
         w = P1.info()
     clocks = clk.stop()
@@ -389,7 +394,9 @@ def run_bsr(a, ws, rank, local):
                                    "sigma=0.05 (seed 2), nocc=N/2, 32x32 blocks (x-lines)",
                        "nnzb_F": int(rp[-1]), "tau": 1e-4,
                        "truncation": {"error": "error-controlled, ||E_i||_F <= tau",
-                                      "block": "per block, ||X_IJ||_F < tau dropped"}[a.rule]},
+                                      "block": "per block, ||X_IJ||_F < tau dropped",
+                                      "mixed": "mixed norm, ||E_i||_M <= tau (block-row sums), "
+                                               "with the mixed-norm stop"}[a.rule]},
             "runs": out, "roofline": roofline,
             "gpu_launches": a.steps * bsr_launches(out[f"{a.rule}:tau=0.0001"]["squares"], a.rule)}), flush=True)
 

@@ -249,21 +249,31 @@ typedef struct sp2_bsr_ctx* sp2_bsr;
  * removal of small matrix parts in its numerical sections but fixes no block rule). */
 typedef enum {
   SP2_TRUNC_BLOCK = 0,  /* drop each off-diagonal block with ||X_IJ||_F < tau */
-  SP2_TRUNC_ERROR = 1   /* error-controlled, ||E_i||_F <= tau: over the off-diagonal blocks in
+  SP2_TRUNC_ERROR = 1,  /* error-controlled, ||E_i||_F <= tau: over the off-diagonal blocks in
                            (||X_IJ||_F^2, I, J) order, drop the longest prefix whose norms,
                            counted twice (a symmetric pair goes together), add up to at most
                            tau^2; the sums are exact integer multiples of 2^(e-40) with
                            2^e <= tau^2 < 2^(e+1) (each 2 ||X_IJ||_F^2 and tau^2 rounded down to
                            a multiple), so the selection does not depend on summation order */
+  SP2_TRUNC_MIXED = 2   /* mixed norm, ||E_i||_2 <= ||E_i||_M <= tau (§6 removes small elements
+                           with the mixed norm of the removed part bounded): in the same order,
+                           drop the longest prefix in which every block row of the matrix of
+                           dropped block norms ||E_IJ||_F sums to at most tau (the spectral
+                           norm of that nonnegative symmetric matrix is at most its largest row
+                           sum); sums in exact integer multiples of 2^(e-40), 2^e <= tau <
+                           2^(e+1), each ||X_IJ||_F and tau rounded down to a multiple */
 } sp2_trunc_rule;
 
 /* N: a multiple of 32, at most 65536.  tau >= 0 (0 keeps every stored block).  opts as
- * for sp2_create (corrections, refine_steps and refine_fp64 are ignored).  Workspace is
+ * for sp2_create (corrections, refine_steps and refine_fp64 are ignored); opts.norm 0 (v_i)
+ * or 1 (the mixed norm m_i with the 32 x 32 blocks, estimated after every square by 32
+ * Lanczos steps on the (N/32) x (N/32) matrix of block norms of X - X^2, the pairing of the
+ * paper's §6 calculations with SP2_TRUNC_MIXED); 2 is SP2_ERR_UNSUPPORTED.  Workspace is
  * about 10 KB per block of (N/32)^2, i.e. ~11 GB at N = 32768.  Rule SP2_TRUNC_BLOCK. */
 sp2_status sp2_create_bsr(int64_t N, int64_t n_occ, double tau, const sp2_opts* opts, sp2_bsr* out);
 
 /* As sp2_create_bsr with the truncation rule `rule` (an sp2_trunc_rule; anything else is
- * SP2_ERR_INVALID_ARG). */
+ * SP2_ERR_INVALID_ARG).  With SP2_TRUNC_MIXED, tau bounds ||E_i||_M (not ||E_i||_F). */
 sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, int32_t rule, const sp2_opts* opts,
                              sp2_bsr* out);
 

@@ -11,18 +11,23 @@
 //      the K both rows hold (increasing K), X_IJ <- S_IJ or 2 X_IJ - S_IJ (Alg. 3),
 //      the FP64 partials of ||X~_{k-1} - S||_F^2 and Tr[X_k], and ||X_IJ||_F^2 of the
 //      new block in a fixed order (row sums left to right, rows top to bottom);
-//   3. stop test on the device (Alg. 3, with the trace guard);
+//   3. stop test on the device (Alg. 3, with the trace guard) on v_{k-1}, or on the mixed
+//      norm m_{k-1} with the 32 x 32 blocks (§2; the spectral norm of the matrix of block
+//      norms of X~ - X~^2, by the Lanczos kernels);
 //   4. truncation: off-diagonal blocks with ||X_IJ||_F^2 < tau^2 are dropped (rule 0),
 //      or the longest prefix in (||X_IJ||_F^2, I, J) order whose doubled norms add up to
 //      at most tau^2 (rule 1, error-controlled: ||E||_F <= tau, sums in exact integer
-//      units); the kept bitmap is set for (I, J) and (J, I), and X~_k is written as BSR
-//      (each kept upper block and its transpose at the rank of its column in its row).
+//      units), or the longest prefix in that order in which every block row's sum of
+//      dropped block norms stays within tau (rule 2, mixed norm: ||E||_M <= tau, §6);
+//      the kept bitmap is set for (I, J) and (J, I), and X~_k is written as BSR (each
+//      kept upper block and its transpose at the rank of its column in its row).
 //
 // All index work is integer and fixed-order, so the pattern of every iterate is
 // reproducible bit for bit (and equals the host's, given the same stored blocks).
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <new>
 
@@ -590,6 +595,166 @@ bsr_errctl_kernel(const DevState* st, const double* n2, const int* row, const in
   }
 }
 
+// ---- mixed-norm truncation (rule 2) ------------------------------------------------------
+// Candidates are the off-diagonal pairs with ||X_IJ||_F = sqrt(n2) <= tau, weighing
+// u_q = floor(||X_IJ||_F / 2^(e-40)) units (2^e <= tau < 2^(e+1)); every block row may take
+// floor(tau / 2^(e-40)) units, and dropping pair q = (I, J) adds u_q to rows I and J.  Dropped:
+// the longest prefix of the key order (n2 bits, q) in which every row stays within the budget.
+// Walking that order, the first candidate that does not fit is the earliest of the rows' own
+// first overflows: restricted to the candidates touching row r the global order is r's own
+// sorted order, and r's sum at a candidate counts exactly r's earlier candidates.  So one CTA
+// per row sorts the row's candidates by key, scans their units and reports the key at which
+// its sum first exceeds the budget; the cut is the smallest reported key and every candidate
+// below it is dropped: the decision of the sequential walk, without a global sort.
+constexpr int kMR = 256;                 // threads of the per-row kernel
+constexpr int kMRMax = MAX_NB;           // candidates of one row: fewer than nb <= MAX_NB
+
+__device__ __forceinline__ void mr_push(double v, int q, double tau, int e, unsigned long long* kb, int* kq,
+                                        unsigned long long* ku, int* n) {
+  const double w = sqrt(v);
+  if (!(w <= tau)) return;
+  const int pos = atomicAdd(n, 1);
+  kb[pos] = (unsigned long long)__double_as_longlong(v);
+  kq[pos] = q;
+  ku[pos] = (unsigned long long)floor(ldexp(w, 40 - e));
+}
+
+__global__ void __launch_bounds__(kMR)
+mix_row_kernel(const DevState* st, const double* __restrict__ n2, const int* __restrict__ ptr,
+               const int* __restrict__ col, int nb, double tau, uint64_t* key_bits, int* key_q) {
+  __shared__ unsigned long long kb[kMRMax];
+  __shared__ unsigned long long ku[kMRMax];
+  __shared__ int kq[kMRMax];
+  __shared__ unsigned long long s_part[kMR + 1];
+  __shared__ int s_n, s_first;
+  if (st && !st->iter_active) return;
+  const int r = blockIdx.x, tid = threadIdx.x;
+  if (!(tau > 0.0)) {
+    if (tid == 0) { key_bits[r] = ~0ull; key_q[r] = INT_MAX; }
+    return;
+  }
+  const int e = ilogb(tau);
+  const unsigned long long budget = (unsigned long long)floor(ldexp(tau, 40 - e));
+  if (tid == 0) { s_n = 0; s_first = INT_MAX; }
+  __syncthreads();
+  for (int q = ptr[r] + tid; q < ptr[r + 1]; q += kMR)          // (r, J > r)
+    if (col[q] != r) mr_push(n2[q], q, tau, e, kb, kq, ku, &s_n);
+  for (int I = tid; I < r; I += kMR) {                          // (I < r, r): search row I
+    int lo = ptr[I], hi = ptr[I + 1];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (col[mid] < r) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo < ptr[I + 1] && col[lo] == r) mr_push(n2[lo], lo, tau, e, kb, kq, ku, &s_n);
+  }
+  __syncthreads();
+  const int n = s_n;
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int i = n + tid; i < P; i += kMR) { kb[i] = ~0ull; kq[i] = INT_MAX; ku[i] = 0ull; }
+  __syncthreads();
+  // bitonic sort by (bits, q), ascending
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < P; i += kMR) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const bool gt = kb[i] > kb[l] || (kb[i] == kb[l] && kq[i] > kq[l]);
+          if (gt == up) {
+            const unsigned long long tb = kb[i], tu = ku[i];
+            const int tq = kq[i];
+            kb[i] = kb[l]; ku[i] = ku[l]; kq[i] = kq[l];
+            kb[l] = tb; ku[l] = tu; kq[l] = tq;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // running sum of units in that order: segments per thread, an exclusive scan of their sums,
+  // then each thread finds the first overflow inside its segment
+  const int seg = (P + kMR - 1) / kMR;
+  const int a = tid * seg, z = min(P, a + seg);
+  unsigned long long loc = 0ull;
+  for (int i = a; i < z; ++i) loc += ku[i];
+  s_part[tid + 1] = loc;
+  if (tid == 0) s_part[0] = 0ull;
+  __syncthreads();
+  if (tid == 0)
+    for (int t = 1; t <= kMR; ++t) s_part[t] += s_part[t - 1];
+  __syncthreads();
+  unsigned long long run = s_part[tid];
+  for (int i = a; i < z; ++i) {
+    run += ku[i];
+    if (run > budget) { atomicMin(&s_first, i); break; }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int f = s_first;
+    key_bits[r] = f < n ? (uint64_t)kb[f] : ~0ull;
+    key_q[r] = f < n ? kq[f] : INT_MAX;
+  }
+}
+
+// the cut: the smallest (bits, q) the rows reported, into cut[0] (bits) and cut[1] (q)
+__global__ void __launch_bounds__(1024)
+mix_cut_kernel(const DevState* st, const uint64_t* key_bits, const int* key_q, int nb, uint64_t* cut) {
+  __shared__ unsigned long long sb[1024];
+  __shared__ int sq[1024];
+  if (st && !st->iter_active) return;
+  const int tid = threadIdx.x;
+  unsigned long long b = ~0ull;
+  int q = INT_MAX;
+  for (int r = tid; r < nb; r += 1024) {
+    const unsigned long long rb = key_bits[r];
+    const int rq = key_q[r];
+    if (rb < b || (rb == b && rq < q)) { b = rb; q = rq; }
+  }
+  sb[tid] = b;
+  sq[tid] = q;
+  __syncthreads();
+  for (int o = 512; o > 0; o >>= 1) {
+    if (tid < o && (sb[tid + o] < sb[tid] || (sb[tid + o] == sb[tid] && sq[tid + o] < sq[tid]))) {
+      sb[tid] = sb[tid + o];
+      sq[tid] = sq[tid + o];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    cut[0] = sb[0];
+    cut[1] = (uint64_t)(uint32_t)sq[0];
+  }
+}
+
+__global__ void mix_keep_kernel(const DevState* st, const double* n2, const int* row, const int* col, const int* nnz_p,
+                                double tau, const uint64_t* cut, uint8_t* keep) {
+  if (st && !st->iter_active) return;
+  const int nnz = *nnz_p;
+  const uint64_t cb = cut[0];
+  const int cq = (int)(uint32_t)cut[1];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += gridDim.x * blockDim.x) {
+    const double v = n2[q];
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const bool cand = tau > 0.0 && row[q] != col[q] && sqrt(v) <= tau;
+    keep[q] = cand && (b < cb || (b == cb && q < cq)) ? 0 : 1;
+  }
+}
+
+// scratch: key bits [nb] (8 B), cut [2] (8 B), key q [nb] (4 B)
+size_t mixctl_scratch_bytes(int nb) { return sizeof(uint64_t) * (nb + 2) + sizeof(int) * nb; }
+
+void launch_mixctl(const DevState* st, const double* n2, const int* ptr, const int* row, const int* col,
+                   const int* nnz_p, int nb, double tau, void* scratch, uint8_t* keep, int grid, cudaStream_t s) {
+  uint64_t* kbits = static_cast<uint64_t*>(scratch);
+  uint64_t* cut = kbits + nb;
+  int* kq = reinterpret_cast<int*>(cut + 2);
+  mix_row_kernel<<<nb, kMR, 0, s>>>(st, n2, ptr, col, nb, tau, kbits, kq);
+  mix_cut_kernel<<<1, 1024, 0, s>>>(st, kbits, kq, nb, cut);
+  mix_keep_kernel<<<grid, 256, 0, s>>>(st, n2, row, col, nnz_p, tau, cut, keep);
+}
+
 // per-round reduction over the pairs and the stop test (stored-diagonal trace)
 __global__ void __launch_bounds__(1024)
 bsr_finalize_kernel(DevState* st, const double* spart, const int* nnz_p, cudaGraphConditionalHandle cond,
@@ -608,7 +773,8 @@ bsr_finalize_kernel(DevState* st, const double* spart, const int* nnz_p, cudaGra
   const int k = st->k + 1;
   const int pk = st->tr[k - 1] > (double)st->nocc ? 1 : 0;
   st->sblocks += (unsigned long long)nnz;
-  record_and_test(st, pk, sqrt(a), b, st->tr[k - 1]);
+  // v_{k-1}, or m_{k-1}: the Lanczos estimate of the mixed norm with the 32 x 32 blocks
+  record_and_test(st, pk, st->norm == 1 ? st->spec_e : sqrt(a), b, st->tr[k - 1]);
   // the loop stops after this round's truncation (the kernels below still run)
   if (use_cond && st->done) cudaGraphSetConditional(cond, 0);
 }
@@ -694,6 +860,9 @@ struct sp2_bsr_ctx {
   uint8_t* skeep = nullptr;
   double* spart = nullptr;       // per-pair partials; also the candidate scratch of rule 1
   double* sn2 = nullptr;         // per-pair ||X_IJ||_F^2 of the newest blocks
+  void* mixscr = nullptr;        // rule 2: per-row overflow keys and the cut
+  void* lz = nullptr;            // norm = 1: Lanczos scratch for the mixed norm (nb x nb)
+  int lzld = 0;
   int* counts = nullptr;
   uint32_t* fbits = nullptr;
   int* frank = nullptr;
@@ -736,6 +905,7 @@ static void bsr_free(sp2_bsr_ctx* h) {
   cudaFree(h->S.ptr); cudaFree(h->S.col); cudaFree(h->S.row); cudaFree(h->S.nnz);
   cudaFree(h->FP.ptr); cudaFree(h->FP.col); cudaFree(h->FP.row); cudaFree(h->FP.nnz);
   cudaFree(h->sbits); cudaFree(h->svals); cudaFree(h->skeep); cudaFree(h->spart); cudaFree(h->sn2);
+  cudaFree(h->mixscr); cudaFree(h->lz);
   cudaFree(h->counts);
   cudaFree(h->fbits); cudaFree(h->frank); cudaFree(h->glo); cudaFree(h->ghi); cudaFree(h->gbad);
   cudaFree(h->st_dev);
@@ -807,10 +977,13 @@ static cudaError_t add_round(sp2_bsr_ctx* h, cudaGraph_t g, cudaStream_t s, int 
   bsr_numeric_kernel<<<numeric_grid(), NUM_THREADS, NUM_SMEM, s>>>(st, Xc, W, h->S, h->svals, h->skeep, h->spart,
                                                                   h->sn2, tau2);
   if (timed) cudaEventRecord(h->nev[2 * h->nrounds++ + 1], s);
+  if (h->lz) launch_lanczos_pairs(st, h->S.row, h->S.col, sn, h->spart, h->lz, nb, h->lzld, s);
   bsr_finalize_kernel<<<1, 1024, 0, s>>>(st, h->spart, sn, h->cond, use_cond);
   if (h->rule == SP2_TRUNC_ERROR)
     bsr_errctl_kernel<<<1, kEC, 0, s>>>(st, h->sn2, h->S.row, h->S.col, sn, reinterpret_cast<uint64_t*>(h->spart),
                                         h->skeep, tau2);
+  else if (h->rule == SP2_TRUNC_MIXED)
+    launch_mixctl(st, h->sn2, h->S.ptr, h->S.row, h->S.col, sn, nb, h->tau, h->mixscr, h->skeep, grid_persistent(), s);
   // 4. truncation -> next iterate
   clear_words_kernel<<<256, 256, 0, s>>>(Xn.bits, (int64_t)nb * W, st);
   set_kept_bits_kernel<<<grid_persistent(), 256, 0, s>>>(st, h->S, h->skeep, W, Xn.bits);
@@ -859,7 +1032,7 @@ extern "C" sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, in
   if (!out) return SP2_ERR_INVALID_ARG;
   *out = nullptr;
   if (N < B || N % B != 0 || N / B > MAX_NB || n_occ < 0 || n_occ > N || !(tau >= 0.0) ||
-      (rule != SP2_TRUNC_BLOCK && rule != SP2_TRUNC_ERROR))
+      (rule != SP2_TRUNC_BLOCK && rule != SP2_TRUNC_ERROR && rule != SP2_TRUNC_MIXED))
     return SP2_ERR_INVALID_ARG;
   sp2_opts o;
   sp2_default_opts(&o);
@@ -867,7 +1040,8 @@ extern "C" sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, in
   if (o.max_iter < 1 || o.max_iter > SP2_MAX_ITER || !(o.qtilde > 0.0) || (o.guard != 0 && o.guard != 1) ||
       (o.launch_mode != 0 && o.launch_mode != 1))
     return SP2_ERR_INVALID_ARG;
-  if (o.norm != 0) return SP2_ERR_UNSUPPORTED;       // the block-sparse stop uses the Frobenius v_i
+  if (o.norm < 0 || o.norm > 2) return SP2_ERR_INVALID_ARG;
+  if (o.norm == 2) return SP2_ERR_UNSUPPORTED;       // v_i or the mixed norm m_i (32 x 32 blocks)
   sp2_bsr_ctx* h = new (std::nothrow) sp2_bsr_ctx();
   if (!h) return SP2_ERR_NOMEM;
   h->N = N; h->nocc = n_occ; h->tau = tau; h->rule = rule; h->opts = o;
@@ -908,11 +1082,17 @@ extern "C" sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, in
        cudaMallocHost(&h->st_host, sizeof(DevState)) == cudaSuccess &&
        cudaMallocHost(&h->xnnz_host, sizeof(int)) == cudaSuccess &&
        cudaEventCreate(&h->ev[0]) == cudaSuccess && cudaEventCreate(&h->ev[1]) == cudaSuccess;
+  if (ok && rule == SP2_TRUNC_MIXED) ok = cudaMalloc(&h->mixscr, mixctl_scratch_bytes(nb)) == cudaSuccess;
+  if (ok && o.norm == 1) {
+    h->lzld = (nb + 63) / 64 * 64;
+    ok = cudaMalloc(&h->lz, lanczos_scratch_bytes(h->lzld)) == cudaSuccess;
+  }
   if (!ok) { (void)cudaGetLastError(); bsr_free(h); return SP2_ERR_NOMEM; }
   DevState init;
   std::memset(&init, 0, sizeof(init));
   init.N = (int32_t)N; init.ld = (int32_t)N; init.nocc = (int32_t)n_occ;
   init.max_iter = o.max_iter; init.guard = o.guard; init.qtilde = o.qtilde; init.round_fp32 = 1;
+  init.norm = o.norm;
   *h->st_host = init;
   *h->xnnz_host = 0;
   if (cudaMemcpy(h->st_dev, &init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -972,6 +1152,9 @@ extern "C" sp2_status sp2_run_bsr(sp2_bsr h, const int32_t* row_ptr_dev, const i
   if (h->rule == SP2_TRUNC_ERROR)
     bsr_errctl_kernel<<<1, kEC, 0, s>>>(nullptr, h->sn2, h->FP.row, h->FP.col, h->FP.nnz,
                                         reinterpret_cast<uint64_t*>(h->spart), h->skeep, tau2);
+  else if (h->rule == SP2_TRUNC_MIXED)
+    launch_mixctl(nullptr, h->sn2, h->FP.ptr, h->FP.row, h->FP.col, h->FP.nnz, nb, h->tau, h->mixscr, h->skeep,
+                  grid_persistent(), s);
   Mat X0 = h->X[0];
   BSR_TRY(cudaMemsetAsync(X0.bits, 0, sizeof(uint32_t) * nb * W, s));
   set_kept_bits_kernel<<<grid_persistent(), 256, 0, s>>>(nullptr, h->FP, h->skeep, W, X0.bits);
@@ -1075,7 +1258,7 @@ __global__ void test_pairs_scatter_kernel(const uint8_t* keepp, int nb, const in
 extern "C" int32_t sp2_test_bsr_keep(const float* dense_dev, int64_t N, double tau, int32_t rule, uint8_t* keep_dev,
                                      void* stream) {
   if (!dense_dev || !keep_dev || N < B || N % B || N / B > MAX_NB || !(tau >= 0.0) ||
-      (rule != SP2_TRUNC_BLOCK && rule != SP2_TRUNC_ERROR))
+      (rule != SP2_TRUNC_BLOCK && rule != SP2_TRUNC_ERROR && rule != SP2_TRUNC_MIXED))
     return SP2_ERR_INVALID_ARG;
   const int nb = (int)(N / B);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1085,31 +1268,40 @@ extern "C" int32_t sp2_test_bsr_keep(const float* dense_dev, int64_t N, double t
     for (int J = I; J < nb; ++J, ++q) { row[q] = I; col[q] = J; }
   double *n2_full = nullptr, *n2p = nullptr;
   uint64_t* scratch = nullptr;
-  int *drow = nullptr, *dcol = nullptr, *dnp = nullptr;
+  void* mscr = nullptr;
+  int *drow = nullptr, *dcol = nullptr, *dnp = nullptr, *dptr = nullptr;
   uint8_t* keepp = nullptr;
   bool ok = cudaMalloc(&n2_full, sizeof(double) * nb * nb) == cudaSuccess &&
             cudaMalloc(&n2p, sizeof(double) * npairs) == cudaSuccess &&
             cudaMalloc(&scratch, sizeof(uint64_t) * npairs) == cudaSuccess &&
             cudaMalloc(&drow, sizeof(int) * npairs) == cudaSuccess &&
             cudaMalloc(&dcol, sizeof(int) * npairs) == cudaSuccess && cudaMalloc(&dnp, sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&keepp, npairs) == cudaSuccess;
+            cudaMalloc(&keepp, npairs) == cudaSuccess && cudaMalloc(&mscr, mixctl_scratch_bytes(nb)) == cudaSuccess &&
+            cudaMalloc(&dptr, sizeof(int) * (nb + 1)) == cudaSuccess;
+  std::vector<int> ptr(nb + 1, 0);
+  for (int I = 0; I < nb; ++I) ptr[I + 1] = ptr[I] + (nb - I);
   if (ok) {
     test_keep_kernel<<<nb * nb, 64, 0, s>>>(dense_dev, nb, tau * tau, keep_dev, n2_full);
     ok = cudaGetLastError() == cudaSuccess;
   }
-  if (ok && rule == SP2_TRUNC_ERROR) {
+  if (ok && (rule == SP2_TRUNC_ERROR || rule == SP2_TRUNC_MIXED)) {
     ok = cudaMemcpyAsync(drow, row.data(), sizeof(int) * npairs, cudaMemcpyHostToDevice, s) == cudaSuccess &&
          cudaMemcpyAsync(dcol, col.data(), sizeof(int) * npairs, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-         cudaMemcpyAsync(dnp, &npairs, sizeof(int), cudaMemcpyHostToDevice, s) == cudaSuccess;
+         cudaMemcpyAsync(dnp, &npairs, sizeof(int), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+         cudaMemcpyAsync(dptr, ptr.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, s) == cudaSuccess;
     if (ok) {
       test_pairs_gather_kernel<<<256, 256, 0, s>>>(n2_full, nb, drow, dcol, npairs, n2p);
-      bsr_errctl_kernel<<<1, kEC, 0, s>>>(nullptr, n2p, drow, dcol, dnp, scratch, keepp, tau * tau);
+      if (rule == SP2_TRUNC_ERROR)
+        bsr_errctl_kernel<<<1, kEC, 0, s>>>(nullptr, n2p, drow, dcol, dnp, scratch, keepp, tau * tau);
+      else
+        launch_mixctl(nullptr, n2p, dptr, drow, dcol, dnp, nb, tau, mscr, keepp, 256, s);
       test_pairs_scatter_kernel<<<256, 256, 0, s>>>(keepp, nb, drow, dcol, npairs, keep_dev);
       ok = cudaGetLastError() == cudaSuccess;
     }
   }
   ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
   cudaFree(n2_full); cudaFree(n2p); cudaFree(scratch); cudaFree(drow); cudaFree(dcol); cudaFree(dnp); cudaFree(keepp);
+  cudaFree(mscr); cudaFree(dptr);
   if (!ok) {
     (void)cudaGetLastError();
     return SP2_ERR_CUDA;

@@ -56,6 +56,12 @@ cudaError_t add_lanczos_nodes(cudaGraph_t g, cudaGraphNode_t dep, DevState* st, 
                               int N, int ld, cudaGraphNode_t* last);
 cudaError_t launch_lanczos(DevState* st, const double* buf0, const double* buf1, const double* S,
                            const double* part, int ntiles, void* lz, int N, int ld, cudaStream_t s);
+// The same estimate for the mixed norm of the block-sparse path: the spectral norm of the nb x nb
+// matrix of block norms of X - X^2, built from the square's upper-pair records (row[q], col[q],
+// part[2q] = ||(X - X^2)_IJ||_F^2, doubled off the diagonal; *nnz_p pairs); ld = nb rounded up
+// to a multiple of 64 for lanczos_scratch_bytes.
+cudaError_t launch_lanczos_pairs(DevState* st, const int* row, const int* col, const int* nnz_p, const double* part,
+                                 void* lz, int nb, int ld, cudaStream_t s);
 // Per-iteration reduction + stop test over `nparts` partial records of `stride` doubles.
 cudaError_t add_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, DevState* st,
                               double* part, int nparts, int stride, cudaGraphConditionalHandle cond,

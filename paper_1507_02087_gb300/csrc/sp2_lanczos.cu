@@ -86,13 +86,16 @@ __device__ __forceinline__ void lz_operands(const DevState* st, const double* bu
   Y = (k & 1) ? buf0 : buf1;
 }
 
+// n x n operator stored with leading dimension ld; the square's (v^2, trace) partial records,
+// ntiles of them (or *ntiles_dev when given), set the scale.
 __global__ void __launch_bounds__(kLzThreads)
-lz_start_kernel(const DevState* st, const double* __restrict__ part, int ntiles, LzScratch* lz) {
+lz_start_kernel(const DevState* st, const double* __restrict__ part, int ntiles, const int* ntiles_dev,
+                LzScratch* lz, int N, int ld) {
   __shared__ double sm[32];
   if (st->done) return;
-  const int N = st->N, ld = st->ld;
+  const int cnt = ntiles_dev ? *ntiles_dev : ntiles;
   double v2 = 0.0;                               // v_{k-1}^2 from the square's partials
-  for (int t = threadIdx.x; t < ntiles; t += kLzThreads) v2 += part[2 * (int64_t)t];
+  for (int t = threadIdx.x; t < cnt; t += kLzThreads) v2 += part[2 * (int64_t)t];
   v2 = block_sum<kLzThreads>(v2, sm);
   double* qp = lz_vec(lz, ld, 0);
   double* q = lz_vec(lz, ld, 1);
@@ -154,11 +157,10 @@ __global__ void lz_form_kernel(const DevState* st, const double* buf0, const dou
 // share of q_j . w; the last CTA to finish its rows then computes alpha_j = q_j . w,
 // r = w - alpha_j q_j - beta_j q_{j-1}, beta_{j+1} = ||r|| and q_{j+1} = r / beta_{j+1} in FP64.
 __global__ void __launch_bounds__(kLzMvThreads)
-lz_step_kernel(const DevState* st, LzScratch* lz, int j) {
+lz_step_kernel(const DevState* st, LzScratch* lz, int j, int N, int ld) {
   __shared__ double sm[32];
   __shared__ int s_last;
   if (st->done || !lz->live) return;
-  const int N = st->N, ld = st->ld;
   const float4* __restrict__ A = reinterpret_cast<const float4*>(lz_a32(lz, ld));
   const float4* __restrict__ q4 = reinterpret_cast<const float4*>(lz_q32(lz, ld));
   double* qp = lz_vec(lz, ld, 0);
@@ -299,6 +301,32 @@ lz_eig_kernel(DevState* st, const LzScratch* lz) {
   }
 }
 
+// Block-sparse path: the mixed norm's matrix of block norms M_IJ = ||(X - X^2)_IJ||_F (nb x nb,
+// both triangles) from the square's upper-pair records (v^2 part counted twice off the
+// diagonal), scaled and rounded to FP32 after a zero fill.
+__global__ void lz_zero_kernel(const DevState* st, LzScratch* lz, int ld) {
+  if (st->done) return;
+  float4* A = reinterpret_cast<float4*>(lz_a32(lz, ld));
+  const int64_t total = (int64_t)ld * ld / 4;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    A[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void lz_form_pairs_kernel(const DevState* st, const int* __restrict__ row, const int* __restrict__ col,
+                                     const int* nnz_p, const double* __restrict__ part, LzScratch* lz, int ld) {
+  if (st->done) return;
+  const int nnz = *nnz_p;
+  const double sc = lz->scale;
+  float* A = lz_a32(lz, ld);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += gridDim.x * blockDim.x) {
+    const int I = row[q], J = col[q];
+    const double v2 = part[2 * (int64_t)q] * (I == J ? 1.0 : 0.5);
+    const float w = (float)(sqrt(v2) * sc);
+    A[(int64_t)I * ld + J] = w;
+    A[(int64_t)J * ld + I] = w;
+  }
+}
+
 int step_blocks(int N) {
   const int b = (N + kLzMvThreads / 32 - 1) / (kLzMvThreads / 32);
   return b < kLzMvBlocks ? (b < 1 ? 1 : b) : kLzMvBlocks;
@@ -322,7 +350,8 @@ cudaError_t add_lanczos_nodes(cudaGraph_t g, cudaGraphNode_t dep, DevState* st, 
   const DevState* cst = st;
   cudaKernelNodeParams kp = {};
   cudaGraphNode_t prev = dep, node;
-  void* a0[] = {&cst, &part, &ntiles, &lz};
+  const int* no_count = nullptr;
+  void* a0[] = {&cst, &part, &ntiles, &no_count, &lz, &N, &ld};
   kp.func = (void*)lz_start_kernel;
   kp.gridDim = dim3(1);
   kp.blockDim = dim3(kLzThreads);
@@ -339,7 +368,7 @@ cudaError_t add_lanczos_nodes(cudaGraph_t g, cudaGraphNode_t dep, DevState* st, 
   prev = node;
   for (int j = 0; j < kLzSteps; ++j) {
     int jj = j;
-    void* a2[] = {&cst, &lz, &jj};
+    void* a2[] = {&cst, &lz, &jj, &N, &ld};
     kp.func = (void*)lz_step_kernel;
     kp.gridDim = dim3(step_blocks(N));
     kp.blockDim = dim3(kLzMvThreads);
@@ -361,9 +390,20 @@ cudaError_t add_lanczos_nodes(cudaGraph_t g, cudaGraphNode_t dep, DevState* st, 
 cudaError_t launch_lanczos(DevState* st, const double* buf0, const double* buf1, const double* S,
                            const double* part, int ntiles, void* scratch, int N, int ld, cudaStream_t s) {
   LzScratch* lz = static_cast<LzScratch*>(scratch);
-  lz_start_kernel<<<1, kLzThreads, 0, s>>>(st, part, ntiles, lz);
+  lz_start_kernel<<<1, kLzThreads, 0, s>>>(st, part, ntiles, nullptr, lz, N, ld);
   lz_form_kernel<<<form_blocks(ld), 256, 0, s>>>(st, buf0, buf1, S, lz);
-  for (int j = 0; j < kLzSteps; ++j) lz_step_kernel<<<step_blocks(N), kLzMvThreads, 0, s>>>(st, lz, j);
+  for (int j = 0; j < kLzSteps; ++j) lz_step_kernel<<<step_blocks(N), kLzMvThreads, 0, s>>>(st, lz, j, N, ld);
+  lz_eig_kernel<<<1, 32, 0, s>>>(st, lz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_pairs(DevState* st, const int* row, const int* col, const int* nnz_p, const double* part,
+                                 void* scratch, int nb, int ld, cudaStream_t s) {
+  LzScratch* lz = static_cast<LzScratch*>(scratch);
+  lz_start_kernel<<<1, kLzThreads, 0, s>>>(st, part, 0, nnz_p, lz, nb, ld);
+  lz_zero_kernel<<<form_blocks(ld), 256, 0, s>>>(st, lz, ld);
+  lz_form_pairs_kernel<<<form_blocks(ld), 256, 0, s>>>(st, row, col, nnz_p, part, lz, ld);
+  for (int j = 0; j < kLzSteps; ++j) lz_step_kernel<<<step_blocks(nb), kLzMvThreads, 0, s>>>(st, lz, j, nb, ld);
   lz_eig_kernel<<<1, 32, 0, s>>>(st, lz);
   return cudaGetLastError();
 }

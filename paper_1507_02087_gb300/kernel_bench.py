@@ -37,7 +37,7 @@ def main():
     ap.add_argument("--bsr", default=None, metavar="LX,LY,LZ",
                     help="time the block-sparse squares instead, on the gapped tight-binding lattice of these "
                          "dimensions (LX = 32), tau 1e-4, stream launches")
-    ap.add_argument("--rule", default="error", choices=["error", "block"])
+    ap.add_argument("--rule", default="error", choices=["error", "block", "mixed"])
     a = ap.parse_args()
     if a.sp2:
         return sp2_forward(a)
@@ -100,7 +100,8 @@ def bsr_squares(a):
     dims = tuple(int(x) for x in a.bsr.split(","))
     tb = inputs.tight_binding(dims=dims)
     rp, ci, vals = (torch.from_numpy(x).cuda() for x in tb.bsr(32))
-    with sp2.BsrPurifier(tb.N, tb.nocc, 1e-4, rule=a.rule, launch_mode=1) as P:
+    with sp2.BsrPurifier(tb.N, tb.nocc, 1e-4, rule=a.rule, launch_mode=1,
+                         norm="mixed" if a.rule == "mixed" else "fro") as P:
         for _ in range(max(1, a.reps)):
             P.run(rp, ci, vals, dense=False)
         w = P.info()

@@ -249,16 +249,17 @@ def sp2_destroy(h: int) -> None:
         lib().sp2_destroy(h)
 
 
-TRUNC_RULES = {"block": 0, "error": 1}
+TRUNC_RULES = {"block": 0, "error": 1, "mixed": 2}
 
 
 class BsrPurifier:
     """Block-sparse F (32 x 32 blocks, BSR) -> D with block truncation tau.
-    rule: "block" (drop blocks with norm below tau) or "error" (||E||_F <= tau)."""
+    rule: "block" (drop blocks with norm below tau), "error" (||E||_F <= tau) or "mixed"
+    (||E||_M <= tau); norm: "fro" (stop on v_i) or "mixed" (m_i with the 32 x 32 blocks)."""
 
     def __init__(self, N: int, nocc: int, tau: float, max_iter: int = 200, guard: bool = True,
-                 qtilde: float = 1.8, launch_mode: int | None = None, rule: str = "block"):
-        o = _opts(max_iter, guard, qtilde, 1, 0, False, launch_mode)
+                 qtilde: float = 1.8, launch_mode: int | None = None, rule: str = "block", norm: str = "fro"):
+        o = _opts(max_iter, guard, qtilde, 1, 0, False, launch_mode, norm=norm)
         h = ctypes.c_void_p()
         _check(lib().sp2_create_bsr_ex(N, nocc, tau, TRUNC_RULES[rule], ctypes.byref(o), ctypes.byref(h)),
                "sp2_create_bsr_ex")
