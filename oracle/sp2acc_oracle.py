@@ -119,10 +119,17 @@ def apply_step(X: np.ndarray, p: int, a: float) -> np.ndarray:
 
 def sp2_acc(F: np.ndarray, nocc: int, homo_out: float, homo_in: float, lumo_in: float, lumo_out: float, *,
             bounds: tuple[float, float] | None = None, qtilde: float = o.QTILDE, guard: bool = True,
-            delta: float = DELTA, sched: Schedule | None = None, norm: str = "fro") -> o.SP2Result:
-    """Alg. 5 step by step in FP64 (Alg. 4 supplies the schedule).  `norm`: "fro" (v_i) or
-    "spectral" (e_i = ||X_i - X_i^2||_2, the error of §2; eigvalsh, small N only)."""
-    err = o.idempotency_error_fro if norm == "fro" else o.idempotency_error_spectral
+            delta: float = DELTA, sched: Schedule | None = None, norm: str = "fro", block: int = 128,
+            perturb=None) -> o.SP2Result:
+    """Alg. 5 step by step in FP64 (Alg. 4 supplies the schedule).  `norm`: "fro" (v_i),
+    "spectral" (e_i = ||X_i - X_i^2||_2, the error of §2; eigvalsh, small N only) or "mixed" (m_i
+    with `block` x `block` blocks).  `perturb(i, X)` (optional) returns Alg. 1's E_i, added to X_0
+    and to every X_i as soon as it is formed, as in the plain oracle."""
+    if norm == "mixed":
+        def err(X, X2):
+            return o.mixed_norm(X - X2, block)
+    else:
+        err = o.idempotency_error_fro if norm == "fro" else o.idempotency_error_spectral
     F = np.asarray(F, dtype=np.float64)
     N = F.shape[0]
     lmin, lmax = o.gershgorin_bounds(F) if bounds is None else bounds
@@ -134,6 +141,8 @@ def sp2_acc(F: np.ndarray, nocc: int, homo_out: float, homo_in: float, lumo_in: 
     if sched is None:
         sched = acc_schedule(lmin, lmax, homo_out, homo_in, lumo_in, lumo_out, delta=delta)
     X = o.initial_scaling(F, lmin, lmax)
+    if perturb is not None:
+        X = X + perturb(0, X)
     X2 = X @ X
     v = [err(X, X2)]
     tr = [float(np.trace(X))]
@@ -143,6 +152,8 @@ def sp2_acc(F: np.ndarray, nocc: int, homo_out: float, homo_in: float, lumo_in: 
     for i in range(1, sched.n_max + 1):
         pi = sched.p[i]
         Xi = apply_step(X, pi, sched.alpha[i])
+        if perturb is not None:
+            Xi = Xi + perturb(i, Xi)
         tr.append(float(np.trace(Xi)))
         p.append(pi)
         if guard and i >= sched.n_min and ((pi == 1 and tr[i] >= tr[i - 1]) or (pi == 0 and tr[i] <= tr[i - 1])):

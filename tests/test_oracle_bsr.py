@@ -231,3 +231,24 @@ def test_bsr_oracle_mixed_rule_and_mixed_norm_stop():
     fro = bo.sp2_bsr(F, tb.nocc, 32, 1e-4, rule="mixed")
     for i in range(min(len(res.v), len(fro.v))):                    # m_i <= v_i on the same iterates
         assert res.v[i] <= fro.v[i] * (1 + 1e-12)
+
+
+def test_bsr_oracle_acc_with_truncation():
+    # SP2-ACC with the block truncation (the accelerated expansion of the §6 calculations):
+    # tau = 0 reproduces the untruncated SP2-ACC oracle exactly; with tau = 1e-4 the result stays
+    # near the projector and takes fewer squares than the trace-based expansion
+    from oracle import sp2acc_oracle as oa
+    tb = inputs.tight_binding(L=4, delta=1.0, t=0.3, sigma=0.05, seed=2, dims=(32, 2, 2))
+    F = tb.dense().numpy()
+    lam = np.linalg.eigvalsh(F)
+    homo, lumo = float(lam[tb.nocc - 1]), float(lam[tb.nocc])
+    acc = (homo - 1e-2, homo, lumo, lumo + 1e-2)
+    plain = oa.sp2_acc(F, tb.nocc, *acc)
+    zero = bo.sp2_bsr(F, tb.nocc, 32, 0.0, rule="error", acc=acc)
+    assert zero.n == plain.n and zero.p == plain.p and np.array_equal(zero.D, plain.D)
+    res = bo.sp2_bsr(F, tb.nocc, 32, 1e-4, rule="error", acc=acc)
+    assert res.stop_reason in (o.STOP_ORDER, o.STOP_TRACE_GUARD, oa.STOP_SCHEDULE)
+    V = np.linalg.eigh(F)[1]
+    exact = V[:, :tb.nocc] @ V[:, :tb.nocc].T
+    assert o.rel_error(res.D, exact, tb.nocc) < 1e-3
+    assert res.n < bo.sp2_bsr(F, tb.nocc, 32, 1e-4, rule="error").n
