@@ -277,6 +277,13 @@ sp2_status sp2_create_bsr(int64_t N, int64_t n_occ, double tau, const sp2_opts* 
 sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, int32_t rule, const sp2_opts* opts,
                              sp2_bsr* out);
 
+/* SP2-ACC (Alg. 4 / Alg. 5) on a block-sparse handle, as sp2_set_homo_lumo: bounds = {homo_out,
+ * homo_in, lumo_in, lumo_out} for the following runs (the schedule is computed on the device from
+ * the run's Gershgorin bounds; the numeric square's epilogue forms ca S + cb X + cc I in FP32 and
+ * the truncation follows it as in the trace-based expansion); NULL returns to Alg. 3.
+ * Synchronous.  SP2_ERR_INVALID_ARG for unordered or non-finite bounds. */
+int32_t sp2_set_homo_lumo_bsr(sp2_bsr h, const double* bounds);
+
 /* F as BSR in device memory: row_ptr [N/32 + 1] (int32), col_idx [nnzb] (int32, sorted
  * in each block row, every diagonal block present), vals [nnzb][32][32] (FP64, row-major
  * blocks); F must be exactly symmetric.  D_dev: NULL, or an N x N FP64 device buffer that

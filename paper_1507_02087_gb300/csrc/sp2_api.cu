@@ -785,6 +785,13 @@ static sp2_status write_acc(DevState* st_dev, DevState* st_host, const double* b
   return SP2_OK;
 }
 
+namespace sp2 {
+bool acc_bounds_ok(const double* bounds) { return acc_bounds_valid(bounds); }
+int32_t write_acc_fields(DevState* st_dev, DevState* st_host, const double* bounds) {
+  return write_acc(st_dev, st_host, bounds);
+}
+}  // namespace sp2
+
 extern "C" int32_t sp2_set_homo_lumo(sp2_handle h, const double* bounds) {
   if (!h || (bounds && !acc_bounds_valid(bounds))) return SP2_ERR_INVALID_ARG;
   int cur = 0;

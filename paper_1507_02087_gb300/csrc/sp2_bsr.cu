@@ -243,7 +243,12 @@ bsr_init_kernel(DevState* st, const int* rp, const int* ci, const double* vals, 
     else if (nocc == 0) { st->done = 1; st->out_mode = OUT_ZERO; }
     else if (nocc == N) { st->done = 1; st->out_mode = OUT_IDENTITY; }
     else if (!(lmax > lmin)) { st->status = SP2_ERR_NO_GAP; st->done = 1; st->out_mode = OUT_NAN; }
-    else st->tr[0] = t;
+    else {
+      st->tr[0] = t;
+      if (st->acc && !acc_schedule(st)) {        // SP2-ACC: Alg. 4 from the bounds just found
+        st->status = SP2_ERR_INVALID_ARG; st->done = 1; st->out_mode = OUT_NAN;
+      }
+    }
   }
 }
 
@@ -372,7 +377,11 @@ bsr_numeric_kernel(DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* s
   if (!st->iter_active) return;
   const int nnz = *P.nnz;
   const int kprev = st->k;
-  const int pk = st->tr[kprev] > (double)st->nocc ? 1 : 0;   // Alg. 3 trace test
+  // Alg. 3 trace test, or the scheduled polynomial of SP2-ACC (Alg. 5): X_k = ca S + cb X + cc I
+  double ca = 0.0, cb = 0.0, cc = 0.0;
+  const int gen = st->acc;
+  const int pk = gen ? acc_step(st, kprev + 1, ca, cb, cc) : (st->tr[kprev] > (double)st->nocc ? 1 : 0);
+  const float fa = (float)ca, fb = (float)cb, fc = (float)cc;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int rg = lane >> 2, cg = lane & 3;
   float* wbuf = num_smem + wid * WARP_FLOATS;
@@ -441,7 +450,8 @@ bsr_numeric_kernel(DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* s
       #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const float sv = acc[i][j];
-        nwv[j] = pk ? sv : fmaf(2.0f, old[j], -sv);
+        nwv[j] = gen ? fmaf(fa, sv, fmaf(fb, old[j], (I == J && r == 8 * cg + j) ? fc : 0.f))
+                     : (pk ? sv : fmaf(2.0f, old[j], -sv));
         const float d = old[j] - sv;
         vloc = fmaf(d, d, vloc);
         if (I == J && r == 8 * cg + j) trloc += (double)nwv[j];
@@ -771,7 +781,8 @@ bsr_finalize_kernel(DevState* st, const double* spart, const int* nnz_p, cudaGra
   b = block_sum<1024>(b, sm);
   if (threadIdx.x != 0) return;
   const int k = st->k + 1;
-  const int pk = st->tr[k - 1] > (double)st->nocc ? 1 : 0;
+  double ca, cb, cc;
+  const int pk = st->acc ? acc_step(st, k, ca, cb, cc) : (st->tr[k - 1] > (double)st->nocc ? 1 : 0);
   st->sblocks += (unsigned long long)nnz;
   // v_{k-1}, or m_{k-1}: the Lanczos estimate of the mixed norm with the 32 x 32 blocks
   record_and_test(st, pk, st->norm == 1 ? st->spec_e : sqrt(a), b, st->tr[k - 1]);
@@ -1113,6 +1124,16 @@ extern "C" sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, in
 }
 
 extern "C" void sp2_destroy_bsr(sp2_bsr h) { bsr_free(h); }
+
+extern "C" int32_t sp2_set_homo_lumo_bsr(sp2_bsr h, const double* bounds) {
+  if (!h || (bounds && !sp2::acc_bounds_ok(bounds))) return SP2_ERR_INVALID_ARG;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  const int32_t r = sp2::write_acc_fields(h->st_dev, h->st_host, bounds);
+  cudaSetDevice(cur);
+  return r;
+}
 
 extern "C" sp2_status sp2_get_work_bsr(sp2_bsr h, int64_t* block_products, int64_t* square_blocks,
                                        double* numeric_ms) {

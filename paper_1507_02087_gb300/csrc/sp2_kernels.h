@@ -20,6 +20,11 @@ struct BatchPtrs {
   double* D[tc::kMaxBatchPtrs];
 };
 
+// SP2-ACC set-up shared by the handles: homo/lumo bounds ordered and finite; the SP2-ACC fields of
+// a device state (and its host copy) written, bounds NULL switching the acceleration off.
+bool acc_bounds_ok(const double* bounds);
+int32_t write_acc_fields(DevState* st_dev, DevState* st_host, const double* bounds);
+
 // ---- FP64 path ----------------------------------------------------------------------------
 // a1 + run set-up: Gershgorin partial bounds over `nparts` blocks, then one block
 // that combines them, handles the trivial occupations and computes Tr[X_0].

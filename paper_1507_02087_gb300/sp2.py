@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
         L.sp2_test_bsr_keep.restype = i32
         L.sp2_test_bsr_square_pattern.argtypes = [vp, i32, vp]
         L.sp2_test_bsr_square_pattern.restype = i32
+        L.sp2_set_homo_lumo_bsr.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.sp2_set_homo_lumo_bsr.restype = i32
         L.sp2_set_bounds.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.sp2_set_bounds.restype = i32
         L.sp2_test_set_perturbation.argtypes = [vp, vp, i64]
@@ -274,6 +276,10 @@ class BsrPurifier:
                                  vals.shape[0], D.data_ptr() if D is not None else None, _stream_ptr(stream)),
                "sp2_run_bsr")
         return D
+
+    def set_homo_lumo(self, bounds) -> None:
+        """SP2-ACC with homo/lumo bounds (homo_out, homo_in, lumo_in, lumo_out); None: Alg. 3."""
+        _check(lib().sp2_set_homo_lumo_bsr(self.h, _bounds4(bounds)), "sp2_set_homo_lumo_bsr")
 
     def info(self) -> dict:
         info = sp2_info()

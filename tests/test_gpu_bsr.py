@@ -282,3 +282,34 @@ def test_bsr_full_size_32cubed_a_posteriori(sp2mod, rule, norm):
     else:
         # ||E_i||_2 <= tau but ||E_i||_F up to sqrt(N) tau: a looser Frobenius budget
         assert bound / math.sqrt(nocc) <= 1e-3
+
+
+@pytest.mark.parametrize("rule,norm", [("error", "fro"), ("mixed", "mixed")])
+def test_bsr_acc_against_oracle(sp2mod, rule, norm):
+    # SP2-ACC (Alg. 4 / Alg. 5) with the block truncation: the schedule comes from the run's
+    # Gershgorin bounds, so with the same bounds the oracle's polynomial sequence must agree
+    tb, (rp, ci, vals) = tb_case((32, 8, 4))
+    F = tb.dense().numpy()
+    lam = np.linalg.eigvalsh(F)
+    homo, lumo = float(lam[tb.nocc - 1]), float(lam[tb.nocc])
+    acc = (homo - 1e-2, homo, lumo, lumo + 1e-2)
+    with sp2mod.BsrPurifier(tb.N, tb.nocc, 1e-4, rule=rule, norm=norm) as P:
+        D0 = P.run(rp, ci, vals)
+        i0 = P.info()
+        P.set_homo_lumo(acc)
+        D = P.run(rp, ci, vals).cpu().numpy()
+        info = P.info()
+        with pytest.raises(sp2mod.SP2Error):
+            P.set_homo_lumo((0.1, 0.0, 0.2, 0.3))
+        P.set_homo_lumo(None)
+        D1 = P.run(rp, ci, vals)
+        i1 = P.info()
+    assert info["status"] == 0
+    ref = bo.sp2_bsr(F, tb.nocc, 32, 1e-4, rule=rule, norm=norm, acc=acc,
+                     bounds=(info["lambda_min"], info["lambda_max"]))
+    assert abs(info["n_iter"] - ref.n) <= 3
+    m = min(info["n_iter"], ref.n)
+    assert list(info["p"][1:m + 1]) == ref.p[1:m + 1]
+    assert o.rel_error(D, ref.D, tb.nocc) <= 4e-6
+    assert info["n_iter"] < i0["n_iter"]
+    assert i1["n_iter"] == i0["n_iter"] and torch.equal(D0, D1)       # back to Alg. 3, same bits
