@@ -111,11 +111,11 @@ typedef struct {
                            scratch of (ld/b)^2 doubles); 2 = the spectral norm e_i itself, the
                            error the stop is defined on (§2), estimated after every square by 32
                            Lanczos steps on X - X^2 (a lower bound of e_i within about 1e-3
-                           relative; 66 small launches and 32 reads of two ld x ld FP64 matrices
-                           per square, scratch of 3 ld doubles + 6 KB): FP64 handles only (SP2,
-                           SP2-ACC and McWeeny), SP2_ERR_UNSUPPORTED elsewhere.
-                           sp2_info.v holds the measure used.  The block-sparse path uses v_i
-                           (any other value: SP2_ERR_UNSUPPORTED) */
+                           relative; X - X^2 scaled and rounded to FP32 once, 35 small launches per
+                           square, scratch of 3 ld doubles + ld (ld + 1) floats + 6 KB): FP64
+                           handles only (SP2, SP2-ACC and McWeeny), SP2_ERR_UNSUPPORTED elsewhere.
+                           sp2_info.v holds the measure used.  Block-sparse handles take 0 or 1
+                           (the mixed norm with the 32 x 32 blocks; see sp2_create_bsr) */
 } sp2_opts;
 
 #define SP2_MAX_ITER 512
