@@ -353,20 +353,34 @@ __device__ __forceinline__ void issue_pair(float* wbuf, int stg, const float* va
   cp_async_commit();
 }
 
-__device__ __forceinline__ void product_tile(const float* wbuf, int stg, int rg, int cg, float (&acc)[4][8]) {
+// Packed FP32 pairs: fma.rn.f32x2 rounds each lane once, exactly as fmaf, and halves the FMA
+// instruction count of the issue-bound inner loop.  acc[i][jp] holds columns (2 jp, 2 jp + 1)
+// of row i (low word first), so the B pairs come straight from the 16-byte shared loads and
+// each A value is broadcast into a pair once per k.
+__device__ __forceinline__ unsigned long long pair_bcast(float x) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
+__device__ __forceinline__ void product_tile(const float* wbuf, int stg, int rg, int cg,
+                                             unsigned long long (&acc)[4][4]) {
   const float* At = wbuf + stg * 2 * BE;
   const float* Bt = At + BE;
   #pragma unroll 8
   for (int k = 0; k < B; ++k) {
     const float4 a = *reinterpret_cast<const float4*>(At + k * B + 4 * rg);
-    const float4 b0 = *reinterpret_cast<const float4*>(Bt + k * B + 8 * cg);
-    const float4 b1 = *reinterpret_cast<const float4*>(Bt + k * B + 8 * cg + 4);
-    const float av[4] = {a.x, a.y, a.z, a.w};
-    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(Bt + k * B + 8 * cg);
+    const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(Bt + k * B + 8 * cg + 4);
+    const unsigned long long av[4] = {pair_bcast(a.x), pair_bcast(a.y), pair_bcast(a.z), pair_bcast(a.w)};
+    const unsigned long long bv[4] = {b0.x, b0.y, b1.x, b1.y};
     #pragma unroll
     for (int i = 0; i < 4; ++i)
       #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      for (int jp = 0; jp < 4; ++jp) ffma2(acc[i][jp], av[i], bv[jp]);
   }
 }
 
@@ -388,11 +402,11 @@ bsr_numeric_kernel(DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* s
   const int gw = blockIdx.x * NUM_WARPS + wid, nw = gridDim.x * NUM_WARPS;
   for (int q = gw; q < nnz; q += nw) {
     const int I = P.row[q], J = P.col[q];
-    float acc[4][8];
+    unsigned long long acc2[4][4];
     #pragma unroll
     for (int i = 0; i < 4; ++i)
       #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+      for (int jp = 0; jp < 4; ++jp) acc2[i][jp] = 0ull;     // +0.0f in both words
     int items = 0;
     const int b0 = X.rp[I], b1 = X.rp[I + 1];
     for (int e0 = b0; e0 < b1; e0 += 32) {
@@ -414,7 +428,7 @@ bsr_numeric_kernel(DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* s
         if (items > 0) {
           cp_async_wait<1>();
           __syncwarp();
-          product_tile(wbuf, (items - 1) & 1, rg, cg, acc);
+          product_tile(wbuf, (items - 1) & 1, rg, cg, acc2);
           __syncwarp();
         }
         ++items;
@@ -423,10 +437,16 @@ bsr_numeric_kernel(DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* s
     if (items > 0) {
       cp_async_wait<0>();
       __syncwarp();
-      product_tile(wbuf, (items - 1) & 1, rg, cg, acc);
+      product_tile(wbuf, (items - 1) & 1, rg, cg, acc2);
       __syncwarp();
     }
     if (lane == 0) atomicAdd(&st->bprod, (unsigned long long)items);
+    float acc[4][8];
+    #pragma unroll
+    for (int i = 0; i < 4; ++i)
+      #pragma unroll
+      for (int jp = 0; jp < 4; ++jp)
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[i][2 * jp]), "=f"(acc[i][2 * jp + 1]) : "l"(acc2[i][jp]));
     // epilogue: X_old (I, J) of X~_{k-1} if stored; the new block is staged in the warp's
     // buffer (row stride B + 1) for the fixed-order norm
     const int po = find_block(X, W, I, J);
