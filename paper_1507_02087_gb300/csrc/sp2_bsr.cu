@@ -320,14 +320,18 @@ __global__ void bsr_sym_kernel(DevState* st, Mat X, int nb, int W, uint32_t* sbi
 // S_IJ = sum_K X_IK X_JK^T run over the K of row I (increasing) that row J also holds.  Both
 // triangles are stored and X_KI is the exact transpose of X_IK, so the operands come from
 // block row K as X_KI and X_KJ: read row-major they give X_IK[r][k] = X_KI[k][r] and
-// X_JK[c][k] = X_KJ[k][c], k-major, without a transpose.  Each product's two blocks are
-// copied into a per-warp double buffer with cp.async while the previous product is
-// computed; each lane accumulates a 4 x 8 tile (rows 4 rg .. 4 rg + 3, columns 8 cg ..
-// 8 cg + 7, lane = 4 rg + cg) with one fmaf per term in increasing K, then k.
+// X_JK[c][k] = X_KJ[k][c], k-major, without a transpose.  Each product is staged as two
+// halves (k rows 0..15, then 16..31 of both blocks) through a per-warp double buffer with
+// cp.async while the previous half is computed (8 KB per warp, so six 4-warp CTAs fit an SM);
+// each lane accumulates a 4 x 8 tile (rows 4 rg .. 4 rg + 3, columns 8 cg .. 8 cg + 7,
+// lane = 4 rg + cg) with one fused multiply-add per term in increasing K, then k.
 constexpr int NUM_WARPS = 4;
 constexpr int NUM_THREADS = 32 * NUM_WARPS;
-constexpr int WARP_FLOATS = 2 * 2 * BE;          // two stages of (X_KI, X_KJ)
+constexpr int HK = B / 2;                         // k rows per staged half
+constexpr int HBE = HK * B;                       // floats of one half block
+constexpr int WARP_FLOATS = 2 * 2 * HBE;          // two stages of (X_KI, X_KJ) halves
 constexpr int NUM_SMEM = NUM_WARPS * WARP_FLOATS * 4;
+static_assert(WARP_FLOATS >= B * (B + 1), "the epilogue stages a block with row stride B + 1");
 
 __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -338,14 +342,15 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// blocks pa (X_KI) and pb (X_KJ) of `vals` into stage `stg` of the warp's buffer
-__device__ __forceinline__ void issue_pair(float* wbuf, int stg, const float* vals, int pa, int pb, int lane) {
-  float* dA = wbuf + stg * 2 * BE;
-  float* dB = dA + BE;
-  const float* sA = vals + (int64_t)pa * BE;
-  const float* sB = vals + (int64_t)pb * BE;
+// half h (k rows 16 h .. 16 h + 15) of blocks pa (X_KI) and pb (X_KJ) into stage `stg`
+__device__ __forceinline__ void issue_half(float* wbuf, int stg, const float* vals, int pa, int pb, int h,
+                                           int lane) {
+  float* dA = wbuf + stg * 2 * HBE;
+  float* dB = dA + HBE;
+  const float* sA = vals + (int64_t)pa * BE + h * HBE;
+  const float* sB = vals + (int64_t)pb * BE + h * HBE;
   #pragma unroll
-  for (int i = 0; i < BE / 128; ++i) {
+  for (int i = 0; i < HBE / 128; ++i) {
     const int off = (i * 32 + lane) * 4;
     cp_async16(dA + off, sA + off);
     cp_async16(dB + off, sB + off);
@@ -368,10 +373,10 @@ __device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long 
 
 __device__ __forceinline__ void product_tile(const float* wbuf, int stg, int rg, int cg,
                                              unsigned long long (&acc)[4][4]) {
-  const float* At = wbuf + stg * 2 * BE;
-  const float* Bt = At + BE;
+  const float* At = wbuf + stg * 2 * HBE;
+  const float* Bt = At + HBE;
   #pragma unroll 8
-  for (int k = 0; k < B; ++k) {
+  for (int k = 0; k < HK; ++k) {
     const float4 a = *reinterpret_cast<const float4*>(At + k * B + 4 * rg);
     const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(Bt + k * B + 8 * cg);
     const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(Bt + k * B + 8 * cg + 4);
@@ -424,14 +429,17 @@ bsr_numeric_kernel(DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* s
         mask &= mask - 1u;
         const int a = __shfl_sync(0xffffffffu, pa, src);
         const int b = __shfl_sync(0xffffffffu, pb, src);
-        issue_pair(wbuf, items & 1, X.vals, a, b, lane);
-        if (items > 0) {
-          cp_async_wait<1>();
-          __syncwarp();
-          product_tile(wbuf, (items - 1) & 1, rg, cg, acc2);
-          __syncwarp();
+        #pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          issue_half(wbuf, items & 1, X.vals, a, b, h, lane);
+          if (items > 0) {
+            cp_async_wait<1>();
+            __syncwarp();
+            product_tile(wbuf, (items - 1) & 1, rg, cg, acc2);
+            __syncwarp();
+          }
+          ++items;
         }
-        ++items;
       }
     }
     if (items > 0) {
@@ -440,7 +448,7 @@ bsr_numeric_kernel(DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* s
       product_tile(wbuf, (items - 1) & 1, rg, cg, acc2);
       __syncwarp();
     }
-    if (lane == 0) atomicAdd(&st->bprod, (unsigned long long)items);
+    if (lane == 0) atomicAdd(&st->bprod, (unsigned long long)(items / 2));
     float acc[4][8];
     #pragma unroll
     for (int i = 0; i < 4; ++i)
