@@ -224,6 +224,25 @@ def test_bsr_launch_modes_agree_and_errors(sp2mod):
         assert P.info()["status"] == 3 and bool(torch.isnan(D).all())
 
 
+def test_bsr_launch_modes_agree_mixed_rule_stop_and_acc(sp2mod):
+    # the mixed-norm selection, the Lanczos mixed-norm stop and SP2-ACC, in the graph and as
+    # plain stream launches: the same kernels, so the same bits and the same recorded m_i
+    tb, (rp, ci, vals) = tb_case((32, 8, 4))
+    lam = np.linalg.eigvalsh(tb.dense().numpy())
+    homo, lumo = float(lam[tb.nocc - 1]), float(lam[tb.nocc])
+    for acc in (None, (homo - 1e-2, homo, lumo, lumo + 1e-2)):
+        out = []
+        for mode in (0, 1):
+            with sp2mod.BsrPurifier(tb.N, tb.nocc, 1e-4, launch_mode=mode, rule="mixed", norm="mixed") as P:
+                if acc is not None:
+                    P.set_homo_lumo(acc)
+                D = P.run(rp, ci, vals)
+                out.append((D, P.info()))
+        (D0, i0), (D1, i1) = out
+        assert i0["status"] == 0 and i0["n_iter"] == i1["n_iter"] and torch.equal(D0, D1)
+        assert list(i0["v"]) == list(i1["v"]) and i0["nnzb"] == i1["nnzb"]
+
+
 @pytest.mark.parametrize("rule,norm", [("error", "fro"), ("mixed", "mixed")])
 def test_bsr_full_size_32cubed_a_posteriori(sp2mod, rule, norm):
     """The 32^3 lattice (N = 32768) in the benchmark's configuration (error-controlled rule,
