@@ -543,13 +543,19 @@ def main():
         F_hn, D_hn = F_h.numpy(), D_h.numpy()
         P.run_host(F_hn, D_hn, stream)          # allocates the staging buffers once
         e2e_ms = []
+        eclk = ClockSampler(local)
+        eclk.start()
         for _ in range(a.e2e_steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             P.run_host(F_hn, D_hn, stream)
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        ec = eclk.stop()
+        # the clocks of these steps: a long run under the power cap can drift below the clocks of
+        # the device-timed steps, which then shows up in the gap between e2e and value
         e2e = {"value": max_over_ranks(statistics.mean(e2e_ms), ws), "unit": "ms",
-               "h2d_bytes_per_step": N * N * 8, "d2h_bytes_per_step": N * N * 8}
+               "h2d_bytes_per_step": N * N * 8, "d2h_bytes_per_step": N * N * 8,
+               "sm_mhz": ec.get("sm_mhz"), "reasons": ec.get("reasons")}
 
     # the plain FP64 path, for the comparison the metric asks for
     fp64 = None
