@@ -110,3 +110,14 @@ def test_struct_layout_matches_c():
     py = [getattr(sp2.sp2_opts, f).offset for f in fields_opts] + [ctypes.sizeof(sp2.sp2_opts)]
     py += [getattr(sp2.sp2_info, f).offset for f in fields_info] + [ctypes.sizeof(sp2.sp2_info)]
     assert vals == py
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without the built library the first call raises
+    from paper_1507_02087_gb300 import sp2
+    monkeypatch.setattr(sp2, "_lib", None)
+    monkeypatch.setattr(sp2, "LIB_PATH", str(tmp_path / "libsp2.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        sp2.lib()
+    with pytest.raises(RuntimeError):
+        sp2.Purifier(64, 32, "fp64")
