@@ -161,8 +161,9 @@ int32_t sp2_set_homo_lumo(sp2_handle h, const double* bounds);
  * bounds: bounds = {lambda_min, lambda_max}, used by every later run of the handle (SP2, SP2-ACC
  * and McWeeny scaling alike) and reported in sp2_info; NULL returns to the Gershgorin bounds.
  * Bounds that do not contain the spectrum void the method's guarantees (no check is made).
- * Synchronous.  SP2_ERR_INVALID_ARG for non-finite or unordered bounds; SP2_ERR_UNSUPPORTED on
- * mixed-precision handles. */
+ * Gershgorin bounds are about sqrt(N) too loose on dense matrices with delocalised eigenvectors,
+ * so tighter bounds (from a previous run, or a few Lanczos steps) save squares on either path.
+ * Synchronous.  SP2_ERR_INVALID_ARG for non-finite or unordered bounds. */
 int32_t sp2_set_bounds(sp2_handle h, const double* bounds);
 
 /* ---- McWeeny expansion (§3) on SP2_PREC_FP64 handles -------------------------------------
@@ -228,6 +229,9 @@ sp2_status sp2_run_batch(sp2_batch hb, const double* const* F_dev, double* const
 
 /* sp2_set_homo_lumo for problem i of a batch (user order). */
 int32_t sp2_set_homo_lumo_batch(sp2_batch hb, int32_t i, const double* bounds);
+
+/* As sp2_set_bounds for problem i of a batch (in the order given to sp2_create_batch). */
+int32_t sp2_set_bounds_batch(sp2_batch hb, int32_t i, const double* bounds);
 
 /* Wait for the batch's last run and describe problem i (arrays valid until the next run). */
 sp2_status sp2_get_info_batch(sp2_batch hb, int32_t i, sp2_info* out);

@@ -837,27 +837,32 @@ extern "C" int32_t sp2_set_mcweeny(sp2_handle h, int32_t mode, double mu, double
   return r;
 }
 
-extern "C" int32_t sp2_set_bounds(sp2_handle h, const double* bounds) {
-  if (!h || (bounds && !(std::isfinite(bounds[0]) && std::isfinite(bounds[1]) && bounds[0] < bounds[1])))
-    return SP2_ERR_INVALID_ARG;
-  if (h->mixed) return SP2_ERR_UNSUPPORTED;
-  int cur = 0;
-  cudaGetDevice(&cur);
-  cudaSetDevice(h->device);
-  sp2_status r = SP2_OK;
+static bool bounds_valid(const double* b) {
+  return std::isfinite(b[0]) && std::isfinite(b[1]) && b[0] < b[1];
+}
+
+// Caller's outer bounds into one device state (and its host copy); NULL switches them off.
+static sp2_status write_bounds(DevState* st_dev, DevState* st_host, const double* bounds) {
   const int32_t on = bounds ? 1 : 0;
   const double b[2] = {bounds ? bounds[0] : 0.0, bounds ? bounds[1] : 0.0};
   static_assert(offsetof(DevState, ub_hi) == offsetof(DevState, ub_lo) + sizeof(double), "ub_lo, ub_hi adjacent");
-  char* base = reinterpret_cast<char*>(h->st_dev);
-  if (cudaDeviceSynchronize() != cudaSuccess ||
-      cudaMemcpy(base + offsetof(DevState, ubounds), &on, sizeof(on), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(base + offsetof(DevState, ub_lo), b, sizeof(b), cudaMemcpyHostToDevice) != cudaSuccess)
-    r = SP2_ERR_CUDA;
-  if (r == SP2_OK) {
-    h->st_host->ubounds = on;
-    h->st_host->ub_lo = b[0];
-    h->st_host->ub_hi = b[1];
-  }
+  char* base = reinterpret_cast<char*>(st_dev);
+  SP2_TRY(cudaDeviceSynchronize());
+  SP2_TRY(cudaMemcpy(base + offsetof(DevState, ubounds), &on, sizeof(on), cudaMemcpyHostToDevice));
+  SP2_TRY(cudaMemcpy(base + offsetof(DevState, ub_lo), b, sizeof(b), cudaMemcpyHostToDevice));
+  st_host->ubounds = on;
+  st_host->ub_lo = b[0];
+  st_host->ub_hi = b[1];
+  return SP2_OK;
+}
+
+extern "C" int32_t sp2_set_bounds(sp2_handle h, const double* bounds) {
+  if (!h || (bounds && !bounds_valid(bounds))) return SP2_ERR_INVALID_ARG;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  const sp2_status r = h->mixed ? write_bounds(h->mixed->st_dev, h->mixed->st_host, bounds)
+                                : write_bounds(h->st_dev, h->st_host, bounds);
   (void)cudaGetLastError();
   cudaSetDevice(cur);
   return r;
@@ -890,6 +895,19 @@ struct sp2_batch_ctx {
   cudaStream_t last_stream = nullptr;
   bool ran = false;
 };
+
+extern "C" int32_t sp2_set_bounds_batch(sp2_batch hb, int32_t i, const double* bounds) {
+  if (!hb || i < 0 || i >= hb->count || (bounds && !bounds_valid(bounds))) return SP2_ERR_INVALID_ARG;
+  if (!hb->mixed) return sp2_set_bounds(hb->singles[i], bounds);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(hb->device);
+  const int k = hb->mixed->internal_of[i];
+  const sp2_status r = write_bounds(hb->mixed->st_dev + k, hb->mixed->st_host + k, bounds);
+  (void)cudaGetLastError();
+  cudaSetDevice(cur);
+  return r;
+}
 
 extern "C" int32_t sp2_set_homo_lumo_batch(sp2_batch hb, int32_t i, const double* bounds) {
   if (!hb || i < 0 || i >= hb->count || (bounds && !acc_bounds_valid(bounds))) return SP2_ERR_INVALID_ARG;

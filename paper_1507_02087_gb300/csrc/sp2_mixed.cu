@@ -110,6 +110,10 @@ batch_init_kernel(const Instance* inst, int count, int pb, BatchPtrs ptrs, const
       bad |= part_bad[i * pb + b];
     }
     if (!isfinite(lo) || !isfinite(hi)) bad = 1;
+    if (st->ubounds) {                           // the caller's outer bounds (§3: any serve)
+      lo = st->ub_lo;
+      hi = st->ub_hi;
+    }
     s_lmin = lo; s_lmax = hi; s_bad = bad;
   }
   __syncthreads();

@@ -111,6 +111,8 @@ def lib() -> ctypes.CDLL:
         L.sp2_test_bsr_square_pattern.restype = i32
         L.sp2_set_homo_lumo_bsr.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.sp2_set_homo_lumo_bsr.restype = i32
+        L.sp2_set_bounds_batch.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
+        L.sp2_set_bounds_batch.restype = i32
         L.sp2_set_bounds.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.sp2_set_bounds.restype = i32
         L.sp2_test_set_perturbation.argtypes = [vp, vp, i64]
@@ -337,6 +339,11 @@ class BatchPurifier:
     def set_homo_lumo(self, i: int, bounds) -> None:
         _check(lib().sp2_set_homo_lumo_batch(self.h, i, _bounds4(bounds)), "sp2_set_homo_lumo_batch")
 
+    def set_bounds(self, i: int, bounds) -> None:
+        """Outer spectral bounds (lambda_min, lambda_max) of problem i; None: Gershgorin."""
+        arr = None if bounds is None else (ctypes.c_double * 2)(*[float(x) for x in bounds])
+        _check(lib().sp2_set_bounds_batch(self.h, i, arr), "sp2_set_bounds_batch")
+
     def close(self):
         sp2_destroy_batch(self.h)
         self.h = 0
@@ -386,7 +393,7 @@ class Purifier:
 
     def set_bounds(self, bounds) -> None:
         """Outer spectral bounds (lambda_min, lambda_max) for the scaling in place of the
-        Gershgorin bounds (FP64 handles); None returns to Gershgorin."""
+        Gershgorin bounds; None returns to Gershgorin."""
         arr = None if bounds is None else (ctypes.c_double * 2)(*[float(x) for x in bounds])
         _check(lib().sp2_set_bounds(self.h, arr), "sp2_set_bounds")
 

@@ -201,3 +201,37 @@ def test_mixed_full_size_n32768_householder(sp2mod):
     err = float(torch.linalg.norm(D - case.D_exact)) / math.sqrt(case.nocc)
     assert err <= TOL_MIXED
     assert torch.equal(D, D.T)
+
+
+def test_mixed_caller_bounds_save_squares(sp2mod):
+    # tight outer bounds (the construction's extreme eigenvalues, widened a little) in place of
+    # the Gershgorin bounds, which are about sqrt(N) too loose here: fewer squares, same accuracy
+    case = inputs.dense_gapped(1024, 500, gap=0.02, seed=31)
+    lam = np.sort(case.lam)
+    tight = (float(lam[0]) - 1e-3, float(lam[-1]) + 1e-3)
+    ref = o.sp2(case.F.numpy(), 500, bounds=tight)
+    F = case.F.cuda()
+    with sp2mod.Purifier(1024, 500, "mixed") as P:
+        P.run(F)
+        n_gersh = P.info()["n_iter"]
+        P.set_bounds(tight)
+        D = P.run(F).cpu().numpy()
+        info = P.info()
+        P.set_bounds(None)
+        P.run(F)
+        assert P.info()["n_iter"] == n_gersh
+    assert (info["lambda_min"], info["lambda_max"]) == tight
+    assert info["status"] == 0 and info["n_iter"] <= ref.n + 1 and info["n_iter"] < n_gersh
+    assert o.rel_error(D, ref.D, 500) <= TOL_MIXED
+    # batches: per problem, the others keep their Gershgorin bounds
+    cases = [inputs.dense_gapped(N, k, gap=0.05, seed=s) for N, k, s in [(256, 100, 1), (512, 250, 2)]]
+    with sp2mod.BatchPurifier([c.N for c in cases], [c.nocc for c in cases], "mixed") as B:
+        lam1 = np.sort(cases[1].lam)
+        B.set_bounds(1, (float(lam1[0]) - 1e-3, float(lam1[-1]) + 1e-3))
+        Ds = B.run([c.F.cuda() for c in cases])
+        infos = [B.info(i) for i in range(2)]
+    assert infos[1]["lambda_max"] == float(lam1[-1]) + 1e-3
+    assert infos[0]["lambda_max"] == pytest.approx(o.gershgorin_bounds(cases[0].F.numpy())[1], rel=1e-12)
+    for c, D, inf in zip(cases, Ds, infos):
+        assert inf["status"] == 0
+        assert o.rel_error(D.cpu().numpy(), o.sp2(c.F.numpy(), c.nocc).D, c.nocc) <= TOL_MIXED
