@@ -288,6 +288,10 @@ sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, int32_t rule,
  * Synchronous.  SP2_ERR_INVALID_ARG for unordered or non-finite bounds. */
 int32_t sp2_set_homo_lumo_bsr(sp2_bsr h, const double* bounds);
 
+/* As sp2_set_bounds on a block-sparse handle: {lambda_min, lambda_max} for the scaling in place
+ * of the Gershgorin bounds of the BSR matrix; NULL returns to them.  Synchronous. */
+int32_t sp2_set_bounds_bsr(sp2_bsr h, const double* bounds);
+
 /* F as BSR in device memory: row_ptr [N/32 + 1] (int32), col_idx [nnzb] (int32, sorted
  * in each block row, every diagonal block present), vals [nnzb][32][32] (FP64, row-major
  * blocks); F must be exactly symmetric.  D_dev: NULL, or an N x N FP64 device buffer that

@@ -785,7 +785,29 @@ static sp2_status write_acc(DevState* st_dev, DevState* st_host, const double* b
   return SP2_OK;
 }
 
+static bool bounds_valid(const double* b) {
+  return std::isfinite(b[0]) && std::isfinite(b[1]) && b[0] < b[1];
+}
+
+// Caller's outer bounds into one device state (and its host copy); NULL switches them off.
+static sp2_status write_bounds(DevState* st_dev, DevState* st_host, const double* bounds) {
+  const int32_t on = bounds ? 1 : 0;
+  const double b[2] = {bounds ? bounds[0] : 0.0, bounds ? bounds[1] : 0.0};
+  static_assert(offsetof(DevState, ub_hi) == offsetof(DevState, ub_lo) + sizeof(double), "ub_lo, ub_hi adjacent");
+  char* base = reinterpret_cast<char*>(st_dev);
+  SP2_TRY(cudaDeviceSynchronize());
+  SP2_TRY(cudaMemcpy(base + offsetof(DevState, ubounds), &on, sizeof(on), cudaMemcpyHostToDevice));
+  SP2_TRY(cudaMemcpy(base + offsetof(DevState, ub_lo), b, sizeof(b), cudaMemcpyHostToDevice));
+  st_host->ubounds = on;
+  st_host->ub_lo = b[0];
+  st_host->ub_hi = b[1];
+  return SP2_OK;
+}
+
 namespace sp2 {
+int32_t write_bound_fields(DevState* st_dev, DevState* st_host, const double* bounds) {
+  return write_bounds(st_dev, st_host, bounds);
+}
 bool acc_bounds_ok(const double* bounds) { return acc_bounds_valid(bounds); }
 int32_t write_acc_fields(DevState* st_dev, DevState* st_host, const double* bounds) {
   return write_acc(st_dev, st_host, bounds);
@@ -835,25 +857,6 @@ extern "C" int32_t sp2_set_mcweeny(sp2_handle h, int32_t mode, double mu, double
   (void)cudaGetLastError();
   cudaSetDevice(cur);
   return r;
-}
-
-static bool bounds_valid(const double* b) {
-  return std::isfinite(b[0]) && std::isfinite(b[1]) && b[0] < b[1];
-}
-
-// Caller's outer bounds into one device state (and its host copy); NULL switches them off.
-static sp2_status write_bounds(DevState* st_dev, DevState* st_host, const double* bounds) {
-  const int32_t on = bounds ? 1 : 0;
-  const double b[2] = {bounds ? bounds[0] : 0.0, bounds ? bounds[1] : 0.0};
-  static_assert(offsetof(DevState, ub_hi) == offsetof(DevState, ub_lo) + sizeof(double), "ub_lo, ub_hi adjacent");
-  char* base = reinterpret_cast<char*>(st_dev);
-  SP2_TRY(cudaDeviceSynchronize());
-  SP2_TRY(cudaMemcpy(base + offsetof(DevState, ubounds), &on, sizeof(on), cudaMemcpyHostToDevice));
-  SP2_TRY(cudaMemcpy(base + offsetof(DevState, ub_lo), b, sizeof(b), cudaMemcpyHostToDevice));
-  st_host->ubounds = on;
-  st_host->ub_lo = b[0];
-  st_host->ub_hi = b[1];
-  return SP2_OK;
 }
 
 extern "C" int32_t sp2_set_bounds(sp2_handle h, const double* bounds) {

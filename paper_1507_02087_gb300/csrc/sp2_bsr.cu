@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -218,6 +219,10 @@ bsr_init_kernel(DevState* st, const int* rp, const int* ci, const double* vals, 
     int bad = 0;
     for (int I = 0; I < nb; ++I) { lo = fmin(lo, lo_in[I]); hi = fmax(hi, hi_in[I]); bad |= bad_in[I]; }
     if (!isfinite(lo) || !isfinite(hi)) bad = 1;
+    if (st->ubounds) {                           // the caller's outer bounds (§3: any serve)
+      lo = st->ub_lo;
+      hi = st->ub_hi;
+    }
     s_lmin = lo; s_lmax = hi; s_bad = bad;
   }
   __syncthreads();
@@ -1152,6 +1157,17 @@ extern "C" sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, in
 }
 
 extern "C" void sp2_destroy_bsr(sp2_bsr h) { bsr_free(h); }
+
+extern "C" int32_t sp2_set_bounds_bsr(sp2_bsr h, const double* bounds) {
+  if (!h || (bounds && !(std::isfinite(bounds[0]) && std::isfinite(bounds[1]) && bounds[0] < bounds[1])))
+    return SP2_ERR_INVALID_ARG;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  const int32_t r = sp2::write_bound_fields(h->st_dev, h->st_host, bounds);
+  cudaSetDevice(cur);
+  return r;
+}
 
 extern "C" int32_t sp2_set_homo_lumo_bsr(sp2_bsr h, const double* bounds) {
   if (!h || (bounds && !sp2::acc_bounds_ok(bounds))) return SP2_ERR_INVALID_ARG;

@@ -23,6 +23,8 @@ struct BatchPtrs {
 // SP2-ACC set-up shared by the handles: homo/lumo bounds ordered and finite; the SP2-ACC fields of
 // a device state (and its host copy) written, bounds NULL switching the acceleration off.
 bool acc_bounds_ok(const double* bounds);
+// The caller's outer spectral bounds (bounds[0] < bounds[1]) into a device state, NULL: Gershgorin.
+int32_t write_bound_fields(DevState* st_dev, DevState* st_host, const double* bounds);
 int32_t write_acc_fields(DevState* st_dev, DevState* st_host, const double* bounds);
 
 // ---- FP64 path ----------------------------------------------------------------------------

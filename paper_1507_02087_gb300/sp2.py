@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
         L.sp2_test_bsr_keep.restype = i32
         L.sp2_test_bsr_square_pattern.argtypes = [vp, i32, vp]
         L.sp2_test_bsr_square_pattern.restype = i32
+        L.sp2_set_bounds_bsr.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.sp2_set_bounds_bsr.restype = i32
         L.sp2_set_homo_lumo_bsr.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         L.sp2_set_homo_lumo_bsr.restype = i32
         L.sp2_set_bounds_batch.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
@@ -282,6 +284,11 @@ class BsrPurifier:
     def set_homo_lumo(self, bounds) -> None:
         """SP2-ACC with homo/lumo bounds (homo_out, homo_in, lumo_in, lumo_out); None: Alg. 3."""
         _check(lib().sp2_set_homo_lumo_bsr(self.h, _bounds4(bounds)), "sp2_set_homo_lumo_bsr")
+
+    def set_bounds(self, bounds) -> None:
+        """Outer spectral bounds (lambda_min, lambda_max) in place of Gershgorin's; None: Gershgorin."""
+        arr = None if bounds is None else (ctypes.c_double * 2)(*[float(x) for x in bounds])
+        _check(lib().sp2_set_bounds_bsr(self.h, arr), "sp2_set_bounds_bsr")
 
     def info(self) -> dict:
         info = sp2_info()

@@ -332,3 +332,31 @@ def test_bsr_acc_against_oracle(sp2mod, rule, norm):
     assert o.rel_error(D, ref.D, tb.nocc) <= 4e-6
     assert info["n_iter"] < i0["n_iter"]
     assert i1["n_iter"] == i0["n_iter"] and torch.equal(D0, D1)       # back to Alg. 3, same bits
+
+
+def test_bsr_caller_bounds(sp2mod):
+    # outer bounds from Weyl's inequality in place of Gershgorin's: without disorder the extreme
+    # eigenvalues are +-sqrt(delta^2 + (6t)^2) (k = 0 is on every periodic lattice), and the onsite
+    # disorder moves each eigenvalue by at most its largest magnitude
+    tb, (rp, ci, vals) = tb_case((32, 8, 4))
+    F = tb.dense().numpy()
+    mn = float(np.max(np.abs(np.abs(tb.onsite) - 1.0)))
+    e = float(np.sqrt(1.0 + (6 * tb.hop) ** 2)) + mn
+    bounds = (-e, e)
+    lam = np.linalg.eigvalsh(F)
+    assert bounds[0] <= lam[0] and lam[-1] <= bounds[1]
+    ref = bo.sp2_bsr(F, tb.nocc, 32, 1e-5, rule="error", bounds=bounds)
+    with sp2mod.BsrPurifier(tb.N, tb.nocc, 1e-5, rule="error") as P:
+        P.run(rp, ci, vals)
+        n_gersh = P.info()["n_iter"]
+        P.set_bounds(bounds)
+        D = P.run(rp, ci, vals).cpu().numpy()
+        info = P.info()
+        with pytest.raises(sp2mod.SP2Error):
+            P.set_bounds((1.0, 1.0))
+        P.set_bounds(None)
+        P.run(rp, ci, vals)
+        assert P.info()["n_iter"] == n_gersh
+    assert (info["lambda_min"], info["lambda_max"]) == bounds
+    assert info["status"] == 0 and abs(info["n_iter"] - ref.n) <= 3 and info["n_iter"] <= n_gersh
+    assert o.rel_error(D, ref.D, tb.nocc) <= 4e-6
