@@ -1,4 +1,6 @@
 """Pins of the block-truncation oracle (Alg. 1 with E_i = block truncation)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -252,3 +254,48 @@ def test_bsr_oracle_acc_with_truncation():
     exact = V[:, :tb.nocc] @ V[:, :tb.nocc].T
     assert o.rel_error(res.D, exact, tb.nocc) < 1e-3
     assert res.n < bo.sp2_bsr(F, tb.nocc, 32, 1e-4, rule="error").n
+
+
+def _per_row_cut(n2, tau):
+    """The per-row formulation of the mixed-norm cut, restated here from its argument (each
+    row's own first overflow in key order; the cut is the earliest over the rows): returns the
+    keep mask it implies, for comparison with the oracle's sequential walk."""
+    nb = n2.shape[0]
+    e, budget = bo.mixed_units(tau)
+    cand = {}
+    for I in range(nb):
+        for J in range(I + 1, nb):
+            w = math.sqrt(float(n2[I, J]))
+            if w <= tau:
+                cand[(I, J)] = ((float(n2[I, J]), I, J), int(math.floor(math.ldexp(w, 40 - e))))
+    first = None
+    for r in range(nb):
+        mine = sorted((key, u) for (I, J), (key, u) in cand.items() if r in (I, J))
+        run = 0
+        for key, u in mine:
+            run += u
+            if run > budget:
+                first = key if first is None or key < first else first
+                break
+    keep = np.ones((nb, nb), dtype=bool)
+    for (I, J), (key, _) in cand.items():
+        if first is None or key < first:
+            keep[I, J] = keep[J, I] = False
+    return keep
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_mixed_cut_per_row_equals_sequential_walk(seed):
+    # random symmetric block-norm patterns with many exact ties and zero blocks
+    g = np.random.Generator(np.random.PCG64(100 + seed))
+    nb, b = int(g.integers(3, 14)), 32
+    levels = 2.0 ** -np.arange(18, 26)
+    norms2 = {}
+    for I in range(nb):
+        for J in range(I + 1, nb):
+            kind = g.integers(0, 3)
+            norms2[(I, J)] = 0.0 if kind == 0 else float(g.choice(levels)) ** 2
+    X = _blocks_with_norms(nb, b, norms2)
+    n2 = bo.block_norms2(X, b)
+    for tau in (2.0 ** -20, 3 * 2.0 ** -21, 2.0 ** -18, 1.0):
+        assert np.array_equal(bo.keep_mask_mixed(X, b, tau), _per_row_cut(n2, tau)), (seed, tau)
