@@ -130,3 +130,17 @@ def test_spectral_stop_dense_between_bounds():
     for i in range(min(len(rs.v), len(rf.v))):
         assert rs.v[i] <= rf.v[i] * (1 + 1e-12) and rf.v[i] <= math.sqrt(120) * rs.v[i] * (1 + 1e-12)
     assert o.rel_error(rs.D, jacobi.density_by_definition(F, 60), 60) < 1e-12
+
+
+@pytest.mark.parametrize("beta", [0.05, 0.2, 0.3, 0.45])
+def test_accelerated_ratio_limit_closed_form(beta):
+    # §3.1: with alpha(beta) of McW-ACC, g1(x, beta) = (p - p^2) / (x - x^2)^2 for
+    # p = p_mw(alpha (x - 1/2) + 1/2) tends, as x -> beta from above, to
+    # 16 (beta - 1.5)^2 (beta - 0.75)^2 / ((beta - 1)^2 (4 beta^2 - 6 beta + 3)^3)
+    alpha, _ = om.mcw_schedule(1.0, 1.0 - 2.0 * beta, True, 1)    # beta_0 = (1 - xi / gamma) / 2
+    a = alpha[1]
+    x = beta + 1e-9
+    p = om.p_mw(a * (x - 0.5) + 0.5)
+    g1 = (p - p * p) / (x - x * x) ** 2
+    closed = 16 * (beta - 1.5) ** 2 * (beta - 0.75) ** 2 / ((beta - 1) ** 2 * (4 * beta ** 2 - 6 * beta + 3) ** 3)
+    assert g1 == pytest.approx(closed, rel=1e-6)
