@@ -21,6 +21,8 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sp2_common.cuh"
 #include "sp2_kernels.h"
 #include "sp2_tc.cuh"
@@ -63,6 +65,13 @@ extern "C" const char* sp2_status_string(int32_t s) {
     default: return "unknown status";
   }
 }
+
+// Host-side NVTX range over an entry point (the enqueue, or the whole call for the synchronous
+// host-buffer entry); a no-op unless a profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 static bool opts_valid(const sp2_opts& o) {
   return o.max_iter >= 1 && o.max_iter <= SP2_MAX_ITER && o.qtilde > 0.0 && (o.guard == 0 || o.guard == 1) &&
@@ -697,6 +706,7 @@ static sp2_status enqueue_run(sp2_ctx* h, const double* F, double* D, cudaStream
 }
 
 extern "C" sp2_status sp2_run(sp2_handle h, const double* F_dev, double* D_dev, void* stream) {
+  NvtxRange range("sp2_run");
   if (!h || !F_dev || !D_dev) return SP2_ERR_INVALID_ARG;
   const size_t bytes = (size_t)h->N * h->N * sizeof(double);
   if (overlaps(F_dev, D_dev, bytes)) return SP2_ERR_INVALID_ARG;
@@ -704,6 +714,7 @@ extern "C" sp2_status sp2_run(sp2_handle h, const double* F_dev, double* D_dev, 
 }
 
 extern "C" sp2_status sp2_run_host(sp2_handle h, const double* F_host, double* D_host, void* stream) {
+  NvtxRange range("sp2_run_host");
   if (!h || !F_host || !D_host) return SP2_ERR_INVALID_ARG;
   const size_t bytes = (size_t)h->N * h->N * sizeof(double);
   if (overlaps(F_host, D_host, bytes)) return SP2_ERR_INVALID_ARG;
@@ -972,6 +983,7 @@ extern "C" sp2_status sp2_create_batch(int32_t count, const int64_t* N, const in
 }
 
 extern "C" sp2_status sp2_run_batch(sp2_batch hb, const double* const* F_dev, double* const* D_dev, void* stream) {
+  NvtxRange range("sp2_run_batch");
   if (!hb || !F_dev || !D_dev) return SP2_ERR_INVALID_ARG;
   for (int i = 0; i < hb->count; ++i) {
     if (!F_dev[i] || !D_dev[i]) return SP2_ERR_INVALID_ARG;

@@ -32,6 +32,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sp2.h"
 #include "sp2_common.cuh"
 #include "sp2_kernels.h"
@@ -1197,6 +1199,8 @@ extern "C" sp2_status sp2_get_work_bsr(sp2_bsr h, int64_t* block_products, int64
 
 extern "C" sp2_status sp2_run_bsr(sp2_bsr h, const int32_t* row_ptr_dev, const int32_t* col_idx_dev,
                                   const double* vals_dev, int64_t nnzb, double* D_dev, void* stream) {
+  nvtxRangePushA("sp2_run_bsr");                  // host-side range over the enqueue
+  struct Pop { ~Pop() { nvtxRangePop(); } } pop;
   if (!h || !row_ptr_dev || !col_idx_dev || !vals_dev || nnzb < h->nb || nnzb > h->cap) return SP2_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int nb = h->nb, W = h->W;
