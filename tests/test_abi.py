@@ -121,3 +121,12 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         sp2.lib()
     with pytest.raises(RuntimeError):
         sp2.Purifier(64, 32, "fp64")
+
+
+def test_binding_types_every_declared_function(built):
+    # the ctypes binding sets argument types for every C-ABI function, so no call goes through
+    # ctypes' default int conversion of pointers and 64-bit sizes
+    from paper_1507_02087_gb300 import sp2
+    L = sp2.lib()
+    untyped = [n for n in declared_functions() if getattr(L, n).argtypes is None]
+    assert not untyped, f"no argtypes in the binding: {untyped}"
