@@ -59,16 +59,30 @@ typedef enum {
   SP2_STOP_SCHEDULE = 4      /* SP2-ACC: the precomputed schedule ended (n_max, Alg. 4) */
 } sp2_stop_reason;
 
-/* Arithmetic of the squaring X -> X^2. */
+/* Arithmetic of the squaring X -> X^2.  The three tensor-core modes share one scheme: X is
+ * held as FP32 values split into 16-bit pieces, squares run on the tcgen05 tensor cores as
+ * sums of piece products with FP32 accumulation, bounds, reductions and the stop test are
+ * FP64, and the low-precision expansion (which detects its own, earlier rounding floor with
+ * the same parameterless test) is followed by a first-order correction of the occupied
+ * subspace driven by F (sp2_opts.corrections) and a refinement pair (sp2_opts.refine_steps).
+ * The derivative pass of the correction always runs at the mode's low precision.  Workspace
+ * of the tensor-core modes: (max_iter + 8) slots of P * 2 * ld^2 bytes (P pieces), ld = N
+ * rounded up to a multiple of 128 (256 with CTA-pair tiles); see sp2_opts.history. */
 typedef enum {
-  SP2_PREC_FP64 = 0,  /* FP64 products and FP64 everything (the plain method) */
-  SP2_PREC_MIXED = 1  /* X held as FP32 values, each stored exactly as three bf16
-                         pieces; squares on the tcgen05 tensor cores as the six piece
-                         products with FP32 accumulation; FP64 bounds, reductions and
-                         stop test; then a first-order correction of the occupied
-                         subspace driven by F (see sp2_opts.corrections) and a
-                         refinement pair.  Needs (max_iter + 8) * 6 * ld^2 bytes of
-                         workspace, ld = N rounded up to a multiple of 128. */
+  SP2_PREC_FP64 = 0,   /* FP64 products and FP64 everything (the plain method) */
+  SP2_PREC_MIXED = 1,  /* = SP2_PREC_BF16X6: each FP32 value stored exactly as three bf16
+                          pieces (P = 3), products as the six piece products with a + b <= 2
+                          (FP32-accurate) */
+  SP2_PREC_BF16X6 = 1,
+  SP2_PREC_BF16X3 = 2, /* the same three bf16 pieces, every product as the three with a + b <= 1
+                          (about 16 significant bits, half the tensor work of BF16X6); a
+                          comparison point: its error after the correction stays near 1e-5 */
+  SP2_PREC_FP16X3 = 3  /* each value as two fp16 pieces of 2^14 x (P = 2, 22 significant bits;
+                          |x| < 4, which every iterate satisfies), products as the three piece
+                          products p0 q0 + p0 q1 + p1 q0 (relative error about 2^-21, half the
+                          tensor work of BF16X6), derivative steps as p0 q0; the correction's
+                          F enters as (F - c I) / w' (c, w' the centre and half-width of the
+                          spectral bounds, so its entries fit the fp16 range) */
 } sp2_precision;
 
 typedef struct {
@@ -323,9 +337,11 @@ sp2_status sp2_get_work_bsr(sp2_bsr h, int64_t* block_products, int64_t* square_
  * Asynchronous on `stream`.  The workspace is one fixed device array inside the
  * library (about 4.2 MB, held on every GPU that loads the library until exit);
  * N > SP2_NOALLOC_MAX_N returns SP2_ERR_INVALID_ARG.  The first call on a device
- * looks up that array's device address, so make it before any stream capture.  All
- * calls share the array: calls that overlap on the GPU race and must be serialised
- * by the caller. */
+ * looks up that array's device address and, under CUDA's default lazy module loading,
+ * may load the library's device code and so allocate the array: make that first call
+ * as a warm-up, outside any region where allocation is not allowed and before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU race and
+ * must be serialised by the caller. */
 #define SP2_NOALLOC_MAX_N 512
 sp2_status sp2_run_fp64_noalloc(const double* F_dev, double* D_dev, int64_t N, int64_t n_occ,
                                 int32_t* info_dev, void* stream);

@@ -29,6 +29,28 @@ extern "C" {
 int32_t sp2_test_tc_gemm(const void* arena_dev, int32_t ld, int32_t nslots, int32_t a_slot, int32_t b_slot,
                          int32_t upper, int32_t tile, float* out_dev, void* stream);
 
+/* As sp2_test_tc_gemm for either piece format of the tensor-core path.  fmt 0: three bf16
+ * planes per slot as above; fmt 1: two fp16 planes per slot holding S x split as
+ * p0 = fp16(S x), p1 = fp16(S x - p0) with S = 2^14, so slot s piece p element (i, j) sits
+ * at ((s * 2 + p) * ld + i) * ld + j and the matrix is (p0 + p1) / S.  lowprec 0 forms the
+ * format's full product (bf16: the six piece products with a + b <= 2; fp16: p0 q0 + p0 q1 +
+ * p1 q0); lowprec 1 the low-precision one (bf16: the three with a + b <= 1; fp16: p0 q0).
+ * out_dev receives C itself (the fp16 scale removed). */
+int32_t sp2_test_tc_gemm_ex(const void* arena_dev, int32_t ld, int32_t nslots, int32_t a_slot, int32_t b_slot,
+                            int32_t upper, int32_t tile, int32_t fmt, int32_t lowprec, float* out_dev,
+                            void* stream);
+
+/* The bounded waits of the tensor-core kernel, made to run out: one launch of the 128 x 128
+ * (one SM per tile) bf16 product C = A A^T over slot 0 of a one-slot arena as in
+ * sp2_test_tc_gemm (ld a multiple of 128, every element computed), with every mbarrier wait
+ * limited to `wait_ms` (1..2000) and CTA 0 leaving the first stage of its copy ring unarmed:
+ * its MMA thread's wait for that stage gives up, the CTA's other warps give up or stop, wait
+ * (bounded) for the copies they issued, free their tensor memory and return, while the other
+ * CTAs finish their tiles.  Returns SP2_ERR_TIMEOUT when the waits gave up as they must, the
+ * tiles of the other CTAs are written to out_dev.  Synchronises `stream`.  No GPU fault is
+ * involved: the kernel returns normally and the context stays usable. */
+int32_t sp2_test_tc_timeout(const void* arena_dev, int32_t ld, int32_t wait_ms, float* out_dev, void* stream);
+
 /* Block truncation decision of the block-sparse path on its own: for every 32 x 32 block
  * (I, J) of the dense, symmetric N x N FP32 device matrix, keep_dev[I * (N/32) + J] = 1 if
  * the block is kept, else 0, under `rule` (an sp2_trunc_rule of sp2.h): SP2_TRUNC_BLOCK

@@ -145,20 +145,24 @@ def square_pattern(keep: np.ndarray) -> np.ndarray:
 
 
 def sp2_bsr(F: np.ndarray, nocc: int, b: int, tau: float, *, bounds=None, max_iter: int = 200,
-            guard: bool = True, rule: str = "block", norm: str = "fro", acc=None):
+            guard: bool = True, rule: str = "block", norm: str = "fro", acc=None, storage: str = "fp64"):
     """Alg. 3 with X~_i = X_i + E_i, E_i the block truncation above (FP64 values);
     rule "block" (drop blocks with norm below tau), "error" (||E_i||_F <= tau) or "mixed"
     (||E_i||_M <= tau through the row sums); norm "fro" (v_i) or "mixed" (m_i with the
     b x b blocks, the pairing of the §6 calculations).  acc = (homo_out, homo_in, lumo_in,
-    lumo_out) runs SP2-ACC (Alg. 4 / Alg. 5) with the same truncation instead of Alg. 3."""
+    lumo_out) runs SP2-ACC (Alg. 4 / Alg. 5) with the same truncation instead of Alg. 3.
+    storage "fp32": every iterate is rounded to FP32 values as soon as it is formed and the
+    truncation is decided on the rounded values (E_i = storage rounding + truncation)."""
     mask = {"block": keep_mask, "error": keep_mask_error, "mixed": keep_mask_mixed}[rule]
 
     def perturb(i, X):
         return apply_mask(X, mask(X, b, tau), b) - X
     if acc is not None:
         from oracle import sp2acc_oracle as oa
-        return oa.sp2_acc(F, nocc, *acc, bounds=bounds, guard=guard, norm=norm, block=b, perturb=perturb)
-    return o.sp2(F, nocc, bounds=bounds, max_iter=max_iter, guard=guard, perturb=perturb, norm=norm, block=b)
+        return oa.sp2_acc(F, nocc, *acc, bounds=bounds, guard=guard, norm=norm, block=b, perturb=perturb,
+                          storage=storage)
+    return o.sp2(F, nocc, bounds=bounds, max_iter=max_iter, guard=guard, perturb=perturb, norm=norm, block=b,
+                 storage=storage)
 
 
 def gershgorin_bounds_blocks(F: np.ndarray) -> tuple[float, float]:

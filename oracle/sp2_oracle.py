@@ -116,16 +116,32 @@ def order_test_stops(v_i: float, v_im2: float, qtilde: float = QTILDE, C: float 
     return math.log(v_i / C) / math.log(v_im2) < qtilde
 
 
+def store_fp32(X: np.ndarray) -> np.ndarray:
+    """The nearest FP32 value of every entry (round to nearest even), held in FP64: the
+    storage part of Alg. 1's perturbation, X~ = X + E with E = fl32(X) - X."""
+    return np.asarray(X, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
 def sp2(F: np.ndarray, nocc: int, *, bounds: tuple[float, float] | None = None,
         max_iter: int = 200, qtilde: float = QTILDE, norm: str = "fro", guard: bool = True,
-        perturb=None, block: int = 128) -> SP2Result:
+        perturb=None, block: int = 128, storage: str = "fp64", trace: str = "diag") -> SP2Result:
     """Alg. 3 step by step in FP64.
 
     `perturb(i, X)` (optional) returns the truncation/noise matrix E_i added to X_i
     (Alg. 1, X~_i = X_i + E_i); by default E_i = 0 (dense, no truncation).
     `norm` is "fro" (v_i, what the GPU path uses by default), "spectral" (e_i, the paper's
     definition; eigvalsh, small N only) or "mixed" (m_i, the mixed norm of §2 with blocks of
-    `block` x `block`)."""
+    `block` x `block`).
+    `storage` "fp32" keeps every iterate as FP32 values: X_0 and each X_i are rounded to the
+    nearest FP32 value as soon as they are formed, before `perturb` (Alg. 1: E_i holds that
+    rounding, plus the truncation if any).  Products, traces, norms and the stop test stay
+    FP64; this is the expansion the low-precision paths carry out in exact arithmetic on
+    their stored iterates, so its stop is where their rounding floor is detected.
+    `trace` "diag" (Alg. 3) takes Tr[X~_{i-1}] from the diagonal of the stored iterate;
+    "fro" takes it from the identity Tr[Y^2] = ||Y||_F^2 for symmetric Y: Tr[X_i] =
+    ||X~_{i-1}||_F^2 after X^2 and 2 Tr[X~_{i-1}] - ||X~_{i-1}||_F^2 after 2X - X^2 (the
+    trace of X_i before its perturbation), and the trace guard compares it with the diagonal
+    sum Tr[X~_{i-1}]."""
     F = np.asarray(F, dtype=np.float64)
     N = F.shape[0]
     if F.shape != (N, N):
@@ -147,9 +163,18 @@ def sp2(F: np.ndarray, nocc: int, *, bounds: tuple[float, float] | None = None,
     else:
         err = idempotency_error_fro if norm == "fro" else idempotency_error_spectral
 
-    X = initial_scaling(F, lmin, lmax)
-    if perturb is not None:
-        X = X + perturb(0, X)
+    if storage not in ("fp64", "fp32") or trace not in ("diag", "fro"):
+        raise ValueError("storage is 'fp64' or 'fp32', trace is 'diag' or 'fro'")
+
+    def stored(i, Y):
+        # X~_i = X_i + E_i: FP32 storage rounding first, then the prescribed perturbation
+        if storage == "fp32":
+            Y = store_fp32(Y)
+        if perturb is not None:
+            Y = Y + perturb(i, Y)
+        return Y
+
+    X = stored(0, initial_scaling(F, lmin, lmax))
     X2 = X @ X
     v = [err(X, X2)]
     tr = [float(np.trace(X))]
@@ -162,11 +187,17 @@ def sp2(F: np.ndarray, nocc: int, *, bounds: tuple[float, float] | None = None,
             Xi, pi = X2, 1                 # X_i = X~_{i-1}^2
         else:
             Xi, pi = 2.0 * X - X2, 0       # X_i = 2 X~_{i-1} - X~_{i-1}^2
-        if perturb is not None:
-            Xi = Xi + perturb(i, Xi)
-        tr.append(float(np.trace(Xi)))
+        if trace == "fro":
+            fro2 = float(np.sum(X * X))
+            tr_prev = float(np.trace(X))
+            tr_i = fro2 if pi == 1 else 2.0 * tr_prev - fro2
+        Xi = stored(i, Xi)
+        if trace == "diag":
+            tr_prev = tr[i - 1]
+            tr_i = float(np.trace(Xi))
+        tr.append(tr_i)
         p.append(pi)
-        if guard and ((pi == 1 and tr[i] >= tr[i - 1]) or (pi == 0 and tr[i] <= tr[i - 1])):
+        if guard and ((pi == 1 and tr[i] >= tr_prev) or (pi == 0 and tr[i] <= tr_prev)):
             return SP2Result(Xi, i, STOP_TRACE_GUARD, lmin, lmax, v, tr, p)
         X2i = Xi @ Xi
         v.append(err(Xi, X2i))

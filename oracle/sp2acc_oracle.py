@@ -120,11 +120,19 @@ def apply_step(X: np.ndarray, p: int, a: float) -> np.ndarray:
 def sp2_acc(F: np.ndarray, nocc: int, homo_out: float, homo_in: float, lumo_in: float, lumo_out: float, *,
             bounds: tuple[float, float] | None = None, qtilde: float = o.QTILDE, guard: bool = True,
             delta: float = DELTA, sched: Schedule | None = None, norm: str = "fro", block: int = 128,
-            perturb=None) -> o.SP2Result:
+            perturb=None, storage: str = "fp64") -> o.SP2Result:
     """Alg. 5 step by step in FP64 (Alg. 4 supplies the schedule).  `norm`: "fro" (v_i),
     "spectral" (e_i = ||X_i - X_i^2||_2, the error of §2; eigvalsh, small N only) or "mixed" (m_i
     with `block` x `block` blocks).  `perturb(i, X)` (optional) returns Alg. 1's E_i, added to X_0
-    and to every X_i as soon as it is formed, as in the plain oracle."""
+    and to every X_i as soon as it is formed, as in the plain oracle; `storage` "fp32" rounds
+    X_0 and every X_i to FP32 values first, as in the plain oracle."""
+    if storage not in ("fp64", "fp32"):
+        raise ValueError("storage is 'fp64' or 'fp32'")
+
+    def stored(i, Y):
+        if storage == "fp32":
+            Y = o.store_fp32(Y)
+        return Y + perturb(i, Y) if perturb is not None else Y
     if norm == "mixed":
         def err(X, X2):
             return o.mixed_norm(X - X2, block)
@@ -140,9 +148,7 @@ def sp2_acc(F: np.ndarray, nocc: int, homo_out: float, homo_in: float, lumo_in: 
         raise ValueError("F has no spectral width: there is no homo-lumo gap")
     if sched is None:
         sched = acc_schedule(lmin, lmax, homo_out, homo_in, lumo_in, lumo_out, delta=delta)
-    X = o.initial_scaling(F, lmin, lmax)
-    if perturb is not None:
-        X = X + perturb(0, X)
+    X = stored(0, o.initial_scaling(F, lmin, lmax))
     X2 = X @ X
     v = [err(X, X2)]
     tr = [float(np.trace(X))]
@@ -151,9 +157,7 @@ def sp2_acc(F: np.ndarray, nocc: int, homo_out: float, homo_in: float, lumo_in: 
         return o.SP2Result(X, 0, o.STOP_EXACT, lmin, lmax, v, tr, p)
     for i in range(1, sched.n_max + 1):
         pi = sched.p[i]
-        Xi = apply_step(X, pi, sched.alpha[i])
-        if perturb is not None:
-            Xi = Xi + perturb(i, Xi)
+        Xi = stored(i, apply_step(X, pi, sched.alpha[i]))
         tr.append(float(np.trace(Xi)))
         p.append(pi)
         if guard and i >= sched.n_min and ((pi == 1 and tr[i] >= tr[i - 1]) or (pi == 0 and tr[i] <= tr[i - 1])):

@@ -116,16 +116,17 @@ static constexpr size_t kTuneBytes = size_t(2) << 30;
 
 static int round_up(int64_t n, int a) { return (int)((n + a - 1) / a * a); }
 
-static int tune_tiles(const std::vector<int64_t>& N) {
+static int tune_tiles(const std::vector<int64_t>& N, int fmt, int lowprec) {
   using namespace sp2::tc;
   const int count = (int)N.size();
+  const int np = np_of(fmt);
   double model[3] = {0.0, 0.0, 0.0};
   size_t bytes[3] = {0, 0, 0};
   for (int c = 1; c <= 2; ++c)
     for (int k = 0; k < count; ++k) {
       const double ld = round_up(N[k], c == 2 ? PT : LD_ALIGN);
       model[c] += ld * ld * ld / (c == 2 ? 1580.0 : 1200.0);
-      bytes[c] += (size_t)2 * NP * (size_t)ld * (size_t)ld * 2;
+      bytes[c] += (size_t)2 * np * (size_t)ld * (size_t)ld * 2;
     }
   const int by_model = model[2] < model[1] ? 2 : 1;
   if (std::max(bytes[1], bytes[2]) > kTuneBytes) return by_model;
@@ -153,13 +154,15 @@ static int tune_tiles(const std::vector<int64_t>& N) {
       std::memset(&I, 0, sizeof(I));
       const int ld = round_up(N[k], pair ? PT : LD_ALIGN);
       __nv_bfloat16* arena = (__nv_bfloat16*)((char*)scratch + off);
-      off += (size_t)2 * NP * (size_t)ld * (size_t)ld * 2;
+      off += (size_t)2 * np * (size_t)ld * (size_t)ld * 2;
       I.ld = ld;
       I.arena = arena;
-      I.slot_elems = (int64_t)NP * ld * ld;
+      I.fmt = fmt;
+      I.np = np;
+      I.slot_elems = (int64_t)np * ld * ld;
       I.tile_off_upper = I.tile_off_upper2 = tiles;
       tiles += sp2::tc_tiles(ld, 1, pair);
-      ok = sp2::tc_make_maps(arena, ld, 2, &I.mapA, &I.mapB) == cudaSuccess;
+      ok = sp2::tc_make_maps(arena, ld, 2, fmt, &I.mapA, &I.mapB) == cudaSuccess;
     }
     if (!ok) break;
     Job j;
@@ -173,6 +176,8 @@ static int tune_tiles(const std::vector<int64_t>& N) {
     j.inst = dinst;
     j.out_slot = 1;
     j.pair = pair;
+    j.fmt = fmt;
+    j.lowprec = lowprec;
     j.err = err;
     ok = cudaMemcpyAsync(dinst, hinst.data(), sizeof(Instance) * count, cudaMemcpyHostToDevice, s) == cudaSuccess &&
          sp2::tc_launch(j, s) == cudaSuccess;
@@ -206,6 +211,9 @@ static int tune_tiles(const std::vector<int64_t>& N) {
 struct MixedEngine {
   int count = 0;
   sp2_opts opts{};
+  int fmt = 0;                     // tc::Fmt of every arena
+  int lp_main = 0;                 // 1: forward, correction and refinement products at low precision
+                                   // (SP2_PREC_BF16X3); the derivative pass always is
   std::vector<int> user_of;        // internal index -> user index
   std::vector<int> internal_of;    // user index -> internal index
   std::vector<int64_t> N, nocc;    // internal order
@@ -266,22 +274,28 @@ struct MixedEngine {
     j.total_tiles = upper ? total_upper : total_full;
     j.inst = inst_dev;
     j.err = err_dev;
+    j.fmt = fmt;
+    j.lowprec = lp_main;
     return j;
   }
 
   // One derivative step: dX_j from X_{j-1} and dX_{j-1} (two products).  dX is a
-  // first-order correction far smaller than X, so its products run on the two leading
-  // pieces (about 16 bits) of each operand, half the tensor-core work of a full product.
+  // first-order correction far smaller than X, so its products run at the format's low
+  // precision: the two leading bf16 pieces (about 16 bits, half the work of a full product)
+  // or the leading fp16 piece (11 bits, a third).
   sp2::tc::Job deriv_job() const {
     sp2::tc::Job j = job(sp2::tc::MODE_DERIV_STEP, 1, sp2::tc::SLOTS_DERIV, 2);
     j.lowprec = 1;
     return j;
   }
 
-  sp2_status init(int cnt, const int64_t* Nu, const int64_t* noccu, const sp2_opts& o) {
+  sp2_status init(int cnt, const int64_t* Nu, const int64_t* noccu, const sp2_opts& o, int precision) {
     using namespace sp2::tc;
     count = cnt;
     opts = o;
+    fmt = precision == SP2_PREC_FP16X3 ? FMT_FP16X2 : FMT_BF16X3;
+    lp_main = precision == SP2_PREC_BF16X3 ? 1 : 0;
+    const int np = np_of(fmt);
     user_of.resize(count);
     std::iota(user_of.begin(), user_of.end(), 0);
     std::stable_sort(user_of.begin(), user_of.end(), [&](int a, int b) { return Nu[a] > Nu[b]; });
@@ -313,7 +327,7 @@ struct MixedEngine {
     arenas.assign(count, nullptr);
     parts.assign(count, nullptr);
     const int H = o.max_iter + 2;
-    pair = (o.tile == 0 ? tune_tiles(N) : o.tile) == 2 ? 1 : 0;
+    pair = (o.tile == 0 ? tune_tiles(N, fmt, lp_main) : o.tile) == 2 ? 1 : 0;
     const int align = pair ? PT : LD_ALIGN;
     auto ld_of = [&](int64_t n) { return round_up(n, align); };
     // Keep every iterate (full history) or recompute them in the derivative pass; without
@@ -323,7 +337,7 @@ struct MixedEngine {
       double full = 0.0;
       for (int k = 0; k < count; ++k) {
         const double ld = (double)ld_of(N[k]);
-        full += (double)(H + 6) * NP * ld * ld * 2.0;
+        full += (double)(H + 6) * np * ld * ld * 2.0;
       }
       size_t free_b = 0, total_b = 0;
       if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { (void)cudaGetLastError(); free_b = 0; }
@@ -345,7 +359,9 @@ struct MixedEngine {
       I.f_slot = base + 3;
       I.r0_slot = base + 4;
       const int nslots = base + 6;
-      I.slot_elems = (int64_t)NP * ld * ld;
+      I.fmt = fmt;
+      I.np = np;
+      I.slot_elems = (int64_t)np * ld * ld;
       I.st = st_dev + k;
       I.tile_off_upper = I.tile_off_upper2 = off_u;
       I.tile_off_full = I.tile_off_full2 = off_f;
@@ -373,7 +389,7 @@ struct MixedEngine {
         mscrs.push_back(ms);
         I.mscr = ms;
       }
-      SP2_TRY(sp2::tc_make_maps(arenas[k], ld, nslots, &I.mapA, &I.mapB));
+      SP2_TRY(sp2::tc_make_maps(arenas[k], ld, nslots, fmt, &I.mapA, &I.mapB));
       st_host[k] = initial_state(N[k], nocc[k], o, ld, 1);
     }
     total_upper = off_u;
@@ -644,7 +660,7 @@ extern "C" sp2_status sp2_create(int64_t N, int64_t nocc, int32_t precision, con
   if (!out) return SP2_ERR_INVALID_ARG;
   *out = nullptr;
   if (N < 1 || N > 65536 || nocc < 0 || nocc > N) return SP2_ERR_INVALID_ARG;
-  if (precision != SP2_PREC_FP64 && precision != SP2_PREC_MIXED) return SP2_ERR_UNSUPPORTED;
+  if (precision < SP2_PREC_FP64 || precision > SP2_PREC_FP16X3) return SP2_ERR_UNSUPPORTED;
   sp2_opts o;
   sp2_default_opts(&o);
   if (opts) o = *opts;
@@ -655,9 +671,9 @@ extern "C" sp2_status sp2_create(int64_t N, int64_t nocc, int32_t precision, con
   h->N = N; h->nocc = nocc; h->precision = precision; h->opts = o;
   if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; (void)cudaGetLastError(); return SP2_ERR_CUDA; }
   sp2_status s;
-  if (precision == SP2_PREC_MIXED) {
+  if (precision != SP2_PREC_FP64) {
     h->mixed = new (std::nothrow) MixedEngine();
-    s = h->mixed ? h->mixed->init(1, &N, &nocc, o) : SP2_ERR_NOMEM;
+    s = h->mixed ? h->mixed->init(1, &N, &nocc, o, precision) : SP2_ERR_NOMEM;
   } else {
     s = create_f64(h);
   }
@@ -955,12 +971,12 @@ extern "C" sp2_status sp2_create_batch(int32_t count, const int64_t* N, const in
   if (count < 1 || count > SP2_MAX_BATCH || !N || !nocc) return SP2_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i)
     if (N[i] < 1 || N[i] > 65536 || nocc[i] < 0 || nocc[i] > N[i]) return SP2_ERR_INVALID_ARG;
-  if (precision != SP2_PREC_FP64 && precision != SP2_PREC_MIXED) return SP2_ERR_UNSUPPORTED;
+  if (precision < SP2_PREC_FP64 || precision > SP2_PREC_FP16X3) return SP2_ERR_UNSUPPORTED;
   sp2_opts o;
   sp2_default_opts(&o);
   if (opts) o = *opts;
   if (!opts_valid(o)) return SP2_ERR_INVALID_ARG;
-  if (precision == SP2_PREC_MIXED && o.refine_steps > 0 && o.refine_fp64 && count > 1) return SP2_ERR_UNSUPPORTED;
+  if (precision != SP2_PREC_FP64 && o.refine_steps > 0 && o.refine_fp64 && count > 1) return SP2_ERR_UNSUPPORTED;
   if (o.norm == 2 && precision != SP2_PREC_FP64) return SP2_ERR_UNSUPPORTED;
   sp2_batch_ctx* hb = new (std::nothrow) sp2_batch_ctx();
   if (!hb) return SP2_ERR_NOMEM;
@@ -969,9 +985,9 @@ extern "C" sp2_status sp2_create_batch(int32_t count, const int64_t* N, const in
   hb->N.assign(N, N + count);
   if (cudaGetDevice(&hb->device) != cudaSuccess) { delete hb; (void)cudaGetLastError(); return SP2_ERR_CUDA; }
   sp2_status s = SP2_OK;
-  if (precision == SP2_PREC_MIXED) {
+  if (precision != SP2_PREC_FP64) {
     hb->mixed = new (std::nothrow) MixedEngine();
-    s = hb->mixed ? hb->mixed->init(count, N, nocc, o) : SP2_ERR_NOMEM;
+    s = hb->mixed ? hb->mixed->init(count, N, nocc, o, precision) : SP2_ERR_NOMEM;
   } else {
     hb->singles.assign(count, nullptr);
     for (int i = 0; i < count && s == SP2_OK; ++i) s = sp2_create(N[i], nocc[i], SP2_PREC_FP64, &o, &hb->singles[i]);

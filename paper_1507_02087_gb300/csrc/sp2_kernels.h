@@ -88,8 +88,9 @@ cudaError_t launch_copy_f64(const DevState* st, const double* X, int ld, int N, 
                             cudaStream_t s);
 
 // ---- tensor-core path ------------------------------------------------------------------------
-// TMA tensor maps over a piece arena of `nslots` ld x ld matrices (boxes of 128 rows).
-cudaError_t tc_make_maps(void* arena, int ld, int nslots, CUtensorMap* mapA, CUtensorMap* mapB);
+// TMA tensor maps over a piece arena of `nslots` ld x ld matrices in piece format `fmt`
+// (tc::Fmt; boxes of 128 rows).
+cudaError_t tc_make_maps(void* arena, int ld, int nslots, int fmt, CUtensorMap* mapA, CUtensorMap* mapB);
 int tc_tiles(int ld, int upper, int pair);
 int tc_grid_for(int total_tiles, int pair);
 cudaError_t tc_launch(const tc::Job& job, cudaStream_t s);

@@ -5,7 +5,10 @@
 //
 //  * bounds / init: Gershgorin bounds per instance, special cases, Tr[X_0].
 //  * scale_split: X_0 = (lmax I - F)/(lmax - lmin) in FP64, rounded to FP32 and stored
-//    as three bf16 pieces (history slot 0); F itself as pieces for the correction.
+//    as pieces (history slot 0); F as pieces for the correction (FMT_BF16X3: F itself;
+//    FMT_FP16X2: F' = (F - c I) / W' with c and W' the centre and half-width of
+//    [lmin, lmax], whose entries lie in [-1, 1] and fit the fp16 range; the shift drops out
+//    of dF and the scale is undone where dX_0 is formed).
 //  * finalize / check: per-instance reduction + stop test after each round of squares;
 //    the loop's condition is cleared once every instance has stopped.
 //  * deriv_advance: advances every instance's derivative loop.
@@ -27,17 +30,8 @@ namespace sp2 {
 
 using tc::Instance;
 
-__device__ __forceinline__ void split3_(float x, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
-  p0 = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(p0);
-  p1 = __float2bfloat16_rn(r1);
-  const float r2 = r1 - __bfloat162float(p1);
-  p2 = __float2bfloat16_rn(r2);
-}
-
-__device__ __forceinline__ float join3_(const __nv_bfloat16* s, int64_t plane, int64_t off) {
-  return (__bfloat162float(s[off]) + __bfloat162float(s[plane + off])) + __bfloat162float(s[2 * plane + off]);
-}
+using tc::piece_load;
+using tc::piece_store;
 
 __device__ __forceinline__ bool ok_run(const DevState* st) {
   return st->status == SP2_OK && st->out_mode == OUT_COPY;
@@ -154,6 +148,8 @@ __global__ void batch_scale_split_kernel(const Instance* inst, int count, int sb
   if (st->done) return;
   const int N = st->N, ld = In.ld;
   const double lmax = st->lmax, w = st->lmax - st->lmin;
+  const int fmt = In.fmt;
+  const double cmid = 0.5 * (st->lmax + st->lmin), hw = 0.5 * w;
   const int64_t plane = (int64_t)ld * ld;
   __nv_bfloat16* X = In.arena + (int64_t)tc::xslot(In.lowmem, In.hist0, 0) * In.slot_elems;
   __nv_bfloat16* Fp = In.arena + (int64_t)In.f_slot * In.slot_elems;
@@ -164,11 +160,9 @@ __global__ void batch_scale_split_kernel(const Instance* inst, int count, int sb
     const double f = F[e];
     const float x = (float)(((r == c ? lmax : 0.0) - f) / w);
     const int64_t off = (int64_t)r * ld + c;
-    __nv_bfloat16 a, bb, cc;
-    split3_(x, a, bb, cc);
-    X[off] = a; X[plane + off] = bb; X[2 * plane + off] = cc;
-    split3_((float)f, a, bb, cc);
-    Fp[off] = a; Fp[plane + off] = bb; Fp[2 * plane + off] = cc;
+    piece_store(fmt, X, plane, off, x);
+    const float fv = fmt == tc::FMT_FP16X2 ? (float)((f - (r == c ? cmid : 0.0)) / hw) : (float)f;
+    piece_store(fmt, Fp, plane, off, fv);
   }
 }
 
@@ -284,11 +278,9 @@ __global__ void batch_corrected_to_pieces_kernel(const Instance* inst, int count
   for (int64_t e = b * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)sb * blockDim.x) {
     const int r = (int)(e / N), c = (int)(e % N);
     const int64_t off = (int64_t)r * ld + c;
-    double val = (double)join3_(X, plane, off);
-    if (corr) val += (double)join3_(dX, plane, off);
-    __nv_bfloat16 a, bb, cc;
-    split3_((float)val, a, bb, cc);
-    R[off] = a; R[plane + off] = bb; R[2 * plane + off] = cc;
+    double val = (double)piece_load(In.fmt, X, plane, off);
+    if (corr) val += (double)piece_load(In.fmt, dX, plane, off);
+    piece_store(In.fmt, R, plane, off, (float)val);
   }
 }
 
@@ -316,8 +308,8 @@ __global__ void batch_assemble_kernel(const Instance* inst, int count, int sb, i
     double val;
     if (mode == OUT_COPY) {
       const int64_t off = (int64_t)r * ld + c;
-      val = (double)join3_(X, plane, off);
-      if (corr) val += (double)join3_(dX, plane, off);
+      val = (double)piece_load(In.fmt, X, plane, off);
+      if (corr) val += (double)piece_load(In.fmt, dX, plane, off);
     } else if (mode == OUT_ZERO) {
       val = 0.0;
     } else if (mode == OUT_IDENTITY) {
@@ -351,11 +343,8 @@ __global__ void mcw_split_kernel(const Instance* inst, const double* Dbuf, doubl
     const double d = Dbuf[off];
     const double ev = Sbuf[off] - d;
     Sbuf[off] = ev;
-    __nv_bfloat16 a, b, cc;
-    split3_((float)d, a, b, cc);
-    Dp[off] = a; Dp[plane + off] = b; Dp[2 * plane + off] = cc;
-    split3_((float)ev, a, b, cc);
-    Ep[off] = a; Ep[plane + off] = b; Ep[2 * plane + off] = cc;
+    piece_store(In.fmt, Dp, plane, off, (float)d);
+    piece_store(In.fmt, Ep, plane, off, (float)ev);
   }
 }
 
@@ -376,7 +365,7 @@ __global__ void mcw_out_kernel(const Instance* inst, const double* Dbuf, const d
     double val;
     if (mode == OUT_COPY && st->status == SP2_OK) {
       const int64_t off = (int64_t)r * ld + c;
-      val = Dbuf[off] + Ebuf[off] - 2.0 * (double)join3_(Pp, plane, off);
+      val = Dbuf[off] + Ebuf[off] - 2.0 * (double)piece_load(In.fmt, Pp, plane, off);
     } else if (mode == OUT_ZERO) {
       val = 0.0;
     } else if (mode == OUT_IDENTITY) {

@@ -7,7 +7,10 @@
 // sp2_run_fp64_noalloc serves them: its workspace is one fixed file-scope device
 // array, created when the library's device code is loaded on a GPU and held until
 // the process exits.  The caller still passes F and D (and, optionally, an info
-// buffer), all in device memory it already owns.
+// buffer), all in device memory it already owns.  With CUDA's lazy module loading
+// (the default), that load may happen inside the first call on a device, which then
+// allocates the array (about 4.2 MB); make that first call as a warm-up, outside any
+// region where allocation is not allowed and before any stream capture.
 //
 // The workspace limits the problem size to N <= SP2_NOALLOC_MAX_N.  Every call shares
 // the one array, so calls whose work overlaps on the GPU (on different streams, or
@@ -17,6 +20,8 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/sp2.h"
 #include "sp2_common.cuh"
@@ -71,8 +76,19 @@ __global__ void noalloc_info_kernel(const DevState* st, int32_t* info) {
 
 }  // namespace
 
+static sp2_status run_noalloc(const double* F_dev, double* D_dev, int64_t N, int64_t n_occ, int32_t* info_dev,
+                              void* stream);
+
 extern "C" sp2_status sp2_run_fp64_noalloc(const double* F_dev, double* D_dev, int64_t N, int64_t n_occ,
                                            int32_t* info_dev, void* stream) {
+  nvtxRangePushA("sp2_run_fp64_noalloc");
+  const sp2_status st = run_noalloc(F_dev, D_dev, N, n_occ, info_dev, stream);
+  nvtxRangePop();
+  return st;
+}
+
+static sp2_status run_noalloc(const double* F_dev, double* D_dev, int64_t N, int64_t n_occ, int32_t* info_dev,
+                              void* stream) {
   if (!F_dev || !D_dev || N < 1 || n_occ < 0 || n_occ > N) return SP2_ERR_INVALID_ARG;
   if (N > kMaxN) return SP2_ERR_INVALID_ARG;   // larger than the fixed workspace
   const size_t bytes = (size_t)N * N * sizeof(double);

@@ -1,21 +1,31 @@
 // Tensor-core (tcgen05) path: definitions shared by the GEMM kernel, the batched
 // elementwise kernels and the host side.
 //
-// Matrices on this path are FP32 values stored exactly as three bf16 "pieces"
-// x = (p0 + p1) + p2 (p0 = bf16(x), p1 = bf16(x - p0), p2 = x - p0 - p1; each
-// difference is exact in FP32, and the last one fits in bf16).  A product X Y^T is
-// the sum of the six piece products p_a q_b with a + b <= 2, each a bf16 MMA with
-// FP32 accumulation, which carries the product to FP32 accuracy.
+// Matrices on this path are FP32 values stored as 16-bit "pieces", in one of two formats:
+//  * FMT_BF16X3: three bf16 pieces x = (p0 + p1) + p2 (p0 = bf16(x), p1 = bf16(x - p0),
+//    p2 = x - p0 - p1; each difference is exact in FP32 and the last one fits in bf16),
+//    so the FP32 value is stored exactly.  A full product X Y^T is the sum of the six
+//    piece products p_a q_b with a + b <= 2 (FP32-accurate); a low-precision product
+//    takes the three with a + b <= 1 (about 16 significant bits).
+//  * FMT_FP16X2: two fp16 pieces of the scaled value S x, S = 2^14 (p0 = fp16(S x),
+//    p1 = fp16(S x - p0)): 22 significant bits, and fp16's exponent range holds every
+//    |x| < 4 (the iterates have |x| <= 1).  A full product is the three piece products
+//    p0 q0 + p0 q1 + p1 q0 (relative error about 2^-21); a low-precision product is p0 q0
+//    alone (11 bits).  Each piece product is exact in FP32, the accumulated sum carries
+//    S^2, which the epilogue removes.
+// Both run as kind::f16 MMAs (fp16 and bf16 inputs at the same tensor-core rate) with FP32
+// accumulation.
 //
-// Every problem ("instance") owns a piece arena: slot s holds the three planes of one
-// ld x ld matrix, plane-major ([slot][piece][row][col], bf16).  A 4-D TMA tensor map
-// (col, row, piece, slot) per instance covers its arena, so a kernel selects operands
-// by instance and slot.  A launch works on the tiles of all live instances of a batch
-// (a single problem is a batch of one).
+// Every problem ("instance") owns a piece arena: slot s holds the planes of one ld x ld
+// matrix, plane-major ([slot][piece][row][col], 16-bit).  A 4-D TMA tensor map (col, row,
+// piece, slot) per instance covers its arena, so a kernel selects operands by instance and
+// slot.  A launch works on the tiles of all live instances of a batch (a single problem is
+// a batch of one).
 #pragma once
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "sp2_common.cuh"
@@ -23,11 +33,19 @@
 namespace sp2 {
 namespace tc {
 
+// Piece formats (sp2_tc.cuh header comment).
+enum Fmt : int32_t { FMT_BF16X3 = 0, FMT_FP16X2 = 1 };
+constexpr float kF16Scale = 16384.f;                 // S = 2^14
+constexpr float kF16InvScale = 1.f / 16384.f;
+constexpr float kF16InvScale2 = 1.f / (16384.f * 16384.f);
+
 constexpr int BM = 128;          // tile rows (MMA M)
 constexpr int BN = 128;          // tile cols (MMA N)
-constexpr int BK = 32;           // k-block: 32 bf16 = 64 B rows, 64-byte swizzle
-constexpr int NP = 3;            // pieces per matrix
-constexpr int STAGES = 4;
+constexpr int BK = 32;           // k-block: 32 16-bit values = 64 B rows, 64-byte swizzle
+constexpr int NP = 3;            // pieces per matrix (FMT_BF16X3; FMT_FP16X2 has 2)
+constexpr int STAGES = 4;        // TMA ring depth (FMT_BF16X3; FMT_FP16X2, with smaller stages, has 6)
+__host__ __device__ constexpr int np_of(int fmt) { return fmt == FMT_FP16X2 ? 2 : 3; }
+__host__ __device__ constexpr int stages_of(int fmt) { return fmt == FMT_FP16X2 ? 6 : 4; }
 // The tensor cores' FP32 accumulation drops the bits an addend loses in alignment
 // (it rounds toward zero), so a long sum of same-sign products drifts low by about
 // K * 2^-25 of its value.  The MMAs therefore accumulate CHUNK_KB k-blocks (64 terms)
@@ -39,6 +57,9 @@ constexpr int A_PIECE_BYTES = BM * BK * 2;
 constexpr int B_PIECE_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = NP * (A_PIECE_BYTES + B_PIECE_BYTES);
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;   // + alignment slack
+__host__ __device__ constexpr int stage_bytes_of(int fmt) { return np_of(fmt) * (A_PIECE_BYTES + B_PIECE_BYTES); }
+static_assert(stages_of(FMT_FP16X2) * stage_bytes_of(FMT_FP16X2) == STAGES * STAGE_BYTES,
+              "both formats use the same shared-memory ring size");
 constexpr int THREADS = 192;     // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
 constexpr int TMEM_COLS = NBUF * BN;   // four 128 x 128 fp32 chunk accumulators
 constexpr int LD_ALIGN = 128;    // ld is a multiple of the tile size
@@ -116,6 +137,8 @@ struct Instance {
   int32_t nparts;           // forward-square partial records (4 doubles each) per launch
   int32_t rec_pair;         // 1: the records come from CTA-pair tiles (16 per 256 x 256 tile)
   double* mscr;             // mixed-norm scratch ((ld/128)^2 + 2 ld/128 doubles), or null
+  int32_t fmt;              // Fmt of the arena
+  int32_t np;               // pieces (planes) per slot: np_of(fmt)
 };
 
 struct Job {
@@ -129,12 +152,56 @@ struct Job {
   int32_t a_slot[2], b_slot[2];   // SLOTS_FIXED operands; SLOTS_REFINE step in a_slot[0]
   int32_t out_slot;
   int32_t pair;         // 1: 256 x 256 CTA-pair tiles (every instance's ld a multiple of 256)
-  int32_t lowprec;      // 1: pieces 0 and 1 of each operand only, the three products with
-                        // a + b <= 1 (about 16 significant bits; the derivative pass)
-  int32_t _pad;
+  int32_t lowprec;      // 1: the low-precision product of the format (FMT_BF16X3: pieces 0 and 1,
+                        // the three products with a + b <= 1, about 16 bits; FMT_FP16X2: p0 q0,
+                        // 11 bits); the derivative pass, and every product of SP2_PREC_BF16X3
+  int32_t fmt;          // Fmt of every instance of the batch
+  int32_t wait_ms;      // limit of every mbarrier wait in ms (0: the default, 2 s)
+  int32_t test_skip;    // testing hook (128 x 128 kernel): 1 = CTA 0 leaves its first ring stage
+                        // unarmed, so that the waits on it give up (see sp2_test_tc_timeout)
   float* out32;         // MODE_STORE_F32
   int32_t* err;         // set to SP2_ERR_TIMEOUT if a wait gave up
 };
+
+// ---- pieces of one value -------------------------------------------------------------------
+// `slot` points at plane 0 of a slot, planes `plane` elements apart.
+__device__ __forceinline__ void split_bf16x3(float x, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
+  p0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(p0);
+  p1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(p1);
+  p2 = __float2bfloat16_rn(r2);
+}
+
+__device__ __forceinline__ void split_fp16x2(float x, __half& p0, __half& p1) {
+  const float y = x * kF16Scale;                  // exact: a power of two
+  p0 = __float2half_rn(y);
+  p1 = __float2half_rn(y - __half2float(p0));     // the difference is exact in FP32
+}
+
+__device__ __forceinline__ float piece_load(int fmt, const __nv_bfloat16* slot, int64_t plane, int64_t off) {
+  if (fmt == FMT_FP16X2) {
+    const __half* h = reinterpret_cast<const __half*>(slot);
+    return (__half2float(h[off]) + __half2float(h[plane + off])) * kF16InvScale;   // exact sum
+  }
+  return (__bfloat162float(slot[off]) + __bfloat162float(slot[plane + off])) + __bfloat162float(slot[2 * plane + off]);
+}
+
+__device__ __forceinline__ void piece_store(int fmt, __nv_bfloat16* slot, int64_t plane, int64_t off, float x) {
+  if (fmt == FMT_FP16X2) {
+    __half* h = reinterpret_cast<__half*>(slot);
+    __half a, b;
+    split_fp16x2(x, a, b);
+    h[off] = a;
+    h[plane + off] = b;
+    return;
+  }
+  __nv_bfloat16 a, b, c;
+  split_bf16x3(x, a, b, c);
+  slot[off] = a;
+  slot[plane + off] = b;
+  slot[2 * plane + off] = c;
+}
 
 __host__ __device__ __forceinline__ int tiles_of(int ld, int upper) {
   const int R = ld / BM;

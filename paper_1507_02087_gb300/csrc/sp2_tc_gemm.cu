@@ -117,10 +117,44 @@ __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
   return r;
 }
 
-// k-blocks per tensor-memory chunk: CHUNK_KB (64 terms), twice that for low-precision jobs,
-// whose three products per k-step fill a chunk in half the time and whose 16-bit target
-// tolerates the larger accumulation bias (about 128 x 2^-25).
-__device__ __forceinline__ int chunk_kb(const Job& job) { return job.lowprec ? 2 * CHUNK_KB : CHUNK_KB; }
+// k-blocks per tensor-memory chunk: CHUNK_KB (64 terms) for full products; for low-precision
+// jobs, whose products per k-step fill a chunk sooner and whose 16-bit (bf16) or 11-bit (fp16)
+// target tolerates the larger accumulation bias, twice (bf16, about 128 x 2^-25) or four times
+// (fp16, one product per k-step) as many, halved until the chunks divide the k-blocks of a tile.
+__device__ __forceinline__ int chunk_kb(const Job& job, int ld) {
+  int ck = !job.lowprec ? CHUNK_KB : (job.fmt == FMT_FP16X2 ? 4 * CHUNK_KB : 2 * CHUNK_KB);
+  const int total = job.nterms * (ld / BK);
+  while (ck > 1 && total % ck != 0) ck >>= 1;
+  return ck;
+}
+
+// Piece products of one k-step, smallest first: (piece of A, piece of B).  The low-precision
+// product is the tail of the list from lp_first.
+template <int FMT>
+struct Products;
+template <>
+struct Products<FMT_BF16X3> {
+  static constexpr int n = 6, lp_first = 3;
+  __device__ static constexpr int a(int q) { return q == 0 ? 2 : (q == 1 || q == 3) ? 1 : 0; }   // 2,1,0,1,0,0
+  __device__ static constexpr int b(int q) { return q == 2 ? 2 : (q == 1 || q == 4) ? 1 : 0; }   // 0,1,2,0,1,0
+};
+template <>
+struct Products<FMT_FP16X2> {
+  static constexpr int n = 3, lp_first = 2;
+  __device__ static constexpr int a(int q) { return q == 0 ? 1 : 0; }                              // 1,0,0
+  __device__ static constexpr int b(int q) { return q == 1 ? 1 : 0; }                              // 0,1,0
+};
+
+template <int FMT>
+__host__ __device__ constexpr uint32_t idesc_of(int M, int N) {
+  return FMT == FMT_FP16X2 ? idesc_f16_f32(M, N) : idesc_bf16_f32(M, N);
+}
+
+// Pieces loaded per operand by one job.
+template <int FMT>
+__device__ __forceinline__ int pieces_loaded(const Job& job) {
+  return job.lowprec ? (FMT == FMT_FP16X2 ? 1 : 2) : np_of(FMT);
+}
 
 __device__ __forceinline__ int tile_off(const Job& job, const Instance& in) {
   if (job.pair) return job.upper ? in.tile_off_upper2 : in.tile_off_full2;
@@ -149,48 +183,50 @@ __device__ __forceinline__ int locate(const Job& job, int t, int& I, int& J) {
   return i;
 }
 
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
-  p0 = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(p0);
-  p1 = __float2bfloat16_rn(r1);
-  const float r2 = r1 - __bfloat162float(p1);
-  p2 = __float2bfloat16_rn(r2);
-}
-
-__device__ __forceinline__ float join3(__nv_bfloat16 p0, __nv_bfloat16 p1, __nv_bfloat16 p2) {
-  return (__bfloat162float(p0) + __bfloat162float(p1)) + __bfloat162float(p2);
-}
-
-// 8 consecutive values (16-byte aligned) from / to the three planes of a slot.
+// 8 consecutive values (16-byte aligned) from / to the planes of a slot.
+template <int FMT>
 __device__ __forceinline__ void load8(const __nv_bfloat16* slot, int64_t plane, int64_t off, float (&x)[8]) {
-  const uint4 a = *reinterpret_cast<const uint4*>(slot + off);
-  const uint4 b = *reinterpret_cast<const uint4*>(slot + plane + off);
-  const uint4 c = *reinterpret_cast<const uint4*>(slot + 2 * plane + off);
-  const __nv_bfloat16* pa = reinterpret_cast<const __nv_bfloat16*>(&a);
-  const __nv_bfloat16* pb = reinterpret_cast<const __nv_bfloat16*>(&b);
-  const __nv_bfloat16* pc = reinterpret_cast<const __nv_bfloat16*>(&c);
-  #pragma unroll
-  for (int e = 0; e < 8; ++e) x[e] = join3(pa[e], pb[e], pc[e]);
+  if constexpr (FMT == FMT_FP16X2) {
+    const uint4 a = *reinterpret_cast<const uint4*>(slot + off);
+    const uint4 b = *reinterpret_cast<const uint4*>(slot + plane + off);
+    const __half* pa = reinterpret_cast<const __half*>(&a);
+    const __half* pb = reinterpret_cast<const __half*>(&b);
+    #pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = (__half2float(pa[e]) + __half2float(pb[e])) * kF16InvScale;
+  } else {
+    const uint4 a = *reinterpret_cast<const uint4*>(slot + off);
+    const uint4 b = *reinterpret_cast<const uint4*>(slot + plane + off);
+    const uint4 c = *reinterpret_cast<const uint4*>(slot + 2 * plane + off);
+    const __nv_bfloat16* pa = reinterpret_cast<const __nv_bfloat16*>(&a);
+    const __nv_bfloat16* pb = reinterpret_cast<const __nv_bfloat16*>(&b);
+    const __nv_bfloat16* pc = reinterpret_cast<const __nv_bfloat16*>(&c);
+    #pragma unroll
+    for (int e = 0; e < 8; ++e)
+      x[e] = (__bfloat162float(pa[e]) + __bfloat162float(pb[e])) + __bfloat162float(pc[e]);
+  }
 }
 
+template <int FMT>
 __device__ __forceinline__ void store8(__nv_bfloat16* slot, int64_t plane, int64_t off, const float (&x)[8]) {
-  uint4 a, b, c;
-  __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(&a);
-  __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>(&b);
-  __nv_bfloat16* pc = reinterpret_cast<__nv_bfloat16*>(&c);
-  #pragma unroll
-  for (int e = 0; e < 8; ++e) split3(x[e], pa[e], pb[e], pc[e]);
-  *reinterpret_cast<uint4*>(slot + off) = a;
-  *reinterpret_cast<uint4*>(slot + plane + off) = b;
-  *reinterpret_cast<uint4*>(slot + 2 * plane + off) = c;
-}
-
-__device__ __forceinline__ void store_one(__nv_bfloat16* slot, int64_t plane, int64_t off, float v) {
-  __nv_bfloat16 a, b, c;
-  split3(v, a, b, c);
-  slot[off] = a;
-  slot[plane + off] = b;
-  slot[2 * plane + off] = c;
+  if constexpr (FMT == FMT_FP16X2) {
+    uint4 a, b;
+    __half* pa = reinterpret_cast<__half*>(&a);
+    __half* pb = reinterpret_cast<__half*>(&b);
+    #pragma unroll
+    for (int e = 0; e < 8; ++e) split_fp16x2(x[e], pa[e], pb[e]);
+    *reinterpret_cast<uint4*>(slot + off) = a;
+    *reinterpret_cast<uint4*>(slot + plane + off) = b;
+  } else {
+    uint4 a, b, c;
+    __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(&a);
+    __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>(&b);
+    __nv_bfloat16* pc = reinterpret_cast<__nv_bfloat16*>(&c);
+    #pragma unroll
+    for (int e = 0; e < 8; ++e) split_bf16x3(x[e], pa[e], pb[e], pc[e]);
+    *reinterpret_cast<uint4*>(slot + off) = a;
+    *reinterpret_cast<uint4*>(slot + plane + off) = b;
+    *reinterpret_cast<uint4*>(slot + 2 * plane + off) = c;
+  }
 }
 
 struct Partials {
@@ -199,16 +235,21 @@ struct Partials {
   double trd;   // sum of the diagonal x
 };
 
-// Epilogue for row r, columns c0 .. c0+31 of the tile, with the accumulated product s;
-// worked in groups of 8 columns (one 16-byte access per plane).  The Frobenius partials
-// of the 32 columns are summed in FP32 in column order, then added to P in FP64.
+// Epilogue for row r, columns c0 .. c0+31 of the tile, with the accumulated product s
+// (FMT_FP16X2: S^2 times the product, removed here); worked in groups of 8 columns (one
+// 16-byte access per plane).  The Frobenius partials of the 32 columns are summed in FP32 in
+// column order, then added to P in FP64.
+template <int FMT>
 __device__ __forceinline__ void epilogue_chunk(const Job& job, const Instance& In, const Resolved& R, int r,
-                                               int c0, const float (&s)[32], Partials& P) {
+                                               int c0, const float (&s_raw)[32], Partials& P) {
   const int ld = In.ld;
   const int64_t plane = (int64_t)ld * ld;
   const bool upper = job.upper != 0;
   if (upper && c0 + 31 < r) return;
   const int64_t row_off = (int64_t)r * ld + c0;
+  float s[32];
+  #pragma unroll
+  for (int j = 0; j < 32; ++j) s[j] = FMT == FMT_FP16X2 ? s_raw[j] * kF16InvScale2 : s_raw[j];
 
   if (job.mode == MODE_STORE_F32) {
     const bool all_keep = !upper || c0 >= r;
@@ -234,14 +275,16 @@ __device__ __forceinline__ void epilogue_chunk(const Job& job, const Instance& I
       for (int j = 0; j < 8; ++j) xn[j] = s[8 * h + j];
     } else {
       float x[8];
-      load8(in, plane, row_off + 8 * h, x);
+      load8<FMT>(in, plane, row_off + 8 * h, x);
       if (job.mode == MODE_DF_COMBINE) {
+        // dX_0 = -dF / (lmax - lmin): the F slot holds F (FMT_BF16X3), or F' = (F - c I) / W'
+        // with c, W' the centre and half-width of [lmin, lmax] (FMT_FP16X2), whose dF' is dF / W'
         const double w = In.st->lmax - In.st->lmin;
-        const float sc = (float)(-1.0 / w);
+        const float sc = FMT == FMT_FP16X2 ? -0.5f : (float)(-1.0 / w);
         #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int64_t toff = (int64_t)(cb + j) * ld + r;
-          const float mt = join3(in[toff], in[plane + toff], in[2 * plane + toff]);
+          const float mt = piece_load(FMT, in, plane, toff);
           xn[j] = sc * ((x[j] + mt) - 2.0f * s[8 * h + j]);
         }
       } else {
@@ -266,16 +309,16 @@ __device__ __forceinline__ void epilogue_chunk(const Job& job, const Instance& I
       }
     }
     if (!upper || cb >= r) {
-      store8(out, plane, row_off + 8 * h, xn);
+      store8<FMT>(out, plane, row_off + 8 * h, xn);
     } else {
       #pragma unroll
       for (int j = 0; j < 8; ++j)
-        if (cb + j >= r) store_one(out, plane, row_off + 8 * h + j, xn[j]);
+        if (cb + j >= r) piece_store(FMT, out, plane, row_off + 8 * h + j, xn[j]);
     }
     if (upper) {
       #pragma unroll
       for (int j = 0; j < 8; ++j)
-        if (cb + j > r) store_one(out, plane, (int64_t)(cb + j) * ld + r, xn[j]);
+        if (cb + j > r) piece_store(FMT, out, plane, (int64_t)(cb + j) * ld + r, xn[j]);
     }
   }
   if (job.mode == MODE_SP2_STEP) {
@@ -284,10 +327,13 @@ __device__ __forceinline__ void epilogue_chunk(const Job& job, const Instance& I
   }
 }
 
+template <int FMT>
 __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
+  constexpr int STG = stages_of(FMT), SBYTES = stage_bytes_of(FMT), NPS = np_of(FMT);
+  using PR = Products<FMT>;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[STAGES];
-  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t full_bar[STG];
+  __shared__ __align__(8) uint64_t empty_bar[STG];
   __shared__ __align__(8) uint64_t accf_bar[NBUF];
   __shared__ __align__(8) uint64_t acce_bar[NBUF];
   __shared__ __align__(8) uint64_t drain_bar;
@@ -296,8 +342,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t wait_ns = job.wait_ms > 0 ? (uint64_t)job.wait_ms * 1000000ull : kWaitNs;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int s = 0; s < STG; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
     for (int a = 0; a < NBUF; ++a) { mbar_init(&accf_bar[a], 1); mbar_init(&acce_bar[a], 4); }
     mbar_init(&drain_bar, 1);
     abort_s = 0;
@@ -313,13 +360,14 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      const int npl = job.lowprec ? 2 : NP;   // pieces loaded per operand
+      const int npl = pieces_loaded<FMT>(job);   // pieces loaded per operand
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      int armed[STAGES];
-      uint32_t armed_par[STAGES];
-      for (int s = 0; s < STAGES; ++s) { armed[s] = 0; armed_par[s] = 0; }
+      int armed[STG];
+      uint32_t armed_par[STG];
+      for (int s = 0; s < STG; ++s) { armed[s] = 0; armed_par[s] = 0; }
+      bool skip_first = job.test_skip != 0 && blockIdx.x == 0;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int I, J;
         const int ii = locate(job, t, I, J);
@@ -331,12 +379,18 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
         const int nkb = In.ld / BK;
         for (int term = 0; term < job.nterms && ok; ++term) {
           for (int kb = 0; kb < nkb; ++kb) {
-            if (abort_s || !mbar_wait(&empty_bar[stage], phase ^ 1, globaltimer_ns() + kWaitNs)) {
+            if (abort_s || !mbar_wait(&empty_bar[stage], phase ^ 1, globaltimer_ns() + wait_ns)) {
               ok = false;
               break;
             }
-            uint8_t* sA = smem + stage * STAGE_BYTES;
-            uint8_t* sB = sA + NP * A_PIECE_BYTES;
+            if (skip_first) {   // testing hook: this stage stays unarmed, the MMA thread's wait gives up
+              skip_first = false;
+              armed[stage] = 0;
+              if (++stage == STG) { stage = 0; phase ^= 1; }
+              continue;
+            }
+            uint8_t* sA = smem + stage * SBYTES;
+            uint8_t* sB = sA + NPS * A_PIECE_BYTES;
             mbar_arrive_expect_tx(&full_bar[stage], npl * (A_PIECE_BYTES + B_PIECE_BYTES));
             for (int p = 0; p < npl; ++p)
               tma_load_4d(sA + p * A_PIECE_BYTES, mA, kb * BK, I * BM, p, R.a[term], &full_bar[stage]);
@@ -344,24 +398,21 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
               tma_load_4d(sB + p * B_PIECE_BYTES, mB, kb * BK, J * BN, p, R.b[term], &full_bar[stage]);
             armed[stage] = 1;
             armed_par[stage] = phase;
-            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+            if (++stage == STG) { stage = 0; phase ^= 1; }
           }
         }
       }
       if (!ok) { abort_s = 1; atomicExch(job.err, (int)SP2_ERR_TIMEOUT); }
       // wait (bounded) until every copy issued here has landed
-      for (int s = 0; s < STAGES; ++s)
-        if (armed[s]) mbar_wait(&full_bar[s], armed_par[s], globaltimer_ns() + kWaitNs);
+      for (int s = 0; s < STG; ++s)
+        if (armed[s]) mbar_wait(&full_bar[s], armed_par[s], globaltimer_ns() + wait_ns);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_f32(BM, BN);
-      // piece pairs (a, b) with a + b <= 2, smallest products first; the last three are the
-      // pairs with a + b <= 1 (low-precision jobs)
-      const int pa[6] = {2, 1, 0, 1, 0, 0};
-      const int pb[6] = {0, 1, 2, 0, 1, 0};
-      const int q0 = job.lowprec ? 3 : 0;
+      constexpr uint32_t idesc = idesc_of<FMT>(BM, BN);
+      // the format's piece products, smallest first; low-precision jobs take the tail
+      const int q0 = job.lowprec ? PR::lp_first : 0;
       int stage = 0, buf = 0;
       uint32_t phase = 0, bphase = 0;
       bool ok = true;
@@ -370,30 +421,30 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
         const int ii = locate(job, t, I, J);
         const Instance& In = job.inst[ii];
         if (!resolve(job, In).active) continue;
-        const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job);
+        const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job, In.ld);
         for (int ch = 0; ch < nchunks && ok; ++ch) {
-          if (abort_s || !mbar_wait(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + kWaitNs)) { ok = false; break; }
+          if (abort_s || !mbar_wait(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + wait_ns)) { ok = false; break; }
           tc_fence_after();
           const uint32_t dt = tmem_base + (uint32_t)(buf * BN);
           uint32_t accumulate = 0;
-          for (int kc = 0; kc < chunk_kb(job); ++kc) {
-            if (abort_s || !mbar_wait(&full_bar[stage], phase, globaltimer_ns() + kWaitNs)) { ok = false; break; }
+          for (int kc = 0; kc < chunk_kb(job, In.ld); ++kc) {
+            if (abort_s || !mbar_wait(&full_bar[stage], phase, globaltimer_ns() + wait_ns)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
-            const uint32_t sB = sA + NP * A_PIECE_BYTES;
+            const uint32_t sA = smem_u32(smem + stage * SBYTES);
+            const uint32_t sB = sA + NPS * A_PIECE_BYTES;
             #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
               #pragma unroll
-              for (int q = 0; q < 6; ++q) {
+              for (int q = 0; q < PR::n; ++q) {
                 if (q < q0) continue;
-                const uint64_t ad = smem_desc_sw64(sA + pa[q] * A_PIECE_BYTES + kk * 32);
-                const uint64_t bd = smem_desc_sw64(sB + pb[q] * B_PIECE_BYTES + kk * 32);
+                const uint64_t ad = smem_desc_sw64(sA + PR::a(q) * A_PIECE_BYTES + kk * 32);
+                const uint64_t bd = smem_desc_sw64(sB + PR::b(q) * B_PIECE_BYTES + kk * 32);
                 mma_bf16(dt, ad, bd, idesc, accumulate);
                 accumulate = 1;
               }
             }
             mma_commit(&empty_bar[stage]);
-            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+            if (++stage == STG) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
           mma_commit(&accf_bar[buf]);
@@ -402,7 +453,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
       }
       if (!ok) { abort_s = 1; atomicExch(job.err, (int)SP2_ERR_TIMEOUT); }
       mma_commit(&drain_bar);
-      mbar_wait(&drain_bar, 0, globaltimer_ns() + kWaitNs);
+      mbar_wait(&drain_bar, 0, globaltimer_ns() + wait_ns);
     }
   } else {
     // ---------------- chunk draining + epilogue (warps 2..5) ----------------
@@ -416,7 +467,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
       const Instance& In = job.inst[ii];
       const Resolved R = resolve(job, In);
       if (!R.active) continue;
-      const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job);
+      const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job, In.ld);
       float acc[BN / 32][32];
       #pragma unroll
       for (int g = 0; g < BN / 32; ++g)
@@ -424,7 +475,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
         for (int j = 0; j < 32; ++j) acc[g][j] = 0.f;
       for (int ch = 0; ch < nchunks; ++ch) {
         int got = 0;
-        if (lane == 0) got = !abort_s && mbar_wait(&accf_bar[buf], bphase, globaltimer_ns() + kWaitNs);
+        if (lane == 0) got = !abort_s && mbar_wait(&accf_bar[buf], bphase, globaltimer_ns() + wait_ns);
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) {
           if (lane == 0) { abort_s = 1; atomicExch(job.err, (int)SP2_ERR_TIMEOUT); }
@@ -450,7 +501,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
       const int r = I * BM + 32 * q + lane;
       Partials P = {0.0, 0.0, 0.0};
       #pragma unroll
-      for (int g = 0; g < BN / 32; ++g) epilogue_chunk(job, In, R, r, J * BN + g * 32, acc[g], P);
+      for (int g = 0; g < BN / 32; ++g) epilogue_chunk<FMT>(job, In, R, r, J * BN + g * 32, acc[g], P);
       if (job.mode == MODE_SP2_STEP) {
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -488,10 +539,13 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
 // CTA's `acce` barrier once it has drained a chunk buffer.
 constexpr int P_SMEM_BYTES = STAGES * STAGE_BYTES + 8192 + 1024;   // + alignment and read slack
 
+template <int FMT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gemm_pair_kernel(const Job job) {
+  constexpr int STG = stages_of(FMT), SBYTES = stage_bytes_of(FMT), NPS = np_of(FMT);
+  using PR = Products<FMT>;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[STAGES];
-  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t full_bar[STG];
+  __shared__ __align__(8) uint64_t empty_bar[STG];
   __shared__ __align__(8) uint64_t accf_bar[P_NBUF];
   __shared__ __align__(8) uint64_t acce_bar[P_NBUF];
   __shared__ __align__(8) uint64_t drain_bar;
@@ -500,10 +554,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t wait_ns = job.wait_ms > 0 ? (uint64_t)job.wait_ms * 1000000ull : kWaitNs;
   const uint32_t rank = cluster_ctarank();
   const int pair_id = blockIdx.x >> 1, npairs = gridDim.x >> 1;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int s = 0; s < STG; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
     for (int a = 0; a < P_NBUF; ++a) { mbar_init(&accf_bar[a], 1); mbar_init(&acce_bar[a], 2 * P_EPI_WARPS); }
     mbar_init(&drain_bar, 1);
     abort_s = 0;
@@ -520,13 +575,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
    if (warp == 0) {
     // ---------------- TMA producer (both CTAs) ----------------
     if (lane == 0) {
-      const int npl = job.lowprec ? 2 : NP;   // pieces loaded per operand
+      const int npl = pieces_loaded<FMT>(job);   // pieces loaded per operand
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      int armed[STAGES];
-      uint32_t armed_par[STAGES];
-      for (int s = 0; s < STAGES; ++s) { armed[s] = 0; armed_par[s] = 0; }
+      int armed[STG];
+      uint32_t armed_par[STG];
+      for (int s = 0; s < STG; ++s) { armed[s] = 0; armed_par[s] = 0; }
       for (int t = pair_id; t < ntiles && ok; t += npairs) {
         int I, J;
         const int ii = locate(job, t, I, J);
@@ -540,12 +595,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
         const int rowB = J * PT + (int)rank * BN;
         for (int term = 0; term < job.nterms && ok; ++term) {
           for (int kb = 0; kb < nkb; ++kb) {
-            if (abort_s || !mbar_wait_cluster(&empty_bar[stage], phase ^ 1, globaltimer_ns() + kWaitNs)) {
+            if (abort_s || !mbar_wait_cluster(&empty_bar[stage], phase ^ 1, globaltimer_ns() + wait_ns)) {
               ok = false;
               break;
             }
-            uint8_t* sA = smem + stage * STAGE_BYTES;
-            uint8_t* sB = sA + NP * A_PIECE_BYTES;
+            uint8_t* sA = smem + stage * SBYTES;
+            uint8_t* sB = sA + NPS * A_PIECE_BYTES;
             const uint32_t fb = mapa_shared(smem_u32(&full_bar[stage]), 0);
             if (rank == 0) mbar_arrive_expect_tx(&full_bar[stage], 2 * npl * (A_PIECE_BYTES + B_PIECE_BYTES));
             for (int p = 0; p < npl; ++p)
@@ -554,7 +609,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
               tma_load_4d_pair(sB + p * B_PIECE_BYTES, mB, kb * BK, rowB, p, R.b[term], fb);
             armed[stage] = 1;
             armed_par[stage] = phase;
-            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+            if (++stage == STG) { stage = 0; phase ^= 1; }
           }
         }
       }
@@ -567,16 +622,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
         while (globaltimer_ns() < until) {}
       }
       if (rank == 0)
-        for (int s = 0; s < STAGES; ++s)
-          if (armed[s]) mbar_wait_cluster(&full_bar[s], armed_par[s], globaltimer_ns() + kWaitNs);
+        for (int s = 0; s < STG; ++s)
+          if (armed[s]) mbar_wait_cluster(&full_bar[s], armed_par[s], globaltimer_ns() + wait_ns);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer (even CTA) ----------------
     if (lane == 0 && rank == 0) {
-      const uint32_t idesc = idesc_bf16_f32(2 * BM, PT);
-      const int pa[6] = {2, 1, 0, 1, 0, 0};
-      const int pb[6] = {0, 1, 2, 0, 1, 0};
-      const int q0 = job.lowprec ? 3 : 0;
+      constexpr uint32_t idesc = idesc_of<FMT>(2 * BM, PT);
+      const int q0 = job.lowprec ? PR::lp_first : 0;
       int stage = 0, buf = 0;
       uint32_t phase = 0, bphase = 0;
       bool ok = true;
@@ -585,36 +638,36 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
         const int ii = locate(job, t, I, J);
         const Instance& In = job.inst[ii];
         if (!resolve(job, In).active) continue;
-        const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job);
+        const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job, In.ld);
         for (int ch = 0; ch < nchunks && ok; ++ch) {
-          if (abort_s || !mbar_wait_cluster(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + kWaitNs)) {
+          if (abort_s || !mbar_wait_cluster(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + wait_ns)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t dt = tmem_base + (uint32_t)(buf * PT);
           uint32_t accumulate = 0;
-          for (int kc = 0; kc < chunk_kb(job); ++kc) {
-            if (abort_s || !mbar_wait_cluster(&full_bar[stage], phase, globaltimer_ns() + kWaitNs)) {
+          for (int kc = 0; kc < chunk_kb(job, In.ld); ++kc) {
+            if (abort_s || !mbar_wait_cluster(&full_bar[stage], phase, globaltimer_ns() + wait_ns)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
-            const uint32_t sB = sA + NP * A_PIECE_BYTES;
+            const uint32_t sA = smem_u32(smem + stage * SBYTES);
+            const uint32_t sB = sA + NPS * A_PIECE_BYTES;
             #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
               #pragma unroll
-              for (int q = 0; q < 6; ++q) {
+              for (int q = 0; q < PR::n; ++q) {
                 if (q < q0) continue;
-                const uint64_t ad = smem_desc_sw64(sA + pa[q] * A_PIECE_BYTES + kk * 32);
-                const uint64_t bd = smem_desc_sw64(sB + pb[q] * B_PIECE_BYTES + kk * 32);
+                const uint64_t ad = smem_desc_sw64(sA + PR::a(q) * A_PIECE_BYTES + kk * 32);
+                const uint64_t bd = smem_desc_sw64(sB + PR::b(q) * B_PIECE_BYTES + kk * 32);
                 mma_bf16_pair(dt, ad, bd, idesc, accumulate);
                 accumulate = 1;
               }
             }
             mma_commit_pair_mc(&empty_bar[stage], 0x3);
-            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+            if (++stage == STG) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
           mma_commit_pair_mc(&accf_bar[buf], 0x3);
@@ -623,7 +676,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
       }
       if (!ok) { abort_s = 1; atomicExch(job.err, (int)SP2_ERR_TIMEOUT); }
       mma_commit_pair_mc(&drain_bar, 0x1);
-      mbar_wait_cluster(&drain_bar, 0, globaltimer_ns() + kWaitNs);
+      mbar_wait_cluster(&drain_bar, 0, globaltimer_ns() + wait_ns);
     }
    }
   } else {
@@ -641,7 +694,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
       const Instance& In = job.inst[ii];
       const Resolved R = resolve(job, In);
       if (!R.active) continue;
-      const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job);
+      const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job, In.ld);
       float acc[BN / 32][32];
       #pragma unroll
       for (int g = 0; g < BN / 32; ++g)
@@ -649,7 +702,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
         for (int j = 0; j < 32; ++j) acc[g][j] = 0.f;
       for (int ch = 0; ch < nchunks; ++ch) {
         int got = 0;
-        if (lane == 0) got = !abort_s && mbar_wait_cluster(&accf_bar[buf], bphase, globaltimer_ns() + kWaitNs);
+        if (lane == 0) got = !abort_s && mbar_wait_cluster(&accf_bar[buf], bphase, globaltimer_ns() + wait_ns);
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) {
           if (lane == 0) { abort_s = 1; atomicExch(job.err, (int)SP2_ERR_TIMEOUT); }
@@ -675,7 +728,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
       const int r = I * PT + (int)rank * BM + 32 * q + lane;
       Partials P = {0.0, 0.0, 0.0};
       #pragma unroll
-      for (int g = 0; g < BN / 32; ++g) epilogue_chunk(job, In, R, r, J * PT + hc * BN + g * 32, acc[g], P);
+      for (int g = 0; g < BN / 32; ++g) epilogue_chunk<FMT>(job, In, R, r, J * PT + hc * BN + g * 32, acc[g], P);
       if (job.mode == MODE_SP2_STEP) {
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -722,21 +775,22 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-cudaError_t tc_make_maps(void* arena, int ld, int nslots, CUtensorMap* mapA, CUtensorMap* mapB) {
+cudaError_t tc_make_maps(void* arena, int ld, int nslots, int fmt, CUtensorMap* mapA, CUtensorMap* mapB) {
   auto enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
   if (ld % tc::LD_ALIGN != 0 || (reinterpret_cast<uintptr_t>(arena) & 15) != 0) return cudaErrorInvalidValue;
-  cuuint64_t dims[4] = {(cuuint64_t)ld, (cuuint64_t)ld, (cuuint64_t)tc::NP, (cuuint64_t)nslots};
-  cuuint64_t strides[3] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * ld * 2, (cuuint64_t)tc::NP * ld * ld * 2};
+  const int np = tc::np_of(fmt);
+  const CUtensorMapDataType dt =
+      fmt == tc::FMT_FP16X2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  cuuint64_t dims[4] = {(cuuint64_t)ld, (cuuint64_t)ld, (cuuint64_t)np, (cuuint64_t)nslots};
+  cuuint64_t strides[3] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * ld * 2, (cuuint64_t)np * ld * ld * 2};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   cuuint32_t boxA[4] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM, 1, 1};
   cuuint32_t boxB[4] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BN, 1, 1};
-  CUresult r1 = enc(mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, arena, dims, strides, boxA, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  CUresult r2 = enc(mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, arena, dims, strides, boxB, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r1 = enc(mapA, dt, 4, arena, dims, strides, boxA, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = enc(mapB, dt, 4, arena, dims, strides, boxB, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -751,14 +805,21 @@ static int sm_count() {
   return n;
 }
 
+// The kernel instance for a job: tile kind x piece format.
+static void* kernel_of(int pair, int fmt) {
+  if (pair) return fmt == tc::FMT_FP16X2 ? (void*)tc::tc_gemm_pair_kernel<tc::FMT_FP16X2>
+                                         : (void*)tc::tc_gemm_pair_kernel<tc::FMT_BF16X3>;
+  return fmt == tc::FMT_FP16X2 ? (void*)tc::tc_gemm_kernel<tc::FMT_FP16X2> : (void*)tc::tc_gemm_kernel<tc::FMT_BF16X3>;
+}
+
 static cudaError_t tc_prepare() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(tc::tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tc::SMEM_BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tc::tc_gemm_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             tc::P_SMEM_BYTES);
+  cudaError_t e = cudaSuccess;
+  for (int pair = 0; pair < 2 && e == cudaSuccess; ++pair)
+    for (int fmt = 0; fmt < 2 && e == cudaSuccess; ++fmt)
+      e = cudaFuncSetAttribute(kernel_of(pair, fmt), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               pair ? tc::P_SMEM_BYTES : tc::SMEM_BYTES);
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -773,7 +834,7 @@ static int pair_slots() {
     cfg.blockDim = dim3(tc::P_THREADS);
     cfg.dynamicSmemBytes = tc::P_SMEM_BYTES;
     int c = 0;
-    if (cudaOccupancyMaxActiveClusters(&c, (void*)tc::tc_gemm_pair_kernel, &cfg) != cudaSuccess || c <= 0) {
+    if (cudaOccupancyMaxActiveClusters(&c, kernel_of(1, tc::FMT_BF16X3), &cfg) != cudaSuccess || c <= 0) {
       (void)cudaGetLastError();
       c = sm_count() / 2;
     }
@@ -798,10 +859,16 @@ int tc_tiles(int ld, int upper, int pair) { return pair ? tc::pair_tiles_of(ld, 
 cudaError_t tc_launch(const tc::Job& job, cudaStream_t s) {
   cudaError_t e = tc_prepare();
   if (e != cudaSuccess) return e;
-  if (job.pair)
-    tc::tc_gemm_pair_kernel<<<tc_grid_for(job.total_tiles, 1), tc::P_THREADS, tc::P_SMEM_BYTES, s>>>(job);
-  else
-    tc::tc_gemm_kernel<<<tc_grid_for(job.total_tiles, 0), tc::THREADS, tc::SMEM_BYTES, s>>>(job);
+  const bool f16 = job.fmt == tc::FMT_FP16X2;
+  if (job.pair) {
+    const dim3 g(tc_grid_for(job.total_tiles, 1));
+    if (f16) tc::tc_gemm_pair_kernel<tc::FMT_FP16X2><<<g, tc::P_THREADS, tc::P_SMEM_BYTES, s>>>(job);
+    else tc::tc_gemm_pair_kernel<tc::FMT_BF16X3><<<g, tc::P_THREADS, tc::P_SMEM_BYTES, s>>>(job);
+  } else {
+    const dim3 g(tc_grid_for(job.total_tiles, 0));
+    if (f16) tc::tc_gemm_kernel<tc::FMT_FP16X2><<<g, tc::THREADS, tc::SMEM_BYTES, s>>>(job);
+    else tc::tc_gemm_kernel<tc::FMT_BF16X3><<<g, tc::THREADS, tc::SMEM_BYTES, s>>>(job);
+  }
   return cudaGetLastError();
 }
 
@@ -812,7 +879,7 @@ cudaError_t tc_add_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, c
   tc::Job j = job;
   void* args[] = {&j};
   cudaKernelNodeParams kp = {};
-  kp.func = job.pair ? (void*)tc::tc_gemm_pair_kernel : (void*)tc::tc_gemm_kernel;
+  kp.func = kernel_of(job.pair, job.fmt);
   kp.gridDim = dim3(tc_grid_for(job.total_tiles, job.pair));
   kp.blockDim = dim3(job.pair ? tc::P_THREADS : tc::THREADS);
   kp.sharedMemBytes = job.pair ? tc::P_SMEM_BYTES : tc::SMEM_BYTES;
@@ -824,20 +891,46 @@ cudaError_t tc_add_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, c
 
 extern "C" int32_t sp2_test_tc_gemm(const void* arena_dev, int32_t ld, int32_t nslots, int32_t a_slot,
                                     int32_t b_slot, int32_t upper, int32_t tile, float* out_dev, void* stream) {
+  return sp2_test_tc_gemm_ex(arena_dev, ld, nslots, a_slot, b_slot, upper, tile, 0, 0, out_dev, stream);
+}
+
+// Shared by the product test entries: one launch of the product of slots a and b, status back.
+static int32_t run_test_product(const void* arena_dev, int32_t ld, int32_t nslots, int32_t a_slot, int32_t b_slot,
+                                int32_t upper, int pair, int32_t fmt, int32_t lowprec, int32_t wait_ms,
+                                int32_t test_skip, float* out_dev, cudaStream_t s);
+
+extern "C" int32_t sp2_test_tc_timeout(const void* arena_dev, int32_t ld, int32_t wait_ms, float* out_dev,
+                                       void* stream) {
+  if (!arena_dev || !out_dev || ld <= 0 || ld % sp2::tc::LD_ALIGN != 0 || wait_ms < 1 || wait_ms > 2000)
+    return SP2_ERR_INVALID_ARG;
+  return run_test_product(arena_dev, ld, 1, 0, 0, 0, 0, 0, 0, wait_ms, 1, out_dev, (cudaStream_t)stream);
+}
+
+extern "C" int32_t sp2_test_tc_gemm_ex(const void* arena_dev, int32_t ld, int32_t nslots, int32_t a_slot,
+                                       int32_t b_slot, int32_t upper, int32_t tile, int32_t fmt, int32_t lowprec,
+                                       float* out_dev, void* stream) {
   if (!arena_dev || !out_dev || ld <= 0 || ld % sp2::tc::LD_ALIGN != 0 || nslots <= 0 || a_slot < 0 ||
       b_slot < 0 || a_slot >= nslots || b_slot >= nslots || (upper != 0 && upper != 1) || tile < 0 || tile > 2 ||
-      (tile == 2 && ld % sp2::tc::PT != 0))
+      (tile == 2 && ld % sp2::tc::PT != 0) || fmt < 0 || fmt > 1 || (lowprec != 0 && lowprec != 1))
     return SP2_ERR_INVALID_ARG;
   const int pair = tile == 2 || (tile == 0 && ld % sp2::tc::PT == 0);
-  cudaStream_t s = (cudaStream_t)stream;
+  return run_test_product(arena_dev, ld, nslots, a_slot, b_slot, upper, pair, fmt, lowprec, 0, 0, out_dev,
+                          (cudaStream_t)stream);
+}
+
+static int32_t run_test_product(const void* arena_dev, int32_t ld, int32_t nslots, int32_t a_slot, int32_t b_slot,
+                                int32_t upper, int pair, int32_t fmt, int32_t lowprec, int32_t wait_ms,
+                                int32_t test_skip, float* out_dev, cudaStream_t s) {
   sp2::tc::Instance hinst;
   std::memset(&hinst, 0, sizeof(hinst));
-  if (sp2::tc_make_maps(const_cast<void*>(arena_dev), ld, nslots, &hinst.mapA, &hinst.mapB) != cudaSuccess) {
+  if (sp2::tc_make_maps(const_cast<void*>(arena_dev), ld, nslots, fmt, &hinst.mapA, &hinst.mapB) != cudaSuccess) {
     (void)cudaGetLastError();
     return SP2_ERR_CUDA;
   }
   hinst.arena = (__nv_bfloat16*)const_cast<void*>(arena_dev);
-  hinst.slot_elems = (int64_t)3 * ld * ld;
+  hinst.fmt = fmt;
+  hinst.np = sp2::tc::np_of(fmt);
+  hinst.slot_elems = (int64_t)hinst.np * ld * ld;
   hinst.ld = ld;
   // device copies of the instance record and the error word (test entry point only)
   sp2::tc::Instance* dinst = nullptr;
@@ -856,6 +949,10 @@ extern "C" int32_t sp2_test_tc_gemm(const void* arena_dev, int32_t ld, int32_t n
   j.rule = sp2::tc::SLOTS_FIXED;
   j.count = 1;
   j.pair = pair;
+  j.fmt = fmt;
+  j.lowprec = lowprec;
+  j.wait_ms = wait_ms;
+  j.test_skip = test_skip;
   j.total_tiles = sp2::tc_tiles(ld, upper, pair);
   j.inst = dinst;
   j.a_slot[0] = a_slot;

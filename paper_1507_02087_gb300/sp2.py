@@ -22,7 +22,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA runtime error", 3: "non-finit
           4: "device-side wait timed out", 5: "out of device memory", 6: "no gap (F = cI)",
           7: "unsupported option"}
 STOP_ORDER, STOP_TRACE_GUARD, STOP_EXACT, STOP_CAP, STOP_SCHEDULE = 0, 1, 2, 3, 4
-PRECISIONS = {"fp64": 0, "mixed": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1, "bf16x6": 1, "bf16x3": 2, "fp16x3": 3}
 MAX_ITER = 512
 
 
@@ -75,6 +75,10 @@ def lib() -> ctypes.CDLL:
         L.sp2_status_string.restype = ctypes.c_char_p
         L.sp2_test_tc_gemm.argtypes = [vp, i32, i32, i32, i32, i32, i32, vp, vp]
         L.sp2_test_tc_gemm.restype = i32
+        L.sp2_test_tc_gemm_ex.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp]
+        L.sp2_test_tc_gemm_ex.restype = i32
+        L.sp2_test_tc_timeout.argtypes = [vp, i32, i32, vp, vp]
+        L.sp2_test_tc_timeout.restype = i32
         L.sp2_run_fp64_noalloc.argtypes = [vp, vp, i64, i64, vp, vp]
         L.sp2_run_fp64_noalloc.restype = i32
         L.sp2_set_homo_lumo.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
@@ -243,11 +247,14 @@ def _info_dict(info) -> dict:
 
 
 def sp2_test_tc_gemm(arena, ld: int, nslots: int, a_slot: int, b_slot: int, upper: bool, out,
-                     stream=None, tile: str = "auto") -> None:
-    """Tensor-core product C = A B^T over a bf16 piece arena (see include/sp2_testing.h).
-    tile: "128" (128 x 128 per SM), "pair" (256 x 256 per SM pair) or "auto"."""
-    _check(lib().sp2_test_tc_gemm(arena.data_ptr(), ld, nslots, a_slot, b_slot, 1 if upper else 0,
-                                  TILES[tile], out.data_ptr(), _stream_ptr(stream)), "sp2_test_tc_gemm")
+                     stream=None, tile: str = "auto", fmt: str = "bf16", lowprec: bool = False) -> None:
+    """Tensor-core product C = A B^T over a piece arena (see include/sp2_testing.h).
+    tile: "128" (128 x 128 per SM), "pair" (256 x 256 per SM pair) or "auto"; fmt "bf16"
+    (three bf16 planes per slot) or "fp16" (two fp16 planes of 2^14 x); lowprec: the format's
+    low-precision product."""
+    _check(lib().sp2_test_tc_gemm_ex(arena.data_ptr(), ld, nslots, a_slot, b_slot, 1 if upper else 0,
+                                     TILES[tile], {"bf16": 0, "fp16": 1}[fmt], 1 if lowprec else 0,
+                                     out.data_ptr(), _stream_ptr(stream)), "sp2_test_tc_gemm_ex")
 
 
 def sp2_destroy(h: int) -> None:

@@ -103,3 +103,70 @@ def test_tile_argument_checked(sp2mod):
         sp2mod.sp2_test_tc_gemm(arena, 384, 1, 0, 0, True, out, tile="pair")   # 384 is not a multiple of 256
     sp2mod.sp2_test_tc_gemm(arena, 384, 1, 0, 0, True, out, tile="auto")       # falls back to 128 x 128 tiles
     assert float(out.abs().max()) == 0.0
+
+
+# ---- the fp16 piece format (SP2_PREC_FP16X3) ---------------------------------------------------
+S16 = 2.0 ** 14
+
+
+def pieces16(x32: torch.Tensor) -> torch.Tensor:
+    """S x = p0 + p1 (+ a remainder below p1's last bit), p_i fp16, S = 2^14."""
+    y = x32 * S16
+    p0 = y.half()
+    p1 = (y - p0.float()).half()
+    return torch.stack([p0, p1])
+
+
+def run16(sp2mod, mats, a, b, upper, tile="auto", lowprec=False):
+    ld = mats[0].shape[0]
+    arena = torch.stack([pieces16(m) for m in mats]).contiguous()
+    out = torch.full((ld, ld), float("nan"), dtype=torch.float32, device="cuda")
+    sp2mod.sp2_test_tc_gemm(arena, ld, len(mats), a, b, upper, out, tile=tile, fmt="fp16", lowprec=lowprec)
+    return out, arena
+
+
+def exact16(arena, a, b, lowprec):
+    """The format's product of the stored pieces in FP64 (each piece product is exact)."""
+    P, Q = arena[a].double(), arena[b].double()
+    C = P[0] @ Q[0].T
+    if not lowprec:
+        C = C + P[0] @ Q[1].T + P[1] @ Q[0].T
+    return C / S16 ** 2
+
+
+@pytest.mark.parametrize("tile", ["128", "pair"])
+@pytest.mark.parametrize("ld", [256, 1024, 4096])
+@pytest.mark.parametrize("lowprec", [False, True])
+def test_fp16_format_product(sp2mod, ld, tile, lowprec):
+    g = torch.Generator(device="cpu").manual_seed(300 + ld)
+    A = (torch.rand(ld, ld, generator=g) * 2 - 1).float().cuda()
+    B = ((torch.rand(ld, ld, generator=g) * 2 - 1) * 1e-2).float().cuda()
+    C, arena = run16(sp2mod, [A, B], 0, 1, False, tile, lowprec)
+    assert torch.isfinite(C).all()
+    R = exact16(arena, 0, 1, lowprec)
+    scale = arena[0].double().abs().sum(0) @ arena[1].double().abs().sum(0).T / S16 ** 2
+    # the piece products are exact: only the FP32 accumulation (64-term chunks) remains
+    assert float(((C.double() - R).abs() / scale).max()) < 1e-5
+    # against the FP64 product of the values: 22-bit pieces, three products (2^-21) or one (2^-11)
+    E = A.double() @ B.double().T
+    assert rel(C, E) < (3e-3 if lowprec else 1e-5)
+
+
+@pytest.mark.parametrize("tile", ["128", "pair"])
+def test_fp16_format_symmetric_square_and_subnormal_pieces(sp2mod, tile):
+    # entries down to 1e-9: the low piece of S x is an fp16 subnormal for |x| < 2^-17 and the
+    # leading one for |x| < 2^-28; the tensor cores must multiply them exactly, not flush them
+    ld = 1024
+    g = torch.Generator(device="cpu").manual_seed(11)
+    X = torch.randn(ld, ld, generator=g, dtype=torch.float64)
+    mag = 10.0 ** torch.empty(ld, ld, dtype=torch.float64).uniform_(-9, -5, generator=g)
+    X = (X.sign() * mag)
+    X = ((X + X.T) / 2).float().cuda()
+    C, arena = run16(sp2mod, [X], 0, 0, True, tile)
+    assert torch.equal(C, C.T)
+    R = exact16(arena, 0, 0, False)
+    scale = arena[0].double().abs().sum(0) @ arena[0].double().abs().sum(0).T / S16 ** 2
+    assert float(((C.double() - R).abs() / scale).max()) < 1e-5
+    # without the subnormal low pieces the product would be off by about 2^-11 of its scale
+    R0 = arena[0][0].double() @ arena[0][0].double().T / S16 ** 2
+    assert float(((R0 - R).abs() / scale).max()) > 1e-5

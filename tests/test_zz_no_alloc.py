@@ -3,15 +3,14 @@
 loop where entering the allocator is not allowed).  It keeps its workspace in one
 fixed device array inside the library instead of allocating.
 
-Checked through the C ABI against the regular FP64 entry point (sp2_run with an
-SP2_PREC_FP64 handle), within the FP64 tolerance the other tests use, on two calls in
-a row that share the same workspace.  This file is collected last so that a run that
-stops at the first failure has already run every other test.
+Checked through the C ABI on consecutive calls that share the same workspace, the
+largest allowed size included: against the regular FP64 entry point (sp2_run with an
+SP2_PREC_FP64 handle and default options), which runs the same kernels with the same
+options, so the results must be identical bit for bit; and against the CPU FP64 oracle,
+within the FP64 tolerance the other tests use (1e-10, stop within one iteration), so
+that a fault shared by both GPU entry points is caught too.  This file is collected last
+so that a run that stops at the first failure has already run every other test.
 """
-import ctypes
-import math
-
-import numpy as np
 import pytest
 import torch
 
@@ -39,22 +38,23 @@ def regular(sp2mod, F, nocc):
     return D, info
 
 
-def rel(A, B, nocc):
-    return float(torch.linalg.norm(A - B)) / math.sqrt(max(nocc, 1))
-
-
-def test_noalloc_matches_regular_entry_on_consecutive_calls():
+def test_noalloc_matches_regular_entry_and_oracle_on_consecutive_calls():
+    from oracle import sp2_oracle as o
     from paper_1507_02087_gb300 import sp2
     sp2.lib()
-    # a larger problem first, then a smaller one: the second call reuses the workspace
-    # the first one filled, including the region beyond its own padded size
-    for N, nocc, gap, seed in [(500, 240, 0.05, 21), (200, 90, 0.1, 22)]:
-        F = inputs.dense_gapped(N, nocc, gap=gap, seed=seed).F.cuda()
+    # the largest allowed size first, then smaller ones: each later call reuses the
+    # workspace the earlier ones filled, including the region beyond its own padded size
+    for N, nocc, gap, seed in [(512, 250, 0.05, 20), (500, 240, 0.05, 21), (200, 90, 0.1, 22)]:
+        case = inputs.dense_gapped(N, nocc, gap=gap, seed=seed)
+        F = case.F.cuda()
         Dn, info_n = noalloc(sp2, F, nocc)
         Dr, info_r = regular(sp2, F, nocc)
         assert info_n[0] == 0
-        assert abs(info_n[1] - info_r["n_iter"]) <= 1
-        assert rel(Dn, Dr, nocc) <= TOL_FP64
+        assert info_n[1] == info_r["n_iter"] and info_n[3] == info_r["hist_len"]
+        assert torch.equal(Dn, Dr)
+        ref = o.sp2(case.F.numpy(), nocc)
+        assert abs(info_n[1] - ref.n) <= 1
+        assert o.rel_error(Dn.cpu().numpy(), ref.D, nocc) <= TOL_FP64
 
 
 def test_noalloc_rejects_oversize_and_bad_arguments():
