@@ -27,10 +27,14 @@ Readings where the paper is silent (each also listed in the design notes):
   * a trace tie Tr[X_{i-1}] == nocc takes the `else` branch (2X - X^2), as written.
   * guard G (not in the paper): with eigenvalues in [0,1], x^2 <= x and 2x - x^2 >= x,
     so in exact arithmetic the trace moves strictly down after X^2 and strictly up
-    after 2X - X^2 unless X is already idempotent.  If after forming X_i the trace
-    did not move that way, rounding or truncation dominates and the expansion stops
-    with n = i (reason TRACE_GUARD).  This catches the repeated-polynomial runs that
-    §4.2 (Thm 2) says trace-based selection cannot bound.
+    after 2X - X^2 unless X is already idempotent.  If after forming X_i the trace did not
+    move that way, and the observed convergence order over the last pair has fallen below
+    qtilde (the order test on v_{i-1}, v_{i-3} without the alternation it needs), rounding
+    or truncation dominates and the expansion stops with n = i (reason TRACE_GUARD).  This
+    catches the repeated-polynomial runs that §4.2 (Thm 2) says trace-based selection
+    cannot bound (their error grows, order ~1), and it does not fire while the error still
+    converges, when a systematic rounding bias summed over many converged eigenvalues can
+    outweigh the trace change of the last unconverged ones.
   * a hard iteration cap (reason CAP) is a safety net only.
   * nocc == 0 gives D = 0 and nocc == N gives D = I directly (the definition of D in
     §1); lmax == lmin (F a multiple of I) with 0 < nocc < N has no gap and is an error.
@@ -102,6 +106,12 @@ def mixed_norm(A: np.ndarray, b: int) -> float:
     P[:N, :N] = A
     M = np.sqrt((P.reshape(nb, b, nb, b) ** 2).sum(axis=(1, 3)))
     return float(np.linalg.norm(M, 2))
+
+
+def order_stagnates(v: list, i: int, qtilde: float = QTILDE) -> bool:
+    """The error condition of the trace guard at X_i: the order test on the last pair,
+    log(v_{i-1} / C) / log(v_{i-3}) < qtilde (with its v_{i-3} < 1 and v = 0 rules), i >= 3."""
+    return i >= 3 and order_test_stops(v[i - 1], v[i - 3], qtilde)
 
 
 def order_test_stops(v_i: float, v_im2: float, qtilde: float = QTILDE, C: float = C2_SP) -> bool:
@@ -197,7 +207,8 @@ def sp2(F: np.ndarray, nocc: int, *, bounds: tuple[float, float] | None = None,
             tr_i = float(np.trace(Xi))
         tr.append(tr_i)
         p.append(pi)
-        if guard and ((pi == 1 and tr[i] >= tr_prev) or (pi == 0 and tr[i] <= tr_prev)):
+        if guard and ((pi == 1 and tr[i] >= tr_prev) or (pi == 0 and tr[i] <= tr_prev)) and \
+                order_stagnates(v, i, qtilde):
             return SP2Result(Xi, i, STOP_TRACE_GUARD, lmin, lmax, v, tr, p)
         X2i = Xi @ Xi
         v.append(err(Xi, X2i))
@@ -231,7 +242,8 @@ def sp2_scalar(lams, nocc: int, lmin: float, lmax: float, *, max_iter: int = 200
             xs_new, pi = [2.0 * x - x * x for x in xs], 0
         tr.append(math.fsum(xs_new))
         p.append(pi)
-        if guard and ((pi == 1 and tr[i] >= tr[i - 1]) or (pi == 0 and tr[i] <= tr[i - 1])):
+        if guard and ((pi == 1 and tr[i] >= tr[i - 1]) or (pi == 0 and tr[i] <= tr[i - 1])) and \
+                order_stagnates(v, i, qtilde):
             return xs_new, i, STOP_TRACE_GUARD, v, tr, p
         v.append(vnorm(xs_new))
         if i >= 2 and p[i] != p[i - 1] and order_test_stops(v[i], v[i - 2], qtilde):

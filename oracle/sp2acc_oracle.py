@@ -27,8 +27,9 @@ Readings (also listed in the design notes):
   * the loop condition of Alg. 4 prints "(not converged) and p_i = p_{i-1}"; read as "or":
     with "and" the schedule would end at its first alternation, long before the bounds
     converge.  The first step has no predecessor and never ends the loop.
-  * the trace guard of the plain oracle (x^2 <= x, 2x - x^2 >= x on [0, 1]) holds only for
-    the unscaled polynomials, so it is checked only from n_min on, where a = 1.
+  * the trace guard of the plain oracle (x^2 <= x, 2x - x^2 >= x on [0, 1], with the order over
+    the last pair below qtilde) holds only for the unscaled polynomials, so it is checked only
+    from n_min on, where a = 1.
   * reaching n_max without the order test firing ends the run with D = X_{n_max}
     (reason STOP_SCHEDULE).
   * outer bounds beyond the spectral bounds (homo_out < lmin, lumo_out > lmax) are clamped
@@ -160,7 +161,8 @@ def sp2_acc(F: np.ndarray, nocc: int, homo_out: float, homo_in: float, lumo_in: 
         Xi = stored(i, apply_step(X, pi, sched.alpha[i]))
         tr.append(float(np.trace(Xi)))
         p.append(pi)
-        if guard and i >= sched.n_min and ((pi == 1 and tr[i] >= tr[i - 1]) or (pi == 0 and tr[i] <= tr[i - 1])):
+        if guard and i >= sched.n_min and ((pi == 1 and tr[i] >= tr[i - 1]) or (pi == 0 and tr[i] <= tr[i - 1])) \
+                and o.order_stagnates(v, i, qtilde):
             return o.SP2Result(Xi, i, o.STOP_TRACE_GUARD, lmin, lmax, v, tr, p)
         X2i = Xi @ Xi
         v.append(err(Xi, X2i))
@@ -188,7 +190,8 @@ def sp2_acc_scalar(lams, nocc: int, lmin: float, lmax: float, sched: Schedule, *
         xs_new = [y * y for y in ys] if pi == 1 else [2.0 * y - y * y for y in ys]
         tr.append(math.fsum(xs_new))
         p.append(pi)
-        if guard and i >= sched.n_min and ((pi == 1 and tr[i] >= tr[i - 1]) or (pi == 0 and tr[i] <= tr[i - 1])):
+        if guard and i >= sched.n_min and ((pi == 1 and tr[i] >= tr[i - 1]) or (pi == 0 and tr[i] <= tr[i - 1])) \
+                and o.order_stagnates(v, i, qtilde):
             return xs_new, i, o.STOP_TRACE_GUARD, p
         v.append(vnorm(xs_new))
         if i >= max(2, sched.n_min) and p[i] != p[i - 1] and o.order_test_stops(v[i], v[i - 2], qtilde):

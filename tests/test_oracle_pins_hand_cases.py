@@ -94,8 +94,8 @@ def round_fp32(r: Fraction) -> Fraction:
 
 def scalar_fp32(x0s, nocc, trace_rule, max_iter=200):
     """SP2 on the eigenvalues with each new value rounded once to FP32 (exact rational
-    arithmetic otherwise): p from the trace, the trace guard, and the order test on
-    v_i = sqrt(sum (x - x^2)^2)."""
+    arithmetic otherwise): p from the trace, the trace guard (trace moved the wrong way and the
+    order test holds on v_{i-1}, v_{i-3}), and the order test on v_i = sqrt(sum (x - x^2)^2)."""
     xs = [Fraction(x) for x in x0s]
     v = [math.sqrt(float(sum((x - x * x) ** 2 for x in xs)))]
     tr = [float(sum(xs))]
@@ -110,7 +110,8 @@ def scalar_fp32(x0s, nocc, trace_rule, max_iter=200):
             t_prev, t_i = float(sum(xs)), float(s2 if pi else 2 * sum(xs) - s2)
         tr.append(t_i)
         p.append(pi)
-        if (pi == 1 and t_i >= t_prev) or (pi == 0 and t_i <= t_prev):
+        if ((pi == 1 and t_i >= t_prev) or (pi == 0 and t_i <= t_prev)) and i >= 3 and \
+                o.order_test_stops(v[i - 1], v[i - 3]):
             return new, i, o.STOP_TRACE_GUARD, p
         v.append(math.sqrt(float(sum((x - x * x) ** 2 for x in new))))
         if i >= 2 and p[i] != p[i - 1] and o.order_test_stops(v[i], v[i - 2]):
