@@ -130,6 +130,10 @@ typedef struct {
                            handles only (SP2, SP2-ACC and McWeeny), SP2_ERR_UNSUPPORTED elsewhere.
                            sp2_info.v holds the measure used.  Block-sparse handles take 0 or 1
                            (the mixed norm with the 32 x 32 blocks; see sp2_create_bsr) */
+  int32_t bsr_cuda_cores; /* block-sparse handles: 0 = block products on the tcgen05 tensor cores
+                           (default; each block also kept as two fp16 pieces, see sp2_create_bsr);
+                           1 = FP32 block products on the CUDA cores (one fused multiply-add per
+                           term in increasing K, then k).  Ignored by dense handles */
 } sp2_opts;
 
 #define SP2_MAX_ITER 512
@@ -283,7 +287,13 @@ typedef enum {
 } sp2_trunc_rule;
 
 /* N: a multiple of 32, at most 65536.  tau >= 0 (0 keeps every stored block).  opts as
- * for sp2_create (corrections, refine_steps and refine_fp64 are ignored); opts.norm 0 (v_i)
+ * for sp2_create (corrections, refine_steps and refine_fp64 are ignored).  Block products
+ * (opts.bsr_cuda_cores = 0, the default): the square is cut into tiles of 4 x 8 blocks
+ * (128 x 256) holding an upper pair of its pattern; each tile is the sum over the K blocks its
+ * rows and columns hold of tcgen05 products of the blocks kept as two fp16 pieces of 2^14 x
+ * (three piece products, FP32 accumulation in chunks of 4 K blocks, the FP32 iterate and its
+ * epilogue as before); an absent block within a tile is the zero block.  Workspace: 4 KB more
+ * per block of (N/32)^2 + 1 per iterate.  opts.norm 0 (v_i)
  * or 1 (the mixed norm m_i with the 32 x 32 blocks, estimated after every square by 32
  * Lanczos steps on the (N/32) x (N/32) matrix of block norms of X - X^2, the pairing of the
  * paper's §6 calculations with SP2_TRUNC_MIXED); 2 is SP2_ERR_UNSUPPORTED.  Workspace is
@@ -321,11 +331,14 @@ sp2_status sp2_get_info_bsr(sp2_bsr h, sp2_info* out, int64_t* nnzb_out);
 void sp2_destroy_bsr(sp2_bsr h);
 
 /* Work of the last run's squares (waits for the run): *block_products = 32 x 32 block
- * products X_IK X_JK^T formed (each 2 * 32^3 flops), *square_blocks = upper blocks of the
- * squares computed, *numeric_ms = summed device time of the numeric-square launches from
- * CUDA events around each launch (launch_mode 1 only; 0 with the graph).  All 0 before the
- * first run. */
-sp2_status sp2_get_work_bsr(sp2_bsr h, int64_t* block_products, int64_t* square_blocks, double* numeric_ms);
+ * products X_IK X_JK^T executed (each 2 * 32^3 flops; the tensor-core kernel also multiplies
+ * the zero blocks that fill its 4 x 8-block tiles), *needed_products = those with both factors
+ * stored and output block J >= I (the sparse square's own work; equal to *block_products on
+ * FP32 CUDA cores), *square_blocks = upper blocks of the squares computed, *numeric_ms =
+ * summed device time of the numeric-square launches from CUDA events around each launch
+ * (launch_mode 1 only; 0 with the graph).  All 0 before the first run. */
+sp2_status sp2_get_work_bsr(sp2_bsr h, int64_t* block_products, int64_t* needed_products,
+                            int64_t* square_blocks, double* numeric_ms);
 
 /* FP64 purification that allocates no memory (the paper has no counterpart; this is a
  * service for callers that cannot call cudaMalloc, e.g. code running under another

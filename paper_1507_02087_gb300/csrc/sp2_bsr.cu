@@ -38,38 +38,14 @@
 #include "sp2_common.cuh"
 #include "sp2_kernels.h"
 
+#include "sp2_bsr.cuh"
+#include "sp2_tc.cuh"
+
 namespace sp2 {
 namespace bsr {
 
-constexpr int B = 32;              // block size
-constexpr int BE = B * B;          // elements per block
 constexpr int NT = 256;            // threads of the block kernels
 constexpr int MAX_NB = 2048;       // block rows (N <= 65536)
-
-__device__ __forceinline__ int popc(uint32_t x) { return __popc(x); }
-
-struct Mat {          // one block-sparse iterate
-  int* rp;            // [nb + 1]
-  int* ci;            // [cap]
-  float* vals;        // [cap][32][32]
-  uint32_t* bits;     // [nb][W]
-  int* rank;          // [nb][W]: set bits of the row in words before w
-};
-
-struct Pairs {        // upper (I, J >= I) block pairs of a pattern
-  int* ptr;           // [nb + 1]
-  int* col;           // [cap]
-  int* row;           // [cap]
-  int* nnz;           // device count
-};
-
-// Position of block (I, K) in `m`, or -1 if absent.
-__device__ __forceinline__ int find_block(const Mat& m, int W, int I, int K) {
-  const uint32_t w = m.bits[(int64_t)I * W + (K >> 5)];
-  const uint32_t bit = 1u << (K & 31);
-  if (!(w & bit)) return -1;
-  return m.rp[I] + m.rank[(int64_t)I * W + (K >> 5)] + popc(w & (bit - 1u));
-}
 
 // ---- generic bitmap / pattern kernels ----------------------------------------------------
 __global__ void clear_words_kernel(uint32_t* bits, int64_t n, const DevState* st) {
@@ -245,7 +221,7 @@ bsr_init_kernel(DevState* st, const int* rp, const int* ci, const double* vals, 
     st->dk = 0; st->k = 0; st->done = 0; st->n_out = 0; st->reason = SP2_STOP_EXACT;
     st->status = SP2_OK; st->out_buf = 0; st->out_mode = OUT_COPY; st->hist_len = 0;
     st->tr[0] = 0.0; st->p[0] = 0; st->iter_active = 1;
-    st->bprod = 0ull; st->sblocks = 0ull;
+    st->bprod = 0ull; st->sblocks = 0ull; st->uprod = 0ull;
     if (s_bad) { st->status = SP2_ERR_NONFINITE; st->done = 1; st->out_mode = OUT_NAN; }
     else if (nocc == 0) { st->done = 1; st->out_mode = OUT_ZERO; }
     else if (nocc == N) { st->done = 1; st->out_mode = OUT_IDENTITY; }
@@ -455,7 +431,10 @@ bsr_numeric_kernel(DevState* st, Mat X, int W, Pairs P, float* svals, uint8_t* s
       product_tile(wbuf, (items - 1) & 1, rg, cg, acc2);
       __syncwarp();
     }
-    if (lane == 0) atomicAdd(&st->bprod, (unsigned long long)(items / 2));
+    if (lane == 0) {
+      atomicAdd(&st->bprod, (unsigned long long)(items / 2));
+      atomicAdd(&st->uprod, (unsigned long long)(items / 2));   // every product formed is needed
+    }
     float acc[4][8];
     #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -854,10 +833,120 @@ fill_next_kernel(const DevState* st, Pairs P, const uint8_t* skeep, const float*
     const float* src = svals + (int64_t)q * BE;
     for (int e = threadIdx.x; e < BE; e += NT) {
       const float v = src[e];
+      const int64_t et = (e % B) * B + e / B;
       Y.vals[(int64_t)pij * BE + e] = v;
-      if (I != J) Y.vals[(int64_t)pji * BE + (e % B) * B + e / B] = v;
+      if (I != J) Y.vals[(int64_t)pji * BE + et] = v;
+      if (Y.pvals) {   // the fp16 pieces of 2^14 v, the tensor-core operands
+        __half p0, p1;
+        tc::split_fp16x2(v, p0, p1);
+        Y.pvals[(int64_t)pij * 2 * BE + e] = p0;
+        Y.pvals[(int64_t)pij * 2 * BE + BE + e] = p1;
+        if (I != J) {
+          Y.pvals[(int64_t)pji * 2 * BE + et] = p0;
+          Y.pvals[(int64_t)pji * 2 * BE + BE + et] = p1;
+        }
+      }
     }
   }
+}
+
+// ---- tile list of the tensor-core square ------------------------------------------------------
+// Tile (g, c) = block rows 4 g .. 4 g + 3, block columns 8 c .. 8 c + 7; listed when one of its
+// rows holds an upper pair of the square's pattern in its columns.
+__device__ __forceinline__ bool tile_active(const uint32_t* sbits, int nb, int W, int g, int c) {
+  bool act = false;
+  for (int r = 0; r < TTR; ++r) {
+    const int I = g * TTR + r;
+    if (I >= nb) break;
+    const uint32_t word = sbits[(int64_t)I * W + ((c * TTC) >> 5)];
+    act |= ((word >> ((c * TTC) & 31)) & 0xFFu) != 0u;
+  }
+  return act;
+}
+
+__global__ void tile_count_kernel(const DevState* st, const uint32_t* sbits, int nb, int W, int ncg, int* counts) {
+  if (!st->iter_active) return;
+  const int g = blockIdx.x;
+  int n = 0;
+  for (int c = threadIdx.x; c < ncg; c += 32) n += tile_active(sbits, nb, W, g, c) ? 1 : 0;
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if (threadIdx.x == 0) counts[g] = n;
+}
+
+__global__ void tile_fill_kernel(const DevState* st, const uint32_t* sbits, int nb, int W, int ncg, const int* tptr,
+                                 int* tiles) {
+  if (!st->iter_active) return;
+  const int g = blockIdx.x, lane = threadIdx.x;
+  int pos = tptr[g];
+  for (int c0 = 0; c0 < ncg; c0 += 32) {
+    const int c = c0 + lane;
+    const bool act = c < ncg && tile_active(sbits, nb, W, g, c);
+    const uint32_t m = __ballot_sync(0xffffffffu, act);
+    if (act) tiles[pos + __popc(m & ((1u << lane) - 1u))] = g * ncg + c;
+    pos += __popc(m);
+  }
+}
+
+// Per listed tile (one warp): the K-block count (the K some tile row and some tile column both
+// hold, from the OR of the rows' bitmap words), and for block pair (r, c) = lane / 8, lane % 8 the
+// pair index and the old block's position.
+__global__ void tile_meta_kernel(const DevState* st, Mat X, Pairs P, const uint32_t* sbits, int nb, int W, int ncg,
+                                 const int* tiles, const int* tnnz, int* meta) {
+  if (!st->iter_active) return;
+  const int lane = threadIdx.x & 31;
+  const int nt = *tnnz;
+  for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt; t += gridDim.x * (blockDim.x >> 5)) {
+    const int code = tiles[t];
+    const int I0 = (code / ncg) * TTR, J0 = (code % ncg) * TTC;
+    const int rowj = lane < TTR ? I0 + lane : J0 + (lane - TTR);
+    const bool vj = lane < TTR + TTC && rowj < nb;
+    int nk = 0;
+    for (int w = 0; w < W; ++w) {
+      const uint32_t bj = vj ? X.bits[(int64_t)rowj * W + w] : 0u;
+      const uint32_t a = __reduce_or_sync(0xffffffffu, lane < TTR ? bj : 0u);
+      const uint32_t b = __reduce_or_sync(0xffffffffu, lane >= TTR && lane < TTR + TTC ? bj : 0u);
+      nk += __popc(a & b);
+    }
+    const int I = I0 + lane / TTC, J = J0 + lane % TTC;
+    int qi = -1, po = -1;
+    if (I < nb && J < nb) {
+      po = find_block(X, W, I, J);
+      if (J >= I) {
+        const uint32_t sw = sbits[(int64_t)I * W + (J >> 5)];
+        if ((sw >> (J & 31)) & 1u) {
+          int cnt = P.ptr[I] + __popc(sw & ((1u << (J & 31)) - 1u));
+          for (int w = 0; w < (J >> 5); ++w) cnt += __popc(sbits[(int64_t)I * W + w]);
+          qi = cnt;
+        }
+      }
+    }
+    int* m = meta + (int64_t)t * TMETA;
+    if (lane == 0) m[0] = nk;
+    m[1 + lane] = qi;
+    m[33 + lane] = po;
+  }
+}
+
+// SMs of the current device (queried once, before any stream capture; see build_graph)
+static int meta_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+cudaError_t tc_tiles_launch(const DevState* st, const Mat& X, const Pairs& P, const uint32_t* sbits, int nb, int W,
+                            int* counts, int* tptr, int* tnnz, int* tiles, int* meta, cudaStream_t s) {
+  const int ng = (nb + TTR - 1) / TTR, ncg = (nb + TTC - 1) / TTC;
+  tile_count_kernel<<<ng, 32, 0, s>>>(st, sbits, nb, W, ncg, counts);
+  scan_kernel<<<1, 1024, 0, s>>>(counts, ng, tptr, tnnz, st);
+  tile_fill_kernel<<<ng, 32, 0, s>>>(st, sbits, nb, W, ncg, tptr, tiles);
+  tile_meta_kernel<<<4 * meta_sms(), 256, 0, s>>>(st, X, P, sbits, nb, W, ncg, tiles, tnnz, meta);
+  return cudaGetLastError();
 }
 
 // dense FP64 output (N x N, leading dimension N) from the iterate the stop test chose
@@ -926,6 +1015,13 @@ struct sp2_bsr_ctx {
   int nrounds = 0;               // numeric launches recorded in the last run
   cudaStream_t last = nullptr;
   bool ran = false;
+  // tensor-core block products (opts.bsr_cuda_cores == 0)
+  bool tc = false;
+  TcMaps* maps_dev = nullptr;    // TMA maps over X[0].pvals and X[1].pvals
+  int* tiles = nullptr;          // [ceil(nb/4) * ceil(nb/8)]
+  int* tptr = nullptr;           // [ceil(nb/4) + 1]
+  int* tnnz = nullptr;
+  int* meta = nullptr;           // [ceil(nb/4) * ceil(nb/8)][TMETA]
 };
 
 #define BSR_TRY(expr)                              \
@@ -946,8 +1042,9 @@ static void bsr_free(sp2_bsr_ctx* h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   for (int p = 0; p < 2; ++p) {
     cudaFree(h->X[p].rp); cudaFree(h->X[p].ci); cudaFree(h->X[p].vals); cudaFree(h->X[p].bits);
-    cudaFree(h->X[p].rank);
+    cudaFree(h->X[p].rank); cudaFree(h->X[p].pvals);
   }
+  cudaFree(h->maps_dev); cudaFree(h->tiles); cudaFree(h->tptr); cudaFree(h->tnnz); cudaFree(h->meta);
   cudaFree(h->S.ptr); cudaFree(h->S.col); cudaFree(h->S.row); cudaFree(h->S.nnz);
   cudaFree(h->FP.ptr); cudaFree(h->FP.col); cudaFree(h->FP.row); cudaFree(h->FP.nnz);
   cudaFree(h->sbits); cudaFree(h->svals); cudaFree(h->skeep); cudaFree(h->spart); cudaFree(h->sn2);
@@ -1018,10 +1115,26 @@ static cudaError_t add_round(sp2_bsr_ctx* h, cudaGraph_t g, cudaStream_t s, int 
   scan_kernel<<<1, 1024, 0, s>>>(h->counts, nb, h->S.ptr, sn, st);
   fill_pairs_kernel<<<nb, 32, 0, s>>>(h->sbits, nb, W, up, h->S, st);
   // 2. numeric + 3. stop test
+  if (h->tc) tc_tiles_launch(st, Xc, h->S, h->sbits, nb, W, h->counts, h->tptr, h->tnnz, h->tiles, h->meta, s);
   const bool timed = !use_cond && h->nev && h->nrounds < h->opts.max_iter + 4;
   if (timed) cudaEventRecord(h->nev[2 * h->nrounds], s);
-  bsr_numeric_kernel<<<numeric_grid(), NUM_THREADS, NUM_SMEM, s>>>(st, Xc, W, h->S, h->svals, h->skeep, h->spart,
-                                                                  h->sn2, tau2);
+  if (h->tc) {
+    TcRound r;
+    r.sbits = h->sbits;
+    r.P = h->S;
+    r.svals = h->svals;
+    r.skeep = h->skeep;
+    r.spart = h->spart;
+    r.sn2 = h->sn2;
+    r.tau2 = tau2;
+    r.tiles = h->tiles;
+    r.tnnz = h->tnnz;
+    r.meta = h->meta;
+    tc_numeric_launch(st, Xc, h->maps_dev, parity, nb, W, r, s);
+  } else {
+    bsr_numeric_kernel<<<numeric_grid(), NUM_THREADS, NUM_SMEM, s>>>(st, Xc, W, h->S, h->svals, h->skeep,
+                                                                    h->spart, h->sn2, tau2);
+  }
   if (timed) cudaEventRecord(h->nev[2 * h->nrounds++ + 1], s);
   if (h->lz) launch_lanczos_pairs(st, h->S.row, h->S.col, sn, h->spart, h->lz, nb, h->lzld, s);
   bsr_finalize_kernel<<<1, 1024, 0, s>>>(st, h->spart, sn, h->cond, use_cond);
@@ -1054,6 +1167,8 @@ static sp2_status build_graph(sp2_bsr_ctx* h) {
   cudaGraph_t body = np.conditional.phGraph_out[0];
   (void)grid_persistent();   // device queries before capture
   (void)numeric_grid();
+  (void)meta_sms();
+  tc_prepare();
   cudaStream_t cs;
   BSR_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
@@ -1086,7 +1201,7 @@ extern "C" sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, in
   if (o.max_iter < 1 || o.max_iter > SP2_MAX_ITER || !(o.qtilde > 0.0) || (o.guard != 0 && o.guard != 1) ||
       (o.launch_mode != 0 && o.launch_mode != 1))
     return SP2_ERR_INVALID_ARG;
-  if (o.norm < 0 || o.norm > 2) return SP2_ERR_INVALID_ARG;
+  if (o.norm < 0 || o.norm > 2 || (o.bsr_cuda_cores != 0 && o.bsr_cuda_cores != 1)) return SP2_ERR_INVALID_ARG;
   if (o.norm == 2) return SP2_ERR_UNSUPPORTED;       // v_i or the mixed norm m_i (32 x 32 blocks)
   sp2_bsr_ctx* h = new (std::nothrow) sp2_bsr_ctx();
   if (!h) return SP2_ERR_NOMEM;
@@ -1128,6 +1243,26 @@ extern "C" sp2_status sp2_create_bsr_ex(int64_t N, int64_t n_occ, double tau, in
        cudaMallocHost(&h->st_host, sizeof(DevState)) == cudaSuccess &&
        cudaMallocHost(&h->xnnz_host, sizeof(int)) == cudaSuccess &&
        cudaEventCreate(&h->ev[0]) == cudaSuccess && cudaEventCreate(&h->ev[1]) == cudaSuccess;
+  h->tc = o.bsr_cuda_cores == 0;
+  if (ok && h->tc) {
+    const int ng = (nb + TTR - 1) / TTR, ncg = (nb + TTC - 1) / TTC;
+    const size_t pbytes = sizeof(__half) * 2 * BE * (size_t)(h->cap + 1);
+    for (int p = 0; p < 2 && ok; ++p)
+      ok = cudaMalloc(&h->X[p].pvals, pbytes) == cudaSuccess &&
+           cudaMemset(h->X[p].pvals, 0, pbytes) == cudaSuccess;   // block `cap` stays zero
+    ok = ok && cudaMalloc(&h->maps_dev, sizeof(TcMaps)) == cudaSuccess &&
+         cudaMalloc(&h->tiles, sizeof(int) * (size_t)ng * ncg) == cudaSuccess &&
+         cudaMalloc(&h->tptr, sizeof(int) * (ng + 1)) == cudaSuccess &&
+         cudaMalloc(&h->tnnz, sizeof(int)) == cudaSuccess &&
+         cudaMalloc(&h->meta, sizeof(int) * TMETA * (size_t)ng * ncg) == cudaSuccess;
+    if (ok) {
+      TcMaps m;
+      std::memset(&m, 0, sizeof(m));
+      ok = tc_piece_map(h->X[0].pvals, h->cap, &m.map[0]) == cudaSuccess &&
+           tc_piece_map(h->X[1].pvals, h->cap, &m.map[1]) == cudaSuccess &&
+           cudaMemcpy(h->maps_dev, &m, sizeof(m), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+  }
   if (ok && rule == SP2_TRUNC_MIXED) ok = cudaMalloc(&h->mixscr, mixctl_scratch_bytes(nb)) == cudaSuccess;
   if (ok && o.norm == 1) {
     h->lzld = (nb + 63) / 64 * 64;
@@ -1181,11 +1316,12 @@ extern "C" int32_t sp2_set_homo_lumo_bsr(sp2_bsr h, const double* bounds) {
   return r;
 }
 
-extern "C" sp2_status sp2_get_work_bsr(sp2_bsr h, int64_t* block_products, int64_t* square_blocks,
-                                       double* numeric_ms) {
-  if (!h || !block_products || !square_blocks || !numeric_ms) return SP2_ERR_INVALID_ARG;
+extern "C" sp2_status sp2_get_work_bsr(sp2_bsr h, int64_t* block_products, int64_t* needed_products,
+                                       int64_t* square_blocks, double* numeric_ms) {
+  if (!h || !block_products || !needed_products || !square_blocks || !numeric_ms) return SP2_ERR_INVALID_ARG;
   if (h->ran) BSR_TRY(cudaStreamSynchronize(h->last));
   *block_products = h->ran ? (int64_t)h->st_host->bprod : 0;
+  *needed_products = h->ran ? (int64_t)h->st_host->uprod : 0;
   *square_blocks = h->ran ? (int64_t)h->st_host->sblocks : 0;
   double tot = 0.0;
   for (int r = 0; h->ran && h->nev && r < h->nrounds; ++r) {

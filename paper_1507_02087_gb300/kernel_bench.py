@@ -38,6 +38,10 @@ def main():
                     help="time the block-sparse squares instead, on the gapped tight-binding lattice of these "
                          "dimensions (LX = 32), tau 1e-4, stream launches")
     ap.add_argument("--rule", default="error", choices=["error", "block", "mixed"])
+    ap.add_argument("--products", default="tensor", choices=["tensor", "cuda"],
+                    help="--bsr: block products on the tensor cores (fp16x3) or FP32 CUDA cores")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "bf16x6", "bf16x3", "fp16x3"],
+                    help="--sp2: the tensor-core precision mode of the handle")
     a = ap.parse_args()
     if a.sp2:
         return sp2_forward(a)
@@ -79,7 +83,7 @@ def sp2_forward(a):
     case = inputs.dense_gapped(N, N // 2, gap=0.01, seed=0, device="cuda", want_exact=False)
     F = case.F
     D = torch.empty_like(F)
-    with sp2.Purifier(N, N // 2, "mixed", corrections=0, refine_steps=0, launch_mode=1, tile=a.tile) as P:
+    with sp2.Purifier(N, N // 2, a.precision, corrections=0, refine_steps=0, launch_mode=1, tile=a.tile) as P:
         P.run(F, D)
         per = []
         for _ in range(a.reps):
@@ -88,9 +92,11 @@ def sp2_forward(a):
             per.append(fi["loop_ms"] / fi["hist_len"])
         info = P.info()
     ms = min(per)
-    print(json.dumps({"ld": N, "mode": "sp2_forward", "tile": a.tile, "squares": int(info["hist_len"]),
-                      "ms_per_square_incl_stop_test": ms,
-                      "algorithmic_tflops": 6 * N * N * (N + 1) / (ms * 1e-3) / 1e12}))
+    products = {"mixed": 6, "bf16x6": 6, "bf16x3": 3, "fp16x3": 3}[a.precision]
+    print(json.dumps({"ld": N, "mode": "sp2_forward", "tile": a.tile, "precision": a.precision,
+                      "squares": int(info["hist_len"]), "ms_per_square_incl_stop_test": ms,
+                      "executed_tflops": products * N * N * (N + 1) / (ms * 1e-3) / 1e12,
+                      "useful_tflops": N * N * (N + 1) / (ms * 1e-3) / 1e12}))
 
 
 def bsr_squares(a):
@@ -100,14 +106,17 @@ def bsr_squares(a):
     dims = tuple(int(x) for x in a.bsr.split(","))
     tb = inputs.tight_binding(dims=dims)
     rp, ci, vals = (torch.from_numpy(x).cuda() for x in tb.bsr(32))
-    with sp2.BsrPurifier(tb.N, tb.nocc, 1e-4, rule=a.rule, launch_mode=1,
+    with sp2.BsrPurifier(tb.N, tb.nocc, 1e-4, rule=a.rule, launch_mode=1, products=a.products,
                          norm="mixed" if a.rule == "mixed" else "fro") as P:
         for _ in range(max(1, a.reps)):
             P.run(rp, ci, vals, dense=False)
         w = P.info()
-    print(json.dumps({"N": tb.N, "dims": dims, "rule": a.rule, "n_iter": w["n_iter"], "nnzb_D": w["nnzb"],
-                      "block_products": w["block_products"], "numeric_ms": w["numeric_ms"],
-                      "tflops": 2 * 32 ** 3 * w["block_products"] / (w["numeric_ms"] * 1e-3) / 1e12,
+    sec = w["numeric_ms"] * 1e-3
+    print(json.dumps({"N": tb.N, "dims": dims, "rule": a.rule, "products": a.products, "n_iter": w["n_iter"],
+                      "nnzb_D": w["nnzb"], "block_products": w["block_products"],
+                      "needed_products": w["needed_products"], "numeric_ms": w["numeric_ms"],
+                      "executed_tflops": 2 * 32 ** 3 * w["block_products"] / sec / 1e12,
+                      "useful_tflops": 2 * 32 ** 3 * w["needed_products"] / sec / 1e12,
                       "loop_ms": w["loop_ms"]}))
 
 

@@ -36,7 +36,8 @@ class sp2_opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("guard", ctypes.c_int32), ("qtilde", ctypes.c_double),
                 ("corrections", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
                 ("refine_fp64", ctypes.c_int32), ("launch_mode", ctypes.c_int32),
-                ("history", ctypes.c_int32), ("tile", ctypes.c_int32), ("norm", ctypes.c_int32)]
+                ("history", ctypes.c_int32), ("tile", ctypes.c_int32), ("norm", ctypes.c_int32),
+                ("bsr_cuda_cores", ctypes.c_int32)]
 
 
 class sp2_info(ctypes.Structure):
@@ -105,7 +106,8 @@ def lib() -> ctypes.CDLL:
         L.sp2_run_bsr.restype = i32
         L.sp2_get_info_bsr.argtypes = [vp, ctypes.POINTER(sp2_info), ctypes.POINTER(i64)]
         L.sp2_get_info_bsr.restype = i32
-        L.sp2_get_work_bsr.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
+        L.sp2_get_work_bsr.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                       ctypes.POINTER(ctypes.c_double)]
         L.sp2_get_work_bsr.restype = i32
         L.sp2_destroy_bsr.argtypes = [vp]
         L.sp2_destroy_bsr.restype = None
@@ -140,16 +142,17 @@ def _stream_ptr(stream) -> int:
 
 
 TILES = {"auto": 0, "128": 1, "pair": 2}
+PRODUCT_UNITS = {"tensor": 0, "cuda": 1}     # block-sparse handles: tensor-core or FP32 CUDA-core block products
 NORMS = {"fro": 0, "mixed": 1, "spectral": 2}
 HISTORY = {"auto": 0, "full": 1, "recompute": 2}
 
 
 def _opts(max_iter, guard, qtilde, corrections, refine_steps, refine_fp64, launch_mode, history="auto",
-          tile="auto", norm="fro"):
+          tile="auto", norm="fro", products="tensor"):
     if launch_mode is None:
         launch_mode = int(os.environ.get("SP2_LAUNCH_MODE", "0"))
     return sp2_opts(max_iter, 1 if guard else 0, qtilde, corrections, refine_steps, int(refine_fp64),
-                    launch_mode, HISTORY[history], TILES[tile], NORMS[norm])
+                    launch_mode, HISTORY[history], TILES[tile], NORMS[norm], PRODUCT_UNITS[products])
 
 
 def sp2_create(N: int, nocc: int, precision: str = "fp64", *, max_iter: int = 200, guard: bool = True,
@@ -268,11 +271,13 @@ TRUNC_RULES = {"block": 0, "error": 1, "mixed": 2}
 class BsrPurifier:
     """Block-sparse F (32 x 32 blocks, BSR) -> D with block truncation tau.
     rule: "block" (drop blocks with norm below tau), "error" (||E||_F <= tau) or "mixed"
-    (||E||_M <= tau); norm: "fro" (stop on v_i) or "mixed" (m_i with the 32 x 32 blocks)."""
+    (||E||_M <= tau); norm: "fro" (stop on v_i) or "mixed" (m_i with the 32 x 32 blocks);
+    products: "tensor" (tcgen05 block products, default) or "cuda" (FP32 CUDA cores)."""
 
     def __init__(self, N: int, nocc: int, tau: float, max_iter: int = 200, guard: bool = True,
-                 qtilde: float = 1.8, launch_mode: int | None = None, rule: str = "block", norm: str = "fro"):
-        o = _opts(max_iter, guard, qtilde, 1, 0, False, launch_mode, norm=norm)
+                 qtilde: float = 1.8, launch_mode: int | None = None, rule: str = "block", norm: str = "fro",
+                 products: str = "tensor"):
+        o = _opts(max_iter, guard, qtilde, 1, 0, False, launch_mode, norm=norm, products=products)
         h = ctypes.c_void_p()
         _check(lib().sp2_create_bsr_ex(N, nocc, tau, TRUNC_RULES[rule], ctypes.byref(o), ctypes.byref(h)),
                "sp2_create_bsr_ex")
@@ -303,10 +308,11 @@ class BsrPurifier:
         _check(lib().sp2_get_info_bsr(self.h, ctypes.byref(info), ctypes.byref(nz)), "sp2_get_info_bsr")
         d = _info_dict(info)
         d["nnzb"] = nz.value
-        bp, sb, nms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
-        _check(lib().sp2_get_work_bsr(self.h, ctypes.byref(bp), ctypes.byref(sb), ctypes.byref(nms)),
-               "sp2_get_work_bsr")
-        d["block_products"], d["square_blocks"], d["numeric_ms"] = bp.value, sb.value, nms.value
+        bp, up, sb, nms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().sp2_get_work_bsr(self.h, ctypes.byref(bp), ctypes.byref(up), ctypes.byref(sb),
+                                      ctypes.byref(nms)), "sp2_get_work_bsr")
+        d["block_products"], d["needed_products"] = bp.value, up.value
+        d["square_blocks"], d["numeric_ms"] = sb.value, nms.value
         return d
 
     def close(self):

@@ -1,10 +1,29 @@
 """Block-sparse path (32 x 32 FP32 blocks, Frobenius block truncation) through the C ABI.
 
 Index work (the truncation decision and the symbolic square) must equal the host's bit
-for bit given the same stored blocks.  The purification itself is compared with the
-FP64 oracle that applies the same truncation after every step: the GPU keeps FP32
-blocks, so its result agrees to FP32 accuracy plus the effect of the few blocks whose
-truncation decision flips between the FP32 and FP64 iterates (each of norm ~tau).
+for bit given the same stored blocks.
+
+The purification is compared with two oracles that apply the same truncation after every
+step (Alg. 1, X~_i = X_i + E_i): the FP64 one, and the one that also rounds every stored
+iterate to FP32 (E_i = storage rounding + truncation), which is what the GPU stores.  The
+block products run on the tensor cores by default (two fp16 pieces of 2^14 x per block,
+three piece products, FP32 accumulation in chunks): the stop must be within one square of
+the FP32-storage oracle's.
+
+D tolerance, derived (not measured): one square's products carry a relative error of at
+most about 2^-20 of ||X||_F (three 22-bit piece products, FP32 chunk sums); the errors of
+the n squares are independent, so they add like sqrt(n), and a perturbation of the iterate
+moves the occupied subspace by at most its size over the scaled gap g0 of X_0 (the gap only
+widens under the SP2 maps); ||X||_F <= sqrt(nocc) for a projector-like iterate.  Hence
+||D - D_ref||_F / sqrt(nocc) <= sqrt(n) 2^-20 / g0, with g0 ~ 0.31 on these lattices
+(about 1.2e-5 at n = 15; measured: 4e-7).
+
+The FP32 CUDA-core block products (an option) accumulate every element in one sequential
+FP32 chain over all N terms: tiny terms that follow the large diagonal term are lost, which
+biases the trace at the rounding floor and lets the trace-chosen polynomial repeat there
+(§4.2: such runs are not bounded under trace selection) for up to four squares before the
+order test can fire; a CPU emulation of that exact arithmetic reproduces its histories digit
+for digit.  Its stop is checked in that wider window.
 """
 import math
 
@@ -17,6 +36,26 @@ from oracle import sp2_oracle as o
 from paper_1507_02087_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
+
+
+def d_tol(n, F, nocc):
+    """sqrt(n) 2^-20 / g0, g0 = the scaled gap of X_0 (module notes)."""
+    lmin, lmax = o.gershgorin_bounds(F)
+    lam = np.linalg.eigvalsh(F)
+    g0 = (lam[nocc] - lam[nocc - 1]) / (lmax - lmin)
+    return math.sqrt(max(n, 1)) * 2.0 ** -20 / g0
+
+
+def assert_parity(info, D, F, nocc, tau, **kw):
+    """Stop within one square of the FP32-storage oracle; D within the derived tolerance of the
+    FP64 oracle (and of the FP32-storage one)."""
+    ref = bo.sp2_bsr(F, nocc, 32, tau, **kw)
+    ref32 = bo.sp2_bsr(F, nocc, 32, tau, storage="fp32", **kw)
+    assert abs(info["n_iter"] - ref32.n) <= 1, (info["n_iter"], ref32.n)
+    tol = d_tol(info["n_iter"], F, nocc)
+    assert o.rel_error(D, ref.D, nocc) <= tol
+    assert o.rel_error(D, ref32.D, nocc) <= tol
+    return ref
 
 
 @pytest.fixture(scope="module")
@@ -121,14 +160,12 @@ def test_bsr_mixed_rule_and_mixed_norm_stop(sp2mod, dims, tau):
     # the §6 pairing: mixed-norm truncation and the mixed-norm stop with the 32 x 32 blocks
     tb, (rp, ci, vals) = tb_case(dims)
     F = tb.dense().numpy()
-    ref = bo.sp2_bsr(F, tb.nocc, 32, tau, rule="mixed", norm="mixed")
     with sp2mod.BsrPurifier(tb.N, tb.nocc, tau, rule="mixed", norm="mixed") as P:
         D = P.run(rp, ci, vals)
         info = P.info()
     assert info["status"] == 0
     assert info["stop_reason"] in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
-    assert ref.n - 3 <= info["n_iter"] <= ref.n + 3
-    assert o.rel_error(D.cpu().numpy(), ref.D, tb.nocc) <= 4e-6
+    ref = assert_parity(info, D.cpu().numpy(), F, tb.nocc, tau, rule="mixed", norm="mixed")
     Dn = D.cpu().numpy()
     assert np.array_equal(Dn, Dn.T)
     # the recorded measure is m_i (Lanczos on the block-norm matrix, exact for nb <= 32 steps),
@@ -148,19 +185,16 @@ def test_bsr_norm_options(sp2mod):
         sp2mod.BsrPurifier(tb.N, tb.nocc, 1e-4, norm="spectral")
 
 
-@pytest.mark.parametrize("dims,tau,tol", [((32, 8, 4), 1e-6, 4e-6), ((32, 8, 8), 1e-4, 4e-6)])
-def test_bsr_error_rule_against_oracle(sp2mod, dims, tau, tol):
+@pytest.mark.parametrize("dims,tau", [((32, 8, 4), 1e-6), ((32, 8, 8), 1e-4)])
+def test_bsr_error_rule_against_oracle(sp2mod, dims, tau):
     tb, (rp, ci, vals) = tb_case(dims)
     F = tb.dense().numpy()
-    ref = bo.sp2_bsr(F, tb.nocc, 32, tau, rule="error")
     with sp2mod.BsrPurifier(tb.N, tb.nocc, tau, rule="error") as P:
         D = P.run(rp, ci, vals)
         info = P.info()
     assert info["status"] == 0
     assert info["stop_reason"] in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
-    assert ref.n - 3 <= info["n_iter"] <= ref.n + 3
-    err = o.rel_error(D.cpu().numpy(), ref.D, tb.nocc)
-    assert err <= tol, err
+    assert_parity(info, D.cpu().numpy(), F, tb.nocc, tau, rule="error")
     Dn = D.cpu().numpy()
     assert np.array_equal(Dn, Dn.T)
 
@@ -185,25 +219,18 @@ def tb_case(dims):
     return tb, (torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda(), torch.from_numpy(vals).cuda())
 
 
-@pytest.mark.parametrize("dims,tau,tol", [((32, 8, 4), 0.0, 3e-6), ((32, 8, 8), 1e-6, 4e-6),
-                                          ((32, 16, 8), 1e-4, 4e-6)])
-def test_bsr_sp2_against_oracle(sp2mod, dims, tau, tol):
+@pytest.mark.parametrize("dims,tau", [((32, 8, 4), 0.0), ((32, 8, 8), 1e-6), ((32, 16, 8), 1e-4)])
+def test_bsr_sp2_against_oracle(sp2mod, dims, tau):
     tb, (rp, ci, vals) = tb_case(dims)
     F = tb.dense().numpy()
-    ref = bo.sp2_bsr(F, tb.nocc, 32, tau)
     with sp2mod.BsrPurifier(tb.N, tb.nocc, tau) as P:
         D = P.run(rp, ci, vals)
         info = P.info()
     assert info["status"] == 0
     assert info["stop_reason"] in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
-    # FP32 blocks reach their rounding floor at a different square than FP64: earlier,
-    # or a few squares later when the trace-chosen polynomial repeats at the floor before
-    # the (alternation-requiring) order test can fire
-    assert ref.n - 3 <= info["n_iter"] <= ref.n + 3
+    ref = assert_parity(info, D.cpu().numpy(), F, tb.nocc, tau)
     assert info["lambda_min"] == pytest.approx(ref.lmin, rel=1e-12)
     assert info["lambda_max"] == pytest.approx(ref.lmax, rel=1e-12)
-    err = o.rel_error(D.cpu().numpy(), ref.D, tb.nocc)
-    assert err <= tol, err
     Dn = D.cpu().numpy()
     assert np.array_equal(Dn, Dn.T)
     # the stored pattern of D is what the truncation keeps
@@ -324,12 +351,10 @@ def test_bsr_acc_against_oracle(sp2mod, rule, norm):
         D1 = P.run(rp, ci, vals)
         i1 = P.info()
     assert info["status"] == 0
-    ref = bo.sp2_bsr(F, tb.nocc, 32, 1e-4, rule=rule, norm=norm, acc=acc,
-                     bounds=(info["lambda_min"], info["lambda_max"]))
-    assert abs(info["n_iter"] - ref.n) <= 3
+    ref = assert_parity(info, D, F, tb.nocc, 1e-4, rule=rule, norm=norm, acc=acc,
+                        bounds=(info["lambda_min"], info["lambda_max"]))
     m = min(info["n_iter"], ref.n)
     assert list(info["p"][1:m + 1]) == ref.p[1:m + 1]
-    assert o.rel_error(D, ref.D, tb.nocc) <= 4e-6
     assert info["n_iter"] < i0["n_iter"]
     assert i1["n_iter"] == i0["n_iter"] and torch.equal(D0, D1)       # back to Alg. 3, same bits
 
@@ -345,7 +370,6 @@ def test_bsr_caller_bounds(sp2mod):
     bounds = (-e, e)
     lam = np.linalg.eigvalsh(F)
     assert bounds[0] <= lam[0] and lam[-1] <= bounds[1]
-    ref = bo.sp2_bsr(F, tb.nocc, 32, 1e-5, rule="error", bounds=bounds)
     with sp2mod.BsrPurifier(tb.N, tb.nocc, 1e-5, rule="error") as P:
         P.run(rp, ci, vals)
         n_gersh = P.info()["n_iter"]
@@ -358,5 +382,35 @@ def test_bsr_caller_bounds(sp2mod):
         P.run(rp, ci, vals)
         assert P.info()["n_iter"] == n_gersh
     assert (info["lambda_min"], info["lambda_max"]) == bounds
-    assert info["status"] == 0 and abs(info["n_iter"] - ref.n) <= 3 and info["n_iter"] <= n_gersh
-    assert o.rel_error(D, ref.D, tb.nocc) <= 4e-6
+    assert info["status"] == 0 and info["n_iter"] <= n_gersh
+    assert_parity(info, D, F, tb.nocc, 1e-5, rule="error", bounds=bounds)
+
+
+@pytest.mark.parametrize("dims,tau,rule", [((32, 8, 4), 1e-6, "error"), ((32, 8, 8), 1e-4, "error"),
+                                           ((32, 8, 8), 1e-6, "block")])
+def test_bsr_cuda_core_products_option(sp2mod, dims, tau, rule):
+    # the FP32 CUDA-core block products: same index work and truncation, D within the derived
+    # tolerance; the stop in the window of its sequential sums (module notes)
+    tb, (rp, ci, vals) = tb_case(dims)
+    F = tb.dense().numpy()
+    with sp2mod.BsrPurifier(tb.N, tb.nocc, tau, rule=rule, products="cuda") as P:
+        D = P.run(rp, ci, vals).cpu().numpy()
+        info = P.info()
+    assert info["status"] == 0 and info["stop_reason"] in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
+    ref = bo.sp2_bsr(F, tb.nocc, 32, tau, rule=rule)
+    ref32 = bo.sp2_bsr(F, tb.nocc, 32, tau, rule=rule, storage="fp32")
+    assert ref32.n - 1 <= info["n_iter"] <= ref32.n + 4
+    assert o.rel_error(D, ref.D, tb.nocc) <= d_tol(info["n_iter"], F, tb.nocc)
+    assert np.array_equal(D, D.T)
+
+
+def test_bsr_tensor_core_products_deterministic(sp2mod):
+    # the same input twice, and the graph against stream launches: the same bits
+    tb, (rp, ci, vals) = tb_case((32, 8, 8))
+    out = []
+    for mode in (0, 0, 1):
+        with sp2mod.BsrPurifier(tb.N, tb.nocc, 1e-4, rule="error", launch_mode=mode) as P:
+            out.append((P.run(rp, ci, vals), P.info()))
+    for D, info in out[1:]:
+        assert info["n_iter"] == out[0][1]["n_iter"] and torch.equal(D, out[0][0])
+    assert out[0][1]["status"] == 0
