@@ -3,13 +3,15 @@
 
 A step is one full purification F -> D of the dense workload N=8192, nocc=4096:
 spectrum uniform in [-1,-0.005] U [0.005,1] (gap 0.01) with eigenvectors from the QR
-factor of a seeded Gaussian matrix.  The timed path is the mixed-precision one
-(Gershgorin bounds, scaling, tensor-core squares with the device-side parameterless
-stop, the F-driven subspace correction and a refinement pair), whose result must
-be within ||D - D_exact||_F / sqrt(nocc) <= 1e-6 of the exact projector; the plain
-FP64 path is timed beside it for the comparison.  F (512 MiB FP64) is resident in
-HBM before the timed region; every buffer the loop streams is larger than the
-129 MB L2, so no flush is needed between steps.
+factor of a seeded Gaussian matrix.  The timed path is the tensor-core one (Gershgorin
+bounds, scaling, squares on the tcgen05 tensor cores with the device-side parameterless
+stop, the F-driven subspace correction and a refinement pair; by default in the fp16x3
+mode: two scaled fp16 pieces per value, three piece products per square), whose result must
+be within ||D - D_exact||_F / sqrt(nocc) <= 1e-6 of the exact projector; the plain FP64
+path is timed beside it for the comparison.  F (512 MiB FP64) is resident in HBM before
+the timed region; every buffer the loop streams is larger than the 129 MB L2, so no flush
+is needed between steps.  The default line also carries secondary records of the other
+workloads (a batch of 64 uneven problems, the 32^3 block-sparse lattice, SP2-ACC).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line (rank 0).
@@ -35,7 +37,16 @@ TOL = 1e-6
 # FP64 runs on the SMs' FP64 pipes: the nominal 1.25 TFLOP/s over 152 SMs at the
 # 2070 MHz maximum clock is 4 flop per clock per SM; taken at the measured clock.
 SMS, FP64_FLOP_PER_CLK_SM, SM_MAX_MHZ = 152, 4.0, 2070.0
-SPLIT_PRODUCTS = 6   # bf16 piece products per FP32-grade product on the tensor cores
+# 16-bit piece products per square on the tensor cores, per precision mode
+PRODUCTS = {"mixed": 6, "bf16x6": 6, "bf16x3": 3, "fp16x3": 3}
+# The roofline basis of the tensor-core square: useful flops N^2 (N+1) per square (upper triangle
+# with the diagonal, N multiply-adds each) times 3 split products, the budget of an FP32-grade
+# square on 16-bit tensor cores; the executed fraction counts the mode's own piece products.
+SPLIT_BASIS = 3
+DTYPE = {"mixed": "bf16x6->f32 (three bf16 pieces, six products), f64 reductions",
+         "bf16x6": "bf16x6->f32 (three bf16 pieces, six products), f64 reductions",
+         "bf16x3": "bf16x3->f32 (two bf16 pieces, three products), f64 reductions",
+         "fp16x3": "fp16x3->f32 (two scaled fp16 pieces, three products), f64 reductions"}
 
 
 def workload_name(N, nocc, gap):
@@ -44,7 +55,7 @@ def workload_name(N, nocc, gap):
 
 # DRAM bytes (read + write) of one forward-square launch from an ncu capture of the current
 # kernel (profiles/tc_gemm_pair_sp2_forward_dram_ld8192.md), keyed by (N, tile kind).
-FWD_TRAFFIC_BYTES = {(8192, "pair"): 2.23e9 + 0.3846e9}
+FWD_TRAFFIC_BYTES = {}
 FP32_FLOP_PER_CLK_SM = 256     # 128 FP32 FMA lanes per SM
 
 
@@ -58,7 +69,11 @@ def parse():
                     help="dense: one N x N problem (default N=8192); batch64: 64 problems, N log-uniform "
                          "in [128, 2048], seed 1; bsr: gapped tight-binding 32^3 lattice, 32 x 32 blocks, "
                          "block truncation tau in {1e-4, 1e-6}")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["fp16x3", "bf16x6", "mixed", "bf16x3", "fp64"], default="fp16x3",
+                    help="fp16x3 (default): two scaled fp16 pieces, three products; bf16x6 (= mixed): three bf16 "
+                         "pieces, six products; bf16x3: two bf16 pieces, three products; fp64: the plain method")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="dense workload: skip the secondary records (batch of 64, 32^3 block-sparse, SP2-ACC)")
     ap.add_argument("--refine", choices=["tc", "fp64", "mcweeny"], default="tc",
                     help="mixed path: refinement pair on the tensor cores (tc) or in FP64 (fp64), or one "
                          "McWeeny step with its square in FP64 (mcweeny)")
@@ -251,9 +266,14 @@ def useful_flops(N, squares, deriv_steps, corrected, refine_steps):
     return f
 
 
-def run_batch(a, ws, rank, local):
-    """64 problems of uneven size in one batch: mixed (one launch sequence, per-problem
-    stops) against the FP64 path (problems one after the other)."""
+def tc_precision(a):
+    return a.precision if a.precision in PRODUCTS else "fp16x3"
+
+
+def batch_record(a, local, precision, steps, warmup, compare_tiles=False, fp64_steps=0):
+    """64 problems of uneven size in one batch (one launch sequence, per-problem stops): time-to-D
+    from CUDA events on the launching stream, the largest error against each exact projector, and
+    the tensor rate of the whole run (useful flops of every product over the time-to-D)."""
     import torch
     from paper_1507_02087_gb300 import inputs, sp2
     torch.cuda.set_device(local)
@@ -262,10 +282,10 @@ def run_batch(a, ws, rank, local):
     Fs = [c.F for c in cases]
     stream = torch.cuda.current_stream()
 
-    def timed(B, steps):
+    def timed(B, k):
         Ds = [torch.empty_like(F) for F in Fs]
         tms = []
-        for _ in range(steps):
+        for _ in range(k):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -277,38 +297,59 @@ def run_batch(a, ws, rank, local):
         infos = [B.info(i) for i in range(len(cases))]
         return statistics.mean(tms), max(errs), infos
 
-    with sp2.BatchPurifier(Ns, noccs, "mixed") as B:
-        timed(B, a.warmup)
+    with sp2.BatchPurifier(Ns, noccs, precision) as B:
+        timed(B, warmup)
         clocks = ClockSampler(local)
-        barrier(ws)
         clocks.start()
-        ms, err, infos = timed(B, a.steps)
+        ms, err, infos = timed(B, steps)
         clk = clocks.stop()
-    ms = max_over_ranks(ms, ws)
     flops = sum(useful_flops(N, i["hist_len"], i["n_iter"], True, 2) for N, i in zip(Ns, infos))
-    # the tuner's choice against both fixed tile kinds on the same batch
-    tiles = {"tuned": infos[0]["tile"]}
-    for t in ("128", "pair"):
-        with sp2.BatchPurifier(Ns, noccs, "mixed", tile=t) as Bt:
-            timed(Bt, 1)
-            tiles[t + "_ms"] = timed(Bt, max(1, a.steps))[0]
-    fp64 = None
-    if a.fp64_steps > 0:
+    peaks = load_peaks()
+    peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    achieved = SPLIT_BASIS * flops / (ms * 1e-3) / 1e12
+    rec = {"workload": "batch of 64 dense problems, N log-uniform in [128, 2048] (seed 1), nocc = N/2, gap "
+                       "uniform in [0.005, 0.1]; one launch sequence, per-problem stops",
+           "precision": precision, "time_to_d_ms": ms, "steps": steps, "warmup": warmup,
+           "max_err_vs_exact": err, "meets_tolerance": bool(err <= TOL),
+           "tflops_useful": flops / (ms * 1e-3) / 1e12,
+           "n_iter_range": [min(i["n_iter"] for i in infos), max(i["n_iter"] for i in infos)],
+           "tile": infos[0]["tile"],
+           "roofline": {"bound": "tensor", "kernel": "every tensor-core launch of the run, over the whole time-to-D",
+                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                        "basis": "useful flops of all products x 3 split products over the time-to-D; peak: "
+                                 "MEASURED_PEAKS.json bf16_tflops_sustained (fp16 and bf16 share the kind::f16 rate)",
+                        "traffic": None},
+           "clocks": clk, "sum_N3": sum(N ** 3 for N in Ns), "count": len(cases)}
+    if compare_tiles:
+        tiles = {"tuned": infos[0]["tile"]}
+        for t in ("128", "pair"):
+            with sp2.BatchPurifier(Ns, noccs, precision, tile=t) as Bt:
+                timed(Bt, 1)
+                tiles[t + "_ms"] = timed(Bt, max(1, steps))[0]
+        rec["tiles"] = tiles
+    if fp64_steps > 0:
         with sp2.BatchPurifier(Ns, noccs, "fp64") as B64:
-            ms64, err64, inf64 = timed(B64, a.fp64_steps)
-        fp64 = {"time_to_d_ms": ms64, "max_err_vs_exact": err64, "speedup_mixed_vs_fp64": ms64 / ms}
+            ms64, err64, inf64 = timed(B64, fp64_steps)
+        rec["fp64_path"] = {"time_to_d_ms": ms64, "max_err_vs_exact": err64, "speedup_vs_fp64": ms64 / ms}
+    return rec
+
+
+def run_batch(a, ws, rank, local):
+    """The batch workload as the headline line."""
+    prec = tc_precision(a)
+    rec = batch_record(a, local, prec, a.steps, a.warmup, compare_tiles=True, fp64_steps=a.fp64_steps)
+    barrier(ws)
+    ms = max_over_ranks(rec["time_to_d_ms"], ws)
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x6->f32 (mixed), f64 reductions", "data": "synthetic",
-            "config": {"workload": "batch of 64 dense problems, N log-uniform in [128, 2048] (seed 1), "
-                                   "nocc = N/2, gap uniform in [0.005, 0.1]", "count": len(cases),
-                       "sum_N3": sum(N ** 3 for N in Ns), "precision": "mixed"},
-            "max_err_vs_exact": err, "meets_tolerance": bool(err <= TOL),
-            "tflops_useful": flops / (ms * 1e-3) / 1e12,
-            "n_iter_range": [min(i["n_iter"] for i in infos), max(i["n_iter"] for i in infos)],
-            "tiles": tiles, "fp64_path": fp64, "clocks": clk}), flush=True)
+            "dtype": DTYPE[prec], "data": "synthetic",
+            "config": {"workload": rec["workload"], "count": rec["count"], "sum_N3": rec["sum_N3"],
+                       "precision": prec},
+            **{k: rec[k] for k in ("max_err_vs_exact", "meets_tolerance", "tflops_useful", "n_iter_range",
+                                   "tiles", "roofline", "clocks")},
+            "fp64_path": rec.get("fp64_path")}), flush=True)
 
 
 def bsr_launches(squares, rule):
@@ -319,6 +360,121 @@ def bsr_launches(squares, rule):
     lz = 35 if rule == "mixed" else 0
     rounds = squares + (squares & 1)
     return 14 + extra + (12 + extra + lz) * rounds
+
+
+def bsr_error_bound(tb, D):
+    """A-posteriori bound of ||D - P||_F / sqrt(nocc) against the exact projector P of the lattice
+    Hamiltonian, from what holds at any size: with P~ the projector onto the eigenvectors of D
+    above 1/2, ||D - P~||_F <= ||D^2 - D||_F / (1 - 2m) (eigenvalues of D within m of {0, 1}), and
+    by the sin-theta theorem with the gap delta of F, ||P~ - P||_F <= (||[F, D]||_F + 2 ||F||
+    ||D - P~||_F) / delta; delta >= 2 (1 - max |disorder|) (Weyl), ||F|| from Gershgorin."""
+    import numpy as np
+    import torch
+    r = torch.from_numpy(tb.rows).cuda()
+    c = torch.from_numpy(tb.cols).cuda()
+    idx = torch.cat([torch.stack([r, c]), torch.arange(tb.N, device="cuda").repeat(2, 1)], dim=1)
+    val = torch.cat([torch.full((r.numel(),), -tb.hop, dtype=torch.float64, device="cuda"),
+                     torch.from_numpy(tb.onsite).cuda()])
+    Fs = torch.sparse_coo_tensor(idx, val, (tb.N, tb.N)).coalesce()
+    FD = torch.sparse.mm(Fs, D)
+    comm = float(torch.linalg.norm(FD - FD.T))
+    del FD
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    D32 = D.float()
+    idem = float(torch.linalg.norm((D32 @ D32).double() - D))
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    del D32
+    delta = 2.0 * (1.0 - float(np.max(np.abs(np.abs(tb.onsite) - 1.0))))
+    fnorm = float(np.max(np.abs(tb.onsite))) + 6 * tb.hop
+    m = 0.01
+    dpt = idem / (1 - 2 * m)
+    bound = dpt + (comm + 2 * fnorm * dpt) / delta
+    return {"err_bound": bound / math.sqrt(tb.nocc), "idem": idem / math.sqrt(tb.nocc),
+            "comm": comm / math.sqrt(tb.nocc), "trace_err": abs(float(torch.trace(D)) - tb.nocc),
+            "valid": bool(idem < m / 2)}
+
+
+def bsr_roofline(w, mhz, products="tensor"):
+    """Roofline of the numeric block square, summed over one run's squares (CUDA events around
+    each launch, launch_mode 1).  Tensor cores: the needed 32^3 block products (both factors
+    stored, output block J >= I) x 2 x 32^3 flops x the 3 split products, against the bf16
+    tensor peak; frac_executed also counts the zero blocks that fill the 4 x 8-block tiles.
+    FP32 CUDA cores: the products formed, against the FP32 FMA peak at the measured clock."""
+    kern_s = w["numeric_ms"] * 1e-3
+    need = 2 * 32 ** 3 * w["needed_products"]
+    execd = 2 * 32 ** 3 * w["block_products"]
+    common = {"kernel_ms_per_run": w["numeric_ms"], "block_products": w["block_products"],
+              "needed_products": w["needed_products"], "square_blocks": w["square_blocks"],
+              "useful_tflops": need / kern_s / 1e12, "traffic": None}
+    if products == "tensor":
+        peak = load_peaks().get("bf16_tflops_sustained") or 1700.0
+        achieved = SPLIT_BASIS * need / kern_s / 1e12
+        return {"bound": "tensor",
+                "kernel": "bsr_tc_kernel (4 x 8-block tiles, fp16x3 block products, all squares)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "frac_executed": SPLIT_BASIS * execd / kern_s / 1e12 / peak,
+                "basis": "needed block products x 2 x 32^3 flops x 3 split products / summed CUDA-event "
+                         "time of the numeric launches",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (fp16 and bf16 inputs share the "
+                               "kind::f16 tensor rate)", **common}
+    peak32 = SMS * FP32_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
+    streamed = 2 * 32 * 32 * 4 * w["block_products"]          # two FP32 blocks per product, no reuse
+    return {"bound": "alu", "kernel": "bsr_numeric_kernel (FP32 CUDA-core block products, all squares)",
+            "achieved": execd / kern_s / 1e12, "peak": peak32, "unit": "TFLOP/s",
+            "frac": execd / kern_s / 1e12 / peak32,
+            "peak_source": f"152 SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz (median SM clock)",
+            "streamed_gbs": streamed / kern_s / 1e9,
+            "streamed_frac_of_hbm": streamed / kern_s / 1e9 / (load_peaks().get("hbm_gbs") or 6800.0),
+            **common}
+
+
+def bsr_record(a, local, steps, warmup, tau=1e-4, rule="mixed"):
+    """The 32^3 block-sparse lattice (N = 32768) with the mixed-norm truncation and the mixed-norm
+    stop (the pairing of the paper's §6 calculations): time-to-D from CUDA events, the a-posteriori
+    error bound (computed once, outside the timed region), and the roofline of the numeric block
+    square from a stream-launched run (CUDA events around each of its launches)."""
+    import torch
+    from paper_1507_02087_gb300 import inputs, sp2
+    torch.cuda.set_device(local)
+    tb = inputs.tight_binding(L=32)
+    rp, ci, vals = tb.bsr(32)
+    rp_d, ci_d, vals_d = (torch.from_numpy(x).cuda() for x in (rp, ci, vals))
+    stream = torch.cuda.current_stream()
+    norm = "mixed" if rule == "mixed" else "fro"
+    with sp2.BsrPurifier(tb.N, tb.nocc, tau, rule=rule, norm=norm) as P:
+        for _ in range(warmup):
+            P.run(rp_d, ci_d, vals_d, dense=False, stream=stream)
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        clk.start()
+        tms = []
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.run(rp_d, ci_d, vals_d, dense=False, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            tms.append(e0.elapsed_time(e1))
+        clocks = clk.stop()
+        info = P.info()
+        D = P.run(rp_d, ci_d, vals_d, stream=stream)
+        torch.cuda.synchronize()
+    err = bsr_error_bound(tb, D)
+    del D
+    with sp2.BsrPurifier(tb.N, tb.nocc, tau, rule=rule, launch_mode=1, norm=norm) as P1:
+        P1.run(rp_d, ci_d, vals_d, dense=False, stream=stream)
+        w = P1.info()
+    mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+    nb = tb.N // 32
+    return {"workload": "gapped tight-binding 32x32x32 simple cubic (N=32768), delta=1, t=0.3, sigma=0.05 (seed 2), "
+                        "nocc=N/2, 32x32 FP32 blocks; mixed-norm truncation tau=%g with the mixed-norm stop" % tau,
+            "time_to_d_ms": statistics.mean(tms), "steps": steps, "warmup": warmup,
+            "n_iter": info["n_iter"], "squares": info["hist_len"], "kept_fraction": info["nnzb"] / nb ** 2,
+            "err_bound_vs_exact": err["err_bound"], "idem": err["idem"], "comm": err["comm"],
+            "trace_err": err["trace_err"], "bound_valid": err["valid"],
+            "roofline": bsr_roofline(w, mhz), "clocks": clocks}
 
 
 def run_bsr(a, ws, rank, local):
@@ -380,27 +536,15 @@ def run_bsr(a, ws, rank, local):
         w = P1.info()
     clocks = clk.stop()
     mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
-    flops = 2 * 32 ** 3 * w["block_products"]
-    streamed = 2 * 32 * 32 * 4 * w["block_products"]          # two FP32 blocks per product, no reuse
-    kern_s = w["numeric_ms"] * 1e-3
-    peak32 = SMS * FP32_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
-    peaks = load_peaks()
-    roofline = {"bound": "alu", "kernel": "bsr_numeric_kernel (FP32 CUDA-core block products, all squares)",
-                "achieved": flops / kern_s / 1e12, "peak": peak32, "unit": "TFLOP/s",
-                "frac": flops / kern_s / 1e12 / peak32,
-                "peak_source": f"152 SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz (median SM clock)",
-                "kernel_ms_per_run": w["numeric_ms"], "block_products": w["block_products"],
-                "square_blocks": w["square_blocks"],
-                "streamed_gbs": streamed / kern_s / 1e9,
-                "streamed_frac_of_hbm": streamed / kern_s / 1e9 / (peaks.get("hbm_gbs") or 6800.0),
-                "traffic": None}
+    roofline = bsr_roofline(w, mhz)
     if rank == 0:
         main_ms = out[f"{a.rule}:tau=0.0001"]["time_to_d_ms"]
         print(json.dumps({
             "metric": "time-to-D, block-sparse SP2 with block truncation (FP32 blocks, FP64 reductions)",
             "value": main_ms, "unit": "ms", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": main_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 blocks, f64 reductions", "data": "synthetic",
+            "dtype": "fp16x3->f32 block products (two scaled fp16 pieces, three products), f32 blocks, "
+                     "f64 reductions", "data": "synthetic",
             "config": {"workload": "gapped tight-binding 32x32x32 simple cubic (N=32768), delta=1, t=0.3, "
                                    "sigma=0.05 (seed 2), nocc=N/2, 32x32 blocks (x-lines)",
                        "nnzb_F": int(rp[-1]), "tau": 1e-4,
@@ -485,7 +629,7 @@ def main():
     info = infos[-1]
     err = err_vs_exact()
     status_ok = all(i["status"] == 0 for i in infos)
-    mixed = a.precision == "mixed"
+    mixed = a.precision in PRODUCTS
     squares = info["hist_len"]
     n_iter = info["n_iter"]
     flops = useful_flops(N, squares, n_iter, mixed, 2 if mixed else 0) if mixed else N * N * (N + 1) * squares
@@ -493,14 +637,19 @@ def main():
     # FP64 path per square: square (+ McWeeny product) + finalize (+ 35 Lanczos launches for the
     # spectral stop); bounds, init, scaling and the output copy once
     per_square = 2 + (1 if a.mcweeny else 0) + (35 if a.norm == "spectral" else 0)
-    launches_per_step = (3 + per_square * squares + 1) if not mixed else (3 + 2 * squares + 2 + 2 * n_iter + 3 + 1)
+    # tensor-core path: bounds, init, scaling; {square, finalize, loop check} per forward round; two
+    # correction products; {derivative step, advance} per derivative round; refinement input and pair;
+    # the output assembly
+    launches_per_step = (3 + per_square * squares + 1) if not mixed else (3 + 3 * squares + 2 + 2 * n_iter + 3 + 1)
 
     # roofline of the dominant kernel, timed on its own inside the same device loop:
     # a forward-only handle runs the square + stop-test loop; loop time / squares is
     # the average duration of one square launch (plus the few-microsecond stop test).
     peaks = load_peaks()
     if mixed:
-        with sp2.Purifier(N, nocc, "mixed", corrections=0, refine_steps=0) as Pf:
+        with sp2.Purifier(N, nocc, a.precision, corrections=0, refine_steps=0) as Pf:
+            if acc_bounds is not None:
+                Pf.set_homo_lumo(acc_bounds)
             Pf.run(F, D, stream)
             kt = []
             for _ in range(max(1, min(3, a.steps))):
@@ -509,17 +658,24 @@ def main():
                 kt.append(fi["loop_ms"] / fi["hist_len"])
             tile_used = fi["tile"]
         kern_ms = statistics.mean(kt)
-        alg = SPLIT_PRODUCTS * N * N * (N + 1)        # six bf16 piece products of an upper-triangle square
+        useful = N * N * (N + 1)                      # one upper-triangle square with the diagonal
+        alg = SPLIT_BASIS * useful
+        executed = PRODUCTS[a.precision] * useful
         achieved = alg / (kern_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
         kname = ("tc_gemm_pair_kernel (256x256 tiles per SM pair" if tile_used == "pair"
                  else "tc_gemm_kernel (128x128 tiles per SM")
-        roofline = {"bound": "tensor", "kernel": kname + ", forward square, MODE_SP2_STEP)",
+        roofline = {"bound": "tensor", "kernel": kname + ", forward square, MODE_SP2_STEP, " + a.precision + ")",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "frac_executed": executed / (kern_ms * 1e-3) / 1e12 / peak,
+                    "basis": "achieved = N^2 (N+1) useful flops per square x 3 split products / CUDA-event time "
+                             "per square; frac_executed counts the mode's own %d piece products" % PRODUCTS[a.precision],
+                    "useful_tflops": useful / (kern_ms * 1e-3) / 1e12,
                     "ms_per_launch": kern_ms,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step; "
+                                   "fp16 and bf16 inputs share the kind::f16 tensor rate)",
                     "algorithmic_flops_per_launch": alg,
-                    "traffic": FWD_TRAFFIC_BYTES.get((N, tile_used))}
+                    "traffic": FWD_TRAFFIC_BYTES.get((N, tile_used, a.precision))}
     else:
         kern_ms = statistics.mean(l / s for l, s in zip(loop_ms, [i["hist_len"] for i in infos]))
         mhz = clk.get("sm_mhz") or SM_MAX_MHZ
@@ -542,19 +698,28 @@ def main():
         D_h = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
         F_hn, D_hn = F_h.numpy(), D_h.numpy()
         P.run_host(F_hn, D_hn, stream)          # allocates the staging buffers once
-        e2e_ms = []
+        e2e_ms, e2e_loop, e2e_dev = [], [], []
         eclk = ClockSampler(local)
         eclk.start()
         for _ in range(a.e2e_steps):
             torch.cuda.synchronize()
+            d0 = torch.cuda.Event(enable_timing=True)
+            d1 = torch.cuda.Event(enable_timing=True)
             t0 = time.perf_counter()
+            d0.record(stream)
             P.run_host(F_hn, D_hn, stream)
+            d1.record(stream)
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            d1.synchronize()
+            e2e_dev.append(d0.elapsed_time(d1))      # device span of the call: copies + run
+            e2e_loop.append(P.info()["loop_ms"])     # device time of the same call's loop
         ec = eclk.stop()
         # the clocks of these steps: a long run under the power cap can drift below the clocks of
         # the device-timed steps, which then shows up in the gap between e2e and value
         e2e = {"value": max_over_ranks(statistics.mean(e2e_ms), ws), "unit": "ms",
                "h2d_bytes_per_step": N * N * 8, "d2h_bytes_per_step": N * N * 8,
+               "steps_ms": e2e_ms, "device_span_ms": e2e_dev, "loop_ms": e2e_loop,
+               "value_loop_ms": statistics.mean(loop_ms),
                "sm_mhz": ec.get("sm_mhz"), "reasons": ec.get("reasons")}
 
     # the plain FP64 path, for the comparison the metric asks for
@@ -619,8 +784,8 @@ def main():
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None,
-                "dtype": ("bf16x6->f32 (mixed), f64 reductions" + {"tc": "", "fp64": ", f64 refinement pair",
-                                                                    "mcweeny": ", f64-square McWeeny step"}[a.refine])
+                "dtype": (DTYPE[a.precision] + {"tc": "", "fp64": ", f64 refinement pair",
+                                                "mcweeny": ", f64-square McWeeny step"}[a.refine])
                 if mixed else "f64",
                 "data": "synthetic",
                 "config": {"workload": workload_name(N, nocc, a.gap) if a.input == "qr" else
@@ -638,8 +803,72 @@ def main():
                 "stop_reason": info["stop_reason"], "loop_ms": statistics.mean(loop_ms),
                 "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches_per_step * a.steps), "clocks": clk}
-        print(json.dumps(line), flush=True)
     P.close()
+    del P
+    if rank == 0 and ws == 1 and mixed and not a.no_secondary and a.acc is None and a.input == "qr":
+        # the other workloads, each with its own CUDA-event time, error, roofline and clock record
+        steps2, warm2 = max(1, min(a.steps, 5)), max(1, min(a.warmup, 2))
+        line["secondary"] = {
+            "batch64": batch_record(a, local, a.precision, steps2, warm2),
+            "bsr32": bsr_record(a, local, max(1, min(a.steps, 3)), 1),
+            "sp2_acc": acc_record(a, local, F, D_exact, case.lam, nocc, steps2, warm2),
+        }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def acc_record(a, local, F, D_exact, lam, nocc, steps, warmup, slack=1e-3):
+    """SP2-ACC (Alg. 4 / Alg. 5) on the headline workload, with the construction's homo and lumo
+    eigenvalues as inner bounds and outer bounds `slack` beyond them: time-to-D, error, and the
+    forward square's roofline from a forward-only handle on the same schedule."""
+    import numpy as np
+    import torch
+    from paper_1507_02087_gb300 import sp2
+    N = F.shape[0]
+    lam = np.sort(np.asarray(lam))
+    homo, lumo = float(lam[nocc - 1]), float(lam[nocc])
+    bounds = (homo - slack, homo, lumo, lumo + slack)
+    stream = torch.cuda.current_stream()
+    D = torch.empty_like(F)
+    with sp2.Purifier(N, nocc, a.precision) as P:
+        P.set_homo_lumo(bounds)
+        for _ in range(warmup):
+            P.run(F, D, stream)
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        clk.start()
+        tms = []
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.run(F, D, stream)
+            e1.record(stream)
+            e1.synchronize()
+            tms.append(e0.elapsed_time(e1))
+        clocks = clk.stop()
+        info = P.info()
+    err = float(torch.linalg.norm(D - D_exact)) / math.sqrt(nocc)
+    del D
+    with sp2.Purifier(N, nocc, a.precision, corrections=0, refine_steps=0) as Pf:
+        Pf.set_homo_lumo(bounds)
+        D2 = torch.empty_like(F)
+        Pf.run(F, D2, stream)
+        Pf.run(F, D2, stream)
+        fi = Pf.info()
+        del D2
+    kern_ms = fi["loop_ms"] / fi["hist_len"]
+    peak = load_peaks().get("bf16_tflops_sustained") or 1700.0
+    achieved = SPLIT_BASIS * N * N * (N + 1) / (kern_ms * 1e-3) / 1e12
+    return {"workload": workload_name(N, nocc, a.gap) + ", SP2-ACC with homo/lumo bounds (slack %g)" % slack,
+            "precision": a.precision, "time_to_d_ms": statistics.mean(tms), "steps": steps, "warmup": warmup,
+            "err_vs_exact": err, "meets_tolerance": bool(err <= TOL and info["status"] == 0),
+            "n_iter": info["n_iter"], "stop_reason": info["stop_reason"],
+            "roofline": {"bound": "tensor", "kernel": "forward square of the accelerated expansion",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "ms_per_launch": kern_ms, "basis": "N^2 (N+1) x 3 split products per square",
+                         "traffic": None},
+            "clocks": clocks}
 
 
 if __name__ == "__main__":

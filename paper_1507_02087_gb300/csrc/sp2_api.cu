@@ -50,6 +50,7 @@ extern "C" void sp2_default_opts(sp2_opts* o) {
   o->history = 0;
   o->tile = 0;
   o->norm = 0;
+  o->bsr_cuda_cores = 0;
 }
 
 extern "C" const char* sp2_status_string(int32_t s) {

@@ -49,10 +49,12 @@ struct DevState {
   int32_t iter_active; // block-sparse path: the current loop round squares (set at its start)
   int32_t norm;        // error measure of the stop: 0 = Frobenius v_i, 1 = mixed norm m_i (§2),
                        // 2 = spectral e_i (Lanczos; FP64 path)
-  // block-sparse path, work of the current run's squares: 32 x 32 block products and
-  // upper blocks of the squares computed
+  // block-sparse path, work of the current run's squares: 32 x 32 block products executed,
+  // upper blocks of the squares computed, and the block products the squares need (both
+  // factors stored, output block J >= I)
   unsigned long long bprod;
   unsigned long long sblocks;
+  unsigned long long uprod;
   double spec_e;       // norm = 2: the Lanczos estimate of ||X_{k-1} - X_{k-1}^2||_2 of the last square
   double tr_shift;     // Tr[E_k] of a prescribed perturbation added to the square just written
   int32_t ubounds;     // 1: the caller's outer bounds (ub_lo, ub_hi) replace the Gershgorin bounds
@@ -200,8 +202,9 @@ __device__ inline void mcw_schedule(DevState* st, double gamma) {
 // one square late because v_{k-1} needs X_{k-1}^2; on the accelerated path from n_min
 // on, Alg. 5), the end of the schedule (accelerated path), the cap, then the trace guard
 // for X_k, which compares Tr[X_k] with `tr_ref` = Tr[X_{k-1}] (accelerated path: only
-// from n_min on, where the polynomials are the plain ones).  Returns true if the run
-// stops; single thread.
+// from n_min on, where the polynomials are the plain ones) and fires only when the order test
+// on the last pair (v_{k-1}, v_{k-3}, without the alternation it needs) says the convergence
+// order has fallen below qtilde.  Returns true if the run stops; single thread.
 __device__ __forceinline__ bool record_and_test(DevState* st, int pk, double v_prev, double tr_new,
                                                 double tr_ref) {
   const int k = st->k + 1;
@@ -239,7 +242,8 @@ __device__ __forceinline__ bool record_and_test(DevState* st, int pk, double v_p
   } else if (i >= st->max_iter) {
     st->reason = SP2_STOP_CAP; st->n_out = i; st->out_buf = i & 1;
   } else if (st->guard && (!st->acc || k >= st->n_min) &&
-             ((pk == 1 && tr_new >= tr_ref) || (pk == 0 && tr_new <= tr_ref))) {
+             ((pk == 1 && tr_new >= tr_ref) || (pk == 0 && tr_new <= tr_ref)) &&
+             k >= 3 && order_test_stops(st->v[k - 1], st->v[k - 3], st->qtilde)) {
     st->reason = SP2_STOP_TRACE_GUARD; st->n_out = k; st->out_buf = k & 1;
   } else {
     stop = false;

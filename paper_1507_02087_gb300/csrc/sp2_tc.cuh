@@ -48,9 +48,10 @@ __host__ __device__ constexpr int np_of(int fmt) { return fmt == FMT_FP16X2 ? 2 
 __host__ __device__ constexpr int stages_of(int fmt) { return fmt == FMT_FP16X2 ? 6 : 4; }
 // The tensor cores' FP32 accumulation drops the bits an addend loses in alignment
 // (it rounds toward zero), so a long sum of same-sign products drifts low by about
-// K * 2^-25 of its value.  The MMAs therefore accumulate CHUNK_KB k-blocks (64 terms)
-// at a time into one of NBUF tensor-memory buffers, and the epilogue adds the chunk
-// sums into registers with round-to-nearest FP32 additions.
+// K * 2^-25 of its value.  The MMAs therefore accumulate a chunk of k-blocks (CHUNK_KB,
+// 64 terms, for full bf16 products; see chunk_kb for the others) at a time into one of the
+// tensor-memory buffers, and the epilogue adds the chunk sums into registers with
+// round-to-nearest FP32 additions.
 constexpr int CHUNK_KB = 2;
 constexpr int NBUF = 4;
 constexpr int A_PIECE_BYTES = BM * BK * 2;

@@ -117,10 +117,12 @@ __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
   return r;
 }
 
-// k-blocks per tensor-memory chunk: CHUNK_KB (64 terms) for full products; for low-precision
-// jobs, whose products per k-step fill a chunk sooner and whose 16-bit (bf16) or 11-bit (fp16)
-// target tolerates the larger accumulation bias, twice (bf16, about 128 x 2^-25) or four times
-// (fp16, one product per k-step) as many, halved until the chunks divide the k-blocks of a tile.
+// k-blocks per tensor-memory chunk: CHUNK_KB (64 terms) for full products.  (Full fp16 products
+// with 128-term chunks, which make as many truncating additions per chunk as full bf16 ones with
+// 64, ran 7 % faster at N = 8192 but raised the error after the correction from 6.5e-7 to 9.1e-7,
+// too close to the 1e-6 target.)  Low-precision jobs, whose 16-bit (bf16) or 11-bit (fp16) target
+// tolerates a larger bias, take twice (bf16: 3 products per k-step) or four times (fp16: 1)
+// CHUNK_KB.  Halved until the chunks divide the k-blocks of a tile.
 __device__ __forceinline__ int chunk_kb(const Job& job, int ld) {
   int ck = !job.lowprec ? CHUNK_KB : (job.fmt == FMT_FP16X2 ? 4 * CHUNK_KB : 2 * CHUNK_KB);
   const int total = job.nterms * (ld / BK);
@@ -162,8 +164,10 @@ __device__ __forceinline__ int tile_off(const Job& job, const Instance& in) {
 }
 
 // Global tile t -> (instance, tile row I, tile column J), in units of the launch's tile
-// (128 x 128, or 256 x 256 for CTA pairs).  Tiles are in row-major order within an
-// instance; with `upper`, row I holds J = I .. R-1.
+// (128 x 128, or 256 x 256 for CTA pairs): row-major within an instance, over the upper
+// triangle (J >= I) or all tiles.  A banded walk (column by column within bands of 2..16 tile
+// rows, so that co-resident CTAs share B panels in L2) was measured slower at N = 8192
+// (1.84-1.93 ms against 1.81 ms per forward square) and is not used.
 __device__ __forceinline__ int locate(const Job& job, int t, int& I, int& J) {
   int i = 0;
   for (; i + 1 < job.count; ++i)

@@ -1,8 +1,13 @@
 """Parity of the FP64 GPU path (through the C ABI) with the CPU FP64 oracle.
 
 Tolerance: ||D - D_oracle||_F / sqrt(nocc) <= 1e-10 and the stopping iteration
-within +-1 of the oracle's.  Both sides compute in FP64 but sum in different
-orders, so the histories agree to rounding until the stagnation floor.
+within +-2 of the oracle's.  Both sides compute in FP64 but sum in different
+orders, so the histories agree to rounding until the stagnation floor.  There the
+stop conditions compare rounding-level values: the trace guard's order condition
+(the order estimate over v_{i-1}, v_{i-3} below q~) is borderline on the square
+after v reaches the floor (N = 64: 1.799 against 1.8) and certain two squares
+later, so the two sides may stop up to two squares apart (rounding-sized
+perturbations of the oracle's iterates move its stop by -2 .. +2 on these inputs).
 """
 import math
 
@@ -35,7 +40,7 @@ def run_gpu(sp2mod, F_np, nocc, **opts):
 
 def compare_with_oracle(D, info, res, nocc, tol=TOL_FP64):
     assert info["status"] == 0
-    assert abs(info["n_iter"] - res.n) <= 1, (info["n_iter"], res.n)
+    assert abs(info["n_iter"] - res.n) <= 2, (info["n_iter"], res.n)
     assert o.rel_error(D, res.D, nocc) <= tol
     m = min(info["n_iter"], res.n)
     assert list(info["p"][1:m + 1]) == list(res.p[1:m + 1])
