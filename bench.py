@@ -54,8 +54,8 @@ def workload_name(N, nocc, gap):
 
 
 # DRAM bytes (read + write) of one forward-square launch from an ncu capture of the current
-# kernel (profiles/tc_gemm_pair_sp2_forward_dram_ld8192.md), keyed by (N, tile kind).
-FWD_TRAFFIC_BYTES = {}
+# kernel (profiles/tc_gemm_pair_sp2_forward_dram_ld8192.md), keyed by (N, tile kind, precision).
+FWD_TRAFFIC_BYTES = {(8192, "pair", "fp16x3"): 1.45e9 + 242.5e6}
 FP32_FLOP_PER_CLK_SM = 256     # 128 FP32 FMA lanes per SM
 
 
@@ -714,11 +714,27 @@ def main():
             e2e_dev.append(d0.elapsed_time(d1))      # device span of the call: copies + run
             e2e_loop.append(P.info()["loop_ms"])     # device time of the same call's loop
         ec = eclk.stop()
+        # the same copies alone (torch, same pinned buffers) and a resident run right after, with
+        # CUDA events: the parts of the e2e device span
+        def span(fn):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1)
+        F_probe = torch.empty_like(F)
+        parts = {"h2d_ms": span(lambda: F_probe.copy_(F_h, non_blocking=True)),
+                 "d2h_ms": span(lambda: D_h.copy_(F_probe, non_blocking=True)),
+                 "resident_run_ms": span(lambda: P.run(F, D, stream))}
+        del F_probe
         # the clocks of these steps: a long run under the power cap can drift below the clocks of
         # the device-timed steps, which then shows up in the gap between e2e and value
         e2e = {"value": max_over_ranks(statistics.mean(e2e_ms), ws), "unit": "ms",
                "h2d_bytes_per_step": N * N * 8, "d2h_bytes_per_step": N * N * 8,
-               "steps_ms": e2e_ms, "device_span_ms": e2e_dev, "loop_ms": e2e_loop,
+               "steps_ms": e2e_ms, "device_span_ms": e2e_dev, "loop_ms": e2e_loop, "parts": parts,
                "value_loop_ms": statistics.mean(loop_ms),
                "sm_mhz": ec.get("sm_mhz"), "reasons": ec.get("reasons")}
 

@@ -150,26 +150,20 @@ __global__ void __launch_bounds__(TTHREADS, 1) bsr_tc_kernel(const TcArgs a) {
               ok = false;
               break;
             }
-            int pos[TTR + TTC];
-            #pragma unroll
-            for (int j = 0; j < TTR + TTC; ++j) pos[j] = __shfl_sync(0xffffffffu, posj, j);
+            // lane j < 12 copies its own block's two pieces: row j of A (j < 4) or row j - 4 of B;
+            // the expected bytes are armed first, so no copy can complete the phase early
             if (lane == 0) {
-              uint8_t* sA = smem + stage * TSTAGE;
-              uint8_t* sB = sA + 2 * A_PLANE;
               mbar_arrive_expect_tx(&full_bar[stage], TSTAGE);
-              #pragma unroll
-              for (int j = 0; j < TTR; ++j)
-                #pragma unroll
-                for (int p = 0; p < 2; ++p)
-                  tma_load_3d(sA + p * A_PLANE + j * PIECE_BYTES, map, 0, 0, 2 * pos[j] + p, &full_bar[stage]);
-              #pragma unroll
-              for (int j = 0; j < TTC; ++j)
-                #pragma unroll
-                for (int p = 0; p < 2; ++p)
-                  tma_load_3d(sB + p * B_PLANE + j * PIECE_BYTES, map, 0, 0, 2 * pos[TTR + j] + p,
-                              &full_bar[stage]);
               armed[stage] = 1;
               armed_par[stage] = phase;
+            }
+            __syncwarp();
+            if (lane < TTR + TTC) {
+              uint8_t* dst = smem + stage * TSTAGE +
+                             (lane < TTR ? lane * PIECE_BYTES : 2 * A_PLANE + (lane - TTR) * PIECE_BYTES);
+              const int plane = lane < TTR ? A_PLANE : B_PLANE;
+              tma_load_3d(dst, map, 0, 0, 2 * posj, &full_bar[stage]);
+              tma_load_3d(dst + plane, map, 0, 0, 2 * posj + 1, &full_bar[stage]);
             }
             if (++stage == TSTG) { stage = 0; phase ^= 1; }
           }
