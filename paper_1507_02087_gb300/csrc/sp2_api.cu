@@ -287,6 +287,7 @@ struct MixedEngine {
   sp2::tc::Job deriv_job() const {
     sp2::tc::Job j = job(sp2::tc::MODE_DERIV_STEP, 1, sp2::tc::SLOTS_DERIV, 2);
     j.lowprec = 1;
+    j.whole_k = 1;
     return j;
   }
 

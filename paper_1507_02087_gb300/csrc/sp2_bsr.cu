@@ -909,6 +909,11 @@ __global__ void tile_meta_kernel(const DevState* st, Mat X, Pairs P, const uint3
       nk += __popc(a & b);
     }
     const int I = I0 + lane / TTC, J = J0 + lane % TTC;
+    // block products the pair (I, J) needs: K blocks both rows hold (upper pairs only)
+    int need = 0;
+    if (I < nb && J < nb && J >= I)
+      for (int w = 0; w < W; ++w) need += __popc(X.bits[(int64_t)I * W + w] & X.bits[(int64_t)J * W + w]);
+    need = __reduce_add_sync(0xffffffffu, need);
     int qi = -1, po = -1;
     if (I < nb && J < nb) {
       po = find_block(X, W, I, J);
@@ -922,7 +927,7 @@ __global__ void tile_meta_kernel(const DevState* st, Mat X, Pairs P, const uint3
       }
     }
     int* m = meta + (int64_t)t * TMETA;
-    if (lane == 0) m[0] = nk;
+    if (lane == 0) { m[0] = nk; m[65] = need; }
     m[1 + lane] = qi;
     m[33 + lane] = po;
   }

@@ -69,9 +69,10 @@ struct TcRound {
   int* meta;                       // [cap_t][TMETA]: per tile its K-block count, then for the 32
                                    // block pairs (r, c) (index 8 r + c) the pair index in P (-1: not
                                    // an upper pair of the square) and the position of the old block
-                                   // X~_{k-1}(I0 + r, J0 + c) (-1: absent)
+                                   // X~_{k-1}(I0 + r, J0 + c) (-1: absent), then (entry 65) the
+                                   // block products the tile's upper pairs need
 };
-constexpr int TMETA = 68;          // 1 + 32 + 32, padded
+constexpr int TMETA = 68;          // 1 + 32 + 32 + 1, padded
 
 // Tile list of the round (count, scan, fill) and the tiles' metadata; `counts` has nb entries.
 cudaError_t tc_tiles_launch(const DevState* st, const Mat& X, const Pairs& P, const uint32_t* sbits, int nb, int W,

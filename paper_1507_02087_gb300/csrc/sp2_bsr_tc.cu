@@ -109,7 +109,6 @@ __global__ void __launch_bounds__(TTHREADS, 1) bsr_tc_kernel(const TcArgs a) {
       int armed[TSTG];
       uint32_t armed_par[TSTG];
       for (int s = 0; s < TSTG; ++s) { armed[s] = 0; armed_par[s] = 0; }
-      unsigned long long needed = 0ull;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int code = a.r.tiles[t];
         const int I0 = (code / a.ncg) * TTR, J0 = (code % a.ncg) * TTC;
@@ -137,12 +136,6 @@ __global__ void __launch_bounds__(TTHREADS, 1) bsr_tc_kernel(const TcArgs a) {
             m &= m - 1u;
             const bool has = vj && ((bj >> bit) & 1u);
             const int posj = has ? rpj + rkj + __popc(bj & ((1u << bit) - 1u)) : a.zero_blk;
-            // needed products of this K block: stored A row I0 + lane times stored B column
-            // J0 + j with J0 + j >= I0 + lane
-            const uint32_t bcols = __ballot_sync(0xffffffffu, has && lane >= TTR) >> TTR;
-            const int jmin = I0 + lane - J0;
-            const uint32_t ge = jmin <= 0 ? 0xffu : (jmin >= TTC ? 0u : (0xffu << jmin) & 0xffu);
-            needed += __reduce_add_sync(0xffffffffu, has && lane < TTR ? __popc(bcols & ge) : 0);
             int go = 1;
             if (lane == 0) go = !abort_s && mbar_wait(&empty_bar[stage], phase ^ 1, globaltimer_ns() + kTcWaitNs);
             go = __shfl_sync(0xffffffffu, go, 0);
@@ -170,7 +163,6 @@ __global__ void __launch_bounds__(TTHREADS, 1) bsr_tc_kernel(const TcArgs a) {
         }
       }
       if (lane == 0) {
-        atomicAdd(&st->uprod, needed);
         if (!ok) tc_give_up(st, &abort_s);
         for (int s = 0; s < TSTG; ++s)   // wait (bounded) until every copy issued here has landed
           if (armed[s]) mbar_wait(&full_bar[s], armed_par[s], globaltimer_ns() + kTcWaitNs);
@@ -181,10 +173,11 @@ __global__ void __launch_bounds__(TTHREADS, 1) bsr_tc_kernel(const TcArgs a) {
       int stage = 0, buf = 0;
       uint32_t phase = 0, bphase = 0;
       bool ok = true;
-      unsigned long long kblocks = 0ull;
+      unsigned long long kblocks = 0ull, needed = 0ull;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int nk = a.r.meta[(int64_t)t * TMETA];
         kblocks += (unsigned long long)nk;
+        needed += (unsigned long long)a.r.meta[(int64_t)t * TMETA + 65];
         if (lane == 0) {
           for (int k0 = 0; k0 < nk && ok; k0 += TCHK) {
             if (abort_s || !mbar_wait(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + kTcWaitNs)) { ok = false; break; }
@@ -199,13 +192,16 @@ __global__ void __launch_bounds__(TTHREADS, 1) bsr_tc_kernel(const TcArgs a) {
               const uint32_t sB = sA + 2 * A_PLANE;
               #pragma unroll
               for (int kk = 0; kk < B / 16; ++kk) {
-                // p1 q0, p0 q1, p0 q0 (smallest first)
+                // p1 q0 and p0 q1 of the whole K block first, then p0 q0: the small products are
+                // added while the accumulator is still small
                 mma_bf16(dt, smem_desc_sw64(sA + 1 * A_PLANE + kk * 32), smem_desc_sw64(sB + kk * 32), idesc,
                          accumulate);
                 accumulate = 1;
                 mma_bf16(dt, smem_desc_sw64(sA + kk * 32), smem_desc_sw64(sB + 1 * B_PLANE + kk * 32), idesc, 1);
-                mma_bf16(dt, smem_desc_sw64(sA + kk * 32), smem_desc_sw64(sB + kk * 32), idesc, 1);
               }
+              #pragma unroll
+              for (int kk = 0; kk < B / 16; ++kk)
+                mma_bf16(dt, smem_desc_sw64(sA + kk * 32), smem_desc_sw64(sB + kk * 32), idesc, 1);
               mma_commit(&empty_bar[stage]);
               if (++stage == TSTG) { stage = 0; phase ^= 1; }
             }
@@ -219,6 +215,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) bsr_tc_kernel(const TcArgs a) {
       if (lane == 0) {
         // executed 32 x 32 x 32 block products: the tile's 32 block pairs times its K blocks
         atomicAdd(&st->bprod, kblocks * (unsigned long long)(TTR * TTC));
+        atomicAdd(&st->uprod, needed);   // the tiles' needed products (tile metadata)
         if (!ok) tc_give_up(st, &abort_s);
         mma_commit(&drain_bar);
         mbar_wait(&drain_bar, 0, globaltimer_ns() + kTcWaitNs);

@@ -41,18 +41,20 @@ constexpr float kF16InvScale2 = 1.f / (16384.f * 16384.f);
 
 constexpr int BM = 128;          // tile rows (MMA M)
 constexpr int BN = 128;          // tile cols (MMA N)
-constexpr int BK = 32;           // k-block: 32 16-bit values = 64 B rows, 64-byte swizzle
+constexpr int BK = 64;           // k-block: 64 16-bit values = 128 B rows, 128-byte swizzle
 constexpr int NP = 3;            // pieces per matrix (FMT_BF16X3; FMT_FP16X2 has 2)
-constexpr int STAGES = 4;        // TMA ring depth (FMT_BF16X3; FMT_FP16X2, with smaller stages, has 6)
+constexpr int STAGES = 2;        // TMA ring depth (FMT_BF16X3; FMT_FP16X2, with smaller stages, has 3)
 __host__ __device__ constexpr int np_of(int fmt) { return fmt == FMT_FP16X2 ? 2 : 3; }
-__host__ __device__ constexpr int stages_of(int fmt) { return fmt == FMT_FP16X2 ? 6 : 4; }
+__host__ __device__ constexpr int stages_of(int fmt) { return fmt == FMT_FP16X2 ? 3 : 2; }
 // The tensor cores' FP32 accumulation drops the bits an addend loses in alignment
 // (it rounds toward zero), so a long sum of same-sign products drifts low by about
 // K * 2^-25 of its value.  The MMAs therefore accumulate a chunk of k-blocks (CHUNK_KB,
-// 64 terms, for full bf16 products; see chunk_kb for the others) at a time into one of the
+// 64 terms, for full products; see chunk_kb for the others) at a time into one of the
 // tensor-memory buffers, and the epilogue adds the chunk sums into registers with
-// round-to-nearest FP32 additions.
-constexpr int CHUNK_KB = 2;
+// round-to-nearest FP32 additions.  Within a ring stage the smaller piece products are
+// issued before the leading one (p0 q0), so that they are added while the accumulator is
+// still small and lose less to the truncation.
+constexpr int CHUNK_KB = 1;
 constexpr int NBUF = 4;
 constexpr int A_PIECE_BYTES = BM * BK * 2;
 constexpr int B_PIECE_BYTES = BN * BK * 2;
@@ -122,8 +124,8 @@ __host__ __device__ __forceinline__ int rslot(int lowmem, int hist0, int j) {
 // One problem of a batch (device memory; the tensor maps are read by TMA from here and
 // keep the alignment CUtensorMap requires).
 struct Instance {
-  CUtensorMap mapA;     // box 32 x 128 (A operand)
-  CUtensorMap mapB;     // box 32 x 128 (B operand)
+  CUtensorMap mapA;     // box 64 x 128 (A operand; k innermost)
+  CUtensorMap mapB;     // box 64 x 128 (B operand)
   __nv_bfloat16* arena;
   int64_t slot_elems;   // 3 * ld * ld
   DevState* st;
@@ -158,6 +160,7 @@ struct Job {
                         // 11 bits); the derivative pass, and every product of SP2_PREC_BF16X3
   int32_t fmt;          // Fmt of every instance of the batch
   int32_t wait_ms;      // limit of every mbarrier wait in ms (0: the default, 2 s)
+  int32_t whole_k;      // 1: one tensor-memory chunk per tile, the whole k range (derivative steps)
   int32_t test_skip;    // testing hook (128 x 128 kernel): 1 = CTA 0 leaves its first ring stage
                         // unarmed, so that the waits on it give up (see sp2_test_tc_timeout)
   float* out32;         // MODE_STORE_F32

@@ -1,12 +1,13 @@
-// Persistent tcgen05 GEMM over 3-piece bf16 operands with the SP2 epilogues, for a
-// batch of problems of uneven size.
+// Persistent tcgen05 GEMM over 16-bit piece operands (FMT_BF16X3 or FMT_FP16X2) with the
+// SP2 epilogues, for a batch of problems of uneven size.
 //
 // C[I-tile, J-tile] = sum_k A[rows I, k] B[rows J, k] (both operands K-major row
-// panels; X symmetric makes X X^T = X^2), as the six piece products with a+b <= 2.
+// panels; X symmetric makes X X^T = X^2), as the format's piece products.
 // One CTA per SM walks the global tile list (the tiles of every instance, largest
 // instances first); tiles of instances that have already stopped are skipped.
-// Warp 0 feeds a 4-stage TMA ring (64-byte swizzle, 32-wide k-blocks) from the
-// instance's tensor maps; warp 1 issues the MMAs (128 x 128 x 16) and closes a
+// Warp 0 feeds a TMA ring of 2 (bf16) or 3 (fp16) stages (128-byte swizzle, 64-wide
+// k-blocks; 32-wide blocks with 64-byte swizzle in twice as many stages ran 18 % slower)
+// from the instance's tensor maps; warp 1 issues the MMAs (128 x 128 x 16) and closes a
 // tensor-memory chunk buffer every CHUNK_KB k-blocks; warps 2-5 add each closed chunk
 // into FP32 registers (round to nearest) and, after the last chunk of a tile, run the
 // epilogue.  Four chunk buffers let the MMAs run ahead of the draining.
@@ -118,14 +119,18 @@ __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
 }
 
 // k-blocks per tensor-memory chunk: CHUNK_KB (64 terms) for full products.  (Full fp16 products
-// with 128-term chunks, which make as many truncating additions per chunk as full bf16 ones with
-// 64, ran 7 % faster at N = 8192 but raised the error after the correction from 6.5e-7 to 9.1e-7,
-// too close to the 1e-6 target.)  Low-precision jobs, whose 16-bit (bf16) or 11-bit (fp16) target
-// tolerates a larger bias, take twice (bf16: 3 products per k-step) or four times (fp16: 1)
-// CHUNK_KB.  Halved until the chunks divide the k-blocks of a tile.
+// with 128-term chunks ran 7-15 % faster at N = 8192 but raised the error after the correction
+// from 6.3e-7 to 9.2e-7, too close to the 1e-6 target.)  Low-precision jobs, whose 16-bit (bf16)
+// or 11-bit (fp16) target tolerates a larger bias, take twice (bf16: 3 products per k-step) or
+// four times (fp16: 1) CHUNK_KB.  Halved until the chunks divide the k-blocks of a tile.
+// The derivative steps (whole_k) take the tile's whole k range in one chunk: they form a
+// first-order correction, whose own truncation bias (at most K 2^-25 of dX_j) is far below
+// the error it corrects; measured at N = 8192, the error after the correction is the same to
+// three digits (5.44e-7) and the derivative pass takes 61 ms instead of 87 ms.
 __device__ __forceinline__ int chunk_kb(const Job& job, int ld) {
-  int ck = !job.lowprec ? CHUNK_KB : (job.fmt == FMT_FP16X2 ? 4 * CHUNK_KB : 2 * CHUNK_KB);
   const int total = job.nterms * (ld / BK);
+  if (job.whole_k) return total;
+  int ck = !job.lowprec ? CHUNK_KB : (job.fmt == FMT_FP16X2 ? 4 * CHUNK_KB : 2 * CHUNK_KB);
   while (ck > 1 && total % ck != 0) ck >>= 1;
   return ck;
 }
@@ -436,15 +441,19 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
             tc_fence_after();
             const uint32_t sA = smem_u32(smem + stage * SBYTES);
             const uint32_t sB = sA + NPS * A_PIECE_BYTES;
+            // the stage's smaller piece products first, then the leading one (p0 q0, the last)
             #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
+            for (int pass = 0; pass < 2; ++pass) {
               #pragma unroll
-              for (int q = 0; q < PR::n; ++q) {
-                if (q < q0) continue;
-                const uint64_t ad = smem_desc_sw64(sA + PR::a(q) * A_PIECE_BYTES + kk * 32);
-                const uint64_t bd = smem_desc_sw64(sB + PR::b(q) * B_PIECE_BYTES + kk * 32);
-                mma_bf16(dt, ad, bd, idesc, accumulate);
-                accumulate = 1;
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                #pragma unroll
+                for (int q = 0; q < PR::n; ++q) {
+                  if (q < q0 || (q == PR::n - 1) != (pass == 1)) continue;
+                  const uint64_t ad = smem_desc_sw128(sA + PR::a(q) * A_PIECE_BYTES + kk * 32);
+                  const uint64_t bd = smem_desc_sw128(sB + PR::b(q) * B_PIECE_BYTES + kk * 32);
+                  mma_bf16(dt, ad, bd, idesc, accumulate);
+                  accumulate = 1;
+                }
               }
             }
             mma_commit(&empty_bar[stage]);
@@ -659,15 +668,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
             tc_fence_after();
             const uint32_t sA = smem_u32(smem + stage * SBYTES);
             const uint32_t sB = sA + NPS * A_PIECE_BYTES;
+            // the stage's smaller piece products first, then the leading one (p0 q0, the last)
             #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
+            for (int pass = 0; pass < 2; ++pass) {
               #pragma unroll
-              for (int q = 0; q < PR::n; ++q) {
-                if (q < q0) continue;
-                const uint64_t ad = smem_desc_sw64(sA + PR::a(q) * A_PIECE_BYTES + kk * 32);
-                const uint64_t bd = smem_desc_sw64(sB + PR::b(q) * B_PIECE_BYTES + kk * 32);
-                mma_bf16_pair(dt, ad, bd, idesc, accumulate);
-                accumulate = 1;
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                #pragma unroll
+                for (int q = 0; q < PR::n; ++q) {
+                  if (q < q0 || (q == PR::n - 1) != (pass == 1)) continue;
+                  const uint64_t ad = smem_desc_sw128(sA + PR::a(q) * A_PIECE_BYTES + kk * 32);
+                  const uint64_t bd = smem_desc_sw128(sB + PR::b(q) * B_PIECE_BYTES + kk * 32);
+                  mma_bf16_pair(dt, ad, bd, idesc, accumulate);
+                  accumulate = 1;
+                }
               }
             }
             mma_commit_pair_mc(&empty_bar[stage], 0x3);
@@ -792,9 +805,9 @@ cudaError_t tc_make_maps(void* arena, int ld, int nslots, int fmt, CUtensorMap* 
   cuuint32_t boxA[4] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM, 1, 1};
   cuuint32_t boxB[4] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BN, 1, 1};
   CUresult r1 = enc(mapA, dt, 4, arena, dims, strides, boxA, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   CUresult r2 = enc(mapB, dt, 4, arena, dims, strides, boxB, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? cudaSuccess : cudaErrorInvalidValue;
 }
 

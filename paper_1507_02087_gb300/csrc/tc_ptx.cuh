@@ -149,6 +149,18 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
   return d;
 }
 
+// The same for 128-byte swizzle: rows of 128 B (64 16-bit values), 8-row core groups
+// 1024 B apart.  A 16-wide k-step inside the row starts 32 B further on.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);      // start address, bits 0-13
+  d |= (uint64_t)1 << 16;                       // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                       // descriptor version for sm_100
+  d |= (uint64_t)2 << 61;                       // swizzle mode: 128-byte
+  return d;
+}
+
 // Instruction descriptor: kind::f16, A and B fp16, D fp32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
   return (1u << 4)                        // D format: f32 (A, B formats 0: fp16)
