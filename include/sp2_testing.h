@@ -51,6 +51,20 @@ int32_t sp2_test_tc_gemm_ex(const void* arena_dev, int32_t ld, int32_t nslots, i
  * involved: the kernel returns normally and the context stays usable. */
 int32_t sp2_test_tc_timeout(const void* arena_dev, int32_t ld, int32_t wait_ms, float* out_dev, void* stream);
 
+/* 1 if this library was built with device-side bounds checks (libsp2_debug.so, built with
+ * SP2_DEVICE_CHECKS=1), 0 for the release library. */
+int32_t sp2_build_device_checks(void);
+
+/* A device-side bounds check made to fail, debug library only: one launch of the bf16 product
+ * of sp2_test_tc_gemm over an arena of `nslots` slots (ld a multiple of 128, 128 x 128 tiles)
+ * whose A operand is slot `bad_slot`, nslots <= bad_slot < nslots + 1024, which the host does not
+ * reject here.  That slot only addresses tensor-map loads, which read zeros outside the map, so
+ * the launch is safe even without the check; with it, every tile is skipped and the call returns
+ * SP2_ERR_BOUNDS.  The release library returns SP2_ERR_UNSUPPORTED without launching anything.
+ * Synchronises `stream`. */
+int32_t sp2_test_tc_bounds(const void* arena_dev, int32_t ld, int32_t nslots, int32_t bad_slot, float* out_dev,
+                           void* stream);
+
 /* Block truncation decision of the block-sparse path on its own: for every 32 x 32 block
  * (I, J) of the dense, symmetric N x N FP32 device matrix, keep_dev[I * (N/32) + J] = 1 if
  * the block is kept, else 0, under `rule` (an sp2_trunc_rule of sp2.h): SP2_TRUNC_BLOCK

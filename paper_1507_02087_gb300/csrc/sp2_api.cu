@@ -63,6 +63,7 @@ extern "C" const char* sp2_status_string(int32_t s) {
     case SP2_ERR_NOMEM: return "out of device memory";
     case SP2_ERR_NO_GAP: return "F has zero spectral width (no gap)";
     case SP2_ERR_UNSUPPORTED: return "unsupported option";
+    case SP2_ERR_BOUNDS: return "device-side bounds check failed (debug library)";
     default: return "unknown status";
   }
 }
@@ -160,6 +161,7 @@ static int tune_tiles(const std::vector<int64_t>& N, int fmt, int lowprec) {
       I.arena = arena;
       I.fmt = fmt;
       I.np = np;
+      I.nslots = 2;
       I.slot_elems = (int64_t)np * ld * ld;
       I.tile_off_upper = I.tile_off_upper2 = tiles;
       tiles += sp2::tc_tiles(ld, 1, pair);
@@ -361,6 +363,7 @@ struct MixedEngine {
       I.f_slot = base + 3;
       I.r0_slot = base + 4;
       const int nslots = base + 6;
+      I.nslots = nslots;
       I.fmt = fmt;
       I.np = np;
       I.slot_elems = (int64_t)np * ld * ld;

@@ -63,6 +63,7 @@ struct TcArgs {
   int parity;
   int nb, W, ncg;                                  // ncg: column groups of 8 blocks
   int zero_blk;                                    // index of the all-zero block
+  int64_t pair_cap;                                // capacity of the square's pair arrays
   TcRound r;
 };
 
@@ -135,7 +136,8 @@ __global__ void __launch_bounds__(TTHREADS, 1) bsr_tc_kernel(const TcArgs a) {
             const int bit = __ffs(m) - 1;
             m &= m - 1u;
             const bool has = vj && ((bj >> bit) & 1u);
-            const int posj = has ? rpj + rkj + __popc(bj & ((1u << bit) - 1u)) : a.zero_blk;
+            int posj = has ? rpj + rkj + __popc(bj & ((1u << bit) - 1u)) : a.zero_blk;
+            if (!dcheck(posj >= 0 && posj <= a.zero_blk, &st->status)) posj = a.zero_blk;
             int go = 1;
             if (lane == 0) go = !abort_s && mbar_wait(&empty_bar[stage], phase ^ 1, globaltimer_ns() + kTcWaitNs);
             go = __shfl_sync(0xffffffffu, go, 0);
@@ -282,8 +284,9 @@ __global__ void __launch_bounds__(TTHREADS, 1) bsr_tc_kernel(const TcArgs a) {
       for (int g = 0; g < 4; ++g) {
         const int J = J0 + 4 * hc + g;
         const int qi = qis[g];               // -1: not an upper pair of the square's pattern
-        if (qi < 0) continue;
-        const int po = pos[g];
+        if (qi < 0 || !dcheck(qi < a.pair_cap, &st->status)) continue;
+        int po = pos[g];
+        if (po >= 0 && !dcheck(po < a.zero_blk, &st->status)) po = -1;
         float old[32];
         if (po >= 0) {
           const float4* src = reinterpret_cast<const float4*>(X.vals + (int64_t)po * BE + lane * B);
@@ -408,6 +411,7 @@ cudaError_t tc_numeric_launch(DevState* st, const Mat& X, const TcMaps* maps, in
   a.W = W;
   a.ncg = (nb + TTC - 1) / TTC;
   a.zero_blk = nb * nb;
+  a.pair_cap = (int64_t)nb * (nb + 1) / 2;
   a.r = r;
   bsr_tc_kernel<<<tc_grid(), TTHREADS, TSMEM, s>>>(a);
   return cudaGetLastError();

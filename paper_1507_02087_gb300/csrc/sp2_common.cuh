@@ -11,7 +11,28 @@
 
 #include "../../include/sp2.h"
 
+// Debug builds (-DSP2_DEVICE_CHECKS=1, the library libsp2_debug.so) check indices that the
+// device computes from its own state against the buffers they address.  A failed check
+// records SP2_ERR_BOUNDS in the run's error word and the guarded access is skipped; release
+// builds compile the checks away.
+#ifndef SP2_DEVICE_CHECKS
+#define SP2_DEVICE_CHECKS 0
+#endif
+
 namespace sp2 {
+
+// `ok` in release builds; in debug builds a false `ok` also records SP2_ERR_BOUNDS in *err
+// (the first error recorded wins).
+__device__ __forceinline__ bool dcheck(bool ok, int32_t* err) {
+#if SP2_DEVICE_CHECKS
+  if (!ok) atomicCAS(err, 0, (int32_t)SP2_ERR_BOUNDS);
+  return ok;
+#else
+  (void)ok;
+  (void)err;
+  return true;
+#endif
+}
 
 // C_2^sp = (71 + 17 sqrt(17)) / 32 (§4), written as a literal of the closed form.
 constexpr double kC2sp = 4.409149863609382;  // the double nearest the closed form

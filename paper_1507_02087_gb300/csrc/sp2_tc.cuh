@@ -142,6 +142,7 @@ struct Instance {
   double* mscr;             // mixed-norm scratch ((ld/128)^2 + 2 ld/128 doubles), or null
   int32_t fmt;              // Fmt of the arena
   int32_t np;               // pieces (planes) per slot: np_of(fmt)
+  int32_t nslots;           // slots of the arena (the tensor maps' outermost extent)
 };
 
 struct Job {

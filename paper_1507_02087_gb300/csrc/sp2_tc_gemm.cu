@@ -54,7 +54,7 @@ __device__ __forceinline__ void acc_coefs(const DevState* st, int j, bool deriv,
   r.cc = deriv ? 0.f : (float)c;
 }
 
-__device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
+__device__ __forceinline__ Resolved resolve_slots(const Job& j, const Instance& I) {
   Resolved r;
   r.a[0] = j.a_slot[0]; r.a[1] = j.a_slot[1];
   r.b[0] = j.b_slot[0]; r.b[1] = j.b_slot[1];
@@ -115,6 +115,36 @@ __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I) {
     }
     default: break;
   }
+  return r;
+}
+
+// The slots of tile (I, J) of instance I.  Debug builds also check the tile and every slot the
+// job's mode touches against the instance (and the history index against the device state's
+// arrays); a tile that fails is skipped by every warp role alike.
+__device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I, int ti, int tj) {
+#if SP2_DEVICE_CHECKS
+  // the history indices first: resolve_slots reads the state's arrays at them
+  if (j.rule != SLOTS_FIXED &&
+      !dcheck(I.st->k >= 0 && I.st->k < SP2_MAX_ITER + 1 && I.st->dk >= 0 && I.st->dk < SP2_MAX_ITER + 1 &&
+                  I.st->n_out >= 0 && I.st->n_out < SP2_MAX_ITER + 2, j.err)) {
+    Resolved z = {};
+    z.active = false;
+    return z;
+  }
+#endif
+  Resolved r = resolve_slots(j, I);
+#if SP2_DEVICE_CHECKS
+  const int ns = I.nslots, T = j.pair ? PT : BM;
+  bool ok = ti >= 0 && tj >= 0 && (ti + 1) * T <= I.ld && (tj + 1) * T <= I.ld;
+  for (int t = 0; t < j.nterms; ++t) ok = ok && r.a[t] >= 0 && r.a[t] < ns && r.b[t] >= 0 && r.b[t] < ns;
+  if (j.mode != MODE_STORE_F32) ok = ok && r.out >= 0 && r.out < ns;
+  if (j.mode == MODE_SP2_STEP || j.mode == MODE_DERIV_STEP || j.mode == MODE_DF_COMBINE)
+    ok = ok && r.in >= 0 && r.in < ns;
+  if (!dcheck(ok, j.err)) r.active = false;
+#else
+  (void)ti;
+  (void)tj;
+#endif
   return r;
 }
 
@@ -381,7 +411,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
         int I, J;
         const int ii = locate(job, t, I, J);
         const Instance& In = job.inst[ii];
-        const Resolved R = resolve(job, In);
+        const Resolved R = resolve(job, In, I, J);
         if (!R.active) continue;
         const CUtensorMap* mA = &In.mapA;
         const CUtensorMap* mB = &In.mapB;
@@ -429,7 +459,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
         int I, J;
         const int ii = locate(job, t, I, J);
         const Instance& In = job.inst[ii];
-        if (!resolve(job, In).active) continue;
+        if (!resolve(job, In, I, J).active) continue;
         const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job, In.ld);
         for (int ch = 0; ch < nchunks && ok; ++ch) {
           if (abort_s || !mbar_wait(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + wait_ns)) { ok = false; break; }
@@ -478,7 +508,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
       int I, J;
       const int ii = locate(job, t, I, J);
       const Instance& In = job.inst[ii];
-      const Resolved R = resolve(job, In);
+      const Resolved R = resolve(job, In, I, J);
       if (!R.active) continue;
       const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job, In.ld);
       float acc[BN / 32][32];
@@ -549,7 +579,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
 // `full` barrier, which the even CTA arms for both.  The even CTA's MMA thread issues
 // 256 x 256 x 16 pair MMAs and multicasts each commit to both CTAs (`empty` stage
 // barriers, `accf` chunk barriers); every epilogue warp of both CTAs arrives on the even
-// CTA's `acce` barrier once it has drained a chunk buffer.
+// CTA's `acce` barrier once it has drained a chunk buffer.  Every poll of a barrier is a
+// CTA-scope try_wait: what a phase orders is either counted by the barrier itself (TMA bytes,
+// MMA commits) or tensor memory, which the tcgen05 fences around the remote arrive order; the
+// cluster-scope acquire form cost 3 % of the run at N = 8192 in memory-barrier stalls.
 constexpr int P_SMEM_BYTES = STAGES * STAGE_BYTES + 8192 + 1024;   // + alignment and read slack
 
 template <int FMT>
@@ -599,7 +632,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
         int I, J;
         const int ii = locate(job, t, I, J);
         const Instance& In = job.inst[ii];
-        const Resolved R = resolve(job, In);
+        const Resolved R = resolve(job, In, I, J);
         if (!R.active) continue;
         const CUtensorMap* mA = &In.mapA;
         const CUtensorMap* mB = &In.mapB;
@@ -608,7 +641,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
         const int rowB = J * PT + (int)rank * BN;
         for (int term = 0; term < job.nterms && ok; ++term) {
           for (int kb = 0; kb < nkb; ++kb) {
-            if (abort_s || !mbar_wait_cluster(&empty_bar[stage], phase ^ 1, globaltimer_ns() + wait_ns)) {
+            if (abort_s || !mbar_wait(&empty_bar[stage], phase ^ 1, globaltimer_ns() + wait_ns)) {
               ok = false;
               break;
             }
@@ -636,7 +669,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
       }
       if (rank == 0)
         for (int s = 0; s < STG; ++s)
-          if (armed[s]) mbar_wait_cluster(&full_bar[s], armed_par[s], globaltimer_ns() + wait_ns);
+          if (armed[s]) mbar_wait(&full_bar[s], armed_par[s], globaltimer_ns() + wait_ns);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer (even CTA) ----------------
@@ -650,10 +683,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
         int I, J;
         const int ii = locate(job, t, I, J);
         const Instance& In = job.inst[ii];
-        if (!resolve(job, In).active) continue;
+        if (!resolve(job, In, I, J).active) continue;
         const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job, In.ld);
         for (int ch = 0; ch < nchunks && ok; ++ch) {
-          if (abort_s || !mbar_wait_cluster(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + wait_ns)) {
+          if (abort_s || !mbar_wait(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + wait_ns)) {
             ok = false;
             break;
           }
@@ -661,7 +694,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
           const uint32_t dt = tmem_base + (uint32_t)(buf * PT);
           uint32_t accumulate = 0;
           for (int kc = 0; kc < chunk_kb(job, In.ld); ++kc) {
-            if (abort_s || !mbar_wait_cluster(&full_bar[stage], phase, globaltimer_ns() + wait_ns)) {
+            if (abort_s || !mbar_wait(&full_bar[stage], phase, globaltimer_ns() + wait_ns)) {
               ok = false;
               break;
             }
@@ -693,7 +726,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
       }
       if (!ok) { abort_s = 1; atomicExch(job.err, (int)SP2_ERR_TIMEOUT); }
       mma_commit_pair_mc(&drain_bar, 0x1);
-      mbar_wait_cluster(&drain_bar, 0, globaltimer_ns() + wait_ns);
+      mbar_wait(&drain_bar, 0, globaltimer_ns() + wait_ns);
     }
    }
   } else {
@@ -709,7 +742,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
       int I, J;
       const int ii = locate(job, t, I, J);
       const Instance& In = job.inst[ii];
-      const Resolved R = resolve(job, In);
+      const Resolved R = resolve(job, In, I, J);
       if (!R.active) continue;
       const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job, In.ld);
       float acc[BN / 32][32];
@@ -719,7 +752,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
         for (int j = 0; j < 32; ++j) acc[g][j] = 0.f;
       for (int ch = 0; ch < nchunks; ++ch) {
         int got = 0;
-        if (lane == 0) got = !abort_s && mbar_wait_cluster(&accf_bar[buf], bphase, globaltimer_ns() + wait_ns);
+        if (lane == 0) got = !abort_s && mbar_wait(&accf_bar[buf], bphase, globaltimer_ns() + wait_ns);
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) {
           if (lane == 0) { abort_s = 1; atomicExch(job.err, (int)SP2_ERR_TIMEOUT); }
@@ -923,6 +956,17 @@ extern "C" int32_t sp2_test_tc_timeout(const void* arena_dev, int32_t ld, int32_
   return run_test_product(arena_dev, ld, 1, 0, 0, 0, 0, 0, 0, wait_ms, 1, out_dev, (cudaStream_t)stream);
 }
 
+extern "C" int32_t sp2_build_device_checks(void) { return SP2_DEVICE_CHECKS ? 1 : 0; }
+
+extern "C" int32_t sp2_test_tc_bounds(const void* arena_dev, int32_t ld, int32_t nslots, int32_t bad_slot,
+                                      float* out_dev, void* stream) {
+  if (!arena_dev || !out_dev || ld <= 0 || ld % sp2::tc::LD_ALIGN != 0 || nslots <= 0 || bad_slot < nslots ||
+      bad_slot >= nslots + 1024)
+    return SP2_ERR_INVALID_ARG;
+  if (!SP2_DEVICE_CHECKS) return SP2_ERR_UNSUPPORTED;
+  return run_test_product(arena_dev, ld, nslots, bad_slot, 0, 0, 0, 0, 0, 0, 0, out_dev, (cudaStream_t)stream);
+}
+
 extern "C" int32_t sp2_test_tc_gemm_ex(const void* arena_dev, int32_t ld, int32_t nslots, int32_t a_slot,
                                        int32_t b_slot, int32_t upper, int32_t tile, int32_t fmt, int32_t lowprec,
                                        float* out_dev, void* stream) {
@@ -947,6 +991,7 @@ static int32_t run_test_product(const void* arena_dev, int32_t ld, int32_t nslot
   hinst.arena = (__nv_bfloat16*)const_cast<void*>(arena_dev);
   hinst.fmt = fmt;
   hinst.np = sp2::tc::np_of(fmt);
+  hinst.nslots = nslots;
   hinst.slot_elems = (int64_t)hinst.np * ld * ld;
   hinst.ld = ld;
   // device copies of the instance record and the error word (test entry point only)

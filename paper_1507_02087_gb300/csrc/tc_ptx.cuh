@@ -207,26 +207,6 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// As mbar_wait, with cluster-scope acquire (arrivals come from both CTAs of the pair).
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, uint64_t deadline) {
-  while (!mbar_try_wait_cluster(bar, parity)) {
-    if (globaltimer_ns() > deadline) return false;
-  }
-  return true;
-}
-
 // 4-D tiled TMA load into this CTA's shared memory whose completion is counted on a
 // barrier of either CTA of the pair (`bar_cluster` from mapa_shared).
 __device__ __forceinline__ void tma_load_4d_pair(void* smem_dst, const CUtensorMap* map, int c0, int c1, int c2,

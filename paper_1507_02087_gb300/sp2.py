@@ -15,12 +15,13 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsp2.so")
+# SP2_LIB=debug selects the build with device-side bounds checks (libsp2_debug.so)
+LIB_PATH = os.path.join(HERE, "libsp2_debug.so" if os.environ.get("SP2_LIB") == "debug" else "libsp2.so")
 
 SP2_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA runtime error", 3: "non-finite value in F",
           4: "device-side wait timed out", 5: "out of device memory", 6: "no gap (F = cI)",
-          7: "unsupported option"}
+          7: "unsupported option", 8: "device-side bounds check failed (debug library)"}
 STOP_ORDER, STOP_TRACE_GUARD, STOP_EXACT, STOP_CAP, STOP_SCHEDULE = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": 0, "mixed": 1, "bf16x6": 1, "bf16x3": 2, "fp16x3": 3}
 MAX_ITER = 512
@@ -80,6 +81,10 @@ def lib() -> ctypes.CDLL:
         L.sp2_test_tc_gemm_ex.restype = i32
         L.sp2_test_tc_timeout.argtypes = [vp, i32, i32, vp, vp]
         L.sp2_test_tc_timeout.restype = i32
+        L.sp2_build_device_checks.argtypes = []
+        L.sp2_build_device_checks.restype = i32
+        L.sp2_test_tc_bounds.argtypes = [vp, i32, i32, i32, vp, vp]
+        L.sp2_test_tc_bounds.restype = i32
         L.sp2_run_fp64_noalloc.argtypes = [vp, vp, i64, i64, vp, vp]
         L.sp2_run_fp64_noalloc.restype = i32
         L.sp2_set_homo_lumo.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]

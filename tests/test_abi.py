@@ -130,3 +130,28 @@ def test_binding_types_every_declared_function(built):
     L = sp2.lib()
     untyped = [n for n in declared_functions() if getattr(L, n).argtypes is None]
     assert not untyped, f"no argtypes in the binding: {untyped}"
+
+
+LIB_DEBUG = os.path.join(ROOT, "paper_1507_02087_gb300", "libsp2_debug.so")
+
+
+@pytest.fixture(scope="module")
+def built_debug():
+    if not os.path.exists(LIB_DEBUG):
+        from paper_1507_02087_gb300 import build
+        build.build(debug=True)
+    return LIB_DEBUG
+
+
+def test_debug_library_exports_the_same_boundary_and_says_so(built, built_debug):
+    out = subprocess.run(["nm", "-D", "--defined-only", built_debug], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    assert not [n for n in declared_functions() if n not in exported]
+    dbg = ctypes.CDLL(built_debug)
+    rel = ctypes.CDLL(built)
+    dbg.sp2_build_device_checks.restype = ctypes.c_int32
+    rel.sp2_build_device_checks.restype = ctypes.c_int32
+    assert dbg.sp2_build_device_checks() == 1 and rel.sp2_build_device_checks() == 0
+    dbg.sp2_status_string.restype = ctypes.c_char_p
+    assert dbg.sp2_status_string(8).startswith(b"device-side bounds")
