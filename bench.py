@@ -11,7 +11,8 @@ be within ||D - D_exact||_F / sqrt(nocc) <= 1e-6 of the exact projector; the pla
 path is timed beside it for the comparison.  F (512 MiB FP64) is resident in HBM before
 the timed region; every buffer the loop streams is larger than the 129 MB L2, so no flush
 is needed between steps.  The default line also carries secondary records of the other
-workloads (a batch of 64 uneven problems, the 32^3 block-sparse lattice, SP2-ACC).
+workloads (N = 400 on the FP64 and tensor-core paths, a batch of 64 uneven problems, the 32^3
+block-sparse lattice, SP2-ACC).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line (rank 0).
@@ -73,7 +74,8 @@ def parse():
                     help="fp16x3 (default): two scaled fp16 pieces, three products; bf16x6 (= mixed): three bf16 "
                          "pieces, six products; bf16x3: two bf16 pieces, three products; fp64: the plain method")
     ap.add_argument("--no-secondary", action="store_true",
-                    help="dense workload: skip the secondary records (batch of 64, 32^3 block-sparse, SP2-ACC)")
+                    help="dense workload: skip the secondary records (N = 400, batch of 64, 32^3 block-sparse, "
+                         "SP2-ACC)")
     ap.add_argument("--refine", choices=["tc", "fp64", "mcweeny"], default="tc",
                     help="mixed path: refinement pair on the tensor cores (tc) or in FP64 (fp64), or one "
                          "McWeeny step with its square in FP64 (mcweeny)")
@@ -825,12 +827,45 @@ def main():
         # the other workloads, each with its own CUDA-event time, error, roofline and clock record
         steps2, warm2 = max(1, min(a.steps, 5)), max(1, min(a.warmup, 2))
         line["secondary"] = {
+            "n400": n400_record(a, local, steps2, warm2),
             "batch64": batch_record(a, local, a.precision, steps2, warm2),
             "bsr32": bsr_record(a, local, max(1, min(a.steps, 3)), 1),
             "sp2_acc": acc_record(a, local, F, D_exact, case.lam, nocc, steps2, warm2),
         }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def n400_record(a, local, steps, warmup):
+    """The small dense case (N = 400, nocc = 200, gap 0.1, seed 0: the construction of the dense
+    tests, plain Alg. 3 with the parameterless stop) on the FP64 path and on the tensor-core path
+    of the headline's precision: time-to-D from CUDA events, error against the exact projector."""
+    import torch
+    from paper_1507_02087_gb300 import inputs, sp2
+    case = inputs.dense_n400()
+    F = case.F.cuda().contiguous()
+    D_exact = case.D_exact.cuda()
+    stream = torch.cuda.current_stream()
+    out = {"workload": "dense N=400 nocc=200 gap=0.1, random-Q (QR of seeded Gaussian, seed 0)"}
+    for prec in ("fp64", a.precision):
+        D = torch.empty_like(F)
+        with sp2.Purifier(400, 200, prec) as P:
+            for _ in range(warmup):
+                P.run(F, D, stream)
+            tms = []
+            for _ in range(steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                P.run(F, D, stream)
+                e1.record(stream)
+                e1.synchronize()
+                tms.append(e0.elapsed_time(e1))
+            info = P.info()
+        out[prec] = {"time_to_d_ms": statistics.mean(tms), "n_iter": info["n_iter"],
+                     "stop_reason": info["stop_reason"], "status": info["status"],
+                     "err_vs_exact": float(torch.linalg.norm(D - D_exact)) / math.sqrt(200)}
+    return out
 
 
 def acc_record(a, local, F, D_exact, lam, nocc, steps, warmup, slack=1e-3):

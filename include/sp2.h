@@ -130,7 +130,10 @@ typedef struct {
                            Lanczos steps on X - X^2 (a lower bound of e_i within about 1e-3
                            relative; X - X^2 scaled and rounded to FP32 once, 35 small launches per
                            square, scratch of 3 ld doubles + ld (ld + 1) floats + 6 KB): FP64
-                           handles only (SP2, SP2-ACC and McWeeny), SP2_ERR_UNSUPPORTED elsewhere.
+                           handles (SP2, SP2-ACC and McWeeny) and single-problem tensor-core
+                           handles (sp2_create with a tensor-core precision; X - X^2 is formed
+                           from the stored X_{k-1} and X_k of the square), SP2_ERR_UNSUPPORTED
+                           for batches.
                            sp2_info.v holds the measure used.  Block-sparse handles take 0 or 1
                            (the mixed norm with the 32 x 32 blocks; see sp2_create_bsr) */
   int32_t bsr_cuda_cores; /* block-sparse handles: 0 = block products on the tcgen05 tensor cores

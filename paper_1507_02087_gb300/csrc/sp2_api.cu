@@ -227,6 +227,7 @@ struct MixedEngine {
   std::vector<void*> arenas;
   std::vector<double*> parts;
   std::vector<double*> mscrs;      // mixed-norm scratch per problem (norm = 1)
+  void* lz = nullptr;              // Lanczos scratch of the spectral-norm stop (norm = 2, one problem)
   double* part_lo = nullptr;
   double* part_hi = nullptr;
   int* part_bad = nullptr;
@@ -251,6 +252,7 @@ struct MixedEngine {
     for (void* a : arenas) cudaFree(a);
     for (double* p : parts) cudaFree(p);
     for (double* p : mscrs) cudaFree(p);
+    cudaFree(lz);
     cudaFree(part_lo);
     cudaFree(part_hi);
     cudaFree(part_bad);
@@ -395,6 +397,13 @@ struct MixedEngine {
         I.mscr = ms;
       }
       SP2_TRY(sp2::tc_make_maps(arenas[k], ld, nslots, fmt, &I.mapA, &I.mapB));
+      if (o.norm == 2) {   // spectral-norm stop: single problems only (one Lanczos scratch)
+        if (count != 1) return SP2_ERR_UNSUPPORTED;
+        if (cudaMalloc(&lz, sp2::lanczos_scratch_bytes(ld)) != cudaSuccess) {
+          (void)cudaGetLastError();
+          return SP2_ERR_NOMEM;
+        }
+      }
       st_host[k] = initial_state(N[k], nocc[k], o, ld, 1);
     }
     total_upper = off_u;
@@ -427,6 +436,12 @@ struct MixedEngine {
     sp2_status s = add_while(graph, nullptr, 0, &cond, &n_fwd, &body);
     if (s != SP2_OK) return s;
     SP2_TRY(sp2::tc_add_node(body, nullptr, 0, job(MODE_SP2_STEP, 1, SLOTS_FORWARD), &n_sq));
+    if (lz) {   // e_{k-1} (Lanczos) between the square and the stop test
+      cudaGraphNode_t n_lz;
+      SP2_TRY(sp2::add_lanczos_tc_nodes(body, n_sq, st_dev, inst_dev, parts[0], inst_host[0].nparts, lz, (int)N[0],
+                                        inst_host[0].ld, &n_lz));
+      n_sq = n_lz;
+    }
     SP2_TRY(sp2::batch_add_forward_tail(body, &n_sq, inst_dev, count, cond));
     last = n_fwd;
     if (opts.corrections > 0) {
@@ -465,6 +480,9 @@ struct MixedEngine {
     using namespace sp2::tc;
     for (int it = 0; it <= opts.max_iter; ++it) {
       SP2_TRY(sp2::tc_launch(job(MODE_SP2_STEP, 1, SLOTS_FORWARD), s));
+      if (lz)
+        SP2_TRY(sp2::launch_lanczos_tc(st_dev, inst_dev, parts[0], inst_host[0].nparts, lz, (int)N[0],
+                                       inst_host[0].ld, s));
       SP2_TRY(sp2::batch_launch_forward_tail(inst_dev, count, s));
     }
     if (opts.corrections > 0) {
@@ -670,7 +688,6 @@ extern "C" sp2_status sp2_create(int64_t N, int64_t nocc, int32_t precision, con
   sp2_default_opts(&o);
   if (opts) o = *opts;
   if (!opts_valid(o)) return SP2_ERR_INVALID_ARG;
-  if (o.norm == 2 && precision != SP2_PREC_FP64) return SP2_ERR_UNSUPPORTED;   // spectral stop: FP64 path
   sp2_ctx* h = new (std::nothrow) sp2_ctx();
   if (!h) return SP2_ERR_NOMEM;
   h->N = N; h->nocc = nocc; h->precision = precision; h->opts = o;

@@ -69,6 +69,12 @@ cudaError_t launch_lanczos(DevState* st, const double* buf0, const double* buf1,
 // to a multiple of 64 for lanczos_scratch_bytes.
 cudaError_t launch_lanczos_pairs(DevState* st, const int* row, const int* col, const int* nnz_p, const double* part,
                                  void* lz, int nb, int ld, cudaStream_t s);
+// The estimate on the tensor-core path, one problem: X_{k-1} and X_k from the instance's piece
+// arena (inst: its device record), part / nparts the forward square's records of 4 doubles.
+cudaError_t add_lanczos_tc_nodes(cudaGraph_t g, cudaGraphNode_t dep, DevState* st, const tc::Instance* inst,
+                                 const double* part, int nparts, void* lz, int N, int ld, cudaGraphNode_t* last);
+cudaError_t launch_lanczos_tc(DevState* st, const tc::Instance* inst, const double* part, int nparts, void* lz,
+                              int N, int ld, cudaStream_t s);
 // Per-iteration reduction + stop test over `nparts` partial records of `stride` doubles.
 cudaError_t add_finalize_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, DevState* st,
                               double* part, int nparts, int stride, cudaGraphConditionalHandle cond,

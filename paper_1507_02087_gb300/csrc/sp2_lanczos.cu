@@ -24,6 +24,7 @@
 
 #include "sp2_common.cuh"
 #include "sp2_kernels.h"
+#include "sp2_tc.cuh"
 
 namespace sp2 {
 namespace {
@@ -86,16 +87,16 @@ __device__ __forceinline__ void lz_operands(const DevState* st, const double* bu
   Y = (k & 1) ? buf0 : buf1;
 }
 
-// n x n operator stored with leading dimension ld; the square's (v^2, trace) partial records,
-// ntiles of them (or *ntiles_dev when given), set the scale.
+// n x n operator stored with leading dimension ld; the square's partial records (v^2 first, `rec`
+// doubles each), ntiles of them (or *ntiles_dev when given), set the scale.
 __global__ void __launch_bounds__(kLzThreads)
-lz_start_kernel(const DevState* st, const double* __restrict__ part, int ntiles, const int* ntiles_dev,
+lz_start_kernel(const DevState* st, const double* __restrict__ part, int ntiles, const int* ntiles_dev, int rec,
                 LzScratch* lz, int N, int ld) {
   __shared__ double sm[32];
   if (st->done) return;
   const int cnt = ntiles_dev ? *ntiles_dev : ntiles;
   double v2 = 0.0;                               // v_{k-1}^2 from the square's partials
-  for (int t = threadIdx.x; t < cnt; t += kLzThreads) v2 += part[2 * (int64_t)t];
+  for (int t = threadIdx.x; t < cnt; t += kLzThreads) v2 += part[rec * (int64_t)t];
   v2 = block_sum<kLzThreads>(v2, sm);
   double* qp = lz_vec(lz, ld, 0);
   double* q = lz_vec(lz, ld, 1);
@@ -150,6 +151,36 @@ __global__ void lz_form_kernel(const DevState* st, const double* buf0, const dou
     if (r < N && r == c2) d0 += c;
     if (r < N && r == c2 + 1) d1 += c;
     A2[e] = make_float2((float)(d0 * f), (float)(d1 * f));
+  }
+}
+
+// The same operator on the tensor-core path (one problem): X_{k-1} and X_k are slots of the
+// instance's piece arena, each element the exact FP32 value of its pieces, so
+//     A 2^-s = ((a + b) X_{k-1} - X_k + c I) (2^-s / a), rounded to FP32,
+// with the step's coefficients (SP2: (1, 0, 0) after X^2, (-1, 2, 0) after 2X - X^2).
+__global__ void lz_form_tc_kernel(const DevState* st, const tc::Instance* inst, LzScratch* lz) {
+  if (st->done) return;
+  const tc::Instance& In = inst[0];
+  const int N = st->N, ld = In.ld, k = st->k;
+  double a, b, c;
+  if (st->acc) {
+    acc_step(st, k + 1, a, b, c);
+  } else {
+    const int pk = st->tr[k] > (double)st->nocc ? 1 : 0;
+    a = pk ? 1.0 : -1.0; b = pk ? 0.0 : 2.0; c = 0.0;
+  }
+  const double ab = a + b, f = lz->scale / a;
+  const int64_t plane = (int64_t)ld * ld;
+  const __nv_bfloat16* xs = In.arena + (int64_t)tc::xslot(In.lowmem, In.hist0, k) * In.slot_elems;
+  const __nv_bfloat16* ys = In.arena + (int64_t)tc::xslot(In.lowmem, In.hist0, k + 1) * In.slot_elems;
+  float* A = lz_a32(lz, ld);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ld), col = (int)(e % ld);
+    const double x = (double)tc::piece_load(In.fmt, xs, plane, e);
+    const double y = (double)tc::piece_load(In.fmt, ys, plane, e);
+    double d = fma(ab, x, -y);
+    if (r < N && r == col) d += c;
+    A[e] = (float)(d * f);
   }
 }
 
@@ -351,7 +382,8 @@ cudaError_t add_lanczos_nodes(cudaGraph_t g, cudaGraphNode_t dep, DevState* st, 
   cudaKernelNodeParams kp = {};
   cudaGraphNode_t prev = dep, node;
   const int* no_count = nullptr;
-  void* a0[] = {&cst, &part, &ntiles, &no_count, &lz, &N, &ld};
+  int rec = 2;
+  void* a0[] = {&cst, &part, &ntiles, &no_count, &rec, &lz, &N, &ld};
   kp.func = (void*)lz_start_kernel;
   kp.gridDim = dim3(1);
   kp.blockDim = dim3(kLzThreads);
@@ -390,8 +422,65 @@ cudaError_t add_lanczos_nodes(cudaGraph_t g, cudaGraphNode_t dep, DevState* st, 
 cudaError_t launch_lanczos(DevState* st, const double* buf0, const double* buf1, const double* S,
                            const double* part, int ntiles, void* scratch, int N, int ld, cudaStream_t s) {
   LzScratch* lz = static_cast<LzScratch*>(scratch);
-  lz_start_kernel<<<1, kLzThreads, 0, s>>>(st, part, ntiles, nullptr, lz, N, ld);
+  lz_start_kernel<<<1, kLzThreads, 0, s>>>(st, part, ntiles, nullptr, 2, lz, N, ld);
   lz_form_kernel<<<form_blocks(ld), 256, 0, s>>>(st, buf0, buf1, S, lz);
+  for (int j = 0; j < kLzSteps; ++j) lz_step_kernel<<<step_blocks(N), kLzMvThreads, 0, s>>>(st, lz, j, N, ld);
+  lz_eig_kernel<<<1, 32, 0, s>>>(st, lz);
+  return cudaGetLastError();
+}
+
+// Tensor-core path, one problem: the estimate for the square just written into `inst`'s arena;
+// `part` holds its nparts records of 4 doubles (v^2 first).
+cudaError_t add_lanczos_tc_nodes(cudaGraph_t g, cudaGraphNode_t dep, DevState* st, const tc::Instance* inst,
+                                 const double* part, int nparts, void* scratch, int N, int ld,
+                                 cudaGraphNode_t* last) {
+  LzScratch* lz = static_cast<LzScratch*>(scratch);
+  const DevState* cst = st;
+  cudaKernelNodeParams kp = {};
+  cudaGraphNode_t prev = dep, node;
+  const int* no_count = nullptr;
+  int rec = 4;
+  void* a0[] = {&cst, &part, &nparts, &no_count, &rec, &lz, &N, &ld};
+  kp.func = (void*)lz_start_kernel;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(kLzThreads);
+  kp.kernelParams = a0;
+  cudaError_t e = cudaGraphAddKernelNode(&node, g, &prev, 1, &kp);
+  if (e != cudaSuccess) return e;
+  prev = node;
+  void* a1[] = {&cst, &inst, &lz};
+  kp.func = (void*)lz_form_tc_kernel;
+  kp.gridDim = dim3(form_blocks(ld));
+  kp.blockDim = dim3(256);
+  kp.kernelParams = a1;
+  if ((e = cudaGraphAddKernelNode(&node, g, &prev, 1, &kp)) != cudaSuccess) return e;
+  prev = node;
+  for (int j = 0; j < kLzSteps; ++j) {
+    int jj = j;
+    void* a2[] = {&cst, &lz, &jj, &N, &ld};
+    kp.func = (void*)lz_step_kernel;
+    kp.gridDim = dim3(step_blocks(N));
+    kp.blockDim = dim3(kLzMvThreads);
+    kp.kernelParams = a2;
+    if ((e = cudaGraphAddKernelNode(&node, g, &prev, 1, &kp)) != cudaSuccess) return e;
+    prev = node;
+  }
+  const LzScratch* clz = lz;
+  void* a3[] = {&st, &clz};
+  kp.func = (void*)lz_eig_kernel;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(32);
+  kp.kernelParams = a3;
+  e = cudaGraphAddKernelNode(&node, g, &prev, 1, &kp);
+  *last = node;
+  return e;
+}
+
+cudaError_t launch_lanczos_tc(DevState* st, const tc::Instance* inst, const double* part, int nparts, void* scratch,
+                              int N, int ld, cudaStream_t s) {
+  LzScratch* lz = static_cast<LzScratch*>(scratch);
+  lz_start_kernel<<<1, kLzThreads, 0, s>>>(st, part, nparts, nullptr, 4, lz, N, ld);
+  lz_form_tc_kernel<<<form_blocks(ld), 256, 0, s>>>(st, inst, lz);
   for (int j = 0; j < kLzSteps; ++j) lz_step_kernel<<<step_blocks(N), kLzMvThreads, 0, s>>>(st, lz, j, N, ld);
   lz_eig_kernel<<<1, 32, 0, s>>>(st, lz);
   return cudaGetLastError();
@@ -400,7 +489,7 @@ cudaError_t launch_lanczos(DevState* st, const double* buf0, const double* buf1,
 cudaError_t launch_lanczos_pairs(DevState* st, const int* row, const int* col, const int* nnz_p, const double* part,
                                  void* scratch, int nb, int ld, cudaStream_t s) {
   LzScratch* lz = static_cast<LzScratch*>(scratch);
-  lz_start_kernel<<<1, kLzThreads, 0, s>>>(st, part, 0, nnz_p, lz, nb, ld);
+  lz_start_kernel<<<1, kLzThreads, 0, s>>>(st, part, 0, nnz_p, 2, lz, nb, ld);
   lz_zero_kernel<<<form_blocks(ld), 256, 0, s>>>(st, lz, ld);
   lz_form_pairs_kernel<<<form_blocks(ld), 256, 0, s>>>(st, row, col, nnz_p, part, lz, ld);
   for (int j = 0; j < kLzSteps; ++j) lz_step_kernel<<<step_blocks(nb), kLzMvThreads, 0, s>>>(st, lz, j, nb, ld);

@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(kFT) batch_finalize_kernel(const Instance* ins
   b = block_sum<kFT>(b, sm);
   c = block_sum<kFT>(c, sm);
   double vk = sqrt(a);
-  if (st->norm && In.mscr) {
+  if (st->norm == 2) vk = st->spec_e;   // e_{k-1}, the Lanczos estimate of the 2-norm (one problem)
+  if (st->norm == 1 && In.mscr) {
     // mixed norm over 128 x 128 blocks: a 128 x 128 tile holds 4 records (one per epilogue
     // warp, 32 rows each); a 256 x 256 pair tile holds 16, record 8 rank + 4 hc + q covering
     // rows 128 rank + 32 q .., columns 128 hc ..; off-diagonal blocks are counted twice

@@ -78,9 +78,12 @@ def test_invalid_arguments_rejected_before_any_cuda_call(built):
                 sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 0, 0, 0, 3)):    # norm
         assert L.sp2_create(10, 5, 1, ctypes.byref(bad), ctypes.byref(h)) == 1
         assert h.value is None
-    # the spectral-norm stop (norm = 2) exists on the FP64 path only
+    # the spectral-norm stop (norm = 2) exists on the FP64 path and for single tensor-core
+    # problems, not for tensor-core batches
     spec = sp2.sp2_opts(10, 1, 1.8, 1, 2, 0, 0, 0, 0, 2)
-    assert L.sp2_create(10, 5, 1, ctypes.byref(spec), ctypes.byref(h)) == 7
+    Ns = (ctypes.c_int64 * 2)(10, 12)
+    occ = (ctypes.c_int64 * 2)(5, 6)
+    assert L.sp2_create_batch(2, Ns, occ, 1, ctypes.byref(spec), ctypes.byref(h)) == 7
     assert h.value is None
     assert L.sp2_run(None, None, None, None) == 1
     assert L.sp2_run_host(None, None, None, None) == 1

@@ -1,7 +1,8 @@
 """The error measures of the stop on the GPU through the C ABI, against the oracle:
 the mixed norm (§2: spectral norm of the matrix of block Frobenius norms of X - X^2, with the
 oracle's block size: 64 on the FP64 path, the 128 x 128 tiles on the mixed path) and the
-spectral norm e_i itself (§2; Lanczos on the FP64 path, against eigvalsh in the oracle)."""
+spectral norm e_i itself (§2; Lanczos on the FP64 path and on single-problem tensor-core
+handles, against eigvalsh in the oracle)."""
 import json
 import math
 import os
@@ -141,11 +142,34 @@ def test_fp64_spectral_mcweeny(sp2mod, mode):
     check_spectral_history(info, ref)
 
 
-def test_spectral_only_on_fp64_handles(sp2mod):
-    for make in (lambda: sp2mod.Purifier(256, 100, "mixed", norm="spectral"),
-                 lambda: sp2mod.BatchPurifier([256, 300], [100, 150], "mixed", norm="spectral")):
-        with pytest.raises(sp2mod.SP2Error):
-            make()
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x6"])
+@pytest.mark.parametrize("N,nocc,gap,seed", [(200, 90, 0.05, 1), (640, 320, 0.02, 2)])
+def test_tensor_core_spectral_stop(sp2mod, N, nocc, gap, seed, prec):
+    # the spectral stop on the tensor-core path: X - X^2 formed from the stored X_{k-1} and X_k,
+    # against the oracle that keeps its iterates as FP32 values and stops on eigvalsh's e_i; the
+    # window is the dense tensor-core one (floor detection, test_gpu_mixed.py notes)
+    case = inputs.dense_gapped(N, nocc, gap=gap, seed=seed)
+    D, info = run(sp2mod, case, prec, norm="spectral")
+    assert info["status"] == 0 and info["stop_reason"] in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
+    F = case.F.numpy()
+    bounds = (info["lambda_min"], info["lambda_max"])
+    ref = o.sp2(F, nocc, norm="spectral", bounds=bounds)
+    ref32 = o.sp2(F, nocc, norm="spectral", bounds=bounds, storage="fp32", trace="fro")
+    assert ref32.n - 3 <= info["n_iter"] <= ref32.n + 2 and info["n_iter"] <= ref.n, (info["n_iter"], ref32.n)
+    assert o.rel_error(D, ref.D, nocc) <= 1e-6
+    # the estimate against the FP32-storage oracle's e_i above the floor: a Lanczos lower bound
+    # (within 2e-2), plus the difference of the two histories' iterates (about 1e-6 absolute)
+    for i in range(min(len(ref32.v), info["hist_len"])):
+        if ref32.v[i] > 1e-3:
+            assert info["v"][i] <= ref32.v[i] * (1 + 1e-3) + 2e-6
+            assert info["v"][i] >= ref32.v[i] * (1 - 2e-2) - 2e-6
+
+
+def test_spectral_only_on_fp64_and_single_tensor_core_handles(sp2mod):
+    with pytest.raises(sp2mod.SP2Error):
+        sp2mod.BatchPurifier([256, 300], [100, 150], "mixed", norm="spectral")
+    with sp2mod.Purifier(256, 100, "fp16x3", norm="spectral") as P:
+        assert P.info()["status"] == 0
     with sp2mod.BatchPurifier([100, 130], [50, 60], "fp64", norm="spectral") as B:
         cases = [inputs.dense_gapped(100, 50, gap=0.1, seed=1), inputs.dense_gapped(130, 60, gap=0.1, seed=2)]
         Ds = B.run([c.F.cuda() for c in cases])
