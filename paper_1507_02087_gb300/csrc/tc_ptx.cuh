@@ -202,9 +202,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx_u32(uint32_t bar, uint32_t
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// Arrive on a barrier of either CTA of the cluster (address from mapa_shared).
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+// Arrive on a barrier of either CTA of the pair (`cluster_addr` from mapa_shared), with relaxed
+// semantics: for an arrive that only hands back tensor memory whose tcgen05.ld reads have
+// already completed (tcgen05.wait::ld), so nothing in memory needs a release fence.
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 
 // 4-D tiled TMA load into this CTA's shared memory whose completion is counted on a

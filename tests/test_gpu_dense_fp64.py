@@ -152,3 +152,26 @@ def test_dense_n2048_against_oracle(sp2mod):
     D, info = run_gpu(sp2mod, F, 1024)
     compare_with_oracle(D, info, res, 1024)
     assert o.rel_error(D, case.D_exact.numpy(), 1024) <= TOL_FP64
+
+
+def fermi_degenerate_case(N=64, nocc=32, seed=5):
+    # eigenvalues nocc - 1 and nocc coincide at 0: no gap at the occupation boundary, so no
+    # expansion can separate the pair (SURVEY-planned non-convergence case)
+    g = inputs.rng(seed)
+    lam = np.concatenate([g.uniform(-1, -0.05, nocc - 1), [0.0, 0.0], g.uniform(0.05, 1, N - nocc - 1)])
+    return inputs.dense_from_spectrum(lam, nocc, seed=seed)
+
+
+def test_no_gap_at_the_fermi_level_ends_at_the_cap(sp2mod):
+    # the degenerate pair oscillates (v stays near 0.3) and the run ends at the cap, as the
+    # oracle's does, with every other eigenvalue converged; no hang, status ok
+    case = fermi_degenerate_case()
+    F = case.F.numpy()
+    ref = o.sp2(F, 32, max_iter=60)
+    assert (ref.n, ref.stop_reason) == (60, o.STOP_CAP)
+    D, info = run_gpu(sp2mod, F, 32, max_iter=60)
+    assert info["status"] == 0 and (info["n_iter"], info["stop_reason"]) == (60, o.STOP_CAP)
+    w = np.linalg.eigvalsh(D)
+    mid = w[(w > 1e-6) & (w < 1 - 1e-6)]
+    assert len(mid) == 2 and abs(mid[0] - mid[1]) < 1e-6       # the pair, still together
+    assert abs(np.trace(D) - 32) < 1.0

@@ -309,3 +309,17 @@ def test_mixed_caller_bounds_save_squares(sp2mod):
     for c, D, inf in zip(cases, Ds, infos):
         assert inf["status"] == 0
         assert o.rel_error(D.cpu().numpy(), o.sp2(c.F.numpy(), c.nocc).D, c.nocc) <= TOL_MIXED
+
+
+def test_no_gap_at_the_fermi_level_ends_without_hanging(sp2mod):
+    # Fermi-level-degenerate F (eigenvalues nocc - 1 and nocc both 0): the tensor-core path ends
+    # by a stop rule within the cap, status ok; the other 62 eigenvalues converge
+    g = inputs.rng(5)
+    lam = np.concatenate([g.uniform(-1, -0.05, 31), [0.0, 0.0], g.uniform(0.05, 1, 31)])
+    case = inputs.dense_from_spectrum(lam, 32, seed=5)
+    for prec in FP32_GRADE:
+        D, info = run_gpu(sp2mod, case.F, 32, prec, max_iter=60)
+        assert info["status"] == 0 and info["n_iter"] <= 60
+        assert info["stop_reason"] in (o.STOP_ORDER, o.STOP_TRACE_GUARD, o.STOP_CAP)
+        w = np.linalg.eigvalsh(D.cpu().numpy())
+        assert np.count_nonzero((w > 1e-3) & (w < 1 - 1e-3)) <= 2
