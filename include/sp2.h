@@ -92,7 +92,10 @@ typedef struct {
   int32_t max_iter;     /* iteration cap, 1..SP2_MAX_ITER (default 200) */
   int32_t guard;        /* 1 = trace guard on (default), 0 = paper's test only */
   double  qtilde;       /* relaxed order, default 1.8 (§2) */
-  int32_t corrections;  /* SP2_PREC_MIXED: first-order subspace corrections, 0 or 1 (default 1) */
+  int32_t corrections;  /* tensor-core precisions: first-order subspace correction, 0 or 1 (default
+                           1).  The correction and the refinement assume X_n is near a projector:
+                           a run that ends at the cap (SP2_STOP_CAP) gets neither, D = X_n.  A
+                           non-finite value in the assembled D is reported as SP2_ERR_NONFINITE */
   int32_t refine_steps; /* SP2_PREC_MIXED: purification steps after the correction, 0 or 2 (default 2):
                            an alternating pair, X^2 and 2X - X^2, which squares the remaining
                            eigenvalue error */

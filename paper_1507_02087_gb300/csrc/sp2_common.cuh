@@ -103,6 +103,14 @@ struct DevState {
   uint8_t p[SP2_MAX_ITER + 2];
 };
 
+// A run whose iterate X_n the tensor-core path corrects and refines: it ran without error to a
+// stop rule.  A run that reached the iteration cap did not converge, and the first-order
+// correction and the refinement, which assume X_n is near a projector, would only push its
+// values out of range; D is then X_n itself.
+__host__ __device__ __forceinline__ bool corrects_run(const DevState* st) {
+  return st->status == SP2_OK && st->out_mode == OUT_COPY && st->reason != SP2_STOP_CAP;
+}
+
 // The paper's convergence-order test (Alg. 3; §2 relaxed order qtilde), only
 // evaluated when v_{i-2} < 1, and in its logarithmic form.
 __device__ __forceinline__ bool order_test_stops(double v_i, double v_im2, double qtilde, double C = kC2sp) {

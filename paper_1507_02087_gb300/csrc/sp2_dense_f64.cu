@@ -285,7 +285,7 @@ mcw_prod_kernel(const DevState* st, double* buf0, double* buf1, const double* S,
 __global__ void __launch_bounds__(kSyrkThreads)
 refine_f64_kernel(const DevState* st, const double* Xin, double* Xout, int ld, int step,
                   double* __restrict__ part) {
-  if (st->status != SP2_OK || st->out_mode != OUT_COPY) return;
+  if (!corrects_run(st)) return;      // failed or capped runs: D stays the assembled X_n
   const int plast = st->p[st->n_out];
   const int pk = step == 2 ? 1 : (step == 0 ? 1 - plast : plast);   // step 2: the plain square X^2
   syrk_f64_tile(Xin, Xout, ld, pk, part);

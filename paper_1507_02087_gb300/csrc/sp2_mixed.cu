@@ -33,10 +33,6 @@ using tc::Instance;
 using tc::piece_load;
 using tc::piece_store;
 
-__device__ __forceinline__ bool ok_run(const DevState* st) {
-  return st->status == SP2_OK && st->out_mode == OUT_COPY;
-}
-
 // ---- bounds and initialisation ------------------------------------------------------------
 constexpr int kGT = 256;
 
@@ -233,7 +229,7 @@ __global__ void batch_check_kernel(const Instance* inst, int count, int which, c
   __syncthreads();
   for (int i = threadIdx.x; i < count; i += blockDim.x) {
     const DevState* st = inst[i].st;
-    const bool more = which == 0 ? !st->done : (ok_run(st) && st->dk < st->n_out);
+    const bool more = which == 0 ? !st->done : (corrects_run(st) && st->dk < st->n_out);
     if (more) atomicOr(&busy, 1);
   }
   __syncthreads();
@@ -249,7 +245,7 @@ __global__ void batch_deriv_advance_kernel(const Instance* inst, int count, cuda
   __syncthreads();
   for (int i = threadIdx.x; i < count; i += blockDim.x) {
     DevState* st = inst[i].st;
-    if (ok_run(st) && st->dk < st->n_out) {
+    if (corrects_run(st) && st->dk < st->n_out) {
       st->dk += 1;
       if (st->dk < st->n_out) atomicOr(&busy, 1);
     }
@@ -267,7 +263,7 @@ __global__ void batch_corrected_to_pieces_kernel(const Instance* inst, int count
   if (i >= count) return;
   const Instance& In = inst[i];
   const DevState* st = In.st;
-  if (!ok_run(st)) return;
+  if (!corrects_run(st)) return;
   const int N = st->N, ld = In.ld;
   const int64_t plane = (int64_t)ld * ld;
   const int n = st->n_out;
@@ -286,13 +282,19 @@ __global__ void batch_corrected_to_pieces_kernel(const Instance* inst, int count
 }
 
 // D in FP64: from slot r0 (after the tensor-core refinement) when from_r0, else
-// X_n (+ dX_n with the correction); 0 / I / NaN for the special outcomes.
+// X_n (+ dX_n with the correction); 0 / I / NaN for the special outcomes.  A run that reached
+// the cap is neither corrected nor refined: D = X_n.  A non-finite value in a D the run
+// reported as ok sets SP2_ERR_NONFINITE.
 __global__ void batch_assemble_kernel(const Instance* inst, int count, int sb, int use_dx, int from_r0,
                                       BatchPtrs ptrs, int to_f64_buf, double* f64_buf) {
   const int i = blockIdx.x / sb, b = blockIdx.x % sb;
   if (i >= count) return;
   const Instance& In = inst[i];
-  const DevState* st = In.st;
+  DevState* st = In.st;
+  if (!corrects_run(st)) {
+    from_r0 = 0;
+    use_dx = 0;
+  }
   const int N = st->N, ld = In.ld;
   const int mode = st->out_mode;
   const int64_t plane = (int64_t)ld * ld;
@@ -318,6 +320,7 @@ __global__ void batch_assemble_kernel(const Instance* inst, int count, int sb, i
     } else {
       val = __longlong_as_double(0x7ff8000000000000ll);
     }
+    if (mode == OUT_COPY && !isfinite(val)) atomicCAS(&st->status, (int32_t)SP2_OK, (int32_t)SP2_ERR_NONFINITE);
     D[(int64_t)r * ldd + c] = val;
   }
 }
@@ -332,7 +335,7 @@ __global__ void batch_assemble_kernel(const Instance* inst, int count, int sb, i
 __global__ void mcw_split_kernel(const Instance* inst, const double* Dbuf, double* Sbuf, int sb) {
   const Instance& In = inst[0];
   const DevState* st = In.st;
-  if (st->status != SP2_OK || st->out_mode != OUT_COPY) return;
+  if (!corrects_run(st)) return;
   const int N = st->N, ld = In.ld;
   const int64_t plane = (int64_t)ld * ld;
   __nv_bfloat16* Dp = In.arena + (int64_t)In.r0_slot * In.slot_elems;
@@ -364,9 +367,11 @@ __global__ void mcw_out_kernel(const Instance* inst, const double* Dbuf, const d
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)sb * blockDim.x) {
     const int r = (int)(e / N), c = (int)(e % N);
     double val;
-    if (mode == OUT_COPY && st->status == SP2_OK) {
+    if (mode == OUT_COPY && corrects_run(st)) {
       const int64_t off = (int64_t)r * ld + c;
       val = Dbuf[off] + Ebuf[off] - 2.0 * (double)piece_load(In.fmt, Pp, plane, off);
+    } else if (mode == OUT_COPY && st->status == SP2_OK) {
+      val = Dbuf[(int64_t)r * ld + c];     // a capped run: X_n as assembled, not refined
     } else if (mode == OUT_ZERO) {
       val = 0.0;
     } else if (mode == OUT_IDENTITY) {

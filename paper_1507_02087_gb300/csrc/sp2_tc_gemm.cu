@@ -62,7 +62,7 @@ __device__ __forceinline__ Resolved resolve_slots(const Job& j, const Instance& 
   r.gen = 0; r.ca = r.cb = r.cc = 0.f;
   if (j.rule == SLOTS_FIXED) return r;
   const DevState* st = I.st;
-  const bool ok_run = st->status == SP2_OK && st->out_mode == OUT_COPY;
+  const bool ok_run = corrects_run(st);   // correction, recompute and refinement jobs
   switch (j.rule) {
     case SLOTS_FORWARD: {
       const int k = st->k;
