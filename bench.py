@@ -39,7 +39,7 @@ TOL = 1e-6
 # 2070 MHz maximum clock is 4 flop per clock per SM; taken at the measured clock.
 SMS, FP64_FLOP_PER_CLK_SM, SM_MAX_MHZ = 152, 4.0, 2070.0
 # 16-bit piece products per square on the tensor cores, per precision mode
-PRODUCTS = {"mixed": 6, "bf16x6": 6, "bf16x3": 3, "fp16x3": 3}
+PRODUCTS = {"mixed": 6, "bf16x6": 6, "bf16x3": 3, "fp16x3": 3, "tf32x3": 3}
 # The roofline basis of the tensor-core square: useful flops N^2 (N+1) per square (upper triangle
 # with the diagonal, N multiply-adds each) times 3 split products, the budget of an FP32-grade
 # square on 16-bit tensor cores; the executed fraction counts the mode's own piece products.
@@ -47,7 +47,8 @@ SPLIT_BASIS = 3
 DTYPE = {"mixed": "bf16x6->f32 (three bf16 pieces, six products), f64 reductions",
          "bf16x6": "bf16x6->f32 (three bf16 pieces, six products), f64 reductions",
          "bf16x3": "bf16x3->f32 (two bf16 pieces, three products), f64 reductions",
-         "fp16x3": "fp16x3->f32 (two scaled fp16 pieces, three products), f64 reductions"}
+         "fp16x3": "fp16x3->f32 (two scaled fp16 pieces, three products), f64 reductions",
+         "tf32x3": "tf32x3->f32 (two tf32 pieces, three products), f64 reductions"}
 
 
 def workload_name(N, nocc, gap):
@@ -60,6 +61,16 @@ FWD_TRAFFIC_BYTES = {(8192, "pair", "fp16x3"): 1.455e9 + 242.1e6}
 FP32_FLOP_PER_CLK_SM = 256     # 128 FP32 FMA lanes per SM
 
 
+def tensor_peak(precision: str) -> tuple[float, str]:
+    """Sustained tensor peak of the mode's MMA kind: the measured bf16 figure (fp16 and bf16 share
+    the kind::f16 rate); kind::tf32 at the nominal ratio 1.1 / 2.25 PFLOP/s of it."""
+    bf = load_peaks().get("bf16_tflops_sustained") or 1700.0
+    if precision == "tf32x3":
+        return bf * 1.1 / 2.25, ("MEASURED_PEAKS.json bf16_tflops_sustained x 1.1/2.25 (the nominal "
+                                 "tf32 / bf16 dense ratio)")
+    return bf, "MEASURED_PEAKS.json bf16_tflops_sustained (fp16 and bf16 share the kind::f16 rate)"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -70,7 +81,7 @@ def parse():
                     help="dense: one N x N problem (default N=8192); batch64: 64 problems, N log-uniform "
                          "in [128, 2048], seed 1; bsr: gapped tight-binding 32^3 lattice, 32 x 32 blocks, "
                          "block truncation tau in {1e-4, 1e-6}")
-    ap.add_argument("--precision", choices=["fp16x3", "bf16x6", "mixed", "bf16x3", "fp64"], default="fp16x3",
+    ap.add_argument("--precision", choices=["fp16x3", "bf16x6", "mixed", "bf16x3", "tf32x3", "fp64"], default="fp16x3",
                     help="fp16x3 (default): two scaled fp16 pieces, three products; bf16x6 (= mixed): three bf16 "
                          "pieces, six products; bf16x3: two bf16 pieces, three products; fp64: the plain method")
     ap.add_argument("--no-secondary", action="store_true",
@@ -306,8 +317,7 @@ def batch_record(a, local, precision, steps, warmup, compare_tiles=False, fp64_s
         ms, err, infos = timed(B, steps)
         clk = clocks.stop()
     flops = sum(useful_flops(N, i["hist_len"], i["n_iter"], True, 2) for N, i in zip(Ns, infos))
-    peaks = load_peaks()
-    peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    peak, peak_src = tensor_peak(precision)
     achieved = SPLIT_BASIS * flops / (ms * 1e-3) / 1e12
     rec = {"workload": "batch of 64 dense problems, N log-uniform in [128, 2048] (seed 1), nocc = N/2, gap "
                        "uniform in [0.005, 0.1]; one launch sequence, per-problem stops",
@@ -319,7 +329,7 @@ def batch_record(a, local, precision, steps, warmup, compare_tiles=False, fp64_s
            "roofline": {"bound": "tensor", "kernel": "every tensor-core launch of the run, over the whole time-to-D",
                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                         "basis": "useful flops of all products x 3 split products over the time-to-D; peak: "
-                                 "MEASURED_PEAKS.json bf16_tflops_sustained (fp16 and bf16 share the kind::f16 rate)",
+                                 + peak_src,
                         "traffic": None},
            "clocks": clk, "sum_N3": sum(N ** 3 for N in Ns), "count": len(cases)}
     if compare_tiles:
@@ -664,7 +674,7 @@ def main():
         alg = SPLIT_BASIS * useful
         executed = PRODUCTS[a.precision] * useful
         achieved = alg / (kern_ms * 1e-3) / 1e12
-        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        peak, peak_src = tensor_peak(a.precision)
         kname = ("tc_gemm_pair_kernel (256x256 tiles per SM pair" if tile_used == "pair"
                  else "tc_gemm_kernel (128x128 tiles per SM")
         roofline = {"bound": "tensor", "kernel": kname + ", forward square, MODE_SP2_STEP, " + a.precision + ")",
@@ -674,8 +684,7 @@ def main():
                              "per square; frac_executed counts the mode's own %d piece products" % PRODUCTS[a.precision],
                     "useful_tflops": useful / (kern_ms * 1e-3) / 1e12,
                     "ms_per_launch": kern_ms,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step; "
-                                   "fp16 and bf16 inputs share the kind::f16 tensor rate)",
+                    "peak_source": peak_src + "; the sustained figure, the kernel is timed inside a long step",
                     "algorithmic_flops_per_launch": alg,
                     "traffic": FWD_TRAFFIC_BYTES.get((N, tile_used, a.precision))}
     else:
@@ -909,7 +918,7 @@ def acc_record(a, local, F, D_exact, lam, nocc, steps, warmup, slack=1e-3):
         fi = Pf.info()
         del D2
     kern_ms = fi["loop_ms"] / fi["hist_len"]
-    peak = load_peaks().get("bf16_tflops_sustained") or 1700.0
+    peak, _ = tensor_peak(a.precision)
     achieved = SPLIT_BASIS * N * N * (N + 1) / (kern_ms * 1e-3) / 1e12
     return {"workload": workload_name(N, nocc, a.gap) + ", SP2-ACC with homo/lumo bounds (slack %g)" % slack,
             "precision": a.precision, "time_to_d_ms": statistics.mean(tms), "steps": steps, "warmup": warmup,

@@ -69,7 +69,7 @@ typedef enum {
  * the same parameterless test) is followed by a first-order correction of the occupied
  * subspace driven by F (sp2_opts.corrections) and a refinement pair (sp2_opts.refine_steps).
  * The derivative pass of the correction always runs at the mode's low precision.  Workspace
- * of the tensor-core modes: (max_iter + 8) slots of P * 2 * ld^2 bytes (P pieces), ld = N
+ * of the tensor-core modes: (max_iter + 8) slots of P * E * ld^2 bytes (P pieces of E bytes), ld = N
  * rounded up to a multiple of 128 (256 with CTA-pair tiles); see sp2_opts.history. */
 typedef enum {
   SP2_PREC_FP64 = 0,   /* FP64 products and FP64 everything (the plain method) */
@@ -80,12 +80,16 @@ typedef enum {
   SP2_PREC_BF16X3 = 2, /* the same three bf16 pieces, every product as the three with a + b <= 1
                           (about 16 significant bits, half the tensor work of BF16X6); a
                           comparison point: its error after the correction stays near 1e-5 */
-  SP2_PREC_FP16X3 = 3  /* each value as two fp16 pieces of 2^14 x (P = 2, 22 significant bits;
+  SP2_PREC_FP16X3 = 3, /* each value as two fp16 pieces of 2^14 x (P = 2, 22 significant bits;
                           |x| < 4, which every iterate satisfies), products as the three piece
                           products p0 q0 + p0 q1 + p1 q0 (relative error about 2^-21, half the
                           tensor work of BF16X6), derivative steps as p0 q0; the correction's
                           F enters as (F - c I) / w' (c, w' the centre and half-width of the
                           spectral bounds, so its entries fit the fp16 range) */
+  SP2_PREC_TF32X3 = 4  /* each value as two tf32 pieces held in FP32 words, hi = tf32(x) and
+                          lo = tf32(x - hi) (P = 2, 4-byte pieces, 22 significant bits, FP32's
+                          exponent range), products as hi lo' + lo hi' + hi hi' on kind::tf32
+                          tensor cores (half the kind::f16 rate), derivative steps as hi hi' */
 } sp2_precision;
 
 typedef struct {

@@ -128,7 +128,7 @@ static int tune_tiles(const std::vector<int64_t>& N, int fmt, int lowprec) {
     for (int k = 0; k < count; ++k) {
       const double ld = round_up(N[k], c == 2 ? PT : LD_ALIGN);
       model[c] += ld * ld * ld / (c == 2 ? 1580.0 : 1200.0);
-      bytes[c] += (size_t)2 * np * (size_t)ld * (size_t)ld * 2;
+      bytes[c] += (size_t)2 * np * (size_t)ld * (size_t)ld * esize_of(fmt);
     }
   const int by_model = model[2] < model[1] ? 2 : 1;
   if (std::max(bytes[1], bytes[2]) > kTuneBytes) return by_model;
@@ -156,13 +156,13 @@ static int tune_tiles(const std::vector<int64_t>& N, int fmt, int lowprec) {
       std::memset(&I, 0, sizeof(I));
       const int ld = round_up(N[k], pair ? PT : LD_ALIGN);
       __nv_bfloat16* arena = (__nv_bfloat16*)((char*)scratch + off);
-      off += (size_t)2 * np * (size_t)ld * (size_t)ld * 2;
+      off += (size_t)2 * np * (size_t)ld * (size_t)ld * esize_of(fmt);
       I.ld = ld;
       I.arena = arena;
       I.fmt = fmt;
       I.np = np;
       I.nslots = 2;
-      I.slot_elems = (int64_t)np * ld * ld;
+      I.slot_elems = sp2::tc::slot_units_of(fmt, ld);
       I.tile_off_upper = I.tile_off_upper2 = tiles;
       tiles += sp2::tc_tiles(ld, 1, pair);
       ok = sp2::tc_make_maps(arena, ld, 2, fmt, &I.mapA, &I.mapB) == cudaSuccess;
@@ -299,7 +299,7 @@ struct MixedEngine {
     using namespace sp2::tc;
     count = cnt;
     opts = o;
-    fmt = precision == SP2_PREC_FP16X3 ? FMT_FP16X2 : FMT_BF16X3;
+    fmt = precision == SP2_PREC_FP16X3 ? FMT_FP16X2 : (precision == SP2_PREC_TF32X3 ? FMT_TF32X2 : FMT_BF16X3);
     lp_main = precision == SP2_PREC_BF16X3 ? 1 : 0;
     const int np = np_of(fmt);
     user_of.resize(count);
@@ -343,7 +343,7 @@ struct MixedEngine {
       double full = 0.0;
       for (int k = 0; k < count; ++k) {
         const double ld = (double)ld_of(N[k]);
-        full += (double)(H + 6) * np * ld * ld * 2.0;
+        full += (double)(H + 6) * np * ld * ld * esize_of(fmt);
       }
       size_t free_b = 0, total_b = 0;
       if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { (void)cudaGetLastError(); free_b = 0; }
@@ -368,7 +368,7 @@ struct MixedEngine {
       I.nslots = nslots;
       I.fmt = fmt;
       I.np = np;
-      I.slot_elems = (int64_t)np * ld * ld;
+      I.slot_elems = sp2::tc::slot_units_of(fmt, ld);
       I.st = st_dev + k;
       I.tile_off_upper = I.tile_off_upper2 = off_u;
       I.tile_off_full = I.tile_off_full2 = off_f;
@@ -683,7 +683,7 @@ extern "C" sp2_status sp2_create(int64_t N, int64_t nocc, int32_t precision, con
   if (!out) return SP2_ERR_INVALID_ARG;
   *out = nullptr;
   if (N < 1 || N > 65536 || nocc < 0 || nocc > N) return SP2_ERR_INVALID_ARG;
-  if (precision < SP2_PREC_FP64 || precision > SP2_PREC_FP16X3) return SP2_ERR_UNSUPPORTED;
+  if (precision < SP2_PREC_FP64 || precision > SP2_PREC_TF32X3) return SP2_ERR_UNSUPPORTED;
   sp2_opts o;
   sp2_default_opts(&o);
   if (opts) o = *opts;
@@ -993,7 +993,7 @@ extern "C" sp2_status sp2_create_batch(int32_t count, const int64_t* N, const in
   if (count < 1 || count > SP2_MAX_BATCH || !N || !nocc) return SP2_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i)
     if (N[i] < 1 || N[i] > 65536 || nocc[i] < 0 || nocc[i] > N[i]) return SP2_ERR_INVALID_ARG;
-  if (precision < SP2_PREC_FP64 || precision > SP2_PREC_FP16X3) return SP2_ERR_UNSUPPORTED;
+  if (precision < SP2_PREC_FP64 || precision > SP2_PREC_TF32X3) return SP2_ERR_UNSUPPORTED;
   sp2_opts o;
   sp2_default_opts(&o);
   if (opts) o = *opts;

@@ -13,11 +13,16 @@
 //    p0 q0 + p0 q1 + p1 q0 (relative error about 2^-21); a low-precision product is p0 q0
 //    alone (11 bits).  Each piece product is exact in FP32, the accumulated sum carries
 //    S^2, which the epilogue removes.
-// Both run as kind::f16 MMAs (fp16 and bf16 inputs at the same tensor-core rate) with FP32
-// accumulation.
+//  * FMT_TF32X2: two tf32 pieces stored as FP32 values, hi = tf32(x) (round to nearest) and
+//    lo = tf32(x - hi): 22 significant bits like FMT_FP16X2, with FP32's exponent range (no
+//    scaling).  A full product is the three piece products hi lo' + lo hi' + hi hi' (relative
+//    error about 2^-21); a low-precision product is hi hi' (11 bits).
+// The 16-bit formats run as kind::f16 MMAs (fp16 and bf16 inputs at the same tensor-core rate),
+// FMT_TF32X2 as kind::tf32 MMAs (half that rate, K = 8 per MMA), all with FP32 accumulation.
 //
 // Every problem ("instance") owns a piece arena: slot s holds the planes of one ld x ld
-// matrix, plane-major ([slot][piece][row][col], 16-bit).  A 4-D TMA tensor map (col, row,
+// matrix, plane-major ([slot][piece][row][col]; 16-bit or, for FMT_TF32X2, 32-bit elements; the
+// arena is addressed in 16-bit units).  A 4-D TMA tensor map (col, row,
 // piece, slot) per instance covers its arena, so a kernel selects operands by instance and
 // slot.  A launch works on the tiles of all live instances of a batch (a single problem is
 // a batch of one).
@@ -34,18 +39,26 @@ namespace sp2 {
 namespace tc {
 
 // Piece formats (sp2_tc.cuh header comment).
-enum Fmt : int32_t { FMT_BF16X3 = 0, FMT_FP16X2 = 1 };
+enum Fmt : int32_t { FMT_BF16X3 = 0, FMT_FP16X2 = 1, FMT_TF32X2 = 2 };
 constexpr float kF16Scale = 16384.f;                 // S = 2^14
 constexpr float kF16InvScale = 1.f / 16384.f;
 constexpr float kF16InvScale2 = 1.f / (16384.f * 16384.f);
 
 constexpr int BM = 128;          // tile rows (MMA M)
 constexpr int BN = 128;          // tile cols (MMA N)
-constexpr int BK = 64;           // k-block: 64 16-bit values = 128 B rows, 128-byte swizzle
-constexpr int NP = 3;            // pieces per matrix (FMT_BF16X3; FMT_FP16X2 has 2)
-constexpr int STAGES = 2;        // TMA ring depth (FMT_BF16X3; FMT_FP16X2, with smaller stages, has 3)
-__host__ __device__ constexpr int np_of(int fmt) { return fmt == FMT_FP16X2 ? 2 : 3; }
-__host__ __device__ constexpr int stages_of(int fmt) { return fmt == FMT_FP16X2 ? 3 : 2; }
+constexpr int BK = 64;           // k-block of the 16-bit formats: 64 values = 128 B rows, 128-byte swizzle
+constexpr int ROW_BYTES = 128;   // one k-block row of any format (FMT_TF32X2: 32 values)
+constexpr int KSTEPS = 4;        // MMAs per k-block row and product: 32 B each (16 16-bit or 8 tf32 values)
+constexpr int NP = 3;            // pieces per matrix (FMT_BF16X3; the two-piece formats have 2)
+constexpr int STAGES = 2;        // TMA ring depth (FMT_BF16X3; the two-piece formats, with smaller stages, 3)
+__host__ __device__ constexpr int np_of(int fmt) { return fmt == FMT_BF16X3 ? 3 : 2; }
+__host__ __device__ constexpr int stages_of(int fmt) { return fmt == FMT_BF16X3 ? 2 : 3; }
+__host__ __device__ constexpr int esize_of(int fmt) { return fmt == FMT_TF32X2 ? 4 : 2; }   // bytes per value
+__host__ __device__ constexpr int bk_of(int fmt) { return ROW_BYTES / esize_of(fmt); }    // values per k-block
+// 16-bit units of one slot (np planes of ld x ld values)
+__host__ __device__ constexpr int64_t slot_units_of(int fmt, int64_t ld) {
+  return (int64_t)np_of(fmt) * ld * ld * (esize_of(fmt) / 2);
+}
 // The tensor cores' FP32 accumulation drops the bits an addend loses in alignment
 // (it rounds toward zero), so a long sum of same-sign products drifts low by about
 // K * 2^-25 of its value.  The MMAs therefore accumulate a chunk of k-blocks (CHUNK_KB,
@@ -54,10 +67,11 @@ __host__ __device__ constexpr int stages_of(int fmt) { return fmt == FMT_FP16X2 
 // round-to-nearest FP32 additions.  Within a ring stage the smaller piece products are
 // issued before the leading one (p0 q0), so that they are added while the accumulator is
 // still small and lose less to the truncation.
-constexpr int CHUNK_KB = 1;
+constexpr int CHUNK_TERMS = 64;
+constexpr int CHUNK_KB = 1;      // CHUNK_TERMS in 16-bit k-blocks (FMT_TF32X2: 2 k-blocks)
 constexpr int NBUF = 4;
-constexpr int A_PIECE_BYTES = BM * BK * 2;
-constexpr int B_PIECE_BYTES = BN * BK * 2;
+constexpr int A_PIECE_BYTES = BM * ROW_BYTES;
+constexpr int B_PIECE_BYTES = BN * ROW_BYTES;
 constexpr int STAGE_BYTES = NP * (A_PIECE_BYTES + B_PIECE_BYTES);
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;   // + alignment slack
 __host__ __device__ constexpr int stage_bytes_of(int fmt) { return np_of(fmt) * (A_PIECE_BYTES + B_PIECE_BYTES); }
@@ -184,7 +198,23 @@ __device__ __forceinline__ void split_fp16x2(float x, __half& p0, __half& p1) {
   p1 = __float2half_rn(y - __half2float(p0));     // the difference is exact in FP32
 }
 
+// The tf32 value nearest x (ties away from zero), as an FP32 value with the low 13 bits zero.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void split_tf32x2(float x, float& hi, float& lo) {
+  hi = round_tf32(x);
+  lo = round_tf32(x - hi);                        // the difference is exact in FP32
+}
+
 __device__ __forceinline__ float piece_load(int fmt, const __nv_bfloat16* slot, int64_t plane, int64_t off) {
+  if (fmt == FMT_TF32X2) {
+    const float* f = reinterpret_cast<const float*>(slot);
+    return f[off] + f[plane + off];               // exact: 22 significant bits in all
+  }
   if (fmt == FMT_FP16X2) {
     const __half* h = reinterpret_cast<const __half*>(slot);
     return (__half2float(h[off]) + __half2float(h[plane + off])) * kF16InvScale;   // exact sum
@@ -193,6 +223,14 @@ __device__ __forceinline__ float piece_load(int fmt, const __nv_bfloat16* slot, 
 }
 
 __device__ __forceinline__ void piece_store(int fmt, __nv_bfloat16* slot, int64_t plane, int64_t off, float x) {
+  if (fmt == FMT_TF32X2) {
+    float* f = reinterpret_cast<float*>(slot);
+    float a, b;
+    split_tf32x2(x, a, b);
+    f[off] = a;
+    f[plane + off] = b;
+    return;
+  }
   if (fmt == FMT_FP16X2) {
     __half* h = reinterpret_cast<__half*>(slot);
     __half a, b;

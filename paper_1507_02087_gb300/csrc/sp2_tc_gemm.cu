@@ -1,4 +1,4 @@
-// Persistent tcgen05 GEMM over 16-bit piece operands (FMT_BF16X3 or FMT_FP16X2) with the
+// Persistent tcgen05 GEMM over piece operands (FMT_BF16X3, FMT_FP16X2 or FMT_TF32X2) with the
 // SP2 epilogues, for a batch of problems of uneven size.
 //
 // C[I-tile, J-tile] = sum_k A[rows I, k] B[rows J, k] (both operands K-major row
@@ -157,10 +157,13 @@ __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I, int
 // first-order correction, whose own truncation bias (at most K 2^-25 of dX_j) is far below
 // the error it corrects; measured at N = 8192, the error after the correction is the same to
 // three digits (5.44e-7) and the derivative pass takes 61 ms instead of 87 ms.
+// FMT_TF32X2 counts as fp16 (one low-precision product), in its 32-wide k-blocks.
 __device__ __forceinline__ int chunk_kb(const Job& job, int ld) {
-  const int total = job.nterms * (ld / BK);
+  const int bk = bk_of(job.fmt);
+  const int total = job.nterms * (ld / bk);
   if (job.whole_k) return total;
-  int ck = !job.lowprec ? CHUNK_KB : (job.fmt == FMT_FP16X2 ? 4 * CHUNK_KB : 2 * CHUNK_KB);
+  const int terms = !job.lowprec ? CHUNK_TERMS : (job.fmt == FMT_BF16X3 ? 2 * CHUNK_TERMS : 4 * CHUNK_TERMS);
+  int ck = terms / bk;
   while (ck > 1 && total % ck != 0) ck >>= 1;
   return ck;
 }
@@ -181,16 +184,28 @@ struct Products<FMT_FP16X2> {
   __device__ static constexpr int a(int q) { return q == 0 ? 1 : 0; }                              // 1,0,0
   __device__ static constexpr int b(int q) { return q == 1 ? 1 : 0; }                              // 0,1,0
 };
+template <>
+struct Products<FMT_TF32X2> : Products<FMT_FP16X2> {};   // lo hi', hi lo', hi hi'
 
 template <int FMT>
 __host__ __device__ constexpr uint32_t idesc_of(int M, int N) {
-  return FMT == FMT_FP16X2 ? idesc_f16_f32(M, N) : idesc_bf16_f32(M, N);
+  return FMT == FMT_TF32X2 ? idesc_tf32_f32(M, N) : (FMT == FMT_FP16X2 ? idesc_f16_f32(M, N) : idesc_bf16_f32(M, N));
+}
+
+// One MMA of the format's kind (kind::tf32 for FMT_TF32X2, kind::f16 otherwise).
+template <int FMT, bool PAIR>
+__device__ __forceinline__ void mma_fmt(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  if constexpr (FMT == FMT_TF32X2) {
+    if constexpr (PAIR) mma_tf32_pair(dt, ad, bd, idesc, acc); else mma_tf32(dt, ad, bd, idesc, acc);
+  } else {
+    if constexpr (PAIR) mma_bf16_pair(dt, ad, bd, idesc, acc); else mma_bf16(dt, ad, bd, idesc, acc);
+  }
 }
 
 // Pieces loaded per operand by one job.
 template <int FMT>
 __device__ __forceinline__ int pieces_loaded(const Job& job) {
-  return job.lowprec ? (FMT == FMT_FP16X2 ? 1 : 2) : np_of(FMT);
+  return job.lowprec ? (FMT == FMT_BF16X3 ? 2 : 1) : np_of(FMT);
 }
 
 __device__ __forceinline__ int tile_off(const Job& job, const Instance& in) {
@@ -225,7 +240,13 @@ __device__ __forceinline__ int locate(const Job& job, int t, int& I, int& J) {
 // 8 consecutive values (16-byte aligned) from / to the planes of a slot.
 template <int FMT>
 __device__ __forceinline__ void load8(const __nv_bfloat16* slot, int64_t plane, int64_t off, float (&x)[8]) {
-  if constexpr (FMT == FMT_FP16X2) {
+  if constexpr (FMT == FMT_TF32X2) {   // 32-byte aligned: off is a multiple of 8 values
+    const float4* hi = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(slot) + off);
+    const float4* lo = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(slot) + plane + off);
+    const float4 h0 = hi[0], h1 = hi[1], l0 = lo[0], l1 = lo[1];
+    x[0] = h0.x + l0.x; x[1] = h0.y + l0.y; x[2] = h0.z + l0.z; x[3] = h0.w + l0.w;
+    x[4] = h1.x + l1.x; x[5] = h1.y + l1.y; x[6] = h1.z + l1.z; x[7] = h1.w + l1.w;
+  } else if constexpr (FMT == FMT_FP16X2) {
     const uint4 a = *reinterpret_cast<const uint4*>(slot + off);
     const uint4 b = *reinterpret_cast<const uint4*>(slot + plane + off);
     const __half* pa = reinterpret_cast<const __half*>(&a);
@@ -247,7 +268,17 @@ __device__ __forceinline__ void load8(const __nv_bfloat16* slot, int64_t plane, 
 
 template <int FMT>
 __device__ __forceinline__ void store8(__nv_bfloat16* slot, int64_t plane, int64_t off, const float (&x)[8]) {
-  if constexpr (FMT == FMT_FP16X2) {
+  if constexpr (FMT == FMT_TF32X2) {
+    float h[8], l[8];
+    #pragma unroll
+    for (int e = 0; e < 8; ++e) split_tf32x2(x[e], h[e], l[e]);
+    float4* hi = reinterpret_cast<float4*>(reinterpret_cast<float*>(slot) + off);
+    float4* lo = reinterpret_cast<float4*>(reinterpret_cast<float*>(slot) + plane + off);
+    hi[0] = make_float4(h[0], h[1], h[2], h[3]);
+    hi[1] = make_float4(h[4], h[5], h[6], h[7]);
+    lo[0] = make_float4(l[0], l[1], l[2], l[3]);
+    lo[1] = make_float4(l[4], l[5], l[6], l[7]);
+  } else if constexpr (FMT == FMT_FP16X2) {
     uint4 a, b;
     __half* pa = reinterpret_cast<__half*>(&a);
     __half* pb = reinterpret_cast<__half*>(&b);
@@ -316,8 +347,9 @@ __device__ __forceinline__ void epilogue_chunk(const Job& job, const Instance& I
       float x[8];
       load8<FMT>(in, plane, row_off + 8 * h, x);
       if (job.mode == MODE_DF_COMBINE) {
-        // dX_0 = -dF / (lmax - lmin): the F slot holds F (FMT_BF16X3), or F' = (F - c I) / W'
-        // with c, W' the centre and half-width of [lmin, lmax] (FMT_FP16X2), whose dF' is dF / W'
+        // dX_0 = -dF / (lmax - lmin): the F slot holds F (FMT_BF16X3, FMT_TF32X2), or F' =
+        // (F - c I) / W' with c, W' the centre and half-width of [lmin, lmax] (FMT_FP16X2),
+        // whose dF' is dF / W'
         const double w = In.st->lmax - In.st->lmin;
         const float sc = FMT == FMT_FP16X2 ? -0.5f : (float)(-1.0 / w);
         #pragma unroll
@@ -415,7 +447,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
         if (!R.active) continue;
         const CUtensorMap* mA = &In.mapA;
         const CUtensorMap* mB = &In.mapB;
-        const int nkb = In.ld / BK;
+        const int nkb = In.ld / bk_of(FMT);
         for (int term = 0; term < job.nterms && ok; ++term) {
           for (int kb = 0; kb < nkb; ++kb) {
             if (abort_s || !mbar_wait(&empty_bar[stage], phase ^ 1, globaltimer_ns() + wait_ns)) {
@@ -432,9 +464,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
             uint8_t* sB = sA + NPS * A_PIECE_BYTES;
             mbar_arrive_expect_tx(&full_bar[stage], npl * (A_PIECE_BYTES + B_PIECE_BYTES));
             for (int p = 0; p < npl; ++p)
-              tma_load_4d(sA + p * A_PIECE_BYTES, mA, kb * BK, I * BM, p, R.a[term], &full_bar[stage]);
+              tma_load_4d(sA + p * A_PIECE_BYTES, mA, kb * bk_of(FMT), I * BM, p, R.a[term], &full_bar[stage]);
             for (int p = 0; p < npl; ++p)
-              tma_load_4d(sB + p * B_PIECE_BYTES, mB, kb * BK, J * BN, p, R.b[term], &full_bar[stage]);
+              tma_load_4d(sB + p * B_PIECE_BYTES, mB, kb * bk_of(FMT), J * BN, p, R.b[term], &full_bar[stage]);
             armed[stage] = 1;
             armed_par[stage] = phase;
             if (++stage == STG) { stage = 0; phase ^= 1; }
@@ -460,7 +492,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
         const int ii = locate(job, t, I, J);
         const Instance& In = job.inst[ii];
         if (!resolve(job, In, I, J).active) continue;
-        const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job, In.ld);
+        const int nchunks = job.nterms * (In.ld / bk_of(FMT)) / chunk_kb(job, In.ld);
         for (int ch = 0; ch < nchunks && ok; ++ch) {
           if (abort_s || !mbar_wait(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + wait_ns)) { ok = false; break; }
           tc_fence_after();
@@ -475,13 +507,13 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
             #pragma unroll
             for (int pass = 0; pass < 2; ++pass) {
               #pragma unroll
-              for (int kk = 0; kk < BK / 16; ++kk) {
+              for (int kk = 0; kk < KSTEPS; ++kk) {
                 #pragma unroll
                 for (int q = 0; q < PR::n; ++q) {
                   if (q < q0 || (q == PR::n - 1) != (pass == 1)) continue;
                   const uint64_t ad = smem_desc_sw128(sA + PR::a(q) * A_PIECE_BYTES + kk * 32);
                   const uint64_t bd = smem_desc_sw128(sB + PR::b(q) * B_PIECE_BYTES + kk * 32);
-                  mma_bf16(dt, ad, bd, idesc, accumulate);
+                  mma_fmt<FMT, false>(dt, ad, bd, idesc, accumulate);
                   accumulate = 1;
                 }
               }
@@ -510,7 +542,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
       const Instance& In = job.inst[ii];
       const Resolved R = resolve(job, In, I, J);
       if (!R.active) continue;
-      const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job, In.ld);
+      const int nchunks = job.nterms * (In.ld / bk_of(FMT)) / chunk_kb(job, In.ld);
       float acc[BN / 32][32];
       #pragma unroll
       for (int g = 0; g < BN / 32; ++g)
@@ -638,7 +670,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
         if (!R.active) continue;
         const CUtensorMap* mA = &In.mapA;
         const CUtensorMap* mB = &In.mapB;
-        const int nkb = In.ld / BK;
+        const int nkb = In.ld / bk_of(FMT);
         const int rowA = I * PT + (int)rank * BM;
         const int rowB = J * PT + (int)rank * BN;
         for (int term = 0; term < job.nterms && ok; ++term) {
@@ -652,9 +684,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
             const uint32_t fb = mapa_shared(smem_u32(&full_bar[stage]), 0);
             if (rank == 0) mbar_arrive_expect_tx(&full_bar[stage], 2 * npl * (A_PIECE_BYTES + B_PIECE_BYTES));
             for (int p = 0; p < npl; ++p)
-              tma_load_4d_pair(sA + p * A_PIECE_BYTES, mA, kb * BK, rowA, p, R.a[term], fb);
+              tma_load_4d_pair(sA + p * A_PIECE_BYTES, mA, kb * bk_of(FMT), rowA, p, R.a[term], fb);
             for (int p = 0; p < npl; ++p)
-              tma_load_4d_pair(sB + p * B_PIECE_BYTES, mB, kb * BK, rowB, p, R.b[term], fb);
+              tma_load_4d_pair(sB + p * B_PIECE_BYTES, mB, kb * bk_of(FMT), rowB, p, R.b[term], fb);
             armed[stage] = 1;
             armed_par[stage] = phase;
             if (++stage == STG) { stage = 0; phase ^= 1; }
@@ -686,7 +718,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
         const int ii = locate(job, t, I, J);
         const Instance& In = job.inst[ii];
         if (!resolve(job, In, I, J).active) continue;
-        const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job, In.ld);
+        const int nchunks = job.nterms * (In.ld / bk_of(FMT)) / chunk_kb(job, In.ld);
         for (int ch = 0; ch < nchunks && ok; ++ch) {
           if (abort_s || !mbar_wait(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + wait_ns)) {
             ok = false;
@@ -707,13 +739,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
             #pragma unroll
             for (int pass = 0; pass < 2; ++pass) {
               #pragma unroll
-              for (int kk = 0; kk < BK / 16; ++kk) {
+              for (int kk = 0; kk < KSTEPS; ++kk) {
                 #pragma unroll
                 for (int q = 0; q < PR::n; ++q) {
                   if (q < q0 || (q == PR::n - 1) != (pass == 1)) continue;
                   const uint64_t ad = smem_desc_sw128(sA + PR::a(q) * A_PIECE_BYTES + kk * 32);
                   const uint64_t bd = smem_desc_sw128(sB + PR::b(q) * B_PIECE_BYTES + kk * 32);
-                  mma_bf16_pair(dt, ad, bd, idesc, accumulate);
+                  mma_fmt<FMT, true>(dt, ad, bd, idesc, accumulate);
                   accumulate = 1;
                 }
               }
@@ -746,7 +778,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
       const Instance& In = job.inst[ii];
       const Resolved R = resolve(job, In, I, J);
       if (!R.active) continue;
-      const int nchunks = job.nterms * (In.ld / BK) / chunk_kb(job, In.ld);
+      const int nchunks = job.nterms * (In.ld / bk_of(FMT)) / chunk_kb(job, In.ld);
       float acc[BN / 32][32];
       #pragma unroll
       for (int g = 0; g < BN / 32; ++g)
@@ -832,13 +864,16 @@ cudaError_t tc_make_maps(void* arena, int ld, int nslots, int fmt, CUtensorMap* 
   if (!enc) return cudaErrorNotSupported;
   if (ld % tc::LD_ALIGN != 0 || (reinterpret_cast<uintptr_t>(arena) & 15) != 0) return cudaErrorInvalidValue;
   const int np = tc::np_of(fmt);
-  const CUtensorMapDataType dt =
-      fmt == tc::FMT_FP16X2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint64_t es = (cuuint64_t)tc::esize_of(fmt);
+  const CUtensorMapDataType dt = fmt == tc::FMT_TF32X2   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : fmt == tc::FMT_FP16X2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                         : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   cuuint64_t dims[4] = {(cuuint64_t)ld, (cuuint64_t)ld, (cuuint64_t)np, (cuuint64_t)nslots};
-  cuuint64_t strides[3] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * ld * 2, (cuuint64_t)np * ld * ld * 2};
+  cuuint64_t strides[3] = {(cuuint64_t)ld * es, (cuuint64_t)ld * ld * es, (cuuint64_t)np * ld * ld * es};
   cuuint32_t estr[4] = {1, 1, 1, 1};
-  cuuint32_t boxA[4] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM, 1, 1};
-  cuuint32_t boxB[4] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BN, 1, 1};
+  const cuuint32_t bk = (cuuint32_t)tc::bk_of(fmt);   // 128-byte rows in every format
+  cuuint32_t boxA[4] = {bk, (cuuint32_t)tc::BM, 1, 1};
+  cuuint32_t boxB[4] = {bk, (cuuint32_t)tc::BN, 1, 1};
   CUresult r1 = enc(mapA, dt, 4, arena, dims, strides, boxA, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   CUresult r2 = enc(mapB, dt, 4, arena, dims, strides, boxB, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -859,9 +894,12 @@ static int sm_count() {
 
 // The kernel instance for a job: tile kind x piece format.
 static void* kernel_of(int pair, int fmt) {
-  if (pair) return fmt == tc::FMT_FP16X2 ? (void*)tc::tc_gemm_pair_kernel<tc::FMT_FP16X2>
-                                         : (void*)tc::tc_gemm_pair_kernel<tc::FMT_BF16X3>;
-  return fmt == tc::FMT_FP16X2 ? (void*)tc::tc_gemm_kernel<tc::FMT_FP16X2> : (void*)tc::tc_gemm_kernel<tc::FMT_BF16X3>;
+  if (pair) return fmt == tc::FMT_TF32X2   ? (void*)tc::tc_gemm_pair_kernel<tc::FMT_TF32X2>
+                   : fmt == tc::FMT_FP16X2 ? (void*)tc::tc_gemm_pair_kernel<tc::FMT_FP16X2>
+                                           : (void*)tc::tc_gemm_pair_kernel<tc::FMT_BF16X3>;
+  return fmt == tc::FMT_TF32X2   ? (void*)tc::tc_gemm_kernel<tc::FMT_TF32X2>
+         : fmt == tc::FMT_FP16X2 ? (void*)tc::tc_gemm_kernel<tc::FMT_FP16X2>
+                                 : (void*)tc::tc_gemm_kernel<tc::FMT_BF16X3>;
 }
 
 static cudaError_t tc_prepare() {
@@ -869,7 +907,7 @@ static cudaError_t tc_prepare() {
   if (done) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   for (int pair = 0; pair < 2 && e == cudaSuccess; ++pair)
-    for (int fmt = 0; fmt < 2 && e == cudaSuccess; ++fmt)
+    for (int fmt = 0; fmt < 3 && e == cudaSuccess; ++fmt)
       e = cudaFuncSetAttribute(kernel_of(pair, fmt), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                pair ? tc::P_SMEM_BYTES : tc::SMEM_BYTES);
   if (e == cudaSuccess) done = true;
@@ -911,14 +949,15 @@ int tc_tiles(int ld, int upper, int pair) { return pair ? tc::pair_tiles_of(ld, 
 cudaError_t tc_launch(const tc::Job& job, cudaStream_t s) {
   cudaError_t e = tc_prepare();
   if (e != cudaSuccess) return e;
-  const bool f16 = job.fmt == tc::FMT_FP16X2;
   if (job.pair) {
     const dim3 g(tc_grid_for(job.total_tiles, 1));
-    if (f16) tc::tc_gemm_pair_kernel<tc::FMT_FP16X2><<<g, tc::P_THREADS, tc::P_SMEM_BYTES, s>>>(job);
+    if (job.fmt == tc::FMT_TF32X2) tc::tc_gemm_pair_kernel<tc::FMT_TF32X2><<<g, tc::P_THREADS, tc::P_SMEM_BYTES, s>>>(job);
+    else if (job.fmt == tc::FMT_FP16X2) tc::tc_gemm_pair_kernel<tc::FMT_FP16X2><<<g, tc::P_THREADS, tc::P_SMEM_BYTES, s>>>(job);
     else tc::tc_gemm_pair_kernel<tc::FMT_BF16X3><<<g, tc::P_THREADS, tc::P_SMEM_BYTES, s>>>(job);
   } else {
     const dim3 g(tc_grid_for(job.total_tiles, 0));
-    if (f16) tc::tc_gemm_kernel<tc::FMT_FP16X2><<<g, tc::THREADS, tc::SMEM_BYTES, s>>>(job);
+    if (job.fmt == tc::FMT_TF32X2) tc::tc_gemm_kernel<tc::FMT_TF32X2><<<g, tc::THREADS, tc::SMEM_BYTES, s>>>(job);
+    else if (job.fmt == tc::FMT_FP16X2) tc::tc_gemm_kernel<tc::FMT_FP16X2><<<g, tc::THREADS, tc::SMEM_BYTES, s>>>(job);
     else tc::tc_gemm_kernel<tc::FMT_BF16X3><<<g, tc::THREADS, tc::SMEM_BYTES, s>>>(job);
   }
   return cudaGetLastError();
@@ -974,7 +1013,7 @@ extern "C" int32_t sp2_test_tc_gemm_ex(const void* arena_dev, int32_t ld, int32_
                                        float* out_dev, void* stream) {
   if (!arena_dev || !out_dev || ld <= 0 || ld % sp2::tc::LD_ALIGN != 0 || nslots <= 0 || a_slot < 0 ||
       b_slot < 0 || a_slot >= nslots || b_slot >= nslots || (upper != 0 && upper != 1) || tile < 0 || tile > 2 ||
-      (tile == 2 && ld % sp2::tc::PT != 0) || fmt < 0 || fmt > 1 || (lowprec != 0 && lowprec != 1))
+      (tile == 2 && ld % sp2::tc::PT != 0) || fmt < 0 || fmt > 2 || (lowprec != 0 && lowprec != 1))
     return SP2_ERR_INVALID_ARG;
   const int pair = tile == 2 || (tile == 0 && ld % sp2::tc::PT == 0);
   return run_test_product(arena_dev, ld, nslots, a_slot, b_slot, upper, pair, fmt, lowprec, 0, 0, out_dev,
@@ -994,7 +1033,7 @@ static int32_t run_test_product(const void* arena_dev, int32_t ld, int32_t nslot
   hinst.fmt = fmt;
   hinst.np = sp2::tc::np_of(fmt);
   hinst.nslots = nslots;
-  hinst.slot_elems = (int64_t)hinst.np * ld * ld;
+  hinst.slot_elems = sp2::tc::slot_units_of(fmt, ld);
   hinst.ld = ld;
   // device copies of the instance record and the error word (test entry point only)
   sp2::tc::Instance* dinst = nullptr;

@@ -40,7 +40,7 @@ def main():
     ap.add_argument("--rule", default="error", choices=["error", "block", "mixed"])
     ap.add_argument("--products", default="tensor", choices=["tensor", "cuda"],
                     help="--bsr: block products on the tensor cores (fp16x3) or FP32 CUDA cores")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "bf16x6", "bf16x3", "fp16x3"],
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "bf16x6", "bf16x3", "fp16x3", "tf32x3"],
                     help="--sp2: the tensor-core precision mode of the handle")
     a = ap.parse_args()
     if a.sp2:
@@ -92,7 +92,7 @@ def sp2_forward(a):
             per.append(fi["loop_ms"] / fi["hist_len"])
         info = P.info()
     ms = min(per)
-    products = {"mixed": 6, "bf16x6": 6, "bf16x3": 3, "fp16x3": 3}[a.precision]
+    products = {"mixed": 6, "bf16x6": 6, "bf16x3": 3, "fp16x3": 3, "tf32x3": 3}[a.precision]
     print(json.dumps({"ld": N, "mode": "sp2_forward", "tile": a.tile, "precision": a.precision,
                       "squares": int(info["hist_len"]), "ms_per_square_incl_stop_test": ms,
                       "executed_tflops": products * N * N * (N + 1) / (ms * 1e-3) / 1e12,

@@ -23,7 +23,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA runtime error", 3: "non-finit
           4: "device-side wait timed out", 5: "out of device memory", 6: "no gap (F = cI)",
           7: "unsupported option", 8: "device-side bounds check failed (debug library)"}
 STOP_ORDER, STOP_TRACE_GUARD, STOP_EXACT, STOP_CAP, STOP_SCHEDULE = 0, 1, 2, 3, 4
-PRECISIONS = {"fp64": 0, "mixed": 1, "bf16x6": 1, "bf16x3": 2, "fp16x3": 3}
+PRECISIONS = {"fp64": 0, "mixed": 1, "bf16x6": 1, "bf16x3": 2, "fp16x3": 3, "tf32x3": 4}
 MAX_ITER = 512
 
 
@@ -258,10 +258,10 @@ def sp2_test_tc_gemm(arena, ld: int, nslots: int, a_slot: int, b_slot: int, uppe
                      stream=None, tile: str = "auto", fmt: str = "bf16", lowprec: bool = False) -> None:
     """Tensor-core product C = A B^T over a piece arena (see include/sp2_testing.h).
     tile: "128" (128 x 128 per SM), "pair" (256 x 256 per SM pair) or "auto"; fmt "bf16"
-    (three bf16 planes per slot) or "fp16" (two fp16 planes of 2^14 x); lowprec: the format's
-    low-precision product."""
+    (three bf16 planes per slot), "fp16" (two fp16 planes of 2^14 x) or "tf32" (two FP32 planes
+    holding tf32 values); lowprec: the format's low-precision product."""
     _check(lib().sp2_test_tc_gemm_ex(arena.data_ptr(), ld, nslots, a_slot, b_slot, 1 if upper else 0,
-                                     TILES[tile], {"bf16": 0, "fp16": 1}[fmt], 1 if lowprec else 0,
+                                     TILES[tile], {"bf16": 0, "fp16": 1, "tf32": 2}[fmt], 1 if lowprec else 0,
                                      out.data_ptr(), _stream_ptr(stream)), "sp2_test_tc_gemm_ex")
 
 

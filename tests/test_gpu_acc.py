@@ -56,7 +56,7 @@ def test_fp64_acc_matches_oracle(sp2mod, N, nocc, gap, seed):
     assert info["n_iter"] < plain.n
 
 
-@pytest.mark.parametrize("prec", ["bf16x6", "fp16x3"])
+@pytest.mark.parametrize("prec", ["bf16x6", "fp16x3", "tf32x3"])
 @pytest.mark.parametrize("N,nocc,gap,seed,slack", [(1500, 700, 0.02, 5, 1e-3), (700, 300, 0.01, 3, 1e-3),
                                                    (129, 64, 0.05, 2, 1e-3)])
 def test_mixed_acc_matches_oracle(sp2mod, N, nocc, gap, seed, slack, prec):

@@ -1,6 +1,7 @@
 """Parity of the tensor-core path (squares, correction, refinement) with the CPU oracle,
 through the C ABI, in its FP32-grade precision modes: bf16x6 (three bf16 pieces, six piece
-products) and fp16x3 (two scaled fp16 pieces, three piece products).
+products), fp16x3 (two scaled fp16 pieces, three piece products) and tf32x3 (two tf32 pieces,
+three piece products on kind::tf32 tensor cores).
 
 Tolerance: ||D - D_ref||_F / sqrt(nocc) <= 1e-6 against the FP64 oracle.
 
@@ -14,9 +15,12 @@ alternating pair (v_i ~ C v_{i-2}^2), so a higher floor is met at most one pair 
 earlier.  At the floor every stop condition compares rounding-level values: the trace choice
 there can delay the alternation the order test needs, and the trace guard's own condition (the
 order estimate over the last pair below q~) becomes certain only once v_{i-3} has reached the
-floor too, up to two squares after v did, on either side.  Window: n32 - 3 <= n <= n32 + 2, and
-never after the FP64 oracle's stop; measured over 21 dense inputs (N = 2 .. 3000), both
-FP32-grade modes and both tile kinds: -3 .. +2, all at or before the FP64 stop.
+floor too, up to two squares after v did, on either side.  An iterate that becomes exactly
+idempotent (v = 0, as tf32x3 reaches on the 2 x 2 input) keeps its polynomial, and the stop
+then waits for the guard's order condition on v_{i-3} = 0: three squares.  Window:
+n32 - 3 <= n <= n32 + 3, and never after the FP64 oracle's stop; measured over 21 dense inputs
+(N = 2 .. 3000), every FP32-grade mode and both tile kinds: bf16x6 and fp16x3 -3 .. +2, tf32x3
+-3 .. +1 and +3 on N = 2, all at or before the FP64 stop.
 """
 import math
 
@@ -29,7 +33,7 @@ from paper_1507_02087_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 TOL_MIXED = 1e-6
-FP32_GRADE = ["bf16x6", "fp16x3"]
+FP32_GRADE = ["bf16x6", "fp16x3", "tf32x3"]
 
 
 @pytest.fixture(scope="module")
@@ -44,7 +48,7 @@ def assert_stop(n, F, nocc, bounds=None, ref=None):
     F = F.cpu().numpy() if isinstance(F, torch.Tensor) else np.asarray(F)
     ref32 = o.sp2(F, nocc, storage="fp32", trace="fro", bounds=bounds)
     ref = ref if ref is not None else o.sp2(F, nocc, bounds=bounds)
-    assert ref32.n - 3 <= n <= ref32.n + 2, (n, ref32.n)
+    assert ref32.n - 3 <= n <= ref32.n + 3, (n, ref32.n)
     assert n <= ref.n, (n, ref.n)
 
 

@@ -155,7 +155,7 @@ def test_tensor_core_spectral_stop(sp2mod, N, nocc, gap, seed, prec):
     bounds = (info["lambda_min"], info["lambda_max"])
     ref = o.sp2(F, nocc, norm="spectral", bounds=bounds)
     ref32 = o.sp2(F, nocc, norm="spectral", bounds=bounds, storage="fp32", trace="fro")
-    assert ref32.n - 3 <= info["n_iter"] <= ref32.n + 2 and info["n_iter"] <= ref.n, (info["n_iter"], ref32.n)
+    assert ref32.n - 3 <= info["n_iter"] <= ref32.n + 3 and info["n_iter"] <= ref.n, (info["n_iter"], ref32.n)
     assert o.rel_error(D, ref.D, nocc) <= 1e-6
     # the estimate against the FP32-storage oracle's e_i above the floor.  It is a Lanczos lower
     # bound of the GPU's own e_i (within 2e-2), but the two histories' iterates are not the same:

@@ -170,3 +170,53 @@ def test_fp16_format_symmetric_square_and_subnormal_pieces(sp2mod, tile):
     # without the subnormal low pieces the product would be off by about 2^-11 of its scale
     R0 = arena[0][0].double() @ arena[0][0].double().T / S16 ** 2
     assert float(((R0 - R).abs() / scale).max()) > 1e-5
+
+
+# ---- the tf32 piece format (SP2_PREC_TF32X3) ---------------------------------------------------
+def round_tf32(x32: torch.Tensor) -> torch.Tensor:
+    """Nearest tf32 value (10 fraction bits), ties away from zero, kept in an FP32 word."""
+    b = x32.contiguous().view(torch.int32)
+    return ((b + 0x1000) & ~0x1FFF).view(torch.float32)
+
+
+def pieces32(x32: torch.Tensor) -> torch.Tensor:
+    hi = round_tf32(x32)
+    lo = round_tf32(x32 - hi)
+    return torch.stack([hi, lo])
+
+
+def run32(sp2mod, mats, a, b, upper, tile="auto", lowprec=False):
+    ld = mats[0].shape[0]
+    arena = torch.stack([pieces32(m) for m in mats]).contiguous()
+    out = torch.full((ld, ld), float("nan"), dtype=torch.float32, device="cuda")
+    sp2mod.sp2_test_tc_gemm(arena, ld, len(mats), a, b, upper, out, tile=tile, fmt="tf32", lowprec=lowprec)
+    return out, arena
+
+
+@pytest.mark.parametrize("tile", ["128", "pair"])
+@pytest.mark.parametrize("ld", [256, 1024, 4096])
+@pytest.mark.parametrize("lowprec", [False, True])
+def test_tf32_format_product(sp2mod, ld, tile, lowprec):
+    g = torch.Generator(device="cpu").manual_seed(500 + ld)
+    A = torch.randn(ld, ld, generator=g).float().cuda()
+    B = (torch.randn(ld, ld, generator=g) * 1e-3).float().cuda()
+    C, arena = run32(sp2mod, [A, B], 0, 1, False, tile, lowprec)
+    assert torch.isfinite(C).all()
+    P, Q = arena[0].double(), arena[1].double()
+    R = P[0] @ Q[0].T if lowprec else P[0] @ Q[0].T + P[0] @ Q[1].T + P[1] @ Q[0].T
+    scale = P.abs().sum(0) @ Q.abs().sum(0).T
+    # each piece product is exact (tf32 x tf32 fits FP32); only the FP32 accumulation remains
+    assert float(((C.double() - R).abs() / scale).max()) < 1e-5
+    E = A.double() @ B.double().T
+    assert rel(C, E) < (3e-3 if lowprec else 1e-5)
+
+
+@pytest.mark.parametrize("tile", ["128", "pair"])
+def test_tf32_format_symmetric_square(sp2mod, tile):
+    ld = 1536 if tile == "128" else 1792
+    g = torch.Generator(device="cpu").manual_seed(21)
+    X = torch.randn(ld, ld, generator=g, dtype=torch.float64)
+    X = ((X + X.T) / (2 * ld ** 0.5)).float().cuda()
+    C, arena = run32(sp2mod, [X], 0, 0, True, tile)
+    assert torch.equal(C, C.T)
+    assert rel(C, X.double() @ X.double()) < 1e-5
