@@ -61,14 +61,13 @@ __host__ __device__ constexpr int64_t slot_units_of(int fmt, int64_t ld) {
 }
 // The tensor cores' FP32 accumulation drops the bits an addend loses in alignment
 // (it rounds toward zero), so a long sum of same-sign products drifts low by about
-// K * 2^-25 of its value.  The MMAs therefore accumulate a chunk of k-blocks (CHUNK_KB,
+// K * 2^-25 of its value.  The MMAs therefore accumulate a chunk of k-terms (CHUNK_TERMS,
 // 64 terms, for full products; see chunk_kb for the others) at a time into one of the
 // tensor-memory buffers, and the epilogue adds the chunk sums into registers with
 // round-to-nearest FP32 additions.  Within a ring stage the smaller piece products are
 // issued before the leading one (p0 q0), so that they are added while the accumulator is
 // still small and lose less to the truncation.
-constexpr int CHUNK_TERMS = 64;
-constexpr int CHUNK_KB = 1;      // CHUNK_TERMS in 16-bit k-blocks (FMT_TF32X2: 2 k-blocks)
+constexpr int CHUNK_TERMS = 64;  // one 16-bit k-block, two FMT_TF32X2 k-blocks
 constexpr int NBUF = 4;
 constexpr int A_PIECE_BYTES = BM * ROW_BYTES;
 constexpr int B_PIECE_BYTES = BN * ROW_BYTES;

@@ -8,7 +8,7 @@
 // Warp 0 feeds a TMA ring of 2 (bf16) or 3 (fp16) stages (128-byte swizzle, 64-wide
 // k-blocks; 32-wide blocks with 64-byte swizzle in twice as many stages ran 18 % slower)
 // from the instance's tensor maps; warp 1 issues the MMAs (128 x 128 x 16) and closes a
-// tensor-memory chunk buffer every CHUNK_KB k-blocks; warps 2-5 add each closed chunk
+// tensor-memory chunk buffer every CHUNK_TERMS k-terms; warps 2-5 add each closed chunk
 // into FP32 registers (round to nearest) and, after the last chunk of a tile, run the
 // epilogue.  Four chunk buffers let the MMAs run ahead of the draining.
 //
@@ -148,11 +148,11 @@ __device__ __forceinline__ Resolved resolve(const Job& j, const Instance& I, int
   return r;
 }
 
-// k-blocks per tensor-memory chunk: CHUNK_KB (64 terms) for full products.  (Full fp16 products
+// k-blocks per tensor-memory chunk: CHUNK_TERMS (64 terms) for full products.  (Full fp16 products
 // with 128-term chunks ran 7-15 % faster at N = 8192 but raised the error after the correction
 // from 6.3e-7 to 9.2e-7, too close to the 1e-6 target.)  Low-precision jobs, whose 16-bit (bf16)
 // or 11-bit (fp16) target tolerates a larger bias, take twice (bf16: 3 products per k-step) or
-// four times (fp16: 1) CHUNK_KB.  Halved until the chunks divide the k-blocks of a tile.
+// four times (fp16, tf32: 1) CHUNK_TERMS.  Halved until the chunks divide the k-blocks of a tile.
 // The derivative steps (whole_k) take the tile's whole k range in one chunk: they form a
 // first-order correction, whose own truncation bias (at most K 2^-25 of dX_j) is far below
 // the error it corrects; measured at N = 8192, the error after the correction is the same to
