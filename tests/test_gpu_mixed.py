@@ -17,10 +17,12 @@ there can delay the alternation the order test needs, and the trace guard's own 
 order estimate over the last pair below q~) becomes certain only once v_{i-3} has reached the
 floor too, up to two squares after v did, on either side.  An iterate that becomes exactly
 idempotent (v = 0, as tf32x3 reaches on the 2 x 2 input) keeps its polynomial, and the stop
-then waits for the guard's order condition on v_{i-3} = 0: three squares.  Window:
-n32 - 3 <= n <= n32 + 3, and never after the FP64 oracle's stop; measured over 21 dense inputs
-(N = 2 .. 3000), every FP32-grade mode and both tile kinds: bf16x6 and fp16x3 -3 .. +2, tf32x3
--3 .. +1 and +3 on N = 2, all at or before the FP64 stop.
+then waits for the guard's order condition on v_{i-3} = 0: three squares, which can be one
+square after the FP64 oracle, whose iterate keeps a rounding-level v > 0 and stops by the order
+test.  Window: n32 - 3 <= n <= n32 + 3; never after the FP64 oracle's stop, or one square after
+it once the run's own history holds v = 0.  Measured over 21 dense inputs (N = 2 .. 3000), every
+FP32-grade mode and both tile kinds: bf16x6 and fp16x3 -3 .. +2, tf32x3 -3 .. +1 and +3 on N = 2
+(13 squares against the FP64 oracle's 12); every other run at or before the FP64 stop.
 """
 import math
 
@@ -43,13 +45,17 @@ def sp2mod():
     return sp2
 
 
-def assert_stop(n, F, nocc, bounds=None, ref=None):
-    """The stopping iteration against the FP32-storage oracle (window in the module notes)."""
+def assert_stop(n, F, nocc, bounds=None, ref=None, v=None):
+    """The stopping iteration against the FP32-storage oracle (window in the module notes).
+
+    v is the run's own history of v_i; a run whose iterate became exactly idempotent (some
+    v_i = 0) may stop one square after the FP64 oracle, every other run at or before it."""
     F = F.cpu().numpy() if isinstance(F, torch.Tensor) else np.asarray(F)
     ref32 = o.sp2(F, nocc, storage="fp32", trace="fro", bounds=bounds)
     ref = ref if ref is not None else o.sp2(F, nocc, bounds=bounds)
     assert ref32.n - 3 <= n <= ref32.n + 3, (n, ref32.n)
-    assert n <= ref.n, (n, ref.n)
+    exact = v is not None and bool(np.any(np.asarray(v)[:n + 1] == 0.0))
+    assert n <= ref.n + (1 if exact else 0), (n, ref.n, exact)
 
 
 def run_gpu(sp2mod, F, nocc, prec="bf16x6", **opts):
@@ -71,7 +77,7 @@ def test_mixed_small_and_ragged(sp2mod, N, nocc, gap, prec):
     D, info = run_gpu(sp2mod, F, nocc, prec)
     assert info["status"] == 0
     assert info["stop_reason"] in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
-    assert_stop(info["n_iter"], F, nocc, ref=ref)
+    assert_stop(info["n_iter"], F, nocc, ref=ref, v=info["v"])
     assert o.rel_error(D.cpu().numpy(), ref.D, nocc) <= TOL_MIXED
     assert torch.equal(D, D.T)
 
@@ -86,7 +92,7 @@ def test_stop_window_edges(sp2mod, N, nocc, gap, seed, prec):
     ref = o.sp2(F, nocc)
     D, info = run_gpu(sp2mod, F, nocc, prec)
     assert info["status"] == 0 and info["stop_reason"] in (o.STOP_ORDER, o.STOP_TRACE_GUARD)
-    assert_stop(info["n_iter"], F, nocc, ref=ref)
+    assert_stop(info["n_iter"], F, nocc, ref=ref, v=info["v"])
     assert o.rel_error(D.cpu().numpy(), ref.D, nocc) <= TOL_MIXED
 
 
@@ -96,7 +102,7 @@ def test_mixed_n400(sp2mod, prec):
     ref = o.sp2(case.F.numpy(), case.nocc)
     D, info = run_gpu(sp2mod, case.F, case.nocc, prec)
     assert info["status"] == 0
-    assert_stop(info["n_iter"], case.F, case.nocc, ref=ref)
+    assert_stop(info["n_iter"], case.F, case.nocc, ref=ref, v=info["v"])
     assert o.rel_error(D.cpu().numpy(), ref.D, case.nocc) <= TOL_MIXED
     inv = o.invariants(case.F.numpy(), D.cpu().numpy(), case.nocc)
     assert inv["trace_err"] < 1e-3 and inv["idem_err"] < 1e-4 and inv["comm_err"] < 1e-4
@@ -108,7 +114,7 @@ def test_mixed_n2048_small_gap(sp2mod, prec):
     ref = o.sp2(case.F.numpy(), 1024)
     D, info = run_gpu(sp2mod, case.F, 1024, prec)
     assert info["status"] == 0
-    assert_stop(info["n_iter"], case.F, 1024, ref=ref)
+    assert_stop(info["n_iter"], case.F, 1024, ref=ref, v=info["v"])
     assert o.rel_error(D.cpu().numpy(), ref.D, 1024) <= TOL_MIXED
 
 
@@ -174,7 +180,7 @@ def test_mixed_tile_kinds(sp2mod, N, nocc, tile, prec):
     ref = o.sp2(case.F.numpy(), nocc)
     D, info = run_gpu(sp2mod, case.F, nocc, prec, tile=tile)
     assert info["status"] == 0
-    assert_stop(info["n_iter"], case.F, nocc, ref=ref)
+    assert_stop(info["n_iter"], case.F, nocc, ref=ref, v=info["v"])
     assert o.rel_error(D.cpu().numpy(), ref.D, nocc) <= TOL_MIXED
     assert torch.equal(D, D.T)
 
@@ -190,7 +196,7 @@ def test_batch_with_pair_tiles(sp2mod, prec):
     for c, k, D, info in zip(cases, noccs, Ds, infos):
         ref = o.sp2(c.F.numpy(), k)
         assert info["status"] == 0
-        assert_stop(info["n_iter"], c.F, k, ref=ref)
+        assert_stop(info["n_iter"], c.F, k, ref=ref, v=info["v"])
         assert o.rel_error(D.cpu().numpy(), ref.D, k) <= TOL_MIXED
 
 
@@ -299,7 +305,7 @@ def test_mixed_caller_bounds_save_squares(sp2mod):
         assert P.info()["n_iter"] == n_gersh
     assert (info["lambda_min"], info["lambda_max"]) == tight
     assert info["status"] == 0 and info["n_iter"] < n_gersh
-    assert_stop(info["n_iter"], case.F, 500, bounds=tight, ref=ref)
+    assert_stop(info["n_iter"], case.F, 500, bounds=tight, ref=ref, v=info["v"])
     assert o.rel_error(D, ref.D, 500) <= TOL_MIXED
     # batches: per problem, the others keep their Gershgorin bounds
     cases = [inputs.dense_gapped(N, k, gap=0.05, seed=s) for N, k, s in [(256, 100, 1), (512, 250, 2)]]
