@@ -76,6 +76,17 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;   // + alignment slack
 __host__ __device__ constexpr int stage_bytes_of(int fmt) { return np_of(fmt) * (A_PIECE_BYTES + B_PIECE_BYTES); }
 static_assert(stages_of(FMT_FP16X2) * stage_bytes_of(FMT_FP16X2) == STAGES * STAGE_BYTES,
               "both formats use the same shared-memory ring size");
+// Ring geometry of one job: a stage holds the pieces the job loads of each operand (npl: all of
+// them for full products, fewer for low-precision ones), and the ring takes as many such stages
+// as fit in its bytes, up to MAX_STAGES (full products: 2 bf16 or 3 fp16 / tf32 stages; one-piece
+// low-precision products: 6).
+constexpr int MAX_STAGES = 6;
+__host__ __device__ constexpr int ring_stage_bytes(int npl) { return npl * (A_PIECE_BYTES + B_PIECE_BYTES); }
+__host__ __device__ constexpr int ring_stages(int npl) {
+  return STAGES * STAGE_BYTES / ring_stage_bytes(npl) < MAX_STAGES ? STAGES * STAGE_BYTES / ring_stage_bytes(npl)
+                                                                   : MAX_STAGES;
+}
+static_assert(ring_stages(1) == MAX_STAGES && ring_stages(2) == 3 && ring_stages(3) == 2, "ring geometry");
 constexpr int THREADS = 192;     // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
 constexpr int TMEM_COLS = NBUF * BN;   // four 128 x 128 fp32 chunk accumulators
 constexpr int LD_ALIGN = 128;    // ld is a multiple of the tile size

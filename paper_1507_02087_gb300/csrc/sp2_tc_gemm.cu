@@ -400,11 +400,13 @@ __device__ __forceinline__ void epilogue_chunk(const Job& job, const Instance& I
 
 template <int FMT>
 __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
-  constexpr int STG = stages_of(FMT), SBYTES = stage_bytes_of(FMT), NPS = np_of(FMT);
+  // the job's ring: stages of the pieces it loads (ring_stages in sp2_tc.cuh)
+  const int npl = pieces_loaded<FMT>(job);
+  const int stg = ring_stages(npl), sbytes = ring_stage_bytes(npl);
   using PR = Products<FMT>;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[STG];
-  __shared__ __align__(8) uint64_t empty_bar[STG];
+  __shared__ __align__(8) uint64_t full_bar[MAX_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[MAX_STAGES];
   __shared__ __align__(8) uint64_t accf_bar[NBUF];
   __shared__ __align__(8) uint64_t acce_bar[NBUF];
   __shared__ __align__(8) uint64_t drain_bar;
@@ -415,7 +417,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t wait_ns = job.wait_ms > 0 ? (uint64_t)job.wait_ms * 1000000ull : kWaitNs;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STG; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int s = 0; s < MAX_STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
     for (int a = 0; a < NBUF; ++a) { mbar_init(&accf_bar[a], 1); mbar_init(&acce_bar[a], 4); }
     mbar_init(&drain_bar, 1);
     abort_s = 0;
@@ -431,13 +433,12 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      const int npl = pieces_loaded<FMT>(job);   // pieces loaded per operand
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      int armed[STG];
-      uint32_t armed_par[STG];
-      for (int s = 0; s < STG; ++s) { armed[s] = 0; armed_par[s] = 0; }
+      int armed[MAX_STAGES];
+      uint32_t armed_par[MAX_STAGES];
+      for (int s = 0; s < MAX_STAGES; ++s) { armed[s] = 0; armed_par[s] = 0; }
       bool skip_first = job.test_skip != 0 && blockIdx.x == 0;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int I, J;
@@ -457,11 +458,11 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
             if (skip_first) {   // testing hook: this stage stays unarmed, the MMA thread's wait gives up
               skip_first = false;
               armed[stage] = 0;
-              if (++stage == STG) { stage = 0; phase ^= 1; }
+              if (++stage == stg) { stage = 0; phase ^= 1; }
               continue;
             }
-            uint8_t* sA = smem + stage * SBYTES;
-            uint8_t* sB = sA + NPS * A_PIECE_BYTES;
+            uint8_t* sA = smem + stage * sbytes;
+            uint8_t* sB = sA + npl * A_PIECE_BYTES;
             mbar_arrive_expect_tx(&full_bar[stage], npl * (A_PIECE_BYTES + B_PIECE_BYTES));
             for (int p = 0; p < npl; ++p)
               tma_load_4d(sA + p * A_PIECE_BYTES, mA, kb * bk_of(FMT), I * BM, p, R.a[term], &full_bar[stage]);
@@ -469,13 +470,13 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
               tma_load_4d(sB + p * B_PIECE_BYTES, mB, kb * bk_of(FMT), J * BN, p, R.b[term], &full_bar[stage]);
             armed[stage] = 1;
             armed_par[stage] = phase;
-            if (++stage == STG) { stage = 0; phase ^= 1; }
+            if (++stage == stg) { stage = 0; phase ^= 1; }
           }
         }
       }
       if (!ok) { abort_s = 1; atomicExch(job.err, (int)SP2_ERR_TIMEOUT); }
       // wait (bounded) until every copy issued here has landed
-      for (int s = 0; s < STG; ++s)
+      for (int s = 0; s < stg; ++s)
         if (armed[s]) mbar_wait(&full_bar[s], armed_par[s], globaltimer_ns() + wait_ns);
     }
   } else if (warp == 1) {
@@ -502,8 +503,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
             if (abort_s || !mbar_wait(&full_bar[stage], phase, globaltimer_ns() + wait_ns) ||
                 (kc == 0 && !mbar_wait(&acce_bar[buf], bphase ^ 1, globaltimer_ns() + wait_ns))) { ok = false; break; }
             tc_fence_after();
-            const uint32_t sA = smem_u32(smem + stage * SBYTES);
-            const uint32_t sB = sA + NPS * A_PIECE_BYTES;
+            const uint32_t sA = smem_u32(smem + stage * sbytes);
+            const uint32_t sB = sA + npl * A_PIECE_BYTES;
             // the stage's smaller piece products first, then the leading one (p0 q0, the last)
             #pragma unroll
             for (int pass = 0; pass < 2; ++pass) {
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const Job job) {
               }
             }
             mma_commit(&empty_bar[stage]);
-            if (++stage == STG) { stage = 0; phase ^= 1; }
+            if (++stage == stg) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
           mma_commit(&accf_bar[buf]);
@@ -622,11 +623,13 @@ constexpr int P_SMEM_BYTES = STAGES * STAGE_BYTES + 8192 + 1024;   // + alignmen
 
 template <int FMT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gemm_pair_kernel(const Job job) {
-  constexpr int STG = stages_of(FMT), SBYTES = stage_bytes_of(FMT), NPS = np_of(FMT);
+  // the job's ring: stages of the pieces it loads (ring_stages in sp2_tc.cuh)
+  const int npl = pieces_loaded<FMT>(job);
+  const int stg = ring_stages(npl), sbytes = ring_stage_bytes(npl);
   using PR = Products<FMT>;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[STG];
-  __shared__ __align__(8) uint64_t empty_bar[STG];
+  __shared__ __align__(8) uint64_t full_bar[MAX_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[MAX_STAGES];
   __shared__ __align__(8) uint64_t accf_bar[P_NBUF];
   __shared__ __align__(8) uint64_t acce_bar[P_NBUF];
   __shared__ __align__(8) uint64_t drain_bar;
@@ -639,7 +642,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
   const uint32_t rank = cluster_ctarank();
   const int pair_id = blockIdx.x >> 1, npairs = gridDim.x >> 1;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STG; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int s = 0; s < MAX_STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
     for (int a = 0; a < P_NBUF; ++a) { mbar_init(&accf_bar[a], 1); mbar_init(&acce_bar[a], 2 * P_EPI_WARPS); }
     mbar_init(&drain_bar, 1);
     abort_s = 0;
@@ -656,13 +659,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
    if (warp == 0) {
     // ---------------- TMA producer (both CTAs) ----------------
     if (lane == 0) {
-      const int npl = pieces_loaded<FMT>(job);   // pieces loaded per operand
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      int armed[STG];
-      uint32_t armed_par[STG];
-      for (int s = 0; s < STG; ++s) { armed[s] = 0; armed_par[s] = 0; }
+      int armed[MAX_STAGES];
+      uint32_t armed_par[MAX_STAGES];
+      for (int s = 0; s < MAX_STAGES; ++s) { armed[s] = 0; armed_par[s] = 0; }
       for (int t = pair_id; t < ntiles && ok; t += npairs) {
         int I, J;
         const int ii = locate(job, t, I, J);
@@ -680,8 +682,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
               ok = false;
               break;
             }
-            uint8_t* sA = smem + stage * SBYTES;
-            uint8_t* sB = sA + NPS * A_PIECE_BYTES;
+            uint8_t* sA = smem + stage * sbytes;
+            uint8_t* sB = sA + npl * A_PIECE_BYTES;
             const uint32_t fb = mapa_shared(smem_u32(&full_bar[stage]), 0);
             if (rank == 0) mbar_arrive_expect_tx(&full_bar[stage], 2 * npl * (A_PIECE_BYTES + B_PIECE_BYTES));
             for (int p = 0; p < npl; ++p)
@@ -690,7 +692,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
               tma_load_4d_pair(sB + p * B_PIECE_BYTES, mB, kb * bk_of(FMT), rowB, p, R.b[term], fb);
             armed[stage] = 1;
             armed_par[stage] = phase;
-            if (++stage == STG) { stage = 0; phase ^= 1; }
+            if (++stage == stg) { stage = 0; phase ^= 1; }
           }
         }
       }
@@ -703,7 +705,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
         while (globaltimer_ns() < until) {}
       }
       if (rank == 0)
-        for (int s = 0; s < STG; ++s)
+        for (int s = 0; s < stg; ++s)
           if (armed[s]) mbar_wait(&full_bar[s], armed_par[s], globaltimer_ns() + wait_ns);
     }
   } else if (warp == 1) {
@@ -734,8 +736,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
               break;
             }
             tc_fence_after();
-            const uint32_t sA = smem_u32(smem + stage * SBYTES);
-            const uint32_t sB = sA + NPS * A_PIECE_BYTES;
+            const uint32_t sA = smem_u32(smem + stage * sbytes);
+            const uint32_t sB = sA + npl * A_PIECE_BYTES;
             // the stage's smaller piece products first, then the leading one (p0 q0, the last)
             #pragma unroll
             for (int pass = 0; pass < 2; ++pass) {
@@ -752,7 +754,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) tc_gem
               }
             }
             mma_commit_pair_mc(&empty_bar[stage], 0x3);
-            if (++stage == STG) { stage = 0; phase ^= 1; }
+            if (++stage == stg) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
           mma_commit_pair_mc(&accf_bar[buf], 0x3);
