@@ -57,7 +57,7 @@ def workload_name(N, nocc, gap):
 
 # DRAM bytes (read + write) of one forward-square launch from an ncu capture of the current
 # kernel (profiles/tc_gemm_pair_sp2_forward_dram_ld8192.md), keyed by (N, tile kind, precision).
-FWD_TRAFFIC_BYTES = {(8192, "pair", "fp16x3"): 1.522e9 + 261.0e6}
+FWD_TRAFFIC_BYTES = {(8192, "pair", "fp16x3"): 1.510e9 + 260.6e6}
 FP32_FLOP_PER_CLK_SM = 256     # 128 FP32 FMA lanes per SM
 
 
