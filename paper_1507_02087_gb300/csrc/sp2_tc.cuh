@@ -50,7 +50,7 @@ constexpr int BK = 64;           // k-block of the 16-bit formats: 64 values = 1
 constexpr int ROW_BYTES = 128;   // one k-block row of any format (FMT_TF32X2: 32 values)
 constexpr int KSTEPS = 4;        // MMAs per k-block row and product: 32 B each (16 16-bit or 8 tf32 values)
 constexpr int NP = 3;            // pieces per matrix (FMT_BF16X3; the two-piece formats have 2)
-constexpr int STAGES = 2;        // TMA ring depth (FMT_BF16X3; the two-piece formats, with smaller stages, 3)
+constexpr int STAGES = 2;        // ring of full FMT_BF16X3 products (its bytes bound every job's ring: ring_stages)
 __host__ __device__ constexpr int np_of(int fmt) { return fmt == FMT_BF16X3 ? 3 : 2; }
 __host__ __device__ constexpr int stages_of(int fmt) { return fmt == FMT_BF16X3 ? 2 : 3; }
 __host__ __device__ constexpr int esize_of(int fmt) { return fmt == FMT_TF32X2 ? 4 : 2; }   // bytes per value

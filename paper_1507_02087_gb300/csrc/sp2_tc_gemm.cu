@@ -5,9 +5,9 @@
 // panels; X symmetric makes X X^T = X^2), as the format's piece products.
 // One CTA per SM walks the global tile list (the tiles of every instance, largest
 // instances first); tiles of instances that have already stopped are skipped.
-// Warp 0 feeds a TMA ring of 2 (bf16) or 3 (fp16) stages (128-byte swizzle, 64-wide
-// k-blocks; 32-wide blocks with 64-byte swizzle in twice as many stages ran 18 % slower)
-// from the instance's tensor maps; warp 1 issues the MMAs (128 x 128 x 16) and closes a
+// Warp 0 feeds a TMA ring (128-byte swizzle, 64-wide k-blocks; 32-wide blocks with 64-byte
+// swizzle in twice as many stages ran 18 % slower) from the instance's tensor maps, whose stages
+// hold the pieces the job loads (ring_stages: 2 to 6 stages); warp 1 issues the MMAs (128 x 128 x 16) and closes a
 // tensor-memory chunk buffer every CHUNK_TERMS k-terms; warps 2-5 add each closed chunk
 // into FP32 registers (round to nearest) and, after the last chunk of a tile, run the
 // epilogue.  Four chunk buffers let the MMAs run ahead of the draining.
