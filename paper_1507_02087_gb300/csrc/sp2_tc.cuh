@@ -1,7 +1,7 @@
 // Tensor-core (tcgen05) path: definitions shared by the GEMM kernel, the batched
 // elementwise kernels and the host side.
 //
-// Matrices on this path are FP32 values stored as 16-bit "pieces", in one of two formats:
+// Matrices on this path are FP32 values stored as "pieces", in one of three formats:
 //  * FMT_BF16X3: three bf16 pieces x = (p0 + p1) + p2 (p0 = bf16(x), p1 = bf16(x - p0),
 //    p2 = x - p0 - p1; each difference is exact in FP32 and the last one fits in bf16),
 //    so the FP32 value is stored exactly.  A full product X Y^T is the sum of the six
