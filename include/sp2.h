@@ -47,7 +47,7 @@ typedef enum {
   SP2_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
   SP2_ERR_NOMEM = 5,        /* workspace allocation failed */
   SP2_ERR_NO_GAP = 6,       /* lmax == lmin with 0 < n_occ < N: F = cI has no gap */
-  SP2_ERR_UNSUPPORTED = 7,  /* option not available in this build */
+  SP2_ERR_UNSUPPORTED = 7,  /* option not supported on this path or handle */
   SP2_ERR_BOUNDS = 8        /* debug library only (libsp2_debug.so, sp2_build_device_checks):
                                a device-side index failed its bounds check and the access it
                                guarded was skipped; the run's results are not valid */

@@ -156,7 +156,7 @@ def test_dense_n2048_against_oracle(sp2mod):
 
 def fermi_degenerate_case(N=64, nocc=32, seed=5):
     # eigenvalues nocc - 1 and nocc coincide at 0: no gap at the occupation boundary, so no
-    # expansion can separate the pair (SURVEY-planned non-convergence case)
+    # expansion can separate the pair: the non-convergence case
     g = inputs.rng(seed)
     lam = np.concatenate([g.uniform(-1, -0.05, nocc - 1), [0.0, 0.0], g.uniform(0.05, 1, N - nocc - 1)])
     return inputs.dense_from_spectrum(lam, nocc, seed=seed)
